@@ -1,0 +1,87 @@
+"""Setup and solve pipeline of the oracle, mirroring the library boundary:
+setup(mesh, coefficients, k, partition, overlap, tau) -> handle;
+solve(handle, rhs, tol) -> u, iterations, residual history, true residual.
+
+Setup follows the paper's order: Galerkin matrices (Sec. 2.1), overlapping
+decomposition and partition of unity (Def. 2.3, 3.2, 2.7), local
+eigenproblems (Eq. 5.12) and coarse space (Def. 5.1), preconditioner
+(Eq. 2.22-2.23).  Solve is right-preconditioned FGMRES.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import decomposition, fem, geneo, schwarz
+from .fgmres import fgmres
+
+
+@dataclass
+class OracleHandle:
+    B: object
+    Dk: object
+    subs: list
+    mu: np.ndarray
+    eigs: list
+    Z: object
+    precond: schwarz.AdditiveSchwarz
+    restart: int
+    max_iters: int
+    Lambda: int
+
+    @property
+    def n(self) -> int:
+        return self.B.shape[0]
+
+    @property
+    def m_i(self):
+        return [e.m for e in self.eigs]
+
+    @property
+    def n0(self) -> int:
+        return int(sum(self.m_i))
+
+    def kept_eigenvalues(self):
+        return [e.lam[: e.m] for e in self.eigs]
+
+
+def setup(xyz, elems, is_boundary, coeff, k, elem_to_sub, n_sub, overlap=2, tau=0.5,
+          levels="two", weighting="as", restart=50, max_iters=1000) -> OracleHandle:
+    B, Dk, _, _ = fem.helmholtz_matrices(xyz, elems, coeff, is_boundary, k)
+    subs, mu = decomposition.decompose(xyz, elems, is_boundary, elem_to_sub, n_sub, overlap)
+    if mu.min() < 1:
+        raise ValueError("some dof lies in no dof(Omega_i): the partition of unity is undefined")
+    Lam = decomposition.multiplicity_lambda(elems, subs, elems.shape[0])
+    eigs, Z = [], None
+    if levels in ("two", "coarse"):
+        for sd in subs:
+            BN, C, w = geneo.local_pencil(xyz, elems, coeff, is_boundary, k, sd, mu)
+            eigs.append(geneo.local_eigen(BN, C, w, tau))
+        Z = geneo.coarse_basis(subs, eigs, B.shape[0])
+    pc = schwarz.AdditiveSchwarz(B, subs, mu, Z, levels, weighting)
+    return OracleHandle(B, Dk, subs, mu, eigs, Z, pc, restart, max_iters, Lam)
+
+
+def setup_problem(p, levels="two", weighting="as") -> OracleHandle:
+    """Convenience wrapper for a workloads.Problem-like object."""
+    m = p.mesh
+    return setup(m.xyz, m.elems, m.is_boundary, p.coeff, p.k, p.elem_to_sub, p.n_sub,
+                 p.overlap, p.tau, levels, weighting, p.restart, p.max_iters)
+
+
+def load_vector(p) -> np.ndarray:
+    """The problem's right-hand sides as load vectors, (n_rhs, n)."""
+    if p.rhs is not None:
+        return np.atleast_2d(p.rhs)
+    m = p.mesh
+    return fem.load_vector_nodal(m.xyz, m.elems, m.is_boundary, p.f_nodal)[None, :]
+
+
+def solve(h: OracleHandle, rhs: np.ndarray, tol=1e-8):
+    """Solves each right-hand side (rows of rhs) independently."""
+    rhs = np.atleast_2d(rhs)
+    out = []
+    for f in rhs:
+        out.append(fgmres(lambda v: h.B @ v, h.precond.apply, f, tol, h.restart, h.max_iters))
+    return out
