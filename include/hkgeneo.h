@@ -1,0 +1,167 @@
+/*
+ * hkgeneo.h - C ABI of the GB300 (sm_103a) solver for the indefinite Helmholtz
+ * problem  -div(A grad u) - k^2 u = f in Omega,  u = 0 on the boundary
+ * (Eq. 1.1 of arXiv 2406.06283), discretised by P1 finite elements
+ * (Sec. 2.1, Eq. 2.11-2.12) and solved by right-preconditioned flexible GMRES
+ * with the two-level additive Schwarz preconditioner (Eq. 2.22-2.23) whose
+ * coarse space is the H_k-GenEO space (Eq. 5.12, Def. 5.1).
+ *
+ * Conventions shared by every call:
+ *  - Every function returns an hk_status; 0 (HK_OK) is success.  No call
+ *    throws, aborts or exits.  hk_last_error() gives a one-line message for
+ *    the most recent failure on the calling thread.
+ *  - Pointers are HOST pointers unless the parameter name ends in _dev
+ *    (device pointers on the handle's device).  Input arrays are read during
+ *    the call only; the caller keeps ownership of every pointer it passes.
+ *  - The library owns every device allocation it makes and frees it in
+ *    hk_destroy.  A handle is bound to the device that was current at
+ *    hk_setup and to the CUDA stream passed there (NULL = the legacy default
+ *    stream).  Calls on one handle must not overlap in time.
+ *  - Degrees of freedom (dofs) are the non-Dirichlet nodes in increasing
+ *    node index; every dof vector (rhs, u, z, ...) is laid out in that order,
+ *    n_rhs vectors one after another (rhs[r * n_dofs + l]).
+ *  - Arrays are 0-based; int32_t for indices, double for values.
+ */
+#ifndef HKGENEO_H
+#define HKGENEO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HK_OK = 0,
+  HK_BAD_ARG = 1,          /* inconsistent sizes, tau <= 0, overlap < 1, NULL pointer, ... */
+  HK_SINGULAR_LOCAL = 2,   /* a local Dirichlet matrix B_i is singular (Remark after Lemma 3.4) */
+  HK_SINGULAR_COARSE = 3,  /* the coarse matrix Z^T B Z is singular */
+  HK_EIG_FAIL = 4,         /* a local eigenproblem could not be reduced or solved */
+  HK_NO_CONVERGENCE = 5,   /* max_iters reached; outputs hold the last iterate */
+  HK_OOM = 6,              /* device allocation failed */
+  HK_TIMEOUT = 7,          /* a bounded device wait ran out */
+  HK_CUDA_ERROR = 8,       /* a CUDA runtime call failed */
+  HK_UNSUPPORTED = 9       /* input outside the library's limits (e.g. a level set wider than 128 dofs) */
+} hk_status;
+
+enum { HK_FP64 = 0, HK_FP32_PRECOND = 1 };                     /* hk_params.precision */
+enum { HK_TWO_LEVEL = 0, HK_ONE_LEVEL = 1, HK_COARSE_ONLY = 2 };  /* hk_params.levels */
+enum { HK_AS = 0, HK_RAS_POU = 1 };                            /* hk_params.weighting */
+
+/* Simplicial mesh (Sec. 2.1: any shape-regular triangulation, d = 2 or 3). */
+typedef struct {
+  int dim;                     /* 2 (triangles) or 3 (tetrahedra) */
+  int n_nodes;
+  const double* xyz;           /* n_nodes * dim coordinates, node-major */
+  int n_elems;
+  const int32_t* elems;        /* n_elems * (dim + 1) node ids */
+  const uint8_t* is_boundary;  /* n_nodes flags; 1 = Dirichlet node (not a dof) */
+} hk_mesh;
+
+/* Decomposition and solver parameters. */
+typedef struct {
+  int n_sub;                   /* number of subdomains N */
+  const int32_t* elem_to_sub;  /* n_elems: non-overlapping element partition {Omega_i'} */
+  int overlap_layers;          /* applications of the one-layer extension of Def. 2.3 (>= 1) */
+  double tau;                  /* keep local eigenvalues lambda < tau (> 0); Def. 5.1 */
+  int precision;               /* HK_FP64: whole solver in FP64.  HK_FP32_PRECOND: the
+                                  preconditioner (local and coarse solves) applied in FP32 from
+                                  factors computed in FP64; Krylov vectors, matvec and Arnoldi FP64. */
+  int levels;                  /* HK_TWO_LEVEL (Eq. 2.23), HK_ONE_LEVEL (Eq. 2.22), HK_COARSE_ONLY */
+  int weighting;               /* HK_AS: unweighted sum of local solves (Eq. 2.22);
+                                  HK_RAS_POU: local solves weighted by 1/mu (variant) */
+  int restart;                 /* FGMRES restart length m (1 .. 256) */
+  int max_iters;               /* total inner iterations allowed per right-hand side */
+} hk_params;
+
+typedef struct hk_handle hk_handle;
+
+/* Setup: device assembly of B = K - k^2 M and D_k = K + k^2 M (Sec. 2.1,
+ * Prop. 2.6), the overlapping subdomains by Def. 2.3 applied overlap_layers
+ * times, dof/ovdof (Def. 3.2) and mu (Def. 2.7), the local Dirichlet factors
+ * of B_i = R_i B R_i^T (Eq. 2.22), the H_k-GenEO eigenproblems (Eq. 5.12) with
+ * the eigenvectors below tau, the coarse basis Z = [E_i Xi_i p_l] (Def. 5.1)
+ * and the coarse matrix E = Z^T B Z with its inverse (Eq. 2.23).
+ *   mesh, elem_coeff (n_elems scalars a_T > 0), k >= 0, params: host inputs.
+ *   cuda_stream: a cudaStream_t (may be NULL).  *out receives the handle.
+ * Errors: HK_BAD_ARG, HK_UNSUPPORTED, HK_SINGULAR_LOCAL, HK_EIG_FAIL,
+ * HK_SINGULAR_COARSE, HK_OOM, HK_CUDA_ERROR; *out is NULL on any error. */
+hk_status hk_setup(const hk_mesh* mesh, const double* elem_coeff, double k,
+                   const hk_params* params, void* cuda_stream, hk_handle** out);
+
+/* Solve B u = rhs for n_rhs right-hand sides (load vectors) with FGMRES
+ * preconditioned on the right by the setup's preconditioner, x_0 = 0, until
+ * the relative residual ||rhs - B u|| / ||rhs|| <= tol (checked on the true
+ * residual) or max_iters inner iterations.
+ *   rhs: n_rhs * n_dofs (host).  u: n_rhs * n_dofs (host, written).
+ *   iters: n_rhs (written).  res_hist: NULL or n_rhs * max_iters, written with
+ *   the recurrence estimates |g_{j+1}| / ||rhs|| of each inner step (unused
+ *   tail left untouched).  final_true_rel_res: NULL or n_rhs.
+ * Returns HK_NO_CONVERGENCE (outputs still written) if any rhs did not
+ * converge.  The host copies in and out are part of the call. */
+hk_status hk_solve(hk_handle* h, int n_rhs, const double* rhs, double tol, double* u,
+                   int32_t* iters, double* res_hist, double* final_true_rel_res);
+
+/* Same as hk_solve with rhs_dev and u_dev in device memory (n_rhs * n_dofs
+ * doubles each).  iters, res_hist and final_true_rel_res are host arrays. */
+hk_status hk_solve_device(hk_handle* h, int n_rhs, const double* rhs_dev, double tol, double* u_dev,
+                          int32_t* iters, double* res_hist, double* final_true_rel_res);
+
+typedef struct {
+  int dim, n_nodes, n_elems, n_dofs, n_sub;
+  int n0;                      /* coarse dimension sum_i m_i */
+  int max_mu;                  /* largest multiplicity mu_l (Def. 2.7) */
+  int lambda_elems;            /* Lambda: most subdomains sharing one element */
+  int max_level;               /* widest level set of any local factor */
+  int max_dof;                 /* largest |dof(Omega_i)| */
+  int nnz;                     /* nonzeros of B */
+  int precision, levels;
+  size_t bytes_resident;       /* device bytes held by the handle */
+  double setup_ms[8];          /* assembly, decomposition, local factors, eigen, coarse, total, -, - */
+} hk_info_t;
+
+hk_status hk_info(const hk_handle* h, hk_info_t* info);
+
+/* Frees every device allocation of the handle.  NULL is accepted. */
+hk_status hk_destroy(hk_handle* h);
+
+const char* hk_status_string(hk_status s);
+const char* hk_last_error(void);
+
+/* ---- Inspection and single-step calls (same data the solve uses) ---- */
+
+/* CSR of B (which = 0) or D_k (which = 1): rowptr n_dofs+1, col/val nnz. */
+hk_status hk_get_matrix(const hk_handle* h, int which, int32_t* rowptr, int32_t* col, double* val);
+
+/* Subdomain i: sizes[0] = |dof(Omega_i)|, sizes[1] = |ovdof \ dof|, sizes[2] = number of
+ * level sets, sizes[3] = m_i.  Any of the arrays may be NULL:
+ * dof: |dof| global dof ids in the factor's level order; gamma: |ovdof \ dof| ids, increasing;
+ * level_ptr: level sets + 1 offsets into dof. */
+hk_status hk_get_subdomain(const hk_handle* h, int i, int32_t* sizes, int32_t* dof, int32_t* gamma,
+                           int32_t* level_ptr);
+
+/* mu_l for every dof (n_dofs). */
+hk_status hk_get_mu(const hk_handle* h, int32_t* mu);
+
+/* Kept eigenvalues of subdomain i (m_i, ascending) and the coarse vectors Z_i
+ * (|dof| x m_i row-major, rows in the level order of hk_get_subdomain's dof). */
+hk_status hk_get_eigen(const hk_handle* h, int i, double* lam, double* Z);
+
+/* E = Z^T B Z and its inverse (n0 x n0 row-major each; either may be NULL). */
+hk_status hk_get_coarse(const hk_handle* h, double* E, double* Einv);
+
+/* z = M^{-1} v (one preconditioner apply, Eq. 2.23 / 2.22) for n_rhs host vectors. */
+hk_status hk_apply_precond(hk_handle* h, int n_rhs, const double* v, double* z);
+
+/* y = B x for n_rhs host vectors. */
+hk_status hk_matvec(hk_handle* h, int n_rhs, const double* x, double* y);
+
+/* Load vector (f, phi_l) of the P1 interpolant of nodal values f_nodal (n_nodes), written to
+ * rhs (n_dofs); exact for piecewise-linear f (Eq. 2.12's right-hand side). */
+hk_status hk_assemble_load(hk_handle* h, const double* f_nodal, double* rhs);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HKGENEO_H */

@@ -1,0 +1,343 @@
+// C ABI of the hkgeneo library: argument checks, phase orchestration,
+// host/device copies, inspection calls.  All arithmetic of the method runs in
+// the kernels of the other translation units.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "hk_internal.cuh"
+
+static thread_local char g_err[512] = "";
+
+void hk_set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+extern "C" const char* hk_last_error(void) { return g_err; }
+
+extern "C" const char* hk_status_string(hk_status s) {
+  switch (s) {
+    case HK_OK: return "HK_OK";
+    case HK_BAD_ARG: return "HK_BAD_ARG";
+    case HK_SINGULAR_LOCAL: return "HK_SINGULAR_LOCAL";
+    case HK_SINGULAR_COARSE: return "HK_SINGULAR_COARSE";
+    case HK_EIG_FAIL: return "HK_EIG_FAIL";
+    case HK_NO_CONVERGENCE: return "HK_NO_CONVERGENCE";
+    case HK_OOM: return "HK_OOM";
+    case HK_TIMEOUT: return "HK_TIMEOUT";
+    case HK_CUDA_ERROR: return "HK_CUDA_ERROR";
+    case HK_UNSUPPORTED: return "HK_UNSUPPORTED";
+  }
+  return "unknown";
+}
+
+void dfree(hk_handle* h, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < h->allocs.size(); ++i)
+    if (h->allocs[i] == p) {
+      h->allocs[i] = h->allocs.back();
+      h->allocs.pop_back();
+      break;
+    }
+  cudaFree(p);
+}
+
+hk_status check_device_status(hk_handle* h, const char* phase) {
+  DevStatus st;
+  cudaError_t e = cudaMemcpyAsync(&st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    hk_set_error("%s: %s", phase, cudaGetErrorString(e));
+    return HK_CUDA_ERROR;
+  }
+  if (st.code != HK_OK) {
+    hk_set_error("%s: %s at index %d (value %.6g)", phase, hk_status_string((hk_status)st.code), st.where, st.value);
+    return (hk_status)st.code;
+  }
+  return HK_OK;
+}
+
+static void destroy_all(hk_handle* h) {
+  if (!h) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->dev);
+  cudaStreamSynchronize(h->stream);
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->h_state) cudaFreeHost(h->h_state);
+  if (h->h_rstate) cudaFreeHost(h->h_rstate);
+  cudaSetDevice(cur);
+  delete h;
+}
+
+extern "C" hk_status hk_destroy(hk_handle* h) {
+  destroy_all(h);
+  return HK_OK;
+}
+
+struct PhaseTimer {
+  cudaEvent_t a, b;
+  cudaStream_t st;
+  explicit PhaseTimer(cudaStream_t s) : st(s) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+  }
+  double stop() {
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventRecord(a, st);
+    return ms;
+  }
+  ~PhaseTimer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+static hk_status setup_impl(hk_handle* h, const hk_mesh* mesh, const double* coeff, const hk_params* prm) {
+  HK_TRY(dalloc(h, &h->d_status, 1));
+  PhaseTimer t(h->stream);
+  HK_TRY(phase_assembly(h, mesh, coeff));
+  h->setup_ms[0] = t.stop();
+  uint8_t* d_elem_in = nullptr;
+  HK_TRY(phase_decomposition(h, prm->elem_to_sub, &d_elem_in));
+  h->setup_ms[1] = t.stop();
+  HK_TRY(phase_local_factors(h));
+  h->setup_ms[2] = t.stop();
+  if (h->p.levels != HK_ONE_LEVEL) {
+    HK_TRY(phase_eigen(h, d_elem_in));
+    h->setup_ms[3] = t.stop();
+    HK_TRY(phase_coarse(h));
+    h->setup_ms[4] = t.stop();
+  }
+  dfree(h, d_elem_in);
+  h->setup_ms[5] = h->setup_ms[0] + h->setup_ms[1] + h->setup_ms[2] + h->setup_ms[3] + h->setup_ms[4];
+  return HK_OK;
+}
+
+extern "C" hk_status hk_setup(const hk_mesh* mesh, const double* elem_coeff, double k, const hk_params* prm,
+                              void* cuda_stream, hk_handle** out) {
+  if (!out) {
+    hk_set_error("out is NULL");
+    return HK_BAD_ARG;
+  }
+  *out = nullptr;
+  if (!mesh || !elem_coeff || !prm || !mesh->xyz || !mesh->elems || !mesh->is_boundary || !prm->elem_to_sub) {
+    hk_set_error("NULL argument");
+    return HK_BAD_ARG;
+  }
+  if ((mesh->dim != 2 && mesh->dim != 3) || mesh->n_nodes <= 0 || mesh->n_elems <= 0 || prm->n_sub <= 0 ||
+      prm->overlap_layers < 1 || !(prm->tau > 0) || !(k >= 0) || prm->restart < 1 ||
+      prm->restart > HK_MAXRESTART || prm->max_iters < 1 || prm->precision < HK_FP64 ||
+      prm->precision > HK_FP32_PRECOND || prm->levels < HK_TWO_LEVEL || prm->levels > HK_COARSE_ONLY ||
+      prm->weighting < HK_AS || prm->weighting > HK_RAS_POU) {
+    hk_set_error("invalid sizes or parameters (dim %d, n_sub %d, overlap %d, tau %g, restart %d)", mesh->dim,
+                 prm->n_sub, prm->overlap_layers, prm->tau, prm->restart);
+    return HK_BAD_ARG;
+  }
+  hk_handle* h = new hk_handle();
+  cudaGetDevice(&h->dev);
+  h->stream = (cudaStream_t)cuda_stream;
+  h->dim = mesh->dim;
+  h->nv = mesh->dim + 1;
+  h->n_nodes = mesh->n_nodes;
+  h->n_elems = mesh->n_elems;
+  h->n_sub = prm->n_sub;
+  h->k = k;
+  h->p = *prm;
+  h->p.elem_to_sub = nullptr;
+  hk_status s = setup_impl(h, mesh, elem_coeff, prm);
+  if (s != HK_OK) {
+    cudaGetLastError();
+    destroy_all(h);
+    return s;
+  }
+  *out = h;
+  return HK_OK;
+}
+
+extern "C" hk_status hk_solve_device(hk_handle* h, int n_rhs, const double* rhs_dev, double tol, double* u_dev,
+                                     int32_t* iters, double* res_hist, double* final_true_rel_res) {
+  if (!h || n_rhs < 1 || !rhs_dev || !u_dev || !iters || !(tol > 0)) {
+    hk_set_error("invalid solve arguments");
+    return HK_BAD_ARG;
+  }
+  return run_fgmres(h, n_rhs, rhs_dev, tol, u_dev, iters, res_hist, final_true_rel_res);
+}
+
+extern "C" hk_status hk_solve(hk_handle* h, int n_rhs, const double* rhs, double tol, double* u, int32_t* iters,
+                              double* res_hist, double* final_true_rel_res) {
+  if (!h || n_rhs < 1 || !rhs || !u || !iters || !(tol > 0)) {
+    hk_set_error("invalid solve arguments");
+    return HK_BAD_ARG;
+  }
+  size_t bytes = sizeof(double) * (size_t)n_rhs * h->n;
+  double *d_in = nullptr, *d_out = nullptr;
+  HK_CUDA(cudaMallocAsync(&d_in, bytes, h->stream));
+  cudaError_t e = cudaMallocAsync(&d_out, bytes, h->stream);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(d_in, h->stream);
+    hk_set_error("cudaMallocAsync: %s", cudaGetErrorString(e));
+    return HK_OOM;
+  }
+  hk_status s = HK_OK;
+  e = cudaMemcpyAsync(d_in, rhs, bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) s = HK_CUDA_ERROR;
+  if (s == HK_OK) s = run_fgmres(h, n_rhs, d_in, tol, d_out, iters, res_hist, final_true_rel_res);
+  if (s == HK_OK || s == HK_NO_CONVERGENCE) {
+    e = cudaMemcpyAsync(u, d_out, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      hk_set_error("copy-out: %s", cudaGetErrorString(e));
+      s = HK_CUDA_ERROR;
+    }
+  }
+  cudaFreeAsync(d_in, h->stream);
+  cudaFreeAsync(d_out, h->stream);
+  cudaStreamSynchronize(h->stream);
+  return s;
+}
+
+extern "C" hk_status hk_info(const hk_handle* h, hk_info_t* info) {
+  if (!h || !info) return HK_BAD_ARG;
+  memset(info, 0, sizeof(*info));
+  info->dim = h->dim;
+  info->n_nodes = h->n_nodes;
+  info->n_elems = h->n_elems;
+  info->n_dofs = h->n;
+  info->n_sub = h->n_sub;
+  info->n0 = h->n0;
+  info->max_mu = h->max_mu;
+  info->lambda_elems = h->lambda_elems;
+  info->max_level = h->max_level;
+  info->max_dof = h->max_dof;
+  info->nnz = h->nnz;
+  info->precision = h->p.precision;
+  info->levels = h->p.levels;
+  info->bytes_resident = h->bytes;
+  for (int i = 0; i < 8; ++i) info->setup_ms[i] = h->setup_ms[i];
+  return HK_OK;
+}
+
+extern "C" hk_status hk_get_matrix(const hk_handle* h, int which, int32_t* rowptr, int32_t* col, double* val) {
+  if (!h || which < 0 || which > 1) return HK_BAD_ARG;
+  cudaStream_t st = h->stream;
+  if (rowptr) HK_CUDA(cudaMemcpyAsync(rowptr, h->d_rowptr, sizeof(int) * (h->n + 1), cudaMemcpyDeviceToHost, st));
+  if (col) HK_CUDA(cudaMemcpyAsync(col, h->d_col, sizeof(int) * h->nnz, cudaMemcpyDeviceToHost, st));
+  if (val)
+    HK_CUDA(cudaMemcpyAsync(val, which == 0 ? h->d_valB : h->d_valD, sizeof(double) * h->nnz, cudaMemcpyDeviceToHost,
+                            st));
+  HK_CUDA(cudaStreamSynchronize(st));
+  return HK_OK;
+}
+
+extern "C" hk_status hk_get_subdomain(const hk_handle* h, int i, int32_t* sizes, int32_t* dof, int32_t* gamma,
+                                      int32_t* level_ptr) {
+  if (!h || i < 0 || i >= h->n_sub) return HK_BAD_ARG;
+  const Sub& u = h->subs[i];
+  cudaStream_t st = h->stream;
+  if (sizes) {
+    sizes[0] = u.nI;
+    sizes[1] = u.nG;
+    sizes[2] = u.L;
+    sizes[3] = u.m;
+  }
+  if (dof) HK_CUDA(cudaMemcpyAsync(dof, h->d_I + u.I_off, sizeof(int) * u.nI, cudaMemcpyDeviceToHost, st));
+  if (gamma && u.nG)
+    HK_CUDA(cudaMemcpyAsync(gamma, h->d_G + u.G_off, sizeof(int) * u.nG, cudaMemcpyDeviceToHost, st));
+  if (level_ptr)
+    HK_CUDA(cudaMemcpyAsync(level_ptr, h->d_lev + u.lev_off, sizeof(int) * (u.L + 1), cudaMemcpyDeviceToHost, st));
+  HK_CUDA(cudaStreamSynchronize(st));
+  return HK_OK;
+}
+
+extern "C" hk_status hk_get_mu(const hk_handle* h, int32_t* mu) {
+  if (!h || !mu) return HK_BAD_ARG;
+  HK_CUDA(cudaMemcpyAsync(mu, h->d_mu, sizeof(int) * h->n, cudaMemcpyDeviceToHost, h->stream));
+  HK_CUDA(cudaStreamSynchronize(h->stream));
+  return HK_OK;
+}
+
+extern "C" hk_status hk_get_eigen(const hk_handle* h, int i, double* lam, double* Z) {
+  if (!h || i < 0 || i >= h->n_sub) return HK_BAD_ARG;
+  const Sub& u = h->subs[i];
+  if (u.m == 0) return HK_OK;
+  cudaStream_t st = h->stream;
+  if (lam) HK_CUDA(cudaMemcpyAsync(lam, h->d_lam + (size_t)i * HK_MAXM, sizeof(double) * u.m, cudaMemcpyDeviceToHost, st));
+  if (Z) HK_CUDA(cudaMemcpyAsync(Z, h->d_Z64 + u.z_off, sizeof(double) * u.nI * u.m, cudaMemcpyDeviceToHost, st));
+  HK_CUDA(cudaStreamSynchronize(st));
+  return HK_OK;
+}
+
+extern "C" hk_status hk_get_coarse(const hk_handle* h, double* E, double* Einv) {
+  if (!h) return HK_BAD_ARG;
+  size_t b = sizeof(double) * (size_t)h->n0 * h->n0;
+  if (h->n0 == 0) return HK_OK;
+  if (E) HK_CUDA(cudaMemcpyAsync(E, h->d_E, b, cudaMemcpyDeviceToHost, h->stream));
+  if (Einv) HK_CUDA(cudaMemcpyAsync(Einv, h->d_Einv64, b, cudaMemcpyDeviceToHost, h->stream));
+  HK_CUDA(cudaStreamSynchronize(h->stream));
+  return HK_OK;
+}
+
+static hk_status with_device_vectors(hk_handle* h, int n_in, int n_out, int s, const double* in, double* out,
+                                     hk_status (*fn)(hk_handle*, int, const double*, double*)) {
+  size_t bi = sizeof(double) * (size_t)s * n_in, bo = sizeof(double) * (size_t)s * n_out;
+  double *d_in = nullptr, *d_out = nullptr;
+  HK_CUDA(cudaMalloc(&d_in, bi));
+  cudaError_t e = cudaMalloc(&d_out, bo);
+  if (e != cudaSuccess) {
+    cudaFree(d_in);
+    return HK_OOM;
+  }
+  hk_status s_ = HK_OK;
+  if (cudaMemcpyAsync(d_in, in, bi, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) s_ = HK_CUDA_ERROR;
+  if (s_ == HK_OK) s_ = fn(h, s, d_in, d_out);
+  if (s_ == HK_OK && cudaMemcpyAsync(out, d_out, bo, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    s_ = HK_CUDA_ERROR;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) s_ = HK_CUDA_ERROR;
+  cudaFree(d_in);
+  cudaFree(d_out);
+  return s_;
+}
+
+static hk_status apply_fn(hk_handle* h, int s, const double* v, double* z) { return op_apply(h, s, v, z, nullptr); }
+static hk_status matvec_fn(hk_handle* h, int s, const double* x, double* y) {
+  return op_matvec(h, s, x, y, nullptr);
+}
+static hk_status load_fn(hk_handle* h, int, const double* f, double* r) { return op_load(h, f, r); }
+
+extern "C" hk_status hk_apply_precond(hk_handle* h, int n_rhs, const double* v, double* z) {
+  if (!h || n_rhs < 1 || !v || !z) return HK_BAD_ARG;
+  HK_TRY(ensure_workspace(h, n_rhs));
+  return with_device_vectors(h, h->n, h->n, n_rhs, v, z, apply_fn);
+}
+
+extern "C" hk_status hk_matvec(hk_handle* h, int n_rhs, const double* x, double* y) {
+  if (!h || n_rhs < 1 || !x || !y) return HK_BAD_ARG;
+  return with_device_vectors(h, h->n, h->n, n_rhs, x, y, matvec_fn);
+}
+
+extern "C" hk_status hk_assemble_load(hk_handle* h, const double* f_nodal, double* rhs) {
+  if (!h || !f_nodal || !rhs) return HK_BAD_ARG;
+  size_t bi = sizeof(double) * (size_t)h->n_nodes;
+  double *d_in = nullptr, *d_out = nullptr;
+  HK_CUDA(cudaMalloc(&d_in, bi));
+  HK_CUDA(cudaMalloc(&d_out, sizeof(double) * h->n));
+  hk_status s = HK_OK;
+  if (cudaMemcpyAsync(d_in, f_nodal, bi, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) s = HK_CUDA_ERROR;
+  if (s == HK_OK) s = load_fn(h, 1, d_in, d_out);
+  if (s == HK_OK &&
+      cudaMemcpyAsync(rhs, d_out, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    s = HK_CUDA_ERROR;
+  cudaStreamSynchronize(h->stream);
+  cudaFree(d_in);
+  cudaFree(d_out);
+  return s;
+}

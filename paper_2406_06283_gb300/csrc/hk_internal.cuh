@@ -1,0 +1,310 @@
+// Internal declarations of the hkgeneo CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "hkgeneo.h"
+
+// Library limits (checked at setup, HK_UNSUPPORTED beyond them).
+#define HK_MAXB 128        // widest level set of a local block-tridiagonal factor
+#define HK_MAXM 256        // most eigenvectors kept on one subdomain
+#define HK_MAXROW 64       // most nonzeros in one row of B
+#define HK_MAXSTAR 64      // most elements around one node
+#define HK_MAXRESTART 256  // longest FGMRES cycle
+
+// Device error record written by kernels (first nonzero code wins).
+struct DevStatus {
+  int code;     // hk_status
+  int where;    // subdomain / row / step that failed
+  double value; // offending value (pivot, ...)
+};
+
+__device__ __forceinline__ void dev_fail(DevStatus* st, int code, int where, double value) {
+  if (atomicCAS(&st->code, 0, code) == 0) {
+    st->where = where;
+    st->value = value;
+  }
+}
+
+void hk_set_error(const char* fmt, ...);
+
+#define HK_TRY(expr)                         \
+  do {                                       \
+    hk_status s_ = (expr);                   \
+    if (s_ != HK_OK) return s_;              \
+  } while (0)
+
+#define HK_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      hk_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_));   \
+      return e_ == cudaErrorMemoryAllocation ? HK_OOM : HK_CUDA_ERROR;                     \
+    }                                                                                      \
+  } while (0)
+
+#define HK_LAUNCH_CHECK() HK_CUDA(cudaGetLastError())
+
+// A device array with its element count.
+template <typename T>
+struct DArr {
+  T* p = nullptr;
+  size_t n = 0;
+};
+
+// Per-subdomain Krylov / apply workspace sizes are derived from these.
+struct Sub {
+  int nI, nG, L;        // |dof|, |ovdof \ dof|, number of level sets
+  int I_off;            // offset of the subdomain's dof rows in concatenated arrays
+  int G_off;            // offset into concatenated Gamma lists
+  int lev_off;          // offset of its level pointer array (L + 1 entries)
+  long long f_off;      // offset of its factor blocks (elements)
+  long long csr_off;    // offset of its local CSR entries
+  int m;                // kept eigenvectors
+  int c_off;            // offset in the coarse vector
+  long long z_off;      // offset of Z_i (nI * m)
+  int bw;               // half bandwidth of D_II in level order
+};
+
+struct hk_handle {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  int dim = 0, nv = 0, n_nodes = 0, n_elems = 0, n = 0, n_sub = 0;
+  double k = 0;
+  hk_params p{};
+  // sizes
+  int nnz = 0, n0 = 0, max_mu = 0, lambda_elems = 0, max_level = 0, max_dof = 0;
+  long long I_total = 0, G_total = 0, f_total = 0, csr_total = 0, z_total = 0;
+  std::vector<Sub> subs;
+  double setup_ms[8] = {0};
+
+  // ---- device data kept for the solve ----
+  DevStatus* d_status = nullptr;
+  double* d_xyz = nullptr;
+  int* d_elems = nullptr;
+  double* d_coeff = nullptr;
+  int* d_dof_of_node = nullptr;   // n_nodes, -1 on Dirichlet nodes
+  int* d_node_of_dof = nullptr;   // n
+  int* d_ne_ptr = nullptr;        // node -> element CSR
+  int* d_ne_idx = nullptr;
+  int* d_rowptr = nullptr;        // CSR of B / D_k over dofs
+  int* d_col = nullptr;
+  double* d_valB = nullptr;
+  double* d_valD = nullptr;
+  int* d_mu = nullptr;            // n
+  // subdomain lists
+  int* d_sub_info = nullptr;      // per subdomain: nI, nG, L, I_off, G_off, lev_off, m, c_off (8 ints)
+  long long* d_sub_off = nullptr; // per subdomain: f_off, csr_off, z_off (3 long long)
+  int* d_I = nullptr;             // I_total: global dof ids, level order
+  int* d_Isorted = nullptr;       // I_total: global dof ids, increasing
+  int* d_perm = nullptr;          // I_total: position in level order of each Isorted entry
+  int* d_G = nullptr;             // G_total: Gamma ids, increasing
+  int* d_lev = nullptr;           // level pointers
+  // local CSR (rows in level order): capacity per row = global row length
+  int* d_lrow = nullptr;          // I_total + n_sub row starts (per subdomain: nI + 1)
+  int* d_lcntI = nullptr;         // I_total: entries inside dof
+  int* d_lcntG = nullptr;         // I_total: entries on Gamma
+  int* d_lcol = nullptr;          // csr_total
+  double* d_lvalB = nullptr;      // csr_total
+  double* d_lvalD = nullptr;      // csr_total
+  float* d_lvalB32 = nullptr;     // csr_total (FP32 form)
+  // pull map
+  int* d_pull_ptr = nullptr;      // n + 1
+  int* d_pull_row = nullptr;      // entries: global row in concatenated level-ordered arrays
+  int* d_pull_sub = nullptr;      // entries: subdomain id
+  // local factors: per level S_j^{-1} (b_j x b_j) then G_j (b_j x b_{j+1}), row-major
+  double* d_F64 = nullptr;
+  float* d_F32 = nullptr;
+  // coarse space
+  double* d_lam = nullptr;        // per subdomain kept eigenvalues (HK_MAXM each)
+  double* d_Z64 = nullptr;        // z_total, per subdomain nI x m row-major
+  float* d_Z32 = nullptr;
+  double* d_E = nullptr;          // n0 x n0
+  double* d_Einv64 = nullptr;
+  float* d_Einv32 = nullptr;
+
+  // ---- solve workspace (grown on demand) ----
+  int ws_rhs = 0, ws_m = 0;
+  double* d_V = nullptr;          // (m + 1) x s x n
+  double* d_Zk = nullptr;         // m x s x n
+  double* d_w = nullptr;          // s x n
+  double* d_x = nullptr;          // s x n
+  double* d_f = nullptr;          // s x n
+  double* d_ybuf64 = nullptr;     // s x I_total local solutions (FP64 form)
+  float* d_ybuf32 = nullptr;      // s x I_total (FP32 form)
+  double* d_c64 = nullptr;        // s x n0 coarse rhs
+  double* d_cc64 = nullptr;       // s x n0 coarse solution
+  float* d_c32 = nullptr;
+  float* d_cc32 = nullptr;
+  double* d_part = nullptr;       // reduction partials
+  unsigned* d_counter = nullptr;  // last-block counters
+  double* d_H = nullptr;          // s x (m+1) x m Hessenberg
+  double* d_cs = nullptr;         // s x m
+  double* d_sn = nullptr;
+  double* d_g = nullptr;          // s x (m+1)
+  double* d_hcol = nullptr;       // s x 2 x (m+1) Gram-Schmidt coefficients
+  int* d_state = nullptr;         // s x 8 per-rhs control words
+  double* d_rstate = nullptr;     // s x 8 per-rhs scalars (||f||, beta, residual, ...)
+  double* d_hist = nullptr;       // s x max_iters
+  int* h_state = nullptr;         // pinned host mirror of d_state
+  double* h_rstate = nullptr;
+
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+};
+
+// Allocation helper: zero-initialised device memory tracked by the handle.
+template <typename T>
+hk_status dalloc(hk_handle* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    hk_set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    return HK_OOM;
+  }
+  h->allocs.push_back((void*)*p);
+  h->bytes += count * sizeof(T);
+  e = cudaMemsetAsync(*p, 0, count * sizeof(T), h->stream);
+  if (e != cudaSuccess) {
+    hk_set_error("cudaMemset failed: %s", cudaGetErrorString(e));
+    return HK_CUDA_ERROR;
+  }
+  return HK_OK;
+}
+
+void dfree(hk_handle* h, void* p);
+
+// Reads the device status record; returns its code with a message.
+hk_status check_device_status(hk_handle* h, const char* phase);
+
+// ---- phases (each file implements one) ----
+hk_status phase_assembly(hk_handle* h, const hk_mesh* mesh, const double* coeff);
+hk_status phase_decomposition(hk_handle* h, const int32_t* elem_to_sub, uint8_t** d_elem_in_out);
+hk_status phase_local_factors(hk_handle* h);
+hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in);
+hk_status phase_coarse(hk_handle* h);
+
+// ---- solve-time operations ----
+hk_status ensure_workspace(hk_handle* h, int s);
+// z = M^{-1} v for s vectors (v, z: s x n device arrays, FP64).  `active` is NULL or
+// the per-rhs state words (8 ints per rhs, word 0 nonzero = process this rhs).
+hk_status op_apply(hk_handle* h, int s, const double* v, double* z, const int* active);
+// y = B x for s vectors.
+hk_status op_matvec(hk_handle* h, int s, const double* x, double* y, const int* active);
+hk_status op_load(hk_handle* h, const double* f_nodal_dev, double* rhs_dev);
+hk_status run_fgmres(hk_handle* h, int s, const double* rhs_dev, double tol, double* u_dev,
+                     int32_t* iters, double* res_hist, double* final_res);
+
+// ---- shared device helpers ----
+// Exclusive scan of n ints in one CTA (setup sizes); total written to *total.
+void launch_scan_exclusive(const int* in, int* out, int n, int* total, cudaStream_t st);
+void launch_to_f32(const double* a, float* b, long long n, cudaStream_t st);
+hk_status upload_sub_info(hk_handle* h);
+
+// Geometry of a P1 simplex: volume and barycentric gradients g[v][d].
+__device__ __forceinline__ double simplex_geometry(int dim, const double* __restrict__ xyz,
+                                                   const int* __restrict__ vid, double g[4][3]) {
+  if (dim == 2) {
+    double x0 = xyz[2 * vid[0]], y0 = xyz[2 * vid[0] + 1];
+    double a = xyz[2 * vid[1]] - x0, c = xyz[2 * vid[1] + 1] - y0;   // edge 1 = (a, c)
+    double b = xyz[2 * vid[2]] - x0, d = xyz[2 * vid[2] + 1] - y0;   // edge 2 = (b, d)
+    double det = a * d - b * c;                                        // columns (a,c), (b,d)
+    double inv = 1.0 / det;
+    // inverse of [[a, b], [c, d]] rows: grad lambda_1 = ( d, -b)/det, grad lambda_2 = (-c, a)/det
+    g[1][0] = d * inv;  g[1][1] = -b * inv;
+    g[2][0] = -c * inv; g[2][1] = a * inv;
+    g[0][0] = -g[1][0] - g[2][0];
+    g[0][1] = -g[1][1] - g[2][1];
+    return fabs(det) * 0.5;
+  } else {
+    double p0[3] = {xyz[3 * vid[0]], xyz[3 * vid[0] + 1], xyz[3 * vid[0] + 2]};
+    double E[3][3];  // E[r][c] = component r of edge c
+    for (int c = 0; c < 3; ++c)
+      for (int r = 0; r < 3; ++r) E[r][c] = xyz[3 * vid[c + 1] + r] - p0[r];
+    double C00 = E[1][1] * E[2][2] - E[1][2] * E[2][1];
+    double C01 = E[1][2] * E[2][0] - E[1][0] * E[2][2];
+    double C02 = E[1][0] * E[2][1] - E[1][1] * E[2][0];
+    double det = E[0][0] * C00 + E[0][1] * C01 + E[0][2] * C02;
+    double inv = 1.0 / det;
+    // rows of E^{-1} are the gradients of lambda_1..3: E^{-1} = adj(E)^T... adj(E)[c][r] = cofactor(r,c)
+    double Inv[3][3];
+    Inv[0][0] = C00 * inv;
+    Inv[1][0] = C01 * inv;
+    Inv[2][0] = C02 * inv;
+    Inv[0][1] = (E[0][2] * E[2][1] - E[0][1] * E[2][2]) * inv;
+    Inv[1][1] = (E[0][0] * E[2][2] - E[0][2] * E[2][0]) * inv;
+    Inv[2][1] = (E[0][1] * E[2][0] - E[0][0] * E[2][1]) * inv;
+    Inv[0][2] = (E[0][1] * E[1][2] - E[0][2] * E[1][1]) * inv;
+    Inv[1][2] = (E[0][2] * E[1][0] - E[0][0] * E[1][2]) * inv;
+    Inv[2][2] = (E[0][0] * E[1][1] - E[0][1] * E[1][0]) * inv;
+    for (int v = 0; v < 3; ++v)
+      for (int d = 0; d < 3; ++d) g[v + 1][d] = Inv[v][d];
+    for (int d = 0; d < 3; ++d) g[0][d] = -(g[1][d] + g[2][d] + g[3][d]);
+    return fabs(det) / 6.0;
+  }
+}
+
+__device__ __forceinline__ int bsearch_int(const int* __restrict__ a, int n, int key) {
+  int lo = 0, hi = n - 1;
+  while (lo <= hi) {
+    int mid = (lo + hi) >> 1;
+    int v = a[mid];
+    if (v == key) return mid;
+    if (v < key) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_sumi(int v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of a double (all threads get the result). `sh` has >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0;
+  if (w == 0) {
+    t = lane < nw ? sh[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) sh[0] = t;
+  }
+  __syncthreads();
+  t = sh[0];
+  __syncthreads();
+  return t;
+}
+__device__ __forceinline__ int block_sumi(int v, int* sh) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sumi(v);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  int t = 0;
+  if (w == 0) {
+    t = lane < nw ? sh[lane] : 0;
+    t = warp_sumi(t);
+    if (lane == 0) sh[0] = t;
+  }
+  __syncthreads();
+  t = sh[0];
+  __syncthreads();
+  return t;
+}

@@ -1,0 +1,257 @@
+"""Thin ctypes binding of libhkgeneo.so (declared in include/hkgeneo.h).
+
+Argument marshalling only: every step of setup and solve runs in the
+library's CUDA kernels.  Functions carry the C names (hk_setup, hk_solve,
+...).  Host arrays are numpy; device arrays are torch CUDA tensors (used only
+for their memory).  A missing library raises HKLibraryMissing - there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libhkgeneo.so")
+
+HK_OK, HK_BAD_ARG, HK_SINGULAR_LOCAL, HK_SINGULAR_COARSE, HK_EIG_FAIL = 0, 1, 2, 3, 4
+HK_NO_CONVERGENCE, HK_OOM, HK_TIMEOUT, HK_CUDA_ERROR, HK_UNSUPPORTED = 5, 6, 7, 8, 9
+HK_FP64, HK_FP32_PRECOND = 0, 1
+HK_TWO_LEVEL, HK_ONE_LEVEL, HK_COARSE_ONLY = 0, 1, 2
+HK_AS, HK_RAS_POU = 0, 1
+
+
+class HKLibraryMissing(RuntimeError):
+    pass
+
+
+class HKError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status} ({_status_name(status)}): {msg}")
+        self.status = status
+
+
+class hk_mesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_nodes", C.c_int), ("xyz", C.POINTER(C.c_double)),
+                ("n_elems", C.c_int), ("elems", C.POINTER(C.c_int32)), ("is_boundary", C.POINTER(C.c_uint8))]
+
+
+class hk_params(C.Structure):
+    _fields_ = [("n_sub", C.c_int), ("elem_to_sub", C.POINTER(C.c_int32)), ("overlap_layers", C.c_int),
+                ("tau", C.c_double), ("precision", C.c_int), ("levels", C.c_int), ("weighting", C.c_int),
+                ("restart", C.c_int), ("max_iters", C.c_int)]
+
+
+class hk_info_t(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_nodes", C.c_int), ("n_elems", C.c_int), ("n_dofs", C.c_int),
+                ("n_sub", C.c_int), ("n0", C.c_int), ("max_mu", C.c_int), ("lambda_elems", C.c_int),
+                ("max_level", C.c_int), ("max_dof", C.c_int), ("nnz", C.c_int), ("precision", C.c_int),
+                ("levels", C.c_int), ("bytes_resident", C.c_size_t), ("setup_ms", C.c_double * 8)]
+
+
+_lib = None
+_P = C.c_void_p
+
+
+def lib():
+    """Loads libhkgeneo.so once; raises HKLibraryMissing if it was not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise HKLibraryMissing(f"{LIB_PATH} not found: run `python -m paper_2406_06283_gb300.build`")
+    L = C.CDLL(LIB_PATH)
+    L.hk_setup.argtypes = [C.POINTER(hk_mesh), _P, C.c_double, C.POINTER(hk_params), _P, C.POINTER(_P)]
+    L.hk_solve.argtypes = [_P, C.c_int, _P, C.c_double, _P, _P, _P, _P]
+    L.hk_solve_device.argtypes = [_P, C.c_int, _P, C.c_double, _P, _P, _P, _P]
+    L.hk_info.argtypes = [_P, C.POINTER(hk_info_t)]
+    L.hk_destroy.argtypes = [_P]
+    L.hk_status_string.argtypes = [C.c_int]
+    L.hk_status_string.restype = C.c_char_p
+    L.hk_last_error.restype = C.c_char_p
+    L.hk_get_matrix.argtypes = [_P, C.c_int, _P, _P, _P]
+    L.hk_get_subdomain.argtypes = [_P, C.c_int, _P, _P, _P, _P]
+    L.hk_get_mu.argtypes = [_P, _P]
+    L.hk_get_eigen.argtypes = [_P, C.c_int, _P, _P]
+    L.hk_get_coarse.argtypes = [_P, _P, _P]
+    L.hk_apply_precond.argtypes = [_P, C.c_int, _P, _P]
+    L.hk_matvec.argtypes = [_P, C.c_int, _P, _P]
+    L.hk_assemble_load.argtypes = [_P, _P, _P]
+    for f in ("hk_setup", "hk_solve", "hk_solve_device", "hk_info", "hk_destroy", "hk_get_matrix",
+              "hk_get_subdomain", "hk_get_mu", "hk_get_eigen", "hk_get_coarse", "hk_apply_precond", "hk_matvec",
+              "hk_assemble_load"):
+        getattr(L, f).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _status_name(s: int) -> str:
+    try:
+        return lib().hk_status_string(s).decode()
+    except Exception:  # noqa: BLE001
+        return str(s)
+
+
+def _check(status: int, where: str, ok=(HK_OK,)):
+    if status not in ok:
+        raise HKError(status, where, lib().hk_last_error().decode())
+    return status
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_P)
+
+
+@dataclass
+class Handle:
+    ptr: C.c_void_p
+    n: int
+    max_iters: int
+    _keep: tuple = ()
+
+    def __del__(self):
+        try:
+            hk_destroy(self)
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def hk_setup(xyz, elems, is_boundary, elem_coeff, k, elem_to_sub, n_sub, overlap=2, tau=0.5,
+             precision=HK_FP64, levels=HK_TWO_LEVEL, weighting=HK_AS, restart=50, max_iters=1000,
+             stream=None) -> Handle:
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    elems = np.ascontiguousarray(elems, dtype=np.int32)
+    bnd = np.ascontiguousarray(is_boundary, dtype=np.uint8)
+    coeff = np.ascontiguousarray(elem_coeff, dtype=np.float64)
+    e2s = np.ascontiguousarray(elem_to_sub, dtype=np.int32)
+    mesh = hk_mesh(xyz.shape[1], xyz.shape[0], xyz.ctypes.data_as(C.POINTER(C.c_double)), elems.shape[0],
+                   elems.ctypes.data_as(C.POINTER(C.c_int32)), bnd.ctypes.data_as(C.POINTER(C.c_uint8)))
+    prm = hk_params(int(n_sub), e2s.ctypes.data_as(C.POINTER(C.c_int32)), int(overlap), float(tau), int(precision),
+                    int(levels), int(weighting), int(restart), int(max_iters))
+    out = _P()
+    _check(lib().hk_setup(C.byref(mesh), _ptr(coeff), float(k), C.byref(prm), _P(stream or 0), C.byref(out)),
+           "hk_setup")
+    h = Handle(out, int((bnd == 0).sum()), int(max_iters))
+    return h
+
+
+def setup_problem(p, precision=HK_FP64, levels=HK_TWO_LEVEL, weighting=HK_AS, stream=None) -> Handle:
+    """hk_setup for a workloads.Problem."""
+    m = p.mesh
+    return hk_setup(m.xyz, m.elems, m.is_boundary, p.coeff, p.k, p.elem_to_sub, p.n_sub, p.overlap, p.tau,
+                    precision, levels, weighting, p.restart, p.max_iters, stream)
+
+
+def hk_destroy(h: Handle):
+    if h.ptr is not None and h.ptr.value:
+        lib().hk_destroy(h.ptr)
+        h.ptr = _P()
+
+
+@dataclass
+class SolveResult:
+    u: object            # (n_rhs, n) numpy array, or a torch tensor for hk_solve_device
+    iters: np.ndarray
+    history: np.ndarray  # (n_rhs, max_iters); entries past iters[r] are zero
+    true_rel_res: np.ndarray
+    status: int
+
+
+def hk_solve(h: Handle, rhs, tol=1e-8) -> SolveResult:
+    rhs = np.ascontiguousarray(np.atleast_2d(rhs), dtype=np.float64)
+    s = rhs.shape[0]
+    u = np.zeros_like(rhs)
+    it = np.zeros(s, dtype=np.int32)
+    hist = np.zeros((s, h.max_iters))
+    res = np.zeros(s)
+    st = _check(lib().hk_solve(h.ptr, s, _ptr(rhs), float(tol), _ptr(u), _ptr(it), _ptr(hist), _ptr(res)),
+                "hk_solve", ok=(HK_OK, HK_NO_CONVERGENCE))
+    return SolveResult(u, it, hist, res, st)
+
+
+def hk_solve_device(h: Handle, rhs_dev, u_dev, tol=1e-8, history=False) -> SolveResult:
+    """rhs_dev, u_dev: contiguous float64 CUDA tensors of shape (n_rhs, n)."""
+    s = int(rhs_dev.shape[0])
+    it = np.zeros(s, dtype=np.int32)
+    hist = np.zeros((s, h.max_iters)) if history else None
+    res = np.zeros(s)
+    st = _check(lib().hk_solve_device(h.ptr, s, _P(rhs_dev.data_ptr()), float(tol), _P(u_dev.data_ptr()), _ptr(it),
+                                      _ptr(hist) if history else None, _ptr(res)),
+                "hk_solve_device", ok=(HK_OK, HK_NO_CONVERGENCE))
+    return SolveResult(u_dev, it, hist, res, st)
+
+
+def hk_info(h: Handle) -> dict:
+    info = hk_info_t()
+    _check(lib().hk_info(h.ptr, C.byref(info)), "hk_info")
+    d = {f: getattr(info, f) for f, _ in hk_info_t._fields_ if f != "setup_ms"}
+    d["setup_ms"] = list(info.setup_ms)
+    return d
+
+
+def hk_get_matrix(h: Handle, which=0):
+    inf = hk_info(h)
+    n, nnz = inf["n_dofs"], inf["nnz"]
+    rp = np.zeros(n + 1, dtype=np.int32)
+    col = np.zeros(nnz, dtype=np.int32)
+    val = np.zeros(nnz)
+    _check(lib().hk_get_matrix(h.ptr, int(which), _ptr(rp), _ptr(col), _ptr(val)), "hk_get_matrix")
+    return rp, col, val
+
+
+def hk_get_subdomain(h: Handle, i: int) -> dict:
+    sizes = np.zeros(4, dtype=np.int32)
+    _check(lib().hk_get_subdomain(h.ptr, int(i), _ptr(sizes), None, None, None), "hk_get_subdomain")
+    nI, nG, L, m = (int(x) for x in sizes)
+    dof = np.zeros(nI, dtype=np.int32)
+    gam = np.zeros(max(nG, 1), dtype=np.int32)
+    lp = np.zeros(L + 1, dtype=np.int32)
+    _check(lib().hk_get_subdomain(h.ptr, int(i), _ptr(sizes), _ptr(dof), _ptr(gam), _ptr(lp)), "hk_get_subdomain")
+    return {"dof": dof, "gamma": gam[:nG], "level_ptr": lp, "m": m}
+
+
+def hk_get_mu(h: Handle) -> np.ndarray:
+    mu = np.zeros(h.n, dtype=np.int32)
+    _check(lib().hk_get_mu(h.ptr, _ptr(mu)), "hk_get_mu")
+    return mu
+
+
+def hk_get_eigen(h: Handle, i: int):
+    sd = hk_get_subdomain(h, i)
+    m, nI = sd["m"], sd["dof"].size
+    lam = np.zeros(max(m, 1))
+    Z = np.zeros((nI, max(m, 1)))
+    _check(lib().hk_get_eigen(h.ptr, int(i), _ptr(lam), _ptr(Z)), "hk_get_eigen")
+    return lam[:m], Z[:, :m], sd["dof"]
+
+
+def hk_get_coarse(h: Handle):
+    n0 = hk_info(h)["n0"]
+    E = np.zeros((n0, n0))
+    Ei = np.zeros((n0, n0))
+    _check(lib().hk_get_coarse(h.ptr, _ptr(E), _ptr(Ei)), "hk_get_coarse")
+    return E, Ei
+
+
+def hk_apply_precond(h: Handle, v) -> np.ndarray:
+    v = np.ascontiguousarray(np.atleast_2d(v), dtype=np.float64)
+    z = np.zeros_like(v)
+    _check(lib().hk_apply_precond(h.ptr, v.shape[0], _ptr(v), _ptr(z)), "hk_apply_precond")
+    return z
+
+
+def hk_matvec(h: Handle, x) -> np.ndarray:
+    x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+    y = np.zeros_like(x)
+    _check(lib().hk_matvec(h.ptr, x.shape[0], _ptr(x), _ptr(y)), "hk_matvec")
+    return y
+
+
+def hk_assemble_load(h: Handle, f_nodal) -> np.ndarray:
+    f = np.ascontiguousarray(f_nodal, dtype=np.float64)
+    out = np.zeros(h.n)
+    _check(lib().hk_assemble_load(h.ptr, _ptr(f), _ptr(out)), "hk_assemble_load")
+    return out

@@ -1,0 +1,197 @@
+"""GPU parity: every step of the CUDA path against the FP64 CPU oracle on the
+same seeded inputs, through the C ABI.
+
+Tolerances (floating point, stated per result):
+  matrices, load vector, matvec      1e-13 relative (same formulas, different summation order)
+  decomposition, mu, level structure bit-exact (integer work)
+  kept eigenvalues                   |d lambda| <= 1e-9 max(|lambda|, 1e-3); counts m_i exact
+  coarse subspaces                   ||P_gpu - P_oracle||_2 <= 1e-8 (bases differ inside clusters)
+  preconditioner apply (FP64 form)   1e-10 relative
+  FGMRES (FP64 form)                 same iteration count; solution 1e-7 relative
+  FGMRES (FP32 preconditioner form)  iterations within +-1; solution 1e-7 relative
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import solver as OS
+from paper_2406_06283_gb300 import hk
+from paper_2406_06283_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    return {
+        "h16_p2_k6_ov1": W.small_problem(cells=16, parts=2, k=6.0, overlap=1, checker=2),
+        "h24_p3_k12_ov2": W.small_problem(cells=24, parts=3, k=12.0, overlap=2, checker=3, seed=8),
+        "h20_p3_k9_ov1_uneven": W.small_problem(cells=20, parts=3, k=9.0, overlap=1, checker=2, seed=5),
+        "h40_p4_k18_ov2": W.small_problem(cells=40, parts=4, k=18.0, overlap=2, checker=4, seed=6, n_rhs=2),
+        "c1": W.config_c1(),
+    }
+
+
+CASES = _cases()
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    p = CASES[request.param]
+    o = OS.setup_problem(p)
+    h = hk.setup_problem(p)
+    yield p, o, h
+    hk.hk_destroy(h)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_matrix_parity(case):
+    p, o, h = case
+    for which, M in ((0, o.B), (1, o.Dk)):
+        rp, col, val = hk.hk_get_matrix(h, which)
+        M = M.tocsr()
+        M.sort_indices()
+        np.testing.assert_array_equal(rp, M.indptr)
+        np.testing.assert_array_equal(col, M.indices)
+        assert _rel(val, M.data) <= 1e-13
+
+
+def test_decomposition_parity(case):
+    p, o, h = case
+    np.testing.assert_array_equal(hk.hk_get_mu(h), o.mu)
+    inf = hk.hk_info(h)
+    assert inf["max_mu"] == o.mu.max()
+    assert inf["lambda_elems"] == o.Lambda
+    Bd = o.B.tocsr()
+    for i, sd in enumerate(o.subs):
+        g = hk.hk_get_subdomain(h, i)
+        np.testing.assert_array_equal(np.sort(g["dof"]), sd.dof)
+        np.testing.assert_array_equal(g["gamma"], np.setdiff1d(sd.ovdof, sd.dof))
+        # level sets make B_i block tridiagonal
+        lp = g["level_ptr"]
+        lev = np.zeros(g["dof"].size, dtype=int)
+        for j in range(lp.size - 1):
+            lev[lp[j]:lp[j + 1]] = j
+        Bi = Bd[g["dof"]][:, g["dof"]].tocoo()
+        assert np.all(np.abs(lev[Bi.row] - lev[Bi.col]) <= 1)
+
+
+def test_load_vector_and_matvec(case):
+    p, o, h = case
+    f_nodal = np.cos(3 * p.mesh.xyz[:, 0]) + p.mesh.xyz[:, 1] ** 2
+    from oracle import fem
+    want = fem.load_vector_nodal(p.mesh.xyz, p.mesh.elems, p.mesh.is_boundary, f_nodal)
+    assert _rel(hk.hk_assemble_load(h, f_nodal), want) <= 1e-13
+    x = np.random.default_rng(1).standard_normal((2, o.n))
+    assert _rel(hk.hk_matvec(h, x), np.stack([o.B @ xi for xi in x])) <= 1e-13
+
+
+def test_eigen_parity(case):
+    p, o, h = case
+    for i, (sd, ev) in enumerate(zip(o.subs, o.eigs)):
+        lam, Z, dof = hk.hk_get_eigen(h, i)
+        assert lam.size == ev.m, f"subdomain {i}: m {lam.size} vs oracle {ev.m}"
+        if ev.m == 0:
+            continue
+        want = ev.lam[: ev.m]
+        assert np.all(np.abs(lam - want) <= 1e-9 * np.maximum(np.abs(want), 1e-3)), (i, lam - want)
+        # same subspace: rows reordered to increasing dof
+        order = np.argsort(dof)
+        Qa = sla.orth(Z[order])
+        Qb = sla.orth(ev.Z)
+        assert Qa.shape[1] == Qb.shape[1] == ev.m
+        assert np.linalg.norm(Qa @ Qa.T - Qb @ Qb.T, 2) <= 1e-8
+
+
+def test_coarse_matrix_spectrum(case):
+    p, o, h = case
+    E, Ei = hk.hk_get_coarse(h)
+    if E.size == 0:
+        return
+    Eo = o.precond.E
+    # E changes by an orthogonal similarity when the bases rotate inside clusters
+    ea = np.sort(np.linalg.eigvals(E).real)
+    eb = np.sort(np.linalg.eigvals(Eo).real)
+    assert np.allclose(ea, eb, rtol=1e-8, atol=1e-10 * np.abs(eb).max())
+    assert np.linalg.norm(E @ Ei - np.eye(E.shape[0])) <= 1e-8 * np.linalg.cond(E)
+
+
+def test_preconditioner_apply_fp64(case):
+    p, o, h = case
+    v = np.random.default_rng(2).standard_normal((3, o.n))
+    z = hk.hk_apply_precond(h, v)
+    want = np.stack([o.precond.apply(vi) for vi in v])
+    assert _rel(z, want) <= 1e-10
+
+
+@pytest.mark.parametrize("levels", [hk.HK_ONE_LEVEL, hk.HK_COARSE_ONLY])
+@pytest.mark.parametrize("weighting", [hk.HK_AS, hk.HK_RAS_POU])
+def test_preconditioner_variants(levels, weighting):
+    p = CASES["h24_p3_k12_ov2"]
+    name = {hk.HK_ONE_LEVEL: "one", hk.HK_COARSE_ONLY: "coarse"}[levels]
+    wname = {hk.HK_AS: "as", hk.HK_RAS_POU: "ras_pou"}[weighting]
+    o = OS.setup_problem(p, levels=name, weighting=wname)
+    h = hk.setup_problem(p, levels=levels, weighting=weighting)
+    v = np.random.default_rng(3).standard_normal((2, o.n))
+    z = hk.hk_apply_precond(h, v)
+    want = np.stack([o.precond.apply(vi) for vi in v])
+    assert _rel(z, want) <= 1e-10
+
+
+def test_solve_parity_fp64(case):
+    p, o, h = case
+    f = OS.load_vector(p)
+    want = OS.solve(o, f, p.tol)
+    got = hk.hk_solve(h, f, p.tol)
+    for r, w in enumerate(want):
+        assert got.iters[r] == w.iters, (got.iters, [x.iters for x in want])
+        assert _rel(got.u[r], w.x) <= 1e-7
+        assert got.true_rel_res[r] <= p.tol
+        hist = got.history[r, : got.iters[r]]
+        np.testing.assert_allclose(hist, w.history, rtol=1e-6, atol=1e-14)
+
+
+def test_solve_parity_fp32_preconditioner(case):
+    p, o, _ = case
+    h = hk.setup_problem(p, precision=hk.HK_FP32_PRECOND)
+    f = OS.load_vector(p)
+    want = OS.solve(o, f, p.tol)
+    got = hk.hk_solve(h, f, p.tol)
+    for r, w in enumerate(want):
+        assert abs(int(got.iters[r]) - w.iters) <= 1, (got.iters, [x.iters for x in want])
+        assert got.true_rel_res[r] <= p.tol
+        assert _rel(got.u[r], w.x) <= 1e-7
+    hk.hk_destroy(h)
+
+
+def test_multi_rhs_equals_single():
+    p = CASES["h40_p4_k18_ov2"]
+    h = hk.setup_problem(p)
+    rhs = np.stack([W.normal(W.stream_seed(77, r), p.mesh.n_dofs) for r in range(3)])
+    together = hk.hk_solve(h, rhs, 1e-8)
+    for r in range(3):
+        alone = hk.hk_solve(h, rhs[r:r + 1], 1e-8)
+        assert alone.iters[0] == together.iters[r]
+        np.testing.assert_array_equal(alone.u[0], together.u[r])
+
+
+def test_errors_are_reported():
+    from oracle import fem
+    p = W.small_problem(cells=8, parts=1, k=1.0, overlap=1)
+    m = p.mesh
+    A, S = fem.assemble(m.xyz, m.elems, p.coeff, m.is_boundary)
+    theta = sla.eigh(A.toarray(), S.toarray(), eigvals_only=True)
+    p.k = float(np.sqrt(theta[0]))
+    with pytest.raises(hk.HKError) as e:
+        hk.setup_problem(p, levels=hk.HK_ONE_LEVEL)
+    assert e.value.status == hk.HK_SINGULAR_LOCAL
+    q = W.small_problem(cells=8, parts=2)
+    with pytest.raises(hk.HKError) as e:
+        hk.hk_setup(q.mesh.xyz, q.mesh.elems, q.mesh.is_boundary, q.coeff, q.k, q.elem_to_sub, 4, tau=-1.0)
+    assert e.value.status == hk.HK_BAD_ARG
+    q.max_iters = 2
+    h = hk.setup_problem(q)
+    r = hk.hk_solve(h, q.rhs, 1e-12)
+    assert r.status == hk.HK_NO_CONVERGENCE and r.iters[0] == 2 and np.isfinite(r.u).all()
