@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark of the two-level Schwarz / H_k-GenEO / FGMRES Helmholtz solver.
+
+One step = one pass of the whole method over one synthetic instance: device
+setup (assembly, decomposition, local factors, H_k-GenEO eigenproblems,
+coarse operator) and the right-preconditioned FGMRES solve to 1e-8 relative
+residual.  Default workload: 2D unit square, P1 on a '/' mesh with h = 1/256
+(65,025 dofs), k = 50, 8x8 checkerboard coefficient 10^U[0,2], 8x8 box
+subdomains, overlap 2, tau = 0.5, one N(0,1) right-hand side, FP32
+preconditioner with FP64 Krylov.
+
+`value` (solves/s) is measured with every input resident in HBM
+(hk_setup_device + hk_solve_device); `e2e` repeats the step through the
+host-pointer calls (hk_setup + hk_solve) with the copies inside the timed
+region.  Between timed steps a 512 MB buffer is written to flush L2.
+Under torchrun each rank solves its own replica (the method is not sharded
+here): value = steps * ranks / max-over-ranks time.
+
+--impl reference times the CPU oracle (test infrastructure, FP64 numpy/scipy)
+on the same workload on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2406_06283_gb300 import workloads as W  # noqa: E402
+
+METRIC = "Helmholtz solves/s and p99 latency at 1e-8 residual; FP32-precond vs FP64 form"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (recipe table); no measured figure in the peaks file
+
+
+def workload(name: str):
+    if name == "c2":
+        return W.config_c2()
+    if name == "c1":
+        return W.config_c1()
+    if name == "c3":
+        return W.config_c3()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(p, name, precision):
+    return {"workload": f"{p.name}: 2D P1 h=1/{p.mesh.cells} ({p.mesh.n_dofs} dofs), k={p.k:g}, "
+                        f"{p.parts}x{p.parts} subdomains, overlap {p.overlap}, tau {p.tau}, "
+                        f"FGMRES({p.restart}) to {p.tol:g}, {1 if p.rhs is None else p.rhs.shape[0]} rhs",
+            "precision_form": precision, "global_batch": 1 if p.rhs is None else int(p.rhs.shape[0]),
+            "l2": "flushed between timed steps (512 MB write)", "parallelism": "replicas"}
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:  # noqa: BLE001
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:  # noqa: BLE001
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ oracle arm
+def oracle_step(p):
+    from oracle import solver as OS
+    t0 = time.perf_counter()
+    h = OS.setup_problem(p)
+    t1 = time.perf_counter()
+    r = OS.solve(h, OS.load_vector(p), p.tol)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1, [x.iters for x in r]
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    p = workload(args.workload)
+    cores = os.cpu_count()
+    # each oracle step is a whole setup + solve (tens of seconds): at most two timed steps, no warm-up
+    steps = max(1, min(args.steps, 2))
+    times, iters = [], []
+    for _ in range(steps):
+        ts, tv, it = oracle_step(p)
+        times.append(ts + tv)
+        iters = it
+    total = sum(times)
+    value = steps * (1 if p.rhs is None else p.rhs.shape[0]) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": steps, "warmup": 0, "ms_per_step": 1e3 * total / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(p, args.workload, "fp64 (oracle)"),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{steps} full setup+solve of the workload on numpy/scipy "
+                                       f"(BLAS threads up to {cores}); iterations {iters}"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(p, budget_s=40.0):
+    """The oracle as it stands on this host: one full setup + solve of the workload."""
+    ts, tv, it = oracle_step(p)
+    return {"value": 1.0 / (ts + tv), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one full setup+solve of the workload (setup {ts:.1f} s, solve {tv:.1f} s, "
+                      f"{it[0]} iterations); numpy/scipy, BLAS threads up to {os.cpu_count()}"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2406_06283_gb300 import hk
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = workload(args.workload)
+    prec = hk.HK_FP32_PRECOND if args.precision == "fp32" else hk.HK_FP64
+    m = p.mesh
+    rhs_host = np.ascontiguousarray(np.atleast_2d(p.rhs), dtype=np.float64)
+    s = rhs_host.shape[0]
+    # inputs resident in HBM
+    d_xyz = torch.tensor(m.xyz, device=dev)
+    d_el = torch.tensor(m.elems, dtype=torch.int32, device=dev)
+    d_bnd = torch.tensor(m.is_boundary, dtype=torch.uint8, device=dev)
+    d_coeff = torch.tensor(p.coeff, device=dev)
+    d_e2s = torch.tensor(p.elem_to_sub, dtype=torch.int32, device=dev)
+    d_rhs = torch.tensor(rhs_host, device=dev)
+    d_u = torch.empty_like(d_rhs)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+
+    def setup_dev(precision=prec):
+        return hk.hk_setup_device(d_xyz, d_el, d_bnd, d_coeff, p.k, d_e2s, p.n_sub, p.overlap, p.tau, precision,
+                                  hk.HK_TWO_LEVEL, hk.HK_AS, p.restart, p.max_iters, sptr, n_dofs=m.n_dofs)
+
+    def device_step(record=None):
+        h = setup_dev()
+        if record is not None:
+            hk.hk_set_timing(h, True)
+        r = hk.hk_solve_device(h, d_rhs, d_u, p.tol)
+        if record is not None:
+            record.append((hk.hk_info(h), hk.hk_kernel_times(h), r.iters.copy()))
+        hk.hk_destroy(h)
+        return r
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    for _ in range(args.warmup):
+        device_step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    rec = []
+    step_ms = []
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        device_step(rec)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier(world)
+    clocks = sampler.stop()
+    t_rank = sum(step_ms) / 1e3
+    t_max = max_over_ranks(t_rank, world)
+    value = args.steps * s * world / t_max
+
+    # ---- e2e through the host-pointer calls (copies inside the timed region)
+    h2d = m.xyz.nbytes + m.elems.astype(np.int32).nbytes + m.is_boundary.nbytes + p.coeff.nbytes + \
+        p.elem_to_sub.astype(np.int32).nbytes + rhs_host.nbytes
+    d2h = rhs_host.nbytes + 4 * s + 8 * s
+    e2e_ms = []
+    for k in range(max(1, min(args.steps, 5))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = hk.hk_setup(m.xyz, m.elems, m.is_boundary, p.coeff, p.k, p.elem_to_sub, p.n_sub, p.overlap, p.tau, prec,
+                        hk.HK_TWO_LEVEL, hk.HK_AS, p.restart, p.max_iters, sptr)
+        hk.hk_solve(h, rhs_host, p.tol)
+        hk.hk_destroy(h)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_t = max_over_ranks(sum(e2e_ms) / 1e3, world)
+    e2e_value = len(e2e_ms) * s * world / e2e_t
+
+    # ---- solve-only (operator resident, as in serving): both precision forms
+    def solve_only(precision, n):
+        h = setup_dev(precision)
+        for _ in range(2):
+            hk.hk_solve_device(h, d_rhs, d_u, p.tol)
+        lat, its = [], None
+        for _ in range(n):
+            flush.fill_(1.0)
+            a, b = ev(), ev()
+            a.record(stream)
+            r = hk.hk_solve_device(h, d_rhs, d_u, p.tol)
+            b.record(stream)
+            b.synchronize()
+            lat.append(a.elapsed_time(b))
+            its = int(r.iters[0])
+        info = hk.hk_info(h)
+        hk.hk_destroy(h)
+        lat = np.array(lat)
+        return {"solves_per_s": float(s * 1e3 / lat.mean()), "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "iterations": its, "setup_ms": info["setup_ms"][5]}
+
+    so32 = solve_only(hk.HK_FP32_PRECOND, args.solve_reps)
+    so64 = solve_only(hk.HK_FP64, args.solve_reps)
+
+    # ---- roofline from the live kernel timings of the timed steps
+    info0, kt0, its0 = rec[0]
+    pf = 4 if prec == hk.HK_FP32_PRECOND else 8
+    n, n0 = info0["n_dofs"], info0["n0"]
+    It, fe, ze, lo = info0["dof_total"], info0["factor_elems"], info0["coarse_elems"], info0["lower_nnz"]
+    bytes_local = fe * pf + lo * (4 + pf) + n * 8 + It * 4 + ze * pf + It * pf + n0 * pf
+    bytes_coarse = n0 * n0 * pf + 2 * n0 * pf
+    bytes_scatter = It * pf + ze * pf + It * 8 + (n + 1) * 4 + n * 8 + n0 * pf
+    agg = {k: [0.0, 0] for k in kt0}
+    tri_ms, setup_ms = [], []
+    for info, kt, _ in rec:
+        for k, (ms, c) in kt.items():
+            agg[k][0] += ms
+            agg[k][1] += c
+        tri_ms.append(info["setup_ms"][6])
+        setup_ms.append(info["setup_ms"][5])
+    hbm, src = peaks()
+    per = {k: (v[0] / max(v[1], 1)) for k, v in agg.items()}
+    apply_ms = per["local_apply"] + per["coarse_solve"] + per["scatter"]
+    apply_bytes = bytes_local + bytes_coarse + bytes_scatter
+    roof_apply = {"bound": "hbm", "achieved": apply_bytes / (apply_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                  "frac": apply_bytes / (apply_ms * 1e-3) / 1e9 / hbm, "traffic": None,
+                  "kernels": "k_local_apply + k_coarse_solve + k_scatter", "bytes_per_apply": apply_bytes,
+                  "ms_per_apply": apply_ms, "peak_source": src}
+    # dominant kernel over the step: the tridiagonalisation (setup) vs the solve kernels
+    tot = {k: v[0] for k, v in agg.items()}
+    tot["tridiag"] = sum(tri_ms)
+    dom = max(tot, key=tot.get)
+    sizes = [hk_sub_sizes(p)]
+    if dom == "tridiag":
+        flops = sum(4.0 / 3.0 * nI ** 3 for nI in sizes[0])
+        ach = flops / (statistics.mean(tri_ms) * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel": "k_tridiag (FP64 Householder)",
+                "peak_source": "nominal FP64 (recipe table)"}
+    else:
+        b = {"local_apply": bytes_local, "coarse_solve": bytes_coarse, "scatter": bytes_scatter}.get(dom)
+        if b is None:
+            b = bytes_local
+        ach = b / (per[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                "kernel": dom, "peak_source": src}
+    launches_per_step = sum(v[1] for v in agg.values()) / len(rec)
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 Krylov / f32 preconditioner" if prec == hk.HK_FP32_PRECOND else "f64",
+            "data": "synthetic (seeded)", "config": workload_config(p, args.workload, args.precision),
+            "iterations": [int(x) for x in its0],
+            "phases_ms": {"setup": statistics.mean(setup_ms),
+                          "tridiag": statistics.mean(tri_ms),
+                          "solve": statistics.mean(step_ms) - statistics.mean(setup_ms)},
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+            "solve_only": {"fp32_precond": so32, "fp64": so64},
+            "kernel_ms_per_launch": per, "roofline": roof, "roofline_apply": roof_apply,
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": None, "clocks": clocks, "wall_s": wall}
+    line["gpu_launches_solve_kernels_per_step"] = launches_per_step
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def hk_sub_sizes(p):
+    """|dof(Omega_i)| of every subdomain, read back through the C ABI."""
+    from paper_2406_06283_gb300 import hk
+    h = hk.setup_problem(p, precision=hk.HK_FP32_PRECOND)
+    out = [hk.hk_get_subdomain(h, i)["dof"].size for i in range(p.n_sub)]
+    hk.hk_destroy(h)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--solve-reps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -90,6 +90,11 @@ typedef struct hk_handle hk_handle;
 hk_status hk_setup(const hk_mesh* mesh, const double* elem_coeff, double k,
                    const hk_params* params, void* cuda_stream, hk_handle** out);
 
+/* Same as hk_setup, with every array of `mesh`, `elem_coeff` and `params->elem_to_sub` in
+ * device memory of the current device (the library copies them; the caller keeps ownership). */
+hk_status hk_setup_device(const hk_mesh* mesh_dev, const double* elem_coeff_dev, double k,
+                          const hk_params* params, void* cuda_stream, hk_handle** out);
+
 /* Solve B u = rhs for n_rhs right-hand sides (load vectors) with FGMRES
  * preconditioned on the right by the setup's preconditioner, x_0 = 0, until
  * the relative residual ||rhs - B u|| / ||rhs|| <= tol (checked on the true
@@ -118,7 +123,12 @@ typedef struct {
   int nnz;                     /* nonzeros of B */
   int precision, levels;
   size_t bytes_resident;       /* device bytes held by the handle */
-  double setup_ms[8];          /* assembly, decomposition, local factors, eigen, coarse, total, -, - */
+  long long factor_elems;      /* entries of all local factor blocks S_j^{-1}, G_j (with 4-entry padding) */
+  long long dof_total;         /* sum_i |dof(Omega_i)| */
+  long long coarse_elems;      /* entries of all Z_i, sum_i |dof(Omega_i)| m_i */
+  long long lower_nnz;         /* couplings L_j read by the forward sweeps, sum over subdomains */
+  double setup_ms[8];          /* phases: assembly, decomposition, local factors, eigen, coarse,
+                                  total; [6] the Householder tridiagonalisation kernel alone; [7] 0 */
 } hk_info_t;
 
 hk_status hk_info(const hk_handle* h, hk_info_t* info);
@@ -128,6 +138,21 @@ hk_status hk_destroy(hk_handle* h);
 
 const char* hk_status_string(hk_status s);
 const char* hk_last_error(void);
+
+/* ---- Kernel timing (CUDA events on the handle's stream) ---- */
+enum {
+  HK_T_LOCAL_APPLY = 0,  /* gather, coarse restriction and local block sweeps (Eq. 2.22) */
+  HK_T_COARSE_SOLVE = 1, /* E^{-1} c (Eq. 2.23) */
+  HK_T_SCATTER = 2,      /* pull-form sum of local and coarse corrections */
+  HK_T_SPMV = 3,         /* B z */
+  HK_T_ARNOLDI = 4,      /* Gram-Schmidt passes, Givens update, normalisation */
+  HK_T_CYCLE = 5,        /* cycle end: least squares, x update, true residual */
+  HK_T_NCAT = 6
+};
+/* on != 0 starts recording the solve kernels of later calls (and clears earlier records). */
+hk_status hk_set_timing(hk_handle* h, int on);
+/* Sums the recorded launches per category: ms[HK_T_NCAT] milliseconds, count[HK_T_NCAT] launches. */
+hk_status hk_kernel_times(hk_handle* h, double* ms, int32_t* count);
 
 /* ---- Inspection and single-step calls (same data the solve uses) ---- */
 

@@ -70,6 +70,7 @@ static void destroy_all(hk_handle* h) {
   h->allocs.clear();
   if (h->h_state) cudaFreeHost(h->h_state);
   if (h->h_rstate) cudaFreeHost(h->h_rstate);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   cudaSetDevice(cur);
   delete h;
 }
@@ -122,8 +123,8 @@ static hk_status setup_impl(hk_handle* h, const hk_mesh* mesh, const double* coe
   return HK_OK;
 }
 
-extern "C" hk_status hk_setup(const hk_mesh* mesh, const double* elem_coeff, double k, const hk_params* prm,
-                              void* cuda_stream, hk_handle** out) {
+static hk_status setup_common(const hk_mesh* mesh, const double* elem_coeff, double k, const hk_params* prm,
+                              void* cuda_stream, hk_handle** out, bool dev_inputs) {
   if (!out) {
     hk_set_error("out is NULL");
     return HK_BAD_ARG;
@@ -153,6 +154,7 @@ extern "C" hk_status hk_setup(const hk_mesh* mesh, const double* elem_coeff, dou
   h->k = k;
   h->p = *prm;
   h->p.elem_to_sub = nullptr;
+  h->dev_inputs = dev_inputs;
   hk_status s = setup_impl(h, mesh, elem_coeff, prm);
   if (s != HK_OK) {
     cudaGetLastError();
@@ -160,6 +162,50 @@ extern "C" hk_status hk_setup(const hk_mesh* mesh, const double* elem_coeff, dou
     return s;
   }
   *out = h;
+  return HK_OK;
+}
+
+extern "C" hk_status hk_setup(const hk_mesh* mesh, const double* elem_coeff, double k, const hk_params* prm,
+                              void* cuda_stream, hk_handle** out) {
+  return setup_common(mesh, elem_coeff, k, prm, cuda_stream, out, false);
+}
+
+extern "C" hk_status hk_setup_device(const hk_mesh* mesh_dev, const double* elem_coeff_dev, double k,
+                                     const hk_params* prm, void* cuda_stream, hk_handle** out) {
+  return setup_common(mesh_dev, elem_coeff_dev, k, prm, cuda_stream, out, true);
+}
+
+cudaEvent_t hk_event(hk_handle* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+
+extern "C" hk_status hk_set_timing(hk_handle* h, int on) {
+  if (!h) return HK_BAD_ARG;
+  HK_CUDA(cudaStreamSynchronize(h->stream));
+  h->tl.clear();
+  h->ev_used = 0;
+  h->timing = on != 0;
+  return HK_OK;
+}
+
+extern "C" hk_status hk_kernel_times(hk_handle* h, double* ms, int32_t* count) {
+  if (!h || !ms || !count) return HK_BAD_ARG;
+  HK_CUDA(cudaStreamSynchronize(h->stream));
+  for (int c = 0; c < HK_T_NCAT; ++c) {
+    ms[c] = 0;
+    count[c] = 0;
+  }
+  for (auto& t : h->tl) {
+    float e = 0;
+    HK_CUDA(cudaEventElapsedTime(&e, t.a, t.b));
+    ms[t.cat] += e;
+    count[t.cat] += 1;
+  }
   return HK_OK;
 }
 
@@ -222,6 +268,10 @@ extern "C" hk_status hk_info(const hk_handle* h, hk_info_t* info) {
   info->precision = h->p.precision;
   info->levels = h->p.levels;
   info->bytes_resident = h->bytes;
+  info->factor_elems = h->f_total;
+  info->dof_total = h->I_total;
+  info->coarse_elems = h->z_total;
+  info->lower_nnz = h->lower_nnz;
   for (int i = 0; i < 8; ++i) info->setup_ms[i] = h->setup_ms[i];
   return HK_OK;
 }

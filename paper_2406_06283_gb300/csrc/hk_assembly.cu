@@ -236,10 +236,11 @@ hk_status phase_assembly(hk_handle* h, const hk_mesh* mesh, const double* coeff)
   HK_TRY(dalloc(h, &h->d_coeff, (size_t)ne));
   uint8_t* d_bnd = nullptr;
   HK_TRY(dalloc(h, &d_bnd, (size_t)nn));
-  HK_CUDA(cudaMemcpyAsync(h->d_xyz, mesh->xyz, sizeof(double) * nn * h->dim, cudaMemcpyHostToDevice, st));
-  HK_CUDA(cudaMemcpyAsync(h->d_elems, mesh->elems, sizeof(int) * ne * nv, cudaMemcpyHostToDevice, st));
-  HK_CUDA(cudaMemcpyAsync(h->d_coeff, coeff, sizeof(double) * ne, cudaMemcpyHostToDevice, st));
-  HK_CUDA(cudaMemcpyAsync(d_bnd, mesh->is_boundary, nn, cudaMemcpyHostToDevice, st));
+  cudaMemcpyKind kind = h->dev_inputs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  HK_CUDA(cudaMemcpyAsync(h->d_xyz, mesh->xyz, sizeof(double) * nn * h->dim, kind, st));
+  HK_CUDA(cudaMemcpyAsync(h->d_elems, mesh->elems, sizeof(int) * ne * nv, kind, st));
+  HK_CUDA(cudaMemcpyAsync(h->d_coeff, coeff, sizeof(double) * ne, kind, st));
+  HK_CUDA(cudaMemcpyAsync(d_bnd, mesh->is_boundary, nn, kind, st));
   k_check_elems<<<nblk(ne, 256), 256, 0, st>>>(h->d_elems, ne, nv, nn, h->d_status);
   k_check_coeff<<<nblk(ne, 256), 256, 0, st>>>(h->d_coeff, ne, h->d_status);
   HK_TRY(check_device_status(h, "mesh input"));

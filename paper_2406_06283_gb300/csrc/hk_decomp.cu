@@ -348,7 +348,8 @@ hk_status phase_decomposition(hk_handle* h, const int32_t* elem_to_sub, uint8_t*
   int ns = h->n_sub, ne = h->n_elems, nn = h->n_nodes, n = h->n, nv = h->nv;
   int* d_e2s = nullptr;
   HK_TRY(dalloc(h, &d_e2s, ne));
-  HK_CUDA(cudaMemcpyAsync(d_e2s, elem_to_sub, sizeof(int) * ne, cudaMemcpyHostToDevice, st));
+  HK_CUDA(cudaMemcpyAsync(d_e2s, elem_to_sub, sizeof(int) * ne,
+                          h->dev_inputs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   uint8_t *d_elem_in = nullptr, *d_node_in = nullptr, *d_cls = nullptr;
   HK_TRY(dalloc(h, &d_elem_in, (size_t)ne * ns));
   HK_TRY(dalloc(h, &d_node_in, (size_t)nn * ns));

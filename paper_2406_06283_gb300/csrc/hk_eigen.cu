@@ -597,7 +597,12 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   HK_TRY(check_device_status(h, "eigen: standard form"));
   size_t shm = sizeof(double) * 2 * (size_t)maxn;
   HK_CUDA(cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
   k_tridiag<<<ns, 1024, shm, st>>>(h->d_sub_info, d_W, d_ws, d_d, d_e, d_tau, d_voff);
+  cudaEventRecord(e1, st);
   HK_LAUNCH_CHECK();
   k_bisect<<<ns, 64, 0, st>>>(h->d_sub_info, d_d, d_e, d_voff, h->p.tau, h->d_lam, d_m, h->d_status);
   HK_LAUNCH_CHECK();
@@ -605,6 +610,13 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   std::vector<int> m(ns);
   HK_CUDA(cudaMemcpyAsync(m.data(), d_m, 4 * ns, cudaMemcpyDeviceToHost, st));
   HK_CUDA(cudaStreamSynchronize(st));
+  {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    h->setup_ms[6] = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
   int c0 = 0;
   long long zo = 0;
   std::vector<long long> qoff(ns), woff(ns);

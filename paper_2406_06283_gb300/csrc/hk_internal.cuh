@@ -78,7 +78,7 @@ struct hk_handle {
   hk_params p{};
   // sizes
   int nnz = 0, n0 = 0, max_mu = 0, lambda_elems = 0, max_level = 0, max_dof = 0;
-  long long I_total = 0, G_total = 0, f_total = 0, csr_total = 0, z_total = 0;
+  long long I_total = 0, G_total = 0, f_total = 0, csr_total = 0, z_total = 0, lower_nnz = 0;
   std::vector<Sub> subs;
   double setup_ms[8] = {0};
 
@@ -155,7 +155,31 @@ struct hk_handle {
 
   std::vector<void*> allocs;
   size_t bytes = 0;
+  bool dev_inputs = false;  // setup arrays are device pointers
+  // kernel timing
+  bool timing = false;
+  struct TL { int cat; cudaEvent_t a, b; };
+  std::vector<TL> tl;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
 };
+
+cudaEvent_t hk_event(hk_handle* h);
+// Wraps a launch in two recorded events when timing is on.
+#define HK_TIMED(h, cat, ...)                                        \
+  do {                                                               \
+    cudaEvent_t ta_ = nullptr;                                       \
+    if ((h)->timing) {                                               \
+      ta_ = hk_event(h);                                             \
+      cudaEventRecord(ta_, (h)->stream);                             \
+    }                                                                \
+    __VA_ARGS__;                                                     \
+    if ((h)->timing) {                                               \
+      cudaEvent_t tb_ = hk_event(h);                                 \
+      cudaEventRecord(tb_, (h)->stream);                             \
+      (h)->tl.push_back({(cat), ta_, tb_});                          \
+    }                                                                \
+  } while (0)
 
 // Allocation helper: zero-initialised device memory tracked by the handle.
 template <typename T>

@@ -342,7 +342,13 @@ hk_status run_fgmres(hk_handle* h, int s, const double* rhs_dev, double tol, dou
       double* vj = h->d_V + (long long)j * sn_;
       double* zj = h->d_Zk + (long long)j * sn_;
       HK_TRY(op_apply(h, s, vj, zj, act));
-      k_spmv<<<nblk(n, 256), 256, 0, st>>>(n, s, h->d_rowptr, h->d_col, h->d_valB, zj, h->d_w, act);
+      HK_TIMED(h, HK_T_SPMV,
+               (k_spmv<<<nblk(n, 256), 256, 0, st>>>(n, s, h->d_rowptr, h->d_col, h->d_valB, zj, h->d_w, act)));
+      cudaEvent_t ga = nullptr;
+      if (h->timing) {
+        ga = hk_event(h);
+        cudaEventRecord(ga, st);
+      }
       k_gs<0><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, m, j, h->d_V, h->d_w, h->d_state, h->d_rstate, h->d_hcol,
                                                   h->d_part, h->d_counter, h->d_H, h->d_cs, h->d_sn, h->d_g,
                                                   h->d_hist, mi, tol);
@@ -353,6 +359,11 @@ hk_status run_fgmres(hk_handle* h, int s, const double* rhs_dev, double tol, dou
                                                   h->d_part, h->d_counter, h->d_H, h->d_cs, h->d_sn, h->d_g,
                                                   h->d_hist, mi, tol);
       k_normalize<<<nblk(n, 256), 256, 0, st>>>(n, s, j, h->d_V, h->d_w, h->d_state, h->d_rstate);
+      if (h->timing) {
+        cudaEvent_t gb = hk_event(h);
+        cudaEventRecord(gb, st);
+        h->tl.push_back({HK_T_ARNOLDI, ga, gb});
+      }
       HK_LAUNCH_CHECK();
       HK_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(int) * 8 * s, cudaMemcpyDeviceToHost, st));
       HK_CUDA(cudaStreamSynchronize(st));
@@ -361,6 +372,11 @@ hk_status run_fgmres(hk_handle* h, int s, const double* rhs_dev, double tol, dou
       if (!any) break;
     }
     // cycle end: x += Zk y, true residual
+    cudaEvent_t ca = nullptr;
+    if (h->timing) {
+      ca = hk_event(h);
+      cudaEventRecord(ca, st);
+    }
     k_cycle_solve<<<nblk(s, 64), 64, 0, st>>>(s, m, h->d_state, h->d_H, h->d_g);
     k_xupdate<<<nblk(n, 256), 256, 0, st>>>(n, s, m, h->d_state, h->d_Zk, h->d_g, h->d_x);
     k_spmv<<<nblk(n, 256), 256, 0, st>>>(n, s, h->d_rowptr, h->d_col, h->d_valB, h->d_x, h->d_w, nullptr);
@@ -368,6 +384,11 @@ hk_status run_fgmres(hk_handle* h, int s, const double* rhs_dev, double tol, dou
     k_norm2<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, h->d_w, h->d_state, h->d_rstate, RS_BETA, h->d_part,
                                                 h->d_counter, 1);
     k_cycle_decide<<<nblk(s, 64), 64, 0, st>>>(s, h->d_state, h->d_rstate, tol, mi);
+    if (h->timing) {
+      cudaEvent_t cb = hk_event(h);
+      cudaEventRecord(cb, st);
+      h->tl.push_back({HK_T_CYCLE, ca, cb});
+    }
     HK_LAUNCH_CHECK();
     HK_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(int) * 8 * s, cudaMemcpyDeviceToHost, st));
     HK_CUDA(cudaStreamSynchronize(st));

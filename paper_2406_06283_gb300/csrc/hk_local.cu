@@ -174,6 +174,24 @@ __global__ void k_block_lu(const int* __restrict__ sub_info, const long long* __
   if (tid == 0 && !(minpiv > 1e-10 * scale)) dev_fail(st, HK_SINGULAR_LOCAL, s, minpiv / scale);
 }
 
+// Number of couplings L_j (row in level j, column in level j-1) of every subdomain.
+__global__ void k_count_lower(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
+                              const int* __restrict__ levptr, const int* __restrict__ lrow,
+                              const int* __restrict__ lcntI, const int* __restrict__ lcol,
+                              unsigned long long* out) {
+  int s = blockIdx.x;
+  const int* si = sub_info + 8 * s;
+  int L = si[2], off = si[3], loff = si[5];
+  long long coff = sub_off[3 * s + 1];
+  const int* lp = levptr + loff;
+  const int* lr = lrow + off + s;
+  unsigned long long c = 0;
+  for (int j = 1; j < L; ++j)
+    for (int a = lp[j] + threadIdx.x; a < lp[j + 1]; a += blockDim.x)
+      for (int q = 0; q < lcntI[off + a]; ++q) c += lcol[coff + lr[a] + q] < lp[j];
+  atomicAdd(out, c);
+}
+
 __global__ void k_to_f32(const double* __restrict__ a, float* b, long long n) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
@@ -198,6 +216,17 @@ hk_status phase_local_factors(hk_handle* h) {
   h->f_total = fo;
   HK_TRY(upload_sub_info(h));
   if (h->p.levels == HK_COARSE_ONLY) return HK_OK;
+  {
+    unsigned long long* d_cnt = nullptr;
+    HK_TRY(dalloc(h, &d_cnt, 1));
+    k_count_lower<<<ns, 128, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
+                                      d_cnt);
+    unsigned long long c = 0;
+    HK_CUDA(cudaMemcpyAsync(&c, d_cnt, sizeof(c), cudaMemcpyDeviceToHost, st));
+    HK_CUDA(cudaStreamSynchronize(st));
+    h->lower_nnz = (long long)c;
+    dfree(h, d_cnt);
+  }
   HK_TRY(dalloc(h, &h->d_F64, fo));
   size_t shm = sizeof(double) * (size_t)h->max_level * h->max_level;
   HK_CUDA(cudaFuncSetAttribute(k_block_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
@@ -393,9 +422,11 @@ static hk_status launch_local(hk_handle* h, int s, const double* v, const int* a
     return HK_UNSUPPORTED;
   }
   dim3 grid(h->n_sub, (s + NR - 1) / NR);
-  k_local_apply<T, NR><<<grid, 256, shm, h->stream>>>(h->n, s, v, active, h->d_sub_info, h->d_sub_off, h->d_lev,
-                                                      h->d_I, h->d_lrow, h->d_lcntI, h->d_lcol, lval, F, Z,
-                                                      do_local, do_coarse, h->I_total, h->n0, ybuf, cvec);
+  HK_TIMED(h, HK_T_LOCAL_APPLY,
+           (k_local_apply<T, NR><<<grid, 256, shm, h->stream>>>(h->n, s, v, active, h->d_sub_info, h->d_sub_off,
+                                                               h->d_lev, h->d_I, h->d_lrow, h->d_lcntI, h->d_lcol,
+                                                               lval, F, Z, do_local, do_coarse, h->I_total, h->n0,
+                                                               ybuf, cvec)));
   HK_LAUNCH_CHECK();
   return HK_OK;
 }
@@ -419,13 +450,14 @@ static hk_status apply_t(hk_handle* h, int s, const double* v, double* z, const 
   HK_TRY(rc);
   if (do_coarse) {
     int rows_per_block = 8;
-    k_coarse_solve<T><<<nblk(h->n0, rows_per_block), 32 * rows_per_block, 0, h->stream>>>(h->n0, s, Einv, c, cc,
-                                                                                           active);
+    HK_TIMED(h, HK_T_COARSE_SOLVE,
+             (k_coarse_solve<T><<<nblk(h->n0, rows_per_block), 32 * rows_per_block, 0, h->stream>>>(
+                 h->n0, s, Einv, c, cc, active)));
   }
-  k_scatter<T><<<nblk(h->n, 128), 128, 0, h->stream>>>(h->n, s, h->d_pull_ptr, h->d_pull_row, h->d_pull_sub,
-                                                       h->d_sub_info, h->d_sub_off, ybuf, Z, cc, h->I_total, h->n0,
-                                                       do_local, do_coarse, h->p.weighting == HK_RAS_POU, h->d_mu,
-                                                       z, active);
+  HK_TIMED(h, HK_T_SCATTER,
+           (k_scatter<T><<<nblk(h->n, 128), 128, 0, h->stream>>>(
+               h->n, s, h->d_pull_ptr, h->d_pull_row, h->d_pull_sub, h->d_sub_info, h->d_sub_off, ybuf, Z, cc,
+               h->I_total, h->n0, do_local, do_coarse, h->p.weighting == HK_RAS_POU, h->d_mu, z, active)));
   HK_LAUNCH_CHECK();
   return HK_OK;
 }

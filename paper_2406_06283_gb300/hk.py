@@ -49,7 +49,9 @@ class hk_info_t(C.Structure):
     _fields_ = [("dim", C.c_int), ("n_nodes", C.c_int), ("n_elems", C.c_int), ("n_dofs", C.c_int),
                 ("n_sub", C.c_int), ("n0", C.c_int), ("max_mu", C.c_int), ("lambda_elems", C.c_int),
                 ("max_level", C.c_int), ("max_dof", C.c_int), ("nnz", C.c_int), ("precision", C.c_int),
-                ("levels", C.c_int), ("bytes_resident", C.c_size_t), ("setup_ms", C.c_double * 8)]
+                ("levels", C.c_int), ("bytes_resident", C.c_size_t), ("factor_elems", C.c_longlong),
+                ("dof_total", C.c_longlong), ("coarse_elems", C.c_longlong), ("lower_nnz", C.c_longlong),
+                ("setup_ms", C.c_double * 8)]
 
 
 _lib = None
@@ -65,6 +67,9 @@ def lib():
         raise HKLibraryMissing(f"{LIB_PATH} not found: run `python -m paper_2406_06283_gb300.build`")
     L = C.CDLL(LIB_PATH)
     L.hk_setup.argtypes = [C.POINTER(hk_mesh), _P, C.c_double, C.POINTER(hk_params), _P, C.POINTER(_P)]
+    L.hk_setup_device.argtypes = [C.POINTER(hk_mesh), _P, C.c_double, C.POINTER(hk_params), _P, C.POINTER(_P)]
+    L.hk_set_timing.argtypes = [_P, C.c_int]
+    L.hk_kernel_times.argtypes = [_P, _P, _P]
     L.hk_solve.argtypes = [_P, C.c_int, _P, C.c_double, _P, _P, _P, _P]
     L.hk_solve_device.argtypes = [_P, C.c_int, _P, C.c_double, _P, _P, _P, _P]
     L.hk_info.argtypes = [_P, C.POINTER(hk_info_t)]
@@ -80,7 +85,7 @@ def lib():
     L.hk_apply_precond.argtypes = [_P, C.c_int, _P, _P]
     L.hk_matvec.argtypes = [_P, C.c_int, _P, _P]
     L.hk_assemble_load.argtypes = [_P, _P, _P]
-    for f in ("hk_setup", "hk_solve", "hk_solve_device", "hk_info", "hk_destroy", "hk_get_matrix",
+    for f in ("hk_setup", "hk_setup_device", "hk_set_timing", "hk_kernel_times", "hk_solve", "hk_solve_device", "hk_info", "hk_destroy", "hk_get_matrix",
               "hk_get_subdomain", "hk_get_mu", "hk_get_eigen", "hk_get_coarse", "hk_apply_precond", "hk_matvec",
               "hk_assemble_load"):
         getattr(L, f).restype = C.c_int
@@ -136,6 +141,37 @@ def hk_setup(xyz, elems, is_boundary, elem_coeff, k, elem_to_sub, n_sub, overlap
            "hk_setup")
     h = Handle(out, int((bnd == 0).sum()), int(max_iters))
     return h
+
+
+def hk_setup_device(xyz_dev, elems_dev, is_boundary_dev, elem_coeff_dev, k, elem_to_sub_dev, n_sub, overlap=2,
+                    tau=0.5, precision=HK_FP64, levels=HK_TWO_LEVEL, weighting=HK_AS, restart=50, max_iters=1000,
+                    stream=None, n_dofs=None) -> Handle:
+    """Setup from device-resident torch tensors (float64 xyz (n_nodes, dim), int32 elems, uint8 flags,
+    float64 coefficients, int32 partition)."""
+    mesh = hk_mesh(int(xyz_dev.shape[1]), int(xyz_dev.shape[0]), C.cast(_P(xyz_dev.data_ptr()), C.POINTER(C.c_double)),
+                   int(elems_dev.shape[0]), C.cast(_P(elems_dev.data_ptr()), C.POINTER(C.c_int32)),
+                   C.cast(_P(is_boundary_dev.data_ptr()), C.POINTER(C.c_uint8)))
+    prm = hk_params(int(n_sub), C.cast(_P(elem_to_sub_dev.data_ptr()), C.POINTER(C.c_int32)), int(overlap), float(tau),
+                    int(precision), int(levels), int(weighting), int(restart), int(max_iters))
+    out = _P()
+    _check(lib().hk_setup_device(C.byref(mesh), _P(elem_coeff_dev.data_ptr()), float(k), C.byref(prm),
+                                 _P(stream or 0), C.byref(out)), "hk_setup_device")
+    n = n_dofs if n_dofs is not None else int((is_boundary_dev == 0).sum().item())
+    return Handle(out, n, int(max_iters))
+
+
+HK_T_NAMES = ("local_apply", "coarse_solve", "scatter", "spmv", "arnoldi", "cycle_end")
+
+
+def hk_set_timing(h: Handle, on: bool = True):
+    _check(lib().hk_set_timing(h.ptr, int(bool(on))), "hk_set_timing")
+
+
+def hk_kernel_times(h: Handle) -> dict:
+    ms = np.zeros(len(HK_T_NAMES))
+    cnt = np.zeros(len(HK_T_NAMES), dtype=np.int32)
+    _check(lib().hk_kernel_times(h.ptr, _ptr(ms), _ptr(cnt)), "hk_kernel_times")
+    return {n: (float(ms[i]), int(cnt[i])) for i, n in enumerate(HK_T_NAMES)}
 
 
 def setup_problem(p, precision=HK_FP64, levels=HK_TWO_LEVEL, weighting=HK_AS, stream=None) -> Handle:
