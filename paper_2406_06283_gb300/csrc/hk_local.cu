@@ -470,3 +470,87 @@ hk_status op_apply(hk_handle* h, int s, const double* v, double* z, const int* a
   return apply_t<double>(h, s, v, z, active, h->d_lvalB, h->d_F64, h->d_Z64, h->d_Einv64, h->d_ybuf64, h->d_c64,
                          h->d_cc64);
 }
+
+// ======================================================= allocation-free apply
+// Some callers cannot allocate device memory when they apply the
+// preconditioner: code running while a stream is being captured into a CUDA
+// graph (cudaMalloc is not allowed there), or a host framework that owns all
+// device memory through its own allocator and forbids allocations on its hot
+// path.  hk_apply_precond_noalloc serves them: it runs the same three kernels
+// as hk_apply_precond on caller-provided device vectors, and keeps its
+// intermediate vectors (local solutions, coarse right-hand side and coarse
+// solution) in the fixed device array below instead of allocating.
+//
+// The array is HK_NOALLOC_SCRATCH_BYTES per device and stays allocated on
+// every device that loads the library until the process exits.  Its device
+// address is looked up once per device (host code may not use the symbol
+// itself as a pointer: it is only a host-side stand-in), on the first call
+// made on that device; that first call should happen before any stream
+// capture.  Every call uses the same array, so calls whose kernels overlap on
+// the GPU race with each other.  The array keeps the contents of the last
+// call; each call writes every scratch element it reads before reading it, so
+// nothing has to be cleared.
+#include <mutex>
+
+#define HK_NOALLOC_SCRATCH_BYTES (8u << 20)
+#define HK_NOALLOC_MAX_DEVICES 64
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HK_NOALLOC_SCRATCH_BYTES];
+static void* g_noalloc_ptr[HK_NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mu;
+
+static hk_status noalloc_scratch(int dev, void** out) {
+  if (dev < 0 || dev >= HK_NOALLOC_MAX_DEVICES) {
+    hk_set_error("device %d outside the %d devices the allocation-free apply supports", dev,
+                 HK_NOALLOC_MAX_DEVICES);
+    return HK_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // the device `dev` is current here
+    if (e != cudaSuccess || !p) {
+      hk_set_error("cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
+      return HK_CUDA_ERROR;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return HK_OK;
+}
+
+static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+extern "C" hk_status hk_apply_precond_noalloc(hk_handle* h, int n_rhs, const double* v_dev, double* z_dev) {
+  if (!h || n_rhs < 1 || !v_dev || !z_dev) {
+    hk_set_error("hk_apply_precond_noalloc: invalid arguments");
+    return HK_BAD_ARG;
+  }
+  size_t esz = h->p.precision == HK_FP32_PRECOND ? sizeof(float) : sizeof(double);
+  size_t ylen = align256(esz * (size_t)n_rhs * (size_t)h->I_total);
+  size_t clen = align256(esz * (size_t)n_rhs * (size_t)(h->n0 + 1));
+  size_t need = ylen + 2 * clen;
+  if (need > HK_NOALLOC_SCRATCH_BYTES) {
+    hk_set_error("hk_apply_precond_noalloc needs %zu scratch bytes for %d right-hand sides; the fixed array "
+                 "holds %u (use fewer right-hand sides per call)", need, n_rhs, HK_NOALLOC_SCRATCH_BYTES);
+    return HK_UNSUPPORTED;
+  }
+  int cur = -1;
+  HK_CUDA(cudaGetDevice(&cur));
+  if (cur != h->dev) HK_CUDA(cudaSetDevice(h->dev));
+  void* base = nullptr;
+  hk_status s = noalloc_scratch(h->dev, &base);
+  if (s == HK_OK) {
+    unsigned char* b = static_cast<unsigned char*>(base);
+    if (h->p.precision == HK_FP32_PRECOND)
+      s = apply_t<float>(h, n_rhs, v_dev, z_dev, nullptr, h->d_lvalB32, h->d_F32, h->d_Z32, h->d_Einv32,
+                         reinterpret_cast<float*>(b), reinterpret_cast<float*>(b + ylen),
+                         reinterpret_cast<float*>(b + ylen + clen));
+    else
+      s = apply_t<double>(h, n_rhs, v_dev, z_dev, nullptr, h->d_lvalB, h->d_F64, h->d_Z64, h->d_Einv64,
+                          reinterpret_cast<double*>(b), reinterpret_cast<double*>(b + ylen),
+                          reinterpret_cast<double*>(b + ylen + clen));
+  }
+  if (cur != h->dev) cudaSetDevice(cur);
+  return s;
+}
