@@ -154,6 +154,9 @@ hk_status hk_set_timing(hk_handle* h, int on);
 /* Sums the recorded launches per category: ms[HK_T_NCAT] milliseconds, count[HK_T_NCAT] launches. */
 hk_status hk_kernel_times(hk_handle* h, double* ms, int32_t* count);
 
+/* Number of CUDA kernels the library has launched in this process so far (all handles). */
+long long hk_kernel_launches(void);
+
 /* ---- Inspection and single-step calls (same data the solve uses) ---- */
 
 /* CSR of B (which = 0) or D_k (which = 1): rowptr n_dofs+1, col/val nnz. */

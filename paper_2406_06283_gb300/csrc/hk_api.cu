@@ -8,6 +8,9 @@
 #include "hk_internal.cuh"
 
 static thread_local char g_err[512] = "";
+std::atomic<long long> g_hk_launches{0};
+
+extern "C" long long hk_kernel_launches(void) { return g_hk_launches.load(); }
 
 void hk_set_error(const char* fmt, ...) {
   va_list ap;

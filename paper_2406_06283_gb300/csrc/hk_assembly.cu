@@ -35,7 +35,7 @@ __global__ void k_scan_exclusive(const int* __restrict__ in, int* __restrict__ o
 }
 
 void launch_scan_exclusive(const int* in, int* out, int n, int* total, cudaStream_t st) {
-  k_scan_exclusive<<<1, 1024, 0, st>>>(in, out, n, total);
+  k_scan_exclusive<<<1, 1024, 0, st>>>(in, out, n, total); HK_COUNT_LAUNCH();
 }
 
 // ---------------------------------------------------------------- kernels
@@ -241,8 +241,8 @@ hk_status phase_assembly(hk_handle* h, const hk_mesh* mesh, const double* coeff)
   HK_CUDA(cudaMemcpyAsync(h->d_elems, mesh->elems, sizeof(int) * ne * nv, kind, st));
   HK_CUDA(cudaMemcpyAsync(h->d_coeff, coeff, sizeof(double) * ne, kind, st));
   HK_CUDA(cudaMemcpyAsync(d_bnd, mesh->is_boundary, nn, kind, st));
-  k_check_elems<<<nblk(ne, 256), 256, 0, st>>>(h->d_elems, ne, nv, nn, h->d_status);
-  k_check_coeff<<<nblk(ne, 256), 256, 0, st>>>(h->d_coeff, ne, h->d_status);
+  k_check_elems<<<nblk(ne, 256), 256, 0, st>>>(h->d_elems, ne, nv, nn, h->d_status); HK_COUNT_LAUNCH();
+  k_check_coeff<<<nblk(ne, 256), 256, 0, st>>>(h->d_coeff, ne, h->d_status); HK_COUNT_LAUNCH();
   HK_TRY(check_device_status(h, "mesh input"));
 
   // dof numbering: interior nodes in increasing node order
@@ -250,7 +250,7 @@ hk_status phase_assembly(hk_handle* h, const hk_mesh* mesh, const double* coeff)
   HK_TRY(dalloc(h, &d_flag, nn));
   HK_TRY(dalloc(h, &d_scan, nn));
   HK_TRY(dalloc(h, &d_tot, 1));
-  k_interior_flags<<<nblk(nn, 256), 256, 0, st>>>(d_bnd, d_flag, nn);
+  k_interior_flags<<<nblk(nn, 256), 256, 0, st>>>(d_bnd, d_flag, nn); HK_COUNT_LAUNCH();
   launch_scan_exclusive(d_flag, d_scan, nn, d_tot, st);
   int n = 0;
   HK_CUDA(cudaMemcpyAsync(&n, d_tot, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -262,18 +262,18 @@ hk_status phase_assembly(hk_handle* h, const hk_mesh* mesh, const double* coeff)
   h->n = n;
   HK_TRY(dalloc(h, &h->d_dof_of_node, nn));
   HK_TRY(dalloc(h, &h->d_node_of_dof, n));
-  k_dof_maps<<<nblk(nn, 256), 256, 0, st>>>(d_bnd, d_scan, h->d_dof_of_node, h->d_node_of_dof, nn);
+  k_dof_maps<<<nblk(nn, 256), 256, 0, st>>>(d_bnd, d_scan, h->d_dof_of_node, h->d_node_of_dof, nn); HK_COUNT_LAUNCH();
 
   // node -> element stars
   int* d_cnt = d_flag;  // reuse
   HK_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int) * nn, st));
-  k_count_star<<<nblk(ne, 256), 256, 0, st>>>(h->d_elems, ne, nv, d_cnt);
+  k_count_star<<<nblk(ne, 256), 256, 0, st>>>(h->d_elems, ne, nv, d_cnt); HK_COUNT_LAUNCH();
   HK_TRY(dalloc(h, &h->d_ne_ptr, nn + 1));
   launch_scan_exclusive(d_cnt, h->d_ne_ptr, nn, h->d_ne_ptr + nn, st);
   HK_TRY(dalloc(h, &h->d_ne_idx, (size_t)ne * nv));
   HK_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int) * nn, st));
-  k_fill_star<<<nblk(ne, 256), 256, 0, st>>>(h->d_elems, ne, nv, h->d_ne_ptr, d_cnt, h->d_ne_idx);
-  k_sort_star<<<nblk(nn, 256), 256, 0, st>>>(h->d_ne_ptr, h->d_ne_idx, nn, h->d_status);
+  k_fill_star<<<nblk(ne, 256), 256, 0, st>>>(h->d_elems, ne, nv, h->d_ne_ptr, d_cnt, h->d_ne_idx); HK_COUNT_LAUNCH();
+  k_sort_star<<<nblk(nn, 256), 256, 0, st>>>(h->d_ne_ptr, h->d_ne_idx, nn, h->d_status); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   HK_TRY(check_device_status(h, "element stars"));
 
@@ -281,7 +281,7 @@ hk_status phase_assembly(hk_handle* h, const hk_mesh* mesh, const double* coeff)
   int* d_rowcnt = nullptr;
   HK_TRY(dalloc(h, &d_rowcnt, n));
   k_row_count<<<nblk(n, 128), 128, 0, st>>>(n, h->d_node_of_dof, h->d_dof_of_node, h->d_ne_ptr, h->d_ne_idx,
-                                            h->d_elems, nv, d_rowcnt, h->d_status);
+                                            h->d_elems, nv, d_rowcnt, h->d_status); HK_COUNT_LAUNCH();
   HK_TRY(dalloc(h, &h->d_rowptr, n + 1));
   launch_scan_exclusive(d_rowcnt, h->d_rowptr, n, h->d_rowptr + n, st);
   HK_TRY(check_device_status(h, "matrix pattern"));
@@ -296,8 +296,8 @@ hk_status phase_assembly(hk_handle* h, const hk_mesh* mesh, const double* coeff)
   HK_TRY(dalloc(h, &d_M, nnz));
   k_row_fill<<<nblk(n, 128), 128, 0, st>>>(n, h->dim, h->d_xyz, h->d_elems, h->d_coeff, h->d_node_of_dof,
                                            h->d_dof_of_node, h->d_ne_ptr, h->d_ne_idx, h->d_rowptr, h->d_col,
-                                           d_K, d_M);
-  k_combine<<<nblk(nnz, 256), 256, 0, st>>>(nnz, h->k * h->k, d_K, d_M, h->d_valB, h->d_valD);
+                                           d_K, d_M); HK_COUNT_LAUNCH();
+  k_combine<<<nblk(nnz, 256), 256, 0, st>>>(nnz, h->k * h->k, d_K, d_M, h->d_valB, h->d_valD); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   HK_CUDA(cudaStreamSynchronize(st));
   dfree(h, d_K);
@@ -312,7 +312,7 @@ hk_status phase_assembly(hk_handle* h, const hk_mesh* mesh, const double* coeff)
 
 hk_status op_load(hk_handle* h, const double* f_nodal_dev, double* rhs_dev) {
   k_load<<<nblk(h->n, 128), 128, 0, h->stream>>>(h->n, h->dim, h->d_xyz, h->d_elems, h->d_node_of_dof,
-                                                 h->d_ne_ptr, h->d_ne_idx, f_nodal_dev, rhs_dev);
+                                                 h->d_ne_ptr, h->d_ne_idx, f_nodal_dev, rhs_dev); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   return HK_OK;
 }

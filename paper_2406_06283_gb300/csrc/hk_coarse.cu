@@ -167,7 +167,7 @@ hk_status phase_coarse(hk_handle* h) {
   if (n0 == 0) return HK_OK;
   uint8_t* d_pair = nullptr;
   HK_TRY(dalloc(h, &d_pair, (size_t)ns * ns));
-  k_coarse_pairs<<<nblk(n, 256), 256, 0, st>>>(n, ns, h->d_rowptr, h->d_col, h->d_pull_ptr, h->d_pull_sub, d_pair);
+  k_coarse_pairs<<<nblk(n, 256), 256, 0, st>>>(n, ns, h->d_rowptr, h->d_col, h->d_pull_ptr, h->d_pull_sub, d_pair); HK_COUNT_LAUNCH();
   std::vector<uint8_t> pair((size_t)ns * ns);
   HK_CUDA(cudaMemcpyAsync(pair.data(), d_pair, pair.size(), cudaMemcpyDeviceToHost, st));
   HK_CUDA(cudaStreamSynchronize(st));
@@ -188,23 +188,25 @@ hk_status phase_coarse(hk_handle* h) {
   for (auto& u : h->subs) maxm = u.m > maxm ? u.m : maxm;
   size_t shm = sizeof(double) * HK_ECHUNK * maxm;
   HK_CUDA(cudaFuncSetAttribute(k_coarse_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  if (np > 0)
+  if (np > 0) {
     k_coarse_block<<<np, 256, shm, st>>>(d_plist, n0, h->d_sub_info, h->d_sub_off, h->d_I, h->d_Isorted,
                                          h->d_perm, h->d_rowptr, h->d_col, h->d_valB, h->d_Z64, h->d_E);
+    HK_COUNT_LAUNCH();
+  }
   HK_LAUNCH_CHECK();
   HK_CUDA(cudaMemcpyAsync(h->d_Einv64, h->d_E, sizeof(double) * n0 * n0, cudaMemcpyDeviceToDevice, st));
   double* d_sc = nullptr;  // [0] max|E|, [1] min pivot
   int* d_piv = nullptr;
   HK_TRY(dalloc(h, &d_sc, 2));
   HK_TRY(dalloc(h, &d_piv, n0));
-  k_absmax<<<304, 256, 0, st>>>(h->d_E, (long long)n0 * n0, d_sc);
+  k_absmax<<<304, 256, 0, st>>>(h->d_E, (long long)n0 * n0, d_sc); HK_COUNT_LAUNCH();
   double big = 1e300;
   HK_CUDA(cudaMemcpyAsync(d_sc + 1, &big, sizeof(double), cudaMemcpyHostToDevice, st));
   for (int k = 0; k < n0; ++k) {
-    k_gj_pivot<<<1, 1024, 0, st>>>(h->d_Einv64, n0, k, d_piv, d_sc + 1);
-    k_gj_elim<<<nblk((long long)n0 * 32, 256), 256, 0, st>>>(h->d_Einv64, n0, k);
+    k_gj_pivot<<<1, 1024, 0, st>>>(h->d_Einv64, n0, k, d_piv, d_sc + 1); HK_COUNT_LAUNCH();
+    k_gj_elim<<<nblk((long long)n0 * 32, 256), 256, 0, st>>>(h->d_Einv64, n0, k); HK_COUNT_LAUNCH();
   }
-  k_gj_unscramble<<<nblk(n0, 128), 128, 0, st>>>(h->d_Einv64, n0, d_piv);
+  k_gj_unscramble<<<nblk(n0, 128), 128, 0, st>>>(h->d_Einv64, n0, d_piv); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   double sc[2];
   HK_CUDA(cudaMemcpyAsync(sc, d_sc, sizeof(sc), cudaMemcpyDeviceToHost, st));
@@ -216,10 +218,9 @@ hk_status phase_coarse(hk_handle* h) {
   if (h->p.precision == HK_FP32_PRECOND) {
     HK_TRY(dalloc(h, &h->d_Einv32, (size_t)n0 * n0));
     launch_to_f32(h->d_Einv64, h->d_Einv32, (long long)n0 * n0, st);
-    HK_TRY(dalloc(h, &h->d_Z32, h->z_total));
-    launch_to_f32(h->d_Z64, h->d_Z32, h->z_total, st);
     HK_LAUNCH_CHECK();
   }
+  HK_TRY(build_apply_z(h));
   HK_CUDA(cudaStreamSynchronize(st));
   dfree(h, d_pair);
   dfree(h, d_plist);

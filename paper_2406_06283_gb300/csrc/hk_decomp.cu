@@ -354,11 +354,11 @@ hk_status phase_decomposition(hk_handle* h, const int32_t* elem_to_sub, uint8_t*
   HK_TRY(dalloc(h, &d_elem_in, (size_t)ne * ns));
   HK_TRY(dalloc(h, &d_node_in, (size_t)nn * ns));
   long long NE = (long long)ne * ns, NN = (long long)nn * ns, ND = (long long)n * ns;
-  k_init_elem_in<<<nblk(NE, 256), 256, 0, st>>>(d_e2s, ne, ns, d_elem_in, h->d_status);
+  k_init_elem_in<<<nblk(NE, 256), 256, 0, st>>>(d_e2s, ne, ns, d_elem_in, h->d_status); HK_COUNT_LAUNCH();
   for (int layer = 0; layer < h->p.overlap_layers; ++layer) {
     k_mark_nodes<<<nblk(NN, 256), 256, 0, st>>>(nn, ns, ne, h->d_dof_of_node, h->d_ne_ptr, h->d_ne_idx, d_elem_in,
-                                                d_node_in);
-    k_grow<<<nblk(NE, 256), 256, 0, st>>>(ne, ns, nn, nv, h->d_elems, d_node_in, d_elem_in);
+                                                d_node_in); HK_COUNT_LAUNCH();
+    k_grow<<<nblk(NE, 256), 256, 0, st>>>(ne, ns, nn, nv, h->d_elems, d_node_in, d_elem_in); HK_COUNT_LAUNCH();
   }
   HK_LAUNCH_CHECK();
   HK_TRY(check_device_status(h, "partition"));
@@ -366,16 +366,16 @@ hk_status phase_decomposition(hk_handle* h, const int32_t* elem_to_sub, uint8_t*
   dfree(h, d_e2s);
   HK_TRY(dalloc(h, &d_cls, (size_t)n * ns));
   k_classify<<<nblk(ND, 256), 256, 0, st>>>(n, ns, ne, h->d_node_of_dof, h->d_ne_ptr, h->d_ne_idx, d_elem_in,
-                                            d_cls);
+                                            d_cls); HK_COUNT_LAUNCH();
   int* d_scal = nullptr;  // [0] max mu, [1] Lambda, [2] max level width
   HK_TRY(dalloc(h, &d_scal, 4));
   HK_TRY(dalloc(h, &h->d_mu, n));
-  k_mu<<<nblk(n, 256), 256, 0, st>>>(n, ns, d_cls, h->d_mu, d_scal, h->d_status);
-  k_elem_mult<<<nblk(ne, 256), 256, 0, st>>>(ne, ns, d_elem_in, d_scal + 1);
+  k_mu<<<nblk(n, 256), 256, 0, st>>>(n, ns, d_cls, h->d_mu, d_scal, h->d_status); HK_COUNT_LAUNCH();
+  k_elem_mult<<<nblk(ne, 256), 256, 0, st>>>(ne, ns, d_elem_in, d_scal + 1); HK_COUNT_LAUNCH();
   int *d_nI = nullptr, *d_nG = nullptr;
   HK_TRY(dalloc(h, &d_nI, ns));
   HK_TRY(dalloc(h, &d_nG, ns));
-  k_count_cls<<<ns, 512, 0, st>>>(n, d_cls, d_nI, d_nG);
+  k_count_cls<<<ns, 512, 0, st>>>(n, d_cls, d_nI, d_nG); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   HK_TRY(check_device_status(h, "partition of unity"));
   std::vector<int> nI(ns), nG(ns), scal(4);
@@ -412,13 +412,13 @@ hk_status phase_decomposition(hk_handle* h, const int32_t* elem_to_sub, uint8_t*
   HK_TRY(dalloc(h, &h->d_perm, Ioff));
   HK_TRY(dalloc(h, &h->d_G, Goff));
   HK_TRY(dalloc(h, &h->d_lev, Ioff + ns));
-  k_compact<<<ns, 1024, 0, st>>>(n, d_cls, h->d_sub_info, h->d_Isorted, h->d_G);
+  k_compact<<<ns, 1024, 0, st>>>(n, d_cls, h->d_sub_info, h->d_Isorted, h->d_G); HK_COUNT_LAUNCH();
   int *d_level = nullptr, *d_L = nullptr, *d_cap = nullptr;
   HK_TRY(dalloc(h, &d_level, Ioff));
   HK_TRY(dalloc(h, &d_L, ns));
   HK_TRY(dalloc(h, &d_cap, ns));
   k_levels<<<ns, 512, 0, st>>>(h->dim, h->d_xyz, h->d_node_of_dof, h->d_rowptr, h->d_col, h->d_sub_info,
-                               h->d_Isorted, d_level, d_L, d_cap, h->d_status);
+                               h->d_Isorted, d_level, d_L, d_cap, h->d_status); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   std::vector<int> L(ns), cap(ns);
   HK_CUDA(cudaMemcpyAsync(L.data(), d_L, sizeof(int) * ns, cudaMemcpyDeviceToHost, st));
@@ -434,7 +434,7 @@ hk_status phase_decomposition(hk_handle* h, const int32_t* elem_to_sub, uint8_t*
   h->csr_total = coff;
   HK_TRY(upload_sub_info(h));
   k_order<<<ns, 512, 0, st>>>(h->d_sub_info, h->d_Isorted, d_level, h->d_lev, h->d_perm, h->d_I, d_scal + 2,
-                              h->d_status);
+                              h->d_status); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   HK_TRY(check_device_status(h, "level order"));
   HK_CUDA(cudaMemcpyAsync(&h->max_level, d_scal + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -448,7 +448,7 @@ hk_status phase_decomposition(hk_handle* h, const int32_t* elem_to_sub, uint8_t*
   int* d_bw = d_L;
   k_local_csr<<<ns, 256, 0, st>>>(h->d_rowptr, h->d_col, h->d_valB, h->d_valD, h->d_sub_info, h->d_sub_off,
                                   h->d_Isorted, h->d_perm, h->d_I, h->d_G, h->d_lrow, h->d_lcntI, h->d_lcntG,
-                                  h->d_lcol, h->d_lvalB, h->d_lvalD, d_bw, h->d_status);
+                                  h->d_lcol, h->d_lvalB, h->d_lvalD, d_bw, h->d_status); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   std::vector<int> bw(ns);
   HK_CUDA(cudaMemcpyAsync(bw.data(), d_bw, sizeof(int) * ns, cudaMemcpyDeviceToHost, st));
@@ -462,7 +462,7 @@ hk_status phase_decomposition(hk_handle* h, const int32_t* elem_to_sub, uint8_t*
   HK_TRY(dalloc(h, &h->d_pull_row, Ioff));
   HK_TRY(dalloc(h, &h->d_pull_sub, Ioff));
   k_pull_fill<<<nblk(n, 256), 256, 0, st>>>(n, ns, d_cls, h->d_sub_info, h->d_Isorted, h->d_perm, h->d_pull_ptr,
-                                            h->d_pull_row, h->d_pull_sub);
+                                            h->d_pull_row, h->d_pull_sub); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   HK_CUDA(cudaStreamSynchronize(st));
   dfree(h, d_cls);

@@ -586,13 +586,13 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
 
   k_gamma_block<<<ns, 128, 0, st>>>(h->dim, h->n_elems, h->d_xyz, h->d_elems, h->d_coeff, h->k * h->k,
                                     h->d_node_of_dof, h->d_dof_of_node, h->d_ne_ptr, h->d_ne_idx, d_elem_in,
-                                    h->d_sub_info, h->d_G, d_Gw, d_ws);
+                                    h->d_sub_info, h->d_G, d_Gw, d_ws); HK_COUNT_LAUNCH();
   k_schur<<<ns, 256, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lrow, h->d_lcntI, h->d_lcntG, h->d_lcol,
-                              h->d_lvalB, d_W, d_Gw, d_Rw, d_ring, d_ws, h->d_status);
+                              h->d_lvalB, d_W, d_Gw, d_Rw, d_ring, d_ws, h->d_status); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   HK_TRY(check_device_status(h, "eigen: Gamma elimination"));
   k_stdform<<<ns, 512, 0, st>>>(h->d_sub_info, h->d_sub_off, d_bw, h->d_I, h->d_mu, h->d_lrow, h->d_lcntI,
-                                h->d_lcol, h->d_lvalD, d_W, d_T, d_L, d_ws, h->d_status);
+                                h->d_lcol, h->d_lvalD, d_W, d_T, d_L, d_ws, h->d_status); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   HK_TRY(check_device_status(h, "eigen: standard form"));
   size_t shm = sizeof(double) * 2 * (size_t)maxn;
@@ -601,10 +601,10 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, st);
-  k_tridiag<<<ns, 1024, shm, st>>>(h->d_sub_info, d_W, d_ws, d_d, d_e, d_tau, d_voff);
+  k_tridiag<<<ns, 1024, shm, st>>>(h->d_sub_info, d_W, d_ws, d_d, d_e, d_tau, d_voff); HK_COUNT_LAUNCH();
   cudaEventRecord(e1, st);
   HK_LAUNCH_CHECK();
-  k_bisect<<<ns, 64, 0, st>>>(h->d_sub_info, d_d, d_e, d_voff, h->p.tau, h->d_lam, d_m, h->d_status);
+  k_bisect<<<ns, 64, 0, st>>>(h->d_sub_info, d_d, d_e, d_voff, h->p.tau, h->d_lam, d_m, h->d_status); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   HK_TRY(check_device_status(h, "eigen: bisection"));
   std::vector<int> m(ns);
@@ -645,10 +645,10 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
     HK_TRY(dalloc(h, &h->d_Z64, zo));
     HK_CUDA(cudaMemcpyAsync(d_qoff, qoff.data(), 8 * ns, cudaMemcpyHostToDevice, st));
     HK_CUDA(cudaMemcpyAsync(d_woff, woff.data(), 8 * ns, cudaMemcpyHostToDevice, st));
-    k_inviter<<<ns, 32, 0, st>>>(h->d_sub_info, d_d, d_e, d_voff, h->d_lam, d_qoff, d_Q, d_woff, d_wk);
+    k_inviter<<<ns, 32, 0, st>>>(h->d_sub_info, d_d, d_e, d_voff, h->d_lam, d_qoff, d_Q, d_woff, d_wk); HK_COUNT_LAUNCH();
     HK_LAUNCH_CHECK();
     k_backtransform<<<ns, 256, 0, st>>>(h->d_sub_info, h->d_sub_off, d_bw, d_W, d_L, d_ws, d_tau, d_voff, d_qoff,
-                                        d_Q, h->d_Z64);
+                                        d_Q, h->d_Z64); HK_COUNT_LAUNCH();
     HK_LAUNCH_CHECK();
     HK_CUDA(cudaStreamSynchronize(st));
     dfree(h, d_Q);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -31,6 +32,10 @@ __device__ __forceinline__ void dev_fail(DevStatus* st, int code, int where, dou
 }
 
 void hk_set_error(const char* fmt, ...);
+
+// Every kernel launch of the library bumps this process-wide counter (hk_kernel_launches()).
+extern std::atomic<long long> g_hk_launches;
+#define HK_COUNT_LAUNCH() g_hk_launches.fetch_add(1, std::memory_order_relaxed)
 
 #define HK_TRY(expr)                         \
   do {                                       \
@@ -111,18 +116,21 @@ struct hk_handle {
   int* d_lcol = nullptr;          // csr_total
   double* d_lvalB = nullptr;      // csr_total
   double* d_lvalD = nullptr;      // csr_total
-  float* d_lvalB32 = nullptr;     // csr_total (FP32 form)
   // pull map
   int* d_pull_ptr = nullptr;      // n + 1
   int* d_pull_row = nullptr;      // entries: global row in concatenated level-ordered arrays
   int* d_pull_sub = nullptr;      // entries: subdomain id
-  // local factors: per level S_j^{-1} (b_j x b_j) then G_j (b_j x b_{j+1}), row-major
+  // local factors: per level S_j^{-1} (b_j x b_j) then G_j (b_j x b_{j+1}), row-major (setup only)
   double* d_F64 = nullptr;
-  float* d_F32 = nullptr;
+  // level records streamed by the apply (see hk_local.cu), their table and the largest record
+  unsigned char* d_pack = nullptr;
+  long long* d_lvtab = nullptr;
+  long long pack_bytes = 0, pack_stage = 0;
   // coarse space
   double* d_lam = nullptr;        // per subdomain kept eigenvalues (HK_MAXM each)
   double* d_Z64 = nullptr;        // z_total, per subdomain nI x m row-major
-  float* d_Z32 = nullptr;
+  void* d_Zr = nullptr;           // Z in the apply's type, row-major (the pull-form prolongation)
+  void* d_Zt = nullptr;           // Z in the apply's type, per subdomain m x nI (the restriction)
   double* d_E = nullptr;          // n0 x n0
   double* d_Einv64 = nullptr;
   float* d_Einv32 = nullptr;
@@ -229,6 +237,7 @@ hk_status run_fgmres(hk_handle* h, int s, const double* rhs_dev, double tol, dou
 void launch_scan_exclusive(const int* in, int* out, int n, int* total, cudaStream_t st);
 void launch_to_f32(const double* a, float* b, long long n, cudaStream_t st);
 hk_status upload_sub_info(hk_handle* h);
+hk_status build_apply_z(hk_handle* h);
 
 // Geometry of a P1 simplex: volume and barycentric gradients g[v][d].
 __device__ __forceinline__ double simplex_geometry(int dim, const double* __restrict__ xyz,

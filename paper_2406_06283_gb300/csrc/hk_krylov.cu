@@ -52,18 +52,21 @@ __global__ void k_spmv(int n, int s, const int* __restrict__ rowptr, const int* 
 }
 
 hk_status op_matvec(hk_handle* h, int s, const double* x, double* y, const int* active) {
-  k_spmv<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->n, s, h->d_rowptr, h->d_col, h->d_valB, x, y, active);
+  k_spmv<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->n, s, h->d_rowptr, h->d_col, h->d_valB, x, y, active); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   return HK_OK;
 }
 
-// Gram-Schmidt pass.  MODE 0: h1 = V^T w.  MODE 1: w -= V h1, then h2 = V^T w.
+// Gram-Schmidt pass.  MODE 0: w = B z_j on the CTA's rows (the matvec, fused), then
+// h1 = V^T w.  MODE 1: w -= V h1, then h2 = V^T w.
 // MODE 2: w -= V h2, ||w||^2, then (last CTA) the Hessenberg column, Givens
 // rotation, residual estimate and stopping decision of every active rhs.
 template <int MODE>
 __global__ void k_gs(int n, int s, int m, int j, const double* __restrict__ V, double* w, int* state,
                      double* rstate, double* hcoef, double* part, unsigned* counter, double* H, double* cs,
-                     double* sn, double* g, double* hist, int max_iters, double tol) {
+                     double* sn, double* g, double* hist, int max_iters, double tol,
+                     const int* __restrict__ rowptr, const int* __restrict__ col, const double* __restrict__ val,
+                     const double* __restrict__ zj) {
   int chunk = (n + gridDim.x - 1) / gridDim.x;
   int l0 = blockIdx.x * chunk, l1 = min(n, l0 + chunk);
   int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -72,6 +75,15 @@ __global__ void k_gs(int n, int s, int m, int j, const double* __restrict__ V, d
   for (int r = 0; r < s; ++r) {
     if (!state[8 * r + ST_ACTIVE]) continue;
     double* wr = w + (long long)r * n;
+    if (MODE == 0) {
+      const double* zr = zj + (long long)r * n;
+      for (int l = l0 + tid; l < l1; l += blockDim.x) {
+        double acc = 0;
+        for (int q = rowptr[l]; q < rowptr[l + 1]; ++q) acc += val[q] * zr[col[q]];
+        wr[l] = acc;
+      }
+      __syncthreads();
+    }
     if (MODE >= 1) {
       const double* hc = hcoef + (long long)r * 2 * (m + 1) + (MODE == 1 ? 0 : m + 1);
       for (int l = l0 + tid; l < l1; l += blockDim.x) {
@@ -98,15 +110,18 @@ __global__ void k_gs(int n, int s, int m, int j, const double* __restrict__ V, d
     }
   }
   if (!last_block(counter)) return;
-  // final reduction in CTA order
-  for (int e = tid; e < s * nc; e += blockDim.x) {
+  // final reduction: one warp per value, lanes over CTAs in a fixed order
+  for (int e = warp; e < s * nc; e += nw) {
     int r = e / nc, i = e % nc;
     if (!state[8 * r + ST_ACTIVE]) continue;
     double acc = 0;
-    for (int b = 0; b < gridDim.x; ++b) acc += part[((long long)b * s + r) * (m + 2) + i];
-    if (MODE == 0) hcoef[(long long)r * 2 * (m + 1) + i] = acc;
-    else if (MODE == 1) hcoef[(long long)r * 2 * (m + 1) + (m + 1) + i] = acc;
-    else rstate[8 * r + RS_HNEXT] = sqrt(acc);
+    for (int b = lane; b < gridDim.x; b += 32) acc += part[((long long)b * s + r) * (m + 2) + i];
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      if (MODE == 0) hcoef[(long long)r * 2 * (m + 1) + i] = acc;
+      else if (MODE == 1) hcoef[(long long)r * 2 * (m + 1) + (m + 1) + i] = acc;
+      else rstate[8 * r + RS_HNEXT] = sqrt(acc);
+    }
   }
   if (MODE == 2) {
     __syncthreads();
@@ -174,11 +189,13 @@ __global__ void k_norm2(int n, int s, const double* __restrict__ u, const int* _
     if (threadIdx.x == 0) part[(long long)blockIdx.x * s + r] = acc;
   }
   if (!last_block(counter)) return;
-  for (int r = threadIdx.x; r < s; r += blockDim.x) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = warp; r < s; r += nw) {
     if (state[8 * r + ST_DONE]) continue;
     double acc = 0;
-    for (int b = 0; b < gridDim.x; ++b) acc += part[(long long)b * s + r];
-    rstate[8 * r + slot] = sqrt_it ? sqrt(acc) : acc;
+    for (int b = lane; b < gridDim.x; b += 32) acc += part[(long long)b * s + r];
+    acc = warp_sum(acc);
+    if (lane == 0) rstate[8 * r + slot] = sqrt_it ? sqrt(acc) : acc;
   }
   __syncthreads();
   if (threadIdx.x == 0) *counter = 0u;
@@ -329,21 +346,19 @@ hk_status run_fgmres(hk_handle* h, int s, const double* rhs_dev, double tol, dou
   HK_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned) * 8, st));
   // ||f|| into RS_BETA, then initialise the per-rhs state from it
   k_norm2<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, h->d_f, h->d_state, h->d_rstate, RS_BETA, h->d_part,
-                                              h->d_counter, 1);
-  k_zero_rhs_init<<<nblk(s, 64), 64, 0, st>>>(s, h->d_state, h->d_rstate);
+                                              h->d_counter, 1); HK_COUNT_LAUNCH();
+  k_zero_rhs_init<<<nblk(s, 64), 64, 0, st>>>(s, h->d_state, h->d_rstate); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   const double* rvec = h->d_f;  // residual of x = 0
   int* act = h->d_state;        // ST_ACTIVE is word 0 of each rhs's 8 words
   while (true) {
-    k_start_cycle<<<nblk(n, 256), 256, 0, st>>>(n, s, m, rvec, h->d_V, h->d_state, h->d_rstate, h->d_g);
-    k_activate<<<nblk(s, 64), 64, 0, st>>>(s, h->d_state);
+    k_start_cycle<<<nblk(n, 256), 256, 0, st>>>(n, s, m, rvec, h->d_V, h->d_state, h->d_rstate, h->d_g); HK_COUNT_LAUNCH();
+    k_activate<<<nblk(s, 64), 64, 0, st>>>(s, h->d_state); HK_COUNT_LAUNCH();
     HK_LAUNCH_CHECK();
     for (int j = 0; j < m; ++j) {
       double* vj = h->d_V + (long long)j * sn_;
       double* zj = h->d_Zk + (long long)j * sn_;
       HK_TRY(op_apply(h, s, vj, zj, act));
-      HK_TIMED(h, HK_T_SPMV,
-               (k_spmv<<<nblk(n, 256), 256, 0, st>>>(n, s, h->d_rowptr, h->d_col, h->d_valB, zj, h->d_w, act)));
       cudaEvent_t ga = nullptr;
       if (h->timing) {
         ga = hk_event(h);
@@ -351,14 +366,14 @@ hk_status run_fgmres(hk_handle* h, int s, const double* rhs_dev, double tol, dou
       }
       k_gs<0><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, m, j, h->d_V, h->d_w, h->d_state, h->d_rstate, h->d_hcol,
                                                   h->d_part, h->d_counter, h->d_H, h->d_cs, h->d_sn, h->d_g,
-                                                  h->d_hist, mi, tol);
+                                                  h->d_hist, mi, tol, h->d_rowptr, h->d_col, h->d_valB, zj); HK_COUNT_LAUNCH();
       k_gs<1><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, m, j, h->d_V, h->d_w, h->d_state, h->d_rstate, h->d_hcol,
                                                   h->d_part, h->d_counter, h->d_H, h->d_cs, h->d_sn, h->d_g,
-                                                  h->d_hist, mi, tol);
+                                                  h->d_hist, mi, tol, h->d_rowptr, h->d_col, h->d_valB, zj); HK_COUNT_LAUNCH();
       k_gs<2><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, m, j, h->d_V, h->d_w, h->d_state, h->d_rstate, h->d_hcol,
                                                   h->d_part, h->d_counter, h->d_H, h->d_cs, h->d_sn, h->d_g,
-                                                  h->d_hist, mi, tol);
-      k_normalize<<<nblk(n, 256), 256, 0, st>>>(n, s, j, h->d_V, h->d_w, h->d_state, h->d_rstate);
+                                                  h->d_hist, mi, tol, h->d_rowptr, h->d_col, h->d_valB, zj); HK_COUNT_LAUNCH();
+      k_normalize<<<nblk(n, 256), 256, 0, st>>>(n, s, j, h->d_V, h->d_w, h->d_state, h->d_rstate); HK_COUNT_LAUNCH();
       if (h->timing) {
         cudaEvent_t gb = hk_event(h);
         cudaEventRecord(gb, st);
@@ -377,13 +392,13 @@ hk_status run_fgmres(hk_handle* h, int s, const double* rhs_dev, double tol, dou
       ca = hk_event(h);
       cudaEventRecord(ca, st);
     }
-    k_cycle_solve<<<nblk(s, 64), 64, 0, st>>>(s, m, h->d_state, h->d_H, h->d_g);
-    k_xupdate<<<nblk(n, 256), 256, 0, st>>>(n, s, m, h->d_state, h->d_Zk, h->d_g, h->d_x);
-    k_spmv<<<nblk(n, 256), 256, 0, st>>>(n, s, h->d_rowptr, h->d_col, h->d_valB, h->d_x, h->d_w, nullptr);
-    k_residual<<<nblk(n, 256), 256, 0, st>>>(n, s, h->d_state, h->d_f, h->d_w);
+    k_cycle_solve<<<nblk(s, 64), 64, 0, st>>>(s, m, h->d_state, h->d_H, h->d_g); HK_COUNT_LAUNCH();
+    k_xupdate<<<nblk(n, 256), 256, 0, st>>>(n, s, m, h->d_state, h->d_Zk, h->d_g, h->d_x); HK_COUNT_LAUNCH();
+    k_spmv<<<nblk(n, 256), 256, 0, st>>>(n, s, h->d_rowptr, h->d_col, h->d_valB, h->d_x, h->d_w, nullptr); HK_COUNT_LAUNCH();
+    k_residual<<<nblk(n, 256), 256, 0, st>>>(n, s, h->d_state, h->d_f, h->d_w); HK_COUNT_LAUNCH();
     k_norm2<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, h->d_w, h->d_state, h->d_rstate, RS_BETA, h->d_part,
-                                                h->d_counter, 1);
-    k_cycle_decide<<<nblk(s, 64), 64, 0, st>>>(s, h->d_state, h->d_rstate, tol, mi);
+                                                h->d_counter, 1); HK_COUNT_LAUNCH();
+    k_cycle_decide<<<nblk(s, 64), 64, 0, st>>>(s, h->d_state, h->d_rstate, tol, mi); HK_COUNT_LAUNCH();
     if (h->timing) {
       cudaEvent_t cb = hk_event(h);
       cudaEventRecord(cb, st);

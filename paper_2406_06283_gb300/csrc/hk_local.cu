@@ -12,6 +12,8 @@
 // each block starting on a 4-element boundary; the sparse L_j is read from
 // the local CSR.  S_j^{-1} is formed in FP64 by Gauss-Jordan elimination with
 // partial pivoting; a pivot below 1e-10 max|B_i| reports HK_SINGULAR_LOCAL.
+#include <algorithm>
+
 #include "hk_internal.cuh"
 
 static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
@@ -198,163 +200,288 @@ __global__ void k_to_f32(const double* __restrict__ a, float* b, long long n) {
 }
 
 void launch_to_f32(const double* a, float* b, long long n, cudaStream_t st) {
-  if (n > 0) k_to_f32<<<nblk(n, 256), 256, 0, st>>>(a, b, n);
+  if (n > 0) {
+    k_to_f32<<<nblk(n, 256), 256, 0, st>>>(a, b, n);
+    HK_COUNT_LAUNCH();
+  }
 }
 
-hk_status phase_local_factors(hk_handle* h) {
-  cudaStream_t st = h->stream;
-  int ns = h->n_sub;
-  std::vector<int> lev(h->I_total + ns);
-  HK_CUDA(cudaMemcpyAsync(lev.data(), h->d_lev, sizeof(int) * lev.size(), cudaMemcpyDeviceToHost, st));
-  HK_CUDA(cudaStreamSynchronize(st));
-  long long fo = 0;
-  for (int s = 0; s < ns; ++s) {
-    Sub& u = h->subs[s];
-    u.f_off = fo;
-    fo += factor_elems(&lev[u.lev_off], u.L);
-  }
-  h->f_total = fo;
-  HK_TRY(upload_sub_info(h));
-  if (h->p.levels == HK_COARSE_ONLY) return HK_OK;
-  {
-    unsigned long long* d_cnt = nullptr;
-    HK_TRY(dalloc(h, &d_cnt, 1));
-    k_count_lower<<<ns, 128, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
-                                      d_cnt);
-    unsigned long long c = 0;
-    HK_CUDA(cudaMemcpyAsync(&c, d_cnt, sizeof(c), cudaMemcpyDeviceToHost, st));
-    HK_CUDA(cudaStreamSynchronize(st));
-    h->lower_nnz = (long long)c;
-    dfree(h, d_cnt);
-  }
-  HK_TRY(dalloc(h, &h->d_F64, fo));
-  size_t shm = sizeof(double) * (size_t)h->max_level * h->max_level;
-  HK_CUDA(cudaFuncSetAttribute(k_block_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  k_block_lu<<<ns, 256, shm, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
-                                   h->d_lvalB, h->d_F64, h->d_status);
-  HK_LAUNCH_CHECK();
-  HK_TRY(check_device_status(h, "local factors"));
-  if (h->p.precision == HK_FP32_PRECOND) {
-    HK_TRY(dalloc(h, &h->d_F32, fo));
-    launch_to_f32(h->d_F64, h->d_F32, fo, st);
-    HK_TRY(dalloc(h, &h->d_lvalB32, h->csr_total));
-    launch_to_f32(h->d_lvalB, h->d_lvalB32, h->csr_total, st);
-    HK_LAUNCH_CHECK();
-    HK_CUDA(cudaStreamSynchronize(st));
-    dfree(h, h->d_F64);
-    h->d_F64 = nullptr;
-  }
-  return HK_OK;
-}
 
 // ====================================================================== apply
-// One CTA per (subdomain, group of NR right-hand sides):
-//   gather r_i = v[dof(Omega_i)] (R_i of Eq. 2.22), coarse restriction
-//   c_i = Z_i^T r_i (R_0 = Z^T, Eq. 2.23), then the two block sweeps, and
-//   the local solution y_i written to ybuf.  T is the arithmetic type
-//   (float in the FP32 form, double in the FP64 form).
+// Level records, streamed by the apply kernel one after another:
+//   forward record j:  S_j^{-1} (b_j x b_j, T) | L_j values (nc_j, T) |
+//                      L_j columns in level j-1 (nc_j, uint16) | L_j row pointers (b_j + 1, uint16)
+//   backward record j: G_j (b_j x b_{j+1}, T)
+// each padded to 16 bytes so that one 1-D TMA bulk copy moves it to shared memory.
+// Level table entry (4 x int64 per level): fwd offset, bwd offset, fwd | bwd bytes << 32,
+// nc | b << 20 | level start << 40.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false after ~2^22 polls (each poll may suspend the thread for a while).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  for (unsigned it = 0; it < (1u << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__host__ __device__ __forceinline__ long long pad16(long long x) { return (x + 15) & ~15LL; }
+__host__ __device__ __forceinline__ int lv_nc(long long e3) { return (int)(e3 & 0xFFFFF); }
+__host__ __device__ __forceinline__ int lv_b(long long e3) { return (int)((e3 >> 20) & 0xFFFFF); }
+__host__ __device__ __forceinline__ int lv_start(long long e3) { return (int)(e3 >> 40); }
+
+// Lower couplings per level (row in level j, column in level j-1).
+__global__ void k_level_counts(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
+                               const int* __restrict__ levptr, const int* __restrict__ lrow,
+                               const int* __restrict__ lcntI, const int* __restrict__ lcol, int* nc_out) {
+  int s = blockIdx.x;
+  const int* si = sub_info + 8 * s;
+  int L = si[2], off = si[3], loff = si[5];
+  long long coff = sub_off[3 * s + 1];
+  const int* lp = levptr + loff;
+  const int* lr = lrow + off + s;
+  for (int j = threadIdx.x; j < L; j += blockDim.x) {
+    int c = 0;
+    if (j > 0)
+      for (int a = lp[j]; a < lp[j + 1]; ++a)
+        for (int q = 0; q < lcntI[off + a]; ++q) c += lcol[coff + lr[a] + q] < lp[j];
+    nc_out[loff + j] = c;
+  }
+}
+
+template <typename T>
+__global__ void k_pack_levels(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
+                              const int* __restrict__ levptr, const int* __restrict__ lrow,
+                              const int* __restrict__ lcntI, const int* __restrict__ lcol,
+                              const double* __restrict__ lvalB, const double* __restrict__ F,
+                              const long long* __restrict__ lvtab, unsigned char* pack) {
+  int s = blockIdx.x, tid = threadIdx.x, T_ = blockDim.x;
+  const int* si = sub_info + 8 * s;
+  int L = si[2], off = si[3], loff = si[5];
+  long long foff = sub_off[3 * s], coff = sub_off[3 * s + 1];
+  const int* lp = levptr + loff;
+  const int* lr = lrow + off + s;
+  long long bo = foff;
+  for (int j = 0; j < L; ++j) {
+    int r0 = lp[j], b = lp[j + 1] - r0, bn = j + 1 < L ? lp[j + 2] - lp[j + 1] : 0;
+    const long long* e = lvtab + 4 * (long long)(loff + j);
+    int nc = lv_nc(e[3]);
+    T* S = reinterpret_cast<T*>(pack + e[0]);
+    T* Lv = S + (long long)b * b;
+    uint16_t* Lc = reinterpret_cast<uint16_t*>(Lv + nc);
+    uint16_t* Lp = Lc + nc;
+    for (int q = tid; q < b * b; q += T_) S[q] = (T)F[bo + q];
+    if (tid == 0 && j > 0) {
+      int pr0 = lp[j - 1], c = 0;
+      for (int a = r0; a < r0 + b; ++a) {
+        Lp[a - r0] = (uint16_t)c;
+        for (int q = 0; q < lcntI[off + a]; ++q) {
+          int col = lcol[coff + lr[a] + q];
+          if (col < r0) {
+            Lv[c] = (T)lvalB[coff + lr[a] + q];
+            Lc[c] = (uint16_t)(col - pr0);
+            ++c;
+          }
+        }
+      }
+      Lp[b] = (uint16_t)c;
+    }
+    if (tid == 0 && j == 0) Lp[0] = 0, Lp[b] = 0;
+    long long go = bo + pad4((long long)b * b);
+    if (bn > 0) {
+      T* G = reinterpret_cast<T*>(pack + e[1]);
+      for (int q = tid; q < b * bn; q += T_) G[q] = (T)F[go + q];
+    }
+    bo = go + pad4((long long)b * bn);
+  }
+}
+
+// One CTA per (subdomain, group of NR right-hand sides): gather r_i = v[dof(Omega_i)]
+// (R_i of Eq. 2.22), coarse restriction c_i = Z_i^T r_i (R_0 = Z^T, Eq. 2.23), the
+// forward and backward block sweeps of B_i^{-1}, and the local solution written to
+// ybuf.  The level records stream through two shared-memory buffers by TMA bulk
+// copies, the copy of record r+2 overlapping the work on record r.  Shared vectors
+// are right-hand-side major (x[rr * nI + a]).  T: float (FP32 form) or double.
 template <typename T, int NR>
-__global__ void k_local_apply(int n, int s_tot, const double* __restrict__ v, const int* __restrict__ active,
-                              const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
-                              const int* __restrict__ levptr, const int* __restrict__ Ilev,
-                              const int* __restrict__ lrow, const int* __restrict__ lcntI,
-                              const int* __restrict__ lcol, const T* __restrict__ lval, const T* __restrict__ F,
-                              const T* __restrict__ Z, int do_local, int do_coarse, long long I_total, int n0,
-                              T* ybuf, T* cvec) {
-  extern __shared__ unsigned char smem_raw[];
-  T* x = reinterpret_cast<T*>(smem_raw);  // nI x NR
+__global__ void __launch_bounds__(256) k_local_apply(
+    int n, int s_tot, const double* __restrict__ v, const int* __restrict__ active,
+    const int* __restrict__ sub_info, const long long* __restrict__ sub_off, const int* __restrict__ Ilev,
+    const long long* __restrict__ lvtab, const unsigned char* __restrict__ pack, const T* __restrict__ Zt,
+    int do_local, int do_coarse, long long I_total, int n0, int stage_bytes, T* ybuf, T* cvec, DevStatus* st) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int sh_fail;
+  unsigned char* stage[2] = {smem_raw, smem_raw + stage_bytes};
   int s = blockIdx.x, r_base = blockIdx.y * NR;
   int tid = threadIdx.x, T_ = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = T_ >> 5;
   const int* si = sub_info + 8 * s;
   int nI = si[0], L = si[2], off = si[3], loff = si[5], m = si[6], c_off = si[7];
-  long long foff = sub_off[3 * s], coff = sub_off[3 * s + 1], zoff = sub_off[3 * s + 2];
-  T* tmp = x + (size_t)nI * NR;           // HK_MAXB x NR
+  long long zoff = sub_off[3 * s + 2];
+  T* x = reinterpret_cast<T*>(smem_raw + 2 * (long long)stage_bytes);  // NR x nI
+  T* tmp = x + (long long)nI * NR;                                       // NR x HK_MAXB
   int nr = s_tot - r_base < NR ? s_tot - r_base : NR;
   bool act[NR];
   for (int r = 0; r < NR; ++r) act[r] = r < nr && (active == nullptr || active[8 * (r_base + r)]);
-  // gather
+  const long long* lv = lvtab + 4 * (long long)loff;
+  int nrec = do_local ? 2 * L - 1 : 0;
+  auto rec_src = [&](int r, unsigned& bytes) -> const unsigned char* {
+    const long long* e = lv + 4 * (r < L ? r : 2 * L - 2 - r);
+    if (r < L) {
+      bytes = (unsigned)(e[2] & 0xffffffffLL);
+      return pack + e[0];
+    }
+    bytes = (unsigned)((unsigned long long)e[2] >> 32);
+    return pack + e[1];
+  };
+  if (tid == 0) {
+    sh_fail = 0;
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int r = 0; r < 2 && r < nrec; ++r) {
+      unsigned bytes;
+      const unsigned char* src = rec_src(r, bytes);
+      mbar_expect_tx(&bar[r], bytes);
+      tma_load_1d(stage[r], src, bytes, &bar[r]);
+    }
+  }
+  // gather (overlaps the first two record copies)
   for (int e = tid; e < nI * NR; e += T_) {
-    int a = e / NR, r = e % NR;
-    x[e] = act[r] ? (T)v[(long long)(r_base + r) * n + Ilev[off + a]] : (T)0;
+    int rr = e / nI, a = e % nI;
+    x[e] = act[rr] ? (T)v[(long long)(r_base + rr) * n + Ilev[off + a]] : (T)0;
   }
   __syncthreads();
-  // coarse restriction c_i = Z_i^T r_i
   if (do_coarse) {
-    for (int e = tid; e < m * NR; e += T_) {
-      int l = e / NR, r = e % NR;
-      if (!act[r]) continue;
-      T acc = 0;
-      const T* zc = Z + zoff + l;
-      for (int a = 0; a < nI; ++a) acc += zc[(long long)a * m] * x[a * NR + r];
-      cvec[(long long)(r_base + r) * n0 + c_off + l] = acc;
+    for (int l = warp; l < m; l += nw) {
+      const T* zc = Zt + zoff + (long long)l * nI;
+      T acc[NR];
+      for (int rr = 0; rr < NR; ++rr) acc[rr] = 0;
+      for (int a = lane; a < nI; a += 32) {
+        T zv = zc[a];
+        for (int rr = 0; rr < NR; ++rr) acc[rr] += zv * x[rr * nI + a];
+      }
+      for (int rr = 0; rr < NR; ++rr) {
+        T t = acc[rr];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0 && act[rr]) cvec[(long long)(r_base + rr) * n0 + c_off + l] = t;
+      }
     }
   }
   if (!do_local) return;
-  const int* lp = levptr + loff;
-  const int* lr = lrow + off + s;
-  long long bo = foff;
-  // forward sweep
-  for (int j = 0; j < L; ++j) {
-    int r0 = lp[j], b = lp[j + 1] - r0, bn = j + 1 < L ? lp[j + 2] - lp[j + 1] : 0;
-    if (j > 0) {
-      for (int e = tid; e < b * NR; e += T_) {
-        int a = r0 + e / NR, r = e % NR;
-        const int* cl = lcol + coff + lr[a];
-        const T* cv = lval + coff + lr[a];
-        int cnt = lcntI[off + a];
-        T acc = x[a * NR + r];
-        for (int q = 0; q < cnt; ++q)
-          if (cl[q] < r0) acc -= cv[q] * x[cl[q] * NR + r];
-        x[a * NR + r] = acc;
+  unsigned phase[2] = {0u, 0u};
+  for (int r = 0; r < nrec; ++r) {
+    int bi = r & 1;
+    if (!mbar_wait_bounded(&bar[bi], phase[bi])) atomicExch(&sh_fail, 1);
+    phase[bi] ^= 1u;
+    __syncthreads();
+    if (sh_fail) {
+      if (tid == 0) dev_fail(st, HK_TIMEOUT, s, r);
+      // let the other buffer's copy (if any) land before the CTA exits
+      if (r + 1 < nrec) mbar_wait_bounded(&bar[bi ^ 1], phase[bi ^ 1]);
+      return;
+    }
+    const unsigned char* buf = stage[bi];
+    int j = r < L ? r : 2 * L - 2 - r;
+    long long e3 = lv[4 * j + 3];
+    int nc = lv_nc(e3), b = lv_b(e3), ls = lv_start(e3);
+    // G threads per output row (a power of two with b * G <= blockDim)
+    int G = 1;
+    while (G < 32 && b * G * 2 <= T_) G <<= 1;
+    int grp = tid / G, gl = tid % G, ngrp = T_ / G;
+    if (r < L) {
+      const T* S = reinterpret_cast<const T*>(buf);
+      const T* Lv = S + (long long)b * b;
+      const uint16_t* Lc = reinterpret_cast<const uint16_t*>(Lv + nc);
+      const uint16_t* Lp = Lc + nc;
+      // t_j = r_j - L_j y_{j-1}  into tmp
+      int ps = j > 0 ? lv_start(lv[4 * (j - 1) + 3]) : 0;
+      for (int q = tid; q < b * NR; q += T_) {
+        int rr = q / b, a = q % b;
+        T acc = x[rr * nI + ls + a];
+        if (j > 0)
+          for (int t = Lp[a]; t < Lp[a + 1]; ++t) acc -= Lv[t] * x[rr * nI + ps + Lc[t]];
+        tmp[rr * HK_MAXB + a] = acc;
       }
       __syncthreads();
-    }
-    const T* Sinv = F + bo;
-    for (int q = warp; q < b; q += nw) {
-      T acc[NR];
-      for (int r = 0; r < NR; ++r) acc[r] = 0;
-      for (int t = lane; t < b; t += 32) {
-        T sv = Sinv[q * b + t];
-        for (int r = 0; r < NR; ++r) acc[r] += sv * x[(r0 + t) * NR + r];
+      // y_j = S_j^{-1} t_j, written in place
+      // every thread runs the same trip count so that the group shuffles see full warps
+      for (int q0 = 0; q0 < b; q0 += ngrp) {
+        int q = q0 + grp;
+        bool valid = q < b;
+        T acc[NR];
+        for (int rr = 0; rr < NR; ++rr) acc[rr] = 0;
+        if (valid)
+          for (int t = gl; t < b; t += G) {
+            T sv = S[q * b + t];
+            for (int rr = 0; rr < NR; ++rr) acc[rr] += sv * tmp[rr * HK_MAXB + t];
+          }
+        for (int rr = 0; rr < NR; ++rr) {
+          T a2 = acc[rr];
+          for (int o = G >> 1; o > 0; o >>= 1) a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+          if (valid && gl == 0) x[rr * nI + ls + q] = a2;
+        }
       }
-      for (int r = 0; r < NR; ++r) {
-        T a = acc[r];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0) tmp[q * NR + r] = a;
-      }
-    }
-    __syncthreads();
-    for (int e = tid; e < b * NR; e += T_) x[r0 * NR + e] = tmp[e];
-    __syncthreads();
-    bo += pad4((long long)b * b) + pad4((long long)b * bn);
-  }
-  // backward sweep: x_j -= G_j x_{j+1}; bo walks back over the blocks
-  {
-    int bl = lp[L] - lp[L - 1];
-    bo -= pad4((long long)bl * bl);  // level L-1 has no G block
-  }
-  for (int j = L - 2; j >= 0; --j) {
-    int r0 = lp[j], b = lp[j + 1] - r0, r1 = lp[j + 1], bn = lp[j + 2] - r1;
-    bo -= pad4((long long)b * b) + pad4((long long)b * bn);
-    const T* Gj = F + bo + pad4((long long)b * b);
-    for (int q = warp; q < b; q += nw) {
-      T acc[NR];
-      for (int r = 0; r < NR; ++r) acc[r] = 0;
-      for (int t = lane; t < bn; t += 32) {
-        T gv = Gj[q * bn + t];
-        for (int r = 0; r < NR; ++r) acc[r] += gv * x[(r1 + t) * NR + r];
-      }
-      for (int r = 0; r < NR; ++r) {
-        T a = acc[r];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0) x[(r0 + q) * NR + r] -= a;
+    } else {
+      const T* Gm = reinterpret_cast<const T*>(buf);
+      int bn = lv_b(lv[4 * (j + 1) + 3]);
+      int ns = ls + b;
+      for (int q0 = 0; q0 < b; q0 += ngrp) {
+        int q = q0 + grp;
+        bool valid = q < b;
+        T acc[NR];
+        for (int rr = 0; rr < NR; ++rr) acc[rr] = 0;
+        if (valid)
+          for (int t = gl; t < bn; t += G) {
+            T gv = Gm[q * bn + t];
+            for (int rr = 0; rr < NR; ++rr) acc[rr] += gv * x[rr * nI + ns + t];
+          }
+        for (int rr = 0; rr < NR; ++rr) {
+          T a2 = acc[rr];
+          for (int o = G >> 1; o > 0; o >>= 1) a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+          if (valid && gl == 0) x[rr * nI + ls + q] -= a2;
+        }
       }
     }
-    __syncthreads();
+    __syncthreads();  // every thread is done with this buffer
+    if (tid == 0 && r + 2 < nrec) {
+      unsigned bytes;
+      const unsigned char* src = rec_src(r + 2, bytes);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&bar[bi], bytes);
+      tma_load_1d(stage[bi], src, bytes, &bar[bi]);
+    }
   }
-  for (int e = tid; e < nI * NR; e += T_) {
-    int a = e / NR, r = e % NR;
-    if (act[r]) ybuf[(long long)(r_base + r) * I_total + off + a] = x[e];
+  for (int e2 = tid; e2 < nI * NR; e2 += T_) {
+    int rr = e2 / nI, a = e2 % nI;
+    if (act[rr]) ybuf[(long long)(r_base + rr) * I_total + off + a] = x[e2];
   }
 }
 
@@ -409,66 +536,181 @@ __global__ void k_scatter(int n, int s, const int* __restrict__ pull_ptr, const 
 }
 
 template <typename T, int NR>
-static hk_status launch_local(hk_handle* h, int s, const double* v, const int* active, const T* lval, const T* F,
-                              const T* Z, T* ybuf, T* cvec, int do_local, int do_coarse) {
-  size_t shm = sizeof(T) * ((size_t)h->max_dof * NR + (size_t)HK_MAXB * NR);
+static hk_status launch_local(hk_handle* h, int s, const double* v, const int* active, const T* Zt, T* ybuf,
+                              T* cvec, int do_local, int do_coarse) {
+  size_t xbytes = sizeof(T) * ((size_t)h->max_dof * NR + (size_t)HK_MAXB * NR);
+  size_t shm = 2 * (size_t)h->pack_stage + xbytes;
   static bool attr_set = false;
   if (!attr_set) {
-    HK_CUDA(cudaFuncSetAttribute(k_local_apply<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    HK_CUDA(cudaFuncSetAttribute(k_local_apply<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     attr_set = true;
   }
-  if (shm > 200 * 1024) {
-    hk_set_error("subdomain too large for the shared-memory apply (%d dofs)", h->max_dof);
+  if (shm > 220 * 1024) {
+    hk_set_error("subdomain too large for the shared-memory apply (%d dofs, record %lld bytes)", h->max_dof,
+                 (long long)h->pack_stage);
     return HK_UNSUPPORTED;
   }
   dim3 grid(h->n_sub, (s + NR - 1) / NR);
   HK_TIMED(h, HK_T_LOCAL_APPLY,
-           (k_local_apply<T, NR><<<grid, 256, shm, h->stream>>>(h->n, s, v, active, h->d_sub_info, h->d_sub_off,
-                                                               h->d_lev, h->d_I, h->d_lrow, h->d_lcntI, h->d_lcol,
-                                                               lval, F, Z, do_local, do_coarse, h->I_total, h->n0,
-                                                               ybuf, cvec)));
+           (k_local_apply<T, NR><<<grid, 256, shm, h->stream>>>(
+               h->n, s, v, active, h->d_sub_info, h->d_sub_off, h->d_I, h->d_lvtab, h->d_pack, Zt, do_local,
+               do_coarse, h->I_total, h->n0, (int)h->pack_stage, ybuf, cvec, h->d_status))); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   return HK_OK;
 }
 
 template <typename T>
-static hk_status apply_t(hk_handle* h, int s, const double* v, double* z, const int* active, const T* lval,
-                         const T* F, const T* Z, const T* Einv, T* ybuf, T* c, T* cc) {
+static hk_status apply_t(hk_handle* h, int s, const double* v, double* z, const int* active, T* ybuf, T* c,
+                         T* cc) {
+  const T* Zr = reinterpret_cast<const T*>(h->d_Zr);
+  const T* Zt = reinterpret_cast<const T*>(h->d_Zt);
+  const T* Einv = sizeof(T) == 4 ? reinterpret_cast<const T*>(h->d_Einv32) : reinterpret_cast<const T*>(h->d_Einv64);
   int do_local = h->p.levels != HK_COARSE_ONLY;
   int do_coarse = h->p.levels != HK_ONE_LEVEL && h->n0 > 0;
-  int NRmax = sizeof(T) == 4 ? 8 : 4;
-  if (h->max_dof > 6000) NRmax = 1;
-  else if (h->max_dof > 3000) NRmax = NRmax > 2 ? 2 : NRmax;
-  int nr = s >= 8 && NRmax >= 8 ? 8 : s >= 4 && NRmax >= 4 ? 4 : s >= 2 && NRmax >= 2 ? 2 : 1;
+  size_t budget = 220 * 1024 - 2 * (size_t)h->pack_stage;
+  int nr = 8;
+  while (nr > 1 && (nr > s || sizeof(T) * ((size_t)h->max_dof + HK_MAXB) * nr > budget)) nr >>= 1;
   hk_status rc;
   switch (nr) {
-    case 8: rc = launch_local<T, 8>(h, s, v, active, lval, F, Z, ybuf, c, do_local, do_coarse); break;
-    case 4: rc = launch_local<T, 4>(h, s, v, active, lval, F, Z, ybuf, c, do_local, do_coarse); break;
-    case 2: rc = launch_local<T, 2>(h, s, v, active, lval, F, Z, ybuf, c, do_local, do_coarse); break;
-    default: rc = launch_local<T, 1>(h, s, v, active, lval, F, Z, ybuf, c, do_local, do_coarse); break;
+    case 8: rc = launch_local<T, 8>(h, s, v, active, Zt, ybuf, c, do_local, do_coarse); break;
+    case 4: rc = launch_local<T, 4>(h, s, v, active, Zt, ybuf, c, do_local, do_coarse); break;
+    case 2: rc = launch_local<T, 2>(h, s, v, active, Zt, ybuf, c, do_local, do_coarse); break;
+    default: rc = launch_local<T, 1>(h, s, v, active, Zt, ybuf, c, do_local, do_coarse); break;
   }
   HK_TRY(rc);
   if (do_coarse) {
     int rows_per_block = 8;
     HK_TIMED(h, HK_T_COARSE_SOLVE,
              (k_coarse_solve<T><<<nblk(h->n0, rows_per_block), 32 * rows_per_block, 0, h->stream>>>(
-                 h->n0, s, Einv, c, cc, active)));
+                 h->n0, s, Einv, c, cc, active))); HK_COUNT_LAUNCH();
   }
   HK_TIMED(h, HK_T_SCATTER,
            (k_scatter<T><<<nblk(h->n, 128), 128, 0, h->stream>>>(
-               h->n, s, h->d_pull_ptr, h->d_pull_row, h->d_pull_sub, h->d_sub_info, h->d_sub_off, ybuf, Z, cc,
-               h->I_total, h->n0, do_local, do_coarse, h->p.weighting == HK_RAS_POU, h->d_mu, z, active)));
+               h->n, s, h->d_pull_ptr, h->d_pull_row, h->d_pull_sub, h->d_sub_info, h->d_sub_off, ybuf, Zr, cc,
+               h->I_total, h->n0, do_local, do_coarse, h->p.weighting == HK_RAS_POU, h->d_mu, z, active))); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   return HK_OK;
 }
 
 hk_status op_apply(hk_handle* h, int s, const double* v, double* z, const int* active) {
   HK_TRY(ensure_workspace(h, s));
-  if (h->p.precision == HK_FP32_PRECOND)
-    return apply_t<float>(h, s, v, z, active, h->d_lvalB32, h->d_F32, h->d_Z32, h->d_Einv32, h->d_ybuf32, h->d_c32,
-                          h->d_cc32);
-  return apply_t<double>(h, s, v, z, active, h->d_lvalB, h->d_F64, h->d_Z64, h->d_Einv64, h->d_ybuf64, h->d_c64,
-                         h->d_cc64);
+  if (h->p.precision == HK_FP32_PRECOND) return apply_t<float>(h, s, v, z, active, h->d_ybuf32, h->d_c32, h->d_cc32);
+  return apply_t<double>(h, s, v, z, active, h->d_ybuf64, h->d_c64, h->d_cc64);
+}
+
+// Transposed (m x |dof|) copy of each Z_i in the apply's arithmetic type.
+template <typename T>
+__global__ void k_transpose_z(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
+                              const double* __restrict__ Z, T* Zt, T* Zr) {
+  int s = blockIdx.x;
+  const int* si = sub_info + 8 * s;
+  int nI = si[0], m = si[6];
+  long long zo = sub_off[3 * s + 2];
+  for (long long e = threadIdx.x; e < (long long)nI * m; e += blockDim.x) {
+    int a = (int)(e / m), l = (int)(e % m);
+    Zt[zo + (long long)l * nI + a] = (T)Z[zo + e];
+    if (Zr) Zr[zo + e] = (T)Z[zo + e];
+  }
+}
+
+hk_status build_apply_z(hk_handle* h) {
+  if (h->n0 == 0) return HK_OK;
+  if (h->p.precision == HK_FP32_PRECOND) {
+    float *zt = nullptr, *zr = nullptr;
+    HK_TRY(dalloc(h, &zt, h->z_total));
+    HK_TRY(dalloc(h, &zr, h->z_total));
+    k_transpose_z<float><<<h->n_sub, 256, 0, h->stream>>>(h->d_sub_info, h->d_sub_off, h->d_Z64, zt, zr); HK_COUNT_LAUNCH();
+    h->d_Zt = zt;
+    h->d_Zr = zr;
+  } else {
+    double* zt = nullptr;
+    HK_TRY(dalloc(h, &zt, h->z_total));
+    k_transpose_z<double><<<h->n_sub, 256, 0, h->stream>>>(h->d_sub_info, h->d_sub_off, h->d_Z64, zt, nullptr); HK_COUNT_LAUNCH();
+    h->d_Zt = zt;
+    h->d_Zr = h->d_Z64;
+  }
+  HK_LAUNCH_CHECK();
+  return HK_OK;
+}
+
+hk_status phase_local_factors(hk_handle* h) {
+  cudaStream_t st = h->stream;
+  int ns = h->n_sub;
+  std::vector<int> lev(h->I_total + ns);
+  HK_CUDA(cudaMemcpyAsync(lev.data(), h->d_lev, sizeof(int) * lev.size(), cudaMemcpyDeviceToHost, st));
+  HK_CUDA(cudaStreamSynchronize(st));
+  long long fo = 0;
+  for (int s = 0; s < ns; ++s) {
+    Sub& u = h->subs[s];
+    u.f_off = fo;
+    fo += factor_elems(&lev[u.lev_off], u.L);
+  }
+  h->f_total = fo;
+  HK_TRY(upload_sub_info(h));
+  if (h->p.levels == HK_COARSE_ONLY) return HK_OK;
+  {
+    unsigned long long* d_cnt = nullptr;
+    HK_TRY(dalloc(h, &d_cnt, 1));
+    k_count_lower<<<ns, 128, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
+                                      d_cnt); HK_COUNT_LAUNCH();
+    unsigned long long c = 0;
+    HK_CUDA(cudaMemcpyAsync(&c, d_cnt, sizeof(c), cudaMemcpyDeviceToHost, st));
+    HK_CUDA(cudaStreamSynchronize(st));
+    h->lower_nnz = (long long)c;
+    dfree(h, d_cnt);
+  }
+  HK_TRY(dalloc(h, &h->d_F64, fo));
+  size_t shm = sizeof(double) * (size_t)h->max_level * h->max_level;
+  HK_CUDA(cudaFuncSetAttribute(k_block_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  k_block_lu<<<ns, 256, shm, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
+                                   h->d_lvalB, h->d_F64, h->d_status); HK_COUNT_LAUNCH();
+  HK_LAUNCH_CHECK();
+  HK_TRY(check_device_status(h, "local factors"));
+  // level records for the apply, in the arithmetic type of the precision form
+  int* d_nc = nullptr;
+  HK_TRY(dalloc(h, &d_nc, h->I_total + ns));
+  k_level_counts<<<ns, 128, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
+                                     d_nc); HK_COUNT_LAUNCH();
+  std::vector<int> nc(h->I_total + ns);
+  HK_CUDA(cudaMemcpyAsync(nc.data(), d_nc, sizeof(int) * nc.size(), cudaMemcpyDeviceToHost, st));
+  HK_CUDA(cudaStreamSynchronize(st));
+  size_t esz = h->p.precision == HK_FP32_PRECOND ? 4 : 8;
+  std::vector<long long> tab(4 * (h->I_total + ns), 0);
+  long long cur = 0, stage = 16;
+  for (int s = 0; s < ns; ++s) {
+    const Sub& u = h->subs[s];
+    const int* lp = &lev[u.lev_off];
+    for (int j = 0; j < u.L; ++j) {
+      long long b = lp[j + 1] - lp[j], bn = j + 1 < u.L ? lp[j + 2] - lp[j + 1] : 0, c = nc[u.lev_off + j];
+      long long fb = pad16(b * b * esz + c * esz + c * 2 + (b + 1) * 2), bb = pad16(b * bn * esz);
+      long long* e = &tab[4 * (size_t)(u.lev_off + j)];
+      e[0] = cur;
+      cur += fb;
+      e[1] = cur;
+      cur += bb;
+      e[2] = fb | (bb << 32);
+      e[3] = c | (b << 20) | ((long long)lp[j] << 40);
+      stage = std::max(stage, std::max(fb, bb));
+    }
+  }
+  h->pack_bytes = cur;
+  h->pack_stage = stage;
+  HK_TRY(dalloc(h, &h->d_lvtab, tab.size()));
+  HK_TRY(dalloc(h, &h->d_pack, cur));
+  HK_CUDA(cudaMemcpyAsync(h->d_lvtab, tab.data(), sizeof(long long) * tab.size(), cudaMemcpyHostToDevice, st));
+  if (esz == 4)
+    k_pack_levels<float><<<ns, 256, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI,
+                                             h->d_lcol, h->d_lvalB, h->d_F64, h->d_lvtab, h->d_pack);
+  else
+    k_pack_levels<double><<<ns, 256, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI,
+                                              h->d_lcol, h->d_lvalB, h->d_F64, h->d_lvtab, h->d_pack);
+  HK_COUNT_LAUNCH();
+  HK_LAUNCH_CHECK();
+  HK_CUDA(cudaStreamSynchronize(st));
+  dfree(h, h->d_F64);
+  h->d_F64 = nullptr;
+  dfree(h, d_nc);
+  return HK_OK;
 }
 
 // ======================================================= allocation-free apply
@@ -543,13 +785,11 @@ extern "C" hk_status hk_apply_precond_noalloc(hk_handle* h, int n_rhs, const dou
   if (s == HK_OK) {
     unsigned char* b = static_cast<unsigned char*>(base);
     if (h->p.precision == HK_FP32_PRECOND)
-      s = apply_t<float>(h, n_rhs, v_dev, z_dev, nullptr, h->d_lvalB32, h->d_F32, h->d_Z32, h->d_Einv32,
-                         reinterpret_cast<float*>(b), reinterpret_cast<float*>(b + ylen),
-                         reinterpret_cast<float*>(b + ylen + clen));
+      s = apply_t<float>(h, n_rhs, v_dev, z_dev, nullptr, reinterpret_cast<float*>(b),
+                         reinterpret_cast<float*>(b + ylen), reinterpret_cast<float*>(b + ylen + clen));
     else
-      s = apply_t<double>(h, n_rhs, v_dev, z_dev, nullptr, h->d_lvalB, h->d_F64, h->d_Z64, h->d_Einv64,
-                          reinterpret_cast<double*>(b), reinterpret_cast<double*>(b + ylen),
-                          reinterpret_cast<double*>(b + ylen + clen));
+      s = apply_t<double>(h, n_rhs, v_dev, z_dev, nullptr, reinterpret_cast<double*>(b),
+                          reinterpret_cast<double*>(b + ylen), reinterpret_cast<double*>(b + ylen + clen));
   }
   if (cur != h->dev) cudaSetDevice(cur);
   return s;

@@ -70,6 +70,8 @@ def lib():
     L.hk_setup_device.argtypes = [C.POINTER(hk_mesh), _P, C.c_double, C.POINTER(hk_params), _P, C.POINTER(_P)]
     L.hk_set_timing.argtypes = [_P, C.c_int]
     L.hk_kernel_times.argtypes = [_P, _P, _P]
+    L.hk_kernel_launches.argtypes = []
+    L.hk_kernel_launches.restype = C.c_longlong
     L.hk_solve.argtypes = [_P, C.c_int, _P, C.c_double, _P, _P, _P, _P]
     L.hk_solve_device.argtypes = [_P, C.c_int, _P, C.c_double, _P, _P, _P, _P]
     L.hk_info.argtypes = [_P, C.POINTER(hk_info_t)]
@@ -161,6 +163,11 @@ def hk_setup_device(xyz_dev, elems_dev, is_boundary_dev, elem_coeff_dev, k, elem
 
 
 HK_T_NAMES = ("local_apply", "coarse_solve", "scatter", "spmv", "arnoldi", "cycle_end")
+
+
+def hk_kernel_launches() -> int:
+    """Kernels the library has launched in this process so far."""
+    return int(lib().hk_kernel_launches())
 
 
 def hk_set_timing(h: Handle, on: bool = True):
