@@ -325,6 +325,53 @@ __global__ void k_pull_fill(int n, int n_sub, const uint8_t* __restrict__ cls, c
   }
 }
 
+// Level sets and level order of arbitrary per-subdomain node sets (global dof ids, increasing):
+// counts[s] nodes at offsets[s] in d_nodes.  Writes the level order (d_nodes_lev), the position of
+// each sorted node in it (d_perm), and level pointers at offsets[s] + s (capacity counts[s] + 1).
+hk_status build_levels(hk_handle* h, const std::vector<int>& counts, const std::vector<int>& offsets,
+                       const int* d_nodes, int* d_levptr, int* d_perm, int* d_nodes_lev, std::vector<int>& L_out,
+                       int* max_width) {
+  cudaStream_t st = h->stream;
+  int ns = (int)counts.size();
+  long long tot = 0;
+  for (int c : counts) tot += c;
+  std::vector<int> info(8 * ns, 0);
+  for (int s = 0; s < ns; ++s) {
+    info[8 * s + 0] = counts[s];
+    info[8 * s + 3] = offsets[s];
+    info[8 * s + 5] = offsets[s] + s;
+  }
+  int *d_info = nullptr, *d_level = nullptr, *d_L = nullptr, *d_cap = nullptr, *d_mw = nullptr;
+  HK_TRY(dalloc(h, &d_info, info.size()));
+  HK_TRY(dalloc(h, &d_level, tot));
+  HK_TRY(dalloc(h, &d_L, ns));
+  HK_TRY(dalloc(h, &d_cap, ns));
+  HK_TRY(dalloc(h, &d_mw, 1));
+  HK_CUDA(cudaMemcpyAsync(d_info, info.data(), sizeof(int) * info.size(), cudaMemcpyHostToDevice, st));
+  k_levels<<<ns, 512, 0, st>>>(h->dim, h->d_xyz, h->d_node_of_dof, h->d_rowptr, h->d_col, d_info, d_nodes, d_level,
+                               d_L, d_cap, h->d_status);
+  HK_COUNT_LAUNCH();
+  HK_LAUNCH_CHECK();
+  L_out.assign(ns, 0);
+  HK_CUDA(cudaMemcpyAsync(L_out.data(), d_L, sizeof(int) * ns, cudaMemcpyDeviceToHost, st));
+  HK_CUDA(cudaStreamSynchronize(st));
+  HK_TRY(check_device_status(h, "level sets"));
+  for (int s = 0; s < ns; ++s) info[8 * s + 2] = L_out[s];
+  HK_CUDA(cudaMemcpyAsync(d_info, info.data(), sizeof(int) * info.size(), cudaMemcpyHostToDevice, st));
+  k_order<<<ns, 512, 0, st>>>(d_info, d_nodes, d_level, d_levptr, d_perm, d_nodes_lev, d_mw, h->d_status);
+  HK_COUNT_LAUNCH();
+  HK_LAUNCH_CHECK();
+  HK_CUDA(cudaMemcpyAsync(max_width, d_mw, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HK_CUDA(cudaStreamSynchronize(st));
+  HK_TRY(check_device_status(h, "level order"));
+  dfree(h, d_info);
+  dfree(h, d_level);
+  dfree(h, d_L);
+  dfree(h, d_cap);
+  dfree(h, d_mw);
+  return HK_OK;
+}
+
 hk_status upload_sub_info(hk_handle* h) {
   std::vector<int> info(8 * h->n_sub);
   std::vector<long long> off(3 * h->n_sub);

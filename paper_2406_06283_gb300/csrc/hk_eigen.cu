@@ -1,5 +1,4 @@
-// H_k-GenEO local eigenproblems (Eq. 5.12) and the coarse basis (Def. 5.1),
-// one CTA per subdomain, FP64 throughout.
+// H_k-GenEO local eigenproblems (Eq. 5.12) and the coarse basis (Def. 5.1).
 //
 // On ovdof(Omega_i) the problem is B^N p = lambda C p with B^N the local
 // Neumann Helmholtz matrix (element sums over Omega_i) and C = Xi D^N Xi,
@@ -7,23 +6,34 @@
 // columns B^N and D^N equal the global B and D_k (the star of a dof lies in
 // Omega_i); only the Gamma-Gamma block of B^N is local.  Eliminating the
 // Gamma unknowns (C vanishes there) gives the symmetric-definite pencil
-//     S p = lambda C_II p,   S = B_II - B_IG (B^N_GG)^{-1} B_GI,
-//     C_II = X D_II X,  X = diag(1/mu),
+//     S p = lambda C_II p,   S = B_II - B_IG (B^N_GG)^{-1} B_GI,  C_II = X D_II X,  X = diag(1/mu),
 // whose eigenvalues are real (the paper's lemma on indefinite pencils).
-// With the Cholesky factor D_II = L L^T (banded in level order) the standard
-// form is  A q = lambda q,  A = L^{-1} (mu S mu) L^{-T},  p = X^{-1} L^{-T} q,
-// and the coarse vector is Xi p = L^{-T} q, already c-normalised.
-// A is reduced to tridiagonal form by Householder reflections; eigenvalues
-// below tau come from Sturm-count bisection, eigenvectors from inverse
-// iteration on the tridiagonal matrix, then the reflections and L^{-T} are
-// applied.  Ties across tau (gap <= 1e-8 max(1,|tau|)) are kept together.
+//
+// Two stages, because FP64 arithmetic on this GPU runs at 1/58 of FP32:
+//  1. FP32 dense stage (candidates).  With D_II = L L^T (banded, level order) the standard form is
+//     A q = lambda q, A = L^{-1} (mu S mu) L^{-T}, p = X^{-1} L^{-T} q.  A is reduced to tridiagonal
+//     form by Householder reflections in FP32; Sturm-count bisection finds every eigenvalue below
+//     tau + delta (delta = 0.05, far above the FP32 error of these eigenvalues), FP32 inverse iteration
+//     on the tridiagonal matrix and the back-transform give approximate eigenvectors p.
+//  2. FP64 refinement on the sparse pencil.  Candidates closer than 1e-3 max(1,|lambda|) form a
+//     cluster; for each cluster the block-tridiagonal LU of B^N - sigma C over level sets of
+//     ovdof(Omega_i) is formed in FP64 (sigma = the cluster's mean candidate), the cluster's vectors
+//     take three steps of block inverse iteration ((B^N - sigma C)^{-1} C, C-orthonormalised after each
+//     step), and a Rayleigh-Ritz step on B^N gives the FP64 eigenpairs.  The Gamma part of each iterate
+//     satisfies the Gamma rows of the pencil exactly, so x^T B^N x = x_I^T S x_I.
+// Selection then keeps lambda < tau on the FP64 values, extending across ties (gap <= 1e-8 max(1,|tau|)),
+// and the coarse vectors are Xi p = p / mu on dof(Omega_i), c-normalised (Def. 5.1).
+#include <algorithm>
+#include <cmath>
+
 #include "hk_internal.cuh"
 
 static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
-struct EigWs {
-  long long W_off, T_off, L_off, G_off, R_off;  // per-subdomain offsets in the workspace
-};
+#define HK_EIG_DELTA 0.05
+#define HK_CLUSTER_GAP 1e-3
+#define HK_MAX_CLUSTER 32
+#define HK_REFINE_STEPS 3
 
 // ---- 1. B^N on Gamma x Gamma: element sums over the subdomain's elements.
 __global__ void k_gamma_block(int dim, int ne, const double* __restrict__ xyz, const int* __restrict__ elems,
@@ -87,7 +97,7 @@ __global__ void k_schur(const int* __restrict__ sub_info, const long long* __res
   double* R = ws + wsR[s];
   int* ring = ring_ws + off;  // up to nI entries
   // dense B_II
-  for (long long e = tid; e < (long long)nI * nI; e += T) W[e] = 0.0;
+  for (long long e = tid; e < (long long)nI * nI; e += T) W[e] = 0.0;  // no division: flat fill
   __syncthreads();
   for (int a = tid; a < nI; a += T) {
     long long b0 = coff + lr[a];
@@ -115,9 +125,9 @@ __global__ void k_schur(const int* __restrict__ sub_info, const long long* __res
     for (int i = k + 1 + tid; i < nG; i += T) BG[(long long)i * nG + k] /= lkk;
     __syncthreads();
     if (tid == 0) BG[(long long)k * nG + k] = lkk;
-    for (long long e = tid; e < (long long)(nG - k - 1) * (nG - k - 1); e += T) {
-      int i = k + 1 + (int)(e / (nG - k - 1)), j = k + 1 + (int)(e % (nG - k - 1));
-      if (j <= i) BG[(long long)i * nG + j] -= BG[(long long)i * nG + k] * BG[(long long)j * nG + k];
+    for (int i = k + 1 + (tid >> 5); i < nG; i += T >> 5) {
+      double lik = BG[(long long)i * nG + k];
+      for (int j = k + 1 + (tid & 31); j <= i; j += 32) BG[(long long)i * nG + j] -= lik * BG[(long long)j * nG + k];
     }
     __syncthreads();
   }
@@ -145,34 +155,39 @@ __global__ void k_schur(const int* __restrict__ sub_info, const long long* __res
   }
   __syncthreads();
   // W[ring a][ring b] -= sum_g B[a][g] X[g][b]
-  for (long long e = tid; e < (long long)nR * nR; e += T) {
-    int ra = (int)(e / nR), rb = (int)(e % nR);
+  for (int ra = tid >> 5; ra < nR; ra += T >> 5) {
     int a = ring[ra];
     long long b0 = coff + lr[a] + lcntI[off + a];
-    double v = 0;
-    for (int q = 0; q < lcntG[off + a]; ++q) v += lvalB[b0 + q] * R[(long long)lcol[b0 + q] * nR + rb];
-    W[(long long)a * nI + ring[rb]] -= v;
+    int cg = lcntG[off + a];
+    for (int rb = tid & 31; rb < nR; rb += 32) {
+      double v = 0;
+      for (int q = 0; q < cg; ++q) v += lvalB[b0 + q] * R[(long long)lcol[b0 + q] * nR + rb];
+      W[(long long)a * nI + ring[rb]] -= v;
+    }
   }
 }
 
-// ---- 3. banded Cholesky of D_II (level order) into Lb (nI x (bw+1)):
-// Lb[a][t] = L[a][a - bw + t].  Then A = L^{-1} (mu S mu) L^{-T}.
-__global__ void k_stdform(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
-                          const int* __restrict__ bw_arr, const int* __restrict__ Ilev, const int* __restrict__ mu,
-                          const int* __restrict__ lrow, const int* __restrict__ lcntI, const int* __restrict__ lcol,
-                          const double* __restrict__ lvalD, const long long* __restrict__ wsW,
-                          const long long* __restrict__ wsT, const long long* __restrict__ wsL, double* ws,
-                          DevStatus* st) {
+// ---- 3. FP32 standard form.  Banded Cholesky of D_II in FP64 into Lb (Lb[a][t] = L[a][a - bw + t]),
+// its FP32 copy L32, and A = L^{-1} (mu S mu) L^{-T} in FP32.  S is read from the FP64 workspace W,
+// which afterwards holds the FP32 transposed intermediate.
+__global__ void k_stdform32(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
+                            const int* __restrict__ bw_arr, const int* __restrict__ Ilev, const int* __restrict__ mu,
+                            const int* __restrict__ lrow, const int* __restrict__ lcntI, const int* __restrict__ lcol,
+                            const double* __restrict__ lvalD, const long long* __restrict__ wsW,
+                            const long long* __restrict__ wsL, const long long* __restrict__ wsA,
+                            const long long* __restrict__ wsL32, double* ws, float* ws32, DevStatus* st) {
   int s = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
   const int* si = sub_info + 8 * s;
   int nI = si[0], off = si[3];
-  int bw = bw_arr[s];
-  int ld = bw + 1;
+  int bw = bw_arr[s], ld = bw + 1;
   long long coff = sub_off[3 * s + 1];
   const int* lr = lrow + off + s;
   double* W = ws + wsW[s];
-  double* Tm = ws + wsT[s];
   double* Lb = ws + wsL[s];
+  float* A = ws32 + wsA[s];  // row stride lda = nI rounded up to 4 (padding columns stay 0)
+  float* L32 = ws32 + wsL32[s];
+  float* Tm = reinterpret_cast<float*>(W);
+  int lda = (nI + 3) & ~3;
   for (long long e = tid; e < (long long)nI * ld; e += T) Lb[e] = 0.0;
   __syncthreads();
   for (int a = tid; a < nI; a += T) {
@@ -183,7 +198,6 @@ __global__ void k_stdform(const int* __restrict__ sub_info, const long long* __r
     }
   }
   __syncthreads();
-  // right-looking banded Cholesky
   for (int k = 0; k < nI; ++k) {
     double piv = Lb[(long long)k * ld + bw];
     if (!(piv > 0.0)) {
@@ -199,115 +213,138 @@ __global__ void k_stdform(const int* __restrict__ sub_info, const long long* __r
     int w = iend - k;
     for (int e = tid; e < w * w; e += T) {
       int i = k + 1 + e / w, j = k + 1 + e % w;
-      if (j <= i) Lb[(long long)i * ld + (j - i + bw)] -= Lb[(long long)i * ld + (k - i + bw)] * Lb[(long long)j * ld + (k - j + bw)];
+      if (j <= i)
+        Lb[(long long)i * ld + (j - i + bw)] -=
+            Lb[(long long)i * ld + (k - i + bw)] * Lb[(long long)j * ld + (k - j + bw)];
     }
     __syncthreads();
   }
-  // W <- mu S mu, then column-wise forward substitution W <- L^{-1} W
-  for (long long e = tid; e < (long long)nI * nI; e += T) {
-    int a = (int)(e / nI), c = (int)(e % nI);
-    W[e] *= (double)mu[Ilev[off + a]] * (double)mu[Ilev[off + c]];
+  for (long long e = tid; e < (long long)nI * ld; e += T) L32[e] = (float)Lb[e];
+  int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+  for (int a = warp; a < nI; a += nw) {
+    double ma = (double)mu[Ilev[off + a]];
+    for (int c = lane; c < lda; c += 32)
+      A[(long long)a * lda + c] =
+          c < nI ? (float)(W[(long long)a * nI + c] * ma * (double)mu[Ilev[off + c]]) : 0.f;
   }
   __syncthreads();
   for (int pass = 0; pass < 2; ++pass) {
-    double* M = pass == 0 ? W : Tm;
+    float* M = pass == 0 ? A : Tm;
     for (int c = tid; c < nI; c += T) {
       for (int a = 0; a < nI; ++a) {
-        double v = M[(long long)a * nI + c];
+        float v = M[(long long)a * lda + c];
         int k0 = max(0, a - bw);
-        const double* la = Lb + (long long)a * ld + (k0 - a + bw);
-        for (int k = k0; k < a; ++k) v -= la[k - k0] * M[(long long)k * nI + c];
-        M[(long long)a * nI + c] = v / Lb[(long long)a * ld + bw];
+        const float* la = L32 + (long long)a * ld + (k0 - a + bw);
+        for (int k = k0; k < a; ++k) v -= la[k - k0] * M[(long long)k * lda + c];
+        M[(long long)a * lda + c] = v / L32[(long long)a * ld + bw];
       }
     }
     __syncthreads();
     if (pass == 0) {
-      for (long long e = tid; e < (long long)nI * nI; e += T) {
-        int a = (int)(e / nI), c = (int)(e % nI);
-        Tm[(long long)c * nI + a] = W[e];
-      }
+      for (int c = warp; c < nI; c += nw)
+        for (int a = lane; a < nI; a += 32) Tm[(long long)c * lda + a] = A[(long long)a * lda + c];
       __syncthreads();
     }
   }
-  // symmetrise into W
-  for (long long e = tid; e < (long long)nI * nI; e += T) {
-    int a = (int)(e / nI), c = (int)(e % nI);
-    W[e] = 0.5 * (Tm[e] + Tm[(long long)c * nI + a]);
-  }
+  for (int a = warp; a < nI; a += nw)
+    for (int c = lane; c < nI; c += 32)
+      A[(long long)a * lda + c] = 0.5f * (Tm[(long long)a * lda + c] + Tm[(long long)c * lda + a]);
 }
 
-// ---- 4. Householder tridiagonalisation of the dense symmetric A (full storage).
-// Reflector k: H_k = I - tau_k v v^T, v[k+1] = 1, v[j] stored in A[k][j] (j >= k+2).
-// d = diagonal, e = off-diagonal of the tridiagonal matrix.
-__global__ void k_tridiag(const int* __restrict__ sub_info, const long long* __restrict__ wsW, double* ws,
-                          double* dvec, double* evec, double* tauv, const int* __restrict__ vec_off) {
-  extern __shared__ double sm[];
+// ---- 4. Householder tridiagonalisation of the dense symmetric A (full storage, row stride lda = n
+// rounded up to 4), FP32 arithmetic, O(n) reductions in FP64.  Reflector k: H_k = I - tau_k v v^T,
+// v[k+1] = 1, v[j] stored in A[k][j] (j >= k+2).  d = diagonal, e = off-diagonal.  The shared vectors
+// v and p are kept zero below the active column and in the padding, so every row loop starts on a
+// 16-byte boundary and moves float4 (entries left of the active column change by exactly zero).
+__global__ void __launch_bounds__(1024) k_tridiag32(const int* __restrict__ sub_info, const long long* __restrict__ wsA,
+                                                    float* ws, double* dvec, double* evec, float* tauv,
+                                                    const int* __restrict__ vec_off) {
+  extern __shared__ __align__(16) float smf[];
   __shared__ double red[32];
-  int s = blockIdx.x, tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
-  const int* si = sub_info + 8 * s;
-  int n = si[0];
-  double* A = ws + wsW[s];
+  int s = blockIdx.x, tid = threadIdx.x, Tn = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = Tn >> 5;
+  int n = sub_info[8 * s];
+  int lda = (n + 3) & ~3, l4 = lda >> 2;
+  float* A = ws + wsA[s];
   double* d = dvec + vec_off[s];
   double* e = evec + vec_off[s];
-  double* tv = tauv + vec_off[s];
-  double* v = sm;       // n
-  double* p = sm + n;   // n
+  float* tv = tauv + vec_off[s];
+  float* v = smf;        // lda
+  float* p = smf + lda;  // lda
+  const float4* v4 = reinterpret_cast<const float4*>(v);
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+  for (int j = tid; j < 2 * lda; j += Tn) smf[j] = 0.f;
+  __syncthreads();
   for (int k = 0; k < n - 2; ++k) {
-    double* rk = A + (long long)k * n;
-    double alpha = rk[k + 1];
+    float* rk = A + (long long)k * lda;
+    double alpha = (double)rk[k + 1];
     double xs = 0;
-    for (int j = k + 2 + tid; j < n; j += T) xs += rk[j] * rk[j];
+    for (int j = k + 2 + tid; j < n; j += Tn) xs += (double)rk[j] * (double)rk[j];
     xs = block_sum(xs, red);
     double tau = 0, beta = alpha;
     if (xs > 0.0) {
       beta = -copysign(sqrt(alpha * alpha + xs), alpha);
       tau = (beta - alpha) / beta;
       double scale = 1.0 / (alpha - beta);
-      for (int j = k + 2 + tid; j < n; j += T) {
-        double vj = rk[j] * scale;
+      for (int j = k + 2 + tid; j < n; j += Tn) {
+        float vj = (float)((double)rk[j] * scale);
         rk[j] = vj;
         v[j] = vj;
       }
     } else {
-      for (int j = k + 2 + tid; j < n; j += T) v[j] = rk[j];
+      for (int j = k + 2 + tid; j < n; j += Tn) v[j] = rk[j];
     }
     if (tid == 0) {
-      v[k + 1] = 1.0;
-      d[k] = rk[k];
+      v[k] = 0.f;
+      p[k] = 0.f;
+      v[k + 1] = 1.f;
+      d[k] = (double)rk[k];
       e[k] = beta;
-      tv[k] = tau;
+      tv[k] = (float)tau;
     }
     __syncthreads();
     if (tau == 0.0) continue;
-    // p = tau * A22 v  (warp per row)
+    float tauf = (float)tau;
+    int c0 = (k + 1) >> 2;
     for (int i = k + 1 + warp; i < n; i += nw) {
-      const double* ri = A + (long long)i * n;
-      double acc = 0;
-      for (int j = k + 1 + lane; j < n; j += 32) acc += ri[j] * v[j];
-      acc = warp_sum(acc);
-      if (lane == 0) p[i] = tau * acc;
+      const float4* ri = reinterpret_cast<const float4*>(A + (long long)i * lda);
+      float acc = 0.f;
+#pragma unroll 4
+      for (int c = c0 + lane; c < l4; c += 32) {
+        float4 a = ri[c], b = v4[c];
+        acc += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+      }
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) p[i] = tauf * acc;
     }
     __syncthreads();
     double pv = 0;
-    for (int j = k + 1 + tid; j < n; j += T) pv += p[j] * v[j];
+    for (int j = k + 1 + tid; j < n; j += Tn) pv += (double)p[j] * (double)v[j];
     pv = block_sum(pv, red);
-    double K = 0.5 * tau * pv;
-    for (int j = k + 1 + tid; j < n; j += T) p[j] -= K * v[j];  // p becomes w
+    float K = (float)(0.5 * tau * pv);
+    for (int j = k + 1 + tid; j < n; j += Tn) p[j] -= K * v[j];  // p becomes w
     __syncthreads();
-    int m = n - k - 1;
-    for (long long q = tid; q < (long long)m * m; q += T) {
-      int i = k + 1 + (int)(q / m), j = k + 1 + (int)(q % m);
-      A[(long long)i * n + j] -= v[i] * p[j] + p[i] * v[j];
+    for (int i = k + 1 + warp; i < n; i += nw) {
+      float4* ri = reinterpret_cast<float4*>(A + (long long)i * lda);
+      float vi = v[i], pi = p[i];
+#pragma unroll 4
+      for (int c = c0 + lane; c < l4; c += 32) {
+        float4 a = ri[c], pv4 = p4[c], vv4 = v4[c];
+        a.x -= vi * pv4.x + pi * vv4.x;
+        a.y -= vi * pv4.y + pi * vv4.y;
+        a.z -= vi * pv4.z + pi * vv4.z;
+        a.w -= vi * pv4.w + pi * vv4.w;
+        ri[c] = a;
+      }
     }
     __syncthreads();
   }
   if (tid == 0) {
     if (n >= 2) {
-      d[n - 2] = A[(long long)(n - 2) * n + n - 2];
-      e[n - 2] = A[(long long)(n - 1) * n + n - 2];
-      tv[n - 2] = 0.0;
+      d[n - 2] = (double)A[(long long)(n - 2) * lda + n - 2];
+      e[n - 2] = (double)A[(long long)(n - 1) * lda + n - 2];
+      tv[n - 2] = 0.f;
     }
-    d[n - 1] = A[(long long)(n - 1) * n + n - 1];
+    d[n - 1] = (double)A[(long long)(n - 1) * lda + n - 1];
   }
 }
 
@@ -324,14 +361,13 @@ __device__ int sturm_count(const double* d, const double* e, int n, double x, do
   return c;
 }
 
-// ---- 5. bisection: eigenvalues 0 .. (count below tau) + extra, selection rule.
-#define HK_EXTRA 8
-__global__ void k_bisect(const int* __restrict__ sub_info, const double* __restrict__ dvec,
-                         const double* __restrict__ evec, const int* __restrict__ vec_off, double tau,
-                         double* lam_all, int* m_out, DevStatus* st) {
+// ---- 5. candidates: every eigenvalue of the tridiagonal matrix below tau + delta, by bisection
+// to 1e-7 of the spectral scale (the FP32 matrix is no more accurate than that).
+__global__ void k_candidates(const int* __restrict__ sub_info, const double* __restrict__ dvec,
+                             const double* __restrict__ evec, const int* __restrict__ vec_off, double tau,
+                             double* lam_hat, int* cnt_out, DevStatus* st) {
   __shared__ double lo_s, hi_s, pm_s;
-  __shared__ int cnt_s, nc_s;
-  __shared__ double lamsh[HK_MAXM + HK_EXTRA];
+  __shared__ int cnt_s;
   int s = blockIdx.x, tid = threadIdx.x;
   int n = sub_info[8 * s];
   const double* d = dvec + vec_off[s];
@@ -345,71 +381,57 @@ __global__ void k_bisect(const int* __restrict__ sub_info, const double* __restr
       if (i < n - 1) me = fmax(me, e[i] * e[i]);
     }
     double span = fmax(fabs(lo), fabs(hi));
-    lo -= 1e-14 * span + 1e-300;
-    hi += 1e-14 * span + 1e-300;
+    lo -= 1e-12 * span + 1e-300;
+    hi += 1e-12 * span + 1e-300;
     lo_s = lo;
     hi_s = hi;
     pm_s = 1e-290 * fmax(1.0, me);
-    int c = tau >= hi ? n : (tau <= lo ? 0 : sturm_count(d, e, n, tau, pm_s));
+    double x = tau + HK_EIG_DELTA;
+    int c = x >= hi ? n : (x <= lo ? 0 : sturm_count(d, e, n, x, pm_s));
     cnt_s = c;
-    nc_s = min(n, c + HK_EXTRA);
+    cnt_out[s] = c;
+    if (c > HK_MAXM) dev_fail(st, HK_UNSUPPORTED, s, c);
   }
   __syncthreads();
-  int c = cnt_s, nc = nc_s;
-  if (nc > HK_MAXM + HK_EXTRA) {
-    if (tid == 0) dev_fail(st, HK_UNSUPPORTED, s, c);
-    return;
-  }
-  for (int t = tid; t < nc; t += blockDim.x) {
+  int c = min(cnt_s, HK_MAXM);
+  double tol = 1e-7 * fmax(fabs(lo_s), fabs(hi_s));
+  for (int t = tid; t < c; t += blockDim.x) {
     double lo = lo_s, hi = hi_s;
-    for (int it = 0; it < 200; ++it) {
+    for (int it = 0; it < 100 && hi - lo > tol; ++it) {
       double mid = 0.5 * (lo + hi);
-      if (mid <= lo || mid >= hi) break;
-      if (hi - lo <= 2.2e-16 * fmax(fabs(lo), fabs(hi))) break;
       if (sturm_count(d, e, n, mid, pm_s) > t) hi = mid; else lo = mid;
     }
-    lamsh[t] = 0.5 * (lo + hi);
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double thr = 1e-8 * fmax(1.0, fabs(tau));
-    int m = c;
-    while (m > 0 && m < nc && lamsh[m] - lamsh[m - 1] <= thr) ++m;
-    if (m == nc && nc < n && m > 0 && lamsh[m - 1] - lamsh[m - 2 >= 0 ? m - 2 : 0] <= thr && m > c)
-      dev_fail(st, HK_EIG_FAIL, s, m);
-    if (m > HK_MAXM) dev_fail(st, HK_UNSUPPORTED, s, m);
-    m_out[s] = m;
-    for (int t = 0; t < m && t < HK_MAXM; ++t) lam_all[(long long)s * HK_MAXM + t] = lamsh[t];
+    lam_hat[(long long)s * HK_MAXM + t] = 0.5 * (lo + hi);
   }
 }
 
-// ---- 6. inverse iteration on T for the kept eigenvalues, with
-// reorthogonalisation inside groups of close eigenvalues.  One thread per
-// group; tridiagonal LU with partial pivoting (as in LAPACK's gttrf).
-__device__ double hash_unit(unsigned long long x) {
+// ---- 6. FP32 inverse iteration on the tridiagonal matrix for the candidates (one thread per group of
+// candidates closer than 1e-3 of the scale, reorthogonalised inside the group), tridiagonal LU with
+// partial pivoting.  Output: candidate-major vectors Q (c x n).
+__device__ float hash_unitf(unsigned long long x) {
   x += 0x9E3779B97F4A7C15ULL;
   x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
   x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
   x ^= x >> 31;
-  return (double)(x >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+  return (float)((double)(x >> 11) * (1.0 / 9007199254740992.0) - 0.5);
 }
 
-__global__ void k_inviter(const int* __restrict__ sub_info, const double* __restrict__ dvec,
-                          const double* __restrict__ evec, const int* __restrict__ vec_off,
-                          const double* __restrict__ lam_all, const long long* __restrict__ qoff, double* Q,
-                          const long long* __restrict__ woff, double* wk) {
+__global__ void k_inviter32(const int* __restrict__ sub_info, const double* __restrict__ dvec,
+                            const double* __restrict__ evec, const int* __restrict__ vec_off,
+                            const double* __restrict__ lam_hat, const int* __restrict__ cnt,
+                            const long long* __restrict__ qoff, float* Q, const long long* __restrict__ woff,
+                            float* wk) {
   int s = blockIdx.x;
-  const int* si = sub_info + 8 * s;
-  int n = si[0], m = si[6];
+  int n = sub_info[8 * s], m = min(cnt[s], HK_MAXM);
   const double* d = dvec + vec_off[s];
   const double* e = evec + vec_off[s];
-  const double* lam = lam_all + (long long)s * HK_MAXM;
-  double* Qs = Q + qoff[s];                 // m vectors of length n (vector-major)
+  const double* lam = lam_hat + (long long)s * HK_MAXM;
+  float* Qs = Q + qoff[s];
   double tnorm = 0;
   for (int i = 0; i < n; ++i)
     tnorm = fmax(tnorm, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0));
-  double ortol = 1e-3 * tnorm, eps = 2.2e-16;
-  // group starts: thread t handles the t-th group
+  double ortol = 1e-3 * tnorm;
+  float epsf = 1.2e-7f;
   int gcount = 0;
   for (int l = 0; l < m; ++l) {
     bool start = l == 0 || lam[l] - lam[l - 1] > ortol;
@@ -417,198 +439,635 @@ __global__ void k_inviter(const int* __restrict__ sub_info, const double* __rest
     if (gcount++ % blockDim.x != threadIdx.x) continue;
     int l1 = l + 1;
     while (l1 < m && lam[l1] - lam[l1 - 1] <= ortol) ++l1;
-    double* dd = wk + woff[s] + (long long)threadIdx.x * 5 * n;
-    double* du = dd + n;
-    double* du2 = du + n;
-    double* dl = du2 + n;
-    double* x = dl + n;
+    float* dd = wk + woff[s] + (long long)threadIdx.x * 5 * n;
+    float* du = dd + n;
+    float* du2 = du + n;
+    float* dl = du2 + n;
+    float* x = dl + n;
     double prev = -1e300;
     for (int t = l; t < l1; ++t) {
       double lt = lam[t];
-      if (lt - prev < 10 * eps * fmax(1.0, fabs(lt))) lt = prev + 10 * eps * fmax(1.0, fabs(prev));
+      if (lt - prev < 1e-6 * fmax(1.0, fabs(lt))) lt = prev + 1e-6 * fmax(1.0, fabs(prev));
       prev = lt;
-      // factor T - lt I
       for (int i = 0; i < n; ++i) {
-        dd[i] = d[i] - lt;
-        du[i] = i < n - 1 ? e[i] : 0.0;
-        dl[i] = i < n - 1 ? e[i] : 0.0;
-        du2[i] = 0.0;
+        dd[i] = (float)(d[i] - lt);
+        du[i] = i < n - 1 ? (float)e[i] : 0.f;
+        dl[i] = i < n - 1 ? (float)e[i] : 0.f;
+        du2[i] = 0.f;
       }
-      unsigned long long pivbits = 0;  // not enough for n > 64; store pivots as sign of du2 marker
       for (int i = 0; i < n - 1; ++i) {
-        if (fabs(dd[i]) >= fabs(dl[i])) {
-          if (dd[i] == 0.0) dd[i] = eps * tnorm;
-          double f = dl[i] / dd[i];
+        if (fabsf(dd[i]) >= fabsf(dl[i])) {
+          if (dd[i] == 0.f) dd[i] = epsf * (float)tnorm;
+          float f = dl[i] / dd[i];
           dl[i] = f;
           dd[i + 1] -= f * du[i];
-          du2[i] = 0.0;
-          x[i] = 0.0;  // no interchange
+          du2[i] = 0.f;
+          x[i] = 0.f;
         } else {
-          double f = dd[i] / dl[i];
+          float f = dd[i] / dl[i];
           dd[i] = dl[i];
           dl[i] = f;
-          double tmp = du[i];
+          float tmp = du[i];
           du[i] = dd[i + 1];
           dd[i + 1] = tmp - f * dd[i + 1];
           if (i < n - 2) {
             du2[i] = du[i + 1];
             du[i + 1] = -f * du[i + 1];
           }
-          x[i] = 1.0;  // interchange marker
+          x[i] = 1.f;
         }
       }
-      if (dd[n - 1] == 0.0) dd[n - 1] = eps * tnorm;
-      (void)pivbits;
-      // pivot markers live in x[0..n-2]; move them into dl's sign-free spare: use Qs vector as rhs
-      double* y = Qs + (long long)t * n;
-      for (int i = 0; i < n; ++i) y[i] = hash_unit(((unsigned long long)s << 32) ^ ((unsigned long long)t << 20) ^ i);
+      if (dd[n - 1] == 0.f) dd[n - 1] = epsf * (float)tnorm;
+      float* y = Qs + (long long)t * n;
+      for (int i = 0; i < n; ++i) y[i] = hash_unitf(((unsigned long long)s << 32) ^ ((unsigned long long)t << 20) ^ i);
       for (int it = 0; it < 3; ++it) {
-        // forward: apply L with interchanges
         for (int i = 0; i < n - 1; ++i) {
-          if (x[i] == 0.0) {
+          if (x[i] == 0.f) {
             y[i + 1] -= dl[i] * y[i];
           } else {
-            double tmp = y[i];
+            float tmp = y[i];
             y[i] = y[i + 1];
             y[i + 1] = tmp - dl[i] * y[i];
           }
         }
-        // back substitution with U (dd, du, du2)
         y[n - 1] /= dd[n - 1];
         if (n > 1) y[n - 2] = (y[n - 2] - du[n - 2] * y[n - 1]) / dd[n - 2];
         for (int i = n - 3; i >= 0; --i) y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) / dd[i];
-        // orthogonalise against the group's earlier vectors (twice)
         for (int rep = 0; rep < 2; ++rep)
           for (int u = l; u < t; ++u) {
-            const double* yu = Qs + (long long)u * n;
+            const float* yu = Qs + (long long)u * n;
             double dot = 0;
-            for (int i = 0; i < n; ++i) dot += yu[i] * y[i];
-            for (int i = 0; i < n; ++i) y[i] -= dot * yu[i];
+            for (int i = 0; i < n; ++i) dot += (double)yu[i] * (double)y[i];
+            for (int i = 0; i < n; ++i) y[i] -= (float)dot * yu[i];
           }
         double nrm = 0;
-        for (int i = 0; i < n; ++i) nrm += y[i] * y[i];
-        nrm = 1.0 / sqrt(nrm);
-        for (int i = 0; i < n; ++i) y[i] *= nrm;
+        for (int i = 0; i < n; ++i) nrm += (double)y[i] * (double)y[i];
+        float inv = (float)(1.0 / sqrt(nrm));
+        for (int i = 0; i < n; ++i) y[i] *= inv;
       }
     }
   }
 }
 
-// ---- 7. back-transform q = H_0 ... H_{n-3} y, then Z = L^{-T} q (row-major nI x m).
-__global__ void k_backtransform(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
-                                const int* __restrict__ bw_arr, const long long* __restrict__ wsW,
-                                const long long* __restrict__ wsL, const double* __restrict__ ws,
-                                const double* __restrict__ tauv, const int* __restrict__ vec_off,
-                                const long long* __restrict__ qoff, double* Q, double* Z) {
+// ---- 7. FP32 back-transform q = H_0 ... H_{n-3} y, then p = mu (L^{-T} q), written in FP64
+// (candidate-major, level order of dof).
+__global__ void k_backtransform32(const int* __restrict__ sub_info, const int* __restrict__ bw_arr,
+                                  const int* __restrict__ Ilev, const int* __restrict__ mu,
+                                  const long long* __restrict__ wsA, const long long* __restrict__ wsL32,
+                                  const float* __restrict__ ws32, const float* __restrict__ tauv,
+                                  const int* __restrict__ vec_off, const int* __restrict__ cnt,
+                                  const long long* __restrict__ qoff, float* Q, double* P) {
   int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int* si = sub_info + 8 * s;
-  int n = si[0], m = si[6];
+  int n = si[0], off = si[3], m = min(cnt[s], HK_MAXM);
   int bw = bw_arr[s], ld = bw + 1;
-  const double* A = ws + wsW[s];
-  const double* Lb = ws + wsL[s];
-  const double* tv = tauv + vec_off[s];
-  double* Qs = Q + qoff[s];
-  double* Zs = Z + sub_off[3 * s + 2];
+  const float* A = ws32 + wsA[s];
+  const float* Lb = ws32 + wsL32[s];
+  const float* tv = tauv + vec_off[s];
+  float* Qs = Q + qoff[s];
+  double* Ps = P + qoff[s];
   for (int k = n - 3; k >= 0; --k) {
-    double tau = tv[k];
-    if (tau == 0.0) continue;
-    const double* rk = A + (long long)k * n;
+    float tau = tv[k];
+    if (tau == 0.f) continue;
+    const float* rk = A + (long long)k * ((n + 3) & ~3);
     for (int l = warp; l < m; l += nw) {
-      double* q = Qs + (long long)l * n;
-      double acc = lane == 0 ? q[k + 1] : 0.0;
+      float* q = Qs + (long long)l * n;
+      float acc = lane == 0 ? q[k + 1] : 0.f;
       for (int j = k + 2 + lane; j < n; j += 32) acc += rk[j] * q[j];
-      acc = warp_sum(acc) * tau;
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      acc *= tau;
       if (lane == 0) q[k + 1] -= acc;
       for (int j = k + 2 + lane; j < n; j += 32) q[j] -= acc * rk[j];
     }
     __syncthreads();
   }
-  // Z[:, l] = L^{-T} q_l (thread per vector)
   for (int l = tid; l < m; l += blockDim.x) {
-    double* q = Qs + (long long)l * n;
+    float* q = Qs + (long long)l * n;
     for (int a = n - 1; a >= 0; --a) {
-      double v = q[a];
+      float v = q[a];
       int cend = min(n - 1, a + bw);
       for (int c = a + 1; c <= cend; ++c) v -= Lb[(long long)c * ld + (a - c + bw)] * q[c];
       q[a] = v / Lb[(long long)a * ld + bw];
     }
-    for (int a = 0; a < n; ++a) Zs[(long long)a * m + l] = q[a];
+    double* p = Ps + (long long)l * n;
+    for (int a = 0; a < n; ++a) p[a] = (double)q[a] * (double)mu[Ilev[off + a]];
+  }
+}
+
+// ---- 8. ovdof(Omega_i) = dof U Gamma: merged sorted list, membership and index in dof / Gamma.
+__global__ void k_o_merge(const int* __restrict__ sub_info, const int* __restrict__ Isorted,
+                          const int* __restrict__ G, const int* __restrict__ o_off, int* O, int* o_kind) {
+  int s = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  const int* si = sub_info + 8 * s;
+  int nI = si[0], nG = si[1], ioff = si[3], goff = si[4], oo = o_off[s];
+  int a = 0, b = 0, k = 0;
+  while (a < nI || b < nG) {
+    bool takeI = b >= nG || (a < nI && Isorted[ioff + a] < G[goff + b]);
+    if (takeI) {
+      O[oo + k] = Isorted[ioff + a];
+      o_kind[oo + k] = a;  // >= 0: index in the sorted dof list
+      ++a;
+    } else {
+      O[oo + k] = G[goff + b];
+      o_kind[oo + k] = -1 - b;  // < 0: -(1 + index in the Gamma list)
+      ++b;
+    }
+    ++k;
+  }
+}
+
+// Local CSR of B^N and C over ovdof in its level order (capacity maxrow per row).  B^N: global B
+// where a dof is involved, the element sums over the subdomain (BG, dense) on Gamma x Gamma.
+// C = X D X on dof x dof, 0 elsewhere.  o2i: level position of each ovdof row in the dof level order
+// (-1 on Gamma).
+__global__ void k_o_csr(const int* __restrict__ sub_info, const int* __restrict__ o_off,
+                        const int* __restrict__ O, const int* __restrict__ o_kind, const int* __restrict__ O_perm,
+                        const int* __restrict__ O_lev, const int* __restrict__ perm_I,
+                        const int* __restrict__ rowptr, const int* __restrict__ col, const double* __restrict__ valB,
+                        const double* __restrict__ valD, const int* __restrict__ mu,
+                        const long long* __restrict__ wsG, const double* __restrict__ ws, int maxrow, int* ocnt,
+                        int* ocol, double* oB, double* oC, int* o2i) {
+  int s = blockIdx.x;
+  const int* si = sub_info + 8 * s;
+  int nI = si[0], nG = si[1], ioff = si[3];
+  int oo = o_off[s], nO = nI + nG;
+  const double* BG = ws + wsG[s];
+  for (int a = threadIdx.x; a < nO; a += blockDim.x) {
+    int g = O_lev[oo + a];
+    int gi = bsearch_int(O + oo, nO, g);
+    int kg = o_kind[oo + gi];
+    o2i[oo + a] = kg >= 0 ? perm_I[ioff + kg] : -1;
+    long long base = (long long)(oo + a) * maxrow;
+    int c = 0;
+    for (int q = rowptr[g]; q < rowptr[g + 1]; ++q) {
+      int h = col[q];
+      int hi = bsearch_int(O + oo, nO, h);
+      if (hi < 0) continue;
+      int kh = o_kind[oo + hi];
+      double b;
+      if (kg >= 0 || kh >= 0) b = valB[q];
+      else b = BG[(long long)(-1 - kg) * nG + (-1 - kh)];
+      double cval = (kg >= 0 && kh >= 0) ? valD[q] / ((double)mu[g] * (double)mu[h]) : 0.0;
+      if (c < maxrow) {
+        ocol[base + c] = O_perm[oo + hi];
+        oB[base + c] = b;
+        oC[base + c] = cval;
+      }
+      ++c;
+    }
+    ocnt[oo + a] = c;
+  }
+}
+
+// Small symmetric eigenproblem by cyclic Jacobi (one thread): A (p x p, row-major, destroyed),
+// eigenvalues ascending in w, eigenvectors as columns of U.
+__device__ void jacobi_eig(double* A, double* U, double* w, int p) {
+  for (int i = 0; i < p; ++i)
+    for (int j = 0; j < p; ++j) U[i * p + j] = i == j ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0, dia = 0;
+    for (int i = 0; i < p; ++i)
+      for (int j = 0; j < p; ++j) (i == j ? dia : off) += A[i * p + j] * A[i * p + j];
+    if (off <= 1e-30 * dia || off == 0.0) break;
+    for (int i = 0; i < p; ++i)
+      for (int j = i + 1; j < p; ++j) {
+        double aij = A[i * p + j];
+        if (aij == 0.0) continue;
+        double th = (A[j * p + j] - A[i * p + i]) / (2 * aij);
+        double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < p; ++k) {
+          double aki = A[k * p + i], akj = A[k * p + j];
+          A[k * p + i] = c * aki - sn * akj;
+          A[k * p + j] = sn * aki + c * akj;
+        }
+        for (int k = 0; k < p; ++k) {
+          double aik = A[i * p + k], ajk = A[j * p + k];
+          A[i * p + k] = c * aik - sn * ajk;
+          A[j * p + k] = sn * aik + c * ajk;
+        }
+        for (int k = 0; k < p; ++k) {
+          double uki = U[k * p + i], ukj = U[k * p + j];
+          U[k * p + i] = c * uki - sn * ukj;
+          U[k * p + j] = sn * uki + c * ukj;
+        }
+      }
+  }
+  for (int i = 0; i < p; ++i) w[i] = A[i * p + i];
+  // sort ascending (selection sort on columns)
+  for (int i = 0; i < p; ++i) {
+    int b = i;
+    for (int j = i + 1; j < p; ++j)
+      if (w[j] < w[b]) b = j;
+    if (b != i) {
+      double t = w[i]; w[i] = w[b]; w[b] = t;
+      for (int k = 0; k < p; ++k) {
+        double u = U[k * p + i]; U[k * p + i] = U[k * p + b]; U[k * p + b] = u;
+      }
+    }
+  }
+}
+
+// Deterministic block-wide dot product of two device vectors.
+__device__ double block_dot(const double* x, const double* y, int n, double* red) {
+  double acc = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += x[i] * y[i];
+  return block_sum(acc, red);
+}
+
+// y = M x for the sparse ovdof matrix M = (which ? C : B^N) - shift C, p vectors (rows in level order).
+__device__ void o_matvec(int nO, int oo, int maxrow, const int* ocnt, const int* ocol, const double* oB,
+                         const double* oC, double shift, int use_B, const double* X, double* Y, int p) {
+  for (int e = threadIdx.x; e < nO * p; e += blockDim.x) {
+    int t = e / nO, a = e % nO;
+    long long base = (long long)(oo + a) * maxrow;
+    int c = min(ocnt[oo + a], maxrow);
+    double acc = 0;
+    for (int q = 0; q < c; ++q) {
+      double v = (use_B ? oB[base + q] : 0.0) + shift * oC[base + q];
+      acc += v * X[(long long)t * nO + ocol[base + q]];
+    }
+    Y[(long long)t * nO + a] = acc;
+  }
+}
+
+// ---- 9. FP64 refinement of one cluster of candidates (one CTA per cluster).
+// Work item: subdomain s, first candidate t0, count p; shift sigma.
+__global__ void k_refine(const int* __restrict__ items, const double* __restrict__ sigmas,
+                         const int* __restrict__ sub_info, const int* __restrict__ o_off,
+                         const int* __restrict__ O_levptr, const int* __restrict__ O_L, int maxrow,
+                         const int* __restrict__ ocnt, const int* __restrict__ ocol, const double* __restrict__ oB,
+                         const double* __restrict__ oC, const int* __restrict__ o2i,
+                         const long long* __restrict__ f_off, const long long* __restrict__ x_off, double* F,
+                         double* Xw, const long long* __restrict__ poff, double* P, double* lam_ref, int max_b,
+                         DevStatus* st) {
+  extern __shared__ double smem[];
+  __shared__ int piv[HK_MAXB];
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ double minpiv, sh_val;
+  __shared__ double Hs[HK_MAX_CLUSTER * HK_MAX_CLUSTER], Us[HK_MAX_CLUSTER * HK_MAX_CLUSTER], ws_[HK_MAX_CLUSTER];
+  int it = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
+  int s = items[4 * it], t0 = items[4 * it + 1], p = items[4 * it + 2];
+  double sigma = sigmas[it];
+  const int* si = sub_info + 8 * s;
+  int nI = si[0], nG = si[1];
+  int oo = o_off[s], nO = nI + nG, L = O_L[s];
+  const int* lp = O_levptr + oo + s;
+  double* S = smem;                           // max_b x max_b
+  double* tv = smem + (long long)max_b * max_b;  // max_b x p
+  double* Fw = F + f_off[it];
+  double* X = Xw + x_off[it];                 // p x nO
+  double* R = X + (long long)p * nO;          // p x nO
+  double* Ps = P + poff[s];
+  // scale for the pivot floor
+  double mx = 0;
+  for (long long e = tid; e < (long long)nO * maxrow; e += T) {
+    int a = (int)(e / maxrow), q = (int)(e % maxrow);
+    if (q < ocnt[oo + a]) mx = fmax(mx, fabs(oB[(long long)oo * maxrow + e] - sigma * oC[(long long)oo * maxrow + e]));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((tid & 31) == 0) red_v[tid >> 5] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m2 = 0;
+    for (int w = 0; w < (T >> 5); ++w) m2 = fmax(m2, red_v[w]);
+    sh_val = m2;
+    minpiv = 1e300;
+  }
+  __syncthreads();
+  double floor_piv = 1e-14 * sh_val;
+  // 1. block LU of M = B^N - sigma C over the ovdof level sets
+  long long bo = 0, prev_go = -1;
+  int prev_r0 = 0;
+  for (int j = 0; j < L; ++j) {
+    int r0 = lp[j], b = lp[j + 1] - r0, r1 = lp[j + 1];
+    int bn = j + 1 < L ? lp[j + 2] - r1 : 0;
+    for (int e = tid; e < b * b; e += T) {
+      int qa = e / b, t = e % b;
+      int a = r0 + qa;
+      long long base = (long long)(oo + a) * maxrow;
+      int cnt = min(ocnt[oo + a], maxrow);
+      double v = 0;
+      for (int q = 0; q < cnt; ++q) {
+        int c = ocol[base + q];
+        double mv = oB[base + q] - sigma * oC[base + q];
+        if (c == r0 + t) v += mv;
+        else if (j > 0 && c >= prev_r0 && c < r0) v -= mv * Fw[prev_go + (long long)(c - prev_r0) * b + t];
+      }
+      S[e] = v;
+    }
+    __syncthreads();
+    gauss_jordan_inverse(S, b, piv, red_v, red_i, &minpiv, floor_piv);
+    for (int e = tid; e < b * b; e += T) Fw[bo + e] = S[e];
+    long long go = bo + (long long)b * b;
+    for (int e = tid; e < b * bn; e += T) {
+      int qt = e / bn, cc = e % bn;
+      int c = r1 + cc;
+      long long base = (long long)(oo + c) * maxrow;
+      int cnt = min(ocnt[oo + c], maxrow);
+      double v = 0;
+      for (int q = 0; q < cnt; ++q) {
+        int a = ocol[base + q];
+        if (a >= r0 && a < r1) v += S[qt * b + (a - r0)] * (oB[base + q] - sigma * oC[base + q]);
+      }
+      Fw[go + e] = v;
+    }
+    __syncthreads();
+    prev_go = go;
+    prev_r0 = r0;
+    bo = go + (long long)b * bn;
+  }
+  // 2. start block: the FP32 candidates, zero on Gamma
+  for (int t = 0; t < p; ++t)
+    for (int a = tid; a < nO; a += T) {
+      int ia = o2i[oo + a];
+      X[(long long)t * nO + a] = ia >= 0 ? Ps[(long long)(t0 + t) * nI + ia] : 0.0;
+    }
+  __syncthreads();
+  for (int step = 0; step < HK_REFINE_STEPS; ++step) {
+    // R = C X, then X = M^{-1} R by the two block sweeps
+    o_matvec(nO, oo, maxrow, ocnt, ocol, oB, oC, 1.0, 0, X, R, p);
+    __syncthreads();
+    long long fo = 0;
+    for (int j = 0; j < L; ++j) {
+      int r0 = lp[j], b = lp[j + 1] - r0, bn = j + 1 < L ? lp[j + 2] - lp[j + 1] : 0;
+      for (int e = tid; e < b * p; e += T) {
+        int t = e / b, a = r0 + e % b;
+        long long base = (long long)(oo + a) * maxrow;
+        int cnt = min(ocnt[oo + a], maxrow);
+        double acc = R[(long long)t * nO + a];
+        for (int q = 0; q < cnt; ++q) {
+          int c = ocol[base + q];
+          if (c < r0) acc -= (oB[base + q] - sigma * oC[base + q]) * R[(long long)t * nO + c];
+        }
+        tv[e] = acc;
+      }
+      __syncthreads();
+      for (int e = tid; e < b * p; e += T) {
+        int t = e / b, q = e % b;
+        const double* Sr = Fw + fo + (long long)q * b;
+        double acc = 0;
+        for (int c = 0; c < b; ++c) acc += Sr[c] * tv[t * b + c];
+        R[(long long)t * nO + r0 + q] = acc;
+      }
+      __syncthreads();
+      fo += (long long)b * b + (long long)b * bn;
+    }
+    // backward: x_j -= G_j x_{j+1}
+    {
+      int bl = lp[L] - lp[L - 1];
+      fo -= (long long)bl * bl;
+    }
+    for (int j = L - 2; j >= 0; --j) {
+      int r0 = lp[j], b = lp[j + 1] - r0, r1 = lp[j + 1], bn = lp[j + 2] - r1;
+      fo -= (long long)b * b + (long long)b * bn;
+      const double* Gm = Fw + fo + (long long)b * b;
+      for (int e = tid; e < b * p; e += T) {
+        int t = e / b, q = e % b;
+        double acc = 0;
+        for (int c = 0; c < bn; ++c) acc += Gm[(long long)q * bn + c] * R[(long long)t * nO + r1 + c];
+        tv[e] = acc;
+      }
+      __syncthreads();
+      for (int e = tid; e < b * p; e += T) {
+        int t = e / b, q = e % b;
+        R[(long long)t * nO + r0 + q] -= tv[e];
+      }
+      __syncthreads();
+    }
+    // X = R, C-orthonormalised (modified Gram-Schmidt twice; CX kept alongside in R)
+    for (long long e = tid; e < (long long)p * nO; e += T) X[e] = R[e];
+    __syncthreads();
+    o_matvec(nO, oo, maxrow, ocnt, ocol, oB, oC, 1.0, 0, X, R, p);  // R = C X
+    __syncthreads();
+    for (int rep = 0; rep < 2; ++rep)
+      for (int t = 0; t < p; ++t) {
+        double* xt = X + (long long)t * nO;
+        double* cxt = R + (long long)t * nO;
+        for (int u = 0; u < t; ++u) {
+          double dcu = block_dot(xt, R + (long long)u * nO, nO, red_v);
+          for (int a = tid; a < nO; a += T) {
+            xt[a] -= dcu * X[(long long)u * nO + a];
+            cxt[a] -= dcu * R[(long long)u * nO + a];
+          }
+          __syncthreads();
+        }
+        double nrm = block_dot(xt, cxt, nO, red_v);
+        double inv = nrm > 0 ? 1.0 / sqrt(nrm) : 0.0;
+        for (int a = tid; a < nO; a += T) {
+          xt[a] *= inv;
+          cxt[a] *= inv;
+        }
+        __syncthreads();
+      }
+  }
+  // 3. Rayleigh-Ritz on B^N: H = X^T B^N X (X is C-orthonormal)
+  o_matvec(nO, oo, maxrow, ocnt, ocol, oB, oC, 0.0, 1, X, R, p);  // R = B^N X
+  __syncthreads();
+  for (int i = 0; i < p; ++i)
+    for (int j = 0; j < p; ++j) {
+      double h = block_dot(X + (long long)i * nO, R + (long long)j * nO, nO, red_v);
+      if (tid == 0) Hs[i * p + j] = h;
+    }
+  __syncthreads();
+  if (tid == 0) {
+    for (int i = 0; i < p; ++i)
+      for (int j = i + 1; j < p; ++j) {
+        double a = 0.5 * (Hs[i * p + j] + Hs[j * p + i]);
+        Hs[i * p + j] = Hs[j * p + i] = a;
+      }
+    jacobi_eig(Hs, Us, ws_, p);
+    for (int i = 0; i < p; ++i) lam_ref[(long long)s * HK_MAXM + t0 + i] = ws_[i];
+    if (!(minpiv > 0)) dev_fail(st, HK_EIG_FAIL, s, minpiv);
+  }
+  __syncthreads();
+  // refined vectors X U, written back (dof part, level order) over the candidates
+  for (int i = 0; i < p; ++i)
+    for (int a = tid; a < nO; a += T) {
+      int ia = o2i[oo + a];
+      if (ia < 0) continue;
+      double acc = 0;
+      for (int k = 0; k < p; ++k) acc += X[(long long)k * nO + a] * Us[k * p + i];
+      Ps[(long long)(t0 + i) * nI + ia] = acc;
+    }
+}
+
+// ---- 10. selection on the FP64 values: keep lambda < tau, extended across ties; order ascending.
+__global__ void k_select(const int* __restrict__ cnt, const double* __restrict__ lam_ref, double tau, int* sel,
+                         int* m_out, double* lam_out, DevStatus* st) {
+  int s = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  int c = min(cnt[s], HK_MAXM);
+  const double* lr = lam_ref + (long long)s * HK_MAXM;
+  int* ord = sel + (long long)s * HK_MAXM;
+  for (int i = 0; i < c; ++i) ord[i] = i;
+  for (int i = 1; i < c; ++i) {
+    int k = ord[i], j = i - 1;
+    while (j >= 0 && lr[ord[j]] > lr[k]) {
+      ord[j + 1] = ord[j];
+      --j;
+    }
+    ord[j + 1] = k;
+  }
+  int m = 0;
+  while (m < c && lr[ord[m]] < tau) ++m;
+  double thr = 1e-8 * fmax(1.0, fabs(tau));
+  while (m > 0 && m < c && lr[ord[m]] - lr[ord[m - 1]] <= thr) ++m;
+  if (m == c && c == cnt[s] && m > 0 && lr[ord[m - 1]] >= tau) dev_fail(st, HK_EIG_FAIL, s, m);
+  m_out[s] = m;
+  for (int i = 0; i < m; ++i) lam_out[(long long)s * HK_MAXM + i] = lr[ord[i]];
+}
+
+// Z_i columns = Xi p = p / mu on dof(Omega_i) (row-major |dof| x m, level order).
+__global__ void k_write_z(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
+                          const int* __restrict__ Ilev, const int* __restrict__ mu, const int* __restrict__ sel,
+                          const long long* __restrict__ poff, const double* __restrict__ P, double* Z) {
+  int s = blockIdx.x;
+  const int* si = sub_info + 8 * s;
+  int nI = si[0], off = si[3], m = si[6];
+  long long zo = sub_off[3 * s + 2];
+  const int* ord = sel + (long long)s * HK_MAXM;
+  const double* Ps = P + poff[s];
+  for (long long e = threadIdx.x; e < (long long)nI * m; e += blockDim.x) {
+    int a = (int)(e / m), l = (int)(e % m);
+    Z[zo + e] = Ps[(long long)ord[l] * nI + a] / (double)mu[Ilev[off + a]];
   }
 }
 
 hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   cudaStream_t st = h->stream;
   int ns = h->n_sub;
-  // workspace layout
-  std::vector<long long> W(ns), Tt(ns), Lw(ns), Gw(ns), Rw(ns);
-  std::vector<int> voff(ns), bw(ns);
-  long long tot = 0;
-  int vo = 0, maxn = 0;
+  // ---- workspace layout (FP64 part and FP32 part)
+  std::vector<long long> W(ns), Lw(ns), Gw(ns), Rw(ns), Aw(ns), L32w(ns);
+  std::vector<int> voff(ns), bw(ns), o_off(ns), oc(ns);
+  long long tot = 0, tot32 = 0;
+  int vo = 0, maxn = 0, O_total = 0;
   for (int s = 0; s < ns; ++s) {
     const Sub& u = h->subs[s];
     long long nI = u.nI, nG = u.nG;
     W[s] = tot; tot += nI * nI;
-    Tt[s] = tot; tot += nI * nI;
     Lw[s] = tot; tot += nI * (u.bw + 1);
     Gw[s] = tot; tot += nG * nG;
     Rw[s] = tot; tot += nG * nI;
     tot = (tot + 3) & ~3LL;
+    Aw[s] = tot32; tot32 += nI * ((nI + 3) & ~3LL);
+    L32w[s] = tot32; tot32 += nI * (u.bw + 1);
+    tot32 = (tot32 + 3) & ~3LL;
     voff[s] = vo;
     vo += u.nI;
     bw[s] = u.bw;
-    if (u.nI > maxn) maxn = u.nI;
+    maxn = std::max(maxn, u.nI);
+    o_off[s] = O_total;
+    oc[s] = u.nI + u.nG;
+    O_total += oc[s];
   }
   double* d_ws = nullptr;
-  long long *d_W = nullptr, *d_T = nullptr, *d_L = nullptr, *d_Gw = nullptr, *d_Rw = nullptr;
-  int *d_voff = nullptr, *d_bw = nullptr, *d_ring = nullptr, *d_m = nullptr;
-  double *d_d = nullptr, *d_e = nullptr, *d_tau = nullptr;
+  float* d_ws32 = nullptr;
+  long long *d_W = nullptr, *d_L = nullptr, *d_Gw = nullptr, *d_Rw = nullptr, *d_A = nullptr, *d_L32 = nullptr;
+  int *d_voff = nullptr, *d_bw = nullptr, *d_ring = nullptr, *d_cnt = nullptr, *d_o_off = nullptr;
+  double *d_d = nullptr, *d_e = nullptr, *d_lamhat = nullptr, *d_lamref = nullptr;
+  float* d_tau = nullptr;
   HK_TRY(dalloc(h, &d_ws, tot));
+  HK_TRY(dalloc(h, &d_ws32, tot32));
   HK_TRY(dalloc(h, &d_W, ns));
-  HK_TRY(dalloc(h, &d_T, ns));
   HK_TRY(dalloc(h, &d_L, ns));
   HK_TRY(dalloc(h, &d_Gw, ns));
   HK_TRY(dalloc(h, &d_Rw, ns));
+  HK_TRY(dalloc(h, &d_A, ns));
+  HK_TRY(dalloc(h, &d_L32, ns));
   HK_TRY(dalloc(h, &d_voff, ns));
   HK_TRY(dalloc(h, &d_bw, ns));
   HK_TRY(dalloc(h, &d_ring, h->I_total));
-  HK_TRY(dalloc(h, &d_m, ns));
+  HK_TRY(dalloc(h, &d_cnt, ns));
+  HK_TRY(dalloc(h, &d_o_off, ns));
   HK_TRY(dalloc(h, &d_d, vo));
   HK_TRY(dalloc(h, &d_e, vo));
   HK_TRY(dalloc(h, &d_tau, vo));
+  HK_TRY(dalloc(h, &d_lamhat, (size_t)ns * HK_MAXM));
+  HK_TRY(dalloc(h, &d_lamref, (size_t)ns * HK_MAXM));
   HK_TRY(dalloc(h, &h->d_lam, (size_t)ns * HK_MAXM));
-  HK_CUDA(cudaMemcpyAsync(d_W, W.data(), 8 * ns, cudaMemcpyHostToDevice, st));
-  HK_CUDA(cudaMemcpyAsync(d_T, Tt.data(), 8 * ns, cudaMemcpyHostToDevice, st));
-  HK_CUDA(cudaMemcpyAsync(d_L, Lw.data(), 8 * ns, cudaMemcpyHostToDevice, st));
-  HK_CUDA(cudaMemcpyAsync(d_Gw, Gw.data(), 8 * ns, cudaMemcpyHostToDevice, st));
-  HK_CUDA(cudaMemcpyAsync(d_Rw, Rw.data(), 8 * ns, cudaMemcpyHostToDevice, st));
-  HK_CUDA(cudaMemcpyAsync(d_voff, voff.data(), 4 * ns, cudaMemcpyHostToDevice, st));
-  HK_CUDA(cudaMemcpyAsync(d_bw, bw.data(), 4 * ns, cudaMemcpyHostToDevice, st));
+  auto up = [&](void* d, const void* hsrc, size_t bytes) {
+    return cudaMemcpyAsync(d, hsrc, bytes, cudaMemcpyHostToDevice, st);
+  };
+  HK_CUDA(up(d_W, W.data(), 8 * ns));
+  HK_CUDA(up(d_L, Lw.data(), 8 * ns));
+  HK_CUDA(up(d_Gw, Gw.data(), 8 * ns));
+  HK_CUDA(up(d_Rw, Rw.data(), 8 * ns));
+  HK_CUDA(up(d_A, Aw.data(), 8 * ns));
+  HK_CUDA(up(d_L32, L32w.data(), 8 * ns));
+  HK_CUDA(up(d_voff, voff.data(), 4 * ns));
+  HK_CUDA(up(d_bw, bw.data(), 4 * ns));
+  HK_CUDA(up(d_o_off, o_off.data(), 4 * ns));
 
+  // ---- B^N on Gamma x Gamma, then the ovdof structure (before the Cholesky of BG overwrites it)
   k_gamma_block<<<ns, 128, 0, st>>>(h->dim, h->n_elems, h->d_xyz, h->d_elems, h->d_coeff, h->k * h->k,
                                     h->d_node_of_dof, h->d_dof_of_node, h->d_ne_ptr, h->d_ne_idx, d_elem_in,
-                                    h->d_sub_info, h->d_G, d_Gw, d_ws); HK_COUNT_LAUNCH();
+                                    h->d_sub_info, h->d_G, d_Gw, d_ws);
+  HK_COUNT_LAUNCH();
+  int *d_O = nullptr, *d_okind = nullptr, *d_Operm = nullptr, *d_Olev = nullptr, *d_Olevptr = nullptr;
+  HK_TRY(dalloc(h, &d_O, O_total));
+  HK_TRY(dalloc(h, &d_okind, O_total));
+  HK_TRY(dalloc(h, &d_Operm, O_total));
+  HK_TRY(dalloc(h, &d_Olev, O_total));
+  HK_TRY(dalloc(h, &d_Olevptr, O_total + ns));
+  k_o_merge<<<ns, 32, 0, st>>>(h->d_sub_info, h->d_Isorted, h->d_G, d_o_off, d_O, d_okind);
+  HK_COUNT_LAUNCH();
+  HK_LAUNCH_CHECK();
+  std::vector<int> OL;
+  int maxbO = 0;
+  HK_TRY(build_levels(h, oc, o_off, d_O, d_Olevptr, d_Operm, d_Olev, OL, &maxbO));
+  int* d_OL = nullptr;
+  HK_TRY(dalloc(h, &d_OL, ns));
+  HK_CUDA(up(d_OL, OL.data(), 4 * ns));
+  std::vector<int> rp(h->n + 1);
+  HK_CUDA(cudaMemcpyAsync(rp.data(), h->d_rowptr, sizeof(int) * (h->n + 1), cudaMemcpyDeviceToHost, st));
+  HK_CUDA(cudaStreamSynchronize(st));
+  int maxrow = 1;
+  for (int i = 0; i < h->n; ++i) maxrow = std::max(maxrow, rp[i + 1] - rp[i]);
+  int *d_ocnt = nullptr, *d_ocol = nullptr, *d_o2i = nullptr;
+  double *d_oB = nullptr, *d_oC = nullptr;
+  HK_TRY(dalloc(h, &d_ocnt, O_total));
+  HK_TRY(dalloc(h, &d_o2i, O_total));
+  HK_TRY(dalloc(h, &d_ocol, (size_t)O_total * maxrow));
+  HK_TRY(dalloc(h, &d_oB, (size_t)O_total * maxrow));
+  HK_TRY(dalloc(h, &d_oC, (size_t)O_total * maxrow));
+  k_o_csr<<<ns, 128, 0, st>>>(h->d_sub_info, d_o_off, d_O, d_okind, d_Operm, d_Olev, h->d_perm, h->d_rowptr,
+                              h->d_col, h->d_valB, h->d_valD, h->d_mu, d_Gw, d_ws, maxrow, d_ocnt, d_ocol, d_oB, d_oC,
+                              d_o2i);
+  HK_COUNT_LAUNCH();
+  HK_LAUNCH_CHECK();
+
+  // ---- FP32 dense stage
   k_schur<<<ns, 256, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lrow, h->d_lcntI, h->d_lcntG, h->d_lcol,
-                              h->d_lvalB, d_W, d_Gw, d_Rw, d_ring, d_ws, h->d_status); HK_COUNT_LAUNCH();
+                              h->d_lvalB, d_W, d_Gw, d_Rw, d_ring, d_ws, h->d_status);
+  HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   HK_TRY(check_device_status(h, "eigen: Gamma elimination"));
-  k_stdform<<<ns, 512, 0, st>>>(h->d_sub_info, h->d_sub_off, d_bw, h->d_I, h->d_mu, h->d_lrow, h->d_lcntI,
-                                h->d_lcol, h->d_lvalD, d_W, d_T, d_L, d_ws, h->d_status); HK_COUNT_LAUNCH();
+  k_stdform32<<<ns, 512, 0, st>>>(h->d_sub_info, h->d_sub_off, d_bw, h->d_I, h->d_mu, h->d_lrow, h->d_lcntI,
+                                  h->d_lcol, h->d_lvalD, d_W, d_L, d_A, d_L32, d_ws, d_ws32, h->d_status);
+  HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   HK_TRY(check_device_status(h, "eigen: standard form"));
-  size_t shm = sizeof(double) * 2 * (size_t)maxn;
-  HK_CUDA(cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  size_t shm = sizeof(float) * 2 * (size_t)((maxn + 3) & ~3);
+  HK_CUDA(cudaFuncSetAttribute(k_tridiag32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, st);
-  k_tridiag<<<ns, 1024, shm, st>>>(h->d_sub_info, d_W, d_ws, d_d, d_e, d_tau, d_voff); HK_COUNT_LAUNCH();
+  k_tridiag32<<<ns, 1024, shm, st>>>(h->d_sub_info, d_A, d_ws32, d_d, d_e, d_tau, d_voff);
+  HK_COUNT_LAUNCH();
   cudaEventRecord(e1, st);
   HK_LAUNCH_CHECK();
-  k_bisect<<<ns, 64, 0, st>>>(h->d_sub_info, d_d, d_e, d_voff, h->p.tau, h->d_lam, d_m, h->d_status); HK_COUNT_LAUNCH();
+  k_candidates<<<ns, 128, 0, st>>>(h->d_sub_info, d_d, d_e, d_voff, h->p.tau, d_lamhat, d_cnt, h->d_status);
+  HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
-  HK_TRY(check_device_status(h, "eigen: bisection"));
-  std::vector<int> m(ns);
-  HK_CUDA(cudaMemcpyAsync(m.data(), d_m, 4 * ns, cudaMemcpyDeviceToHost, st));
+  HK_TRY(check_device_status(h, "eigen: candidates"));
+  std::vector<int> cnt(ns);
+  std::vector<double> lamhat((size_t)ns * HK_MAXM);
+  HK_CUDA(cudaMemcpyAsync(cnt.data(), d_cnt, 4 * ns, cudaMemcpyDeviceToHost, st));
+  HK_CUDA(cudaMemcpyAsync(lamhat.data(), d_lamhat, sizeof(double) * lamhat.size(), cudaMemcpyDeviceToHost, st));
   HK_CUDA(cudaStreamSynchronize(st));
   {
     float ms = 0;
@@ -617,47 +1076,128 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
+  std::vector<long long> poff(ns), woff(ns);
+  long long ptot = 0, wtot = 0;
+  for (int s = 0; s < ns; ++s) {
+    poff[s] = ptot;
+    ptot += (long long)h->subs[s].nI * cnt[s];
+    woff[s] = wtot;
+    wtot += 5LL * h->subs[s].nI * std::max(1, std::min(cnt[s], 32));
+  }
+  float *d_Q = nullptr, *d_wk = nullptr;
+  double* d_P = nullptr;
+  long long *d_poff = nullptr, *d_woff = nullptr;
+  HK_TRY(dalloc(h, &d_Q, ptot));
+  HK_TRY(dalloc(h, &d_P, ptot));
+  HK_TRY(dalloc(h, &d_wk, wtot));
+  HK_TRY(dalloc(h, &d_poff, ns));
+  HK_TRY(dalloc(h, &d_woff, ns));
+  HK_CUDA(up(d_poff, poff.data(), 8 * ns));
+  HK_CUDA(up(d_woff, woff.data(), 8 * ns));
+  k_inviter32<<<ns, 32, 0, st>>>(h->d_sub_info, d_d, d_e, d_voff, d_lamhat, d_cnt, d_poff, d_Q, d_woff, d_wk);
+  HK_COUNT_LAUNCH();
+  k_backtransform32<<<ns, 256, 0, st>>>(h->d_sub_info, d_bw, h->d_I, h->d_mu, d_A, d_L32, d_ws32, d_tau, d_voff,
+                                        d_cnt, d_poff, d_Q, d_P);
+  HK_COUNT_LAUNCH();
+  HK_LAUNCH_CHECK();
+
+  // ---- FP64 refinement: clusters of candidates, one CTA each
+  std::vector<int> levO(O_total + ns);
+  HK_CUDA(cudaMemcpyAsync(levO.data(), d_Olevptr, sizeof(int) * levO.size(), cudaMemcpyDeviceToHost, st));
+  HK_CUDA(cudaStreamSynchronize(st));
+  std::vector<long long> fsize(ns, 0);
+  for (int s = 0; s < ns; ++s) {
+    const int* lp = &levO[o_off[s] + s];
+    for (int j = 0; j < OL[s]; ++j) {
+      long long b = lp[j + 1] - lp[j], bn = j + 1 < OL[s] ? lp[j + 2] - lp[j + 1] : 0;
+      fsize[s] += b * b + b * bn;
+    }
+  }
+  std::vector<int> items;
+  std::vector<double> sig;
+  std::vector<long long> foff, xoff;
+  long long ftot = 0, xtot = 0;
+  int pmax = 1;
+  for (int s = 0; s < ns; ++s) {
+    const double* lh = &lamhat[(size_t)s * HK_MAXM];
+    int c = std::min(cnt[s], HK_MAXM);
+    int t = 0;
+    while (t < c) {
+      int t1 = t + 1;
+      while (t1 < c && t1 - t < HK_MAX_CLUSTER &&
+             lh[t1] - lh[t1 - 1] <= HK_CLUSTER_GAP * std::max(1.0, std::fabs(lh[t1]))) ++t1;
+      double sm = 0;
+      for (int q = t; q < t1; ++q) sm += lh[q];
+      items.push_back(s); items.push_back(t); items.push_back(t1 - t); items.push_back(0);
+      sig.push_back(sm / (t1 - t));
+      foff.push_back(ftot);
+      ftot += fsize[s];
+      xoff.push_back(xtot);
+      xtot += 2LL * (t1 - t) * oc[s];
+      pmax = std::max(pmax, t1 - t);
+      t = t1;
+    }
+  }
+  int nit = (int)sig.size();
+  if (nit > 0) {
+    int* d_items = nullptr;
+    double *d_sig = nullptr, *d_F = nullptr, *d_X = nullptr;
+    long long *d_foff = nullptr, *d_xoff = nullptr;
+    HK_TRY(dalloc(h, &d_items, items.size()));
+    HK_TRY(dalloc(h, &d_sig, nit));
+    HK_TRY(dalloc(h, &d_foff, nit));
+    HK_TRY(dalloc(h, &d_xoff, nit));
+    HK_TRY(dalloc(h, &d_F, ftot));
+    HK_TRY(dalloc(h, &d_X, xtot));
+    HK_CUDA(up(d_items, items.data(), 4 * items.size()));
+    HK_CUDA(up(d_sig, sig.data(), 8 * nit));
+    HK_CUDA(up(d_foff, foff.data(), 8 * nit));
+    HK_CUDA(up(d_xoff, xoff.data(), 8 * nit));
+    size_t rshm = sizeof(double) * ((size_t)maxbO * maxbO + (size_t)maxbO * pmax);
+    HK_CUDA(cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rshm));
+    k_refine<<<nit, 256, rshm, st>>>(d_items, d_sig, h->d_sub_info, d_o_off, d_Olevptr, d_OL, maxrow, d_ocnt, d_ocol,
+                                     d_oB, d_oC, d_o2i, d_foff, d_xoff, d_F, d_X, d_poff, d_P, d_lamref, maxbO,
+                                     h->d_status);
+    HK_COUNT_LAUNCH();
+    HK_LAUNCH_CHECK();
+    HK_CUDA(cudaStreamSynchronize(st));
+    HK_TRY(check_device_status(h, "eigen: refinement"));
+    void* tmpf[] = {d_items, d_sig, d_foff, d_xoff, d_F, d_X};
+    for (void* p : tmpf) dfree(h, p);
+  }
+  int *d_sel = nullptr, *d_m = nullptr;
+  HK_TRY(dalloc(h, &d_sel, (size_t)ns * HK_MAXM));
+  HK_TRY(dalloc(h, &d_m, ns));
+  k_select<<<ns, 32, 0, st>>>(d_cnt, d_lamref, h->p.tau, d_sel, d_m, h->d_lam, h->d_status);
+  HK_COUNT_LAUNCH();
+  HK_LAUNCH_CHECK();
+  HK_TRY(check_device_status(h, "eigen: selection"));
+  std::vector<int> m(ns);
+  HK_CUDA(cudaMemcpyAsync(m.data(), d_m, 4 * ns, cudaMemcpyDeviceToHost, st));
+  HK_CUDA(cudaStreamSynchronize(st));
   int c0 = 0;
   long long zo = 0;
-  std::vector<long long> qoff(ns), woff(ns);
-  long long wtot = 0;
   for (int s = 0; s < ns; ++s) {
     Sub& u = h->subs[s];
     u.m = m[s];
     u.c_off = c0;
     u.z_off = zo;
-    qoff[s] = zo;
     c0 += u.m;
     zo += (long long)u.nI * u.m;
-    woff[s] = wtot;
-    wtot += 5LL * u.nI * (u.m < 32 ? (u.m > 0 ? u.m : 1) : 32);
   }
   h->n0 = c0;
   h->z_total = zo;
   HK_TRY(upload_sub_info(h));
   if (c0 > 0) {
-    double *d_Q = nullptr, *d_wk = nullptr;
-    long long *d_qoff = nullptr, *d_woff = nullptr;
-    HK_TRY(dalloc(h, &d_Q, zo));
-    HK_TRY(dalloc(h, &d_wk, wtot));
-    HK_TRY(dalloc(h, &d_qoff, ns));
-    HK_TRY(dalloc(h, &d_woff, ns));
     HK_TRY(dalloc(h, &h->d_Z64, zo));
-    HK_CUDA(cudaMemcpyAsync(d_qoff, qoff.data(), 8 * ns, cudaMemcpyHostToDevice, st));
-    HK_CUDA(cudaMemcpyAsync(d_woff, woff.data(), 8 * ns, cudaMemcpyHostToDevice, st));
-    k_inviter<<<ns, 32, 0, st>>>(h->d_sub_info, d_d, d_e, d_voff, h->d_lam, d_qoff, d_Q, d_woff, d_wk); HK_COUNT_LAUNCH();
+    k_write_z<<<ns, 256, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_I, h->d_mu, d_sel, d_poff, d_P, h->d_Z64);
+    HK_COUNT_LAUNCH();
     HK_LAUNCH_CHECK();
-    k_backtransform<<<ns, 256, 0, st>>>(h->d_sub_info, h->d_sub_off, d_bw, d_W, d_L, d_ws, d_tau, d_voff, d_qoff,
-                                        d_Q, h->d_Z64); HK_COUNT_LAUNCH();
-    HK_LAUNCH_CHECK();
-    HK_CUDA(cudaStreamSynchronize(st));
-    dfree(h, d_Q);
-    dfree(h, d_wk);
-    dfree(h, d_qoff);
-    dfree(h, d_woff);
   }
   HK_CUDA(cudaStreamSynchronize(st));
-  void* tmp[] = {d_ws, d_W, d_T, d_L, d_Gw, d_Rw, d_voff, d_bw, d_ring, d_m, d_d, d_e, d_tau};
+  void* tmp[] = {d_ws, d_ws32, d_W, d_L, d_Gw, d_Rw, d_A, d_L32, d_voff, d_bw, d_ring, d_cnt, d_o_off, d_d, d_e,
+                 d_tau, d_lamhat, d_lamref, d_O, d_okind, d_Operm, d_Olev, d_Olevptr, d_OL, d_ocnt, d_o2i, d_ocol,
+                 d_oB, d_oC, d_Q, d_P, d_wk, d_poff, d_woff, d_sel, d_m};
   for (void* p : tmp) dfree(h, p);
   return HK_OK;
 }

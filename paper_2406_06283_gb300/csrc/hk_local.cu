@@ -30,73 +30,6 @@ long long factor_elems(const int* lp, int L) {
   return t;
 }
 
-// In-place Gauss-Jordan inverse of the b x b row-major matrix A (shared
-// memory) with partial pivoting; returns through *minpiv the smallest |pivot|.
-__device__ void gauss_jordan_inverse(double* A, int b, int* piv, double* red_v, int* red_i, double* minpiv) {
-  int tid = threadIdx.x, T = blockDim.x;
-  for (int k = 0; k < b; ++k) {
-    // pivot search in column k, rows k..b-1 (ties -> smallest row)
-    double best = -1.0;
-    int bi = k;
-    for (int i = k + tid; i < b; i += T) {
-      double v = fabs(A[i * b + k]);
-      if (v > best) { best = v; bi = i; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_xor_sync(0xffffffffu, best, o);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      double bv = red_v[0];
-      int bj = red_i[0];
-      for (int w = 1; w < (T >> 5); ++w)
-        if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bj)) { bv = red_v[w]; bj = red_i[w]; }
-      piv[k] = bj;
-      if (bv < *minpiv) *minpiv = bv;
-    }
-    __syncthreads();
-    int p = piv[k];
-    if (p != k)
-      for (int c = tid; c < b; c += T) {
-        double t = A[k * b + c];
-        A[k * b + c] = A[p * b + c];
-        A[p * b + c] = t;
-      }
-    __syncthreads();
-    double pv = A[k * b + k];
-    double inv = pv != 0.0 ? 1.0 / pv : 0.0;
-    __syncthreads();
-    if (tid == 0) A[k * b + k] = 1.0;
-    __syncthreads();
-    for (int c = tid; c < b; c += T) A[k * b + c] *= inv;
-    __syncthreads();
-    // eliminate column k from every other row
-    for (int e = tid; e < b * b; e += T) {
-      int i = e / b, c = e % b;
-      if (i == k || c == k) continue;
-      A[i * b + c] -= A[i * b + k] * A[k * b + c];
-    }
-    __syncthreads();
-    for (int i = tid; i < b; i += T)
-      if (i != k) A[i * b + k] = -A[i * b + k] * A[k * b + k];
-    __syncthreads();
-  }
-  // undo the row interchanges as column interchanges, in reverse order
-  for (int k = b - 1; k >= 0; --k) {
-    int p = piv[k];
-    if (p != k)
-      for (int r = tid; r < b; r += T) {
-        double t = A[r * b + k];
-        A[r * b + k] = A[r * b + p];
-        A[r * b + p] = t;
-      }
-    __syncthreads();
-  }
-}
-
 __global__ void k_block_lu(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
                            const int* __restrict__ levptr, const int* __restrict__ lrow,
                            const int* __restrict__ lcntI, const int* __restrict__ lcol,
