@@ -10,19 +10,23 @@
 // whose eigenvalues are real (the paper's lemma on indefinite pencils).
 //
 // Two stages, because FP64 arithmetic on this GPU runs at 1/58 of FP32:
-//  1. FP32 dense stage (candidates).  With D_II = L L^T (banded, level order) the standard form is
-//     A q = lambda q, A = L^{-1} (mu S mu) L^{-T}, p = X^{-1} L^{-T} q.  A is reduced to tridiagonal
-//     form by Householder reflections in FP32; Sturm-count bisection finds every eigenvalue below
-//     tau + delta (delta = 0.05, far above the FP32 error of these eigenvalues), FP32 inverse iteration
-//     on the tridiagonal matrix and the back-transform give approximate eigenvectors p.
+//  1. FP32 dense stage (eigenvalue candidates).  With D_II = L L^T (banded, level order) the standard
+//     form is A q = lambda q, A = L^{-1} (mu S mu) L^{-T}.  A is reduced to tridiagonal form by
+//     Householder reflections in FP32, and 32-way multisection on Sturm counts finds every eigenvalue
+//     below tau + delta (delta = 0.05, far above the FP32 error of these eigenvalues).
 //  2. FP64 refinement on the sparse pencil.  Candidates closer than 1e-3 max(1,|lambda|) form a
 //     cluster; for each cluster the block-tridiagonal LU of B^N - sigma C over level sets of
-//     ovdof(Omega_i) is formed in FP64 (sigma = the cluster's mean candidate), the cluster's vectors
-//     take three steps of block inverse iteration ((B^N - sigma C)^{-1} C, C-orthonormalised after each
-//     step), and a Rayleigh-Ritz step on B^N gives the FP64 eigenpairs.  The Gamma part of each iterate
-//     satisfies the Gamma rows of the pencil exactly, so x^T B^N x = x_I^T S x_I.
+//     ovdof(Omega_i) is formed in FP64 (sigma = the cluster's mean candidate), a seeded block of
+//     cluster size + 2 guard vectors takes five steps of block inverse iteration
+//     ((B^N - sigma C)^{-1} C, C-orthonormalised after each step; the contraction per step is
+//     |lambda - sigma| over the distance to the next eigenvalue outside the block), and a Rayleigh-Ritz
+//     step on B^N gives FP64 eigenpairs; the window of Ritz values closest to the cluster's candidates
+//     is kept.  The Gamma part of each iterate satisfies the Gamma rows of the pencil exactly, so
+//     x^T B^N x = x_I^T S x_I.
 // Selection then keeps lambda < tau on the FP64 values, extending across ties (gap <= 1e-8 max(1,|tau|)),
 // and the coarse vectors are Xi p = p / mu on dof(Omega_i), c-normalised (Def. 5.1).
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 
@@ -33,7 +37,9 @@ static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 #define HK_EIG_DELTA 0.05
 #define HK_CLUSTER_GAP 1e-3
 #define HK_MAX_CLUSTER 32
-#define HK_REFINE_STEPS 3
+#define HK_REFINE_STEPS 5
+#define HK_GUARD 2
+#define HK_MAX_BLOCK (HK_MAX_CLUSTER + HK_GUARD)
 
 // ---- 1. B^N on Gamma x Gamma: element sums over the subdomain's elements.
 __global__ void k_gamma_block(int dim, int ne, const double* __restrict__ xyz, const int* __restrict__ elems,
@@ -228,18 +234,52 @@ __global__ void k_stdform32(const int* __restrict__ sub_info, const long long* _
           c < nI ? (float)(W[(long long)a * nI + c] * ma * (double)mu[Ilev[off + c]]) : 0.f;
   }
   __syncthreads();
+  // column-parallel forward substitution M <- L^{-1} M; each thread keeps the last bw+1 solved
+  // entries of its own column in a shared-memory ring (ring[slot * T + tid])
+  extern __shared__ float ring[];
+  int R = bw + 1;
   for (int pass = 0; pass < 2; ++pass) {
     float* M = pass == 0 ? A : Tm;
-    for (int c = tid; c < nI; c += T) {
-      for (int a = 0; a < nI; ++a) {
+    for (int c0 = 0; c0 < nI; c0 += T) {
+      int c = c0 + tid;
+      bool act = c < nI;
+      int wslot = 0;  // a % R, carried along
+      for (int a = 0; a < nI && act; ++a) {
         float v = M[(long long)a * lda + c];
         int k0 = max(0, a - bw);
         const float* la = L32 + (long long)a * ld + (k0 - a + bw);
-        for (int k = k0; k < a; ++k) v -= la[k - k0] * M[(long long)k * lda + c];
-        M[(long long)a * lda + c] = v / L32[(long long)a * ld + bw];
+        int slot = wslot - (a - k0);  // k0 % R
+        if (slot < 0) slot += R;
+        int len = a - k0, seg = min(len, R - slot);  // [slot, R) then [0, len - seg)
+        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+        const float* r1 = ring + (long long)slot * T + tid;
+        int q = 0;
+        for (; q + 4 <= seg; q += 4) {
+          acc0 += la[q] * r1[(long long)q * T];
+          acc1 += la[q + 1] * r1[(long long)(q + 1) * T];
+          acc2 += la[q + 2] * r1[(long long)(q + 2) * T];
+          acc3 += la[q + 3] * r1[(long long)(q + 3) * T];
+        }
+        for (; q < seg; ++q) acc0 += la[q] * r1[(long long)q * T];
+        const float* la2 = la + seg;
+        const float* r2 = ring + tid;
+        int rest = len - seg;
+        q = 0;
+        for (; q + 4 <= rest; q += 4) {
+          acc0 += la2[q] * r2[(long long)q * T];
+          acc1 += la2[q + 1] * r2[(long long)(q + 1) * T];
+          acc2 += la2[q + 2] * r2[(long long)(q + 2) * T];
+          acc3 += la2[q + 3] * r2[(long long)(q + 3) * T];
+        }
+        for (; q < rest; ++q) acc0 += la2[q] * r2[(long long)q * T];
+        v -= (acc0 + acc1) + (acc2 + acc3);
+        v /= L32[(long long)a * ld + bw];
+        ring[wslot * T + tid] = v;
+        M[(long long)a * lda + c] = v;
+        if (++wslot == R) wslot = 0;
       }
+      __syncthreads();
     }
-    __syncthreads();
     if (pass == 0) {
       for (int c = warp; c < nI; c += nw)
         for (int a = lane; a < nI; a += 32) Tm[(long long)c * lda + a] = A[(long long)a * lda + c];
@@ -252,306 +292,204 @@ __global__ void k_stdform32(const int* __restrict__ sub_info, const long long* _
 }
 
 // ---- 4. Householder tridiagonalisation of the dense symmetric A (full storage, row stride lda = n
-// rounded up to 4), FP32 arithmetic, O(n) reductions in FP64.  Reflector k: H_k = I - tau_k v v^T,
-// v[k+1] = 1, v[j] stored in A[k][j] (j >= k+2).  d = diagonal, e = off-diagonal.  The shared vectors
-// v and p are kept zero below the active column and in the padding, so every row loop starts on a
-// 16-byte boundary and moves float4 (entries left of the active column change by exactly zero).
-__global__ void __launch_bounds__(1024) k_tridiag32(const int* __restrict__ sub_info, const long long* __restrict__ wsA,
-                                                    float* ws, double* dvec, double* evec, float* tauv,
-                                                    const int* __restrict__ vec_off) {
+// rounded up to 4) in FP32, O(n) reductions in FP64; only the tridiagonal (d, e) is kept.
+// Step k forms the reflector H_k = I - tau v v^T (v[k+1] = 1) from row k, then needs p = tau A22 v and
+// w = p - (tau/2)(p.v) v for the rank-2 update A22 -= v w^T + w v^T.  The update of step k-1 and the
+// product of step k share one pass: each row i > k is read once, the pending update (v', w') of step
+// k-1 is applied and written back, and its dot with the new v accumulated.  Row k itself takes the
+// pending update in a shared-memory copy.
+// The CS CTAs of a thread-block cluster share one matrix: CTA r owns the rows i = r (mod CS), every
+// CTA rebuilds row k and the reflector redundantly (same arithmetic, same result), and the entries of
+// p are exchanged through distributed shared memory after one cluster barrier per step.  Shared
+// vectors are zero below the active column and in the padding, so row loops start on a 16-byte
+// boundary and move float4.
+template <int CS>
+__global__ void __launch_bounds__(1024) k_tridiag32(const int* __restrict__ sub_info,
+                                                    const long long* __restrict__ wsA, float* ws, double* dvec,
+                                                    double* evec, const int* __restrict__ vec_off) {
   extern __shared__ __align__(16) float smf[];
   __shared__ double red[32];
-  int s = blockIdx.x, tid = threadIdx.x, Tn = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = Tn >> 5;
+  int s = blockIdx.x / CS, r = blockIdx.x % CS;
+  int tid = threadIdx.x, Tn = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = Tn >> 5;
   int n = sub_info[8 * s];
   int lda = (n + 3) & ~3, l4 = lda >> 2;
   float* A = ws + wsA[s];
   double* d = dvec + vec_off[s];
   double* e = evec + vec_off[s];
-  float* tv = tauv + vec_off[s];
-  float* v = smf;        // lda
-  float* p = smf + lda;  // lda
-  const float4* v4 = reinterpret_cast<const float4*>(v);
-  const float4* p4 = reinterpret_cast<const float4*>(p);
-  for (int j = tid; j < 2 * lda; j += Tn) smf[j] = 0.f;
-  __syncthreads();
+  float* vo = smf;            // v of the pending update
+  float* wo = vo + lda;       // w of the pending update
+  float* vn = wo + lda;       // v of the current step
+  float* pb = vn + lda;       // p, double buffered (2 * lda)
+  float* rowk = pb + 2 * lda; // row k with the pending update applied
+  const float4* vo4 = reinterpret_cast<const float4*>(vo);
+  const float4* wo4 = reinterpret_cast<const float4*>(wo);
+  const float4* vn4 = reinterpret_cast<const float4*>(vn);
+  for (int j = tid; j < 6 * lda; j += Tn) smf[j] = 0.f;
+  if (CS > 1) cooperative_groups::this_cluster().sync(); else __syncthreads();
   for (int k = 0; k < n - 2; ++k) {
-    float* rk = A + (long long)k * lda;
-    double alpha = (double)rk[k + 1];
+    // row k, brought up to date
+    const float* gk = A + (long long)k * lda;
+    float vk = vo[k], wk = wo[k];
+    for (int j = k + tid; j < n; j += Tn) rowk[j] = gk[j] - (vk * wo[j] + wk * vo[j]);
+    __syncthreads();
+    double alpha = (double)rowk[k + 1];
     double xs = 0;
-    for (int j = k + 2 + tid; j < n; j += Tn) xs += (double)rk[j] * (double)rk[j];
+    for (int j = k + 2 + tid; j < n; j += Tn) xs += (double)rowk[j] * (double)rowk[j];
     xs = block_sum(xs, red);
-    double tau = 0, beta = alpha;
+    double tau = 0, beta = alpha, scale = 0;
     if (xs > 0.0) {
       beta = -copysign(sqrt(alpha * alpha + xs), alpha);
       tau = (beta - alpha) / beta;
-      double scale = 1.0 / (alpha - beta);
-      for (int j = k + 2 + tid; j < n; j += Tn) {
-        float vj = (float)((double)rk[j] * scale);
-        rk[j] = vj;
-        v[j] = vj;
-      }
-    } else {
-      for (int j = k + 2 + tid; j < n; j += Tn) v[j] = rk[j];
+      scale = 1.0 / (alpha - beta);
     }
+    for (int j = k + 2 + tid; j < n; j += Tn) vn[j] = (float)((double)rowk[j] * scale);
     if (tid == 0) {
-      v[k] = 0.f;
-      p[k] = 0.f;
-      v[k + 1] = 1.f;
-      d[k] = (double)rk[k];
-      e[k] = beta;
-      tv[k] = (float)tau;
+      vn[k] = 0.f;
+      vn[k + 1] = xs > 0.0 ? 1.f : 0.f;
+      if (r == 0) {
+        d[k] = (double)rowk[k];
+        e[k] = beta;
+      }
     }
     __syncthreads();
-    if (tau == 0.0) continue;
+    // fused pass over the owned rows i > k
     float tauf = (float)tau;
+    float* pc = pb + (k & 1) * lda;
     int c0 = (k + 1) >> 2;
-    for (int i = k + 1 + warp; i < n; i += nw) {
-      const float4* ri = reinterpret_cast<const float4*>(A + (long long)i * lda);
+    int i0 = k + 1 + (((r - (k + 1)) % CS) + CS) % CS;
+    for (int i = i0 + CS * warp; i < n; i += CS * nw) {
+      float4* ri = reinterpret_cast<float4*>(A + (long long)i * lda);
+      float vi = vo[i], wi = wo[i];
       float acc = 0.f;
 #pragma unroll 4
       for (int c = c0 + lane; c < l4; c += 32) {
-        float4 a = ri[c], b = v4[c];
-        acc += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+        float4 a = ri[c], vv = vo4[c], ww = wo4[c], nv = vn4[c];
+        a.x -= vi * ww.x + wi * vv.x;
+        a.y -= vi * ww.y + wi * vv.y;
+        a.z -= vi * ww.z + wi * vv.z;
+        a.w -= vi * ww.w + wi * vv.w;
+        ri[c] = a;
+        acc += a.x * nv.x + a.y * nv.y + a.z * nv.z + a.w * nv.w;
       }
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) p[i] = tauf * acc;
+      if (lane == 0) pc[i] = tauf * acc;
+    }
+    if (CS > 1) {
+      cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+      cl.sync();  // owners' rows and p entries are complete and visible
+      for (int i = k + 1 + tid; i < n; i += Tn) {
+        int owner = i % CS;
+        if (owner != r) pc[i] = *cl.map_shared_rank(pc + i, owner);
+      }
     }
     __syncthreads();
     double pv = 0;
-    for (int j = k + 1 + tid; j < n; j += Tn) pv += (double)p[j] * (double)v[j];
+    for (int j = k + 1 + tid; j < n; j += Tn) pv += (double)pc[j] * (double)vn[j];
     pv = block_sum(pv, red);
     float K = (float)(0.5 * tau * pv);
-    for (int j = k + 1 + tid; j < n; j += Tn) p[j] -= K * v[j];  // p becomes w
-    __syncthreads();
-    for (int i = k + 1 + warp; i < n; i += nw) {
-      float4* ri = reinterpret_cast<float4*>(A + (long long)i * lda);
-      float vi = v[i], pi = p[i];
-#pragma unroll 4
-      for (int c = c0 + lane; c < l4; c += 32) {
-        float4 a = ri[c], pv4 = p4[c], vv4 = v4[c];
-        a.x -= vi * pv4.x + pi * vv4.x;
-        a.y -= vi * pv4.y + pi * vv4.y;
-        a.z -= vi * pv4.z + pi * vv4.z;
-        a.w -= vi * pv4.w + pi * vv4.w;
-        ri[c] = a;
-      }
+    for (int j = tid; j < lda; j += Tn) {
+      float vj = j > k ? vn[j] : 0.f;
+      vo[j] = vj;
+      wo[j] = j > k ? pc[j] - K * vj : 0.f;
     }
     __syncthreads();
   }
-  if (tid == 0) {
+  if (CS > 1) cooperative_groups::this_cluster().sync(); else __syncthreads();
+  if (r == 0 && tid == 0 && n >= 1) {
     if (n >= 2) {
-      d[n - 2] = (double)A[(long long)(n - 2) * lda + n - 2];
-      e[n - 2] = (double)A[(long long)(n - 1) * lda + n - 2];
-      tv[n - 2] = 0.f;
+      int a2 = n - 2, a3 = n - 1;
+      float x22 = A[(long long)a2 * lda + a2] - 2.f * vo[a2] * wo[a2];
+      float x32 = A[(long long)a3 * lda + a2] - (vo[a3] * wo[a2] + wo[a3] * vo[a2]);
+      float x33 = A[(long long)a3 * lda + a3] - 2.f * vo[a3] * wo[a3];
+      d[a2] = (double)x22;
+      e[a2] = (double)x32;
+      d[a3] = (double)x33;
+    } else {
+      d[0] = (double)A[0];
     }
-    d[n - 1] = (double)A[(long long)(n - 1) * lda + n - 1];
   }
 }
 
-__device__ int sturm_count(const double* d, const double* e, int n, double x, double pivmin) {
+// Sturm count (number of eigenvalues below x) of the symmetric tridiagonal matrix (d, e), FP32.
+__device__ __forceinline__ int sturm_count32(const float* d, const float* e2, int n, float x, float pivmin) {
   int c = 0;
-  double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  if (q < 0) ++c;
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  c += q < 0.f;
   for (int i = 1; i < n; ++i) {
-    q = d[i] - x - e[i - 1] * e[i - 1] / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    if (q < 0) ++c;
+    q = d[i] - x - e2[i - 1] / q;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    c += q < 0.f;
   }
   return c;
 }
 
-// ---- 5. candidates: every eigenvalue of the tridiagonal matrix below tau + delta, by bisection
-// to 1e-7 of the spectral scale (the FP32 matrix is no more accurate than that).
+// ---- 5. candidates: every eigenvalue of the tridiagonal matrix below tau + delta.  The FP32
+// tridiagonal matrix sits in shared memory; each warp refines one eigenvalue by 32-way multisection
+// (its lanes count at 32 points of the current bracket) down to 1e-6 of the spectral scale.
 __global__ void k_candidates(const int* __restrict__ sub_info, const double* __restrict__ dvec,
                              const double* __restrict__ evec, const int* __restrict__ vec_off, double tau,
                              double* lam_hat, int* cnt_out, DevStatus* st) {
-  __shared__ double lo_s, hi_s, pm_s;
+  extern __shared__ float smc[];
+  __shared__ float lo_s, hi_s, pm_s;
   __shared__ int cnt_s;
-  int s = blockIdx.x, tid = threadIdx.x;
+  int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   int n = sub_info[8 * s];
-  const double* d = dvec + vec_off[s];
-  const double* e = evec + vec_off[s];
+  float* d = smc;
+  float* e2 = smc + n;
+  const double* dg = dvec + vec_off[s];
+  const double* eg = evec + vec_off[s];
+  for (int i = tid; i < n; i += blockDim.x) {
+    d[i] = (float)dg[i];
+    e2[i] = i < n - 1 ? (float)(eg[i] * eg[i]) : 0.f;
+  }
+  __syncthreads();
   if (tid == 0) {
     double lo = 1e300, hi = -1e300, me = 0;
     for (int i = 0; i < n; ++i) {
-      double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
-      lo = fmin(lo, d[i] - r);
-      hi = fmax(hi, d[i] + r);
-      if (i < n - 1) me = fmax(me, e[i] * e[i]);
+      double r = (i > 0 ? fabs(eg[i - 1]) : 0.0) + (i < n - 1 ? fabs(eg[i]) : 0.0);
+      lo = fmin(lo, dg[i] - r);
+      hi = fmax(hi, dg[i] + r);
+      if (i < n - 1) me = fmax(me, eg[i] * eg[i]);
     }
     double span = fmax(fabs(lo), fabs(hi));
-    lo -= 1e-12 * span + 1e-300;
-    hi += 1e-12 * span + 1e-300;
-    lo_s = lo;
-    hi_s = hi;
-    pm_s = 1e-290 * fmax(1.0, me);
-    double x = tau + HK_EIG_DELTA;
-    int c = x >= hi ? n : (x <= lo ? 0 : sturm_count(d, e, n, x, pm_s));
+    lo -= 1e-6 * span + 1e-30;
+    hi += 1e-6 * span + 1e-30;
+    lo_s = (float)lo;
+    hi_s = (float)hi;
+    pm_s = (float)(1e-30 * fmax(1.0, me));
+    float x = (float)(tau + HK_EIG_DELTA);
+    int c = x >= hi_s ? n : (x <= lo_s ? 0 : sturm_count32(d, e2, n, x, pm_s));
     cnt_s = c;
     cnt_out[s] = c;
     if (c > HK_MAXM) dev_fail(st, HK_UNSUPPORTED, s, c);
   }
   __syncthreads();
   int c = min(cnt_s, HK_MAXM);
-  double tol = 1e-7 * fmax(fabs(lo_s), fabs(hi_s));
-  for (int t = tid; t < c; t += blockDim.x) {
-    double lo = lo_s, hi = hi_s;
-    for (int it = 0; it < 100 && hi - lo > tol; ++it) {
-      double mid = 0.5 * (lo + hi);
-      if (sturm_count(d, e, n, mid, pm_s) > t) hi = mid; else lo = mid;
+  float tol = 1e-6f * fmaxf(fabsf(lo_s), fabsf(hi_s));
+  for (int t = warp; t < c; t += nw) {
+    float lo = lo_s, hi = hi_s;
+    for (int it = 0; it < 12 && hi - lo > tol; ++it) {
+      float x = lo + (hi - lo) * (float)(lane + 1) / 33.f;
+      int below = sturm_count32(d, e2, n, x, pm_s) > t;  // eigenvalue t lies below x
+      unsigned mask = __ballot_sync(0xffffffffu, below);
+      int first = mask ? __ffs(mask) - 1 : 32;          // lowest point above eigenvalue t
+      float nlo = first == 0 ? lo : lo + (hi - lo) * (float)first / 33.f;
+      float nhi = first == 32 ? hi : lo + (hi - lo) * (float)(first + 1) / 33.f;
+      lo = nlo;
+      hi = nhi;
     }
-    lam_hat[(long long)s * HK_MAXM + t] = 0.5 * (lo + hi);
+    if (lane == 0) lam_hat[(long long)s * HK_MAXM + t] = 0.5 * ((double)lo + (double)hi);
   }
 }
 
-// ---- 6. FP32 inverse iteration on the tridiagonal matrix for the candidates (one thread per group of
-// candidates closer than 1e-3 of the scale, reorthogonalised inside the group), tridiagonal LU with
-// partial pivoting.  Output: candidate-major vectors Q (c x n).
+// Deterministic start vectors for the refinement: SplitMix64 finaliser of a key, mapped to [-0.5, 0.5).
 __device__ float hash_unitf(unsigned long long x) {
   x += 0x9E3779B97F4A7C15ULL;
   x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
   x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
   x ^= x >> 31;
   return (float)((double)(x >> 11) * (1.0 / 9007199254740992.0) - 0.5);
-}
-
-__global__ void k_inviter32(const int* __restrict__ sub_info, const double* __restrict__ dvec,
-                            const double* __restrict__ evec, const int* __restrict__ vec_off,
-                            const double* __restrict__ lam_hat, const int* __restrict__ cnt,
-                            const long long* __restrict__ qoff, float* Q, const long long* __restrict__ woff,
-                            float* wk) {
-  int s = blockIdx.x;
-  int n = sub_info[8 * s], m = min(cnt[s], HK_MAXM);
-  const double* d = dvec + vec_off[s];
-  const double* e = evec + vec_off[s];
-  const double* lam = lam_hat + (long long)s * HK_MAXM;
-  float* Qs = Q + qoff[s];
-  double tnorm = 0;
-  for (int i = 0; i < n; ++i)
-    tnorm = fmax(tnorm, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0));
-  double ortol = 1e-3 * tnorm;
-  float epsf = 1.2e-7f;
-  int gcount = 0;
-  for (int l = 0; l < m; ++l) {
-    bool start = l == 0 || lam[l] - lam[l - 1] > ortol;
-    if (!start) continue;
-    if (gcount++ % blockDim.x != threadIdx.x) continue;
-    int l1 = l + 1;
-    while (l1 < m && lam[l1] - lam[l1 - 1] <= ortol) ++l1;
-    float* dd = wk + woff[s] + (long long)threadIdx.x * 5 * n;
-    float* du = dd + n;
-    float* du2 = du + n;
-    float* dl = du2 + n;
-    float* x = dl + n;
-    double prev = -1e300;
-    for (int t = l; t < l1; ++t) {
-      double lt = lam[t];
-      if (lt - prev < 1e-6 * fmax(1.0, fabs(lt))) lt = prev + 1e-6 * fmax(1.0, fabs(prev));
-      prev = lt;
-      for (int i = 0; i < n; ++i) {
-        dd[i] = (float)(d[i] - lt);
-        du[i] = i < n - 1 ? (float)e[i] : 0.f;
-        dl[i] = i < n - 1 ? (float)e[i] : 0.f;
-        du2[i] = 0.f;
-      }
-      for (int i = 0; i < n - 1; ++i) {
-        if (fabsf(dd[i]) >= fabsf(dl[i])) {
-          if (dd[i] == 0.f) dd[i] = epsf * (float)tnorm;
-          float f = dl[i] / dd[i];
-          dl[i] = f;
-          dd[i + 1] -= f * du[i];
-          du2[i] = 0.f;
-          x[i] = 0.f;
-        } else {
-          float f = dd[i] / dl[i];
-          dd[i] = dl[i];
-          dl[i] = f;
-          float tmp = du[i];
-          du[i] = dd[i + 1];
-          dd[i + 1] = tmp - f * dd[i + 1];
-          if (i < n - 2) {
-            du2[i] = du[i + 1];
-            du[i + 1] = -f * du[i + 1];
-          }
-          x[i] = 1.f;
-        }
-      }
-      if (dd[n - 1] == 0.f) dd[n - 1] = epsf * (float)tnorm;
-      float* y = Qs + (long long)t * n;
-      for (int i = 0; i < n; ++i) y[i] = hash_unitf(((unsigned long long)s << 32) ^ ((unsigned long long)t << 20) ^ i);
-      for (int it = 0; it < 3; ++it) {
-        for (int i = 0; i < n - 1; ++i) {
-          if (x[i] == 0.f) {
-            y[i + 1] -= dl[i] * y[i];
-          } else {
-            float tmp = y[i];
-            y[i] = y[i + 1];
-            y[i + 1] = tmp - dl[i] * y[i];
-          }
-        }
-        y[n - 1] /= dd[n - 1];
-        if (n > 1) y[n - 2] = (y[n - 2] - du[n - 2] * y[n - 1]) / dd[n - 2];
-        for (int i = n - 3; i >= 0; --i) y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) / dd[i];
-        for (int rep = 0; rep < 2; ++rep)
-          for (int u = l; u < t; ++u) {
-            const float* yu = Qs + (long long)u * n;
-            double dot = 0;
-            for (int i = 0; i < n; ++i) dot += (double)yu[i] * (double)y[i];
-            for (int i = 0; i < n; ++i) y[i] -= (float)dot * yu[i];
-          }
-        double nrm = 0;
-        for (int i = 0; i < n; ++i) nrm += (double)y[i] * (double)y[i];
-        float inv = (float)(1.0 / sqrt(nrm));
-        for (int i = 0; i < n; ++i) y[i] *= inv;
-      }
-    }
-  }
-}
-
-// ---- 7. FP32 back-transform q = H_0 ... H_{n-3} y, then p = mu (L^{-T} q), written in FP64
-// (candidate-major, level order of dof).
-__global__ void k_backtransform32(const int* __restrict__ sub_info, const int* __restrict__ bw_arr,
-                                  const int* __restrict__ Ilev, const int* __restrict__ mu,
-                                  const long long* __restrict__ wsA, const long long* __restrict__ wsL32,
-                                  const float* __restrict__ ws32, const float* __restrict__ tauv,
-                                  const int* __restrict__ vec_off, const int* __restrict__ cnt,
-                                  const long long* __restrict__ qoff, float* Q, double* P) {
-  int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int* si = sub_info + 8 * s;
-  int n = si[0], off = si[3], m = min(cnt[s], HK_MAXM);
-  int bw = bw_arr[s], ld = bw + 1;
-  const float* A = ws32 + wsA[s];
-  const float* Lb = ws32 + wsL32[s];
-  const float* tv = tauv + vec_off[s];
-  float* Qs = Q + qoff[s];
-  double* Ps = P + qoff[s];
-  for (int k = n - 3; k >= 0; --k) {
-    float tau = tv[k];
-    if (tau == 0.f) continue;
-    const float* rk = A + (long long)k * ((n + 3) & ~3);
-    for (int l = warp; l < m; l += nw) {
-      float* q = Qs + (long long)l * n;
-      float acc = lane == 0 ? q[k + 1] : 0.f;
-      for (int j = k + 2 + lane; j < n; j += 32) acc += rk[j] * q[j];
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      acc *= tau;
-      if (lane == 0) q[k + 1] -= acc;
-      for (int j = k + 2 + lane; j < n; j += 32) q[j] -= acc * rk[j];
-    }
-    __syncthreads();
-  }
-  for (int l = tid; l < m; l += blockDim.x) {
-    float* q = Qs + (long long)l * n;
-    for (int a = n - 1; a >= 0; --a) {
-      float v = q[a];
-      int cend = min(n - 1, a + bw);
-      for (int c = a + 1; c <= cend; ++c) v -= Lb[(long long)c * ld + (a - c + bw)] * q[c];
-      q[a] = v / Lb[(long long)a * ld + bw];
-    }
-    double* p = Ps + (long long)l * n;
-    for (int a = 0; a < n; ++a) p[a] = (double)q[a] * (double)mu[Ilev[off + a]];
-  }
 }
 
 // ---- 8. ovdof(Omega_i) = dof U Gamma: merged sorted list, membership and index in dof / Gamma.
@@ -700,16 +638,18 @@ __global__ void k_refine(const int* __restrict__ items, const double* __restrict
                          const int* __restrict__ ocnt, const int* __restrict__ ocol, const double* __restrict__ oB,
                          const double* __restrict__ oC, const int* __restrict__ o2i,
                          const long long* __restrict__ f_off, const long long* __restrict__ x_off, double* F,
-                         double* Xw, const long long* __restrict__ poff, double* P, double* lam_ref, int max_b,
-                         DevStatus* st) {
+                         double* Xw, const long long* __restrict__ poff, double* P, const double* __restrict__ lam_hat,
+                         double* lam_ref, int max_b, DevStatus* st) {
   extern __shared__ double smem[];
   __shared__ int piv[HK_MAXB];
   __shared__ double red_v[32];
   __shared__ int red_i[32];
   __shared__ double minpiv, sh_val;
-  __shared__ double Hs[HK_MAX_CLUSTER * HK_MAX_CLUSTER], Us[HK_MAX_CLUSTER * HK_MAX_CLUSTER], ws_[HK_MAX_CLUSTER];
+  __shared__ double Hs[HK_MAX_BLOCK * HK_MAX_BLOCK], Us[HK_MAX_BLOCK * HK_MAX_BLOCK], ws_[HK_MAX_BLOCK];
+  __shared__ int win_s;
   int it = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
-  int s = items[4 * it], t0 = items[4 * it + 1], p = items[4 * it + 2];
+  int s = items[4 * it], t0 = items[4 * it + 1], pc = items[4 * it + 2];
+  int p = pc + HK_GUARD;  // block: cluster + guard vectors
   double sigma = sigmas[it];
   const int* si = sub_info + 8 * s;
   int nI = si[0], nG = si[1];
@@ -779,11 +719,12 @@ __global__ void k_refine(const int* __restrict__ items, const double* __restrict
     prev_r0 = r0;
     bo = go + (long long)b * bn;
   }
-  // 2. start block: the FP32 candidates, zero on Gamma
+  // 2. seeded start block on dof, zero on Gamma
   for (int t = 0; t < p; ++t)
     for (int a = tid; a < nO; a += T) {
       int ia = o2i[oo + a];
-      X[(long long)t * nO + a] = ia >= 0 ? Ps[(long long)(t0 + t) * nI + ia] : 0.0;
+      unsigned long long key = ((unsigned long long)s << 40) ^ ((unsigned long long)(t0 * 64 + t) << 20) ^ a;
+      X[(long long)t * nO + a] = ia >= 0 ? (double)hash_unitf(key) : 0.0;
     }
   __syncthreads();
   for (int step = 0; step < HK_REFINE_STEPS; ++step) {
@@ -879,17 +820,30 @@ __global__ void k_refine(const int* __restrict__ items, const double* __restrict
         Hs[i * p + j] = Hs[j * p + i] = a;
       }
     jacobi_eig(Hs, Us, ws_, p);
-    for (int i = 0; i < p; ++i) lam_ref[(long long)s * HK_MAXM + t0 + i] = ws_[i];
+    // the window of pc consecutive Ritz values closest to the cluster's candidates
+    int best = 0;
+    double bestd = 1e300;
+    for (int w0 = 0; w0 + pc <= p; ++w0) {
+      double dsum = 0;
+      for (int i = 0; i < pc; ++i) dsum += fabs(ws_[w0 + i] - lam_hat[(long long)s * HK_MAXM + t0 + i]);
+      if (dsum < bestd) {
+        bestd = dsum;
+        best = w0;
+      }
+    }
+    win_s = best;
+    for (int i = 0; i < pc; ++i) lam_ref[(long long)s * HK_MAXM + t0 + i] = ws_[best + i];
     if (!(minpiv > 0)) dev_fail(st, HK_EIG_FAIL, s, minpiv);
   }
   __syncthreads();
-  // refined vectors X U, written back (dof part, level order) over the candidates
-  for (int i = 0; i < p; ++i)
+  // refined vectors X U (the selected window), written (dof part, level order) over the candidates
+  int w0 = win_s;
+  for (int i = 0; i < pc; ++i)
     for (int a = tid; a < nO; a += T) {
       int ia = o2i[oo + a];
       if (ia < 0) continue;
       double acc = 0;
-      for (int k = 0; k < p; ++k) acc += X[(long long)k * nO + a] * Us[k * p + i];
+      for (int k = 0; k < p; ++k) acc += X[(long long)k * nO + a] * Us[k * p + w0 + i];
       Ps[(long long)(t0 + i) * nI + ia] = acc;
     }
 }
@@ -1045,22 +999,62 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   HK_TRY(check_device_status(h, "eigen: Gamma elimination"));
-  k_stdform32<<<ns, 512, 0, st>>>(h->d_sub_info, h->d_sub_off, d_bw, h->d_I, h->d_mu, h->d_lrow, h->d_lcntI,
-                                  h->d_lcol, h->d_lvalD, d_W, d_L, d_A, d_L32, d_ws, d_ws32, h->d_status);
+  int maxbw = 0;
+  for (int s = 0; s < ns; ++s) maxbw = std::max(maxbw, bw[s]);
+  int sf_threads = 512;
+  while (sf_threads > 64 && sizeof(float) * (size_t)(maxbw + 1) * sf_threads > 200 * 1024) sf_threads >>= 1;
+  size_t sf_shm = sizeof(float) * (size_t)(maxbw + 1) * sf_threads;
+  if (sf_shm > 200 * 1024) {
+    hk_set_error("local band width %d too large for the standard-form kernel", maxbw);
+    return HK_UNSUPPORTED;
+  }
+  HK_CUDA(cudaFuncSetAttribute(k_stdform32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf_shm));
+  k_stdform32<<<ns, sf_threads, sf_shm, st>>>(h->d_sub_info, h->d_sub_off, d_bw, h->d_I, h->d_mu, h->d_lrow,
+                                              h->d_lcntI, h->d_lcol, h->d_lvalD, d_W, d_L, d_A, d_L32, d_ws, d_ws32,
+                                              h->d_status);
   HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   HK_TRY(check_device_status(h, "eigen: standard form"));
-  size_t shm = sizeof(float) * 2 * (size_t)((maxn + 3) & ~3);
-  HK_CUDA(cudaFuncSetAttribute(k_tridiag32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  size_t shm = sizeof(float) * 6 * (size_t)((maxn + 3) & ~3);
+  int CS = 1;
+  while (CS < 4 && (long long)ns * CS * 2 <= 152) CS *= 2;  // spread a few subdomains over more SMs
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, st);
-  k_tridiag32<<<ns, 1024, shm, st>>>(h->d_sub_info, d_A, d_ws32, d_d, d_e, d_tau, d_voff);
-  HK_COUNT_LAUNCH();
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ns * CS);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = shm;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (CS == 4) {
+      HK_CUDA(cudaFuncSetAttribute(k_tridiag32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      HK_CUDA(cudaLaunchKernelEx(&cfg, k_tridiag32<4>, (const int*)h->d_sub_info, (const long long*)d_A, d_ws32, d_d,
+                                 d_e, (const int*)d_voff));
+    } else if (CS == 2) {
+      HK_CUDA(cudaFuncSetAttribute(k_tridiag32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      HK_CUDA(cudaLaunchKernelEx(&cfg, k_tridiag32<2>, (const int*)h->d_sub_info, (const long long*)d_A, d_ws32, d_d,
+                                 d_e, (const int*)d_voff));
+    } else {
+      HK_CUDA(cudaFuncSetAttribute(k_tridiag32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      HK_CUDA(cudaLaunchKernelEx(&cfg, k_tridiag32<1>, (const int*)h->d_sub_info, (const long long*)d_A, d_ws32, d_d,
+                                 d_e, (const int*)d_voff));
+    }
+    HK_COUNT_LAUNCH();
+  }
   cudaEventRecord(e1, st);
   HK_LAUNCH_CHECK();
-  k_candidates<<<ns, 128, 0, st>>>(h->d_sub_info, d_d, d_e, d_voff, h->p.tau, d_lamhat, d_cnt, h->d_status);
+  size_t cshm = sizeof(float) * 2 * (size_t)maxn;
+  HK_CUDA(cudaFuncSetAttribute(k_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cshm));
+  k_candidates<<<ns, 512, cshm, st>>>(h->d_sub_info, d_d, d_e, d_voff, h->p.tau, d_lamhat, d_cnt, h->d_status);
   HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   HK_TRY(check_device_status(h, "eigen: candidates"));
@@ -1076,30 +1070,17 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
-  std::vector<long long> poff(ns), woff(ns);
-  long long ptot = 0, wtot = 0;
+  std::vector<long long> poff(ns);
+  long long ptot = 0;
   for (int s = 0; s < ns; ++s) {
     poff[s] = ptot;
     ptot += (long long)h->subs[s].nI * cnt[s];
-    woff[s] = wtot;
-    wtot += 5LL * h->subs[s].nI * std::max(1, std::min(cnt[s], 32));
   }
-  float *d_Q = nullptr, *d_wk = nullptr;
   double* d_P = nullptr;
-  long long *d_poff = nullptr, *d_woff = nullptr;
-  HK_TRY(dalloc(h, &d_Q, ptot));
+  long long* d_poff = nullptr;
   HK_TRY(dalloc(h, &d_P, ptot));
-  HK_TRY(dalloc(h, &d_wk, wtot));
   HK_TRY(dalloc(h, &d_poff, ns));
-  HK_TRY(dalloc(h, &d_woff, ns));
   HK_CUDA(up(d_poff, poff.data(), 8 * ns));
-  HK_CUDA(up(d_woff, woff.data(), 8 * ns));
-  k_inviter32<<<ns, 32, 0, st>>>(h->d_sub_info, d_d, d_e, d_voff, d_lamhat, d_cnt, d_poff, d_Q, d_woff, d_wk);
-  HK_COUNT_LAUNCH();
-  k_backtransform32<<<ns, 256, 0, st>>>(h->d_sub_info, d_bw, h->d_I, h->d_mu, d_A, d_L32, d_ws32, d_tau, d_voff,
-                                        d_cnt, d_poff, d_Q, d_P);
-  HK_COUNT_LAUNCH();
-  HK_LAUNCH_CHECK();
 
   // ---- FP64 refinement: clusters of candidates, one CTA each
   std::vector<int> levO(O_total + ns);
@@ -1133,8 +1114,8 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
       foff.push_back(ftot);
       ftot += fsize[s];
       xoff.push_back(xtot);
-      xtot += 2LL * (t1 - t) * oc[s];
-      pmax = std::max(pmax, t1 - t);
+      xtot += 2LL * (t1 - t + HK_GUARD) * oc[s];
+      pmax = std::max(pmax, t1 - t + HK_GUARD);
       t = t1;
     }
   }
@@ -1156,8 +1137,8 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
     size_t rshm = sizeof(double) * ((size_t)maxbO * maxbO + (size_t)maxbO * pmax);
     HK_CUDA(cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rshm));
     k_refine<<<nit, 256, rshm, st>>>(d_items, d_sig, h->d_sub_info, d_o_off, d_Olevptr, d_OL, maxrow, d_ocnt, d_ocol,
-                                     d_oB, d_oC, d_o2i, d_foff, d_xoff, d_F, d_X, d_poff, d_P, d_lamref, maxbO,
-                                     h->d_status);
+                                     d_oB, d_oC, d_o2i, d_foff, d_xoff, d_F, d_X, d_poff, d_P, d_lamhat, d_lamref,
+                                     maxbO, h->d_status);
     HK_COUNT_LAUNCH();
     HK_LAUNCH_CHECK();
     HK_CUDA(cudaStreamSynchronize(st));
@@ -1197,7 +1178,7 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   HK_CUDA(cudaStreamSynchronize(st));
   void* tmp[] = {d_ws, d_ws32, d_W, d_L, d_Gw, d_Rw, d_A, d_L32, d_voff, d_bw, d_ring, d_cnt, d_o_off, d_d, d_e,
                  d_tau, d_lamhat, d_lamref, d_O, d_okind, d_Operm, d_Olev, d_Olevptr, d_OL, d_ocnt, d_o2i, d_ocol,
-                 d_oB, d_oC, d_Q, d_P, d_wk, d_poff, d_woff, d_sel, d_m};
+                 d_oB, d_oC, d_P, d_poff, d_sel, d_m};
   for (void* p : tmp) dfree(h, p);
   return HK_OK;
 }
