@@ -37,6 +37,17 @@ extern "C" const char* hk_status_string(hk_status s) {
   return "unknown";
 }
 
+void hk_pool_init(int dev) {
+  static bool done[64] = {false};
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    unsigned long long keep = ~0ULL;  // keep freed blocks in the pool
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  done[dev] = true;
+}
+
 void dfree(hk_handle* h, void* p) {
   if (!p) return;
   for (size_t i = 0; i < h->allocs.size(); ++i)
@@ -45,7 +56,7 @@ void dfree(hk_handle* h, void* p) {
       h->allocs.pop_back();
       break;
     }
-  cudaFree(p);
+  cudaFreeAsync(p, h->stream);
 }
 
 hk_status check_device_status(hk_handle* h, const char* phase) {
@@ -69,8 +80,9 @@ static void destroy_all(hk_handle* h) {
   cudaGetDevice(&cur);
   cudaSetDevice(h->dev);
   cudaStreamSynchronize(h->stream);
-  for (void* p : h->allocs) cudaFree(p);
+  for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
   h->allocs.clear();
+  cudaStreamSynchronize(h->stream);
   if (h->h_state) cudaFreeHost(h->h_state);
   if (h->h_rstate) cudaFreeHost(h->h_rstate);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);

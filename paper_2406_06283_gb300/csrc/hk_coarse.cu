@@ -6,6 +6,8 @@
 // fixed summation order.  E^{-1} is formed by Gauss-Jordan elimination with
 // partial pivoting (one column per step); a pivot below 1e-10 max|E| reports
 // HK_SINGULAR_COARSE.
+#include <algorithm>
+
 #include "hk_internal.cuh"
 
 static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
@@ -82,83 +84,155 @@ __global__ void k_absmax(const double* __restrict__ a, long long n, double* out)
   }
 }
 
-// Step k, part 1 (one CTA): pivot search in column k, row swap, scaling of row k.
-__global__ void k_gj_pivot(double* A, int n0, int k, int* piv, double* minpiv) {
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The wait is bounded: after
+// ~2^24 polls the barrier gives up, records HK_TIMEOUT and returns false.
+struct GridBar {
+  unsigned count;
+  unsigned gen;
+};
+
+__device__ bool grid_barrier(GridBar* gb, unsigned nblocks, unsigned& my_gen, DevStatus* st, int* sh_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned g = my_gen;
+    __threadfence();
+    unsigned arrived = atomicAdd(&gb->count, 1u) + 1u;
+    if (arrived == nblocks) {
+      gb->count = 0u;
+      __threadfence();
+      atomicExch(&gb->gen, g + 1u);
+    } else {
+      unsigned spins = 0;
+      while (atomicAdd(&gb->gen, 0u) == g) {
+        if (++spins > (1u << 24)) {
+          ok = 0;
+          dev_fail(st, HK_TIMEOUT, blockIdx.x, 0);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    *sh_ok = ok;
+  }
+  my_gen += 1u;
+  __syncthreads();
+  return *sh_ok != 0;
+}
+
+// In-place Gauss-Jordan inverse of the n0 x n0 matrix A with partial pivoting and implicit row
+// interchanges: step k picks the unused row p_k with the largest |A[p][k]|, scales it, and eliminates
+// column k from every other row; column k then holds column p_k of the accumulated transform.  The
+// inverse is Inv[k][j] = A[p_k][q_j] with q the inverse of p (applied by k_gj_unpermute).  Rows are
+// owned by CTAs (row i by CTA i mod gridDim); the pivot search of step k+1 is fused into the
+// elimination of step k (per-CTA maxima, reduced redundantly by every CTA after the barrier), so each
+// step costs one grid barrier.  Ties go to the smallest row index.
+__global__ void k_gj_persistent(double* A, int n0, int* piv, int* used, double* pmax_v, int* pmax_i,
+                                GridBar* gb, double* minpiv, DevStatus* st) {
   __shared__ double rv[32];
   __shared__ int ri[32];
-  __shared__ int p_s;
-  __shared__ double inv_s;
-  int tid = threadIdx.x;
-  double best = -1;
-  int bi = k;
-  for (int i = k + tid; i < n0; i += blockDim.x) {
-    double v = fabs(A[(long long)i * n0 + k]);
-    if (v > best) { best = v; bi = i; }
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    double ov = __shfl_xor_sync(0xffffffffu, best, o);
-    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-  }
-  if ((tid & 31) == 0) { rv[tid >> 5] = best; ri[tid >> 5] = bi; }
-  __syncthreads();
-  if (tid == 0) {
-    double bv = rv[0];
-    int bj = ri[0];
-    for (int w = 1; w < (blockDim.x >> 5); ++w)
-      if (rv[w] > bv || (rv[w] == bv && ri[w] < bj)) { bv = rv[w]; bj = ri[w]; }
-    p_s = bj;
-    piv[k] = bj;
-    if (bv < *minpiv) *minpiv = bv;
-  }
-  __syncthreads();
-  int p = p_s;
-  if (p != k)
-    for (int c = tid; c < n0; c += blockDim.x) {
-      double t = A[(long long)k * n0 + c];
-      A[(long long)k * n0 + c] = A[(long long)p * n0 + c];
-      A[(long long)p * n0 + c] = t;
+  __shared__ int sh_ok, sh_p;
+  __shared__ double sh_f;
+  extern __shared__ double prow[];  // the scaled pivot row
+  int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+  unsigned G = gridDim.x, my_gen = 0;
+  // initial pivot search for column 0 (every CTA over its rows)
+  auto local_max = [&](int col, int buf) {
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = blockIdx.x + G * tid; i < n0; i += G * T) {
+      if (used[i]) continue;
+      double v = fabs(A[(long long)i * n0 + col]);
+      if (v > best || (v == best && i < bi)) { best = v; bi = i; }
     }
-  __syncthreads();
-  if (tid == 0) {
-    double pv = A[(long long)k * n0 + k];
-    inv_s = pv != 0.0 ? 1.0 / pv : 0.0;
-    A[(long long)k * n0 + k] = 1.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double bv = rv[0];
+      int bj = ri[0];
+      for (int w = 1; w < nw; ++w)
+        if (rv[w] > bv || (rv[w] == bv && ri[w] < bj)) { bv = rv[w]; bj = ri[w]; }
+      pmax_v[buf * G + blockIdx.x] = bv;
+      pmax_i[buf * G + blockIdx.x] = bj;
+    }
+    __syncthreads();
+  };
+  local_max(0, 0);
+  if (!grid_barrier(gb, G, my_gen, st, &sh_ok)) return;
+  int pprev = -1;  // pivot row of the previous step, written back by its owner after the barrier
+  for (int k = 0; k < n0; ++k) {
+    if (pprev >= 0 && blockIdx.x == (unsigned)(pprev % (int)G)) {
+      for (int j = tid; j < n0; j += T) A[(long long)pprev * n0 + j] = prow[j];
+      __syncthreads();
+    }
+    int buf = k & 1;
+    // every CTA reduces the per-CTA maxima the same way (warp 0, lanes over CTAs)
+    if (warp == 0) {
+      double bv = -1.0;
+      int bj = 0x7fffffff;
+      for (unsigned b = lane; b < G; b += 32) {
+        double v = pmax_v[buf * G + b];
+        int i = pmax_i[buf * G + b];
+        if (v > bv || (v == bv && i < bj)) { bv = v; bj = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (ov > bv || (ov == bv && oi < bj)) { bv = ov; bj = oi; }
+      }
+      if (lane == 0) {
+        sh_p = bj;
+        double pv = A[(long long)bj * n0 + k];
+        sh_f = pv != 0.0 ? 1.0 / pv : 0.0;
+        if (blockIdx.x == 0) {
+          piv[k] = bj;
+          if (fabs(pv) < *minpiv) *minpiv = fabs(pv);
+        }
+      }
+    }
+    __syncthreads();
+    int p = sh_p;
+    double f = sh_f;
+    // scaled pivot row (column k of it becomes f)
+    for (int j = tid; j < n0; j += T) prow[j] = j == k ? f : A[(long long)p * n0 + j] * f;
+    __syncthreads();
+    // eliminate column k from the owned rows other than p (row p is rewritten after the barrier,
+    // once no CTA reads its unscaled values any more)
+    for (int i = blockIdx.x + G * warp; i < n0; i += G * nw) {
+      double* ai = A + (long long)i * n0;
+      if (i == p) continue;
+      double g = ai[k];
+      __syncwarp();
+      if (g != 0.0)
+        for (int j = lane; j < n0; j += 32) ai[j] = j == k ? -g * f : ai[j] - g * prow[j];
+    }
+    if (blockIdx.x == (unsigned)(p % G) && tid == 0) used[p] = 1;
+    __syncthreads();
+    if (k + 1 < n0) local_max(k + 1, (k + 1) & 1);
+    if (!grid_barrier(gb, G, my_gen, st, &sh_ok)) return;
+    pprev = p;
   }
-  __syncthreads();
-  double inv = inv_s;
-  for (int c = tid; c < n0; c += blockDim.x) A[(long long)k * n0 + c] *= inv;
+  if (pprev >= 0 && blockIdx.x == (unsigned)(pprev % (int)G))
+    for (int j = tid; j < n0; j += T) A[(long long)pprev * n0 + j] = prow[j];
 }
 
-// Step k, part 2: eliminate column k from every other row (one warp per row).
-__global__ void k_gj_elim(double* A, int n0, int k) {
-  int lane = threadIdx.x & 31;
-  int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (i >= n0 || i == k) return;
-  double* ri = A + (long long)i * n0;
-  const double* rk = A + (long long)k * n0;
-  double f = 0;
-  if (lane == 0) f = ri[k];
-  f = __shfl_sync(0xffffffffu, f, 0);
-  if (f == 0.0) return;
-  for (int c = lane; c < n0; c += 32)
-    if (c != k) ri[c] -= f * rk[c];
-  __syncwarp();
-  if (lane == 0) ri[k] = -f * rk[k];
+// Inv[k][j] = A[p_k][q_j], q = p^{-1}.
+__global__ void k_gj_unpermute(const double* __restrict__ A, double* Inv, int n0, const int* __restrict__ piv,
+                               const int* __restrict__ qinv) {
+  int k = blockIdx.x;
+  const double* ar = A + (long long)piv[k] * n0;
+  for (int j = threadIdx.x; j < n0; j += blockDim.x) Inv[(long long)k * n0 + j] = ar[qinv[j]];
 }
 
-__global__ void k_gj_unscramble(double* A, int n0, const int* __restrict__ piv) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n0) return;
-  double* row = A + (long long)r * n0;
-  for (int k = n0 - 1; k >= 0; --k) {
-    int p = piv[k];
-    if (p != k) {
-      double t = row[k];
-      row[k] = row[p];
-      row[p] = t;
-    }
-  }
+__global__ void k_invert_perm(const int* __restrict__ piv, int* qinv, int n0) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n0) qinv[piv[k]] = k;
 }
 
 hk_status phase_coarse(hk_handle* h) {
@@ -199,15 +273,51 @@ hk_status phase_coarse(hk_handle* h) {
   int* d_piv = nullptr;
   HK_TRY(dalloc(h, &d_sc, 2));
   HK_TRY(dalloc(h, &d_piv, n0));
-  k_absmax<<<304, 256, 0, st>>>(h->d_E, (long long)n0 * n0, d_sc); HK_COUNT_LAUNCH();
+  k_absmax<<<304, 256, 0, st>>>(h->d_E, (long long)n0 * n0, d_sc);
+  HK_COUNT_LAUNCH();
   double big = 1e300;
   HK_CUDA(cudaMemcpyAsync(d_sc + 1, &big, sizeof(double), cudaMemcpyHostToDevice, st));
-  for (int k = 0; k < n0; ++k) {
-    k_gj_pivot<<<1, 1024, 0, st>>>(h->d_Einv64, n0, k, d_piv, d_sc + 1); HK_COUNT_LAUNCH();
-    k_gj_elim<<<nblk((long long)n0 * 32, 256), 256, 0, st>>>(h->d_Einv64, n0, k); HK_COUNT_LAUNCH();
+  {
+    // one cooperative launch; grid = co-resident CTAs (at most one per SM here)
+    int threads = 512, nsm = 0, per_sm = 0, dev = h->dev;
+    size_t pshm = sizeof(double) * (size_t)n0;
+    HK_CUDA(cudaFuncSetAttribute(k_gj_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
+    HK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    HK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_persistent, threads, pshm));
+    if (per_sm < 1) {
+      hk_set_error("coarse inverse: no co-resident CTA possible (n0 = %d)", n0);
+      return HK_UNSUPPORTED;
+    }
+    // each step costs one grid barrier plus n0^2 / G FP64 updates per CTA: 64 CTAs balance the two
+    int G = std::min(std::min(nsm, 64), std::max(1, n0 / 8));
+    int *d_used = nullptr, *d_pi = nullptr, *d_q = nullptr;
+    double* d_pv = nullptr;
+    GridBar* d_gb = nullptr;
+    double* d_work = h->d_Einv64;  // A, then unpermuted into a copy
+    double* d_tmp = nullptr;
+    HK_TRY(dalloc(h, &d_used, n0));
+    HK_TRY(dalloc(h, &d_pi, 2 * G));
+    HK_TRY(dalloc(h, &d_pv, 2 * G));
+    HK_TRY(dalloc(h, &d_q, n0));
+    HK_TRY(dalloc(h, &d_gb, 1));
+    HK_TRY(dalloc(h, &d_tmp, (size_t)n0 * n0));
+    void* args[] = {&d_work, &n0, &d_piv, &d_used, &d_pv, &d_pi, &d_gb, &d_sc, &h->d_status};
+    double* minp = d_sc + 1;
+    args[7] = &minp;
+    HK_CUDA(cudaLaunchCooperativeKernel((void*)k_gj_persistent, dim3(G), dim3(threads), args, pshm, st));
+    HK_COUNT_LAUNCH();
+    HK_LAUNCH_CHECK();
+    HK_TRY(check_device_status(h, "coarse inverse"));
+    k_invert_perm<<<nblk(n0, 256), 256, 0, st>>>(d_piv, d_q, n0);
+    HK_COUNT_LAUNCH();
+    k_gj_unpermute<<<n0, 256, 0, st>>>(d_work, d_tmp, n0, d_piv, d_q);
+    HK_COUNT_LAUNCH();
+    HK_CUDA(cudaMemcpyAsync(h->d_Einv64, d_tmp, sizeof(double) * (size_t)n0 * n0, cudaMemcpyDeviceToDevice, st));
+    HK_LAUNCH_CHECK();
+    HK_CUDA(cudaStreamSynchronize(st));
+    void* fr[] = {d_used, d_pi, d_pv, d_q, d_gb, d_tmp};
+    for (void* q : fr) dfree(h, q);
   }
-  k_gj_unscramble<<<nblk(n0, 128), 128, 0, st>>>(h->d_Einv64, n0, d_piv); HK_COUNT_LAUNCH();
-  HK_LAUNCH_CHECK();
   double sc[2];
   HK_CUDA(cudaMemcpyAsync(sc, d_sc, sizeof(sc), cudaMemcpyDeviceToHost, st));
   HK_CUDA(cudaStreamSynchronize(st));

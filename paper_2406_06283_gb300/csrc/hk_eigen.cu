@@ -173,27 +173,27 @@ __global__ void k_schur(const int* __restrict__ sub_info, const long long* __res
   }
 }
 
-// ---- 3. FP32 standard form.  Banded Cholesky of D_II in FP64 into Lb (Lb[a][t] = L[a][a - bw + t]),
-// its FP32 copy L32, and A = L^{-1} (mu S mu) L^{-T} in FP32.  S is read from the FP64 workspace W,
-// which afterwards holds the FP32 transposed intermediate.
-__global__ void k_stdform32(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
-                            const int* __restrict__ bw_arr, const int* __restrict__ Ilev, const int* __restrict__ mu,
-                            const int* __restrict__ lrow, const int* __restrict__ lcntI, const int* __restrict__ lcol,
-                            const double* __restrict__ lvalD, const long long* __restrict__ wsW,
-                            const long long* __restrict__ wsL, const long long* __restrict__ wsA,
-                            const long long* __restrict__ wsL32, double* ws, float* ws32, DevStatus* st) {
+// ---- 3. FP32 standard form A = L^{-1} (mu S mu) L^{-T} with D_II = L L^T.
+// (a) banded Cholesky of D_II in FP64 (one CTA per subdomain): Lb[a][t] = L[a][a - bw + t], and its
+//     FP32 copy L32;
+// (b) Y = L^{-1} (mu S mu) column by column (S read in FP64 and scaled on the fly);
+// (c) A = L^{-1} Y^T, where column c of Y^T is row c of Y, read through shared-memory tiles.
+// In (b) and (c) each CTA owns a tile of columns and each thread one column; the last bw solved
+// entries of a column sit in a shared-memory ring, and the next 8 input rows are loaded ahead.
+// A is symmetric up to rounding and is used as computed.
+__global__ void k_dchol(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
+                        const int* __restrict__ bw_arr, const int* __restrict__ lrow, const int* __restrict__ lcntI,
+                        const int* __restrict__ lcol, const double* __restrict__ lvalD,
+                        const long long* __restrict__ wsL, const long long* __restrict__ wsL32, double* ws,
+                        float* ws32, DevStatus* st) {
   int s = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
   const int* si = sub_info + 8 * s;
   int nI = si[0], off = si[3];
   int bw = bw_arr[s], ld = bw + 1;
   long long coff = sub_off[3 * s + 1];
   const int* lr = lrow + off + s;
-  double* W = ws + wsW[s];
   double* Lb = ws + wsL[s];
-  float* A = ws32 + wsA[s];  // row stride lda = nI rounded up to 4 (padding columns stay 0)
   float* L32 = ws32 + wsL32[s];
-  float* Tm = reinterpret_cast<float*>(W);
-  int lda = (nI + 3) & ~3;
   for (long long e = tid; e < (long long)nI * ld; e += T) Lb[e] = 0.0;
   __syncthreads();
   for (int a = tid; a < nI; a += T) {
@@ -216,125 +216,176 @@ __global__ void k_stdform32(const int* __restrict__ sub_info, const long long* _
     for (int i = k + 1 + tid; i <= iend; i += T) Lb[(long long)i * ld + (k - i + bw)] /= lkk;
     __syncthreads();
     if (tid == 0) Lb[(long long)k * ld + bw] = lkk;
-    int w = iend - k;
-    for (int e = tid; e < w * w; e += T) {
-      int i = k + 1 + e / w, j = k + 1 + e % w;
-      if (j <= i)
-        Lb[(long long)i * ld + (j - i + bw)] -=
-            Lb[(long long)i * ld + (k - i + bw)] * Lb[(long long)j * ld + (k - j + bw)];
+    for (int i = k + 1 + (tid >> 5); i <= iend; i += T >> 5) {
+      double lik = Lb[(long long)i * ld + (k - i + bw)];
+      for (int j = k + 1 + (tid & 31); j <= i; j += 32)
+        Lb[(long long)i * ld + (j - i + bw)] -= lik * Lb[(long long)j * ld + (k - j + bw)];
     }
     __syncthreads();
   }
   for (long long e = tid; e < (long long)nI * ld; e += T) L32[e] = (float)Lb[e];
-  int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
-  for (int a = warp; a < nI; a += nw) {
-    double ma = (double)mu[Ilev[off + a]];
-    for (int c = lane; c < lda; c += 32)
-      A[(long long)a * lda + c] =
-          c < nI ? (float)(W[(long long)a * nI + c] * ma * (double)mu[Ilev[off + c]]) : 0.f;
-  }
-  __syncthreads();
-  // column-parallel forward substitution M <- L^{-1} M; each thread keeps the last bw+1 solved
-  // entries of its own column in a shared-memory ring (ring[slot * T + tid])
-  extern __shared__ float ring[];
-  int R = bw + 1;
-  for (int pass = 0; pass < 2; ++pass) {
-    float* M = pass == 0 ? A : Tm;
-    for (int c0 = 0; c0 < nI; c0 += T) {
-      int c = c0 + tid;
-      bool act = c < nI;
-      int wslot = 0;  // a % R, carried along
-      for (int a = 0; a < nI && act; ++a) {
-        float v = M[(long long)a * lda + c];
-        int k0 = max(0, a - bw);
-        const float* la = L32 + (long long)a * ld + (k0 - a + bw);
-        int slot = wslot - (a - k0);  // k0 % R
-        if (slot < 0) slot += R;
-        int len = a - k0, seg = min(len, R - slot);  // [slot, R) then [0, len - seg)
-        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
-        const float* r1 = ring + (long long)slot * T + tid;
-        int q = 0;
-        for (; q + 4 <= seg; q += 4) {
-          acc0 += la[q] * r1[(long long)q * T];
-          acc1 += la[q + 1] * r1[(long long)(q + 1) * T];
-          acc2 += la[q + 2] * r1[(long long)(q + 2) * T];
-          acc3 += la[q + 3] * r1[(long long)(q + 3) * T];
-        }
-        for (; q < seg; ++q) acc0 += la[q] * r1[(long long)q * T];
-        const float* la2 = la + seg;
-        const float* r2 = ring + tid;
-        int rest = len - seg;
-        q = 0;
-        for (; q + 4 <= rest; q += 4) {
-          acc0 += la2[q] * r2[(long long)q * T];
-          acc1 += la2[q + 1] * r2[(long long)(q + 1) * T];
-          acc2 += la2[q + 2] * r2[(long long)(q + 2) * T];
-          acc3 += la2[q + 3] * r2[(long long)(q + 3) * T];
-        }
-        for (; q < rest; ++q) acc0 += la2[q] * r2[(long long)q * T];
-        v -= (acc0 + acc1) + (acc2 + acc3);
-        v /= L32[(long long)a * ld + bw];
-        ring[wslot * T + tid] = v;
-        M[(long long)a * lda + c] = v;
-        if (++wslot == R) wslot = 0;
-      }
-      __syncthreads();
-    }
-    if (pass == 0) {
-      for (int c = warp; c < nI; c += nw)
-        for (int a = lane; a < nI; a += 32) Tm[(long long)c * lda + a] = A[(long long)a * lda + c];
-      __syncthreads();
-    }
-  }
-  for (int a = warp; a < nI; a += nw)
-    for (int c = lane; c < nI; c += 32)
-      A[(long long)a * lda + c] = 0.5f * (Tm[(long long)a * lda + c] + Tm[(long long)c * lda + a]);
 }
 
-// ---- 4. Householder tridiagonalisation of the dense symmetric A (full storage, row stride lda = n
-// rounded up to 4) in FP32, O(n) reductions in FP64; only the tridiagonal (d, e) is kept.
-// Step k forms the reflector H_k = I - tau v v^T (v[k+1] = 1) from row k, then needs p = tau A22 v and
-// w = p - (tau/2)(p.v) v for the rank-2 update A22 -= v w^T + w v^T.  The update of step k-1 and the
-// product of step k share one pass: each row i > k is read once, the pending update (v', w') of step
-// k-1 is applied and written back, and its dot with the new v accumulated.  Row k itself takes the
-// pending update in a shared-memory copy.
-// The CS CTAs of a thread-block cluster share one matrix: CTA r owns the rows i = r (mod CS), every
-// CTA rebuilds row k and the reflector redundantly (same arithmetic, same result), and the entries of
-// p are exchanged through distributed shared memory after one cluster barrier per step.  Shared
-// vectors are zero below the active column and in the padding, so row loops start on a 16-byte
-// boundary and move float4.
+// One forward substitution step for row a of a thread's column: v = (x - sum L[a][k] y[k]) / L[a][a]
+// with the previous solved entries y[k], k in [a - bw, a), in the ring.
+__device__ __forceinline__ float ring_solve_row(float x, int a, int bw, int ld, int R, int wslot,
+                                                const float* __restrict__ L32, const float* ring, int T, int tid) {
+  int k0 = max(0, a - bw);
+  const float* la = L32 + (long long)a * ld + (k0 - a + bw);
+  int slot = wslot - (a - k0);
+  if (slot < 0) slot += R;
+  int len = a - k0, seg = min(len, R - slot);
+  float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+  const float* r1 = ring + (long long)slot * T + tid;
+  int q = 0;
+  for (; q + 4 <= seg; q += 4) {
+    acc0 += la[q] * r1[(long long)q * T];
+    acc1 += la[q + 1] * r1[(long long)(q + 1) * T];
+    acc2 += la[q + 2] * r1[(long long)(q + 2) * T];
+    acc3 += la[q + 3] * r1[(long long)(q + 3) * T];
+  }
+  for (; q < seg; ++q) acc0 += la[q] * r1[(long long)q * T];
+  const float* la2 = la + seg;
+  const float* r2 = ring + tid;
+  int rest = len - seg;
+  q = 0;
+  for (; q + 4 <= rest; q += 4) {
+    acc0 += la2[q] * r2[(long long)q * T];
+    acc1 += la2[q + 1] * r2[(long long)(q + 1) * T];
+    acc2 += la2[q + 2] * r2[(long long)(q + 2) * T];
+    acc3 += la2[q + 3] * r2[(long long)(q + 3) * T];
+  }
+  for (; q < rest; ++q) acc0 += la2[q] * r2[(long long)q * T];
+  return (x - ((acc0 + acc1) + (acc2 + acc3))) / L32[(long long)a * ld + bw];
+}
+
+#define HK_SF_TILE 128   // columns per CTA in the standard-form solves (= threads)
+#define HK_SF_AHEAD 8    // rows loaded ahead
+
+// (b): Y[:, tile] = L^{-1} (mu S mu)[:, tile].  grid = (subdomain, column tile).
+__global__ void __launch_bounds__(HK_SF_TILE) k_sf_solve1(const int* __restrict__ sub_info,
+                                                          const int* __restrict__ bw_arr,
+                                                          const int* __restrict__ Ilev, const int* __restrict__ mu,
+                                                          const long long* __restrict__ wsW,
+                                                          const long long* __restrict__ wsA,
+                                                          const long long* __restrict__ wsL32,
+                                                          const double* __restrict__ ws, float* ws32) {
+  extern __shared__ float ring[];
+  int s = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
+  const int* si = sub_info + 8 * s;
+  int nI = si[0], off = si[3];
+  int c = blockIdx.y * T + tid;
+  if (blockIdx.y * T >= nI) return;
+  int bw = bw_arr[s], ld = bw + 1, R = bw + 1, lda = (nI + 3) & ~3;
+  const double* W = ws + wsW[s];
+  float* Y = ws32 + wsA[s];  // output slot (the caller passes the Y workspace offsets)
+  const float* L32 = ws32 + wsL32[s];
+  bool act = c < nI;
+  double mc = act ? (double)mu[Ilev[off + c]] : 0.0;
+  int wslot = 0;
+  for (int a0 = 0; a0 < nI; a0 += HK_SF_AHEAD) {
+    float xin[HK_SF_AHEAD];
+#pragma unroll
+    for (int u = 0; u < HK_SF_AHEAD; ++u) {
+      int a = a0 + u;
+      xin[u] = (act && a < nI) ? (float)(W[(long long)a * nI + c] * mc * (double)mu[Ilev[off + a]]) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < HK_SF_AHEAD; ++u) {
+      int a = a0 + u;
+      if (a >= nI) break;
+      float v = ring_solve_row(xin[u], a, bw, ld, R, wslot, L32, ring, T, tid);
+      ring[(long long)wslot * T + tid] = v;
+      if (act) Y[(long long)a * lda + c] = v;
+      if (++wslot == R) wslot = 0;
+    }
+  }
+}
+
+// (c): A[:, tile] = L^{-1} (Y^T)[:, tile]; the tile's columns are rows of Y, staged 32 entries at a
+// time through shared memory so that global reads stay coalesced.
+__global__ void __launch_bounds__(HK_SF_TILE) k_sf_solve2(const int* __restrict__ sub_info,
+                                                          const int* __restrict__ bw_arr,
+                                                          const long long* __restrict__ wsY,
+                                                          const long long* __restrict__ wsA,
+                                                          const long long* __restrict__ wsL32, float* ws32) {
+  extern __shared__ float ring[];
+  __shared__ float stage[32][HK_SF_TILE + 1];
+  int s = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
+  int nI = sub_info[8 * s];
+  int c0 = blockIdx.y * T, c = c0 + tid;
+  if (c0 >= nI) return;
+  int bw = bw_arr[s], ld = bw + 1, R = bw + 1, lda = (nI + 3) & ~3;
+  const float* Y = reinterpret_cast<const float*>(ws32 + wsY[s]);
+  float* A = ws32 + wsA[s];
+  const float* L32 = ws32 + wsL32[s];
+  bool act = c < nI;
+  int wslot = 0;
+  for (int a0 = 0; a0 < nI; a0 += 32) {
+    // stage Y[c0 + i][a0 + j] -> stage[j][i]: a warp reads 32 consecutive entries of one row
+    __syncthreads();
+    int lane = tid & 31, wp = tid >> 5, nwp = T >> 5;
+    for (int i = wp; i < T; i += nwp) {
+      int row = c0 + i, col = a0 + lane;
+      stage[lane][i] = (row < nI && col < nI) ? Y[(long long)row * lda + col] : 0.f;
+    }
+    __syncthreads();
+    for (int u = 0; u < 32 && a0 + u < nI; ++u) {
+      int a = a0 + u;
+      float v = ring_solve_row(stage[u][tid], a, bw, ld, R, wslot, L32, ring, T, tid);
+      ring[(long long)wslot * T + tid] = v;
+      if (act) A[(long long)a * lda + c] = v;
+      if (++wslot == R) wslot = 0;
+    }
+  }
+}
+
+// ---- 4. Householder tridiagonalisation of the dense symmetric A in FP32 (O(n) reductions in FP64),
+// reading and writing only the lower triangle (row stride lda = n rounded up to 4); only the
+// tridiagonal (d, e) is kept.
+// Step k forms the reflector H_k = I - tau v v^T (v[k+1] = 1) from column k below the diagonal, then
+// needs p = tau A22 v and w = p - (tau/2)(p.v) v for the rank-2 update A22 -= v w^T + w v^T.  The
+// update of step k-1 and the product of step k share one pass over the lower triangle: row i is read
+// once, the pending update (v', w') is applied and written back, its dot with v gives the row part of
+// p_i, and a_ij v_i (j < i) is the column part of p_j, summed in a per-warp shared-memory slice.
+// The CS CTAs of a thread-block cluster share one matrix (CTA r owns rows i = r mod CS); each CTA
+// rebuilds column k and the reflector redundantly, and the partial p vectors of the CTAs are added in
+// rank order through distributed shared memory after one cluster barrier per step.  Shared vectors are
+// zero below the active column and in the padding so that row loops start on a 16-byte boundary.
+#define HK_TRI_WARPS 32
 template <int CS>
-__global__ void __launch_bounds__(1024) k_tridiag32(const int* __restrict__ sub_info,
-                                                    const long long* __restrict__ wsA, float* ws, double* dvec,
-                                                    double* evec, const int* __restrict__ vec_off) {
+__global__ void __launch_bounds__(HK_TRI_WARPS * 32) k_tridiag32(const int* __restrict__ sub_info,
+                                                                 const long long* __restrict__ wsA, float* ws,
+                                                                 double* dvec, double* evec,
+                                                                 const int* __restrict__ vec_off) {
   extern __shared__ __align__(16) float smf[];
   __shared__ double red[32];
   int s = blockIdx.x / CS, r = blockIdx.x % CS;
   int tid = threadIdx.x, Tn = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = Tn >> 5;
   int n = sub_info[8 * s];
-  int lda = (n + 3) & ~3, l4 = lda >> 2;
+  int lda = (n + 3) & ~3;
   float* A = ws + wsA[s];
   double* d = dvec + vec_off[s];
   double* e = evec + vec_off[s];
-  float* vo = smf;            // v of the pending update
-  float* wo = vo + lda;       // w of the pending update
-  float* vn = wo + lda;       // v of the current step
-  float* pb = vn + lda;       // p, double buffered (2 * lda)
-  float* rowk = pb + 2 * lda; // row k with the pending update applied
+  float* vo = smf;             // v of the pending update
+  float* wo = vo + lda;        // w of the pending update
+  float* vn = wo + lda;        // v of the current step
+  float* pp = vn + lda;        // this CTA's partial p, double buffered (2 * lda)
+  float* pf = pp + 2 * lda;    // full p
+  float* colk = pf + lda;      // column k with the pending update applied
+  float* cacc = colk + lda;    // per-warp column sums (nw * lda)
   const float4* vo4 = reinterpret_cast<const float4*>(vo);
   const float4* wo4 = reinterpret_cast<const float4*>(wo);
   const float4* vn4 = reinterpret_cast<const float4*>(vn);
-  for (int j = tid; j < 6 * lda; j += Tn) smf[j] = 0.f;
+  for (int j = tid; j < (7 + nw) * lda; j += Tn) smf[j] = 0.f;
   if (CS > 1) cooperative_groups::this_cluster().sync(); else __syncthreads();
   for (int k = 0; k < n - 2; ++k) {
-    // row k, brought up to date
-    const float* gk = A + (long long)k * lda;
     float vk = vo[k], wk = wo[k];
-    for (int j = k + tid; j < n; j += Tn) rowk[j] = gk[j] - (vk * wo[j] + wk * vo[j]);
+    for (int j = k + tid; j < n; j += Tn) colk[j] = A[(long long)j * lda + k] - (vo[j] * wk + wo[j] * vk);
     __syncthreads();
-    double alpha = (double)rowk[k + 1];
+    double alpha = (double)colk[k + 1];
     double xs = 0;
-    for (int j = k + 2 + tid; j < n; j += Tn) xs += (double)rowk[j] * (double)rowk[j];
+    for (int j = k + 2 + tid; j < n; j += Tn) xs += (double)colk[j] * (double)colk[j];
     xs = block_sum(xs, red);
     double tau = 0, beta = alpha, scale = 0;
     if (xs > 0.0) {
@@ -342,27 +393,32 @@ __global__ void __launch_bounds__(1024) k_tridiag32(const int* __restrict__ sub_
       tau = (beta - alpha) / beta;
       scale = 1.0 / (alpha - beta);
     }
-    for (int j = k + 2 + tid; j < n; j += Tn) vn[j] = (float)((double)rowk[j] * scale);
+    for (int j = k + 2 + tid; j < n; j += Tn) vn[j] = (float)((double)colk[j] * scale);
     if (tid == 0) {
       vn[k] = 0.f;
       vn[k + 1] = xs > 0.0 ? 1.f : 0.f;
       if (r == 0) {
-        d[k] = (double)rowk[k];
+        d[k] = (double)colk[k];
         e[k] = beta;
       }
     }
+    // clear this step's column sums
+    for (int j = k + 1 + lane; j < n; j += 32) cacc[warp * lda + j] = 0.f;
     __syncthreads();
-    // fused pass over the owned rows i > k
-    float tauf = (float)tau;
-    float* pc = pb + (k & 1) * lda;
-    int c0 = (k + 1) >> 2;
+    // fused pass over the owned rows i > k, columns [k+1, i].  Column k (being read by every CTA of
+    // the cluster during this step) is never written: the head chunk holding column k+1 and the
+    // chunk holding the diagonal are done element by element, the chunks between them as float4.
+    float* pc = pp + (k & 1) * lda;
+    float* my = cacc + warp * lda;
     int i0 = k + 1 + (((r - (k + 1)) % CS) + CS) % CS;
+    int hc = (k + 1) >> 2;
     for (int i = i0 + CS * warp; i < n; i += CS * nw) {
-      float4* ri = reinterpret_cast<float4*>(A + (long long)i * lda);
-      float vi = vo[i], wi = wo[i];
+      float* rowp = A + (long long)i * lda;
+      float4* ri = reinterpret_cast<float4*>(rowp);
+      float vi = vo[i], wi = wo[i], vni = vn[i];
+      int cl = i >> 2;  // chunk holding the diagonal
       float acc = 0.f;
-#pragma unroll 4
-      for (int c = c0 + lane; c < l4; c += 32) {
+      for (int c = hc + 1 + lane; c < cl; c += 32) {
         float4 a = ri[c], vv = vo4[c], ww = wo4[c], nv = vn4[c];
         a.x -= vi * ww.x + wi * vv.x;
         a.y -= vi * ww.y + wi * vv.y;
@@ -370,32 +426,62 @@ __global__ void __launch_bounds__(1024) k_tridiag32(const int* __restrict__ sub_
         a.w -= vi * ww.w + wi * vv.w;
         ri[c] = a;
         acc += a.x * nv.x + a.y * nv.y + a.z * nv.z + a.w * nv.w;
+        float4* m4 = reinterpret_cast<float4*>(my) + c;
+        float4 mm = *m4;
+        mm.x += a.x * vni;
+        mm.y += a.y * vni;
+        mm.z += a.z * vni;
+        mm.w += a.w * vni;
+        *m4 = mm;
+      }
+      // head chunk (columns k+1 .. 4 hc + 3) on lanes 0-3, diagonal chunk (4 cl .. i) on lanes 4-7,
+      // one element per lane
+      {
+        int j = lane < 4 ? 4 * hc + lane : (lane < 8 && cl > hc ? 4 * cl + lane - 4 : -1);
+        if (j >= k + 1 && j <= i) {
+          float a = rowp[j] - (vi * wo[j] + wi * vo[j]);
+          rowp[j] = a;
+          acc += a * vn[j];
+          if (j < i) my[j] += a * vni;
+        }
       }
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) pc[i] = tauf * acc;
+      if (lane == 0) pc[i] = acc;  // row part (owned rows only)
+      __syncwarp();
+    }
+    __syncthreads();
+    // partial p of this CTA: row parts of its rows + column sums of all its warps
+    for (int j = k + 1 + tid; j < n; j += Tn) {
+      float t = (j % CS == r) ? pc[j] : 0.f;
+      for (int w = 0; w < nw; ++w) t += cacc[w * lda + j];
+      pc[j] = t;
     }
     if (CS > 1) {
       cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
-      cl.sync();  // owners' rows and p entries are complete and visible
-      for (int i = k + 1 + tid; i < n; i += Tn) {
-        int owner = i % CS;
-        if (owner != r) pc[i] = *cl.map_shared_rank(pc + i, owner);
+      cl.sync();
+      for (int j = k + 1 + tid; j < n; j += Tn) {
+        float t = 0.f;
+        for (int q = 0; q < CS; ++q) t += q == r ? pc[j] : *cl.map_shared_rank(pc + j, q);
+        pf[j] = (float)tau * t;
       }
+    } else {
+      __syncthreads();
+      for (int j = k + 1 + tid; j < n; j += Tn) pf[j] = (float)tau * pc[j];
     }
     __syncthreads();
     double pv = 0;
-    for (int j = k + 1 + tid; j < n; j += Tn) pv += (double)pc[j] * (double)vn[j];
+    for (int j = k + 1 + tid; j < n; j += Tn) pv += (double)pf[j] * (double)vn[j];
     pv = block_sum(pv, red);
     float K = (float)(0.5 * tau * pv);
     for (int j = tid; j < lda; j += Tn) {
       float vj = j > k ? vn[j] : 0.f;
       vo[j] = vj;
-      wo[j] = j > k ? pc[j] - K * vj : 0.f;
+      wo[j] = j > k ? pf[j] - K * vj : 0.f;
     }
     __syncthreads();
   }
   if (CS > 1) cooperative_groups::this_cluster().sync(); else __syncthreads();
-  if (r == 0 && tid == 0 && n >= 1) {
+  if (r == 0 && tid == 0) {
     if (n >= 2) {
       int a2 = n - 2, a3 = n - 1;
       float x22 = A[(long long)a2 * lda + a2] - 2.f * vo[a2] * wo[a2];
@@ -894,7 +980,7 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   cudaStream_t st = h->stream;
   int ns = h->n_sub;
   // ---- workspace layout (FP64 part and FP32 part)
-  std::vector<long long> W(ns), Lw(ns), Gw(ns), Rw(ns), Aw(ns), L32w(ns);
+  std::vector<long long> W(ns), Lw(ns), Gw(ns), Rw(ns), Aw(ns), L32w(ns), Yw(ns);
   std::vector<int> voff(ns), bw(ns), o_off(ns), oc(ns);
   long long tot = 0, tot32 = 0;
   int vo = 0, maxn = 0, O_total = 0;
@@ -907,6 +993,7 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
     Rw[s] = tot; tot += nG * nI;
     tot = (tot + 3) & ~3LL;
     Aw[s] = tot32; tot32 += nI * ((nI + 3) & ~3LL);
+    Yw[s] = tot32; tot32 += nI * ((nI + 3) & ~3LL);
     L32w[s] = tot32; tot32 += nI * (u.bw + 1);
     tot32 = (tot32 + 3) & ~3LL;
     voff[s] = vo;
@@ -919,7 +1006,8 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   }
   double* d_ws = nullptr;
   float* d_ws32 = nullptr;
-  long long *d_W = nullptr, *d_L = nullptr, *d_Gw = nullptr, *d_Rw = nullptr, *d_A = nullptr, *d_L32 = nullptr;
+  long long *d_W = nullptr, *d_L = nullptr, *d_Gw = nullptr, *d_Rw = nullptr, *d_A = nullptr, *d_L32 = nullptr,
+            *d_Y = nullptr;
   int *d_voff = nullptr, *d_bw = nullptr, *d_ring = nullptr, *d_cnt = nullptr, *d_o_off = nullptr;
   double *d_d = nullptr, *d_e = nullptr, *d_lamhat = nullptr, *d_lamref = nullptr;
   float* d_tau = nullptr;
@@ -931,6 +1019,7 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   HK_TRY(dalloc(h, &d_Rw, ns));
   HK_TRY(dalloc(h, &d_A, ns));
   HK_TRY(dalloc(h, &d_L32, ns));
+  HK_TRY(dalloc(h, &d_Y, ns));
   HK_TRY(dalloc(h, &d_voff, ns));
   HK_TRY(dalloc(h, &d_bw, ns));
   HK_TRY(dalloc(h, &d_ring, h->I_total));
@@ -951,6 +1040,7 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   HK_CUDA(up(d_Rw, Rw.data(), 8 * ns));
   HK_CUDA(up(d_A, Aw.data(), 8 * ns));
   HK_CUDA(up(d_L32, L32w.data(), 8 * ns));
+  HK_CUDA(up(d_Y, Yw.data(), 8 * ns));
   HK_CUDA(up(d_voff, voff.data(), 4 * ns));
   HK_CUDA(up(d_bw, bw.data(), 4 * ns));
   HK_CUDA(up(d_o_off, o_off.data(), 4 * ns));
@@ -1001,21 +1091,31 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   HK_TRY(check_device_status(h, "eigen: Gamma elimination"));
   int maxbw = 0;
   for (int s = 0; s < ns; ++s) maxbw = std::max(maxbw, bw[s]);
-  int sf_threads = 512;
-  while (sf_threads > 64 && sizeof(float) * (size_t)(maxbw + 1) * sf_threads > 200 * 1024) sf_threads >>= 1;
-  size_t sf_shm = sizeof(float) * (size_t)(maxbw + 1) * sf_threads;
-  if (sf_shm > 200 * 1024) {
-    hk_set_error("local band width %d too large for the standard-form kernel", maxbw);
+  size_t sf_shm = sizeof(float) * (size_t)(maxbw + 1) * HK_SF_TILE;
+  if (sf_shm > 180 * 1024) {
+    hk_set_error("local band width %d too large for the standard-form kernels", maxbw);
     return HK_UNSUPPORTED;
   }
-  HK_CUDA(cudaFuncSetAttribute(k_stdform32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf_shm));
-  k_stdform32<<<ns, sf_threads, sf_shm, st>>>(h->d_sub_info, h->d_sub_off, d_bw, h->d_I, h->d_mu, h->d_lrow,
-                                              h->d_lcntI, h->d_lcol, h->d_lvalD, d_W, d_L, d_A, d_L32, d_ws, d_ws32,
-                                              h->d_status);
+  k_dchol<<<ns, 512, 0, st>>>(h->d_sub_info, h->d_sub_off, d_bw, h->d_lrow, h->d_lcntI, h->d_lcol, h->d_lvalD, d_L,
+                              d_L32, d_ws, d_ws32, h->d_status);
+  HK_COUNT_LAUNCH();
+  HK_LAUNCH_CHECK();
+  HK_TRY(check_device_status(h, "eigen: Cholesky of D_II"));
+  dim3 sfgrid(ns, (maxn + HK_SF_TILE - 1) / HK_SF_TILE);
+  HK_CUDA(cudaFuncSetAttribute(k_sf_solve1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf_shm));
+  HK_CUDA(cudaFuncSetAttribute(k_sf_solve2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf_shm));
+  k_sf_solve1<<<sfgrid, HK_SF_TILE, sf_shm, st>>>(h->d_sub_info, d_bw, h->d_I, h->d_mu, d_W, d_Y, d_L32, d_ws,
+                                                  d_ws32);
+  HK_COUNT_LAUNCH();
+  k_sf_solve2<<<sfgrid, HK_SF_TILE, sf_shm, st>>>(h->d_sub_info, d_bw, d_Y, d_A, d_L32, d_ws32);
   HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   HK_TRY(check_device_status(h, "eigen: standard form"));
-  size_t shm = sizeof(float) * 6 * (size_t)((maxn + 3) & ~3);
+  size_t shm = sizeof(float) * (7 + HK_TRI_WARPS) * (size_t)((maxn + 3) & ~3);
+  if (shm > 225 * 1024) {
+    hk_set_error("subdomain with %d dofs too large for the shared-memory tridiagonalisation", maxn);
+    return HK_UNSUPPORTED;
+  }
   int CS = 1;
   while (CS < 4 && (long long)ns * CS * 2 <= 152) CS *= 2;  // spread a few subdomains over more SMs
   cudaEvent_t e0, e1;
@@ -1025,7 +1125,7 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ns * CS);
-    cfg.blockDim = dim3(1024);
+    cfg.blockDim = dim3(HK_TRI_WARPS * 32);
     cfg.dynamicSmemBytes = shm;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
@@ -1176,7 +1276,7 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
     HK_LAUNCH_CHECK();
   }
   HK_CUDA(cudaStreamSynchronize(st));
-  void* tmp[] = {d_ws, d_ws32, d_W, d_L, d_Gw, d_Rw, d_A, d_L32, d_voff, d_bw, d_ring, d_cnt, d_o_off, d_d, d_e,
+  void* tmp[] = {d_ws, d_ws32, d_W, d_L, d_Gw, d_Rw, d_A, d_L32, d_Y, d_voff, d_bw, d_ring, d_cnt, d_o_off, d_d, d_e,
                  d_tau, d_lamhat, d_lamref, d_O, d_okind, d_Operm, d_Olev, d_Olevptr, d_OL, d_ocnt, d_o2i, d_ocol,
                  d_oB, d_oC, d_P, d_poff, d_sel, d_m};
   for (void* p : tmp) dfree(h, p);

@@ -189,12 +189,16 @@ cudaEvent_t hk_event(hk_handle* h);
     }                                                                \
   } while (0)
 
-// Allocation helper: zero-initialised device memory tracked by the handle.
+// Allocation helper: zero-initialised device memory tracked by the handle, from the device's
+// stream-ordered memory pool (hk_pool_init keeps freed blocks cached in the pool, so repeated setups
+// and solves do not go back to the driver).
+void hk_pool_init(int dev);
 template <typename T>
 hk_status dalloc(hk_handle* h, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  hk_pool_init(h->dev);
+  cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), h->stream);
   if (e != cudaSuccess) {
     hk_set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
     return HK_OOM;
