@@ -39,7 +39,9 @@ from paper_2406_06283_gb300 import workloads as W  # noqa: E402
 
 METRIC = "Helmholtz solves/s and p99 latency at 1e-8 residual; FP32-precond vs FP64 form"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (recipe table); no measured figure in the peaks file
+# DRAM bytes (read + write) of one k_tridiag32 launch from an ncu capture of the same kernel, per workload;
+# None until a capture of the current kernel exists.
+TRIDIAG_TRAFFIC = {}
 
 
 def workload(name: str):
@@ -339,11 +341,15 @@ def run_ours(args, world, rank, local):
     dom = max(tot, key=tot.get)
     sizes = [hk_sub_sizes(p)]
     if dom == "tridiag":
-        flops = sum(4.0 / 3.0 * nI ** 3 for nI in sizes[0])
-        ach = flops / (statistics.mean(tri_ms) * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel": "k_tridiag (FP64 Householder)",
-                "peak_source": "nominal FP64 (recipe table)"}
+        # Householder reduction in FP32 on the lower triangle: step k reads and writes the trailing
+        # triangle rows i > k, columns k+1..i once, 4 B * 2 * (n-k-1)(n-k)/2; summed over k this is
+        # 4 (n-1) n (n+1) / 3 bytes per subdomain of n = |dof(Omega_i)| unknowns.
+        b = sum(4.0 * (nI - 1) * nI * (nI + 1) / 3.0 for nI in sizes[0])
+        ach = b / (statistics.mean(tri_ms) * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": TRIDIAG_TRAFFIC.get(args.workload), "algorithmic_bytes": b,
+                "kernel": "k_tridiag32 (FP32 Householder tridiagonalisation, lower triangle, 2-CTA clusters)",
+                "ms_per_launch": statistics.mean(tri_ms), "peak_source": src}
     else:
         b = {"local_apply": bytes_local, "coarse_solve": bytes_coarse, "scatter": bytes_scatter}.get(dom)
         if b is None:

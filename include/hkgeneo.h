@@ -42,7 +42,8 @@ typedef enum {
   HK_OOM = 6,              /* device allocation failed */
   HK_TIMEOUT = 7,          /* a bounded device wait ran out */
   HK_CUDA_ERROR = 8,       /* a CUDA runtime call failed */
-  HK_UNSUPPORTED = 9       /* input outside the library's limits (e.g. a level set wider than 128 dofs) */
+  HK_UNSUPPORTED = 9,      /* input outside the library's limits (e.g. a level set wider than 256 dofs) */
+  HK_PENDING = 10          /* hk_server_poll: the request has not finished yet */
 } hk_status;
 
 enum { HK_FP64 = 0, HK_FP32_PRECOND = 1 };                     /* hk_params.precision */
@@ -129,6 +130,7 @@ typedef struct {
   long long lower_nnz;         /* couplings L_j read by the forward sweeps, sum over subdomains */
   double setup_ms[8];          /* phases: assembly, decomposition, local factors, eigen, coarse,
                                   total; [6] the Householder tridiagonalisation kernel alone; [7] 0 */
+  size_t bytes_peak;           /* most device bytes the handle held at once (setup temporaries included) */
 } hk_info_t;
 
 hk_status hk_info(const hk_handle* h, hk_info_t* info);
@@ -200,6 +202,81 @@ hk_status hk_matvec(hk_handle* h, int n_rhs, const double* x, double* y);
 /* Load vector (f, phi_l) of the P1 interpolant of nodal values f_nodal (n_nodes), written to
  * rhs (n_dofs); exact for piecewise-linear f (Eq. 2.12's right-hand side). */
 hk_status hk_assemble_load(hk_handle* h, const double* f_nodal, double* rhs);
+
+/* ---- Serving: a request loop over cached operators ----
+ *
+ * A server owns a set of operators (problem descriptions: mesh, coefficients, k,
+ * parameters) and answers solve requests on them.  The method has no serving
+ * layer; this is the deployment form of the same setup (hk_setup) and solve
+ * (hk_solve), with three properties:
+ *  - Operator cache.  An operator's setup (factors, coarse space, E^{-1}) is
+ *    built on its first request and kept resident, keyed by the operator's
+ *    content (a 64-bit FNV-1a hash of every input array and parameter), so
+ *    later right-hand sides skip setup.  Adding identical content twice
+ *    returns the same id.
+ *  - Admission by device memory.  The resident operators (their
+ *    hk_info_t.bytes_resident, solve workspaces included) plus reservations for
+ *    setups and solves in flight stay within `device_mem_budget`.  A setup
+ *    reserves its peak: 24 KiB per dof (2D) or 64 KiB per dof (3D) before the
+ *    operator's first setup, 1.25 x the measured hk_info_t.bytes_peak after it.
+ *    A solve of s right-hand sides on n dofs reserves the workspace it lacks:
+ *    8 s ((2 restart + 6) n + (restart + 1)(restart + 4) + max_iters) bytes plus
+ *    the preconditioner's buffers and 1 MiB.  When a batch does not fit, idle
+ *    operators are evicted, least recently used first; a request waits while
+ *    the memory is held by work in flight.  A request whose operator cannot fit
+ *    even in an empty server fails with HK_OOM.
+ *  - Continuous batching.  `n_slots` worker threads each drive their own CUDA
+ *    stream.  A free slot takes the oldest waiting request whose operator is
+ *    not in use, together with every other waiting request on that operator
+ *    with the same tol (up to `max_batch_rhs` right-hand sides), and solves
+ *    them as one multi-right-hand-side FGMRES.  Work on different operators
+ *    overlaps on the device.  Each right-hand side's arithmetic is the same
+ *    alone and in a batch: results do not depend on the mix.
+ * All calls are thread-safe.  Times are milliseconds since hk_server_create. */
+typedef struct hk_server hk_server;
+
+/* device_mem_budget: bytes (> 0) on the current device; n_slots: worker threads/streams (1..64);
+ * max_batch_rhs: most right-hand sides solved together (1..64). */
+hk_status hk_server_create(size_t device_mem_budget, int n_slots, int max_batch_rhs, hk_server** out);
+
+/* Registers an operator (arguments as hk_setup; the arrays are copied).  No device work happens
+ * here.  *op_id receives the operator's id. */
+hk_status hk_server_add_operator(hk_server* srv, const hk_mesh* mesh, const double* elem_coeff, double k,
+                                 const hk_params* params, uint64_t* op_id);
+
+/* Queues n_rhs right-hand sides (n_rhs * n_dofs doubles, copied) on operator op_id.
+ * *ticket identifies the request for hk_server_poll. */
+hk_status hk_server_submit(hk_server* srv, uint64_t op_id, int n_rhs, const double* rhs, double tol,
+                           uint64_t* ticket);
+
+typedef struct {
+  double submit_ms, start_ms, end_ms; /* queued, taken by a slot, finished */
+  int32_t batch_rhs;                  /* right-hand sides in the solve that served the request */
+  int32_t setup_ran;                  /* 1 if the operator's setup ran for this batch (cache miss) */
+  int32_t slot;                       /* worker slot */
+  int32_t n_rhs;
+} hk_request_info;
+
+/* Waits up to wait_ms (0 = do not wait, < 0 = without limit) for request `ticket`.  While it
+ * runs: HK_PENDING.  Once finished: writes the outputs as hk_solve does (u: n_rhs * n_dofs,
+ * iters: n_rhs, res_hist: NULL or n_rhs * max_iters, final_true_rel_res: NULL or n_rhs,
+ * info: NULL or one record), forgets the ticket and returns the request's status.  An unknown
+ * ticket gives HK_BAD_ARG. */
+hk_status hk_server_poll(hk_server* srv, uint64_t ticket, int wait_ms, double* u, int32_t* iters,
+                         double* res_hist, double* final_true_rel_res, hk_request_info* info);
+
+typedef struct {
+  long long submitted, completed, failed; /* requests */
+  long long setups, evictions, batches, cache_hits;
+  int resident_ops, n_ops, queued;
+  size_t bytes_in_use, bytes_peak, budget;
+} hk_server_stats;
+
+hk_status hk_server_get_stats(hk_server* srv, hk_server_stats* out);
+
+/* Finishes the work in flight, fails the queued requests (their tickets are dropped), frees every
+ * operator and the server.  NULL is accepted. */
+hk_status hk_server_destroy(hk_server* srv);
 
 #ifdef __cplusplus
 }

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "hk_internal.cuh"
 
@@ -38,20 +39,22 @@ extern "C" const char* hk_status_string(hk_status s) {
 }
 
 void hk_pool_init(int dev) {
-  static bool done[64] = {false};
-  if (dev < 0 || dev >= 64 || done[dev]) return;
-  cudaMemPool_t pool;
-  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-    unsigned long long keep = ~0ULL;  // keep freed blocks in the pool
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-  }
-  done[dev] = true;
+  static std::once_flag done[64];
+  if (dev < 0 || dev >= 64) return;
+  std::call_once(done[dev], [dev] {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      unsigned long long keep = ~0ULL;  // keep freed blocks in the pool
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+  });
 }
 
 void dfree(hk_handle* h, void* p) {
   if (!p) return;
   for (size_t i = 0; i < h->allocs.size(); ++i)
-    if (h->allocs[i] == p) {
+    if (h->allocs[i].first == p) {
+      h->bytes -= h->allocs[i].second;
       h->allocs[i] = h->allocs.back();
       h->allocs.pop_back();
       break;
@@ -80,7 +83,7 @@ static void destroy_all(hk_handle* h) {
   cudaGetDevice(&cur);
   cudaSetDevice(h->dev);
   cudaStreamSynchronize(h->stream);
-  for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
+  for (auto& a : h->allocs) cudaFreeAsync(a.first, h->stream);
   h->allocs.clear();
   cudaStreamSynchronize(h->stream);
   if (h->h_state) cudaFreeHost(h->h_state);
@@ -288,6 +291,7 @@ extern "C" hk_status hk_info(const hk_handle* h, hk_info_t* info) {
   info->coarse_elems = h->z_total;
   info->lower_nnz = h->lower_nnz;
   for (int i = 0; i < 8; ++i) info->setup_ms[i] = h->setup_ms[i];
+  info->bytes_peak = h->bytes_peak;
   return HK_OK;
 }
 

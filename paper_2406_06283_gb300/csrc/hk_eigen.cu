@@ -725,7 +725,7 @@ __global__ void k_refine(const int* __restrict__ items, const double* __restrict
                          const double* __restrict__ oC, const int* __restrict__ o2i,
                          const long long* __restrict__ f_off, const long long* __restrict__ x_off, double* F,
                          double* Xw, const long long* __restrict__ poff, double* P, const double* __restrict__ lam_hat,
-                         double* lam_ref, int max_b, DevStatus* st) {
+                         double* lam_ref, int max_b, int s_in_smem, DevStatus* st) {
   extern __shared__ double smem[];
   __shared__ int piv[HK_MAXB];
   __shared__ double red_v[32];
@@ -741,8 +741,8 @@ __global__ void k_refine(const int* __restrict__ items, const double* __restrict
   int nI = si[0], nG = si[1];
   int oo = o_off[s], nO = nI + nG, L = O_L[s];
   const int* lp = O_levptr + oo + s;
-  double* S = smem;                           // max_b x max_b
-  double* tv = smem + (long long)max_b * max_b;  // max_b x p
+  double* tv = smem;                          // max_b x p
+  double* Ssm = smem + (long long)max_b * p;  // max_b x max_b when the level blocks fit in shared memory
   double* Fw = F + f_off[it];
   double* X = Xw + x_off[it];                 // p x nO
   double* R = X + (long long)p * nO;          // p x nO
@@ -770,6 +770,7 @@ __global__ void k_refine(const int* __restrict__ items, const double* __restrict
   for (int j = 0; j < L; ++j) {
     int r0 = lp[j], b = lp[j + 1] - r0, r1 = lp[j + 1];
     int bn = j + 1 < L ? lp[j + 2] - r1 : 0;
+    double* S = s_in_smem ? Ssm : Fw + bo;  // wide levels: in place in the factor array
     for (int e = tid; e < b * b; e += T) {
       int qa = e / b, t = e % b;
       int a = r0 + qa;
@@ -786,7 +787,8 @@ __global__ void k_refine(const int* __restrict__ items, const double* __restrict
     }
     __syncthreads();
     gauss_jordan_inverse(S, b, piv, red_v, red_i, &minpiv, floor_piv);
-    for (int e = tid; e < b * b; e += T) Fw[bo + e] = S[e];
+    if (s_in_smem)
+      for (int e = tid; e < b * b; e += T) Fw[bo + e] = S[e];
     long long go = bo + (long long)b * b;
     for (int e = tid; e < b * bn; e += T) {
       int qt = e / bn, cc = e % bn;
@@ -1235,10 +1237,12 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
     HK_CUDA(up(d_foff, foff.data(), 8 * nit));
     HK_CUDA(up(d_xoff, xoff.data(), 8 * nit));
     size_t rshm = sizeof(double) * ((size_t)maxbO * maxbO + (size_t)maxbO * pmax);
+    int s_in_smem = rshm <= 190 * 1024;
+    if (!s_in_smem) rshm = sizeof(double) * (size_t)maxbO * pmax;
     HK_CUDA(cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rshm));
     k_refine<<<nit, 256, rshm, st>>>(d_items, d_sig, h->d_sub_info, d_o_off, d_Olevptr, d_OL, maxrow, d_ocnt, d_ocol,
                                      d_oB, d_oC, d_o2i, d_foff, d_xoff, d_F, d_X, d_poff, d_P, d_lamhat, d_lamref,
-                                     maxbO, h->d_status);
+                                     maxbO, s_in_smem, h->d_status);
     HK_COUNT_LAUNCH();
     HK_LAUNCH_CHECK();
     HK_CUDA(cudaStreamSynchronize(st));

@@ -11,7 +11,7 @@
 #include "hkgeneo.h"
 
 // Library limits (checked at setup, HK_UNSUPPORTED beyond them).
-#define HK_MAXB 128        // widest level set of a local block-tridiagonal factor
+#define HK_MAXB 256        // widest level set of a local block-tridiagonal factor
 #define HK_MAXM 256        // most eigenvectors kept on one subdomain
 #define HK_MAXROW 64       // most nonzeros in one row of B
 #define HK_MAXSTAR 64      // most elements around one node
@@ -161,7 +161,8 @@ struct hk_handle {
   int* h_state = nullptr;         // pinned host mirror of d_state
   double* h_rstate = nullptr;
 
-  std::vector<void*> allocs;
+  std::vector<std::pair<void*, size_t>> allocs;  // live allocations and their sizes
+  size_t bytes_peak = 0;
   size_t bytes = 0;
   bool dev_inputs = false;  // setup arrays are device pointers
   // kernel timing
@@ -203,8 +204,9 @@ hk_status dalloc(hk_handle* h, T** p, size_t count) {
     hk_set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
     return HK_OOM;
   }
-  h->allocs.push_back((void*)*p);
+  h->allocs.emplace_back((void*)*p, count * sizeof(T));
   h->bytes += count * sizeof(T);
+  if (h->bytes > h->bytes_peak) h->bytes_peak = h->bytes;
   e = cudaMemsetAsync(*p, 0, count * sizeof(T), h->stream);
   if (e != cudaSuccess) {
     hk_set_error("cudaMemset failed: %s", cudaGetErrorString(e));

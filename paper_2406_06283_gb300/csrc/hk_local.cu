@@ -33,7 +33,7 @@ long long factor_elems(const int* lp, int L) {
 __global__ void k_block_lu(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
                            const int* __restrict__ levptr, const int* __restrict__ lrow,
                            const int* __restrict__ lcntI, const int* __restrict__ lcol,
-                           const double* __restrict__ lval, double* F, DevStatus* st) {
+                           const double* __restrict__ lval, double* F, int s_in_smem, DevStatus* st) {
   extern __shared__ double smem[];
   __shared__ int piv[HK_MAXB];
   __shared__ double red_v[32];
@@ -45,7 +45,6 @@ __global__ void k_block_lu(const int* __restrict__ sub_info, const long long* __
   long long foff = sub_off[3 * s], coff = sub_off[3 * s + 1];
   const int* lp = levptr + loff;
   const int* lr = lrow + off + s;
-  double* S = smem;
   // scale for the singularity test: max |B_i| entry
   double mx = 0;
   for (int a = tid; a < nI; a += T)
@@ -68,7 +67,8 @@ __global__ void k_block_lu(const int* __restrict__ sub_info, const long long* __
     int r0 = lp[j], b = lp[j + 1] - r0;
     int r1 = lp[j + 1];
     int bn = j + 1 < L ? lp[j + 2] - r1 : 0;
-    // S = D_j - L_j G_{j-1}
+    // S = D_j - L_j G_{j-1}, in shared memory, or in place in the factor array for wide levels
+    double* S = s_in_smem ? smem : F + bo;
     for (int e = tid; e < b * b; e += T) {
       int qa = e / b, t = e % b;
       int a = r0 + qa;
@@ -85,7 +85,8 @@ __global__ void k_block_lu(const int* __restrict__ sub_info, const long long* __
     }
     __syncthreads();
     gauss_jordan_inverse(S, b, piv, red_v, red_i, &minpiv);
-    for (int e = tid; e < b * b; e += T) F[bo + e] = S[e];
+    if (s_in_smem)
+      for (int e = tid; e < b * b; e += T) F[bo + e] = S[e];
     long long go = bo + pad4((long long)b * b);
     // G_j = S_j^{-1} U_j, with U_j[a, c] = B[c, a] read from the rows of level j+1
     for (int e = tid; e < b * bn; e += T) {
@@ -473,11 +474,9 @@ static hk_status launch_local(hk_handle* h, int s, const double* v, const int* a
                               T* cvec, int do_local, int do_coarse) {
   size_t xbytes = sizeof(T) * ((size_t)h->max_dof * NR + (size_t)HK_MAXB * NR);
   size_t shm = 2 * (size_t)h->pack_stage + xbytes;
-  static bool attr_set = false;
-  if (!attr_set) {
-    HK_CUDA(cudaFuncSetAttribute(k_local_apply<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-    attr_set = true;
-  }
+  static const cudaError_t attr_rc =  // once per instantiation (thread-safe static initialisation)
+      cudaFuncSetAttribute(k_local_apply<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  HK_CUDA(attr_rc);
   if (shm > 220 * 1024) {
     hk_set_error("subdomain too large for the shared-memory apply (%d dofs, record %lld bytes)", h->max_dof,
                  (long long)h->pack_stage);
@@ -594,9 +593,11 @@ hk_status phase_local_factors(hk_handle* h) {
   }
   HK_TRY(dalloc(h, &h->d_F64, fo));
   size_t shm = sizeof(double) * (size_t)h->max_level * h->max_level;
+  int s_in_smem = shm <= 200 * 1024;
+  if (!s_in_smem) shm = 0;
   HK_CUDA(cudaFuncSetAttribute(k_block_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   k_block_lu<<<ns, 256, shm, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
-                                   h->d_lvalB, h->d_F64, h->d_status); HK_COUNT_LAUNCH();
+                                   h->d_lvalB, h->d_F64, s_in_smem, h->d_status); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   HK_TRY(check_device_status(h, "local factors"));
   // level records for the apply, in the arithmetic type of the precision form

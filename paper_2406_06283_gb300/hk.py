@@ -18,7 +18,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libhkgeneo.so")
 
 HK_OK, HK_BAD_ARG, HK_SINGULAR_LOCAL, HK_SINGULAR_COARSE, HK_EIG_FAIL = 0, 1, 2, 3, 4
-HK_NO_CONVERGENCE, HK_OOM, HK_TIMEOUT, HK_CUDA_ERROR, HK_UNSUPPORTED = 5, 6, 7, 8, 9
+HK_NO_CONVERGENCE, HK_OOM, HK_TIMEOUT, HK_CUDA_ERROR, HK_UNSUPPORTED, HK_PENDING = 5, 6, 7, 8, 9, 10
 HK_FP64, HK_FP32_PRECOND = 0, 1
 HK_TWO_LEVEL, HK_ONE_LEVEL, HK_COARSE_ONLY = 0, 1, 2
 HK_AS, HK_RAS_POU = 0, 1
@@ -51,7 +51,19 @@ class hk_info_t(C.Structure):
                 ("max_level", C.c_int), ("max_dof", C.c_int), ("nnz", C.c_int), ("precision", C.c_int),
                 ("levels", C.c_int), ("bytes_resident", C.c_size_t), ("factor_elems", C.c_longlong),
                 ("dof_total", C.c_longlong), ("coarse_elems", C.c_longlong), ("lower_nnz", C.c_longlong),
-                ("setup_ms", C.c_double * 8)]
+                ("setup_ms", C.c_double * 8), ("bytes_peak", C.c_size_t)]
+
+
+class hk_request_info(C.Structure):
+    _fields_ = [("submit_ms", C.c_double), ("start_ms", C.c_double), ("end_ms", C.c_double),
+                ("batch_rhs", C.c_int32), ("setup_ran", C.c_int32), ("slot", C.c_int32), ("n_rhs", C.c_int32)]
+
+
+class hk_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("completed", C.c_longlong), ("failed", C.c_longlong),
+                ("setups", C.c_longlong), ("evictions", C.c_longlong), ("batches", C.c_longlong),
+                ("cache_hits", C.c_longlong), ("resident_ops", C.c_int), ("n_ops", C.c_int), ("queued", C.c_int),
+                ("bytes_in_use", C.c_size_t), ("bytes_peak", C.c_size_t), ("budget", C.c_size_t)]
 
 
 _lib = None
@@ -87,6 +99,16 @@ def lib():
     L.hk_apply_precond.argtypes = [_P, C.c_int, _P, _P]
     L.hk_matvec.argtypes = [_P, C.c_int, _P, _P]
     L.hk_assemble_load.argtypes = [_P, _P, _P]
+    L.hk_server_create.argtypes = [C.c_size_t, C.c_int, C.c_int, C.POINTER(_P)]
+    L.hk_server_add_operator.argtypes = [_P, C.POINTER(hk_mesh), _P, C.c_double, C.POINTER(hk_params),
+                                         C.POINTER(C.c_uint64)]
+    L.hk_server_submit.argtypes = [_P, C.c_uint64, C.c_int, _P, C.c_double, C.POINTER(C.c_uint64)]
+    L.hk_server_poll.argtypes = [_P, C.c_uint64, C.c_int, _P, _P, _P, _P, C.POINTER(hk_request_info)]
+    L.hk_server_get_stats.argtypes = [_P, C.POINTER(hk_server_stats)]
+    L.hk_server_destroy.argtypes = [_P]
+    for f in ("hk_server_create", "hk_server_add_operator", "hk_server_submit", "hk_server_poll",
+              "hk_server_get_stats", "hk_server_destroy"):
+        getattr(L, f).restype = C.c_int
     for f in ("hk_setup", "hk_setup_device", "hk_set_timing", "hk_kernel_times", "hk_solve", "hk_solve_device", "hk_info", "hk_destroy", "hk_get_matrix",
               "hk_get_subdomain", "hk_get_mu", "hk_get_eigen", "hk_get_coarse", "hk_apply_precond", "hk_matvec",
               "hk_assemble_load"):
@@ -298,3 +320,98 @@ def hk_assemble_load(h: Handle, f_nodal) -> np.ndarray:
     out = np.zeros(h.n)
     _check(lib().hk_assemble_load(h.ptr, _ptr(f), _ptr(out)), "hk_assemble_load")
     return out
+
+
+# ---- serving (hk_server_*) ----
+
+@dataclass
+class Server:
+    ptr: C.c_void_p
+    n_dofs: dict        # op id -> n_dofs
+    max_iters: dict     # op id -> max_iters
+
+    def __del__(self):
+        try:
+            hk_server_destroy(self)
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def hk_server_create(budget_bytes: int, n_slots: int = 4, max_batch_rhs: int = 16) -> Server:
+    out = _P()
+    _check(lib().hk_server_create(int(budget_bytes), int(n_slots), int(max_batch_rhs), C.byref(out)),
+           "hk_server_create")
+    return Server(out, {}, {})
+
+
+def hk_server_add_operator(srv: Server, xyz, elems, is_boundary, elem_coeff, k, elem_to_sub, n_sub, overlap=2,
+                           tau=0.5, precision=HK_FP64, levels=HK_TWO_LEVEL, weighting=HK_AS, restart=50,
+                           max_iters=1000) -> int:
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    elems = np.ascontiguousarray(elems, dtype=np.int32)
+    bnd = np.ascontiguousarray(is_boundary, dtype=np.uint8)
+    coeff = np.ascontiguousarray(elem_coeff, dtype=np.float64)
+    e2s = np.ascontiguousarray(elem_to_sub, dtype=np.int32)
+    mesh = hk_mesh(xyz.shape[1], xyz.shape[0], xyz.ctypes.data_as(C.POINTER(C.c_double)), elems.shape[0],
+                   elems.ctypes.data_as(C.POINTER(C.c_int32)), bnd.ctypes.data_as(C.POINTER(C.c_uint8)))
+    prm = hk_params(int(n_sub), e2s.ctypes.data_as(C.POINTER(C.c_int32)), int(overlap), float(tau), int(precision),
+                    int(levels), int(weighting), int(restart), int(max_iters))
+    op = C.c_uint64()
+    _check(lib().hk_server_add_operator(srv.ptr, C.byref(mesh), _ptr(coeff), float(k), C.byref(prm), C.byref(op)),
+           "hk_server_add_operator")
+    srv.n_dofs[op.value] = int((bnd == 0).sum())
+    srv.max_iters[op.value] = int(max_iters)
+    return op.value
+
+
+def server_add_problem(srv: Server, p, precision=HK_FP64) -> int:
+    """hk_server_add_operator for a workloads.Problem."""
+    m = p.mesh
+    return hk_server_add_operator(srv, m.xyz, m.elems, m.is_boundary, p.coeff, p.k, p.elem_to_sub, p.n_sub,
+                                  p.overlap, p.tau, precision, HK_TWO_LEVEL, HK_AS, p.restart, p.max_iters)
+
+
+def hk_server_submit(srv: Server, op: int, rhs, tol=1e-8) -> int:
+    rhs = np.ascontiguousarray(np.atleast_2d(rhs), dtype=np.float64)
+    t = C.c_uint64()
+    _check(lib().hk_server_submit(srv.ptr, C.c_uint64(op), rhs.shape[0], _ptr(rhs), float(tol), C.byref(t)),
+           "hk_server_submit")
+    return t.value
+
+
+@dataclass
+class ServedResult:
+    u: np.ndarray
+    iters: np.ndarray
+    history: np.ndarray
+    true_rel_res: np.ndarray
+    status: int
+    info: dict
+
+
+def hk_server_poll(srv: Server, ticket: int, op: int, n_rhs: int, wait_ms: int = -1):
+    """None while the request runs; else a ServedResult (raises HKError on a failed request)."""
+    n, mi = srv.n_dofs[op], srv.max_iters[op]
+    u = np.zeros((n_rhs, n))
+    it = np.zeros(n_rhs, dtype=np.int32)
+    hist = np.zeros((n_rhs, mi))
+    res = np.zeros(n_rhs)
+    info = hk_request_info()
+    st = lib().hk_server_poll(srv.ptr, C.c_uint64(ticket), int(wait_ms), _ptr(u), _ptr(it), _ptr(hist), _ptr(res),
+                              C.byref(info))
+    if st == HK_PENDING:
+        return None
+    _check(st, "hk_server_poll", ok=(HK_OK, HK_NO_CONVERGENCE))
+    return ServedResult(u, it, hist, res, st, {f: getattr(info, f) for f, _ in hk_request_info._fields_})
+
+
+def hk_server_get_stats(srv: Server) -> dict:
+    s = hk_server_stats()
+    _check(lib().hk_server_get_stats(srv.ptr, C.byref(s)), "hk_server_get_stats")
+    return {f: getattr(s, f) for f, _ in hk_server_stats._fields_}
+
+
+def hk_server_destroy(srv: Server):
+    if srv.ptr is not None and srv.ptr.value:
+        lib().hk_server_destroy(srv.ptr)
+        srv.ptr = _P()

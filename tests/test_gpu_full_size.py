@@ -1,0 +1,115 @@
+"""Parity at the benchmark sizes, in the launch configuration bench.py times.
+
+* h = 1/256, k = 50 checkerboard workload (65,025 dofs, 64 subdomains, one N(0,1) right-hand side):
+  the whole oracle runs (about half a minute); iteration counts, solution, every subdomain's kept
+  eigenvalues and coarse subspace are compared with the tolerances of test_gpu_parity.py.
+* h = 1/512, k = 100 layered workload (261,121 dofs, 256 subdomains, 16 right-hand sides): too large for
+  the oracle as a whole, so the eigenproblems of sampled subdomains are compared one by one, and the
+  rest is checked through properties that hold at any size: the true residual recomputed with the
+  oracle's own assembly of B, right-hand sides solved together equal to each solved alone, and
+  E E^{-1} = I for the coarse inverse.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import decomposition as OD
+from oracle import fem as OF
+from oracle import geneo as OG
+from oracle import solver as OS
+from paper_2406_06283_gb300 import hk
+from paper_2406_06283_gb300 import workloads as W
+from test_gpu_parity import oracle_count_range
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _check_eigen(h, i, ev):
+    lam, Z, dof = hk.hk_get_eigen(h, i)
+    assert lam.size == ev.m, (i, lam.size, ev.m)
+    if ev.m == 0:
+        return
+    want = ev.lam[: ev.m]
+    assert np.all(np.abs(lam - want) <= 1e-9 * np.maximum(np.abs(want), 1e-3)), (i, np.max(np.abs(lam - want)))
+    order = np.argsort(dof)
+    Qa, Qb = sla.orth(Z[order]), sla.orth(ev.Z)
+    assert np.linalg.norm(Qa @ Qa.T - Qb @ Qb.T, 2) <= 1e-8
+
+
+@pytest.fixture(scope="module")
+def c2():
+    p = W.config_c2()
+    o = OS.setup_problem(p)
+    return p, o
+
+
+def test_c2_full_parity_fp64(c2):
+    p, o = c2
+    h = hk.setup_problem(p)
+    for i, ev in enumerate(o.eigs):
+        _check_eigen(h, i, ev)
+    want = OS.solve(o, p.rhs, p.tol)[0]
+    got = hk.hk_solve(h, p.rhs, p.tol)
+    lo, hi = oracle_count_range(o, p.rhs[0], p.tol, trials=2)
+    assert lo <= got.iters[0] <= hi, (got.iters[0], want.iters, (lo, hi))
+    assert _rel(got.u[0], want.x) <= 1e-7
+    assert got.true_rel_res[0] <= p.tol
+    hk.hk_destroy(h)
+
+
+def test_c2_full_parity_fp32_preconditioner(c2):
+    p, o = c2
+    h = hk.setup_problem(p, precision=hk.HK_FP32_PRECOND)
+    want = OS.solve(o, p.rhs, p.tol)[0]
+    got = hk.hk_solve(h, p.rhs, p.tol)
+    lo, hi = oracle_count_range(o, p.rhs[0], p.tol, trials=2, eps=6e-8)
+    assert lo - 1 <= got.iters[0] <= hi + 1, (got.iters[0], want.iters, (lo, hi))
+    assert _rel(got.u[0], want.x) <= 1e-7
+    hk.hk_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def c3():
+    p = W.config_c3()
+    h = hk.setup_problem(p, precision=hk.HK_FP32_PRECOND)
+    yield p, h
+    hk.hk_destroy(h)
+
+
+@pytest.mark.parametrize("i", [0, 17, 136, 255])
+def test_c3_sampled_eigenproblems(c3, i):
+    p, h = c3
+    m = p.mesh
+    subs, mu = OD.decompose(m.xyz, m.elems, m.is_boundary, p.elem_to_sub, p.n_sub, p.overlap)
+    BN, C, w = OG.local_pencil(m.xyz, m.elems, p.coeff, m.is_boundary, p.k, subs[i], mu)
+    _check_eigen(h, i, OG.local_eigen(BN, C, w, p.tau))
+
+
+def test_c3_coarse_inverse(c3):
+    p, h = c3
+    E, Ei = hk.hk_get_coarse(h)
+    assert E.shape[0] > 1000
+    r = np.random.default_rng(4).standard_normal(E.shape[0])
+    assert _rel(E @ (Ei @ r), r) <= 1e-10
+
+
+def test_c3_true_residual_and_batching(c3):
+    p, h = c3
+    m = p.mesh
+    B, _, _, _ = OF.helmholtz_matrices(m.xyz, m.elems, p.coeff, m.is_boundary, p.k)
+    got = hk.hk_solve(h, p.rhs, p.tol)
+    for r in range(p.rhs.shape[0]):
+        res = np.linalg.norm(p.rhs[r] - B @ got.u[r]) / np.linalg.norm(p.rhs[r])
+        assert abs(res - got.true_rel_res[r]) <= 1e-6 * res, (r, res, got.true_rel_res[r])
+        if got.status == hk.HK_OK:
+            assert res <= 1.05 * p.tol, (r, res)
+        hist = got.history[r, : got.iters[r]]
+        for c0 in range(0, hist.size, p.restart):  # GMRES residual estimates never increase within a cycle
+            assert np.all(np.diff(hist[c0:c0 + p.restart]) <= 1e-14), (r, c0)
+    alone = hk.hk_solve(h, p.rhs[5:6], p.tol)
+    assert alone.iters[0] == got.iters[5]
+    np.testing.assert_array_equal(alone.u[0], got.u[5])

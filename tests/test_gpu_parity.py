@@ -38,6 +38,8 @@ def _cases():
         "h20_p3_k9_ov1_uneven": W.small_problem(cells=20, parts=3, k=9.0, overlap=1, checker=2, seed=5),
         "h40_p4_k18_ov2": W.small_problem(cells=40, parts=4, k=18.0, overlap=2, checker=4, seed=6, n_rhs=2),
         "c1": W.config_c1(),
+        "3d_h8_p2_k4_ov1": W.small_problem_3d(cells=8, parts=2, k=4.0, overlap=1),
+        "3d_h12_p3_k6_ov2": W.small_problem_3d(cells=12, parts=3, k=6.0, overlap=2, seed=10),
     }
 
 
