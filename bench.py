@@ -165,6 +165,16 @@ def oracle_step(p):
 def run_reference(args, world, rank):
     if rank != 0:
         return
+    if args.workload == "c5":
+        cb = serving_cpu_baseline(W.config_c5())
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "solves/s",
+                "n_gpus": args.gpus, "steps": 1, "warmup": 0, "ms_per_step": 1e3 / cb["value"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": "c5 serving operators (oracle sample)"},
+                "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     p = workload(args.workload)
     cores = os.cpu_count()
     # each oracle step is a whole setup + solve (tens of seconds): at most two timed steps, no warm-up
@@ -382,6 +392,116 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ serving workload
+def run_serving(args, world, rank, local):
+    """24 cached operators behind hk_server_*: the operator cache is warmed once (one request per
+    operator, setups timed), then the same 2,000-request recipe is replayed (a) as one burst, which
+    measures capacity, and (b) as Poisson streams at fractions of that capacity, which measure latency.
+    Every solve goes through the public serving calls, host right-hand sides in, host solutions out."""
+    import torch
+
+    from paper_2406_06283_gb300 import hk
+
+    torch.cuda.set_device(local)
+    ops = W.config_c5()
+    prec = hk.HK_FP32_PRECOND if args.precision == "fp32" else hk.HK_FP64
+    budget = int(args.budget_gb * (1 << 30))
+    srv = hk.hk_server_create(budget, n_slots=args.slots, max_batch_rhs=16)
+    ids = [hk.server_add_problem(srv, p, prec) for p in ops]
+    launches0 = hk.hk_kernel_launches()
+
+    def replay(stream, burst):
+        tickets = [None] * len(stream)
+        t0 = time.perf_counter()
+
+        def submit():
+            for q, (ta, o, idx) in enumerate(stream):
+                if not burst:
+                    d = ta - (time.perf_counter() - t0)
+                    if d > 0:
+                        time.sleep(d)
+                tickets[q] = hk.hk_server_submit(srv, ids[o], ops[o].rhs[idx], 1e-8)
+        th = threading.Thread(target=submit)
+        th.start()
+        lat, first, last, nrhs, its, bad = [], None, None, 0, [], 0
+        for q, (ta, o, idx) in enumerate(stream):
+            while tickets[q] is None:
+                time.sleep(0.0005)
+            r = hk.hk_server_poll(srv, tickets[q], ids[o], len(idx), wait_ms=-1)
+            inf = r.info
+            lat.append(inf["end_ms"] - inf["submit_ms"])
+            first = inf["submit_ms"] if first is None else min(first, inf["submit_ms"])
+            last = inf["end_ms"] if last is None else max(last, inf["end_ms"])
+            nrhs += len(idx)
+            its.extend(int(x) for x in r.iters)
+            bad += int(r.status != hk.HK_OK)
+        th.join()
+        span = (last - first) / 1e3
+        return {"requests": len(stream), "rhs": nrhs, "solves_per_s": nrhs / span, "requests_per_s": len(stream) / span,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_iters": float(np.mean(its)), "not_converged": bad, "span_s": span}
+
+    # warm the operator cache: one single-rhs request per operator
+    t0 = time.perf_counter()
+    warm = replay([(0.0, i, [0]) for i in range(len(ops))], burst=True)
+    warm_s = time.perf_counter() - t0
+    st_warm = hk.hk_server_get_stats(srv)
+    sampler = ClockSampler(local)
+    sampler.start()
+    burst = replay(W.serving_stream(len(ops), args.requests, 1.0, seed=5), burst=True)
+    rates = {}
+    for frac in (0.5, 0.8):
+        lam = frac * burst["requests_per_s"]
+        rates[f"{frac:.1f}x_capacity"] = replay(W.serving_stream(len(ops), args.requests, lam, seed=5), burst=False)
+        rates[f"{frac:.1f}x_capacity"]["arrival_rate_per_s"] = lam
+    clocks = sampler.stop()
+    launches = hk.hk_kernel_launches() - launches0
+    stats = hk.hk_server_get_stats(srv)
+    hk.hk_server_destroy(srv)
+    n_avg = float(np.mean([p.mesh.n_dofs for p in ops]))
+    line = {"metric": METRIC, "value": burst["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+            "steps": args.requests, "warmup": len(ops), "ms_per_step": 1e3 * burst["span_s"] / args.requests,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 Krylov / f32 preconditioner" if prec == hk.HK_FP32_PRECOND else "f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": "c5 serving: 24 cached operators (16 2D h in 1/128..1/512, k in [20,100], "
+                                   "checkerboard a in 10^U[0,2]; 8 3D h=1/32 Kuhn tets, k=20, 4x4x4 boxes); "
+                                   f"{args.requests} requests, 1-4 rhs each, tol 1e-8",
+                       "slots": args.slots, "max_batch_rhs": 16, "budget_gb": args.budget_gb,
+                       "precision_form": args.precision, "parallelism": "replicas",
+                       "l2": "inputs of the stream exceed L2 (24 operators, several GB resident)"},
+            "latency_ms": {"p50": burst["p50_ms"], "p99": burst["p99_ms"]},
+            "serving": {"burst": burst, "poisson": rates, "warm_cache": {"seconds": warm_s, **warm},
+                        "stats": stats, "setups_during_warm": st_warm["setups"]},
+            "e2e": {"value": burst["solves_per_s"], "unit": "solves/s",
+                    "h2d_bytes_per_step": int(8 * n_avg * 2.5), "d2h_bytes_per_step": int(8 * n_avg * 2.5),
+                    "note": "value is already end to end: host rhs in, host u out, through hk_server_*"},
+            "gpu_launches": int(launches), "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = serving_cpu_baseline(ops)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def serving_cpu_baseline(ops, budget_s=25.0):
+    """The oracle on the smallest operators of the serving set, setup + one solve each, until budget_s."""
+    from oracle import solver as OS
+    order = sorted(range(len(ops)), key=lambda i: ops[i].mesh.n_dofs * max(1, ops[i].mesh.dim - 1) ** 3)
+    t0, done, names = time.perf_counter(), 0, []
+    for i in order:
+        p = ops[i]
+        h = OS.setup_problem(p)
+        OS.solve(h, p.rhs[:1], p.tol)
+        done += 1
+        names.append(p.name)
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"setup + one solve of {done} serving operators ({', '.join(names)}), no cache reuse; "
+                      f"numpy/scipy, BLAS threads up to {os.cpu_count()}"}
+
+
 def hk_sub_sizes(p):
     """|dof(Omega_i)| of every subdomain, read back through the C ABI."""
     from paper_2406_06283_gb300 import hk
@@ -397,7 +517,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5"])
+    ap.add_argument("--requests", type=int, default=2000, help="c5: requests per replay")
+    ap.add_argument("--slots", type=int, default=4, help="c5: server worker slots")
+    ap.add_argument("--budget-gb", type=float, default=64.0, help="c5: server device-memory budget")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--solve-reps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -407,6 +530,8 @@ def main():
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "c5":
+        run_serving(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <set>
 
 #include "hk_internal.cuh"
 
@@ -48,6 +49,22 @@ void hk_pool_init(int dev) {
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
   });
+}
+
+hk_status hk_allow_smem_fn(const void* fn) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  HK_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({fn, dev})) return HK_OK;
+  int optin = 0;
+  HK_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa;
+  HK_CUDA(cudaFuncGetAttributes(&fa, fn));
+  HK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
+  done.insert({fn, dev});
+  return HK_OK;
 }
 
 void dfree(hk_handle* h, void* p) {

@@ -261,7 +261,7 @@ hk_status phase_coarse(hk_handle* h) {
   int maxm = 0;
   for (auto& u : h->subs) maxm = u.m > maxm ? u.m : maxm;
   size_t shm = sizeof(double) * HK_ECHUNK * maxm;
-  HK_CUDA(cudaFuncSetAttribute(k_coarse_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  HK_TRY(hk_allow_smem(k_coarse_block));
   if (np > 0) {
     k_coarse_block<<<np, 256, shm, st>>>(d_plist, n0, h->d_sub_info, h->d_sub_off, h->d_I, h->d_Isorted,
                                          h->d_perm, h->d_rowptr, h->d_col, h->d_valB, h->d_Z64, h->d_E);
@@ -281,7 +281,7 @@ hk_status phase_coarse(hk_handle* h) {
     // one cooperative launch; grid = co-resident CTAs (at most one per SM here)
     int threads = 512, nsm = 0, per_sm = 0, dev = h->dev;
     size_t pshm = sizeof(double) * (size_t)n0;
-    HK_CUDA(cudaFuncSetAttribute(k_gj_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
+    HK_TRY(hk_allow_smem(k_gj_persistent));
     HK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     HK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_persistent, threads, pshm));
     if (per_sm < 1) {

@@ -412,41 +412,84 @@ __global__ void __launch_bounds__(HK_TRI_WARPS * 32) k_tridiag32(const int* __re
     float* my = cacc + warp * lda;
     int i0 = k + 1 + (((r - (k + 1)) % CS) + CS) % CS;
     int hc = (k + 1) >> 2;
-    for (int i = i0 + CS * warp; i < n; i += CS * nw) {
-      float* rowp = A + (long long)i * lda;
-      float4* ri = reinterpret_cast<float4*>(rowp);
-      float vi = vo[i], wi = wo[i], vni = vn[i];
-      int cl = i >> 2;  // chunk holding the diagonal
-      float acc = 0.f;
-      for (int c = hc + 1 + lane; c < cl; c += 32) {
-        float4 a = ri[c], vv = vo4[c], ww = wo4[c], nv = vn4[c];
-        a.x -= vi * ww.x + wi * vv.x;
-        a.y -= vi * ww.y + wi * vv.y;
-        a.z -= vi * ww.z + wi * vv.z;
-        a.w -= vi * ww.w + wi * vv.w;
-        ri[c] = a;
-        acc += a.x * nv.x + a.y * nv.y + a.z * nv.z + a.w * nv.w;
-        float4* m4 = reinterpret_cast<float4*>(my) + c;
-        float4 mm = *m4;
-        mm.x += a.x * vni;
-        mm.y += a.y * vni;
-        mm.z += a.z * vni;
-        mm.w += a.w * vni;
-        *m4 = mm;
+    float4* my4 = reinterpret_cast<float4*>(my);
+    // Each warp takes its rows four at a time (rows CS*nw apart): the four rows' loads of a chunk are
+    // issued together, so a lane has four independent loads in flight instead of one per row.
+    const int RG = 4;
+    for (int ib = i0 + CS * warp; ib < n; ib += RG * CS * nw) {
+      float4* A4 = reinterpret_cast<float4*>(A);
+      int ro[RG];  // row offsets in float4 units (n <= 1440: fits in int)
+      float vi[RG], wi[RG], vni[RG], acc[RG];
+      int cl[RG], clmax = 0;
+#pragma unroll
+      for (int q = 0; q < RG; ++q) {
+        int i = ib + q * CS * nw;
+        bool ok = i < n;
+        int ii = ok ? i : ib;
+        ro[q] = ii * (lda >> 2);
+        vi[q] = ok ? vo[i] : 0.f;
+        wi[q] = ok ? wo[i] : 0.f;
+        vni[q] = ok ? vn[i] : 0.f;
+        cl[q] = ok ? (i >> 2) : 0;  // chunk holding the diagonal (0: row absent)
+        clmax = max(clmax, cl[q]);
+        acc[q] = 0.f;
       }
-      // head chunk (columns k+1 .. 4 hc + 3) on lanes 0-3, diagonal chunk (4 cl .. i) on lanes 4-7,
-      // one element per lane
-      {
-        int j = lane < 4 ? 4 * hc + lane : (lane < 8 && cl > hc ? 4 * cl + lane - 4 : -1);
-        if (j >= k + 1 && j <= i) {
-          float a = rowp[j] - (vi * wo[j] + wi * vo[j]);
-          rowp[j] = a;
-          acc += a * vn[j];
-          if (j < i) my[j] += a * vni;
+      for (int c = hc + 1 + lane; c < clmax; c += 32) {
+        float4 a[RG];
+#pragma unroll
+        for (int q = 0; q < RG; ++q)
+          if (c < cl[q]) a[q] = A4[ro[q] + c];
+        float4 vv = vo4[c], ww = wo4[c], nv = vn4[c];
+        float4 cs = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < RG; ++q) {
+          if (c >= cl[q]) continue;
+          float4 t = a[q];
+          t.x -= vi[q] * ww.x + wi[q] * vv.x;
+          t.y -= vi[q] * ww.y + wi[q] * vv.y;
+          t.z -= vi[q] * ww.z + wi[q] * vv.z;
+          t.w -= vi[q] * ww.w + wi[q] * vv.w;
+          A4[ro[q] + c] = t;
+          acc[q] += t.x * nv.x + t.y * nv.y + t.z * nv.z + t.w * nv.w;
+          cs.x += t.x * vni[q];
+          cs.y += t.y * vni[q];
+          cs.z += t.z * vni[q];
+          cs.w += t.w * vni[q];
         }
+        float4 mm = my4[c];
+        mm.x += cs.x;
+        mm.y += cs.y;
+        mm.z += cs.z;
+        mm.w += cs.w;
+        my4[c] = mm;
       }
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) pc[i] = acc;  // row part (owned rows only)
+      __syncwarp();
+      // head chunk (columns k+1 .. 4 hc + 3) and diagonal chunk (4 cl .. i), one element per lane:
+      // lanes 8q .. 8q+7 serve row q (0-3 head, 4-7 diagonal chunk).  Rows of one group write
+      // disjoint elements of `my` only when their columns differ, so the groups take turns.
+#pragma unroll
+      for (int q = 0; q < RG; ++q) {
+        int i = ib + q * CS * nw;
+        int l8 = lane - 8 * q;
+        if (i < n && l8 >= 0 && l8 < 8) {
+          int j = l8 < 4 ? 4 * hc + l8 : (cl[q] > hc ? 4 * cl[q] + l8 - 4 : -1);
+          if (j >= k + 1 && j <= i) {
+            float* rowp = A + (long long)i * lda;
+            float a = rowp[j] - (vi[q] * wo[j] + wi[q] * vo[j]);
+            rowp[j] = a;
+            acc[q] += a * vn[j];
+            if (j < i) my[j] += a * vni[q];
+          }
+        }
+        __syncwarp();
+      }
+#pragma unroll
+      for (int q = 0; q < RG; ++q) {
+        float t = acc[q];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        int i = ib + q * CS * nw;
+        if (lane == 0 && i < n) pc[i] = t;  // row part (owned rows only)
+      }
       __syncwarp();
     }
     __syncthreads();
@@ -1104,8 +1147,8 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   HK_LAUNCH_CHECK();
   HK_TRY(check_device_status(h, "eigen: Cholesky of D_II"));
   dim3 sfgrid(ns, (maxn + HK_SF_TILE - 1) / HK_SF_TILE);
-  HK_CUDA(cudaFuncSetAttribute(k_sf_solve1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf_shm));
-  HK_CUDA(cudaFuncSetAttribute(k_sf_solve2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf_shm));
+  HK_TRY(hk_allow_smem(k_sf_solve1));
+  HK_TRY(hk_allow_smem(k_sf_solve2));
   k_sf_solve1<<<sfgrid, HK_SF_TILE, sf_shm, st>>>(h->d_sub_info, d_bw, h->d_I, h->d_mu, d_W, d_Y, d_L32, d_ws,
                                                   d_ws32);
   HK_COUNT_LAUNCH();
@@ -1138,15 +1181,15 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     if (CS == 4) {
-      HK_CUDA(cudaFuncSetAttribute(k_tridiag32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      HK_TRY(hk_allow_smem(k_tridiag32<4>));
       HK_CUDA(cudaLaunchKernelEx(&cfg, k_tridiag32<4>, (const int*)h->d_sub_info, (const long long*)d_A, d_ws32, d_d,
                                  d_e, (const int*)d_voff));
     } else if (CS == 2) {
-      HK_CUDA(cudaFuncSetAttribute(k_tridiag32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      HK_TRY(hk_allow_smem(k_tridiag32<2>));
       HK_CUDA(cudaLaunchKernelEx(&cfg, k_tridiag32<2>, (const int*)h->d_sub_info, (const long long*)d_A, d_ws32, d_d,
                                  d_e, (const int*)d_voff));
     } else {
-      HK_CUDA(cudaFuncSetAttribute(k_tridiag32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      HK_TRY(hk_allow_smem(k_tridiag32<1>));
       HK_CUDA(cudaLaunchKernelEx(&cfg, k_tridiag32<1>, (const int*)h->d_sub_info, (const long long*)d_A, d_ws32, d_d,
                                  d_e, (const int*)d_voff));
     }
@@ -1155,7 +1198,7 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   cudaEventRecord(e1, st);
   HK_LAUNCH_CHECK();
   size_t cshm = sizeof(float) * 2 * (size_t)maxn;
-  HK_CUDA(cudaFuncSetAttribute(k_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cshm));
+  HK_TRY(hk_allow_smem(k_candidates));
   k_candidates<<<ns, 512, cshm, st>>>(h->d_sub_info, d_d, d_e, d_voff, h->p.tau, d_lamhat, d_cnt, h->d_status);
   HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
@@ -1239,7 +1282,7 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
     size_t rshm = sizeof(double) * ((size_t)maxbO * maxbO + (size_t)maxbO * pmax);
     int s_in_smem = rshm <= 190 * 1024;
     if (!s_in_smem) rshm = sizeof(double) * (size_t)maxbO * pmax;
-    HK_CUDA(cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rshm));
+    HK_TRY(hk_allow_smem(k_refine));
     k_refine<<<nit, 256, rshm, st>>>(d_items, d_sig, h->d_sub_info, d_o_off, d_Olevptr, d_OL, maxrow, d_ocnt, d_ocol,
                                      d_oB, d_oC, d_o2i, d_foff, d_xoff, d_F, d_X, d_poff, d_P, d_lamhat, d_lamref,
                                      maxbO, s_in_smem, h->d_status);

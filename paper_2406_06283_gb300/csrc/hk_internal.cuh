@@ -217,6 +217,16 @@ hk_status dalloc(hk_handle* h, T** p, size_t count) {
 
 void dfree(hk_handle* h, void* p);
 
+// Raises a kernel's dynamic shared-memory limit once, to the device's opt-in maximum minus the
+// kernel's static shared memory.  The limit is a per-kernel global setting: raising it to the maximum
+// once (instead of to each launch's size) keeps concurrent setups on other host threads from
+// lowering it under a launch.  The launch still asks for exactly the bytes it uses.
+hk_status hk_allow_smem_fn(const void* fn);
+template <typename F>
+hk_status hk_allow_smem(F* fn) {
+  return hk_allow_smem_fn(reinterpret_cast<const void*>(fn));
+}
+
 // Reads the device status record; returns its code with a message.
 hk_status check_device_status(hk_handle* h, const char* phase);
 

@@ -474,9 +474,7 @@ static hk_status launch_local(hk_handle* h, int s, const double* v, const int* a
                               T* cvec, int do_local, int do_coarse) {
   size_t xbytes = sizeof(T) * ((size_t)h->max_dof * NR + (size_t)HK_MAXB * NR);
   size_t shm = 2 * (size_t)h->pack_stage + xbytes;
-  static const cudaError_t attr_rc =  // once per instantiation (thread-safe static initialisation)
-      cudaFuncSetAttribute(k_local_apply<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-  HK_CUDA(attr_rc);
+  HK_TRY(hk_allow_smem(k_local_apply<T, NR>));
   if (shm > 220 * 1024) {
     hk_set_error("subdomain too large for the shared-memory apply (%d dofs, record %lld bytes)", h->max_dof,
                  (long long)h->pack_stage);
@@ -595,7 +593,7 @@ hk_status phase_local_factors(hk_handle* h) {
   size_t shm = sizeof(double) * (size_t)h->max_level * h->max_level;
   int s_in_smem = shm <= 200 * 1024;
   if (!s_in_smem) shm = 0;
-  HK_CUDA(cudaFuncSetAttribute(k_block_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  HK_TRY(hk_allow_smem(k_block_lu));
   k_block_lu<<<ns, 256, shm, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
                                    h->d_lvalB, h->d_F64, s_in_smem, h->d_status); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();

@@ -219,6 +219,52 @@ def config_c3(n_rhs: int = 16) -> Problem:
     return Problem("c3_h512_k100_p16", m, a, 100.0, 16, box_partition(m, 16), rhs=rhs)
 
 
+def config_c5(seed: int = 5, pool: int = 8):
+    """Serving workload: 24 operators and a request-stream recipe.
+
+    16 operators in 2D: h = 1/cells with cells uniform in {128, 192, 256, 384, 512}, k ~ U[20, 100],
+    an 8x8 checkerboard a in 10^U[0,2], P x P boxes with P = max(ceil(k / 6), ceil(cells / 32)), so that
+    H k <= 6 and a box holds at most 32 x 32 cells (|dof(Omega_i)| <= 35^2, as at h = 1/256 and 1/512
+    with 8x8 and 16x16 boxes), overlap 2.
+    8 operators in 3D: unit cube, Kuhn tetrahedra, h = 1/32 (29,791 dofs), k = 20, 4x4x4 boxes,
+    a from a 4x4x4 checkerboard.  Each operator carries `pool` seeded N(0,1) right-hand sides that
+    the requests of serving_stream draw from.
+    """
+    ops, meshes = [], {}
+    choices = [128, 192, 256, 384, 512]
+    for i in range(16):
+        u = uniform(stream_seed(seed, i, 0), 2)
+        cells = choices[min(int(u[0] * len(choices)), len(choices) - 1)]
+        k = 20.0 + 80.0 * float(u[1])
+        P = max(int(math.ceil(k / 6.0)), -(-cells // 32))
+        m = meshes.setdefault(cells, square_mesh(cells))
+        a = checkerboard(m, 8, stream_seed(seed, i, 1))
+        rhs = np.stack([normal(stream_seed(seed, i, 2, r), m.n_dofs) for r in range(pool)])
+        ops.append(Problem(f"c5_op{i:02d}_2d_h{cells}_k{k:.1f}_p{P}", m, a, k, P, box_partition(m, P), rhs=rhs))
+    cube = cube_mesh(32)
+    for i in range(16, 24):
+        a = checkerboard(cube, 4, stream_seed(seed, i, 1))
+        rhs = np.stack([normal(stream_seed(seed, i, 2, r), cube.n_dofs) for r in range(pool)])
+        ops.append(Problem(f"c5_op{i:02d}_3d_h32_k20_p4", cube, a, 20.0, 4, box_partition(cube, 4), rhs=rhs))
+    return ops
+
+
+def serving_stream(n_ops: int, n_requests: int, rate: float, seed: int = 5, pool: int = 8, max_rhs: int = 4):
+    """Poisson arrivals: exponential inter-arrival times of mean 1/rate seconds, operator uniform,
+    s ~ U{1..max_rhs} right-hand sides drawn (seeded) from the operator's pool.
+    Returns a list of (arrival_s, op_index, rhs_indices)."""
+    u = uniform(stream_seed(seed, 1000, int(rate * 1000)), 3 * n_requests + pool * max_rhs * n_requests)
+    t, out = 0.0, []
+    for q in range(n_requests):
+        t += -math.log(max(1.0 - float(u[3 * q]), 1e-300)) / rate
+        op = min(int(u[3 * q + 1] * n_ops), n_ops - 1)
+        s = 1 + min(int(u[3 * q + 2] * max_rhs), max_rhs - 1)
+        base = 3 * n_requests + q * max_rhs
+        idx = [min(int(u[base + r] * pool), pool - 1) for r in range(s)]
+        out.append((t, op, idx))
+    return out
+
+
 def small_problem(cells: int = 16, parts: int = 2, k: float = 6.0, overlap: int = 1,
                   seed: int = 7, n_rhs: int = 1, checker: int = 0, tau: float = 0.5) -> Problem:
     """A small seeded 2D case for parity tests that the oracle finishes in seconds."""

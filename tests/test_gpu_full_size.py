@@ -113,3 +113,25 @@ def test_c3_true_residual_and_batching(c3):
     alone = hk.hk_solve(h, p.rhs[5:6], p.tol)
     assert alone.iters[0] == got.iters[5]
     np.testing.assert_array_equal(alone.u[0], got.u[5])
+
+
+def test_3d_h32_serving_operator():
+    """A 3D operator of the serving set (h = 1/32 Kuhn tetrahedra, 29,791 dofs, 4x4x4 boxes, k = 20):
+    level sets up to 13^2 = 169 dofs wide, so the FP64 block inverses of the eigen refinement run in
+    the factor array rather than shared memory.  Sampled subdomain eigenproblems against the oracle,
+    then a solve in the FP32 preconditioner form checked through the oracle's own B."""
+    p = W.config_c5()[16]
+    m = p.mesh
+    h = hk.setup_problem(p, precision=hk.HK_FP32_PRECOND)
+    assert hk.hk_info(h)["max_level"] <= 256
+    subs, mu = OD.decompose(m.xyz, m.elems, m.is_boundary, p.elem_to_sub, p.n_sub, p.overlap)
+    for i in (0, 21, 42, 63):
+        BN, C, w = OG.local_pencil(m.xyz, m.elems, p.coeff, m.is_boundary, p.k, subs[i], mu)
+        _check_eigen(h, i, OG.local_eigen(BN, C, w, p.tau))
+    B, _, _, _ = OF.helmholtz_matrices(m.xyz, m.elems, p.coeff, m.is_boundary, p.k)
+    got = hk.hk_solve(h, p.rhs[:2], p.tol)
+    assert got.status == hk.HK_OK
+    for r in range(2):
+        res = np.linalg.norm(p.rhs[r] - B @ got.u[r]) / np.linalg.norm(p.rhs[r])
+        assert res <= 1.05 * p.tol
+    hk.hk_destroy(h)
