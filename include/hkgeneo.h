@@ -131,6 +131,8 @@ typedef struct {
   double setup_ms[8];          /* phases: assembly, decomposition, local factors, eigen, coarse,
                                   total; [6] the Householder tridiagonalisation kernel alone; [7] 0 */
   size_t bytes_peak;           /* most device bytes the handle held at once (setup temporaries included) */
+  long long graph_solves;      /* solves run as one CUDA graph (device-side loops); the others were
+                                  driven from the host (kernel timing on, or graph capture unavailable) */
 } hk_info_t;
 
 hk_status hk_info(const hk_handle* h, hk_info_t* info);

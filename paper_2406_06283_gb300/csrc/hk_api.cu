@@ -11,6 +11,7 @@
 
 static thread_local char g_err[512] = "";
 std::atomic<long long> g_hk_launches{0};
+thread_local int g_hk_capture_count = -1;
 
 extern "C" long long hk_kernel_launches(void) { return g_hk_launches.load(); }
 
@@ -100,6 +101,12 @@ static void destroy_all(hk_handle* h) {
   cudaGetDevice(&cur);
   cudaSetDevice(h->dev);
   cudaStreamSynchronize(h->stream);
+  hk_drop_graphs(h);
+  if (h->cap_stream) {
+    cudaStreamSynchronize(h->cap_stream);
+    cudaStreamDestroy(h->cap_stream);
+    h->cap_stream = nullptr;
+  }
   for (auto& a : h->allocs) cudaFreeAsync(a.first, h->stream);
   h->allocs.clear();
   cudaStreamSynchronize(h->stream);
@@ -309,6 +316,7 @@ extern "C" hk_status hk_info(const hk_handle* h, hk_info_t* info) {
   info->lower_nnz = h->lower_nnz;
   for (int i = 0; i < 8; ++i) info->setup_ms[i] = h->setup_ms[i];
   info->bytes_peak = h->bytes_peak;
+  info->graph_solves = h->graph_solves;
   return HK_OK;
 }
 

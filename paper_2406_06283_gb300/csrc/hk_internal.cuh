@@ -6,6 +6,7 @@
 
 #include <atomic>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "hkgeneo.h"
@@ -35,7 +36,14 @@ void hk_set_error(const char* fmt, ...);
 
 // Every kernel launch of the library bumps this process-wide counter (hk_kernel_launches()).
 extern std::atomic<long long> g_hk_launches;
-#define HK_COUNT_LAUNCH() g_hk_launches.fetch_add(1, std::memory_order_relaxed)
+// >= 0 while this thread captures a CUDA graph: captured kernels are counted here, and the graph's
+// executions are added to g_hk_launches after each replay.
+extern thread_local int g_hk_capture_count;
+inline void hk_count_launch() {
+  if (g_hk_capture_count >= 0) ++g_hk_capture_count;
+  else g_hk_launches.fetch_add(1, std::memory_order_relaxed);
+}
+#define HK_COUNT_LAUNCH() hk_count_launch()
 
 #define HK_TRY(expr)                         \
   do {                                       \
@@ -165,6 +173,21 @@ struct hk_handle {
   size_t bytes_peak = 0;
   size_t bytes = 0;
   bool dev_inputs = false;  // setup arrays are device pointers
+  // FGMRES solve as one CUDA graph per (right-hand sides, tol), its cycle and inner-step loops run on
+  // the device by conditional WHILE nodes (see hk_krylov.cu)
+  struct SolveGraph {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int iter_kernels = 0, cycle_kernels = 0;
+  };
+  std::map<std::pair<int, double>, SolveGraph> graphs;
+  bool graphs_ok = true;        // false after a failed graph build: the host-driven loop is used
+  long long graph_solves = 0;
+  cudaStream_t cap_stream = nullptr;  // blocking stream for graphs when the handle's stream is the legacy one
+  int* d_ctl = nullptr;         // [0] inner step j, [1] cycles run, [2] inner steps run
+  const int* g_jp = nullptr;    // while an inner step is captured: the device word holding j
+  long long g_jstride = 0;      // ... and the distance between consecutive Krylov vectors
+
   // kernel timing
   bool timing = false;
   struct TL { int cat; cudaEvent_t a, b; };
@@ -239,6 +262,10 @@ hk_status phase_coarse(hk_handle* h);
 
 // ---- solve-time operations ----
 hk_status ensure_workspace(hk_handle* h, int s);
+// Destroys the cached solve graphs (their kernels hold workspace pointers).
+void hk_drop_graphs(hk_handle* h);
+// Raises the shared-memory limit of every apply kernel instantiation (before any graph capture).
+hk_status apply_prepare(hk_handle* h);
 // z = M^{-1} v for s vectors (v, z: s x n device arrays, FP64).  `active` is NULL or
 // the per-rhs state words (8 ints per rhs, word 0 nonzero = process this rhs).
 hk_status op_apply(hk_handle* h, int s, const double* v, double* z, const int* active);

@@ -62,11 +62,13 @@ hk_status op_matvec(hk_handle* h, int s, const double* x, double* y, const int* 
 // MODE 2: w -= V h2, ||w||^2, then (last CTA) the Hessenberg column, Givens
 // rotation, residual estimate and stopping decision of every active rhs.
 template <int MODE>
-__global__ void k_gs(int n, int s, int m, int j, const double* __restrict__ V, double* w, int* state,
-                     double* rstate, double* hcoef, double* part, unsigned* counter, double* H, double* cs,
-                     double* sn, double* g, double* hist, int max_iters, double tol,
+__global__ void k_gs(int n, int s, int m, int j, const int* __restrict__ jp, const double* __restrict__ V,
+                     double* w, int* state, double* rstate, double* hcoef, double* part, unsigned* counter,
+                     double* H, double* cs, double* sn, double* g, double* hist, int max_iters, double tol,
                      const int* __restrict__ rowptr, const int* __restrict__ col, const double* __restrict__ val,
-                     const double* __restrict__ zj) {
+                     const double* __restrict__ Zk) {
+  if (jp) j = *jp;  // captured inner step: j read on the device
+  const double* zj = Zk + (long long)j * s * n;
   int chunk = (n + gridDim.x - 1) / gridDim.x;
   int l0 = blockIdx.x * chunk, l1 = min(n, l0 + chunk);
   int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -163,10 +165,12 @@ __global__ void k_gs(int n, int s, int m, int j, const double* __restrict__ V, d
   if (tid == 0) *counter = 0u;
 }
 
-__global__ void k_normalize(int n, int s, int j, double* V, const double* __restrict__ w,
-                            const int* __restrict__ state, const double* __restrict__ rstate) {
+__global__ void k_normalize(int n, int s, int j, const int* __restrict__ jp, double* V,
+                            const double* __restrict__ w, const int* __restrict__ state,
+                            const double* __restrict__ rstate) {
   int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n) return;
+  if (jp) j = *jp;
   for (int r = 0; r < s; ++r) {
     if (!state[8 * r + ST_ACTIVE]) continue;
     double inv = 1.0 / rstate[8 * r + RS_HNEXT];
@@ -289,12 +293,47 @@ __global__ void k_zero_rhs_init(int s, int* state, double* rstate) {
   }
 }
 
+// ---- device-side loop control of the graph form.  ctl[0] = inner step j of the cycle, ctl[1] = cycles
+// run, ctl[2] = inner steps run.  Both loops are bounded by counters that only grow: the inner one by
+// j < m, the outer one by the cycle count.
+__global__ void k_ctl_cycle_begin(int* ctl, cudaGraphConditionalHandle inner) {
+  ctl[0] = 0;
+  cudaGraphSetConditional(inner, 1u);  // a nested condition keeps its last value: re-arm it every cycle
+}
+
+__global__ void k_ctl_step_end(int s, const int* __restrict__ state, int* ctl, int m,
+                               cudaGraphConditionalHandle inner) {
+  int j = ++ctl[0];
+  ++ctl[2];
+  int any = 0;
+  for (int r = 0; r < s; ++r) any |= state[8 * r + ST_ACTIVE];
+  cudaGraphSetConditional(inner, (any && j < m) ? 1u : 0u);
+}
+
+__global__ void k_ctl_cycle_end(int s, const int* __restrict__ state, int* ctl, int max_cycles,
+                                cudaGraphConditionalHandle outer) {
+  int c = ++ctl[1];
+  int all = 1;
+  for (int r = 0; r < s; ++r) all &= state[8 * r + ST_DONE] != 0;
+  cudaGraphSetConditional(outer, (!all && c < max_cycles) ? 1u : 0u);
+}
+
+void hk_drop_graphs(hk_handle* h) {
+  for (auto& kv : h->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.g) cudaGraphDestroy(kv.second.g);
+  }
+  h->graphs.clear();
+}
+
 hk_status ensure_workspace(hk_handle* h, int s) {
   int m = h->p.restart;
   if (h->ws_rhs >= s && h->ws_m == m) return HK_OK;
+  hk_drop_graphs(h);
+  HK_TRY(apply_prepare(h));
   void* old[] = {h->d_V, h->d_Zk, h->d_w, h->d_x, h->d_f, h->d_ybuf64, h->d_ybuf32, h->d_c64, h->d_cc64,
                  h->d_c32, h->d_cc32, h->d_part, h->d_counter, h->d_H, h->d_cs, h->d_sn, h->d_g, h->d_hcol,
-                 h->d_state, h->d_rstate, h->d_hist};
+                 h->d_state, h->d_rstate, h->d_hist, h->d_ctl};
   for (void* p : old)
     if (p) dfree(h, p);
   if (h->h_state) cudaFreeHost(h->h_state);
@@ -326,6 +365,7 @@ hk_status ensure_workspace(hk_handle* h, int s) {
   HK_TRY(dalloc(h, &h->d_state, (size_t)s * 8));
   HK_TRY(dalloc(h, &h->d_rstate, (size_t)s * 8));
   HK_TRY(dalloc(h, &h->d_hist, (size_t)s * h->p.max_iters));
+  HK_TRY(dalloc(h, &h->d_ctl, 4));
   HK_CUDA(cudaMallocHost(&h->h_state, sizeof(int) * s * 8));
   HK_CUDA(cudaMallocHost(&h->h_rstate, sizeof(double) * s * 8));
   h->ws_rhs = s;
@@ -333,88 +373,201 @@ hk_status ensure_workspace(hk_handle* h, int s) {
   return HK_OK;
 }
 
-hk_status run_fgmres(hk_handle* h, int s, const double* rhs_dev, double tol, double* u_dev, int32_t* iters,
-                     double* res_hist, double* final_res) {
-  HK_TRY(ensure_workspace(h, s));
+// Residual of x = 0 and per-rhs state; w = f so that every cycle starts from w.
+static hk_status fgmres_init(hk_handle* h, int s, const double* rhs_dev) {
   cudaStream_t st = h->stream;
-  int n = h->n, m = h->p.restart, mi = h->p.max_iters;
+  int n = h->n, mi = h->p.max_iters;
   long long sn_ = (long long)s * n;
   HK_CUDA(cudaMemcpyAsync(h->d_f, rhs_dev, sizeof(double) * sn_, cudaMemcpyDeviceToDevice, st));
+  HK_CUDA(cudaMemcpyAsync(h->d_w, rhs_dev, sizeof(double) * sn_, cudaMemcpyDeviceToDevice, st));
   HK_CUDA(cudaMemsetAsync(h->d_x, 0, sizeof(double) * sn_, st));
   HK_CUDA(cudaMemsetAsync(h->d_hist, 0, sizeof(double) * (size_t)s * mi, st));
   HK_CUDA(cudaMemsetAsync(h->d_state, 0, sizeof(int) * s * 8, st));
   HK_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned) * 8, st));
+  HK_CUDA(cudaMemsetAsync(h->d_ctl, 0, sizeof(int) * 4, st));
   // ||f|| into RS_BETA, then initialise the per-rhs state from it
   k_norm2<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, h->d_f, h->d_state, h->d_rstate, RS_BETA, h->d_part,
                                               h->d_counter, 1); HK_COUNT_LAUNCH();
   k_zero_rhs_init<<<nblk(s, 64), 64, 0, st>>>(s, h->d_state, h->d_rstate); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
-  const double* rvec = h->d_f;  // residual of x = 0
-  int* act = h->d_state;        // ST_ACTIVE is word 0 of each rhs's 8 words
-  while (true) {
-    k_start_cycle<<<nblk(n, 256), 256, 0, st>>>(n, s, m, rvec, h->d_V, h->d_state, h->d_rstate, h->d_g); HK_COUNT_LAUNCH();
-    k_activate<<<nblk(s, 64), 64, 0, st>>>(s, h->d_state); HK_COUNT_LAUNCH();
-    HK_LAUNCH_CHECK();
-    for (int j = 0; j < m; ++j) {
-      double* vj = h->d_V + (long long)j * sn_;
-      double* zj = h->d_Zk + (long long)j * sn_;
-      HK_TRY(op_apply(h, s, vj, zj, act));
-      cudaEvent_t ga = nullptr;
-      if (h->timing) {
-        ga = hk_event(h);
-        cudaEventRecord(ga, st);
-      }
-      k_gs<0><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, m, j, h->d_V, h->d_w, h->d_state, h->d_rstate, h->d_hcol,
-                                                  h->d_part, h->d_counter, h->d_H, h->d_cs, h->d_sn, h->d_g,
-                                                  h->d_hist, mi, tol, h->d_rowptr, h->d_col, h->d_valB, zj); HK_COUNT_LAUNCH();
-      k_gs<1><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, m, j, h->d_V, h->d_w, h->d_state, h->d_rstate, h->d_hcol,
-                                                  h->d_part, h->d_counter, h->d_H, h->d_cs, h->d_sn, h->d_g,
-                                                  h->d_hist, mi, tol, h->d_rowptr, h->d_col, h->d_valB, zj); HK_COUNT_LAUNCH();
-      k_gs<2><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, m, j, h->d_V, h->d_w, h->d_state, h->d_rstate, h->d_hcol,
-                                                  h->d_part, h->d_counter, h->d_H, h->d_cs, h->d_sn, h->d_g,
-                                                  h->d_hist, mi, tol, h->d_rowptr, h->d_col, h->d_valB, zj); HK_COUNT_LAUNCH();
-      k_normalize<<<nblk(n, 256), 256, 0, st>>>(n, s, j, h->d_V, h->d_w, h->d_state, h->d_rstate); HK_COUNT_LAUNCH();
-      if (h->timing) {
-        cudaEvent_t gb = hk_event(h);
-        cudaEventRecord(gb, st);
-        h->tl.push_back({HK_T_ARNOLDI, ga, gb});
-      }
-      HK_LAUNCH_CHECK();
-      HK_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(int) * 8 * s, cudaMemcpyDeviceToHost, st));
-      HK_CUDA(cudaStreamSynchronize(st));
-      bool any = false;
-      for (int r = 0; r < s; ++r) any |= h->h_state[8 * r + ST_ACTIVE] != 0;
-      if (!any) break;
-    }
-    // cycle end: x += Zk y, true residual
-    cudaEvent_t ca = nullptr;
-    if (h->timing) {
-      ca = hk_event(h);
-      cudaEventRecord(ca, st);
-    }
-    k_cycle_solve<<<nblk(s, 64), 64, 0, st>>>(s, m, h->d_state, h->d_H, h->d_g); HK_COUNT_LAUNCH();
-    k_xupdate<<<nblk(n, 256), 256, 0, st>>>(n, s, m, h->d_state, h->d_Zk, h->d_g, h->d_x); HK_COUNT_LAUNCH();
-    k_spmv<<<nblk(n, 256), 256, 0, st>>>(n, s, h->d_rowptr, h->d_col, h->d_valB, h->d_x, h->d_w, nullptr); HK_COUNT_LAUNCH();
-    k_residual<<<nblk(n, 256), 256, 0, st>>>(n, s, h->d_state, h->d_f, h->d_w); HK_COUNT_LAUNCH();
-    k_norm2<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, h->d_w, h->d_state, h->d_rstate, RS_BETA, h->d_part,
-                                                h->d_counter, 1); HK_COUNT_LAUNCH();
-    k_cycle_decide<<<nblk(s, 64), 64, 0, st>>>(s, h->d_state, h->d_rstate, tol, mi); HK_COUNT_LAUNCH();
-    if (h->timing) {
-      cudaEvent_t cb = hk_event(h);
-      cudaEventRecord(cb, st);
-      h->tl.push_back({HK_T_CYCLE, ca, cb});
-    }
-    HK_LAUNCH_CHECK();
-    HK_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(int) * 8 * s, cudaMemcpyDeviceToHost, st));
-    HK_CUDA(cudaStreamSynchronize(st));
-    bool all_done = true;
-    for (int r = 0; r < s; ++r) all_done &= h->h_state[8 * r + ST_DONE] != 0;
-    if (all_done) break;
-    rvec = h->d_w;
+  return HK_OK;
+}
+
+// beta = ||r||, v_0 = r / beta, g = beta e_1 for every rhs not done; activate them.
+static hk_status fgmres_cycle_start(hk_handle* h, int s) {
+  cudaStream_t st = h->stream;
+  int n = h->n, m = h->p.restart;
+  k_start_cycle<<<nblk(n, 256), 256, 0, st>>>(n, s, m, h->d_w, h->d_V, h->d_state, h->d_rstate, h->d_g); HK_COUNT_LAUNCH();
+  k_activate<<<nblk(s, 64), 64, 0, st>>>(s, h->d_state); HK_COUNT_LAUNCH();
+  HK_LAUNCH_CHECK();
+  return HK_OK;
+}
+
+// Inner step j: z_j = M^{-1} v_j, w = B z_j, CGS2, Givens, v_{j+1}.  With jp != NULL every kernel reads
+// j from *jp (the captured form); otherwise j is passed by value.
+static hk_status fgmres_step(hk_handle* h, int s, double tol, int j, const int* jp) {
+  cudaStream_t st = h->stream;
+  int n = h->n, m = h->p.restart, mi = h->p.max_iters;
+  long long sn_ = (long long)s * n;
+  const double* vj = h->d_V + (jp ? 0 : (long long)j * sn_);
+  double* zj = h->d_Zk + (jp ? 0 : (long long)j * sn_);
+  h->g_jp = jp;
+  h->g_jstride = sn_;
+  hk_status rc = op_apply(h, s, vj, zj, h->d_state);
+  h->g_jp = nullptr;
+  HK_TRY(rc);
+  cudaEvent_t ga = nullptr;
+  if (h->timing) {
+    ga = hk_event(h);
+    cudaEventRecord(ga, st);
   }
+  k_gs<0><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, m, j, jp, h->d_V, h->d_w, h->d_state, h->d_rstate, h->d_hcol,
+                                              h->d_part, h->d_counter, h->d_H, h->d_cs, h->d_sn, h->d_g, h->d_hist,
+                                              mi, tol, h->d_rowptr, h->d_col, h->d_valB, h->d_Zk); HK_COUNT_LAUNCH();
+  k_gs<1><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, m, j, jp, h->d_V, h->d_w, h->d_state, h->d_rstate, h->d_hcol,
+                                              h->d_part, h->d_counter, h->d_H, h->d_cs, h->d_sn, h->d_g, h->d_hist,
+                                              mi, tol, h->d_rowptr, h->d_col, h->d_valB, h->d_Zk); HK_COUNT_LAUNCH();
+  k_gs<2><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, m, j, jp, h->d_V, h->d_w, h->d_state, h->d_rstate, h->d_hcol,
+                                              h->d_part, h->d_counter, h->d_H, h->d_cs, h->d_sn, h->d_g, h->d_hist,
+                                              mi, tol, h->d_rowptr, h->d_col, h->d_valB, h->d_Zk); HK_COUNT_LAUNCH();
+  k_normalize<<<nblk(n, 256), 256, 0, st>>>(n, s, j, jp, h->d_V, h->d_w, h->d_state, h->d_rstate); HK_COUNT_LAUNCH();
+  if (h->timing) {
+    cudaEvent_t gb = hk_event(h);
+    cudaEventRecord(gb, st);
+    h->tl.push_back({HK_T_ARNOLDI, ga, gb});
+  }
+  HK_LAUNCH_CHECK();
+  return HK_OK;
+}
+
+// Cycle end: x += Zk y, w = f - B x, ||w||, done / new cycle decision.
+static hk_status fgmres_cycle_end(hk_handle* h, int s, double tol) {
+  cudaStream_t st = h->stream;
+  int n = h->n, m = h->p.restart, mi = h->p.max_iters;
+  cudaEvent_t ca = nullptr;
+  if (h->timing) {
+    ca = hk_event(h);
+    cudaEventRecord(ca, st);
+  }
+  k_cycle_solve<<<nblk(s, 64), 64, 0, st>>>(s, m, h->d_state, h->d_H, h->d_g); HK_COUNT_LAUNCH();
+  k_xupdate<<<nblk(n, 256), 256, 0, st>>>(n, s, m, h->d_state, h->d_Zk, h->d_g, h->d_x); HK_COUNT_LAUNCH();
+  k_spmv<<<nblk(n, 256), 256, 0, st>>>(n, s, h->d_rowptr, h->d_col, h->d_valB, h->d_x, h->d_w, nullptr); HK_COUNT_LAUNCH();
+  k_residual<<<nblk(n, 256), 256, 0, st>>>(n, s, h->d_state, h->d_f, h->d_w); HK_COUNT_LAUNCH();
+  k_norm2<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, h->d_w, h->d_state, h->d_rstate, RS_BETA, h->d_part,
+                                              h->d_counter, 1); HK_COUNT_LAUNCH();
+  k_cycle_decide<<<nblk(s, 64), 64, 0, st>>>(s, h->d_state, h->d_rstate, tol, mi); HK_COUNT_LAUNCH();
+  if (h->timing) {
+    cudaEvent_t cb = hk_event(h);
+    cudaEventRecord(cb, st);
+    h->tl.push_back({HK_T_CYCLE, ca, cb});
+  }
+  HK_LAUNCH_CHECK();
+  return HK_OK;
+}
+
+// Captures the whole solve (after fgmres_init) into one graph:
+//   WHILE (not all done, cycles < max_iters + 2) {            outer, handle c_out
+//     cycle start; j = 0; re-arm c_in
+//     WHILE (some rhs active and j < m) { inner step j; j++ } inner, handle c_in
+//     cycle end
+//   }
+static hk_status build_solve_graph(hk_handle* h, int s, double tol, hk_handle::SolveGraph& G) {
+  cudaStream_t st = h->stream;
+  int m = h->p.restart, max_cycles = h->p.max_iters + 2;
+  cudaGraph_t g = nullptr;
+  HK_CUDA(cudaGraphCreate(&g, 0));
+  G.g = g;
+  cudaGraphConditionalHandle c_out, c_in;
+  HK_CUDA(cudaGraphConditionalHandleCreate(&c_out, g, 1, cudaGraphCondAssignDefault));
+  HK_CUDA(cudaGraphConditionalHandleCreate(&c_in, g, 0, 0));
+  cudaGraphNodeParams po = {};
+  po.type = cudaGraphNodeTypeConditional;
+  po.conditional.handle = c_out;
+  po.conditional.type = cudaGraphCondTypeWhile;
+  po.conditional.size = 1;
+  cudaGraphNode_t n_out;
+  HK_CUDA(cudaGraphAddNode(&n_out, g, nullptr, nullptr, 0, &po));
+  cudaGraph_t body_out = po.conditional.phGraph_out[0];
+  cudaGraph_t body_in = nullptr;
+  hk_status rc = HK_OK;
+  cudaError_t e = cudaStreamBeginCaptureToGraph(st, body_out, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    hk_set_error("graph capture: %s", cudaGetErrorString(e));
+    return HK_CUDA_ERROR;
+  }
+  g_hk_capture_count = 0;
+  rc = fgmres_cycle_start(h, s);
+  if (rc == HK_OK) {
+    k_ctl_cycle_begin<<<1, 1, 0, st>>>(h->d_ctl, c_in);
+    HK_COUNT_LAUNCH();
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+    cudaGraphNodeParams pi = {};
+    pi.type = cudaGraphNodeTypeConditional;
+    pi.conditional.handle = c_in;
+    pi.conditional.type = cudaGraphCondTypeWhile;
+    pi.conditional.size = 1;
+    cudaGraphNode_t n_in = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&n_in, body_out, deps, nullptr, nd, &pi);
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(st, &n_in, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+      body_in = pi.conditional.phGraph_out[0];
+      rc = fgmres_cycle_end(h, s, tol);
+      k_ctl_cycle_end<<<1, 1, 0, st>>>(s, h->d_state, h->d_ctl, max_cycles, c_out);
+      HK_COUNT_LAUNCH();
+    } else {
+      hk_set_error("graph capture: %s", cudaGetErrorString(e));
+      rc = HK_CUDA_ERROR;
+    }
+  }
+  G.cycle_kernels = g_hk_capture_count;
+  cudaGraph_t tmp = nullptr;
+  e = cudaStreamEndCapture(st, &tmp);
+  if (rc == HK_OK && e != cudaSuccess) {
+    hk_set_error("graph capture: %s", cudaGetErrorString(e));
+    rc = HK_CUDA_ERROR;
+  }
+  if (rc == HK_OK) {
+    e = cudaStreamBeginCaptureToGraph(st, body_in, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      hk_set_error("graph capture: %s", cudaGetErrorString(e));
+      rc = HK_CUDA_ERROR;
+    } else {
+      g_hk_capture_count = 0;
+      rc = fgmres_step(h, s, tol, 0, h->d_ctl);
+      k_ctl_step_end<<<1, 1, 0, st>>>(s, h->d_state, h->d_ctl, m, c_in);
+      HK_COUNT_LAUNCH();
+      G.iter_kernels = g_hk_capture_count;
+      e = cudaStreamEndCapture(st, &tmp);
+      if (rc == HK_OK && e != cudaSuccess) {
+        hk_set_error("graph capture: %s", cudaGetErrorString(e));
+        rc = HK_CUDA_ERROR;
+      }
+    }
+  }
+  g_hk_capture_count = -1;
+  if (rc == HK_OK) {
+    e = cudaGraphInstantiate(&G.exec, g, 0);
+    if (e != cudaSuccess) {
+      hk_set_error("graph instantiate: %s", cudaGetErrorString(e));
+      rc = HK_CUDA_ERROR;
+    }
+  }
+  cudaGetLastError();
+  return rc;
+}
+
+static hk_status fgmres_results(hk_handle* h, int s, double* u_dev, int32_t* iters, double* res_hist,
+                                double* final_res, int* ctl_out) {
+  cudaStream_t st = h->stream;
+  int n = h->n, mi = h->p.max_iters;
+  long long sn_ = (long long)s * n;
   HK_CUDA(cudaMemcpyAsync(u_dev, h->d_x, sizeof(double) * sn_, cudaMemcpyDeviceToDevice, st));
   HK_CUDA(cudaMemcpyAsync(h->h_rstate, h->d_rstate, sizeof(double) * 8 * s, cudaMemcpyDeviceToHost, st));
   HK_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(int) * 8 * s, cudaMemcpyDeviceToHost, st));
+  if (ctl_out) HK_CUDA(cudaMemcpyAsync(ctl_out, h->d_ctl, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
   if (res_hist)
     HK_CUDA(cudaMemcpyAsync(res_hist, h->d_hist, sizeof(double) * (size_t)s * mi, cudaMemcpyDeviceToHost, st));
   HK_CUDA(cudaStreamSynchronize(st));
@@ -425,4 +578,66 @@ hk_status run_fgmres(hk_handle* h, int s, const double* rhs_dev, double tol, dou
     allconv &= h->h_state[8 * r + ST_CONV] != 0;
   }
   return allconv ? HK_OK : HK_NO_CONVERGENCE;
+}
+
+hk_status run_fgmres(hk_handle* h, int s, const double* rhs_dev, double tol, double* u_dev, int32_t* iters,
+                     double* res_hist, double* final_res) {
+  HK_TRY(ensure_workspace(h, s));
+  cudaStream_t st = h->stream;
+  int m = h->p.restart;
+  HK_TRY(fgmres_init(h, s, rhs_dev));
+  if (!h->timing && h->graphs_ok) {
+    // one graph launch for the whole solve; the loops run on the device.  The legacy default stream
+    // cannot be captured: then the graph is captured and launched on a private blocking stream, which
+    // the legacy stream orders with the work before and after it.
+    cudaStream_t gs = h->stream;
+    if (gs == nullptr || gs == cudaStreamLegacy) {
+      if (!h->cap_stream) HK_CUDA(cudaStreamCreate(&h->cap_stream));
+      gs = h->cap_stream;
+    }
+    auto key = std::make_pair(s, tol);
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+      hk_handle::SolveGraph G;
+      cudaStream_t user = h->stream;
+      h->stream = gs;
+      hk_status brc = build_solve_graph(h, s, tol, G);
+      h->stream = user;
+      if (brc != HK_OK) {
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+        if (G.g) cudaGraphDestroy(G.g);
+        h->graphs_ok = false;  // keep the kernels, drive the loops from the host
+      } else {
+        it = h->graphs.emplace(key, G).first;
+      }
+    }
+    if (h->graphs_ok) {
+      HK_CUDA(cudaGraphLaunch(it->second.exec, gs));
+      h->graph_solves++;
+      int ctl[4] = {0, 0, 0, 0};
+      hk_status rs = fgmres_results(h, s, u_dev, iters, res_hist, final_res, ctl);
+      g_hk_launches.fetch_add((long long)it->second.cycle_kernels * ctl[1] + (long long)it->second.iter_kernels * ctl[2],
+                              std::memory_order_relaxed);
+      return rs;
+    }
+  }
+  // host-driven loops (kernel timing on, or no graph support): the same kernels
+  while (true) {
+    HK_TRY(fgmres_cycle_start(h, s));
+    for (int j = 0; j < m; ++j) {
+      HK_TRY(fgmres_step(h, s, tol, j, nullptr));
+      HK_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(int) * 8 * s, cudaMemcpyDeviceToHost, st));
+      HK_CUDA(cudaStreamSynchronize(st));
+      bool any = false;
+      for (int r = 0; r < s; ++r) any |= h->h_state[8 * r + ST_ACTIVE] != 0;
+      if (!any) break;
+    }
+    HK_TRY(fgmres_cycle_end(h, s, tol));
+    HK_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(int) * 8 * s, cudaMemcpyDeviceToHost, st));
+    HK_CUDA(cudaStreamSynchronize(st));
+    bool all_done = true;
+    for (int r = 0; r < s; ++r) all_done &= h->h_state[8 * r + ST_DONE] != 0;
+    if (all_done) break;
+  }
+  return fgmres_results(h, s, u_dev, iters, res_hist, final_res, nullptr);
 }

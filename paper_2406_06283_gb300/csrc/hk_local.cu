@@ -268,8 +268,10 @@ __global__ void __launch_bounds__(256) k_local_apply(
     int n, int s_tot, const double* __restrict__ v, const int* __restrict__ active,
     const int* __restrict__ sub_info, const long long* __restrict__ sub_off, const int* __restrict__ Ilev,
     const long long* __restrict__ lvtab, const unsigned char* __restrict__ pack, const T* __restrict__ Zt,
-    int do_local, int do_coarse, long long I_total, int n0, int stage_bytes, T* ybuf, T* cvec, DevStatus* st) {
+    int do_local, int do_coarse, long long I_total, int n0, int stage_bytes, T* ybuf, T* cvec, DevStatus* st,
+    const int* __restrict__ jp, long long jstride) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  if (jp) v += (long long)(*jp) * jstride;  // captured inner step: v = v_j with j read on the device
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int sh_fail;
   unsigned char* stage[2] = {smem_raw, smem_raw + stage_bytes};
@@ -445,9 +447,10 @@ __global__ void k_scatter(int n, int s, const int* __restrict__ pull_ptr, const 
                           const long long* __restrict__ sub_off, const T* __restrict__ ybuf,
                           const T* __restrict__ Z, const T* __restrict__ cc, long long I_total, int n0,
                           int do_local, int do_coarse, int ras, const int* __restrict__ mu, double* z,
-                          const int* __restrict__ active) {
+                          const int* __restrict__ active, const int* __restrict__ jp, long long jstride) {
   int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n) return;
+  if (jp) z += (long long)(*jp) * jstride;  // captured inner step: z = z_j
   int p0 = pull_ptr[l], p1 = pull_ptr[l + 1];
   T wl = ras ? (T)1 / (T)mu[l] : (T)1;
   for (int r = 0; r < s; ++r) {
@@ -484,7 +487,8 @@ static hk_status launch_local(hk_handle* h, int s, const double* v, const int* a
   HK_TIMED(h, HK_T_LOCAL_APPLY,
            (k_local_apply<T, NR><<<grid, 256, shm, h->stream>>>(
                h->n, s, v, active, h->d_sub_info, h->d_sub_off, h->d_I, h->d_lvtab, h->d_pack, Zt, do_local,
-               do_coarse, h->I_total, h->n0, (int)h->pack_stage, ybuf, cvec, h->d_status))); HK_COUNT_LAUNCH();
+               do_coarse, h->I_total, h->n0, (int)h->pack_stage, ybuf, cvec, h->d_status, h->g_jp,
+               h->g_jstride))); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   return HK_OK;
 }
@@ -517,8 +521,21 @@ static hk_status apply_t(hk_handle* h, int s, const double* v, double* z, const 
   HK_TIMED(h, HK_T_SCATTER,
            (k_scatter<T><<<nblk(h->n, 128), 128, 0, h->stream>>>(
                h->n, s, h->d_pull_ptr, h->d_pull_row, h->d_pull_sub, h->d_sub_info, h->d_sub_off, ybuf, Zr, cc,
-               h->I_total, h->n0, do_local, do_coarse, h->p.weighting == HK_RAS_POU, h->d_mu, z, active))); HK_COUNT_LAUNCH();
+               h->I_total, h->n0, do_local, do_coarse, h->p.weighting == HK_RAS_POU, h->d_mu, z, active, h->g_jp,
+               h->g_jstride))); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
+  return HK_OK;
+}
+
+hk_status apply_prepare(hk_handle*) {
+  HK_TRY(hk_allow_smem(k_local_apply<float, 1>));
+  HK_TRY(hk_allow_smem(k_local_apply<float, 2>));
+  HK_TRY(hk_allow_smem(k_local_apply<float, 4>));
+  HK_TRY(hk_allow_smem(k_local_apply<float, 8>));
+  HK_TRY(hk_allow_smem(k_local_apply<double, 1>));
+  HK_TRY(hk_allow_smem(k_local_apply<double, 2>));
+  HK_TRY(hk_allow_smem(k_local_apply<double, 4>));
+  HK_TRY(hk_allow_smem(k_local_apply<double, 8>));
   return HK_OK;
 }
 

@@ -51,7 +51,7 @@ class hk_info_t(C.Structure):
                 ("max_level", C.c_int), ("max_dof", C.c_int), ("nnz", C.c_int), ("precision", C.c_int),
                 ("levels", C.c_int), ("bytes_resident", C.c_size_t), ("factor_elems", C.c_longlong),
                 ("dof_total", C.c_longlong), ("coarse_elems", C.c_longlong), ("lower_nnz", C.c_longlong),
-                ("setup_ms", C.c_double * 8), ("bytes_peak", C.c_size_t)]
+                ("setup_ms", C.c_double * 8), ("bytes_peak", C.c_size_t), ("graph_solves", C.c_longlong)]
 
 
 class hk_request_info(C.Structure):

@@ -213,6 +213,27 @@ def test_multi_rhs_equals_single():
         np.testing.assert_array_equal(alone.u[0], together.u[r])
 
 
+def test_graph_solve_equals_host_driven_solve():
+    """The solve runs as one CUDA graph whose cycle and inner-step loops are conditional WHILE nodes;
+    with kernel timing on, the same kernels are driven from the host loop.  Both give the same bits,
+    for repeated solves (the cached graph), a second tolerance (a second graph) and several rhs."""
+    p = CASES["h40_p4_k18_ov2"]
+    for precision in (hk.HK_FP64, hk.HK_FP32_PRECOND):
+        h = hk.setup_problem(p, precision=precision)
+        rhs = np.stack([W.normal(W.stream_seed(91, r), p.mesh.n_dofs) for r in range(3)])
+        for tol in (1e-8, 1e-6, 1e-8):
+            g = hk.hk_solve(h, rhs, tol)
+            hk.hk_set_timing(h, True)
+            l = hk.hk_solve(h, rhs, tol)
+            hk.hk_set_timing(h, False)
+            np.testing.assert_array_equal(g.iters, l.iters)
+            np.testing.assert_array_equal(g.u, l.u)
+            np.testing.assert_array_equal(g.history, l.history)
+            np.testing.assert_array_equal(g.true_rel_res, l.true_rel_res)
+        assert hk.hk_info(h)["graph_solves"] == 3
+        hk.hk_destroy(h)
+
+
 def test_errors_are_reported():
     from oracle import fem
     p = W.small_problem(cells=8, parts=1, k=1.0, overlap=1)
