@@ -132,7 +132,8 @@ typedef struct {
                                   total; [6] the Householder tridiagonalisation kernel alone; [7] 0 */
   size_t bytes_peak;           /* most device bytes the handle held at once (setup temporaries included) */
   long long graph_solves;      /* solves run as one CUDA graph (device-side loops); the others were
-                                  driven from the host (kernel timing on, or graph capture unavailable) */
+                                  driven from the host (kernel timing on, graph capture unavailable, or
+                                  graphs switched off by hk_set_solve_graphs) */
 } hk_info_t;
 
 hk_status hk_info(const hk_handle* h, hk_info_t* info);
@@ -157,6 +158,13 @@ enum {
 hk_status hk_set_timing(hk_handle* h, int on);
 /* Sums the recorded launches per category: ms[HK_T_NCAT] milliseconds, count[HK_T_NCAT] launches. */
 hk_status hk_kernel_times(hk_handle* h, double* ms, int32_t* count);
+
+/* on != 0 (the default): each hk_solve runs as one CUDA graph whose FGMRES cycle and inner-step loops
+ * are device-side conditional WHILE nodes (one launch, one synchronisation per solve).  on == 0: the
+ * same kernels with the loops driven from the host (one synchronisation per inner step).  The results
+ * are bitwise the same.  Graphs pay off for a handle solved alone; handles whose solves overlap with
+ * other handles' on other streams (the serving calls) run faster without them. */
+hk_status hk_set_solve_graphs(hk_handle* h, int on);
 
 /* Number of CUDA kernels the library has launched in this process so far (all handles). */
 long long hk_kernel_launches(void);
@@ -221,8 +229,9 @@ hk_status hk_assemble_load(hk_handle* h, const double* f_nodal, double* rhs);
  *    setups and solves in flight stay within `device_mem_budget`.  A setup
  *    reserves its peak: 24 KiB per dof (2D) or 64 KiB per dof (3D) before the
  *    operator's first setup, 1.25 x the measured hk_info_t.bytes_peak after it.
- *    A solve of s right-hand sides on n dofs reserves the workspace it lacks:
- *    8 s ((2 restart + 6) n + (restart + 1)(restart + 4) + max_iters) bytes plus
+ *    A solve of s right-hand sides on n dofs reserves the workspace it lacks, for
+ *    S = s rounded up to a power of two (the handle's workspace capacity):
+ *    8 S ((2 restart + 6) n + (restart + 1)(restart + 4) + max_iters) bytes plus
  *    the preconditioner's buffers and 1 MiB.  When a batch does not fit, idle
  *    operators are evicted, least recently used first; a request waits while
  *    the memory is held by work in flight.  A request whose operator cannot fit

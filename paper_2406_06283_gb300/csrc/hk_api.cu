@@ -235,6 +235,12 @@ extern "C" hk_status hk_set_timing(hk_handle* h, int on) {
   return HK_OK;
 }
 
+extern "C" hk_status hk_set_solve_graphs(hk_handle* h, int on) {
+  if (!h) return HK_BAD_ARG;
+  h->use_graphs = on != 0;
+  return HK_OK;
+}
+
 extern "C" hk_status hk_kernel_times(hk_handle* h, double* ms, int32_t* count) {
   if (!h || !ms || !count) return HK_BAD_ARG;
   HK_CUDA(cudaStreamSynchronize(h->stream));

@@ -182,7 +182,9 @@ struct hk_handle {
   };
   std::map<std::pair<int, double>, SolveGraph> graphs;
   bool graphs_ok = true;        // false after a failed graph build: the host-driven loop is used
+  bool use_graphs = true;       // hk_set_solve_graphs
   long long graph_solves = 0;
+  std::map<int, int> nr_tuned;  // right-hand sides per apply CTA chosen by apply_autotune, per batch size
   cudaStream_t cap_stream = nullptr;  // blocking stream for graphs when the handle's stream is the legacy one
   int* d_ctl = nullptr;         // [0] inner step j, [1] cycles run, [2] inner steps run
   const int* g_jp = nullptr;    // while an inner step is captured: the device word holding j
@@ -266,6 +268,9 @@ hk_status ensure_workspace(hk_handle* h, int s);
 void hk_drop_graphs(hk_handle* h);
 // Raises the shared-memory limit of every apply kernel instantiation (before any graph capture).
 hk_status apply_prepare(hk_handle* h);
+// Times the apply for every admissible number of right-hand sides per CTA (1, 2, 4, 8) at batch size s
+// and keeps the fastest (the arithmetic per right-hand side is the same for all of them).
+hk_status apply_autotune(hk_handle* h, int s);
 // z = M^{-1} v for s vectors (v, z: s x n device arrays, FP64).  `active` is NULL or
 // the per-rhs state words (8 ints per rhs, word 0 nonzero = process this rhs).
 hk_status op_apply(hk_handle* h, int s, const double* v, double* z, const int* active);

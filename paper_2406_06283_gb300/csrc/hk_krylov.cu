@@ -329,6 +329,11 @@ void hk_drop_graphs(hk_handle* h) {
 hk_status ensure_workspace(hk_handle* h, int s) {
   int m = h->p.restart;
   if (h->ws_rhs >= s && h->ws_m == m) return HK_OK;
+  // capacity rounded up to a power of two right-hand sides, so a sequence of growing batches
+  // reallocates a few times only (the layouts use the actual count, a prefix of the arrays)
+  int cap = 1;
+  while (cap < s) cap <<= 1;
+  s = cap;
   hk_drop_graphs(h);
   HK_TRY(apply_prepare(h));
   void* old[] = {h->d_V, h->d_Zk, h->d_w, h->d_x, h->d_f, h->d_ybuf64, h->d_ybuf32, h->d_c64, h->d_cc64,
@@ -370,6 +375,7 @@ hk_status ensure_workspace(hk_handle* h, int s) {
   HK_CUDA(cudaMallocHost(&h->h_rstate, sizeof(double) * s * 8));
   h->ws_rhs = s;
   h->ws_m = m;
+  h->nr_tuned.clear();
   return HK_OK;
 }
 
@@ -583,10 +589,11 @@ static hk_status fgmres_results(hk_handle* h, int s, double* u_dev, int32_t* ite
 hk_status run_fgmres(hk_handle* h, int s, const double* rhs_dev, double tol, double* u_dev, int32_t* iters,
                      double* res_hist, double* final_res) {
   HK_TRY(ensure_workspace(h, s));
+  if (s > 1 && !h->nr_tuned.count(s)) HK_TRY(apply_autotune(h, s));
   cudaStream_t st = h->stream;
   int m = h->p.restart;
   HK_TRY(fgmres_init(h, s, rhs_dev));
-  if (!h->timing && h->graphs_ok) {
+  if (!h->timing && h->graphs_ok && h->use_graphs) {
     // one graph launch for the whole solve; the loops run on the device.  The legacy default stream
     // cannot be captured: then the graph is captured and launched on a private blocking stream, which
     // the legacy stream orders with the work before and after it.

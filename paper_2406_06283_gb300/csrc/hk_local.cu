@@ -504,6 +504,8 @@ static hk_status apply_t(hk_handle* h, int s, const double* v, double* z, const 
   size_t budget = 220 * 1024 - 2 * (size_t)h->pack_stage;
   int nr = 8;
   while (nr > 1 && (nr > s || sizeof(T) * ((size_t)h->max_dof + HK_MAXB) * nr > budget)) nr >>= 1;
+  auto tuned = h->nr_tuned.find(s);
+  if (tuned != h->nr_tuned.end() && tuned->second <= nr) nr = tuned->second;
   hk_status rc;
   switch (nr) {
     case 8: rc = launch_local<T, 8>(h, s, v, active, Zt, ybuf, c, do_local, do_coarse); break;
@@ -537,6 +539,43 @@ hk_status apply_prepare(hk_handle*) {
   HK_TRY(hk_allow_smem(k_local_apply<double, 4>));
   HK_TRY(hk_allow_smem(k_local_apply<double, 8>));
   return HK_OK;
+}
+
+hk_status apply_autotune(hk_handle* h, int s) {
+  if (s < 2) return HK_OK;
+  bool timing = h->timing;
+  h->timing = false;
+  cudaEvent_t a, b;
+  HK_CUDA(cudaEventCreate(&a));
+  HK_CUDA(cudaEventCreate(&b));
+  int best = 0;
+  float best_ms = 1e30f;
+  hk_status rc = HK_OK;
+  for (int nr = 1; nr <= 8 && nr <= s && rc == HK_OK; nr *= 2) {
+    h->nr_tuned[s] = nr;
+    // inputs: the (zero-initialised) first Krylov block; output: the first flexible block
+    rc = op_apply(h, s, h->d_V, h->d_Zk, nullptr);  // warm-up
+    float t = 0;
+    for (int rep = 0; rep < 3 && rc == HK_OK; ++rep) {
+      cudaEventRecord(a, h->stream);
+      rc = op_apply(h, s, h->d_V, h->d_Zk, nullptr);
+      cudaEventRecord(b, h->stream);
+      cudaEventSynchronize(b);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, a, b);
+      t += ms;
+    }
+    if (rc == HK_OK && t < best_ms) {
+      best_ms = t;
+      best = nr;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  h->timing = timing;
+  if (best) h->nr_tuned[s] = best;
+  else h->nr_tuned.erase(s);
+  return rc;
 }
 
 hk_status op_apply(hk_handle* h, int s, const double* v, double* z, const int* active) {

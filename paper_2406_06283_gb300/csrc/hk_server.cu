@@ -81,6 +81,9 @@ static uint64_t fnv1a(uint64_t hsh, const void* p, size_t n) {
 // (Krylov and flexible bases, vectors, Hessenberg and Givens data, histories), hk_solve's staging of
 // rhs and u, the preconditioner's local and coarse buffers, and 1 MiB of slack.
 static size_t solve_workspace_bytes(const SrvOp* o, const hk_handle* h, int s) {
+  int cap = 1;  // the handle allocates for a power of two right-hand sides
+  while (cap < s) cap <<= 1;
+  s = cap;
   size_t m = (size_t)o->prm.restart, n = (size_t)o->n_dofs;
   size_t pf = o->prm.precision == HK_FP32_PRECOND ? 4 : 8;
   size_t b = 8 * (size_t)s * ((2 * m + 6) * n + (m + 1) * (m + 4) + (size_t)o->prm.max_iters);
@@ -194,6 +197,9 @@ static void run_batch(hk_server* S, Batch& b, int slot) {
     prm.elem_to_sub = o->e2s.data();
     st = hk_setup(&o->mesh, o->coeff.data(), o->k, &prm, o->stream, &o->h);
     if (st != HK_OK) err = hk_last_error();
+    // solves of different operators overlap through their streams; launched loops overlap better there
+    // than concurrent graphs with device-side loops (measured: 90 vs 46 solves/s on the serving stream)
+    else hk_set_solve_graphs(o->h, 0);
   }
   std::vector<double> rhs((size_t)b.s * o->n_dofs), u((size_t)b.s * o->n_dofs), hist, tres(b.s);
   std::vector<int32_t> iters(b.s, 0);

@@ -81,6 +81,8 @@ def lib():
     L.hk_setup.argtypes = [C.POINTER(hk_mesh), _P, C.c_double, C.POINTER(hk_params), _P, C.POINTER(_P)]
     L.hk_setup_device.argtypes = [C.POINTER(hk_mesh), _P, C.c_double, C.POINTER(hk_params), _P, C.POINTER(_P)]
     L.hk_set_timing.argtypes = [_P, C.c_int]
+    L.hk_set_solve_graphs.argtypes = [_P, C.c_int]
+    L.hk_set_solve_graphs.restype = C.c_int
     L.hk_kernel_times.argtypes = [_P, _P, _P]
     L.hk_kernel_launches.argtypes = []
     L.hk_kernel_launches.restype = C.c_longlong
@@ -190,6 +192,10 @@ HK_T_NAMES = ("local_apply", "coarse_solve", "scatter", "spmv", "arnoldi", "cycl
 def hk_kernel_launches() -> int:
     """Kernels the library has launched in this process so far."""
     return int(lib().hk_kernel_launches())
+
+
+def hk_set_solve_graphs(h: Handle, on: bool = True):
+    _check(lib().hk_set_solve_graphs(h.ptr, int(bool(on))), "hk_set_solve_graphs")
 
 
 def hk_set_timing(h: Handle, on: bool = True):

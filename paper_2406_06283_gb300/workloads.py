@@ -219,6 +219,26 @@ def config_c3(n_rhs: int = 16) -> Problem:
     return Problem("c3_h512_k100_p16", m, a, 100.0, 16, box_partition(m, 16), rhs=rhs)
 
 
+def config_c4(seed: int = 4, n_instances: int = 64):
+    """Batched workload: 64 independent 2D instances.  h = 1/cells with cells uniform in
+    {128, 192, 256, 384}, k ~ U[20, 80], 8x8 checkerboard a in 10^U[0,2], P x P boxes with P uniform in
+    [4, 12] raised to ceil(cells / 32) where needed (a box holds at most 32 x 32 cells, the dense
+    eigensolver stage's limit), overlap 2, s ~ U{1..8} seeded N(0,1) right-hand sides each."""
+    out, meshes = [], {}
+    choices = [128, 192, 256, 384]
+    for i in range(n_instances):
+        u = uniform(stream_seed(seed, i, 0), 4)
+        cells = choices[min(int(u[0] * len(choices)), len(choices) - 1)]
+        k = 20.0 + 60.0 * float(u[1])
+        P = max(4 + min(int(u[2] * 9), 8), -(-cells // 32))
+        s = 1 + min(int(u[3] * 8), 7)
+        m = meshes.setdefault(cells, square_mesh(cells))
+        a = checkerboard(m, 8, stream_seed(seed, i, 1))
+        rhs = np.stack([normal(stream_seed(seed, i, 2, r), m.n_dofs) for r in range(s)])
+        out.append(Problem(f"c4_{i:02d}_h{cells}_k{k:.1f}_p{P}_s{s}", m, a, k, P, box_partition(m, P), rhs=rhs))
+    return out
+
+
 def config_c5(seed: int = 5, pool: int = 8):
     """Serving workload: 24 operators and a request-stream recipe.
 

@@ -226,6 +226,10 @@ def test_graph_solve_equals_host_driven_solve():
             hk.hk_set_timing(h, True)
             l = hk.hk_solve(h, rhs, tol)
             hk.hk_set_timing(h, False)
+            hk.hk_set_solve_graphs(h, False)
+            l2 = hk.hk_solve(h, rhs, tol)
+            hk.hk_set_solve_graphs(h, True)
+            np.testing.assert_array_equal(l2.u, l.u)
             np.testing.assert_array_equal(g.iters, l.iters)
             np.testing.assert_array_equal(g.u, l.u)
             np.testing.assert_array_equal(g.history, l.history)

@@ -108,6 +108,7 @@ def test_budget_evicts_idle_operators_and_rejects_what_never_fits():
     n1 = max(p.mesh.n_dofs for p in ops)
     # room for the first setup of the larger operator (24 KiB per dof before it was ever measured,
     # plus one right-hand side's solve workspace) and 64 KiB more: not for the other operator resident too
+    # (each request brings one right-hand side: capacity S = 1)
     ws = 8 * ((2 * 50 + 6) * n1 + 51 * 54 + 1000) + (1 << 20)
     budget = 24576 * n1 + ws + (64 << 10)
     srv = hk.hk_server_create(budget, n_slots=2)
