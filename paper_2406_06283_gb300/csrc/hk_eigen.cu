@@ -40,6 +40,7 @@ static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 #define HK_REFINE_STEPS 5
 #define HK_GUARD 2
 #define HK_MAX_BLOCK (HK_MAX_CLUSTER + HK_GUARD)
+#define HK_SCHUR_DINV 1024
 
 // ---- 1. B^N on Gamma x Gamma: element sums over the subdomain's elements.
 __global__ void k_gamma_block(int dim, int ne, const double* __restrict__ xyz, const int* __restrict__ elems,
@@ -91,6 +92,8 @@ __global__ void k_schur(const int* __restrict__ sub_info, const long long* __res
                         const int* __restrict__ lcol, const double* __restrict__ lvalB,
                         const long long* __restrict__ wsW, const long long* __restrict__ wsG,
                         const long long* __restrict__ wsR, int* ring_ws, double* ws, DevStatus* st) {
+  __shared__ double sh_piv[2];
+  __shared__ double dinv[HK_SCHUR_DINV];  // reciprocal Cholesky diagonal of B^N_GG
   __shared__ int shi[32];
   __shared__ int nR_sh;
   int s = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
@@ -119,18 +122,28 @@ __global__ void k_schur(const int* __restrict__ sub_info, const long long* __res
   __syncthreads();
   int nR = nR_sh;
   if (nG == 0 || nR == 0) return;
-  // Cholesky of BGG in place (lower), right-looking
+  // Cholesky of BGG in place (lower), right-looking.  The pivot's square root and reciprocal are
+  // computed once, by thread 0 (FP64 division and square root are slow: per thread they would fill
+  // the FP64 pipe), and kept for the triangular solves below.
   for (int k = 0; k < nG; ++k) {
-    double piv = BG[(long long)k * nG + k];
-    if (piv <= 0.0) {
-      if (tid == 0) dev_fail(st, HK_EIG_FAIL, s, piv);
+    if (tid == 0) {
+      double piv = BG[(long long)k * nG + k];
+      sh_piv[0] = piv;
+      if (piv > 0.0) {
+        double lkk = sqrt(piv), il = 1.0 / lkk;
+        BG[(long long)k * nG + k] = lkk;
+        sh_piv[1] = il;
+        if (k < HK_SCHUR_DINV) dinv[k] = il;
+      }
+    }
+    __syncthreads();
+    if (!(sh_piv[0] > 0.0)) {
+      if (tid == 0) dev_fail(st, HK_EIG_FAIL, s, sh_piv[0]);
       return;
     }
-    double lkk = sqrt(piv);
+    double il = sh_piv[1];
+    for (int i = k + 1 + tid; i < nG; i += T) BG[(long long)i * nG + k] *= il;
     __syncthreads();
-    for (int i = k + 1 + tid; i < nG; i += T) BG[(long long)i * nG + k] /= lkk;
-    __syncthreads();
-    if (tid == 0) BG[(long long)k * nG + k] = lkk;
     for (int i = k + 1 + (tid >> 5); i < nG; i += T >> 5) {
       double lik = BG[(long long)i * nG + k];
       for (int j = k + 1 + (tid & 31); j <= i; j += 32) BG[(long long)i * nG + j] -= lik * BG[(long long)j * nG + k];
@@ -151,12 +164,12 @@ __global__ void k_schur(const int* __restrict__ sub_info, const long long* __res
     for (int i = 0; i < nG; ++i) {
       double v = R[(long long)i * nR + r];
       for (int k = 0; k < i; ++k) v -= BG[(long long)i * nG + k] * R[(long long)k * nR + r];
-      R[(long long)i * nR + r] = v / BG[(long long)i * nG + i];
+      R[(long long)i * nR + r] = i < HK_SCHUR_DINV ? v * dinv[i] : v / BG[(long long)i * nG + i];
     }
     for (int i = nG - 1; i >= 0; --i) {
       double v = R[(long long)i * nR + r];
       for (int k = i + 1; k < nG; ++k) v -= BG[(long long)k * nG + i] * R[(long long)k * nR + r];
-      R[(long long)i * nR + r] = v / BG[(long long)i * nG + i];
+      R[(long long)i * nR + r] = i < HK_SCHUR_DINV ? v * dinv[i] : v / BG[(long long)i * nG + i];
     }
   }
   __syncthreads();
@@ -204,18 +217,27 @@ __global__ void k_dchol(const int* __restrict__ sub_info, const long long* __res
     }
   }
   __syncthreads();
+  __shared__ double sh_piv[2];
   for (int k = 0; k < nI; ++k) {
-    double piv = Lb[(long long)k * ld + bw];
-    if (!(piv > 0.0)) {
-      if (tid == 0) dev_fail(st, HK_EIG_FAIL, s, piv);
+    // pivot square root and reciprocal once, by thread 0 (see k_schur)
+    if (tid == 0) {
+      double piv = Lb[(long long)k * ld + bw];
+      sh_piv[0] = piv;
+      if (piv > 0.0) {
+        double lkk = sqrt(piv);
+        Lb[(long long)k * ld + bw] = lkk;
+        sh_piv[1] = 1.0 / lkk;
+      }
+    }
+    __syncthreads();
+    if (!(sh_piv[0] > 0.0)) {
+      if (tid == 0) dev_fail(st, HK_EIG_FAIL, s, sh_piv[0]);
       return;
     }
-    double lkk = sqrt(piv);
+    double il = sh_piv[1];
     int iend = min(nI - 1, k + bw);
+    for (int i = k + 1 + tid; i <= iend; i += T) Lb[(long long)i * ld + (k - i + bw)] *= il;
     __syncthreads();
-    for (int i = k + 1 + tid; i <= iend; i += T) Lb[(long long)i * ld + (k - i + bw)] /= lkk;
-    __syncthreads();
-    if (tid == 0) Lb[(long long)k * ld + bw] = lkk;
     for (int i = k + 1 + (tid >> 5); i <= iend; i += T >> 5) {
       double lik = Lb[(long long)i * ld + (k - i + bw)];
       for (int j = k + 1 + (tid & 31); j <= i; j += 32)

@@ -432,12 +432,15 @@ __device__ inline void gauss_jordan_inverse(double* A, int b, int* piv, double* 
         A[p * b + c] = t;
       }
     __syncthreads();
-    double pv = A[k * b + k];
-    if (fabs(pv) < pivot_floor) pv = pv < 0 ? -pivot_floor : pivot_floor;
-    double inv = pv != 0.0 ? 1.0 / pv : 0.0;
+    // the reciprocal pivot once, by thread 0 (an FP64 division per thread would fill the FP64 pipe)
+    if (tid == 0) {
+      double pv = A[k * b + k];
+      if (fabs(pv) < pivot_floor) pv = pv < 0 ? -pivot_floor : pivot_floor;
+      red_v[0] = pv != 0.0 ? 1.0 / pv : 0.0;
+      A[k * b + k] = 1.0;
+    }
     __syncthreads();
-    if (tid == 0) A[k * b + k] = 1.0;
-    __syncthreads();
+    double inv = red_v[0];
     for (int c = tid; c < b; c += T) A[k * b + c] *= inv;
     __syncthreads();
     // eliminate column k from every other row

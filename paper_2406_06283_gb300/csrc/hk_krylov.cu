@@ -21,7 +21,7 @@ static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 // state words per rhs
 enum { ST_ACTIVE = 0, ST_DONE = 1, ST_ITERS = 2, ST_JD = 3, ST_CONV = 4 };
 // real state per rhs
-enum { RS_NF = 0, RS_HNEXT = 1, RS_EST = 2, RS_TRUE = 3, RS_BETA = 4 };
+enum { RS_NF = 0, RS_HNEXT = 1, RS_EST = 2, RS_TRUE = 3, RS_BETA = 4, RS_HINV = 5 };
 
 __device__ __forceinline__ bool last_block(unsigned* counter) {
   __shared__ bool amlast;
@@ -122,7 +122,11 @@ __global__ void k_gs(int n, int s, int m, int j, const int* __restrict__ jp, con
     if (lane == 0) {
       if (MODE == 0) hcoef[(long long)r * 2 * (m + 1) + i] = acc;
       else if (MODE == 1) hcoef[(long long)r * 2 * (m + 1) + (m + 1) + i] = acc;
-      else rstate[8 * r + RS_HNEXT] = sqrt(acc);
+      else {
+        double hn = sqrt(acc);
+        rstate[8 * r + RS_HNEXT] = hn;
+        rstate[8 * r + RS_HINV] = hn > 0.0 ? 1.0 / hn : 0.0;  // once here, not per entry in k_normalize
+      }
     }
   }
   if (MODE == 2) {
@@ -173,7 +177,7 @@ __global__ void k_normalize(int n, int s, int j, const int* __restrict__ jp, dou
   if (jp) j = *jp;
   for (int r = 0; r < s; ++r) {
     if (!state[8 * r + ST_ACTIVE]) continue;
-    double inv = 1.0 / rstate[8 * r + RS_HNEXT];
+    double inv = rstate[8 * r + RS_HINV];
     V[((long long)(j + 1) * s + r) * n + l] = w[(long long)r * n + l] * inv;
   }
 }
