@@ -805,17 +805,16 @@ __device__ void jacobi_eig(double* A, double* U, double* w, int p) {
 }
 
 // Deterministic block-wide dot product of two device vectors.
-// Warp-level pieces of the refinement (one warp per candidate cluster).
-__device__ __forceinline__ double warp_dot(const double* x, const double* y, int n, int lane) {
+__device__ double block_dot(const double* x, const double* y, int n, double* red) {
   double acc = 0;
-  for (int i = lane; i < n; i += 32) acc += x[i] * y[i];
-  return warp_sum(acc);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += x[i] * y[i];
+  return block_sum(acc, red);
 }
 
-__device__ void o_matvec_w(int nO, int oo, int maxrow, const int* ocnt, const int* ocol, const double* oB,
-                           const double* oC, double shift, int use_B, const double* X, double* Y, int p,
-                           int lane) {
-  for (int e = lane; e < nO * p; e += 32) {
+// y = M x for the sparse ovdof matrix M = (which ? C : B^N) - shift C, p vectors (rows in level order).
+__device__ void o_matvec(int nO, int oo, int maxrow, const int* ocnt, const int* ocol, const double* oB,
+                         const double* oC, double shift, int use_B, const double* X, double* Y, int p) {
+  for (int e = threadIdx.x; e < nO * p; e += blockDim.x) {
     int t = e / nO, a = e % nO;
     long long base = (long long)(oo + a) * maxrow;
     int c = min(ocnt[oo + a], maxrow);
@@ -828,113 +827,62 @@ __device__ void o_matvec_w(int nO, int oo, int maxrow, const int* ocnt, const in
   }
 }
 
-// In-place Gauss-Jordan inverse of the b x b row-major A by one warp, partial pivoting (largest |entry|,
-// ties to the smallest row: the same pivots, hence the same arithmetic, as the block version), pivots
-// below pivot_floor replaced by +-pivot_floor.  minpiv (lane-uniform) receives the smallest |pivot|.
-__device__ void gj_inverse_warp(double* A, int b, int* piv, double& minpiv, double pivot_floor, int lane) {
-  for (int k = 0; k < b; ++k) {
-    double best = -1.0;
-    int bi = k;
-    for (int i = k + lane; i < b; i += 32) {
-      double v = fabs(A[i * b + k]);
-      if (v > best) { best = v; bi = i; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_xor_sync(0xffffffffu, best, o);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    if (lane == 0) piv[k] = bi;
-    minpiv = fmin(minpiv, best);
-    if (bi != k)
-      for (int c = lane; c < b; c += 32) {
-        double t = A[k * b + c];
-        A[k * b + c] = A[bi * b + c];
-        A[bi * b + c] = t;
-      }
-    __syncwarp();
-    double pv = A[k * b + k];
-    if (fabs(pv) < pivot_floor) pv = pv < 0 ? -pivot_floor : pivot_floor;
-    double inv = pv != 0.0 ? 1.0 / pv : 0.0;
-    __syncwarp();
-    for (int c = lane; c < b; c += 32) A[k * b + c] = (c == k ? 1.0 : A[k * b + c]) * inv;
-    __syncwarp();
-    // eliminate column k from every other row (row k and column k are only read here)
-    {
-      int i = lane / b, c = lane % b;
-      for (int e = lane; e < b * b; e += 32) {
-        if (i != k && c != k) A[i * b + c] -= A[i * b + k] * A[k * b + c];
-        c += 32;
-        while (c >= b) { c -= b; ++i; }
-      }
-    }
-    __syncwarp();
-    for (int i = lane; i < b; i += 32)
-      if (i != k) A[i * b + k] = -A[i * b + k] * A[k * b + k];
-    __syncwarp();
-  }
-  for (int k = b - 1; k >= 0; --k) {
-    int p = piv[k];
-    if (p != k)
-      for (int r = lane; r < b; r += 32) {
-        double t = A[r * b + k];
-        A[r * b + k] = A[r * b + p];
-        A[r * b + p] = t;
-      }
-    __syncwarp();
-  }
-}
-
-// ---- 9. FP64 refinement of one cluster of candidates per warp.  Block LU of M = B^N - sigma C over
-// the ovdof level sets (sigma = the cluster's mean candidate), HK_REFINE_STEPS steps of block inverse
-// iteration X <- M^{-1} C X with C-orthonormalisation (the cluster plus HK_GUARD guard vectors), then
-// Rayleigh-Ritz on B^N; the window of Ritz values closest to the candidates is kept.  Per-warp shared
-// memory: [tv: max_b x pmax][S: max_b^2 if it fits][H, U: pmax^2 each][w: pmax][piv: max_b ints].
-__global__ void k_refine_w(const int* __restrict__ items, int n_items, const double* __restrict__ sigmas,
-                           const int* __restrict__ sub_info, const int* __restrict__ o_off,
-                           const int* __restrict__ O_levptr, const int* __restrict__ O_L, int maxrow,
-                           const int* __restrict__ ocnt, const int* __restrict__ ocol, const double* __restrict__ oB,
-                           const double* __restrict__ oC, const int* __restrict__ o2i,
-                           const long long* __restrict__ f_off, const long long* __restrict__ x_off, double* F,
-                           double* Xw, const long long* __restrict__ poff, double* P,
-                           const double* __restrict__ lam_hat, double* lam_ref, int max_b, int pmax, int s_in_smem,
-                           long long warp_doubles, DevStatus* st) {
-  extern __shared__ double smw[];
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int it = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (it >= n_items) return;  // whole warps only
-  double* tv = smw + warp * warp_doubles;                         // max_b x pmax
-  double* Ssm = tv + (long long)max_b * pmax;                     // max_b^2 (if s_in_smem)
-  double* Hs = Ssm + (s_in_smem ? (long long)max_b * max_b : 0);  // pmax^2
-  double* Us = Hs + (long long)pmax * pmax;                       // pmax^2
-  double* ws_ = Us + (long long)pmax * pmax;                      // pmax
-  int* piv = reinterpret_cast<int*>(ws_ + pmax);                  // max_b
+// ---- 9. FP64 refinement of one cluster of candidates (one CTA per cluster).
+// Work item: subdomain s, first candidate t0, count p; shift sigma.
+__global__ void k_refine(const int* __restrict__ items, const double* __restrict__ sigmas,
+                         const int* __restrict__ sub_info, const int* __restrict__ o_off,
+                         const int* __restrict__ O_levptr, const int* __restrict__ O_L, int maxrow,
+                         const int* __restrict__ ocnt, const int* __restrict__ ocol, const double* __restrict__ oB,
+                         const double* __restrict__ oC, const int* __restrict__ o2i,
+                         const long long* __restrict__ f_off, const long long* __restrict__ x_off, double* F,
+                         double* Xw, const long long* __restrict__ poff, double* P, const double* __restrict__ lam_hat,
+                         double* lam_ref, int max_b, int s_in_smem, DevStatus* st) {
+  extern __shared__ double smem[];
+  __shared__ int piv[HK_MAXB];
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ double minpiv, sh_val;
+  __shared__ double Hs[HK_MAX_BLOCK * HK_MAX_BLOCK], Us[HK_MAX_BLOCK * HK_MAX_BLOCK], ws_[HK_MAX_BLOCK];
+  __shared__ int win_s;
+  int it = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
   int s = items[4 * it], t0 = items[4 * it + 1], pc = items[4 * it + 2];
-  int p = pc + HK_GUARD;
+  int p = pc + HK_GUARD;  // block: cluster + guard vectors
   double sigma = sigmas[it];
   const int* si = sub_info + 8 * s;
   int nI = si[0], nG = si[1];
   int oo = o_off[s], nO = nI + nG, L = O_L[s];
   const int* lp = O_levptr + oo + s;
+  double* tv = smem;                          // max_b x p
+  double* Ssm = smem + (long long)max_b * p;  // max_b x max_b when the level blocks fit in shared memory
   double* Fw = F + f_off[it];
-  double* X = Xw + x_off[it];
-  double* R = X + (long long)p * nO;
+  double* X = Xw + x_off[it];                 // p x nO
+  double* R = X + (long long)p * nO;          // p x nO
   double* Ps = P + poff[s];
+  // scale for the pivot floor
   double mx = 0;
-  for (long long e = lane; e < (long long)nO * maxrow; e += 32) {
+  for (long long e = tid; e < (long long)nO * maxrow; e += T) {
     int a = (int)(e / maxrow), q = (int)(e % maxrow);
     if (q < ocnt[oo + a]) mx = fmax(mx, fabs(oB[(long long)oo * maxrow + e] - sigma * oC[(long long)oo * maxrow + e]));
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  double floor_piv = 1e-14 * mx, minpiv = 1e300;
-  // 1. block LU of M over the level sets
+  if ((tid & 31) == 0) red_v[tid >> 5] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m2 = 0;
+    for (int w = 0; w < (T >> 5); ++w) m2 = fmax(m2, red_v[w]);
+    sh_val = m2;
+    minpiv = 1e300;
+  }
+  __syncthreads();
+  double floor_piv = 1e-14 * sh_val;
+  // 1. block LU of M = B^N - sigma C over the ovdof level sets
   long long bo = 0, prev_go = -1;
   int prev_r0 = 0;
   for (int j = 0; j < L; ++j) {
     int r0 = lp[j], b = lp[j + 1] - r0, r1 = lp[j + 1];
     int bn = j + 1 < L ? lp[j + 2] - r1 : 0;
-    double* S = s_in_smem ? Ssm : Fw + bo;
-    for (int e = lane; e < b * b; e += 32) {
+    double* S = s_in_smem ? Ssm : Fw + bo;  // wide levels: in place in the factor array
+    for (int e = tid; e < b * b; e += T) {
       int qa = e / b, t = e % b;
       int a = r0 + qa;
       long long base = (long long)(oo + a) * maxrow;
@@ -948,12 +896,12 @@ __global__ void k_refine_w(const int* __restrict__ items, int n_items, const dou
       }
       S[e] = v;
     }
-    __syncwarp();
-    gj_inverse_warp(S, b, piv, minpiv, floor_piv, lane);
+    __syncthreads();
+    gauss_jordan_inverse(S, b, piv, red_v, red_i, &minpiv, floor_piv);
     if (s_in_smem)
-      for (int e = lane; e < b * b; e += 32) Fw[bo + e] = S[e];
+      for (int e = tid; e < b * b; e += T) Fw[bo + e] = S[e];
     long long go = bo + (long long)b * b;
-    for (int e = lane; e < b * bn; e += 32) {
+    for (int e = tid; e < b * bn; e += T) {
       int qt = e / bn, cc = e % bn;
       int c = r1 + cc;
       long long base = (long long)(oo + c) * maxrow;
@@ -965,26 +913,27 @@ __global__ void k_refine_w(const int* __restrict__ items, int n_items, const dou
       }
       Fw[go + e] = v;
     }
-    __syncwarp();
+    __syncthreads();
     prev_go = go;
     prev_r0 = r0;
     bo = go + (long long)b * bn;
   }
   // 2. seeded start block on dof, zero on Gamma
   for (int t = 0; t < p; ++t)
-    for (int a = lane; a < nO; a += 32) {
+    for (int a = tid; a < nO; a += T) {
       int ia = o2i[oo + a];
       unsigned long long key = ((unsigned long long)s << 40) ^ ((unsigned long long)(t0 * 64 + t) << 20) ^ a;
       X[(long long)t * nO + a] = ia >= 0 ? (double)hash_unitf(key) : 0.0;
     }
-  __syncwarp();
+  __syncthreads();
   for (int step = 0; step < HK_REFINE_STEPS; ++step) {
-    o_matvec_w(nO, oo, maxrow, ocnt, ocol, oB, oC, 1.0, 0, X, R, p, lane);  // R = C X
-    __syncwarp();
+    // R = C X, then X = M^{-1} R by the two block sweeps
+    o_matvec(nO, oo, maxrow, ocnt, ocol, oB, oC, 1.0, 0, X, R, p);
+    __syncthreads();
     long long fo = 0;
     for (int j = 0; j < L; ++j) {
       int r0 = lp[j], b = lp[j + 1] - r0, bn = j + 1 < L ? lp[j + 2] - lp[j + 1] : 0;
-      for (int e = lane; e < b * p; e += 32) {
+      for (int e = tid; e < b * p; e += T) {
         int t = e / b, a = r0 + e % b;
         long long base = (long long)(oo + a) * maxrow;
         int cnt = min(ocnt[oo + a], maxrow);
@@ -995,17 +944,18 @@ __global__ void k_refine_w(const int* __restrict__ items, int n_items, const dou
         }
         tv[e] = acc;
       }
-      __syncwarp();
-      for (int e = lane; e < b * p; e += 32) {
+      __syncthreads();
+      for (int e = tid; e < b * p; e += T) {
         int t = e / b, q = e % b;
         const double* Sr = Fw + fo + (long long)q * b;
         double acc = 0;
         for (int c = 0; c < b; ++c) acc += Sr[c] * tv[t * b + c];
         R[(long long)t * nO + r0 + q] = acc;
       }
-      __syncwarp();
+      __syncthreads();
       fo += (long long)b * b + (long long)b * bn;
     }
+    // backward: x_j -= G_j x_{j+1}
     {
       int bl = lp[L] - lp[L - 1];
       fo -= (long long)bl * bl;
@@ -1014,78 +964,81 @@ __global__ void k_refine_w(const int* __restrict__ items, int n_items, const dou
       int r0 = lp[j], b = lp[j + 1] - r0, r1 = lp[j + 1], bn = lp[j + 2] - r1;
       fo -= (long long)b * b + (long long)b * bn;
       const double* Gm = Fw + fo + (long long)b * b;
-      for (int e = lane; e < b * p; e += 32) {
+      for (int e = tid; e < b * p; e += T) {
         int t = e / b, q = e % b;
         double acc = 0;
         for (int c = 0; c < bn; ++c) acc += Gm[(long long)q * bn + c] * R[(long long)t * nO + r1 + c];
         tv[e] = acc;
       }
-      __syncwarp();
-      for (int e = lane; e < b * p; e += 32) {
+      __syncthreads();
+      for (int e = tid; e < b * p; e += T) {
         int t = e / b, q = e % b;
         R[(long long)t * nO + r0 + q] -= tv[e];
       }
-      __syncwarp();
+      __syncthreads();
     }
-    for (long long e = lane; e < (long long)p * nO; e += 32) X[e] = R[e];
-    __syncwarp();
-    o_matvec_w(nO, oo, maxrow, ocnt, ocol, oB, oC, 1.0, 0, X, R, p, lane);  // R = C X
-    __syncwarp();
+    // X = R, C-orthonormalised (modified Gram-Schmidt twice; CX kept alongside in R)
+    for (long long e = tid; e < (long long)p * nO; e += T) X[e] = R[e];
+    __syncthreads();
+    o_matvec(nO, oo, maxrow, ocnt, ocol, oB, oC, 1.0, 0, X, R, p);  // R = C X
+    __syncthreads();
     for (int rep = 0; rep < 2; ++rep)
       for (int t = 0; t < p; ++t) {
         double* xt = X + (long long)t * nO;
         double* cxt = R + (long long)t * nO;
         for (int u = 0; u < t; ++u) {
-          double dcu = warp_dot(xt, R + (long long)u * nO, nO, lane);
-          for (int a = lane; a < nO; a += 32) {
+          double dcu = block_dot(xt, R + (long long)u * nO, nO, red_v);
+          for (int a = tid; a < nO; a += T) {
             xt[a] -= dcu * X[(long long)u * nO + a];
             cxt[a] -= dcu * R[(long long)u * nO + a];
           }
-          __syncwarp();
+          __syncthreads();
         }
-        double nrm = warp_dot(xt, cxt, nO, lane);
+        double nrm = block_dot(xt, cxt, nO, red_v);
         double inv = nrm > 0 ? 1.0 / sqrt(nrm) : 0.0;
-        for (int a = lane; a < nO; a += 32) {
+        for (int a = tid; a < nO; a += T) {
           xt[a] *= inv;
           cxt[a] *= inv;
         }
-        __syncwarp();
+        __syncthreads();
       }
   }
-  // 3. Rayleigh-Ritz on B^N (X is C-orthonormal)
-  o_matvec_w(nO, oo, maxrow, ocnt, ocol, oB, oC, 0.0, 1, X, R, p, lane);  // R = B^N X
-  __syncwarp();
+  // 3. Rayleigh-Ritz on B^N: H = X^T B^N X (X is C-orthonormal)
+  o_matvec(nO, oo, maxrow, ocnt, ocol, oB, oC, 0.0, 1, X, R, p);  // R = B^N X
+  __syncthreads();
   for (int i = 0; i < p; ++i)
     for (int j = 0; j < p; ++j) {
-      double hv = warp_dot(X + (long long)i * nO, R + (long long)j * nO, nO, lane);
-      if (lane == 0) Hs[i * p + j] = hv;
+      double h = block_dot(X + (long long)i * nO, R + (long long)j * nO, nO, red_v);
+      if (tid == 0) Hs[i * p + j] = h;
     }
-  __syncwarp();
-  int w0 = 0;
-  if (lane == 0) {
+  __syncthreads();
+  if (tid == 0) {
     for (int i = 0; i < p; ++i)
       for (int j = i + 1; j < p; ++j) {
         double a = 0.5 * (Hs[i * p + j] + Hs[j * p + i]);
         Hs[i * p + j] = Hs[j * p + i] = a;
       }
     jacobi_eig(Hs, Us, ws_, p);
+    // the window of pc consecutive Ritz values closest to the cluster's candidates
+    int best = 0;
     double bestd = 1e300;
-    for (int c0 = 0; c0 + pc <= p; ++c0) {
+    for (int w0 = 0; w0 + pc <= p; ++w0) {
       double dsum = 0;
-      for (int i = 0; i < pc; ++i) dsum += fabs(ws_[c0 + i] - lam_hat[(long long)s * HK_MAXM + t0 + i]);
+      for (int i = 0; i < pc; ++i) dsum += fabs(ws_[w0 + i] - lam_hat[(long long)s * HK_MAXM + t0 + i]);
       if (dsum < bestd) {
         bestd = dsum;
-        w0 = c0;
+        best = w0;
       }
     }
-    for (int i = 0; i < pc; ++i) lam_ref[(long long)s * HK_MAXM + t0 + i] = ws_[w0 + i];
+    win_s = best;
+    for (int i = 0; i < pc; ++i) lam_ref[(long long)s * HK_MAXM + t0 + i] = ws_[best + i];
     if (!(minpiv > 0)) dev_fail(st, HK_EIG_FAIL, s, minpiv);
   }
-  w0 = __shfl_sync(0xffffffffu, w0, 0);
-  __syncwarp();
+  __syncthreads();
   // refined vectors X U (the selected window), written (dof part, level order) over the candidates
+  int w0 = win_s;
   for (int i = 0; i < pc; ++i)
-    for (int a = lane; a < nO; a += 32) {
+    for (int a = tid; a < nO; a += T) {
       int ia = o2i[oo + a];
       if (ia < 0) continue;
       double acc = 0;
@@ -1342,7 +1295,7 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   HK_TRY(dalloc(h, &d_poff, ns));
   HK_CUDA(up(d_poff, poff.data(), 8 * ns));
 
-  // ---- FP64 refinement: clusters of candidates, one warp each
+  // ---- FP64 refinement: clusters of candidates, one CTA each
   std::vector<int> levO(O_total + ns);
   HK_CUDA(cudaMemcpyAsync(levO.data(), d_Olevptr, sizeof(int) * levO.size(), cudaMemcpyDeviceToHost, st));
   HK_CUDA(cudaStreamSynchronize(st));
@@ -1394,22 +1347,13 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
     HK_CUDA(up(d_sig, sig.data(), 8 * nit));
     HK_CUDA(up(d_foff, foff.data(), 8 * nit));
     HK_CUDA(up(d_xoff, xoff.data(), 8 * nit));
-    // one warp per cluster; per-warp shared memory as laid out in k_refine_w
-    long long wd_small = (long long)maxbO * pmax + 2LL * pmax * pmax + pmax + (maxbO + 1) / 2 + 1;
-    long long wd_full = wd_small + (long long)maxbO * maxbO;
-    int s_in_smem = (size_t)wd_full * 8 <= 100 * 1024;
-    long long wd = s_in_smem ? wd_full : wd_small;
-    // FP64 issue rate per SM is the bound: spread the warps over every SM before stacking them
-    int nsm = 152;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev);
-    long long wpb_fit = std::max(1LL, std::min(8LL, (200LL * 1024) / (wd * 8)));
-    int wpb = (int)std::max(1LL, std::min(wpb_fit, (long long)nit / (4LL * nsm)));
-    size_t rshm = (size_t)wd * 8 * wpb;
-    HK_TRY(hk_allow_smem(k_refine_w));
-    k_refine_w<<<nblk(nit, wpb), 32 * wpb, rshm, st>>>(d_items, nit, d_sig, h->d_sub_info, d_o_off, d_Olevptr, d_OL,
-                                                       maxrow, d_ocnt, d_ocol, d_oB, d_oC, d_o2i, d_foff, d_xoff, d_F,
-                                                       d_X, d_poff, d_P, d_lamhat, d_lamref, maxbO, pmax, s_in_smem,
-                                                       wd, h->d_status);
+    size_t rshm = sizeof(double) * ((size_t)maxbO * maxbO + (size_t)maxbO * pmax);
+    int s_in_smem = rshm <= 190 * 1024;
+    if (!s_in_smem) rshm = sizeof(double) * (size_t)maxbO * pmax;
+    HK_TRY(hk_allow_smem(k_refine));
+    k_refine<<<nit, 256, rshm, st>>>(d_items, d_sig, h->d_sub_info, d_o_off, d_Olevptr, d_OL, maxrow, d_ocnt, d_ocol,
+                                     d_oB, d_oC, d_o2i, d_foff, d_xoff, d_F, d_X, d_poff, d_P, d_lamhat, d_lamref,
+                                     maxbO, s_in_smem, h->d_status);
     HK_COUNT_LAUNCH();
     HK_LAUNCH_CHECK();
     HK_CUDA(cudaStreamSynchronize(st));
