@@ -8,6 +8,8 @@
 // HK_SINGULAR_COARSE.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "hk_internal.cuh"
 
 static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
@@ -84,66 +86,52 @@ __global__ void k_absmax(const double* __restrict__ a, long long n, double* out)
   }
 }
 
-// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The wait is bounded: after
-// ~2^24 polls the barrier gives up, records HK_TIMEOUT and returns false.
-struct GridBar {
-  unsigned count;
-  unsigned gen;
-};
+// Blocked in-place Gauss-Jordan inverse of the n0 x n0 matrix A with partial pivoting and implicit row
+// interchanges.  Unblocked, step k picks the unused row p_k with the largest |A[p][k]|, scales it, and
+// eliminates column k from every other row; column k then holds column p_k of the accumulated
+// transform, and the inverse is Inv[k][j] = A[p_k][q_j] with q the inverse of p (k_gj_unpermute).
+// Blocked, the steps of a panel of HK_GJ_NB columns touch only the panel's columns (k_gj_panel); the
+// panel's composite row transform is then I + sum_j (C_j - e_{p_j}) e_{p_j}^T, C_j the panel's final
+// column j, so every other column gets the rank-HK_GJ_NB update A[:, c] += (C - E_P) A[P, c] with the
+// pivot rows P read before it (k_gj_update).  Same pivots as the unblocked form, FP64 throughout.
+#define HK_GJ_NB 32
 
-__device__ bool grid_barrier(GridBar* gb, unsigned nblocks, unsigned& my_gen, DevStatus* st, int* sh_ok) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    unsigned g = my_gen;
-    __threadfence();
-    unsigned arrived = atomicAdd(&gb->count, 1u) + 1u;
-    if (arrived == nblocks) {
-      gb->count = 0u;
-      __threadfence();
-      atomicExch(&gb->gen, g + 1u);
-    } else {
-      unsigned spins = 0;
-      while (atomicAdd(&gb->gen, 0u) == g) {
-        if (++spins > (1u << 24)) {
-          ok = 0;
-          dev_fail(st, HK_TIMEOUT, blockIdx.x, 0);
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    *sh_ok = ok;
-  }
-  my_gen += 1u;
-  __syncthreads();
-  return *sh_ok != 0;
-}
-
-// In-place Gauss-Jordan inverse of the n0 x n0 matrix A with partial pivoting and implicit row
-// interchanges: step k picks the unused row p_k with the largest |A[p][k]|, scales it, and eliminates
-// column k from every other row; column k then holds column p_k of the accumulated transform.  The
-// inverse is Inv[k][j] = A[p_k][q_j] with q the inverse of p (applied by k_gj_unpermute).  Rows are
-// owned by CTAs (row i by CTA i mod gridDim); the pivot search of step k+1 is fused into the
-// elimination of step k (per-CTA maxima, reduced redundantly by every CTA after the barrier), so each
-// step costs one grid barrier.  Ties go to the smallest row index.
-__global__ void k_gj_persistent(double* A, int n0, int* piv, int* used, double* pmax_v, int* pmax_i,
-                                GridBar* gb, double* minpiv, DevStatus* st) {
+// Panel steps k0 .. k1-1 on columns k0 .. k1-1 (k1 - k0 <= HK_GJ_NB) by one thread-block cluster of G
+// CTAs.  Row i is owned by CTA i mod G, which keeps the row's panel entries (and its used flag) in
+// shared memory for the whole panel: Ps[r][j] holds A[i][k0 + j] for i = me + G r.  Each step reduces
+// the per-CTA maxima through distributed shared memory, every CTA reads the unscaled pivot row from its
+// owner's shared memory and scales its own copy, eliminates its rows and searches its rows for the next
+// pivot; the step ends at the cluster barrier, after which the owner overwrites the pivot row with the
+// scaled one (no CTA reads it any more).  Ties go to the smallest row index.
+__global__ void k_gj_panel(double* A, int n0, int k0, int k1, int* piv, int* used, double* minpiv) {
+  extern __shared__ double Ps[];  // nloc x HK_GJ_NB, then nloc used flags
   __shared__ double rv[32];
   __shared__ int ri[32];
-  __shared__ int sh_ok, sh_p;
+  __shared__ double cmax_v[2];  // this CTA's maximum for the next column (double buffered)
+  __shared__ int cmax_i[2];
+  __shared__ int sh_p;
   __shared__ double sh_f;
-  extern __shared__ double prow[];  // the scaled pivot row
+  __shared__ double prow[HK_GJ_NB];  // the scaled pivot row
+  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
   int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
-  unsigned G = gridDim.x, my_gen = 0;
-  // initial pivot search for column 0 (every CTA over its rows)
-  auto local_max = [&](int col, int buf) {
+  int nb = k1 - k0;
+  int G = (int)cl.num_blocks(), me = (int)cl.block_rank();
+  int nloc = me < n0 ? (n0 - me + G - 1) / G : 0;
+  int nloc_max = (n0 + G - 1) / G;
+  int* uloc = reinterpret_cast<int*>(Ps + (long long)nloc_max * HK_GJ_NB);
+  for (int e = tid; e < nloc * nb; e += T) {
+    int r = e / nb, j = e % nb;
+    Ps[r * HK_GJ_NB + j] = A[(long long)(me + G * r) * n0 + k0 + j];
+  }
+  for (int r = tid; r < nloc; r += T) uloc[r] = used[me + G * r];
+  __syncthreads();
+  auto local_max = [&](int jc, int buf) {
     double best = -1.0;
     int bi = 0x7fffffff;
-    for (int i = blockIdx.x + G * tid; i < n0; i += G * T) {
-      if (used[i]) continue;
-      double v = fabs(A[(long long)i * n0 + col]);
+    for (int r = tid; r < nloc; r += T) {
+      if (uloc[r]) continue;
+      double v = fabs(Ps[r * HK_GJ_NB + jc]);
+      int i = me + G * r;
       if (v > best || (v == best && i < bi)) { best = v; bi = i; }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -158,68 +146,127 @@ __global__ void k_gj_persistent(double* A, int n0, int* piv, int* used, double* 
       int bj = ri[0];
       for (int w = 1; w < nw; ++w)
         if (rv[w] > bv || (rv[w] == bv && ri[w] < bj)) { bv = rv[w]; bj = ri[w]; }
-      pmax_v[buf * G + blockIdx.x] = bv;
-      pmax_i[buf * G + blockIdx.x] = bj;
+      cmax_v[buf] = bv;
+      cmax_i[buf] = bj;
+    }
+  };
+  local_max(0, k0 & 1);
+  cl.sync();
+  int pprev = -1;
+  for (int k = k0; k < k1; ++k) {
+    int jk = k - k0;
+    if (pprev >= 0 && me == pprev % G) {  // deferred: the scaled previous pivot row into its owner's rows
+      int rp = pprev / G;
+      for (int j = tid; j < nb; j += T) Ps[rp * HK_GJ_NB + j] = prow[j];
     }
     __syncthreads();
-  };
-  local_max(0, 0);
-  if (!grid_barrier(gb, G, my_gen, st, &sh_ok)) return;
-  int pprev = -1;  // pivot row of the previous step, written back by its owner after the barrier
-  for (int k = 0; k < n0; ++k) {
-    if (pprev >= 0 && blockIdx.x == (unsigned)(pprev % (int)G)) {
-      for (int j = tid; j < n0; j += T) A[(long long)pprev * n0 + j] = prow[j];
-      __syncthreads();
-    }
     int buf = k & 1;
-    // every CTA reduces the per-CTA maxima the same way (warp 0, lanes over CTAs)
     if (warp == 0) {
       double bv = -1.0;
       int bj = 0x7fffffff;
-      for (unsigned b = lane; b < G; b += 32) {
-        double v = pmax_v[buf * G + b];
-        int i = pmax_i[buf * G + b];
-        if (v > bv || (v == bv && i < bj)) { bv = v; bj = i; }
+      if (lane < G) {
+        bv = *cl.map_shared_rank(&cmax_v[buf], lane);
+        bj = *cl.map_shared_rank(&cmax_i[buf], lane);
       }
       for (int o = 16; o > 0; o >>= 1) {
         double ov = __shfl_xor_sync(0xffffffffu, bv, o);
         int oi = __shfl_xor_sync(0xffffffffu, bj, o);
         if (ov > bv || (ov == bv && oi < bj)) { bv = ov; bj = oi; }
       }
-      if (lane == 0) {
-        sh_p = bj;
-        double pv = A[(long long)bj * n0 + k];
-        sh_f = pv != 0.0 ? 1.0 / pv : 0.0;
-        if (blockIdx.x == 0) {
-          piv[k] = bj;
-          if (fabs(pv) < *minpiv) *minpiv = fabs(pv);
-        }
+      if (lane == 0) sh_p = bj;
+    }
+    __syncthreads();
+    int p = sh_p, owner = p % G, rp = p / G;
+    const double* prem = cl.map_shared_rank(Ps + (long long)rp * HK_GJ_NB, owner);  // unscaled pivot row
+    if (tid == 0) {
+      double pv = prem[jk];
+      sh_f = pv != 0.0 ? 1.0 / pv : 0.0;
+      if (me == 0) {
+        piv[k] = p;
+        if (fabs(pv) < *minpiv) *minpiv = fabs(pv);
       }
     }
     __syncthreads();
-    int p = sh_p;
     double f = sh_f;
-    // scaled pivot row (column k of it becomes f)
-    for (int j = tid; j < n0; j += T) prow[j] = j == k ? f : A[(long long)p * n0 + j] * f;
+    double pj_ = tid < nb ? prem[tid] : 0.0;
+    __syncthreads();  // prow of the previous step was consumed above
+    if (tid < nb) prow[tid] = tid == jk ? f : pj_ * f;
     __syncthreads();
-    // eliminate column k from the owned rows other than p (row p is rewritten after the barrier,
-    // once no CTA reads its unscaled values any more)
-    for (int i = blockIdx.x + G * warp; i < n0; i += G * nw) {
-      double* ai = A + (long long)i * n0;
-      if (i == p) continue;
-      double g = ai[k];
+    // eliminate column k from the owned rows other than p
+    for (int r = warp; r < nloc; r += nw) {
+      if (me + G * r == p) continue;
+      double* ar = Ps + r * HK_GJ_NB;
+      double g = ar[jk];
       __syncwarp();
-      if (g != 0.0)
-        for (int j = lane; j < n0; j += 32) ai[j] = j == k ? -g * f : ai[j] - g * prow[j];
+      if (g != 0.0 && lane < nb) ar[lane] = lane == jk ? -g * f : ar[lane] - g * prow[lane];
     }
-    if (blockIdx.x == (unsigned)(p % G) && tid == 0) used[p] = 1;
+    if (me == owner && tid == 0) uloc[rp] = 1;
     __syncthreads();
-    if (k + 1 < n0) local_max(k + 1, (k + 1) & 1);
-    if (!grid_barrier(gb, G, my_gen, st, &sh_ok)) return;
+    if (k + 1 < k1) local_max(jk + 1, (k + 1) & 1);
+    cl.sync();
     pprev = p;
   }
-  if (pprev >= 0 && blockIdx.x == (unsigned)(pprev % (int)G))
-    for (int j = tid; j < n0; j += T) A[(long long)pprev * n0 + j] = prow[j];
+  if (pprev >= 0 && me == pprev % G) {
+    int rp = pprev / G;
+    for (int j = tid; j < nb; j += T) Ps[rp * HK_GJ_NB + j] = prow[j];
+  }
+  __syncthreads();
+  for (int e = tid; e < nloc * nb; e += T) {
+    int r = e / nb, j = e % nb;
+    A[(long long)(me + G * r) * n0 + k0 + j] = Ps[r * HK_GJ_NB + j];
+  }
+  for (int r = tid; r < nloc; r += T) used[me + G * r] = uloc[r];
+}
+
+// Q[j][c] = A[p_{k0+j}][c] for the panel's pivot rows (read before the update changes them).
+__global__ void k_gj_pivot_rows(const double* __restrict__ A, int n0, int k0, int nb, const int* __restrict__ piv,
+                                double* Q) {
+  int j = blockIdx.y;
+  const double* src = A + (long long)piv[k0 + j] * n0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n0; c += gridDim.x * blockDim.x)
+    Q[(long long)j * n0 + c] = src[c];
+}
+
+// A[i][c] += sum_j (A[i][k0+j] - [i == p_j]) Q[j][c] for every column c outside the panel: a 64 x 64
+// output tile per CTA, 256 threads with 4 x 4 outputs each, the panel slice and Q slice in shared memory.
+__global__ void __launch_bounds__(256) k_gj_update(double* A, int n0, int k0, int nb, const int* __restrict__ piv,
+                                                   const double* __restrict__ Q) {
+  __shared__ double Cs[64][HK_GJ_NB + 1];
+  __shared__ double Qs[HK_GJ_NB][64];
+  __shared__ int pj[HK_GJ_NB];
+  int i0 = blockIdx.y * 64, c0 = blockIdx.x * 64, tid = threadIdx.x;
+  if (tid < nb) pj[tid] = piv[k0 + tid];
+  __syncthreads();
+  for (int e = tid; e < 64 * HK_GJ_NB; e += 256) {
+    int r = e / HK_GJ_NB, j = e % HK_GJ_NB;
+    int i = i0 + r;
+    double v = 0.0;
+    if (i < n0 && j < nb) v = A[(long long)i * n0 + k0 + j] - (i == pj[j] ? 1.0 : 0.0);
+    Cs[r][j] = v;
+  }
+  for (int e = tid; e < HK_GJ_NB * 64; e += 256) {
+    int j = e / 64, c = e % 64;
+    Qs[j][c] = (j < nb && c0 + c < n0) ? Q[(long long)j * n0 + c0 + c] : 0.0;
+  }
+  __syncthreads();
+  int tr = (tid / 16) * 4, tc = (tid % 16) * 4;
+  double acc[4][4] = {};
+  for (int j = 0; j < nb; ++j) {
+    double a[4], q[4];
+    for (int u = 0; u < 4; ++u) a[u] = Cs[tr + u][j];
+    for (int u = 0; u < 4; ++u) q[u] = Qs[j][tc + u];
+    for (int u = 0; u < 4; ++u)
+      for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * q[v];
+  }
+  for (int u = 0; u < 4; ++u) {
+    int i = i0 + tr + u;
+    if (i >= n0) continue;
+    for (int v = 0; v < 4; ++v) {
+      int c = c0 + tc + v;
+      if (c >= n0 || (c >= k0 && c < k0 + nb)) continue;
+      A[(long long)i * n0 + c] += acc[u][v];
+    }
+  }
 }
 
 // Inv[k][j] = A[p_k][q_j], q = p^{-1}.
@@ -278,34 +325,51 @@ hk_status phase_coarse(hk_handle* h) {
   double big = 1e300;
   HK_CUDA(cudaMemcpyAsync(d_sc + 1, &big, sizeof(double), cudaMemcpyHostToDevice, st));
   {
-    // one cooperative launch; grid = co-resident CTAs (at most one per SM here)
-    int threads = 512, nsm = 0, per_sm = 0, dev = h->dev;
-    size_t pshm = sizeof(double) * (size_t)n0;
-    HK_TRY(hk_allow_smem(k_gj_persistent));
-    HK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    HK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_persistent, threads, pshm));
-    if (per_sm < 1) {
-      hk_set_error("coarse inverse: no co-resident CTA possible (n0 = %d)", n0);
+    // blocked: per panel one launch of one thread-block cluster, then the rank-HK_GJ_NB update
+    int threads = 256;  // a panel step is short: cheap barriers matter more than threads
+    // cluster size: enough CTAs that each holds its rows' panel entries in shared memory
+    auto panel_smem = [&](int g) { return (size_t)((n0 + g - 1) / g) * (HK_GJ_NB * sizeof(double) + sizeof(int)); };
+    int G = std::min(8, std::max(1, n0 / 64));
+    while (G < 8 && panel_smem(G) > 200 * 1024) G *= 2;
+    if (panel_smem(G) > 200 * 1024) G = 16;  // non-portable cluster size
+    if (panel_smem(G) > 200 * 1024) {
+      hk_set_error("coarse dimension %d too large for the shared-memory panel factorisation", n0);
       return HK_UNSUPPORTED;
     }
-    // each step costs one grid barrier plus n0^2 / G FP64 updates per CTA: 64 CTAs balance the two
-    int G = std::min(std::min(nsm, 64), std::max(1, n0 / 8));
-    int *d_used = nullptr, *d_pi = nullptr, *d_q = nullptr;
-    double* d_pv = nullptr;
-    GridBar* d_gb = nullptr;
+    HK_TRY(hk_allow_smem(k_gj_panel));
+    if (G > 8) HK_CUDA(cudaFuncSetAttribute(k_gj_panel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    int *d_used = nullptr, *d_q = nullptr;
+    double* d_Q = nullptr;
     double* d_work = h->d_Einv64;  // A, then unpermuted into a copy
     double* d_tmp = nullptr;
     HK_TRY(dalloc(h, &d_used, n0));
-    HK_TRY(dalloc(h, &d_pi, 2 * G));
-    HK_TRY(dalloc(h, &d_pv, 2 * G));
     HK_TRY(dalloc(h, &d_q, n0));
-    HK_TRY(dalloc(h, &d_gb, 1));
+    HK_TRY(dalloc(h, &d_Q, (size_t)HK_GJ_NB * n0));
     HK_TRY(dalloc(h, &d_tmp, (size_t)n0 * n0));
-    void* args[] = {&d_work, &n0, &d_piv, &d_used, &d_pv, &d_pi, &d_gb, &d_sc, &h->d_status};
     double* minp = d_sc + 1;
-    args[7] = &minp;
-    HK_CUDA(cudaLaunchCooperativeKernel((void*)k_gj_persistent, dim3(G), dim3(threads), args, pshm, st));
-    HK_COUNT_LAUNCH();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = panel_smem(G);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = G;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    for (int k0 = 0; k0 < n0; k0 += HK_GJ_NB) {
+      int k1 = std::min(n0, k0 + HK_GJ_NB), nb = k1 - k0;
+      HK_CUDA(cudaLaunchKernelEx(&cfg, k_gj_panel, d_work, n0, k0, k1, d_piv, d_used, minp));
+      HK_COUNT_LAUNCH();
+      if (nb < n0) {
+        k_gj_pivot_rows<<<dim3(nblk(n0, 256), nb), 256, 0, st>>>(d_work, n0, k0, nb, d_piv, d_Q);
+        HK_COUNT_LAUNCH();
+        k_gj_update<<<dim3(nblk(n0, 64), nblk(n0, 64)), 256, 0, st>>>(d_work, n0, k0, nb, d_piv, d_Q);
+        HK_COUNT_LAUNCH();
+      }
+    }
     HK_LAUNCH_CHECK();
     HK_TRY(check_device_status(h, "coarse inverse"));
     k_invert_perm<<<nblk(n0, 256), 256, 0, st>>>(d_piv, d_q, n0);
@@ -315,7 +379,7 @@ hk_status phase_coarse(hk_handle* h) {
     HK_CUDA(cudaMemcpyAsync(h->d_Einv64, d_tmp, sizeof(double) * (size_t)n0 * n0, cudaMemcpyDeviceToDevice, st));
     HK_LAUNCH_CHECK();
     HK_CUDA(cudaStreamSynchronize(st));
-    void* fr[] = {d_used, d_pi, d_pv, d_q, d_gb, d_tmp};
+    void* fr[] = {d_used, d_q, d_tmp, d_Q};
     for (void* q : fr) dfree(h, q);
   }
   double sc[2];
