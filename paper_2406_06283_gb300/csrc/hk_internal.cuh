@@ -186,6 +186,9 @@ struct hk_handle {
   long long graph_solves = 0;
   std::map<int, int> nr_tuned;  // right-hand sides per apply CTA chosen by apply_autotune, per batch size
   cudaStream_t cap_stream = nullptr;  // blocking stream for graphs when the handle's stream is the legacy one
+  cudaStream_t aux_stream = nullptr;  // setup: local factors overlapping the eigenproblems
+  cudaEvent_t ev_lf = nullptr;
+  bool lf_pending = false;
   int* d_ctl = nullptr;         // [0] inner step j, [1] cycles run, [2] inner steps run
   const int* g_jp = nullptr;    // while an inner step is captured: the device word holding j
   long long g_jstride = 0;      // ... and the distance between consecutive Krylov vectors
@@ -258,7 +261,8 @@ hk_status check_device_status(hk_handle* h, const char* phase);
 // ---- phases (each file implements one) ----
 hk_status phase_assembly(hk_handle* h, const hk_mesh* mesh, const double* coeff);
 hk_status phase_decomposition(hk_handle* h, const int32_t* elem_to_sub, uint8_t** d_elem_in_out);
-hk_status phase_local_factors(hk_handle* h);
+hk_status phase_local_factors_begin(hk_handle* h);
+hk_status phase_local_factors_end(hk_handle* h);
 hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in);
 hk_status phase_coarse(hk_handle* h);
 

@@ -619,7 +619,11 @@ hk_status build_apply_z(hk_handle* h) {
   return HK_OK;
 }
 
-hk_status phase_local_factors(hk_handle* h) {
+// Host work, sizes and allocations of the local factorisation on the setup stream; then the factor
+// kernels (block LU, level records) on the handle's auxiliary stream, where they overlap the
+// eigenproblems (which leave SMs and the FP64 pipes idle for most of their time).
+// phase_local_factors_end joins them.
+hk_status phase_local_factors_begin(hk_handle* h) {
   cudaStream_t st = h->stream;
   int ns = h->n_sub;
   std::vector<int> lev(h->I_total + ns);
@@ -634,34 +638,26 @@ hk_status phase_local_factors(hk_handle* h) {
   h->f_total = fo;
   HK_TRY(upload_sub_info(h));
   if (h->p.levels == HK_COARSE_ONLY) return HK_OK;
+  int* d_nc = nullptr;
   {
     unsigned long long* d_cnt = nullptr;
     HK_TRY(dalloc(h, &d_cnt, 1));
+    HK_TRY(dalloc(h, &d_nc, h->I_total + ns));
     k_count_lower<<<ns, 128, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
                                       d_cnt); HK_COUNT_LAUNCH();
+    k_level_counts<<<ns, 128, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
+                                       d_nc); HK_COUNT_LAUNCH();
     unsigned long long c = 0;
     HK_CUDA(cudaMemcpyAsync(&c, d_cnt, sizeof(c), cudaMemcpyDeviceToHost, st));
     HK_CUDA(cudaStreamSynchronize(st));
     h->lower_nnz = (long long)c;
     dfree(h, d_cnt);
   }
-  HK_TRY(dalloc(h, &h->d_F64, fo));
-  size_t shm = sizeof(double) * (size_t)h->max_level * h->max_level;
-  int s_in_smem = shm <= 200 * 1024;
-  if (!s_in_smem) shm = 0;
-  HK_TRY(hk_allow_smem(k_block_lu));
-  k_block_lu<<<ns, 256, shm, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
-                                   h->d_lvalB, h->d_F64, s_in_smem, h->d_status); HK_COUNT_LAUNCH();
-  HK_LAUNCH_CHECK();
-  HK_TRY(check_device_status(h, "local factors"));
-  // level records for the apply, in the arithmetic type of the precision form
-  int* d_nc = nullptr;
-  HK_TRY(dalloc(h, &d_nc, h->I_total + ns));
-  k_level_counts<<<ns, 128, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
-                                     d_nc); HK_COUNT_LAUNCH();
   std::vector<int> nc(h->I_total + ns);
   HK_CUDA(cudaMemcpyAsync(nc.data(), d_nc, sizeof(int) * nc.size(), cudaMemcpyDeviceToHost, st));
   HK_CUDA(cudaStreamSynchronize(st));
+  dfree(h, d_nc);
+  // level records for the apply, in the arithmetic type of the precision form
   size_t esz = h->p.precision == HK_FP32_PRECOND ? 4 : 8;
   std::vector<long long> tab(4 * (h->I_total + ns), 0);
   long long cur = 0, stage = 16;
@@ -683,21 +679,43 @@ hk_status phase_local_factors(hk_handle* h) {
   }
   h->pack_bytes = cur;
   h->pack_stage = stage;
+  HK_TRY(dalloc(h, &h->d_F64, fo));
   HK_TRY(dalloc(h, &h->d_lvtab, tab.size()));
   HK_TRY(dalloc(h, &h->d_pack, cur));
   HK_CUDA(cudaMemcpyAsync(h->d_lvtab, tab.data(), sizeof(long long) * tab.size(), cudaMemcpyHostToDevice, st));
+  size_t shm = sizeof(double) * (size_t)h->max_level * h->max_level;
+  int s_in_smem = shm <= 200 * 1024;
+  if (!s_in_smem) shm = 0;
+  HK_TRY(hk_allow_smem(k_block_lu));
+  // the auxiliary stream starts after everything above (allocations, memsets, table upload)
+  if (!h->aux_stream) HK_CUDA(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
+  if (!h->ev_lf) HK_CUDA(cudaEventCreateWithFlags(&h->ev_lf, cudaEventDisableTiming));
+  HK_CUDA(cudaEventRecord(h->ev_lf, st));
+  HK_CUDA(cudaStreamWaitEvent(h->aux_stream, h->ev_lf, 0));
+  cudaStream_t ax = h->aux_stream;
+  k_block_lu<<<ns, 256, shm, ax>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
+                                   h->d_lvalB, h->d_F64, s_in_smem, h->d_status); HK_COUNT_LAUNCH();
   if (esz == 4)
-    k_pack_levels<float><<<ns, 256, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI,
+    k_pack_levels<float><<<ns, 256, 0, ax>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI,
                                              h->d_lcol, h->d_lvalB, h->d_F64, h->d_lvtab, h->d_pack);
   else
-    k_pack_levels<double><<<ns, 256, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI,
+    k_pack_levels<double><<<ns, 256, 0, ax>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI,
                                               h->d_lcol, h->d_lvalB, h->d_F64, h->d_lvtab, h->d_pack);
   HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
-  HK_CUDA(cudaStreamSynchronize(st));
+  HK_CUDA(cudaEventRecord(h->ev_lf, ax));
+  h->lf_pending = true;
+  return HK_OK;
+}
+
+// Joins the factor kernels into the setup stream, checks them, frees the FP64 factors.
+hk_status phase_local_factors_end(hk_handle* h) {
+  if (!h->lf_pending) return HK_OK;
+  h->lf_pending = false;
+  HK_CUDA(cudaStreamWaitEvent(h->stream, h->ev_lf, 0));
+  HK_TRY(check_device_status(h, "local factors"));
   dfree(h, h->d_F64);
   h->d_F64 = nullptr;
-  dfree(h, d_nc);
   return HK_OK;
 }
 
