@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(HK_SF_TILE) k_sf_solve2(const int* __restrict_
 // rebuilds column k and the reflector redundantly, and the partial p vectors of the CTAs are added in
 // rank order through distributed shared memory after one cluster barrier per step.  Shared vectors are
 // zero below the active column and in the padding so that row loops start on a 16-byte boundary.
-#define HK_TRI_WARPS 32
+#define HK_TRI_WARPS 16
 template <int CS>
 __global__ void __launch_bounds__(HK_TRI_WARPS * 32) k_tridiag32(const int* __restrict__ sub_info,
                                                                  const long long* __restrict__ wsA, float* ws,
@@ -555,9 +555,13 @@ __global__ void __launch_bounds__(HK_TRI_WARPS * 32) k_tridiag32(const int* __re
     __syncthreads();
     // partial p of this CTA: row parts of its rows + column sums of all its warps
     for (int j = k + 1 + tid; j < n; j += Tn) {
-      float t = (j % CS == r) ? pc[j] : 0.f;
-      for (int w = 0; w < nw; ++w) t += cacc[w * lda + j];
-      pc[j] = t;
+      float t0 = (j % CS == r) ? pc[j] : 0.f, t1 = 0.f;
+#pragma unroll
+      for (int w = 0; w < HK_TRI_WARPS; w += 2) {
+        t0 += cacc[w * lda + j];
+        t1 += cacc[(w + 1) * lda + j];
+      }
+      pc[j] = t0 + t1;
     }
     if (CS > 1) {
       cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
@@ -1230,7 +1234,14 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
     return HK_UNSUPPORTED;
   }
   int CS = 1;
-  while (CS < 4 && (long long)ns * CS * 2 <= 152) CS *= 2;  // spread a few subdomains over more SMs
+  {
+    // spread the subdomains over the SMs: a cluster of CS CTAs per subdomain, as many CTAs as fit at
+    // once (two per SM when their shared memory allows)
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev);
+    int per_sm = 2 * (shm + 2048) <= 228 * 1024 ? 2 : 1;
+    while (CS < 4 && (long long)ns * CS * 2 <= (long long)nsm * per_sm) CS *= 2;
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
