@@ -1362,7 +1362,7 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
     int s_in_smem = rshm <= 190 * 1024;
     if (!s_in_smem) rshm = sizeof(double) * (size_t)maxbO * pmax;
     HK_TRY(hk_allow_smem(k_refine));
-    k_refine<<<nit, 256, rshm, st>>>(d_items, d_sig, h->d_sub_info, d_o_off, d_Olevptr, d_OL, maxrow, d_ocnt, d_ocol,
+    k_refine<<<nit, 128, rshm, st>>>(d_items, d_sig, h->d_sub_info, d_o_off, d_Olevptr, d_OL, maxrow, d_ocnt, d_ocol,
                                      d_oB, d_oC, d_o2i, d_foff, d_xoff, d_F, d_X, d_poff, d_P, d_lamhat, d_lamref,
                                      maxbO, s_in_smem, h->d_status);
     HK_COUNT_LAUNCH();

@@ -447,11 +447,16 @@ __device__ inline void gauss_jordan_inverse(double* A, int b, int* piv, double* 
     double inv = red_v[0];
     for (int c = tid; c < b; c += T) A[k * b + c] *= inv;
     __syncthreads();
-    // eliminate column k from every other row
-    for (int e = tid; e < b * b; e += T) {
-      int i = e / b, c = e % b;
-      if (i == k || c == k) continue;
-      A[i * b + c] -= A[i * b + k] * A[k * b + c];
+    // eliminate column k from every other row: a warp per row, lanes over the columns (column k and
+    // row k are only read here)
+    {
+      int lane = tid & 31, nwarp = T >> 5;
+      for (int i = tid >> 5; i < b; i += nwarp) {
+        if (i == k) continue;
+        double g = A[i * b + k];
+        for (int c = lane; c < b; c += 32)
+          if (c != k) A[i * b + c] -= g * A[k * b + c];
+      }
     }
     __syncthreads();
     for (int i = tid; i < b; i += T)
