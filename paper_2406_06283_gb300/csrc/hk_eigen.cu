@@ -250,10 +250,13 @@ __global__ void k_dchol(const int* __restrict__ sub_info, const long long* __res
 
 // One forward substitution step for row a of a thread's column: v = (x - sum L[a][k] y[k]) / L[a][a]
 // with the previous solved entries y[k], k in [a - bw, a), in the ring.
-__device__ __forceinline__ float ring_solve_row(float x, int a, int bw, int ld, int R, int wslot,
-                                                const float* __restrict__ L32, const float* ring, int T, int tid) {
+// x_a = (x - sum_{k in band, k < a} L[a][k] x_k) / L[a][a] for one column (this thread's), the previous
+// band of solutions in the ring (slot-major, T columns).  Lrow: row a of L in band storage (ld = bw + 1,
+// column k at Lrow[k - a + bw]) staged in shared memory, with 1 / L[a][a] at Lrow[bw].
+__device__ __forceinline__ float ring_solve_row(float x, int a, int bw, int R, int wslot, const float* Lrow,
+                                                const float* ring, int T, int tid) {
   int k0 = max(0, a - bw);
-  const float* la = L32 + (long long)a * ld + (k0 - a + bw);
+  const float* la = Lrow + (k0 - a + bw);
   int slot = wslot - (a - k0);
   if (slot < 0) slot += R;
   int len = a - k0, seg = min(len, R - slot);
@@ -278,11 +281,25 @@ __device__ __forceinline__ float ring_solve_row(float x, int a, int bw, int ld, 
     acc3 += la2[q + 3] * r2[(long long)(q + 3) * T];
   }
   for (; q < rest; ++q) acc0 += la2[q] * r2[(long long)q * T];
-  return (x - ((acc0 + acc1) + (acc2 + acc3))) / L32[(long long)a * ld + bw];
+  return (x - ((acc0 + acc1) + (acc2 + acc3))) * Lrow[bw];
 }
 
 #define HK_SF_TILE 128   // columns per CTA in the standard-form solves (= threads)
 #define HK_SF_AHEAD 8    // rows loaded ahead
+#define HK_SF_CHUNK 32   // rows of L staged in shared memory at a time
+
+// Rows a0 .. a0 + HK_SF_CHUNK - 1 of the banded L (ld = bw + 1 per row) into shared memory, diagonal
+// entries replaced by their reciprocals.  All threads of the CTA take part; barriers on both sides.
+__device__ __forceinline__ void stage_band_rows(float* Lsh, const float* L32, int a0, int nI, int bw, int T,
+                                                int tid) {
+  int ld = bw + 1, rows = min(HK_SF_CHUNK, nI - a0);
+  __syncthreads();
+  for (int e = tid; e < rows * ld; e += T) {
+    float v = L32[(long long)a0 * ld + e];
+    Lsh[e] = (e % ld == bw) ? 1.f / v : v;
+  }
+  __syncthreads();
+}
 
 // (b): Y[:, tile] = L^{-1} (mu S mu)[:, tile].  grid = (subdomain, column tile).
 __global__ void __launch_bounds__(HK_SF_TILE) k_sf_solve1(const int* __restrict__ sub_info,
@@ -304,8 +321,10 @@ __global__ void __launch_bounds__(HK_SF_TILE) k_sf_solve1(const int* __restrict_
   const float* L32 = ws32 + wsL32[s];
   bool act = c < nI;
   double mc = act ? (double)mu[Ilev[off + c]] : 0.0;
+  float* Lsh = ring + (long long)R * T;  // HK_SF_CHUNK x ld
   int wslot = 0;
   for (int a0 = 0; a0 < nI; a0 += HK_SF_AHEAD) {
+    if (a0 % HK_SF_CHUNK == 0) stage_band_rows(Lsh, L32, a0, nI, bw, T, tid);
     float xin[HK_SF_AHEAD];
 #pragma unroll
     for (int u = 0; u < HK_SF_AHEAD; ++u) {
@@ -316,7 +335,7 @@ __global__ void __launch_bounds__(HK_SF_TILE) k_sf_solve1(const int* __restrict_
     for (int u = 0; u < HK_SF_AHEAD; ++u) {
       int a = a0 + u;
       if (a >= nI) break;
-      float v = ring_solve_row(xin[u], a, bw, ld, R, wslot, L32, ring, T, tid);
+      float v = ring_solve_row(xin[u], a, bw, R, wslot, Lsh + (a % HK_SF_CHUNK) * ld, ring, T, tid);
       ring[(long long)wslot * T + tid] = v;
       if (act) Y[(long long)a * lda + c] = v;
       if (++wslot == R) wslot = 0;
@@ -342,6 +361,7 @@ __global__ void __launch_bounds__(HK_SF_TILE) k_sf_solve2(const int* __restrict_
   float* A = ws32 + wsA[s];
   const float* L32 = ws32 + wsL32[s];
   bool act = c < nI;
+  float* Lsh = ring + (long long)R * T;  // HK_SF_CHUNK x ld
   int wslot = 0;
   for (int a0 = 0; a0 < nI; a0 += 32) {
     // stage Y[c0 + i][a0 + j] -> stage[j][i]: a warp reads 32 consecutive entries of one row
@@ -352,9 +372,10 @@ __global__ void __launch_bounds__(HK_SF_TILE) k_sf_solve2(const int* __restrict_
       stage[lane][i] = (row < nI && col < nI) ? Y[(long long)row * lda + col] : 0.f;
     }
     __syncthreads();
+    stage_band_rows(Lsh, L32, a0, nI, bw, T, tid);
     for (int u = 0; u < 32 && a0 + u < nI; ++u) {
       int a = a0 + u;
-      float v = ring_solve_row(stage[u][tid], a, bw, ld, R, wslot, L32, ring, T, tid);
+      float v = ring_solve_row(stage[u][tid], a, bw, R, wslot, Lsh + u * ld, ring, T, tid);
       ring[(long long)wslot * T + tid] = v;
       if (act) A[(long long)a * lda + c] = v;
       if (++wslot == R) wslot = 0;
@@ -1208,12 +1229,12 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   HK_TRY(check_device_status(h, "eigen: Gamma elimination"));
   int maxbw = 0;
   for (int s = 0; s < ns; ++s) maxbw = std::max(maxbw, bw[s]);
-  size_t sf_shm = sizeof(float) * (size_t)(maxbw + 1) * HK_SF_TILE;
+  size_t sf_shm = sizeof(float) * (size_t)(maxbw + 1) * (HK_SF_TILE + HK_SF_CHUNK);
   if (sf_shm > 180 * 1024) {
     hk_set_error("local band width %d too large for the standard-form kernels", maxbw);
     return HK_UNSUPPORTED;
   }
-  k_dchol<<<ns, 512, 0, st>>>(h->d_sub_info, h->d_sub_off, d_bw, h->d_lrow, h->d_lcntI, h->d_lcol, h->d_lvalD, d_L,
+  k_dchol<<<ns, 128, 0, st>>>(h->d_sub_info, h->d_sub_off, d_bw, h->d_lrow, h->d_lcntI, h->d_lcol, h->d_lvalD, d_L,
                               d_L32, d_ws, d_ws32, h->d_status);
   HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
