@@ -205,47 +205,46 @@ __global__ void k_dchol(const int* __restrict__ sub_info, const long long* __res
   int bw = bw_arr[s], ld = bw + 1;
   long long coff = sub_off[3 * s + 1];
   const int* lr = lrow + off + s;
-  double* Lb = ws + wsL[s];
-  float* L32 = ws32 + wsL32[s];
-  for (long long e = tid; e < (long long)nI * ld; e += T) Lb[e] = 0.0;
+  // the factor is only used in FP32 (the standard form of the candidate stage): factor in FP32
+  float* Lb = ws32 + wsL32[s];
+  for (long long e = tid; e < (long long)nI * ld; e += T) Lb[e] = 0.f;
   __syncthreads();
   for (int a = tid; a < nI; a += T) {
     long long b0 = coff + lr[a];
     for (int q = 0; q < lcntI[off + a]; ++q) {
       int c = lcol[b0 + q];
-      if (c <= a) Lb[(long long)a * ld + (c - a + bw)] = lvalD[b0 + q];
+      if (c <= a) Lb[(long long)a * ld + (c - a + bw)] = (float)lvalD[b0 + q];
     }
   }
   __syncthreads();
-  __shared__ double sh_piv[2];
+  __shared__ float sh_piv[2];
   for (int k = 0; k < nI; ++k) {
     // pivot square root and reciprocal once, by thread 0 (see k_schur)
     if (tid == 0) {
-      double piv = Lb[(long long)k * ld + bw];
+      float piv = Lb[(long long)k * ld + bw];
       sh_piv[0] = piv;
-      if (piv > 0.0) {
-        double lkk = sqrt(piv);
+      if (piv > 0.f) {
+        float lkk = sqrtf(piv);
         Lb[(long long)k * ld + bw] = lkk;
-        sh_piv[1] = 1.0 / lkk;
+        sh_piv[1] = 1.f / lkk;
       }
     }
     __syncthreads();
-    if (!(sh_piv[0] > 0.0)) {
+    if (!(sh_piv[0] > 0.f)) {
       if (tid == 0) dev_fail(st, HK_EIG_FAIL, s, sh_piv[0]);
       return;
     }
-    double il = sh_piv[1];
+    float il = sh_piv[1];
     int iend = min(nI - 1, k + bw);
     for (int i = k + 1 + tid; i <= iend; i += T) Lb[(long long)i * ld + (k - i + bw)] *= il;
     __syncthreads();
     for (int i = k + 1 + (tid >> 5); i <= iend; i += T >> 5) {
-      double lik = Lb[(long long)i * ld + (k - i + bw)];
+      float lik = Lb[(long long)i * ld + (k - i + bw)];
       for (int j = k + 1 + (tid & 31); j <= i; j += 32)
         Lb[(long long)i * ld + (j - i + bw)] -= lik * Lb[(long long)j * ld + (k - j + bw)];
     }
     __syncthreads();
   }
-  for (long long e = tid; e < (long long)nI * ld; e += T) L32[e] = (float)Lb[e];
 }
 
 // One forward substitution step for row a of a thread's column: v = (x - sum L[a][k] y[k]) / L[a][a]
@@ -1234,7 +1233,7 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
     hk_set_error("local band width %d too large for the standard-form kernels", maxbw);
     return HK_UNSUPPORTED;
   }
-  k_dchol<<<ns, 128, 0, st>>>(h->d_sub_info, h->d_sub_off, d_bw, h->d_lrow, h->d_lcntI, h->d_lcol, h->d_lvalD, d_L,
+  k_dchol<<<ns, 512, 0, st>>>(h->d_sub_info, h->d_sub_off, d_bw, h->d_lrow, h->d_lcntI, h->d_lcol, h->d_lvalD, d_L,
                               d_L32, d_ws, d_ws32, h->d_status);
   HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();

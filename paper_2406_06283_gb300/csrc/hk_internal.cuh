@@ -272,7 +272,7 @@ hk_status ensure_workspace(hk_handle* h, int s);
 void hk_drop_graphs(hk_handle* h);
 // Raises the shared-memory limit of every apply kernel instantiation (before any graph capture).
 hk_status apply_prepare(hk_handle* h);
-// Times the apply for every admissible number of right-hand sides per CTA (1, 2, 4, 8) at batch size s
+// Times the apply for every admissible number of right-hand sides per CTA (1, 2, 4, 8, 16) at batch size s
 // and keeps the fastest (the arithmetic per right-hand side is the same for all of them).
 hk_status apply_autotune(hk_handle* h, int s);
 // z = M^{-1} v for s vectors (v, z: s x n device arrays, FP64).  `active` is NULL or

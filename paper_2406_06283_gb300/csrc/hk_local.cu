@@ -502,12 +502,13 @@ static hk_status apply_t(hk_handle* h, int s, const double* v, double* z, const 
   int do_local = h->p.levels != HK_COARSE_ONLY;
   int do_coarse = h->p.levels != HK_ONE_LEVEL && h->n0 > 0;
   size_t budget = 220 * 1024 - 2 * (size_t)h->pack_stage;
-  int nr = 8;
+  int nr = 16;
   while (nr > 1 && (nr > s || sizeof(T) * ((size_t)h->max_dof + HK_MAXB) * nr > budget)) nr >>= 1;
   auto tuned = h->nr_tuned.find(s);
   if (tuned != h->nr_tuned.end() && tuned->second <= nr) nr = tuned->second;
   hk_status rc;
   switch (nr) {
+    case 16: rc = launch_local<T, 16>(h, s, v, active, Zt, ybuf, c, do_local, do_coarse); break;
     case 8: rc = launch_local<T, 8>(h, s, v, active, Zt, ybuf, c, do_local, do_coarse); break;
     case 4: rc = launch_local<T, 4>(h, s, v, active, Zt, ybuf, c, do_local, do_coarse); break;
     case 2: rc = launch_local<T, 2>(h, s, v, active, Zt, ybuf, c, do_local, do_coarse); break;
@@ -534,10 +535,12 @@ hk_status apply_prepare(hk_handle*) {
   HK_TRY(hk_allow_smem(k_local_apply<float, 2>));
   HK_TRY(hk_allow_smem(k_local_apply<float, 4>));
   HK_TRY(hk_allow_smem(k_local_apply<float, 8>));
+  HK_TRY(hk_allow_smem(k_local_apply<float, 16>));
   HK_TRY(hk_allow_smem(k_local_apply<double, 1>));
   HK_TRY(hk_allow_smem(k_local_apply<double, 2>));
   HK_TRY(hk_allow_smem(k_local_apply<double, 4>));
   HK_TRY(hk_allow_smem(k_local_apply<double, 8>));
+  HK_TRY(hk_allow_smem(k_local_apply<double, 16>));
   return HK_OK;
 }
 
@@ -551,7 +554,7 @@ hk_status apply_autotune(hk_handle* h, int s) {
   int best = 0;
   float best_ms = 1e30f;
   hk_status rc = HK_OK;
-  for (int nr = 1; nr <= 8 && nr <= s && rc == HK_OK; nr *= 2) {
+  for (int nr = 1; nr <= 16 && nr <= s && rc == HK_OK; nr *= 2) {
     h->nr_tuned[s] = nr;
     // inputs: the (zero-initialised) first Krylov block; output: the first flexible block
     rc = op_apply(h, s, h->d_V, h->d_Zk, nullptr);  // warm-up
