@@ -234,10 +234,14 @@ def run_ours(args, world, rank, local):
         return hk.hk_setup_device(d_xyz, d_el, d_bnd, d_coeff, p.k, d_e2s, p.n_sub, p.overlap, p.tau, precision,
                                   hk.HK_TWO_LEVEL, hk.HK_AS, p.restart, p.max_iters, sptr, n_dofs=m.n_dofs)
 
-    def device_step(record=None, timing=False):
+    def device_step(record=None, timing=False, graphs=True):
         """One step: setup + solve + destroy.  With timing, the solve records per-kernel CUDA events,
-        which drives its loops from the host instead of the captured graph (used once, untimed)."""
+        which drives its loops from the host instead of the captured graph (used once, untimed).
+        graphs=False launches the solve's kernels one by one (profilers cannot see kernel nodes of a
+        graph with conditional nodes)."""
         h = setup_dev()
+        if not graphs:
+            hk.hk_set_solve_graphs(h, False)
         if timing:
             hk.hk_set_timing(h, True)
         r = hk.hk_solve_device(h, d_rhs, d_u, p.tol)
@@ -254,7 +258,7 @@ def run_ours(args, world, rank, local):
     rec = []
     step_ms = []
     if args.profile_run:
-        device_step()
+        device_step(graphs=False)
         torch.cuda.synchronize()
         if rank == 0:
             print(json.dumps({"profile_run": True, "workload": p.name}), flush=True)
@@ -598,7 +602,8 @@ def main():
     ap.add_argument("--solve-reps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-run", action="store_true",
-                    help="one warm-up step and one step, nothing else (for ncu captures)")
+                    help="one warm-up step and one step with the solve's kernels launched one by one, "
+                         "nothing else (for ncu captures)")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":

@@ -199,11 +199,12 @@ hk_status hk_apply_precond(hk_handle* h, int n_rhs, const double* v, double* z);
  * framework that forbids allocations on its hot path).  z_dev = M^{-1} v_dev for n_rhs device
  * vectors (n_rhs * n_dofs doubles each, caller-owned).  Intermediate vectors live in one fixed
  * 8 MiB device array per device, held from library load until process exit; a request that
- * needs more (n_rhs * (sum_i |dof(Omega_i)| + 2 (n0 + 1)) elements of 4 bytes in the FP32 form,
+ * needs more (n_rhs * (2 sum_i |dof(Omega_i)| + 2 (n0 + 1)) elements of 4 bytes in the FP32 form,
  * 8 in the FP64 form, each part rounded up to 256 bytes) returns HK_UNSUPPORTED before any
  * launch.  The first call on a device looks the array's address up (call it before any stream
- * capture).  All calls share the array: calls that overlap on the GPU race.  Runs on the
- * handle's stream; calls no cudaMalloc/cudaFree or allocating library routine. */
+ * capture).  All calls share the array: calls that overlap on the GPU race.  Ordered on the
+ * handle's stream (the coarse part runs on the handle's auxiliary stream, forked from and
+ * joined back into it); calls no cudaMalloc/cudaFree or allocating library routine. */
 hk_status hk_apply_precond_noalloc(hk_handle* h, int n_rhs, const double* v_dev, double* z_dev);
 
 /* y = B x for n_rhs host vectors. */

@@ -109,6 +109,9 @@ static void destroy_all(hk_handle* h) {
   }
   if (h->ev_lf) cudaEventDestroy(h->ev_lf);
   h->ev_lf = nullptr;
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  h->ev_fork = h->ev_join = nullptr;
   if (h->cap_stream) {
     cudaStreamSynchronize(h->cap_stream);
     cudaStreamDestroy(h->cap_stream);

@@ -90,7 +90,7 @@ struct hk_handle {
   double k = 0;
   hk_params p{};
   // sizes
-  int nnz = 0, n0 = 0, max_mu = 0, lambda_elems = 0, max_level = 0, max_dof = 0;
+  int nnz = 0, n0 = 0, max_mu = 0, lambda_elems = 0, max_level = 0, max_dof = 0, max_L = 0, n_sm = 0;
   long long I_total = 0, G_total = 0, f_total = 0, csr_total = 0, z_total = 0, lower_nnz = 0;
   std::vector<Sub> subs;
   double setup_ms[8] = {0};
@@ -188,6 +188,7 @@ struct hk_handle {
   cudaStream_t cap_stream = nullptr;  // blocking stream for graphs when the handle's stream is the legacy one
   cudaStream_t aux_stream = nullptr;  // setup: local factors overlapping the eigenproblems
   cudaEvent_t ev_lf = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // apply: coarse path beside the local sweeps
   bool lf_pending = false;
   int* d_ctl = nullptr;         // [0] inner step j, [1] cycles run, [2] inner steps run
   const int* g_jp = nullptr;    // while an inner step is captured: the device word holding j

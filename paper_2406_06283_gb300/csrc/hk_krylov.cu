@@ -354,12 +354,12 @@ hk_status ensure_workspace(hk_handle* h, int s) {
   HK_TRY(dalloc(h, &h->d_x, (size_t)s * n));
   HK_TRY(dalloc(h, &h->d_f, (size_t)s * n));
   if (h->p.precision == HK_FP32_PRECOND) {
-    HK_TRY(dalloc(h, &h->d_ybuf32, (size_t)s * h->I_total));
+    HK_TRY(dalloc(h, &h->d_ybuf32, 2 * (size_t)s * h->I_total));  // local solutions | coarse prolongation
     HK_TRY(dalloc(h, &h->d_c32, (size_t)s * (h->n0 + 1)));
     HK_TRY(dalloc(h, &h->d_cc32, (size_t)s * (h->n0 + 1)));
     h->d_ybuf64 = nullptr; h->d_c64 = nullptr; h->d_cc64 = nullptr;
   } else {
-    HK_TRY(dalloc(h, &h->d_ybuf64, (size_t)s * h->I_total));
+    HK_TRY(dalloc(h, &h->d_ybuf64, 2 * (size_t)s * h->I_total));  // local solutions | coarse prolongation
     HK_TRY(dalloc(h, &h->d_c64, (size_t)s * (h->n0 + 1)));
     HK_TRY(dalloc(h, &h->d_cc64, (size_t)s * (h->n0 + 1)));
     h->d_ybuf32 = nullptr; h->d_c32 = nullptr; h->d_cc32 = nullptr;

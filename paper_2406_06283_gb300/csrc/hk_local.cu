@@ -12,6 +12,9 @@
 // each block starting on a 4-element boundary; the sparse L_j is read from
 // the local CSR.  S_j^{-1} is formed in FP64 by Gauss-Jordan elimination with
 // partial pivoting; a pivot below 1e-10 max|B_i| reports HK_SINGULAR_LOCAL.
+// For the apply, the forward step is rewritten with W_j = S_j^{-1} L_j as
+//     y_j = [-W_j | S_j^{-1}] [y_{j-1}; r_j],
+// one dense product over two consecutive levels of the level-ordered vector.
 #include <algorithm>
 
 #include "hk_internal.cuh"
@@ -142,13 +145,15 @@ void launch_to_f32(const double* a, float* b, long long n, cudaStream_t st) {
 
 
 // ====================================================================== apply
-// Level records, streamed by the apply kernel one after another:
-//   forward record j:  S_j^{-1} (b_j x b_j, T) | L_j values (nc_j, T) |
-//                      L_j columns in level j-1 (nc_j, uint16) | L_j row pointers (b_j + 1, uint16)
-//   backward record j: G_j (b_j x b_{j+1}, T)
-// each padded to 16 bytes so that one 1-D TMA bulk copy moves it to shared memory.
+// Level records, streamed by the apply kernel one after another, row-major with rows
+// padded to a multiple of 4 entries (zeros), so that rows start on 16-byte boundaries:
+//   forward record j:  F_j = [-W_j | S_j^{-1}]   b_j x pad4(b_{j-1} + b_j), T
+//   backward record j: G_j                      b_j x pad4(b_{j+1}),       T
+// A record streams as chunks of consecutive rows, one 1-D TMA bulk copy each, of at most
+// HK_CHUNK_BYTES (one chunk per record on 2D subdomains).
 // Level table entry (4 x int64 per level): fwd offset, bwd offset, fwd | bwd bytes << 32,
-// nc | b << 20 | level start << 40.
+// fwd rows per chunk | bwd rows per chunk << 10 | b << 20 | level start << 40.
+#define HK_CHUNK_BYTES (32 * 1024)
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
@@ -187,7 +192,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 }
 
 __host__ __device__ __forceinline__ long long pad16(long long x) { return (x + 15) & ~15LL; }
-__host__ __device__ __forceinline__ int lv_nc(long long e3) { return (int)(e3 & 0xFFFFF); }
+__host__ __device__ __forceinline__ int lv_rcf(long long e3) { return (int)(e3 & 0x3FF); }
+__host__ __device__ __forceinline__ int lv_rcb(long long e3) { return (int)((e3 >> 10) & 0x3FF); }
 __host__ __device__ __forceinline__ int lv_b(long long e3) { return (int)((e3 >> 20) & 0xFFFFF); }
 __host__ __device__ __forceinline__ int lv_start(long long e3) { return (int)(e3 >> 40); }
 
@@ -225,270 +231,553 @@ __global__ void k_pack_levels(const int* __restrict__ sub_info, const long long*
   long long bo = foff;
   for (int j = 0; j < L; ++j) {
     int r0 = lp[j], b = lp[j + 1] - r0, bn = j + 1 < L ? lp[j + 2] - lp[j + 1] : 0;
+    int pr0 = j > 0 ? lp[j - 1] : r0, bp = r0 - pr0;
     const long long* e = lvtab + 4 * (long long)(loff + j);
-    int nc = lv_nc(e[3]);
-    T* S = reinterpret_cast<T*>(pack + e[0]);
-    T* Lv = S + (long long)b * b;
-    uint16_t* Lc = reinterpret_cast<uint16_t*>(Lv + nc);
-    uint16_t* Lp = Lc + nc;
-    for (int q = tid; q < b * b; q += T_) S[q] = (T)F[bo + q];
-    if (tid == 0 && j > 0) {
-      int pr0 = lp[j - 1], c = 0;
-      for (int a = r0; a < r0 + b; ++a) {
-        Lp[a - r0] = (uint16_t)c;
-        for (int q = 0; q < lcntI[off + a]; ++q) {
-          int col = lcol[coff + lr[a] + q];
-          if (col < r0) {
-            Lv[c] = (T)lvalB[coff + lr[a] + q];
-            Lc[c] = (uint16_t)(col - pr0);
-            ++c;
-          }
-        }
-      }
-      Lp[b] = (uint16_t)c;
-    }
-    if (tid == 0 && j == 0) Lp[0] = 0, Lp[b] = 0;
+    int ldf = (int)pad4(bp + b), ldb = (int)pad4(bn);
     long long go = bo + pad4((long long)b * b);
+    T* Fr = reinterpret_cast<T*>(pack + e[0]);
+    for (int q = tid; q < b * ldf; q += T_) {
+      int row = q / ldf, col = q % ldf;
+      double v = 0;
+      if (col < bp) {
+        // -W_j[row][c] = -sum_a S_j^{-1}[row][a] B[a][c]; B symmetric: the couplings of row c of
+        // level j-1 with level j
+        int c = pr0 + col;
+        const int* cl = lcol + coff + lr[c];
+        const double* cv = lvalB + coff + lr[c];
+        for (int t = 0; t < lcntI[off + c]; ++t) {
+          int a = cl[t];
+          if (a >= r0 && a < r0 + b) v -= F[bo + (long long)row * b + (a - r0)] * cv[t];
+        }
+      } else if (col < bp + b) {
+        v = F[bo + (long long)row * b + (col - bp)];
+      }
+      Fr[q] = (T)v;
+    }
     if (bn > 0) {
-      T* G = reinterpret_cast<T*>(pack + e[1]);
-      for (int q = tid; q < b * bn; q += T_) G[q] = (T)F[go + q];
+      T* Gr = reinterpret_cast<T*>(pack + e[1]);
+      for (int q = tid; q < b * ldb; q += T_) {
+        int row = q / ldb, col = q % ldb;
+        Gr[q] = col < bn ? (T)F[go + (long long)row * bn + col] : (T)0;
+      }
     }
     bo = go + pad4((long long)b * bn);
   }
 }
 
 // One CTA per (subdomain, group of NR right-hand sides): gather r_i = v[dof(Omega_i)]
-// (R_i of Eq. 2.22), coarse restriction c_i = Z_i^T r_i (R_0 = Z^T, Eq. 2.23), the
-// forward and backward block sweeps of B_i^{-1}, and the local solution written to
-// ybuf.  The level records stream through two shared-memory buffers by TMA bulk
-// copies, the copy of record r+2 overlapping the work on record r.  Shared vectors
-// are right-hand-side major (x[rr * nI + a]).  T: float (FP32 form) or double.
+// (R_i of Eq. 2.22), the forward and backward block sweeps of B_i^{-1}, and the local
+// solution written to ybuf.  T: float (FP32 form) or double.
+//
+// Warp roles.  The last warp is the producer: one lane streams the 2L-1 level records
+// into a ring of K shared-memory stages by 1-D TMA bulk copies, each stage guarded by a
+// "full" mbarrier (transaction bytes) and an "empty" mbarrier (one arrival per sweeping
+// warp), so up to K records are in flight while the sweeps run.  The other warps gather
+// together, then split into sweep groups: group g owns right-hand sides
+// g*R .. g*R+R-1 (R = min(NR, 4)) and has WG warps.  A level's rows are spread over the
+// group's threads, G lanes per row on contiguous 4-column chunks (G as large as keeps
+// every row in one pass), then a shuffle sum over the G lanes.  A level step is a few
+// dependent shared-memory loads and FMAs and one or two barriers of the group only.
+// Shared vectors are level-row major within a group, x[(g * (nI + 4) + a) * R + i]; four
+// zero rows after each group's rows keep the padded last columns of a record finite.
+// Every wait is bounded; a wait that gives up reports HK_TIMEOUT, and the producer lets
+// the copies it has in flight land before the CTA exits.
+#define HK_APPLY_MAXK 24
+
+// R-vector loads and stores of shared-memory rows, as 16- or 8-byte accesses where the
+// row size allows (rows are aligned to their size).
+template <typename T, int R>
+__device__ __forceinline__ void ldv(T* o, const T* p) {
+  if constexpr (sizeof(T) == 4 && R == 4) {
+    float4 q = *reinterpret_cast<const float4*>(p);
+    o[0] = q.x, o[1] = q.y, o[2] = q.z, o[3] = q.w;
+  } else if constexpr (sizeof(T) == 4 && R == 2) {
+    float2 q = *reinterpret_cast<const float2*>(p);
+    o[0] = q.x, o[1] = q.y;
+  } else if constexpr (sizeof(T) == 8 && R % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < R; i += 2) {
+      double2 q = *reinterpret_cast<const double2*>(p + i);
+      o[i] = q.x, o[i + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < R; ++i) o[i] = p[i];
+  }
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void stv(T* p, const T* o) {
+  if constexpr (sizeof(T) == 4 && R == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+  } else if constexpr (sizeof(T) == 4 && R == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
+  } else if constexpr (sizeof(T) == 8 && R % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < R; i += 2) *reinterpret_cast<double2*>(p + i) = make_double2(o[i], o[i + 1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < R; ++i) p[i] = o[i];
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that also gives up once another warp of the CTA has flagged a failure.
+__device__ __forceinline__ bool mbar_wait_or_fail(uint64_t* bar, unsigned parity, const volatile int* fail) {
+  for (unsigned it = 0; it < (1u << 22); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63u) == 63u && *fail) return false;
+  }
+  return false;
+}
+
+// Barrier over the WG warps of a sweep group that also ORs a flag across them.
+__device__ __forceinline__ int group_any(int flag, int WG, int id) {
+  if (WG == 1) {
+    __syncwarp();
+    return __any_sync(0xffffffffu, flag);
+  }
+  int r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.s32 q, %1, 0;\n bar.red.or.pred p, %2, %3, q;\n selp.s32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"(flag), "r"(id), "r"(WG * 32)
+      : "memory");
+  return r;
+}
+
+__device__ __forceinline__ void group_sync(int WG, int id) {
+  if (WG == 1) __syncwarp();
+  else asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(WG * 32) : "memory");
+}
+
+// Four consecutive entries of a record row (16-byte aligned).
+template <typename T>
+__device__ __forceinline__ void ld4(T* m, const T* p) {
+  if constexpr (sizeof(T) == 4) {
+    float4 q = *reinterpret_cast<const float4*>(p);
+    m[0] = q.x, m[1] = q.y, m[2] = q.z, m[3] = q.w;
+  } else {
+    double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    m[0] = a.x, m[1] = a.y, m[2] = b.x, m[3] = b.y;
+  }
+}
+
+// acc += sum over the 4-column chunks v0 .. v1-1 of one record row of  row[t] * x[t]
+// (x[t] an R-vector in shared memory).
+template <typename T, int R>
+__device__ __forceinline__ void row_chunk_dot(const T* __restrict__ row, const T* xin, int v0, int v1, T (&acc)[R]) {
+#pragma unroll 2
+  for (int v = v0; v < v1; ++v) {
+    T m[4];
+    ld4<T>(m, row + 4 * v);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      T w[R];
+      ldv<T, R>(w, xin + (4 * v + u) * R);
+#pragma unroll
+      for (int i = 0; i < R; ++i) acc[i] += m[u] * w[i];
+    }
+  }
+}
+
 template <typename T, int NR>
-__global__ void __launch_bounds__(256) k_local_apply(
+__global__ void __launch_bounds__(1024, 1) k_local_apply(
     int n, int s_tot, const double* __restrict__ v, const int* __restrict__ active,
     const int* __restrict__ sub_info, const long long* __restrict__ sub_off, const int* __restrict__ Ilev,
-    const long long* __restrict__ lvtab, const unsigned char* __restrict__ pack, const T* __restrict__ Zt,
-    int do_local, int do_coarse, long long I_total, int n0, int stage_bytes, T* ybuf, T* cvec, DevStatus* st,
-    const int* __restrict__ jp, long long jstride) {
+    const long long* __restrict__ lvtab, const unsigned char* __restrict__ pack, long long I_total,
+    int stage_bytes, int K, int WG, int max_L, T* ybuf, DevStatus* st, const int* __restrict__ jp,
+    long long jstride) {
+  constexpr int R = NR < 4 ? NR : 4;
+  constexpr int WS = NR / R;  // sweep groups
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  if (jp) v += (long long)(*jp) * jstride;  // captured inner step: v = v_j with j read on the device
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t full[HK_APPLY_MAXK], empty[HK_APPLY_MAXK];
   __shared__ int sh_fail;
-  unsigned char* stage[2] = {smem_raw, smem_raw + stage_bytes};
+  if (jp) v += (long long)(*jp) * jstride;  // captured inner step: v = v_j with j read on the device
   int s = blockIdx.x, r_base = blockIdx.y * NR;
-  int tid = threadIdx.x, T_ = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = T_ >> 5;
+  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int nwarps = blockDim.x >> 5, nwc = nwarps - 1;  // consumer warps; the last warp produces
+  int nct = nwc * 32;
+  bool producer = warp == nwarps - 1;
   const int* si = sub_info + 8 * s;
-  int nI = si[0], L = si[2], off = si[3], loff = si[5], m = si[6], c_off = si[7];
-  long long zoff = sub_off[3 * s + 2];
-  T* x = reinterpret_cast<T*>(smem_raw + 2 * (long long)stage_bytes);  // NR x nI
-  T* tmp = x + (long long)nI * NR;                                       // NR x HK_MAXB
+  int nI = si[0], L = si[2], off = si[3], loff = si[5];
+  int xs = nI + 4;  // rows per group slice of x
+  // shared memory: record ring | level table (4 x int64 per level) | x
+  long long* tab = reinterpret_cast<long long*>(smem_raw + (long long)K * stage_bytes);
+  T* x = reinterpret_cast<T*>(tab + 4 * (long long)max_L);  // WS groups x (nI + 4) x R
   int nr = s_tot - r_base < NR ? s_tot - r_base : NR;
-  bool act[NR];
-  for (int r = 0; r < NR; ++r) act[r] = r < nr && (active == nullptr || active[8 * (r_base + r)]);
-  const long long* lv = lvtab + 4 * (long long)loff;
-  int nrec = do_local ? 2 * L - 1 : 0;
-  auto rec_src = [&](int r, unsigned& bytes) -> const unsigned char* {
-    const long long* e = lv + 4 * (r < L ? r : 2 * L - 2 - r);
-    if (r < L) {
-      bytes = (unsigned)(e[2] & 0xffffffffLL);
-      return pack + e[0];
-    }
-    bytes = (unsigned)((unsigned long long)e[2] >> 32);
-    return pack + e[1];
+  int nlev = 2 * L - 1;  // level steps: forward 0 .. L-1, backward L-2 .. 0
+  // the producer's position in the chunk stream: level step ps_rs, chunk ps_c
+  int ps_rs = 0, ps_c = 0;
+  auto next_chunk = [&](const unsigned char*& src, unsigned& bytes) -> bool {
+    if (ps_rs >= nlev) return false;
+    bool fwd = ps_rs < L;
+    const long long* e = tab + 4 * (fwd ? ps_rs : 2 * L - 2 - ps_rs);
+    long long e3 = e[3];
+    int b = lv_b(e3), rc = fwd ? lv_rcf(e3) : lv_rcb(e3);
+    long long tot = fwd ? (e[2] & 0xffffffffLL) : (long long)((unsigned long long)e[2] >> 32);
+    long long rowb = tot / b;
+    int row0 = ps_c * rc, nrows = b - row0 < rc ? b - row0 : rc;
+    src = pack + (fwd ? e[0] : e[1]) + row0 * rowb;
+    bytes = (unsigned)(nrows * rowb);
+    if (row0 + nrows >= b) ++ps_rs, ps_c = 0;
+    else ++ps_c;
+    return true;
   };
+  for (int e = tid; e < 4 * L; e += blockDim.x) tab[e] = lvtab[4 * (long long)loff + e];
   if (tid == 0) {
     sh_fail = 0;
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    for (int r = 0; r < 2 && r < nrec; ++r) {
-      unsigned bytes;
-      const unsigned char* src = rec_src(r, bytes);
-      mbar_expect_tx(&bar[r], bytes);
-      tma_load_1d(stage[r], src, bytes, &bar[r]);
+    for (int k = 0; k < K; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], WS * WG);
     }
-  }
-  // gather (overlaps the first two record copies)
-  for (int e = tid; e < nI * NR; e += T_) {
-    int rr = e / nI, a = e % nI;
-    x[e] = act[rr] ? (T)v[(long long)(r_base + rr) * n + Ilev[off + a]] : (T)0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (do_coarse) {
-    for (int l = warp; l < m; l += nw) {
-      const T* zc = Zt + zoff + (long long)l * nI;
-      T acc[NR];
-      for (int rr = 0; rr < NR; ++rr) acc[rr] = 0;
-      for (int a = lane; a < nI; a += 32) {
-        T zv = zc[a];
-        for (int rr = 0; rr < NR; ++rr) acc[rr] += zv * x[rr * nI + a];
-      }
-      for (int rr = 0; rr < NR; ++rr) {
-        T t = acc[rr];
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0 && act[rr]) cvec[(long long)(r_base + rr) * n0 + c_off + l] = t;
-      }
+  int issued = 0;
+  if (producer && lane == 0) {
+    const unsigned char* src;
+    unsigned bytes;
+    for (; issued < K && next_chunk(src, bytes); ++issued) {
+      mbar_expect_tx(&full[issued], bytes);
+      tma_load_1d(smem_raw + (long long)issued * stage_bytes, src, bytes, &full[issued]);
     }
   }
-  if (!do_local) return;
-  unsigned phase[2] = {0u, 0u};
-  for (int r = 0; r < nrec; ++r) {
-    int bi = r & 1;
-    if (!mbar_wait_bounded(&bar[bi], phase[bi])) atomicExch(&sh_fail, 1);
-    phase[bi] ^= 1u;
-    __syncthreads();
-    if (sh_fail) {
-      if (tid == 0) dev_fail(st, HK_TIMEOUT, s, r);
-      // let the other buffer's copy (if any) land before the CTA exits
-      if (r + 1 < nrec) mbar_wait_bounded(&bar[bi ^ 1], phase[bi ^ 1]);
-      return;
-    }
-    const unsigned char* buf = stage[bi];
-    int j = r < L ? r : 2 * L - 2 - r;
-    long long e3 = lv[4 * j + 3];
-    int nc = lv_nc(e3), b = lv_b(e3), ls = lv_start(e3);
-    // G threads per output row (a power of two with b * G <= blockDim)
-    int G = 1;
-    while (G < 32 && b * G * 2 <= T_) G <<= 1;
-    int grp = tid / G, gl = tid % G, ngrp = T_ / G;
-    if (r < L) {
-      const T* S = reinterpret_cast<const T*>(buf);
-      const T* Lv = S + (long long)b * b;
-      const uint16_t* Lc = reinterpret_cast<const uint16_t*>(Lv + nc);
-      const uint16_t* Lp = Lc + nc;
-      // t_j = r_j - L_j y_{j-1}  into tmp
-      int ps = j > 0 ? lv_start(lv[4 * (j - 1) + 3]) : 0;
-      for (int q = tid; q < b * NR; q += T_) {
-        int rr = q / b, a = q % b;
-        T acc = x[rr * nI + ls + a];
-        if (j > 0)
-          for (int t = Lp[a]; t < Lp[a + 1]; ++t) acc -= Lv[t] * x[rr * nI + ps + Lc[t]];
-        tmp[rr * HK_MAXB + a] = acc;
+  if (!producer) {
+    // gather, four elements per thread in flight (index loads, then value loads)
+    int tot = nI * NR;
+    for (int e0 = tid; e0 < tot; e0 += 4 * nct) {
+      int idx[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int e = e0 + u * nct;
+        idx[u] = e < tot ? Ilev[off + e % nI] : 0;
       }
-      __syncthreads();
-      // y_j = S_j^{-1} t_j, written in place
-      // every thread runs the same trip count so that the group shuffles see full warps
-      for (int q0 = 0; q0 < b; q0 += ngrp) {
-        int q = q0 + grp;
-        bool valid = q < b;
-        T acc[NR];
-        for (int rr = 0; rr < NR; ++rr) acc[rr] = 0;
-        if (valid)
-          for (int t = gl; t < b; t += G) {
-            T sv = S[q * b + t];
-            for (int rr = 0; rr < NR; ++rr) acc[rr] += sv * tmp[rr * HK_MAXB + t];
-          }
-        for (int rr = 0; rr < NR; ++rr) {
-          T a2 = acc[rr];
-          for (int o = G >> 1; o > 0; o >>= 1) a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-          if (valid && gl == 0) x[rr * nI + ls + q] = a2;
-        }
-      }
-    } else {
-      const T* Gm = reinterpret_cast<const T*>(buf);
-      int bn = lv_b(lv[4 * (j + 1) + 3]);
-      int ns = ls + b;
-      for (int q0 = 0; q0 < b; q0 += ngrp) {
-        int q = q0 + grp;
-        bool valid = q < b;
-        T acc[NR];
-        for (int rr = 0; rr < NR; ++rr) acc[rr] = 0;
-        if (valid)
-          for (int t = gl; t < bn; t += G) {
-            T gv = Gm[q * bn + t];
-            for (int rr = 0; rr < NR; ++rr) acc[rr] += gv * x[rr * nI + ns + t];
-          }
-        for (int rr = 0; rr < NR; ++rr) {
-          T a2 = acc[rr];
-          for (int o = G >> 1; o > 0; o >>= 1) a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-          if (valid && gl == 0) x[rr * nI + ls + q] -= a2;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int e = e0 + u * nct;
+        if (e < tot) {
+          int rr = e / nI, a = e % nI;
+          bool on = rr < nr && (active == nullptr || active[8 * (r_base + rr)]);
+          x[((long long)(rr / R) * xs + a) * R + rr % R] = on ? (T)v[(long long)(r_base + rr) * n + idx[u]] : (T)0;
         }
       }
     }
-    __syncthreads();  // every thread is done with this buffer
-    if (tid == 0 && r + 2 < nrec) {
-      unsigned bytes;
-      const unsigned char* src = rec_src(r + 2, bytes);
+    for (int e = tid; e < WS * 4 * R; e += nct) {  // the zero rows after each group's slice
+      int g = e / (4 * R), q = e % (4 * R);
+      x[((long long)g * xs + nI) * R + q] = (T)0;
+    }
+  }
+  __syncthreads();
+  if (producer) {
+    if (lane != 0) return;
+    const unsigned char* src;
+    unsigned bytes;
+    bool failed = false;
+    for (; next_chunk(src, bytes); ++issued) {
+      int k = issued % K;
+      if (!mbar_wait_or_fail(&empty[k], (unsigned)((issued / K) - 1) & 1u, &sh_fail)) {
+        if (atomicExch(&sh_fail, 1) == 0) dev_fail(st, HK_TIMEOUT, s, issued);
+        failed = true;
+        break;
+      }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_expect_tx(&bar[bi], bytes);
-      tma_load_1d(stage[bi], src, bytes, &bar[bi]);
+      mbar_expect_tx(&full[k], bytes);
+      tma_load_1d(smem_raw + (long long)k * stage_bytes, src, bytes, &full[k]);
+    }
+    if (failed) {  // let the copies in flight land before the CTA exits
+      for (int r = issued - K < 0 ? 0 : issued - K; r < issued; ++r)
+        mbar_wait_bounded(&full[r % K], (unsigned)(r / K) & 1u);
+    }
+    return;
+  }
+  int g = warp / WG, wr = warp % WG;
+  int bar_id = 1 + g, nthr = 32 * WG, gt = wr * 32 + lane;
+  T* xg = x + (long long)g * xs * R;
+  int ks = 0;            // stage of the next chunk
+  unsigned kph = 0;       // its phase parity
+  for (int rs = 0; rs < nlev; ++rs) {
+    bool fwd = rs < L;
+    int j = fwd ? rs : 2 * L - 2 - rs;
+    long long e3 = tab[4 * j + 3];
+    int b = lv_b(e3), ls = lv_start(e3), rc = fwd ? lv_rcf(e3) : lv_rcb(e3);
+    // forward: input rows [ls - bo, ls + b) = [y_{j-1}; r_j]; backward: x_{j+1} at [ls + b, ls + b + bo)
+    int bo = fwd ? (j > 0 ? ls - lv_start(tab[4 * (j - 1) + 3]) : 0) : lv_b(tab[4 * (j + 1) + 3]);
+    int ld = fwd ? (int)pad4(bo + b) : (int)pad4(bo);
+    const T* xin = xg + (long long)(fwd ? ls - bo : ls + b) * R;
+    int lg = 0;  // G = 2^lg lanes per row, as many as keep b * G <= nthr (one pass)
+    while (lg < 5 && (b << (lg + 1)) <= nthr) ++lg;
+    int G = 1 << lg;
+    int q = gt >> lg, gl = gt & (G - 1);
+    int nv = ld >> 2, cv = (nv + G - 1) >> lg;
+    int v0 = gl * cv, v1 = min(nv, v0 + cv);
+    T acc[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) acc[i] = (T)0;
+    bool okl = true;
+    for (int row0 = 0; row0 < b; row0 += rc) {
+      int k = ks;
+      bool ok = mbar_wait_or_fail(&full[k], kph, &sh_fail);
+      if (++ks == K) ks = 0, kph ^= 1u;
+      if (!ok) {
+        if (atomicExch(&sh_fail, 1) == 0) dev_fail(st, HK_TIMEOUT, s, rs);
+        okl = false;
+        continue;
+      }
+      const T* buf = reinterpret_cast<const T*>(smem_raw + (long long)k * stage_bytes);
+      if (q >= row0 && q < b && q < row0 + rc) row_chunk_dot<T, R>(buf + (long long)(q - row0) * ld, xin, v0, v1, acc);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[k]);
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+      for (int o = G >> 1; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+    bool own = q < b && gl == 0;
+    if (fwd) {
+      // y_j = [-W_j | S_j^{-1}] [y_{j-1}; r_j]: every read of r_j ends before y_j overwrites it
+      if (group_any(!okl, WG, bar_id)) return;
+      if (own) stv<T, R>(xg + (long long)(ls + q) * R, acc);
+      group_sync(WG, bar_id);
+    } else {
+      // x_j = y_j - G_j x_{j+1}
+      if (okl && own) {
+        T y[R];
+        ldv<T, R>(y, xg + (long long)(ls + q) * R);
+#pragma unroll
+        for (int i = 0; i < R; ++i) y[i] -= acc[i];
+        stv<T, R>(xg + (long long)(ls + q) * R, y);
+      }
+      if (group_any(!okl, WG, bar_id)) return;
     }
   }
-  for (int e2 = tid; e2 < nI * NR; e2 += T_) {
-    int rr = e2 / nI, a = e2 % nI;
-    if (act[rr]) ybuf[(long long)(r_base + rr) * I_total + off + a] = x[e2];
+  for (int e = gt; e < nI * R; e += nthr) {
+    int a = e / R, i = e % R, rr = g * R + i;
+    if (rr < nr && (active == nullptr || active[8 * (r_base + rr)]))
+      ybuf[(long long)(r_base + rr) * I_total + off + a] = xg[e];
   }
 }
 
-// cc = E^{-1} c for s vectors (E^{-1} dense n0 x n0 row-major): one warp per row.
-template <typename T>
-__global__ void k_coarse_solve(int n0, int s, const T* __restrict__ Einv, const T* __restrict__ c, T* cc,
-                               const int* __restrict__ active) {
-  int lane = threadIdx.x & 31;
-  int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (row >= n0) return;
-  const T* er = Einv + (long long)row * n0;
-  for (int r = 0; r < s; ++r) {
-    if (active && !active[8 * r]) continue;
-    const T* cr = c + (long long)r * n0;
-    T acc = 0;
-    for (int t = lane; t < n0; t += 32) acc += er[t] * cr[t];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) cc[(long long)r * n0 + row] = acc;
+// c_i = Z_i^T v[dof(Omega_i)]  (R_0 = Z^T applied to R_i v, Eq. 2.23) for RB right-hand sides
+// per CTA: the gather of r_i into shared memory (right-hand sides fastest), then a warp per
+// coarse vector l (lanes over dofs, then a fixed shuffle tree).  It runs beside the local
+// sweeps, on the auxiliary stream, so the coarse path leaves the sweeps' critical path.
+template <typename T, int RB>
+__global__ void __launch_bounds__(256) k_restrict(int n, int s_tot, const double* __restrict__ v,
+                                                  const int* __restrict__ active, const int* __restrict__ sub_info,
+                                                  const long long* __restrict__ sub_off, const int* __restrict__ Ilev,
+                                                  const T* __restrict__ Zt, int n0, T* cvec,
+                                                  const int* __restrict__ jp, long long jstride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* r = reinterpret_cast<T*>(smem_raw);  // nI x RB
+  if (jp) v += (long long)(*jp) * jstride;
+  int sb = blockIdx.x, r_base = blockIdx.y * RB;
+  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int* si = sub_info + 8 * sb;
+  int nI = si[0], off = si[3], m = si[6], c_off = si[7];
+  long long zoff = sub_off[3 * sb + 2];
+  int nr = s_tot - r_base < RB ? s_tot - r_base : RB;
+  int tot = nI * RB;
+  for (int e0 = tid; e0 < tot; e0 += 4 * blockDim.x) {
+    int idx[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int e = e0 + u * blockDim.x;
+      idx[u] = e < tot ? Ilev[off + e % nI] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int e = e0 + u * blockDim.x;
+      if (e < tot) {
+        int rr = e / nI, a = e % nI;
+        bool on = rr < nr && (active == nullptr || active[8 * (r_base + rr)]);
+        r[a * RB + rr] = on ? (T)v[(long long)(r_base + rr) * n + idx[u]] : (T)0;
+      }
+    }
+  }
+  __syncthreads();
+  for (int l = warp; l < m; l += nw) {
+    const T* zc = Zt + zoff + (long long)l * nI;
+    T acc[RB];
+#pragma unroll
+    for (int rr = 0; rr < RB; ++rr) acc[rr] = 0;
+#pragma unroll 4
+    for (int a = lane; a < nI; a += 32) {
+      T zv = zc[a];
+#pragma unroll
+      for (int rr = 0; rr < RB; ++rr) acc[rr] += zv * r[a * RB + rr];
+    }
+#pragma unroll
+    for (int rr = 0; rr < RB; ++rr) {
+      T t = acc[rr];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0 && rr < nr && (active == nullptr || active[8 * (r_base + rr)]))
+        cvec[(long long)(r_base + rr) * n0 + c_off + l] = t;
+    }
   }
 }
 
-// z_l = sum over (i, a) holding l of  w * y_i[a] + (Z_i cc_i)[a]   (pull form of
-// the sums in Eq. 2.22-2.23; w = 1, or 1/mu_l for the RAS variant).
-template <typename T>
+// cc_r = E^{-1} c_r for s right-hand sides (E^{-1} dense n0 x n0 row-major), CR right-hand
+// sides per pass: c of the pass is copied once into shared memory (CR x n0), then a warp per
+// row of E^{-1} (rows strided over the grid) streams the row with eight loads in flight per
+// lane.  Each lane sums its columns lane, lane + 32, ... in order, then a fixed shuffle tree.
+#define HK_CS_THREADS 512
+template <typename T, int CR>
+__global__ void __launch_bounds__(HK_CS_THREADS) k_coarse_solve(int n0, int s, const T* __restrict__ Einv,
+                                                                const T* __restrict__ c, T* cc,
+                                                                const int* __restrict__ active) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* cs = reinterpret_cast<T*>(smem_raw);  // CR x n0
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r0 = 0; r0 < s; r0 += CR) {
+    int nr = s - r0 < CR ? s - r0 : CR;
+    __syncthreads();
+    for (int e = threadIdx.x; e < CR * n0; e += blockDim.x) {
+      int r = e / n0, t = e % n0;
+      cs[e] = r < nr ? c[(long long)(r0 + r) * n0 + t] : (T)0;
+    }
+    __syncthreads();
+    for (int row = blockIdx.x * nw + warp; row < n0; row += gridDim.x * nw) {
+      const T* er = Einv + (long long)row * n0;
+      T acc[CR];
+#pragma unroll
+      for (int r = 0; r < CR; ++r) acc[r] = 0;
+#pragma unroll 8
+      for (int t = lane; t < n0; t += 32) {
+        T ev = er[t];
+#pragma unroll
+        for (int r = 0; r < CR; ++r) acc[r] += ev * cs[r * n0 + t];
+      }
+#pragma unroll
+      for (int r = 0; r < CR; ++r) {
+        T a = acc[r];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0 && r < nr && (!active || active[8 * (r0 + r)])) cc[(long long)(r0 + r) * n0 + row] = a;
+      }
+    }
+  }
+}
+
+// zc_i = Z_i cc_i for CR right-hand sides per CTA (the coarse prolongation of Eq. 2.23 on each
+// subdomain; the scatter adds it over the holders of every dof): cc_i in shared memory, a
+// thread per dof of Omega_i summing over the coarse vectors in order.
+template <typename T, int CR>
+__global__ void __launch_bounds__(256) k_prolong(int s, const int* __restrict__ sub_info,
+                                                 const long long* __restrict__ sub_off, const T* __restrict__ Zt,
+                                                 const T* __restrict__ cc, int n0, long long I_total, T* zc,
+                                                 const int* __restrict__ active) {
+  __shared__ T ccs[HK_MAXM * CR];
+  int sb = blockIdx.x, r0 = blockIdx.y * CR;
+  const int* si = sub_info + 8 * sb;
+  int nI = si[0], off = si[3], m = si[6], c_off = si[7];
+  long long zoff = sub_off[3 * sb + 2];
+  int nr = s - r0 < CR ? s - r0 : CR;
+  for (int e = threadIdx.x; e < m * CR; e += blockDim.x) {
+    int q = e / CR, r = e % CR;
+    ccs[e] = r < nr ? cc[(long long)(r0 + r) * n0 + c_off + q] : (T)0;
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < nI; a += blockDim.x) {
+    T acc[CR];
+#pragma unroll
+    for (int r = 0; r < CR; ++r) acc[r] = 0;
+    for (int q = 0; q < m; ++q) {
+      T zv = Zt[zoff + (long long)q * nI + a];
+#pragma unroll
+      for (int r = 0; r < CR; ++r) acc[r] += zv * ccs[q * CR + r];
+    }
+#pragma unroll
+    for (int r = 0; r < CR; ++r)
+      if (r < nr && (!active || active[8 * (r0 + r)])) zc[(long long)(r0 + r) * I_total + off + a] = acc[r];
+  }
+}
+
+// z_l = sum over (i, a) holding l of  w * y_i[a] + zc_i[a]   (pull form of the sums in
+// Eq. 2.22-2.23; w = 1, or 1/mu_l for the RAS variant).  A thread per dof, right-hand sides
+// innermost in chunks of SR; holders in a fixed order, so every run gives the same bits.
+template <typename T, int SR>
 __global__ void k_scatter(int n, int s, const int* __restrict__ pull_ptr, const int* __restrict__ pull_row,
-                          const int* __restrict__ pull_sub, const int* __restrict__ sub_info,
-                          const long long* __restrict__ sub_off, const T* __restrict__ ybuf,
-                          const T* __restrict__ Z, const T* __restrict__ cc, long long I_total, int n0,
-                          int do_local, int do_coarse, int ras, const int* __restrict__ mu, double* z,
+                          const T* __restrict__ ybuf, const T* __restrict__ zc, long long I_total, int do_local,
+                          int do_coarse, int ras, const int* __restrict__ mu, double* z,
                           const int* __restrict__ active, const int* __restrict__ jp, long long jstride) {
   int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n) return;
   if (jp) z += (long long)(*jp) * jstride;  // captured inner step: z = z_j
   int p0 = pull_ptr[l], p1 = pull_ptr[l + 1];
   T wl = ras ? (T)1 / (T)mu[l] : (T)1;
-  for (int r = 0; r < s; ++r) {
-    if (active && !active[8 * r]) continue;
-    T acc = 0;
+  for (int r0 = 0; r0 < s; r0 += SR) {
+    int nr = s - r0 < SR ? s - r0 : SR;
+    T acc[SR];
+#pragma unroll
+    for (int r = 0; r < SR; ++r) acc[r] = 0;
     for (int p = p0; p < p1; ++p) {
       int row = pull_row[p];
-      if (do_local) acc += wl * ybuf[(long long)r * I_total + row];
-      if (do_coarse) {
-        int sb = pull_sub[p];
-        const int* si = sub_info + 8 * sb;
-        int m = si[6], c_off = si[7], a = row - si[3];
-        const T* zr = Z + sub_off[3 * sb + 2] + (long long)a * m;
-        const T* cr = cc + (long long)r * n0 + c_off;
-        for (int q = 0; q < m; ++q) acc += zr[q] * cr[q];
-      }
+#pragma unroll
+      for (int r = 0; r < SR; ++r)
+        if (r < nr) {
+          long long o = (long long)(r0 + r) * I_total + row;
+          if (do_local) acc[r] += wl * ybuf[o];
+          if (do_coarse) acc[r] += zc[o];
+        }
     }
-    z[(long long)r * n + l] = (double)acc;
+#pragma unroll
+    for (int r = 0; r < SR; ++r)
+      if (r < nr && (!active || active[8 * (r0 + r)])) z[(long long)(r0 + r) * n + l] = (double)acc[r];
   }
 }
 
+// Launch shape of k_local_apply<T, NR> for this handle: warps per sweep group, ring depth,
+// threads and dynamic shared memory.  The ring gets as many stages (up to 16) as fit in
+// half an SM's shared memory, so that two CTAs can share an SM, and at least two.
+struct ApplyShape {
+  int WG = 1, K = 0, threads = 0;
+  size_t shm = 0;
+};
+
+// Warps of a sweep group: a level is spread over at least max_level threads, four lanes per
+// row where that fits in eight warps.
+static int apply_wg(const hk_handle* h) {
+  int wg = (4 * h->max_level + 31) / 32;
+  int wmin = (h->max_level + 31) / 32;
+  return std::max(1, std::max(wmin, std::min(wg, 8)));
+}
+
 template <typename T, int NR>
-static hk_status launch_local(hk_handle* h, int s, const double* v, const int* active, const T* Zt, T* ybuf,
-                              T* cvec, int do_local, int do_coarse) {
-  size_t xbytes = sizeof(T) * ((size_t)h->max_dof * NR + (size_t)HK_MAXB * NR);
-  size_t shm = 2 * (size_t)h->pack_stage + xbytes;
+static ApplyShape apply_shape(hk_handle* h, int s) {
+  constexpr int R = NR < 4 ? NR : 4, WS = NR / R;
+  ApplyShape a;
+  a.WG = apply_wg(h);
+  a.threads = 32 * (WS * a.WG + 1);
+  size_t vec = 32 * (size_t)h->max_L + sizeof(T) * (size_t)NR * ((size_t)h->max_dof + 4);
+  size_t stage = (size_t)h->pack_stage;
+  if (!h->n_sm) cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->dev);
+  long long ctas = (long long)h->n_sub * ((s + NR - 1) / NR);
+  // one wave: the whole shared memory for a deep ring; more: half of it, so two CTAs share an SM
+  size_t budget = ctas <= h->n_sm ? 220 * 1024 : 112 * 1024;
+  int K = HK_APPLY_MAXK;
+  while (K > 4 && K * stage + vec > budget) --K;
+  while (K > 2 && K * stage + vec > 220 * 1024) --K;
+  a.K = K;
+  a.shm = K * stage + vec;
+  return a;
+}
+
+template <typename T, int NR>
+static hk_status launch_local(hk_handle* h, int s, const double* v, const int* active, T* ybuf) {
+  ApplyShape a = apply_shape<T, NR>(h, s);
   HK_TRY(hk_allow_smem(k_local_apply<T, NR>));
-  if (shm > 220 * 1024) {
-    hk_set_error("subdomain too large for the shared-memory apply (%d dofs, record %lld bytes)", h->max_dof,
-                 (long long)h->pack_stage);
+  if (a.shm > 220 * 1024 || h->max_level > HK_MAXB || a.threads > 1024) {
+    hk_set_error("subdomain too large for the shared-memory apply (%d dofs, level %d, record %lld bytes)",
+                 h->max_dof, h->max_level, (long long)h->pack_stage);
     return HK_UNSUPPORTED;
   }
   dim3 grid(h->n_sub, (s + NR - 1) / NR);
   HK_TIMED(h, HK_T_LOCAL_APPLY,
-           (k_local_apply<T, NR><<<grid, 256, shm, h->stream>>>(
-               h->n, s, v, active, h->d_sub_info, h->d_sub_off, h->d_I, h->d_lvtab, h->d_pack, Zt, do_local,
-               do_coarse, h->I_total, h->n0, (int)h->pack_stage, ybuf, cvec, h->d_status, h->g_jp,
-               h->g_jstride))); HK_COUNT_LAUNCH();
+           (k_local_apply<T, NR><<<grid, a.threads, a.shm, h->stream>>>(
+               h->n, s, v, active, h->d_sub_info, h->d_sub_off, h->d_I, h->d_lvtab, h->d_pack, h->I_total,
+               (int)h->pack_stage, a.K, a.WG, h->max_L, ybuf, h->d_status, h->g_jp, h->g_jstride))); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   return HK_OK;
 }
@@ -496,41 +785,130 @@ static hk_status launch_local(hk_handle* h, int s, const double* v, const int* a
 template <typename T>
 static hk_status apply_t(hk_handle* h, int s, const double* v, double* z, const int* active, T* ybuf, T* c,
                          T* cc) {
-  const T* Zr = reinterpret_cast<const T*>(h->d_Zr);
   const T* Zt = reinterpret_cast<const T*>(h->d_Zt);
   const T* Einv = sizeof(T) == 4 ? reinterpret_cast<const T*>(h->d_Einv32) : reinterpret_cast<const T*>(h->d_Einv64);
   int do_local = h->p.levels != HK_COARSE_ONLY;
   int do_coarse = h->p.levels != HK_ONE_LEVEL && h->n0 > 0;
   size_t budget = 220 * 1024 - 2 * (size_t)h->pack_stage;
   int nr = 16;
-  while (nr > 1 && (nr > s || sizeof(T) * ((size_t)h->max_dof + HK_MAXB) * nr > budget)) nr >>= 1;
+  budget -= 32 * (size_t)h->max_L;
+  int wg = apply_wg(h);
+  while (nr > 1 && (nr > s || sizeof(T) * ((size_t)h->max_dof + 4) * nr > budget ||
+                    (nr / std::min(nr, 4)) * wg + 1 > 32))
+    nr >>= 1;
   auto tuned = h->nr_tuned.find(s);
   if (tuned != h->nr_tuned.end() && tuned->second <= nr) nr = tuned->second;
-  hk_status rc;
-  switch (nr) {
-    case 16: rc = launch_local<T, 16>(h, s, v, active, Zt, ybuf, c, do_local, do_coarse); break;
-    case 8: rc = launch_local<T, 8>(h, s, v, active, Zt, ybuf, c, do_local, do_coarse); break;
-    case 4: rc = launch_local<T, 4>(h, s, v, active, Zt, ybuf, c, do_local, do_coarse); break;
-    case 2: rc = launch_local<T, 2>(h, s, v, active, Zt, ybuf, c, do_local, do_coarse); break;
-    default: rc = launch_local<T, 1>(h, s, v, active, Zt, ybuf, c, do_local, do_coarse); break;
-  }
-  HK_TRY(rc);
+  // The coarse path (restriction, E^{-1}) and the local sweeps are independent until the
+  // scatter: the coarse path runs on the auxiliary stream, forked from and joined back into
+  // the handle's stream (in a captured solve graph these become parallel branches).
+  int cr = s >= 8 ? 8 : s >= 4 ? 4 : s >= 2 ? 2 : 1;
+  T* zc = ybuf + (size_t)s * h->I_total;  // coarse prolongation per subdomain row
+  bool fork = do_local && do_coarse && h->aux_stream && h->ev_fork && h->ev_join;
+  cudaStream_t main_st = h->stream;
   if (do_coarse) {
-    int rows_per_block = 8;
-    HK_TIMED(h, HK_T_COARSE_SOLVE,
-             (k_coarse_solve<T><<<nblk(h->n0, rows_per_block), 32 * rows_per_block, 0, h->stream>>>(
-                 h->n0, s, Einv, c, cc, active))); HK_COUNT_LAUNCH();
+    if (fork) {
+      HK_CUDA(cudaEventRecord(h->ev_fork, main_st));
+      HK_CUDA(cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0));
+      h->stream = h->aux_stream;
+    }
+    int rb = cr;
+    dim3 rg(h->n_sub, (s + rb - 1) / rb);
+    size_t rshm = sizeof(T) * (size_t)h->max_dof * rb;
+    // coarse solve: right-hand sides per pass as many (up to 8) as fit in shared memory with c
+    int ccr = cr;
+    while (ccr > 1 && sizeof(T) * (size_t)ccr * h->n0 > 200 * 1024) ccr >>= 1;
+    size_t cshm = sizeof(T) * (size_t)ccr * h->n0;
+    if (!h->n_sm) cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->dev);
+    int cgrid = std::max(1, std::min(nblk(h->n0, HK_CS_THREADS / 32), 2 * h->n_sm));
+    bool cs_ok = cshm <= 200 * 1024;
+#define HK_RESTRICT(RBV)                                                                                     \
+  k_restrict<T, RBV><<<rg, 256, rshm, h->stream>>>(h->n, s, v, active, h->d_sub_info, h->d_sub_off, h->d_I, Zt, \
+                                                   h->n0, c, h->g_jp, h->g_jstride)
+#define HK_CSOLVE(CRV) k_coarse_solve<T, CRV><<<cgrid, HK_CS_THREADS, cshm, h->stream>>>(h->n0, s, Einv, c, cc, active)
+#define HK_PROLONG(CRV)                                                                                          \
+  k_prolong<T, CRV><<<rg, 256, 0, h->stream>>>(s, h->d_sub_info, h->d_sub_off, Zt, cc, h->n0, h->I_total, zc, active)
+    if (cs_ok) {
+      HK_TIMED(h, HK_T_COARSE_SOLVE, {
+        switch (rb) {
+          case 8: HK_RESTRICT(8); break;
+          case 4: HK_RESTRICT(4); break;
+          case 2: HK_RESTRICT(2); break;
+          default: HK_RESTRICT(1); break;
+        }
+        switch (ccr) {
+          case 8: HK_CSOLVE(8); break;
+          case 4: HK_CSOLVE(4); break;
+          case 2: HK_CSOLVE(2); break;
+          default: HK_CSOLVE(1); break;
+        }
+        switch (rb) {
+          case 8: HK_PROLONG(8); break;
+          case 4: HK_PROLONG(4); break;
+          case 2: HK_PROLONG(2); break;
+          default: HK_PROLONG(1); break;
+        }
+      });
+    }
+#undef HK_RESTRICT
+#undef HK_CSOLVE
+#undef HK_PROLONG
+    HK_COUNT_LAUNCH();
+    HK_COUNT_LAUNCH();
+    HK_COUNT_LAUNCH();
+    h->stream = main_st;
+    if (fork) HK_CUDA(cudaEventRecord(h->ev_join, h->aux_stream));
+    if (!cs_ok) {
+      hk_set_error("coarse space too large for the coarse solve (n0 = %d)", h->n0);
+      return HK_UNSUPPORTED;
+    }
+    HK_LAUNCH_CHECK();
   }
-  HK_TIMED(h, HK_T_SCATTER,
-           (k_scatter<T><<<nblk(h->n, 128), 128, 0, h->stream>>>(
-               h->n, s, h->d_pull_ptr, h->d_pull_row, h->d_pull_sub, h->d_sub_info, h->d_sub_off, ybuf, Zr, cc,
-               h->I_total, h->n0, do_local, do_coarse, h->p.weighting == HK_RAS_POU, h->d_mu, z, active, h->g_jp,
-               h->g_jstride))); HK_COUNT_LAUNCH();
+  hk_status rc = HK_OK;
+  if (do_local) {
+    switch (nr) {
+      case 16: rc = launch_local<T, 16>(h, s, v, active, ybuf); break;
+      case 8: rc = launch_local<T, 8>(h, s, v, active, ybuf); break;
+      case 4: rc = launch_local<T, 4>(h, s, v, active, ybuf); break;
+      case 2: rc = launch_local<T, 2>(h, s, v, active, ybuf); break;
+      default: rc = launch_local<T, 1>(h, s, v, active, ybuf); break;
+    }
+  }
+  if (fork) HK_CUDA(cudaStreamWaitEvent(main_st, h->ev_join, 0));
+  HK_TRY(rc);
+#define HK_SCATTER_LAUNCH(SRV)                                                                                \
+  HK_TIMED(h, HK_T_SCATTER,                                                                                   \
+           (k_scatter<T, SRV><<<nblk(h->n, 128), 128, 0, h->stream>>>(                                        \
+               h->n, s, h->d_pull_ptr, h->d_pull_row, ybuf, zc, h->I_total, do_local, do_coarse,              \
+               h->p.weighting == HK_RAS_POU, h->d_mu, z, active, h->g_jp, h->g_jstride)))
+  switch (cr) {
+    case 8: HK_SCATTER_LAUNCH(8); break;
+    case 4: HK_SCATTER_LAUNCH(4); break;
+    case 2: HK_SCATTER_LAUNCH(2); break;
+    default: HK_SCATTER_LAUNCH(1); break;
+  }
+#undef HK_SCATTER_LAUNCH
+  HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   return HK_OK;
 }
 
 hk_status apply_prepare(hk_handle*) {
+  HK_TRY(hk_allow_smem(k_coarse_solve<float, 1>));
+  HK_TRY(hk_allow_smem(k_coarse_solve<float, 2>));
+  HK_TRY(hk_allow_smem(k_coarse_solve<float, 4>));
+  HK_TRY(hk_allow_smem(k_coarse_solve<float, 8>));
+  HK_TRY(hk_allow_smem(k_coarse_solve<double, 1>));
+  HK_TRY(hk_allow_smem(k_coarse_solve<double, 2>));
+  HK_TRY(hk_allow_smem(k_coarse_solve<double, 4>));
+  HK_TRY(hk_allow_smem(k_coarse_solve<double, 8>));
+  HK_TRY(hk_allow_smem(k_restrict<float, 1>));
+  HK_TRY(hk_allow_smem(k_restrict<float, 2>));
+  HK_TRY(hk_allow_smem(k_restrict<float, 4>));
+  HK_TRY(hk_allow_smem(k_restrict<float, 8>));
+  HK_TRY(hk_allow_smem(k_restrict<double, 1>));
+  HK_TRY(hk_allow_smem(k_restrict<double, 2>));
+  HK_TRY(hk_allow_smem(k_restrict<double, 4>));
+  HK_TRY(hk_allow_smem(k_restrict<double, 8>));
   HK_TRY(hk_allow_smem(k_local_apply<float, 1>));
   HK_TRY(hk_allow_smem(k_local_apply<float, 2>));
   HK_TRY(hk_allow_smem(k_local_apply<float, 4>));
@@ -633,8 +1011,10 @@ hk_status phase_local_factors_begin(hk_handle* h) {
   HK_CUDA(cudaMemcpyAsync(lev.data(), h->d_lev, sizeof(int) * lev.size(), cudaMemcpyDeviceToHost, st));
   HK_CUDA(cudaStreamSynchronize(st));
   long long fo = 0;
+  h->max_L = 0;
   for (int s = 0; s < ns; ++s) {
     Sub& u = h->subs[s];
+    h->max_L = std::max(h->max_L, u.L);
     u.f_off = fo;
     fo += factor_elems(&lev[u.lev_off], u.L);
   }
@@ -669,15 +1049,20 @@ hk_status phase_local_factors_begin(hk_handle* h) {
     const int* lp = &lev[u.lev_off];
     for (int j = 0; j < u.L; ++j) {
       long long b = lp[j + 1] - lp[j], bn = j + 1 < u.L ? lp[j + 2] - lp[j + 1] : 0, c = nc[u.lev_off + j];
-      long long fb = pad16(b * b * esz + c * esz + c * 2 + (b + 1) * 2), bb = pad16(b * bn * esz);
+      long long bp = j > 0 ? lp[j] - lp[j - 1] : 0;
+      long long rowf = pad4(bp + b) * esz, rowb = pad4(bn) * esz;  // multiples of 16 bytes
+      long long fb = b * rowf, bb = b * rowb;
+      long long rcf = std::max(1LL, std::min(b, HK_CHUNK_BYTES / rowf));
+      long long rcb = bn > 0 ? std::max(1LL, std::min(b, HK_CHUNK_BYTES / rowb)) : 1;
+      (void)c;
       long long* e = &tab[4 * (size_t)(u.lev_off + j)];
       e[0] = cur;
       cur += fb;
       e[1] = cur;
       cur += bb;
       e[2] = fb | (bb << 32);
-      e[3] = c | (b << 20) | ((long long)lp[j] << 40);
-      stage = std::max(stage, std::max(fb, bb));
+      e[3] = rcf | (rcb << 10) | (b << 20) | ((long long)lp[j] << 40);
+      stage = std::max(stage, std::max(rcf * rowf, rcb * rowb));
     }
   }
   h->pack_bytes = cur;
@@ -693,6 +1078,8 @@ hk_status phase_local_factors_begin(hk_handle* h) {
   // the auxiliary stream starts after everything above (allocations, memsets, table upload)
   if (!h->aux_stream) HK_CUDA(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
   if (!h->ev_lf) HK_CUDA(cudaEventCreateWithFlags(&h->ev_lf, cudaEventDisableTiming));
+  if (!h->ev_fork) HK_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  if (!h->ev_join) HK_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   HK_CUDA(cudaEventRecord(h->ev_lf, st));
   HK_CUDA(cudaStreamWaitEvent(h->aux_stream, h->ev_lf, 0));
   cudaStream_t ax = h->aux_stream;
@@ -727,10 +1114,11 @@ hk_status phase_local_factors_end(hk_handle* h) {
 // preconditioner: code running while a stream is being captured into a CUDA
 // graph (cudaMalloc is not allowed there), or a host framework that owns all
 // device memory through its own allocator and forbids allocations on its hot
-// path.  hk_apply_precond_noalloc serves them: it runs the same three kernels
-// as hk_apply_precond on caller-provided device vectors, and keeps its
-// intermediate vectors (local solutions, coarse right-hand side and coarse
-// solution) in the fixed device array below instead of allocating.
+// path.  hk_apply_precond_noalloc serves them: it runs the same kernels as
+// hk_apply_precond on caller-provided device vectors, and keeps its
+// intermediate vectors (local solutions, coarse prolongation, coarse
+// right-hand side and coarse solution) in the fixed device array below
+// instead of allocating.
 //
 // The array is HK_NOALLOC_SCRATCH_BYTES per device and stays allocated on
 // every device that loads the library until the process exits.  Its device
@@ -778,7 +1166,7 @@ extern "C" hk_status hk_apply_precond_noalloc(hk_handle* h, int n_rhs, const dou
     return HK_BAD_ARG;
   }
   size_t esz = h->p.precision == HK_FP32_PRECOND ? sizeof(float) : sizeof(double);
-  size_t ylen = align256(esz * (size_t)n_rhs * (size_t)h->I_total);
+  size_t ylen = align256(esz * 2 * (size_t)n_rhs * (size_t)h->I_total);
   size_t clen = align256(esz * (size_t)n_rhs * (size_t)(h->n0 + 1));
   size_t need = ylen + 2 * clen;
   if (need > HK_NOALLOC_SCRATCH_BYTES) {
