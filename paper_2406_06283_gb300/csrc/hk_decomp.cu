@@ -455,7 +455,7 @@ hk_status phase_decomposition(hk_handle* h, const int32_t* elem_to_sub, uint8_t*
   HK_TRY(dalloc(h, &h->d_sub_off, 3 * ns));
   HK_TRY(upload_sub_info(h));
   HK_TRY(dalloc(h, &h->d_Isorted, Ioff));
-  HK_TRY(dalloc(h, &h->d_I, Ioff));
+  HK_TRY(dalloc(h, &h->d_I, Ioff + 4));  // + 4: the apply copies 16-byte aligned spans of it
   HK_TRY(dalloc(h, &h->d_perm, Ioff));
   HK_TRY(dalloc(h, &h->d_G, Goff));
   HK_TRY(dalloc(h, &h->d_lev, Ioff + ns));

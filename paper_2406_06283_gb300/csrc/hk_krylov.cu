@@ -60,62 +60,63 @@ hk_status op_matvec(hk_handle* h, int s, const double* x, double* y, const int* 
 // Gram-Schmidt pass.  MODE 0: w = B z_j on the CTA's rows (the matvec, fused), then
 // h1 = V^T w.  MODE 1: w -= V h1, then h2 = V^T w.
 // MODE 2: w -= V h2, ||w||^2, then (last CTA) the Hessenberg column, Givens
-// rotation, residual estimate and stopping decision of every active rhs.
+// rotation, residual estimate and stopping decision.
+// Grid (RED_BLOCKS, s): blockIdx.y is the right-hand side, so the right-hand sides of a
+// batch run side by side; each has its own completion counter, and the last CTA of a
+// right-hand side adds its partials in CTA order.  The partition into row chunks does not
+// depend on the batch size, so a right-hand side gives the same bits alone and in a batch.
 template <int MODE>
 __global__ void k_gs(int n, int s, int m, int j, const int* __restrict__ jp, const double* __restrict__ V,
                      double* w, int* state, double* rstate, double* hcoef, double* part, unsigned* counter,
                      double* H, double* cs, double* sn, double* g, double* hist, int max_iters, double tol,
                      const int* __restrict__ rowptr, const int* __restrict__ col, const double* __restrict__ val,
                      const double* __restrict__ Zk) {
+  int r = blockIdx.y;
+  if (!state[8 * r + ST_ACTIVE]) return;  // uniform over the CTAs of this right-hand side
   if (jp) j = *jp;  // captured inner step: j read on the device
   const double* zj = Zk + (long long)j * s * n;
   int chunk = (n + gridDim.x - 1) / gridDim.x;
   int l0 = blockIdx.x * chunk, l1 = min(n, l0 + chunk);
   int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  int nc = MODE == 2 ? 1 : j + 1;  // values per rhs
+  int nc = MODE == 2 ? 1 : j + 1;  // values
   __shared__ double red[32];
-  for (int r = 0; r < s; ++r) {
-    if (!state[8 * r + ST_ACTIVE]) continue;
-    double* wr = w + (long long)r * n;
-    if (MODE == 0) {
-      const double* zr = zj + (long long)r * n;
-      for (int l = l0 + tid; l < l1; l += blockDim.x) {
-        double acc = 0;
-        for (int q = rowptr[l]; q < rowptr[l + 1]; ++q) acc += val[q] * zr[col[q]];
-        wr[l] = acc;
-      }
-      __syncthreads();
-    }
-    if (MODE >= 1) {
-      const double* hc = hcoef + (long long)r * 2 * (m + 1) + (MODE == 1 ? 0 : m + 1);
-      for (int l = l0 + tid; l < l1; l += blockDim.x) {
-        double acc = wr[l];
-        for (int i = 0; i <= j; ++i) acc -= hc[i] * V[((long long)i * s + r) * n + l];
-        wr[l] = acc;
-      }
-      __syncthreads();
-    }
-    double* pr = part + ((long long)blockIdx.x * s + r) * (m + 2);
-    if (MODE <= 1) {
-      for (int i = warp; i <= j; i += nw) {
-        const double* vi = V + ((long long)i * s + r) * n;
-        double acc = 0;
-        for (int l = l0 + lane; l < l1; l += 32) acc += wr[l] * vi[l];
-        acc = warp_sum(acc);
-        if (lane == 0) pr[i] = acc;
-      }
-    } else {
+  double* wr = w + (long long)r * n;
+  if (MODE == 0) {
+    const double* zr = zj + (long long)r * n;
+    for (int l = l0 + tid; l < l1; l += blockDim.x) {
       double acc = 0;
-      for (int l = l0 + tid; l < l1; l += blockDim.x) acc += wr[l] * wr[l];
-      acc = block_sum(acc, red);
-      if (tid == 0) pr[0] = acc;
+      for (int q = rowptr[l]; q < rowptr[l + 1]; ++q) acc += val[q] * zr[col[q]];
+      wr[l] = acc;
     }
+    __syncthreads();
   }
-  if (!last_block(counter)) return;
+  if (MODE >= 1) {
+    const double* hc = hcoef + (long long)r * 2 * (m + 1) + (MODE == 1 ? 0 : m + 1);
+    for (int l = l0 + tid; l < l1; l += blockDim.x) {
+      double acc = wr[l];
+      for (int i = 0; i <= j; ++i) acc -= hc[i] * V[((long long)i * s + r) * n + l];
+      wr[l] = acc;
+    }
+    __syncthreads();
+  }
+  double* pr = part + ((long long)blockIdx.x * s + r) * (m + 2);
+  if (MODE <= 1) {
+    for (int i = warp; i <= j; i += nw) {
+      const double* vi = V + ((long long)i * s + r) * n;
+      double acc = 0;
+      for (int l = l0 + lane; l < l1; l += 32) acc += wr[l] * vi[l];
+      acc = warp_sum(acc);
+      if (lane == 0) pr[i] = acc;
+    }
+  } else {
+    double acc = 0;
+    for (int l = l0 + tid; l < l1; l += blockDim.x) acc += wr[l] * wr[l];
+    acc = block_sum(acc, red);
+    if (tid == 0) pr[0] = acc;
+  }
+  if (!last_block(counter + 8 + r)) return;
   // final reduction: one warp per value, lanes over CTAs in a fixed order
-  for (int e = warp; e < s * nc; e += nw) {
-    int r = e / nc, i = e % nc;
-    if (!state[8 * r + ST_ACTIVE]) continue;
+  for (int i = warp; i < nc; i += nw) {
     double acc = 0;
     for (int b = lane; b < gridDim.x; b += 32) acc += part[((long long)b * s + r) * (m + 2) + i];
     acc = warp_sum(acc);
@@ -131,8 +132,7 @@ __global__ void k_gs(int n, int s, int m, int j, const int* __restrict__ jp, con
   }
   if (MODE == 2) {
     __syncthreads();
-    for (int r = tid; r < s; r += blockDim.x) {
-      if (!state[8 * r + ST_ACTIVE]) continue;
+    if (tid == 0) {
       double* Hr = H + (long long)r * (m + 1) * m;  // H[i][jj] at i * m + jj
       const double* h1 = hcoef + (long long)r * 2 * (m + 1);
       const double* h2 = h1 + (m + 1);
@@ -166,7 +166,7 @@ __global__ void k_gs(int n, int s, int m, int j, const int* __restrict__ jp, con
     }
   }
   __syncthreads();
-  if (tid == 0) *counter = 0u;
+  if (tid == 0) counter[8 + r] = 0u;
 }
 
 __global__ void k_normalize(int n, int s, int j, const int* __restrict__ jp, double* V,
@@ -365,7 +365,7 @@ hk_status ensure_workspace(hk_handle* h, int s) {
     h->d_ybuf32 = nullptr; h->d_c32 = nullptr; h->d_cc32 = nullptr;
   }
   HK_TRY(dalloc(h, &h->d_part, (size_t)RED_BLOCKS * s * (m + 2)));
-  HK_TRY(dalloc(h, &h->d_counter, 8));
+  HK_TRY(dalloc(h, &h->d_counter, 8 + (size_t)s));  // [0]: norms; [8 + r]: Gram-Schmidt of rhs r
   HK_TRY(dalloc(h, &h->d_H, (size_t)s * (m + 1) * m));
   HK_TRY(dalloc(h, &h->d_cs, (size_t)s * m));
   HK_TRY(dalloc(h, &h->d_sn, (size_t)s * m));
@@ -393,7 +393,7 @@ static hk_status fgmres_init(hk_handle* h, int s, const double* rhs_dev) {
   HK_CUDA(cudaMemsetAsync(h->d_x, 0, sizeof(double) * sn_, st));
   HK_CUDA(cudaMemsetAsync(h->d_hist, 0, sizeof(double) * (size_t)s * mi, st));
   HK_CUDA(cudaMemsetAsync(h->d_state, 0, sizeof(int) * s * 8, st));
-  HK_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned) * 8, st));
+  HK_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned) * (8 + (size_t)s), st));
   HK_CUDA(cudaMemsetAsync(h->d_ctl, 0, sizeof(int) * 4, st));
   // ||f|| into RS_BETA, then initialise the per-rhs state from it
   k_norm2<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, h->d_f, h->d_state, h->d_rstate, RS_BETA, h->d_part,
@@ -431,13 +431,13 @@ static hk_status fgmres_step(hk_handle* h, int s, double tol, int j, const int* 
     ga = hk_event(h);
     cudaEventRecord(ga, st);
   }
-  k_gs<0><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, m, j, jp, h->d_V, h->d_w, h->d_state, h->d_rstate, h->d_hcol,
+  k_gs<0><<<dim3(RED_BLOCKS, s), RED_THREADS, 0, st>>>(n, s, m, j, jp, h->d_V, h->d_w, h->d_state, h->d_rstate, h->d_hcol,
                                               h->d_part, h->d_counter, h->d_H, h->d_cs, h->d_sn, h->d_g, h->d_hist,
                                               mi, tol, h->d_rowptr, h->d_col, h->d_valB, h->d_Zk); HK_COUNT_LAUNCH();
-  k_gs<1><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, m, j, jp, h->d_V, h->d_w, h->d_state, h->d_rstate, h->d_hcol,
+  k_gs<1><<<dim3(RED_BLOCKS, s), RED_THREADS, 0, st>>>(n, s, m, j, jp, h->d_V, h->d_w, h->d_state, h->d_rstate, h->d_hcol,
                                               h->d_part, h->d_counter, h->d_H, h->d_cs, h->d_sn, h->d_g, h->d_hist,
                                               mi, tol, h->d_rowptr, h->d_col, h->d_valB, h->d_Zk); HK_COUNT_LAUNCH();
-  k_gs<2><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, s, m, j, jp, h->d_V, h->d_w, h->d_state, h->d_rstate, h->d_hcol,
+  k_gs<2><<<dim3(RED_BLOCKS, s), RED_THREADS, 0, st>>>(n, s, m, j, jp, h->d_V, h->d_w, h->d_state, h->d_rstate, h->d_hcol,
                                               h->d_part, h->d_counter, h->d_H, h->d_cs, h->d_sn, h->d_g, h->d_hist,
                                               mi, tol, h->d_rowptr, h->d_col, h->d_valB, h->d_Zk); HK_COUNT_LAUNCH();
   k_normalize<<<nblk(n, 256), 256, 0, st>>>(n, s, j, jp, h->d_V, h->d_w, h->d_state, h->d_rstate); HK_COUNT_LAUNCH();

@@ -283,6 +283,7 @@ __global__ void k_pack_levels(const int* __restrict__ sub_info, const long long*
 // Every wait is bounded; a wait that gives up reports HK_TIMEOUT, and the producer lets
 // the copies it has in flight land before the CTA exits.
 #define HK_APPLY_MAXK 24
+#define HK_APPLY_MAXT 768  // threads of a CTA at most (24 warps)
 
 // R-vector loads and stores of shared-memory rows, as 16- or 8-byte accesses where the
 // row size allows (rows are aligned to their size).
@@ -385,16 +386,16 @@ __device__ __forceinline__ void row_chunk_dot(const T* __restrict__ row, const T
 }
 
 template <typename T, int NR>
-__global__ void __launch_bounds__(1024, 1) k_local_apply(
+__global__ void __launch_bounds__(HK_APPLY_MAXT, 1) k_local_apply(
     int n, int s_tot, const double* __restrict__ v, const int* __restrict__ active,
     const int* __restrict__ sub_info, const long long* __restrict__ sub_off, const int* __restrict__ Ilev,
     const long long* __restrict__ lvtab, const unsigned char* __restrict__ pack, long long I_total,
-    int stage_bytes, int K, int WG, int max_L, T* ybuf, DevStatus* st, const int* __restrict__ jp,
+    int stage_bytes, int K, int WG, int max_L, int max_dof, T* ybuf, DevStatus* st, const int* __restrict__ jp,
     long long jstride) {
   constexpr int R = NR < 4 ? NR : 4;
   constexpr int WS = NR / R;  // sweep groups
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full[HK_APPLY_MAXK], empty[HK_APPLY_MAXK];
+  __shared__ __align__(8) uint64_t full[HK_APPLY_MAXK], empty[HK_APPLY_MAXK], meta;
   __shared__ int sh_fail;
   if (jp) v += (long long)(*jp) * jstride;  // captured inner step: v = v_j with j read on the device
   int s = blockIdx.x, r_base = blockIdx.y * NR;
@@ -405,9 +406,14 @@ __global__ void __launch_bounds__(1024, 1) k_local_apply(
   const int* si = sub_info + 8 * s;
   int nI = si[0], L = si[2], off = si[3], loff = si[5];
   int xs = nI + 4;  // rows per group slice of x
-  // shared memory: record ring | level table (4 x int64 per level) | x
+  // shared memory: record ring | level table (4 x int64 per level) | step parameters (int4 per
+  // level step) | dof indices (16-byte aligned span around dof(Omega_i)) | x
   long long* tab = reinterpret_cast<long long*>(smem_raw + (long long)K * stage_bytes);
-  T* x = reinterpret_cast<T*>(tab + 4 * (long long)max_L);  // WS groups x (nI + 4) x R
+  int4* lvp = reinterpret_cast<int4*>(tab + 4 * (long long)max_L);
+  int* idx = reinterpret_cast<int*>(lvp + 2 * (long long)max_L);
+  int ioff = off & 3;  // position of the first index in the aligned span
+  int ispan = (ioff + nI + 3) & ~3;
+  T* x = reinterpret_cast<T*>(idx + ((max_dof + 7) & ~3));  // WS groups x (nI + 4) x R
   int nr = s_tot - r_base < NR ? s_tot - r_base : NR;
   int nlev = 2 * L - 1;  // level steps: forward 0 .. L-1, backward L-2 .. 0
   // the producer's position in the chunk stream: level step ps_rs, chunk ps_c
@@ -427,18 +433,24 @@ __global__ void __launch_bounds__(1024, 1) k_local_apply(
     else ++ps_c;
     return true;
   };
-  for (int e = tid; e < 4 * L; e += blockDim.x) tab[e] = lvtab[4 * (long long)loff + e];
   if (tid == 0) {
     sh_fail = 0;
     for (int k = 0; k < K; ++k) {
       mbar_init(&full[k], 1);
       mbar_init(&empty[k], WS * WG);
     }
+    mbar_init(&meta, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // the level table and the dof indices by two bulk copies
+    mbar_expect_tx(&meta, 32u * L + 4u * ispan);
+    tma_load_1d(tab, lvtab + 4 * (long long)loff, 32u * L, &meta);
+    tma_load_1d(idx, Ilev + (off - ioff), 4u * ispan, &meta);
   }
   __syncthreads();
+  bool meta_ok = mbar_wait_or_fail(&meta, 0u, &sh_fail);
+  if (!meta_ok && tid == 0 && atomicExch(&sh_fail, 1) == 0) dev_fail(st, HK_TIMEOUT, s, -1);
   int issued = 0;
-  if (producer && lane == 0) {
+  if (producer && lane == 0 && meta_ok) {
     const unsigned char* src;
     unsigned bytes;
     for (; issued < K && next_chunk(src, bytes); ++issued) {
@@ -446,25 +458,39 @@ __global__ void __launch_bounds__(1024, 1) k_local_apply(
       tma_load_1d(smem_raw + (long long)issued * stage_bytes, src, bytes, &full[issued]);
     }
   }
-  if (!producer) {
-    // gather, four elements per thread in flight (index loads, then value loads)
+  int nthr = 32 * WG;
+  if (!producer && meta_ok) {
+    // gather, eight values per thread in flight
     int tot = nI * NR;
-    for (int e0 = tid; e0 < tot; e0 += 4 * nct) {
-      int idx[4];
+    for (int e0 = tid; e0 < tot; e0 += 8 * nct) {
+      T val[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         int e = e0 + u * nct;
-        idx[u] = e < tot ? Ilev[off + e % nI] : 0;
+        int rr = e / nI, a = e - rr * nI;
+        bool on = e < tot && rr < nr && (active == nullptr || active[8 * (r_base + rr)]);
+        val[u] = on ? (T)v[(long long)(r_base + rr) * n + idx[ioff + a]] : (T)0;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         int e = e0 + u * nct;
         if (e < tot) {
-          int rr = e / nI, a = e % nI;
-          bool on = rr < nr && (active == nullptr || active[8 * (r_base + rr)]);
-          x[((long long)(rr / R) * xs + a) * R + rr % R] = on ? (T)v[(long long)(r_base + rr) * n + idx[u]] : (T)0;
+          int rr = e / nI, a = e - rr * nI;
+          x[((long long)(rr / R) * xs + a) * R + rr % R] = val[u];
         }
       }
+    }
+    // per level step: b | lg << 16, ld | bo << 16, level start, rows per chunk
+    for (int rs = tid; rs < nlev; rs += nct) {
+      bool fwd = rs < L;
+      int j = fwd ? rs : 2 * L - 2 - rs;
+      long long e3 = tab[4 * j + 3];
+      int b = lv_b(e3), ls = lv_start(e3), rc = fwd ? lv_rcf(e3) : lv_rcb(e3);
+      int bo = fwd ? (j > 0 ? ls - lv_start(tab[4 * (j - 1) + 3]) : 0) : lv_b(tab[4 * (j + 1) + 3]);
+      int ld = fwd ? (int)pad4(bo + b) : (int)pad4(bo);
+      int lg = 0;  // G = 2^lg lanes per row, as many as keep b * G <= nthr (one pass)
+      while (lg < 5 && (b << (lg + 1)) <= nthr) ++lg;
+      lvp[rs] = make_int4(b | (lg << 16), ld | (bo << 16), ls, rc);
     }
     for (int e = tid; e < WS * 4 * R; e += nct) {  // the zero rows after each group's slice
       int g = e / (4 * R), q = e % (4 * R);
@@ -473,7 +499,7 @@ __global__ void __launch_bounds__(1024, 1) k_local_apply(
   }
   __syncthreads();
   if (producer) {
-    if (lane != 0) return;
+    if (lane != 0 || !meta_ok) return;
     const unsigned char* src;
     unsigned bytes;
     bool failed = false;
@@ -494,22 +520,18 @@ __global__ void __launch_bounds__(1024, 1) k_local_apply(
     }
     return;
   }
+  if (!meta_ok) return;
   int g = warp / WG, wr = warp % WG;
-  int bar_id = 1 + g, nthr = 32 * WG, gt = wr * 32 + lane;
+  int bar_id = 1 + g, gt = wr * 32 + lane;
   T* xg = x + (long long)g * xs * R;
   int ks = 0;            // stage of the next chunk
   unsigned kph = 0;       // its phase parity
   for (int rs = 0; rs < nlev; ++rs) {
     bool fwd = rs < L;
-    int j = fwd ? rs : 2 * L - 2 - rs;
-    long long e3 = tab[4 * j + 3];
-    int b = lv_b(e3), ls = lv_start(e3), rc = fwd ? lv_rcf(e3) : lv_rcb(e3);
+    int4 pv = lvp[rs];
+    int b = pv.x & 0xFFFF, lg = pv.x >> 16, ld = pv.y & 0xFFFF, bo = pv.y >> 16, ls = pv.z, rc = pv.w;
     // forward: input rows [ls - bo, ls + b) = [y_{j-1}; r_j]; backward: x_{j+1} at [ls + b, ls + b + bo)
-    int bo = fwd ? (j > 0 ? ls - lv_start(tab[4 * (j - 1) + 3]) : 0) : lv_b(tab[4 * (j + 1) + 3]);
-    int ld = fwd ? (int)pad4(bo + b) : (int)pad4(bo);
     const T* xin = xg + (long long)(fwd ? ls - bo : ls + b) * R;
-    int lg = 0;  // G = 2^lg lanes per row, as many as keep b * G <= nthr (one pass)
-    while (lg < 5 && (b << (lg + 1)) <= nthr) ++lg;
     int G = 1 << lg;
     int q = gt >> lg, gl = gt & (G - 1);
     int nv = ld >> 2, cv = (nv + G - 1) >> lg;
@@ -579,23 +601,18 @@ __global__ void __launch_bounds__(256) k_restrict(int n, int s_tot, const double
   int nI = si[0], off = si[3], m = si[6], c_off = si[7];
   long long zoff = sub_off[3 * sb + 2];
   int nr = s_tot - r_base < RB ? s_tot - r_base : RB;
-  int tot = nI * RB;
-  for (int e0 = tid; e0 < tot; e0 += 4 * blockDim.x) {
-    int idx[4];
+  bool on[RB];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      int e = e0 + u * blockDim.x;
-      idx[u] = e < tot ? Ilev[off + e % nI] : 0;
-    }
+  for (int rr = 0; rr < RB; ++rr) on[rr] = rr < nr && (active == nullptr || active[8 * (r_base + rr)]);
+  // gather: per dof its index, then the RB values, all in flight
+#pragma unroll 4
+  for (int a = tid; a < nI; a += blockDim.x) {
+    int gi = Ilev[off + a];
+    T val[RB];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      int e = e0 + u * blockDim.x;
-      if (e < tot) {
-        int rr = e / nI, a = e % nI;
-        bool on = rr < nr && (active == nullptr || active[8 * (r_base + rr)]);
-        r[a * RB + rr] = on ? (T)v[(long long)(r_base + rr) * n + idx[u]] : (T)0;
-      }
-    }
+    for (int rr = 0; rr < RB; ++rr) val[rr] = on[rr] ? (T)v[(long long)(r_base + rr) * n + gi] : (T)0;
+#pragma unroll
+    for (int rr = 0; rr < RB; ++rr) r[a * RB + rr] = val[rr];
   }
   __syncthreads();
   for (int l = warp; l < m; l += nw) {
@@ -620,41 +637,73 @@ __global__ void __launch_bounds__(256) k_restrict(int n, int s_tot, const double
 }
 
 // cc_r = E^{-1} c_r for s right-hand sides (E^{-1} dense n0 x n0 row-major), CR right-hand
-// sides per pass: c of the pass is copied once into shared memory (CR x n0), then a warp per
-// row of E^{-1} (rows strided over the grid) streams the row with eight loads in flight per
-// lane.  Each lane sums its columns lane, lane + 32, ... in order, then a fixed shuffle tree.
-#define HK_CS_THREADS 512
+// sides per pass.  A warp takes two rows of E^{-1} and streams them once per pass, sixteen
+// loads in flight per lane; c is staged through shared memory in tiles of tc columns, stored
+// column-major with a row pitch that makes the 16-byte reads of consecutive lanes hit
+// distinct banks.  Each lane sums its columns lane, lane + 32, ... in order, then a fixed
+// shuffle tree, so every run gives the same bits.
+#define HK_CS_THREADS 256
+#define HK_CS_RPW 2
+template <typename T, int CR>
+__host__ __device__ constexpr int cs_pitch() {
+  constexpr int VW = 16 / (int)sizeof(T);  // elements per 16 bytes
+  return CR <= VW ? CR : ((CR / VW) % 2 == 1 ? CR : CR + VW);
+}
+
 template <typename T, int CR>
 __global__ void __launch_bounds__(HK_CS_THREADS) k_coarse_solve(int n0, int s, const T* __restrict__ Einv,
                                                                 const T* __restrict__ c, T* cc,
-                                                                const int* __restrict__ active) {
+                                                                const int* __restrict__ active, int tc) {
+  constexpr int CS = cs_pitch<T, CR>();
+  constexpr int RV = CR >= 4 ? 4 : CR;  // right-hand sides per shared-memory read
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* cs = reinterpret_cast<T*>(smem_raw);  // CR x n0
+  T* cs = reinterpret_cast<T*>(smem_raw);  // tc x CS
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int row0 = (blockIdx.x * nw + warp) * HK_CS_RPW;
+  const T* e0p = Einv + (long long)min(row0, n0 - 1) * n0;
+  const T* e1p = Einv + (long long)min(row0 + 1, n0 - 1) * n0;
   for (int r0 = 0; r0 < s; r0 += CR) {
     int nr = s - r0 < CR ? s - r0 : CR;
-    __syncthreads();
-    for (int e = threadIdx.x; e < CR * n0; e += blockDim.x) {
-      int r = e / n0, t = e % n0;
-      cs[e] = r < nr ? c[(long long)(r0 + r) * n0 + t] : (T)0;
-    }
-    __syncthreads();
-    for (int row = blockIdx.x * nw + warp; row < n0; row += gridDim.x * nw) {
-      const T* er = Einv + (long long)row * n0;
-      T acc[CR];
+    T acc0[CR], acc1[CR];
 #pragma unroll
-      for (int r = 0; r < CR; ++r) acc[r] = 0;
-#pragma unroll 8
-      for (int t = lane; t < n0; t += 32) {
-        T ev = er[t];
+    for (int r = 0; r < CR; ++r) acc0[r] = acc1[r] = 0;
+    for (int t0 = 0; t0 < n0; t0 += tc) {
+      int tn = n0 - t0 < tc ? n0 - t0 : tc;
+      __syncthreads();
+#pragma unroll 2
+      for (int t = threadIdx.x; t < tn; t += blockDim.x) {
+        T val[CR];
 #pragma unroll
-        for (int r = 0; r < CR; ++r) acc[r] += ev * cs[r * n0 + t];
+        for (int r = 0; r < CR; ++r) val[r] = r < nr ? c[(long long)(r0 + r) * n0 + t0 + t] : (T)0;
+#pragma unroll
+        for (int r = 0; r < CR; ++r) cs[t * CS + r] = val[r];
       }
+      __syncthreads();
+#pragma unroll 8
+      for (int t = lane; t < tn; t += 32) {
+        T ea = e0p[t0 + t], eb = e1p[t0 + t];
 #pragma unroll
-      for (int r = 0; r < CR; ++r) {
-        T a = acc[r];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0 && r < nr && (!active || active[8 * (r0 + r)])) cc[(long long)(r0 + r) * n0 + row] = a;
+        for (int r4 = 0; r4 < CR; r4 += RV) {
+          T w[RV];
+          ldv<T, RV>(w, cs + t * CS + r4);
+#pragma unroll
+          for (int i = 0; i < RV; ++i) {
+            acc0[r4 + i] += ea * w[i];
+            acc1[r4 + i] += eb * w[i];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < CR; ++r) {
+      T a = acc0[r], b = acc1[r];
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+      }
+      if (lane == 0 && r < nr && (!active || active[8 * (r0 + r)])) {
+        if (row0 < n0) cc[(long long)(r0 + r) * n0 + row0] = a;
+        if (row0 + 1 < n0) cc[(long long)(r0 + r) * n0 + row0 + 1] = b;
       }
     }
   }
@@ -750,7 +799,8 @@ static ApplyShape apply_shape(hk_handle* h, int s) {
   ApplyShape a;
   a.WG = apply_wg(h);
   a.threads = 32 * (WS * a.WG + 1);
-  size_t vec = 32 * (size_t)h->max_L + sizeof(T) * (size_t)NR * ((size_t)h->max_dof + 4);
+  size_t vec = 64 * (size_t)h->max_L + 4 * (size_t)((h->max_dof + 7) & ~3) +
+               sizeof(T) * (size_t)NR * ((size_t)h->max_dof + 4);
   size_t stage = (size_t)h->pack_stage;
   if (!h->n_sm) cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->dev);
   long long ctas = (long long)h->n_sub * ((s + NR - 1) / NR);
@@ -768,7 +818,7 @@ template <typename T, int NR>
 static hk_status launch_local(hk_handle* h, int s, const double* v, const int* active, T* ybuf) {
   ApplyShape a = apply_shape<T, NR>(h, s);
   HK_TRY(hk_allow_smem(k_local_apply<T, NR>));
-  if (a.shm > 220 * 1024 || h->max_level > HK_MAXB || a.threads > 1024) {
+  if (a.shm > 220 * 1024 || h->max_level > HK_MAXB || a.threads > HK_APPLY_MAXT) {
     hk_set_error("subdomain too large for the shared-memory apply (%d dofs, level %d, record %lld bytes)",
                  h->max_dof, h->max_level, (long long)h->pack_stage);
     return HK_UNSUPPORTED;
@@ -777,7 +827,7 @@ static hk_status launch_local(hk_handle* h, int s, const double* v, const int* a
   HK_TIMED(h, HK_T_LOCAL_APPLY,
            (k_local_apply<T, NR><<<grid, a.threads, a.shm, h->stream>>>(
                h->n, s, v, active, h->d_sub_info, h->d_sub_off, h->d_I, h->d_lvtab, h->d_pack, h->I_total,
-               (int)h->pack_stage, a.K, a.WG, h->max_L, ybuf, h->d_status, h->g_jp, h->g_jstride))); HK_COUNT_LAUNCH();
+               (int)h->pack_stage, a.K, a.WG, h->max_L, h->max_dof, ybuf, h->d_status, h->g_jp, h->g_jstride))); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   return HK_OK;
 }
@@ -791,10 +841,10 @@ static hk_status apply_t(hk_handle* h, int s, const double* v, double* z, const 
   int do_coarse = h->p.levels != HK_ONE_LEVEL && h->n0 > 0;
   size_t budget = 220 * 1024 - 2 * (size_t)h->pack_stage;
   int nr = 16;
-  budget -= 32 * (size_t)h->max_L;
+  budget -= 64 * (size_t)h->max_L + 4 * (size_t)((h->max_dof + 7) & ~3);
   int wg = apply_wg(h);
   while (nr > 1 && (nr > s || sizeof(T) * ((size_t)h->max_dof + 4) * nr > budget ||
-                    (nr / std::min(nr, 4)) * wg + 1 > 32))
+                    32 * ((nr / std::min(nr, 4)) * wg + 1) > HK_APPLY_MAXT))
     nr >>= 1;
   auto tuned = h->nr_tuned.find(s);
   if (tuned != h->nr_tuned.end() && tuned->second <= nr) nr = tuned->second;
@@ -814,17 +864,19 @@ static hk_status apply_t(hk_handle* h, int s, const double* v, double* z, const 
     int rb = cr;
     dim3 rg(h->n_sub, (s + rb - 1) / rb);
     size_t rshm = sizeof(T) * (size_t)h->max_dof * rb;
-    // coarse solve: right-hand sides per pass as many (up to 8) as fit in shared memory with c
-    int ccr = cr;
-    while (ccr > 1 && sizeof(T) * (size_t)ccr * h->n0 > 200 * 1024) ccr >>= 1;
-    size_t cshm = sizeof(T) * (size_t)ccr * h->n0;
-    if (!h->n_sm) cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->dev);
-    int cgrid = std::max(1, std::min(nblk(h->n0, HK_CS_THREADS / 32), 2 * h->n_sm));
+    // coarse solve: up to 16 right-hand sides per pass, c staged in column tiles
+    int ccr = s >= 16 ? 16 : s >= 8 ? 8 : cr;
+    int pitch = sizeof(T) == 4 ? (ccr == 16 ? cs_pitch<float, 16>() : ccr == 8 ? cs_pitch<float, 8>() : ccr == 4 ? cs_pitch<float, 4>() : ccr)
+                               : (ccr == 16 ? cs_pitch<double, 16>() : ccr == 8 ? cs_pitch<double, 8>() : ccr == 4 ? cs_pitch<double, 4>() : ccr);
+    int tc = (int)std::min<long long>(((long long)h->n0 + 31) / 32 * 32, (long long)(48 * 1024 / (sizeof(T) * pitch)) / 32 * 32);
+    tc = std::max(tc, 32);
+    size_t cshm = sizeof(T) * (size_t)tc * pitch;
+    int cgrid = std::max(1, nblk(h->n0, (HK_CS_THREADS / 32) * HK_CS_RPW));
     bool cs_ok = cshm <= 200 * 1024;
 #define HK_RESTRICT(RBV)                                                                                     \
   k_restrict<T, RBV><<<rg, 256, rshm, h->stream>>>(h->n, s, v, active, h->d_sub_info, h->d_sub_off, h->d_I, Zt, \
                                                    h->n0, c, h->g_jp, h->g_jstride)
-#define HK_CSOLVE(CRV) k_coarse_solve<T, CRV><<<cgrid, HK_CS_THREADS, cshm, h->stream>>>(h->n0, s, Einv, c, cc, active)
+#define HK_CSOLVE(CRV) k_coarse_solve<T, CRV><<<cgrid, HK_CS_THREADS, cshm, h->stream>>>(h->n0, s, Einv, c, cc, active, tc)
 #define HK_PROLONG(CRV)                                                                                          \
   k_prolong<T, CRV><<<rg, 256, 0, h->stream>>>(s, h->d_sub_info, h->d_sub_off, Zt, cc, h->n0, h->I_total, zc, active)
     if (cs_ok) {
@@ -836,6 +888,7 @@ static hk_status apply_t(hk_handle* h, int s, const double* v, double* z, const 
           default: HK_RESTRICT(1); break;
         }
         switch (ccr) {
+          case 16: HK_CSOLVE(16); break;
           case 8: HK_CSOLVE(8); break;
           case 4: HK_CSOLVE(4); break;
           case 2: HK_CSOLVE(2); break;
@@ -897,10 +950,12 @@ hk_status apply_prepare(hk_handle*) {
   HK_TRY(hk_allow_smem(k_coarse_solve<float, 2>));
   HK_TRY(hk_allow_smem(k_coarse_solve<float, 4>));
   HK_TRY(hk_allow_smem(k_coarse_solve<float, 8>));
+  HK_TRY(hk_allow_smem(k_coarse_solve<float, 16>));
   HK_TRY(hk_allow_smem(k_coarse_solve<double, 1>));
   HK_TRY(hk_allow_smem(k_coarse_solve<double, 2>));
   HK_TRY(hk_allow_smem(k_coarse_solve<double, 4>));
   HK_TRY(hk_allow_smem(k_coarse_solve<double, 8>));
+  HK_TRY(hk_allow_smem(k_coarse_solve<double, 16>));
   HK_TRY(hk_allow_smem(k_restrict<float, 1>));
   HK_TRY(hk_allow_smem(k_restrict<float, 2>));
   HK_TRY(hk_allow_smem(k_restrict<float, 4>));
