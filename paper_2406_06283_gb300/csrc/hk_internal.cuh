@@ -182,6 +182,7 @@ struct hk_handle {
   };
   std::map<std::pair<int, double>, SolveGraph> graphs;
   bool graphs_ok = true;        // false after a failed graph build: the host-driven loop is used
+  int coop_state = 0;           // cooperative Gram-Schmidt launch: 0 unknown, 1 usable, -1 not
   bool use_graphs = true;       // hk_set_solve_graphs
   long long graph_solves = 0;
   std::map<int, int> nr_tuned;  // right-hand sides per apply CTA chosen by apply_autotune, per batch size

@@ -169,6 +169,171 @@ __global__ void k_gs(int n, int s, int m, int j, const int* __restrict__ jp, con
   if (tid == 0) counter[8 + r] = 0u;
 }
 
+// ---- one inner step's Gram-Schmidt as a single cooperative launch (batches of at most
+// HK_COOP_RHS right-hand sides).  The same arithmetic as k_gs<0..2> + k_normalize in the same
+// order (row chunks of RED_BLOCKS CTAs, warp-per-value reductions with lanes over CTAs), so
+// both forms give the same bits; the four dependent passes are separated by grid barriers
+// instead of kernel boundaries, and every CTA reduces the partial sums it needs itself.
+#define HK_COOP_RHS 4
+
+// Grid-wide barrier of a cooperative launch: arrival counter and generation word; the spin is
+// bounded (about a second), after which HK_TIMEOUT is recorded and the CTA goes on.
+__device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, DevStatus* st) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vg = gen;
+    unsigned g0 = *vg;
+    __threadfence();
+    if (atomicAdd(count, 1u) == gridDim.x - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      unsigned it = 0;
+      while (*vg == g0) {
+        if (++it > (1u << 25)) {
+          dev_fail(st, HK_TIMEOUT, -2, 0.0);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// sum over CTAs b (lanes over b, then the shuffle tree) of part[(b * s + r) * (m + 2) + i], for
+// i < nc, into out[i]: a warp per value, the order of k_gs's final reduction.
+__device__ __forceinline__ void reduce_parts(const double* part, int s, int r, int m, int nc, double* out) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < nc; i += nw) {
+    double acc = 0;
+    for (int b = lane; b < gridDim.x; b += 32) acc += part[((long long)b * s + r) * (m + 2) + i];
+    acc = warp_sum(acc);
+    if (lane == 0) out[i] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_arnoldi_coop(
+    int n, int s, int m, int j, const int* __restrict__ jp, double* V, double* w, int* state, double* rstate,
+    double* hcoef, double* partA, double* partB, unsigned* bar, double* H, double* cs, double* sn, double* g,
+    double* hist, int max_iters, double tol, const int* __restrict__ rowptr, const int* __restrict__ col,
+    const double* __restrict__ val, const double* __restrict__ Zk, DevStatus* st) {
+  __shared__ double red[32];
+  __shared__ double hsh[HK_COOP_RHS][HK_MAXRESTART + 1];
+  __shared__ int act[HK_COOP_RHS];
+  if (jp) j = *jp;
+  const double* zj = Zk + (long long)j * s * n;
+  int chunk = (n + gridDim.x - 1) / gridDim.x;
+  int l0 = blockIdx.x * chunk, l1 = min(n, l0 + chunk);
+  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  if (tid < s) act[tid] = state[8 * tid + ST_ACTIVE];
+  __syncthreads();
+  // A: w = B z_j, h1 partials
+  for (int r = 0; r < s; ++r) {
+    if (!act[r]) continue;
+    double* wr = w + (long long)r * n;
+    const double* zr = zj + (long long)r * n;
+    for (int l = l0 + tid; l < l1; l += blockDim.x) {
+      double acc = 0;
+      for (int q = rowptr[l]; q < rowptr[l + 1]; ++q) acc += val[q] * zr[col[q]];
+      wr[l] = acc;
+    }
+    __syncthreads();
+    double* pr = partA + ((long long)blockIdx.x * s + r) * (m + 2);
+    for (int i = warp; i <= j; i += nw) {
+      const double* vi = V + ((long long)i * s + r) * n;
+      double acc = 0;
+      for (int l = l0 + lane; l < l1; l += 32) acc += wr[l] * vi[l];
+      acc = warp_sum(acc);
+      if (lane == 0) pr[i] = acc;
+    }
+  }
+  grid_barrier(bar, bar + 1, st);
+  // B: h1, w -= V h1, h2 partials;  C: h2, w -= V h2, ||w||^2 partials
+  for (int pass = 0; pass < 2; ++pass) {
+    const double* pin = pass == 0 ? partA : partB;
+    double* pout = pass == 0 ? partB : partA;
+    for (int r = 0; r < s; ++r) {
+      if (!act[r]) continue;
+      double* hr = hsh[r];
+      reduce_parts(pin, s, r, m, j + 1, hr);
+      __syncthreads();
+      if (blockIdx.x == 0)
+        for (int i = tid; i <= j; i += blockDim.x) hcoef[(long long)r * 2 * (m + 1) + pass * (m + 1) + i] = hr[i];
+      double* wr = w + (long long)r * n;
+      for (int l = l0 + tid; l < l1; l += blockDim.x) {
+        double acc = wr[l];
+        for (int i = 0; i <= j; ++i) acc -= hr[i] * V[((long long)i * s + r) * n + l];
+        wr[l] = acc;
+      }
+      __syncthreads();
+      double* pr = pout + ((long long)blockIdx.x * s + r) * (m + 2);
+      if (pass == 0) {
+        for (int i = warp; i <= j; i += nw) {
+          const double* vi = V + ((long long)i * s + r) * n;
+          double acc = 0;
+          for (int l = l0 + lane; l < l1; l += 32) acc += wr[l] * vi[l];
+          acc = warp_sum(acc);
+          if (lane == 0) pr[i] = acc;
+        }
+      } else {
+        double acc = 0;
+        for (int l = l0 + tid; l < l1; l += blockDim.x) acc += wr[l] * wr[l];
+        acc = block_sum(acc, red);
+        if (tid == 0) pr[0] = acc;
+      }
+      __syncthreads();
+    }
+    grid_barrier(bar, bar + 1, st);
+  }
+  // D: ||w||, v_{j+1} = w / ||w|| on the CTA's rows; CTA 0: Hessenberg column, Givens, stop test
+  for (int r = 0; r < s; ++r) {
+    if (!act[r]) continue;
+    reduce_parts(partA, s, r, m, 1, &hsh[r][0]);
+    __syncthreads();
+    double hn = sqrt(hsh[r][0]);
+    double hinv = hn > 0.0 ? 1.0 / hn : 0.0;
+    const double* wr = w + (long long)r * n;
+    double* vn = V + ((long long)(j + 1) * s + r) * n;
+    for (int l = l0 + tid; l < l1; l += blockDim.x) vn[l] = wr[l] * hinv;
+    if (blockIdx.x == 0 && tid == 0) {
+      rstate[8 * r + RS_HNEXT] = hn;
+      rstate[8 * r + RS_HINV] = hinv;
+      double* Hr = H + (long long)r * (m + 1) * m;
+      const double* h1 = hcoef + (long long)r * 2 * (m + 1);
+      const double* h2 = h1 + (m + 1);
+      double* csr = cs + (long long)r * m;
+      double* snr = sn + (long long)r * m;
+      double* gr = g + (long long)r * (m + 1);
+      for (int i = 0; i <= j; ++i) Hr[i * m + j] = h1[i] + h2[i];
+      Hr[(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        double a = Hr[i * m + j], b = Hr[(i + 1) * m + j];
+        Hr[i * m + j] = csr[i] * a + snr[i] * b;
+        Hr[(i + 1) * m + j] = -snr[i] * a + csr[i] * b;
+      }
+      double a = Hr[j * m + j], b = Hr[(j + 1) * m + j];
+      double den = hypot(a, b);
+      csr[j] = a / den;
+      snr[j] = b / den;
+      Hr[j * m + j] = den;
+      Hr[(j + 1) * m + j] = 0.0;
+      gr[j + 1] = -snr[j] * gr[j];
+      gr[j] = csr[j] * gr[j];
+      int it = ++state[8 * r + ST_ITERS];
+      double nf = rstate[8 * r + RS_NF];
+      double est = fabs(gr[j + 1]);
+      rstate[8 * r + RS_EST] = est;
+      if (hist && it <= max_iters) hist[(long long)r * max_iters + it - 1] = est / nf;
+      state[8 * r + ST_JD] = j + 1;
+      bool stop = est <= tol * nf || it >= max_iters || hn == 0.0 || j + 1 == m;
+      if (stop) state[8 * r + ST_ACTIVE] = 0;
+    }
+  }
+}
+
 __global__ void k_normalize(int n, int s, int j, const int* __restrict__ jp, double* V,
                             const double* __restrict__ w, const int* __restrict__ state,
                             const double* __restrict__ rstate) {
@@ -364,7 +529,7 @@ hk_status ensure_workspace(hk_handle* h, int s) {
     HK_TRY(dalloc(h, &h->d_cc64, (size_t)s * (h->n0 + 1)));
     h->d_ybuf32 = nullptr; h->d_c32 = nullptr; h->d_cc32 = nullptr;
   }
-  HK_TRY(dalloc(h, &h->d_part, (size_t)RED_BLOCKS * s * (m + 2)));
+  HK_TRY(dalloc(h, &h->d_part, 2 * (size_t)RED_BLOCKS * s * (m + 2)));  // two buffers (cooperative step)
   HK_TRY(dalloc(h, &h->d_counter, 8 + (size_t)s));  // [0]: norms; [8 + r]: Gram-Schmidt of rhs r
   HK_TRY(dalloc(h, &h->d_H, (size_t)s * (m + 1) * m));
   HK_TRY(dalloc(h, &h->d_cs, (size_t)s * m));
@@ -413,6 +578,19 @@ static hk_status fgmres_cycle_start(hk_handle* h, int s) {
   return HK_OK;
 }
 
+// Whether the cooperative Gram-Schmidt launch fits on this device (RED_BLOCKS CTAs resident).
+static bool coop_ready(hk_handle* h) {
+  if (h->coop_state == 0) {
+    int coop = 0, nsm = 0, per = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_arnoldi_coop, RED_THREADS, 0);
+    h->coop_state = (coop && (long long)nsm * per >= RED_BLOCKS) ? 1 : -1;
+    cudaGetLastError();
+  }
+  return h->coop_state > 0;
+}
+
 // Inner step j: z_j = M^{-1} v_j, w = B z_j, CGS2, Givens, v_{j+1}.  With jp != NULL every kernel reads
 // j from *jp (the captured form); otherwise j is passed by value.
 static hk_status fgmres_step(hk_handle* h, int s, double tol, int j, const int* jp) {
@@ -430,6 +608,23 @@ static hk_status fgmres_step(hk_handle* h, int s, double tol, int j, const int* 
   if (h->timing) {
     ga = hk_event(h);
     cudaEventRecord(ga, st);
+  }
+  if (s <= HK_COOP_RHS && coop_ready(h)) {
+    double* partB = h->d_part + (size_t)RED_BLOCKS * s * (m + 2);
+    unsigned* bar = h->d_counter + 2;
+    double* V = h->d_V;
+    const double* Zk = h->d_Zk;
+    void* args[] = {&n, &s, &m, &j, (void*)&jp, &V, &h->d_w, &h->d_state, &h->d_rstate, &h->d_hcol, &h->d_part,
+                    &partB, &bar, &h->d_H, &h->d_cs, &h->d_sn, &h->d_g, &h->d_hist, &mi, &tol, &h->d_rowptr,
+                    &h->d_col, &h->d_valB, (void*)&Zk, &h->d_status};
+    HK_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_coop, dim3(RED_BLOCKS), dim3(RED_THREADS), args, 0, st));
+    HK_COUNT_LAUNCH();
+    if (h->timing) {
+      cudaEvent_t gb = hk_event(h);
+      cudaEventRecord(gb, st);
+      h->tl.push_back({HK_T_ARNOLDI, ga, gb});
+    }
+    return HK_OK;
   }
   k_gs<0><<<dim3(RED_BLOCKS, s), RED_THREADS, 0, st>>>(n, s, m, j, jp, h->d_V, h->d_w, h->d_state, h->d_rstate, h->d_hcol,
                                               h->d_part, h->d_counter, h->d_H, h->d_cs, h->d_sn, h->d_g, h->d_hist,
