@@ -39,9 +39,9 @@ from paper_2406_06283_gb300 import workloads as W  # noqa: E402
 
 METRIC = "Helmholtz solves/s and p99 latency at 1e-8 residual; FP32-precond vs FP64 form"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# DRAM bytes (read + write) of one k_tridiag32 launch from an ncu capture of the same kernel, per workload;
-# None until a capture of the current kernel exists.
-TRIDIAG_TRAFFIC = {}
+# DRAM bytes (read + write) of one k_tridiag32 launch from an ncu capture of the same kernel, per workload
+# (profiles/k_tridiag32_h256_k50.md); absent until a capture of the current kernel exists.
+TRIDIAG_TRAFFIC = {"c2": 6741196032 + 27854091520}
 
 
 def workload(name: str):
