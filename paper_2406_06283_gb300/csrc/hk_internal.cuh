@@ -133,6 +133,7 @@ struct hk_handle {
   // level records streamed by the apply (see hk_local.cu), their table and the largest record
   unsigned char* d_pack = nullptr;
   long long* d_lvtab = nullptr;
+  long long* d_lvfo = nullptr;    // setup only: per level, offset of its blocks in the FP64 factors
   long long pack_bytes = 0, pack_stage = 0;
   // coarse space
   double* d_lam = nullptr;        // per subdomain kept eigenvalues (HK_MAXM each)

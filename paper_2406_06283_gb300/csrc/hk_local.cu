@@ -3,40 +3,115 @@
 //
 // In level order B_i is block tridiagonal: diagonal blocks D_j, couplings
 // L_j = B[level j, level j-1] and U_j = B[level j, level j+1] = L_{j+1}^T.
-// Its block LU uses the Schur complements
-//     S_0 = D_0,   S_j = D_j - L_j S_{j-1}^{-1} U_{j-1},
-// and a solve B_i x = r is the pair of sweeps
-//     forward   y_j = S_j^{-1} (r_j - L_j y_{j-1})
-//     backward  x_j = y_j - G_j x_{j+1},   G_j = S_j^{-1} U_j.
-// Setup stores S_j^{-1} (b_j x b_j) and G_j (b_j x b_{j+1}) densely, row-major,
-// each block starting on a 4-element boundary; the sparse L_j is read from
-// the local CSR.  S_j^{-1} is formed in FP64 by Gauss-Jordan elimination with
-// partial pivoting; a pivot below 1e-10 max|B_i| reports HK_SINGULAR_LOCAL.
-// For the apply, the forward step is rewritten with W_j = S_j^{-1} L_j as
-//     y_j = [-W_j | S_j^{-1}] [y_{j-1}; r_j],
-// one dense product over two consecutive levels of the level-ordered vector.
+// It is factored from both ends towards the middle level M = (L-1)/2 (a twisted
+// block factorisation), with the Schur complements
+//     top     S_0 = D_0,          S_j = D_j - L_j S_{j-1}^{-1} U_{j-1}      (j < M)
+//     bottom  T_{L-1} = D_{L-1},  T_j = D_j - U_j T_{j+1}^{-1} L_{j+1}      (j > M)
+//     middle  Sigma = D_M - L_M S_{M-1}^{-1} U_{M-1} - U_M T_{M+1}^{-1} L_{M+1},
+// and a solve B_i x = r runs two half sweeps at once:
+//     y_j = S_j^{-1} (r_j - L_j y_{j-1})          j = 0 .. M-1
+//     z_j = T_j^{-1} (r_j - U_j z_{j+1})          j = L-1 .. M+1
+//     x_M = Sigma^{-1} (r_M - L_M y_{M-1} - U_M z_{M+1})
+//     x_j = y_j - G_j x_{j+1},  G_j = S_j^{-1} U_j    j = M-1 .. 0
+//     x_j = z_j - H_j x_{j-1},  H_j = T_j^{-1} L_j    j = M+1 .. L-1
+// so the dependent chain is about L steps instead of 2L - 1.  Setup stores, per
+// level, the inverse block (b_j x b_j) and the coupling product (G_j, b_j x b_{j+1},
+// above the middle; H_j, b_j x b_{j-1}, below it; none at the middle) densely,
+// row-major, each starting on a 4-element boundary.  Inverses are formed in FP64 by
+// Gauss-Jordan elimination with partial pivoting; a pivot below 1e-10 max|B_i|
+// reports HK_SINGULAR_LOCAL.  For the apply, the first-sweep steps are rewritten as one
+// dense product over consecutive levels of the level-ordered vector, e.g.
+//     y_j = [-S_j^{-1} L_j | S_j^{-1}] [y_{j-1}; r_j].
 #include <algorithm>
 
 #include "hk_internal.cuh"
 
 static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 __host__ __device__ __forceinline__ long long pad4(long long x) { return (x + 3) & ~3LL; }
+__host__ __device__ __forceinline__ int twist_mid(int L) { return (L - 1) / 2; }
+
+// Columns of the coupling product stored after the inverse block of level j.
+__host__ __device__ __forceinline__ long long coupling_cols(const int* lp, int L, int j) {
+  int M = twist_mid(L);
+  if (j < M) return lp[j + 2] - lp[j + 1];
+  if (j > M) return lp[j] - lp[j - 1];
+  return 0;
+}
 
 // Element count of the factor blocks of one subdomain.
 long long factor_elems(const int* lp, int L) {
   long long t = 0;
   for (int j = 0; j < L; ++j) {
     long long b = lp[j + 1] - lp[j];
-    long long bn = j + 1 < L ? lp[j + 2] - lp[j + 1] : 0;
-    t += pad4(b * b) + pad4(b * bn);
+    t += pad4(b * b) + pad4(b * coupling_cols(lp, L, j));
   }
   return t;
 }
 
+// One level of the twisted factorisation: the Schur complement of level j with the
+// coupling products of its already eliminated neighbours (G_{j-1} above, H_{j+1} below),
+// its inverse, and its own coupling product (G_j = X^{-1} U_j towards the middle from the
+// top, H_j = X^{-1} L_j from the bottom).
+__device__ void twisted_level(int j, int L, const int* lp, const long long* fo, const int* lr, const int* lcntI,
+                              const int* lcol, const double* lval, int off, long long coff, double* F, double* S,
+                              int s_in_smem, int* piv, double* red_v, int* red_i, double* minpiv) {
+  int tid = threadIdx.x, T = blockDim.x, M = twist_mid(L);
+  int r0 = lp[j], b = lp[j + 1] - r0;
+  bool up = j > 0 && j <= M;        // eliminated neighbour above (top part or middle)
+  bool down = j < L - 1 && j >= M;  // eliminated neighbour below (bottom part or middle)
+  int pr0 = j > 0 ? lp[j - 1] : r0, nr0 = lp[j + 1], nr1 = j + 1 < L ? lp[j + 2] : nr0;
+  const double* Gp = up ? F + fo[j - 1] + pad4((long long)(r0 - pr0) * (r0 - pr0)) : nullptr;  // G_{j-1}: b_{j-1} x b
+  const double* Hn = down ? F + fo[j + 1] + pad4((long long)(nr1 - nr0) * (nr1 - nr0)) : nullptr;  // H_{j+1}: b_{j+1} x b
+  double* X = s_in_smem ? S : F + fo[j];
+  for (int e = tid; e < b * b; e += T) {
+    int qa = e / b, t = e % b;
+    int a = r0 + qa;
+    const int* cl = lcol + coff + lr[a];
+    const double* cv = lval + coff + lr[a];
+    int cnt = lcntI[off + a];
+    double v = 0;
+    for (int q = 0; q < cnt; ++q) {
+      int c = cl[q];
+      if (c == r0 + t) v += cv[q];
+      else if (up && c >= pr0 && c < r0) v -= cv[q] * Gp[(long long)(c - pr0) * b + t];
+      else if (down && c >= nr0 && c < nr1) v -= cv[q] * Hn[(long long)(c - nr0) * b + t];
+    }
+    X[e] = v;
+  }
+  __syncthreads();
+  gauss_jordan_inverse(X, b, piv, red_v, red_i, minpiv);
+  if (s_in_smem)
+    for (int e = tid; e < b * b; e += T) F[fo[j] + e] = X[e];
+  if (j == M) {
+    __syncthreads();
+    return;
+  }
+  // coupling product: rows of the neighbour level towards the middle, whose entries in level j
+  // are the coupling (B symmetric)
+  int c0 = j < M ? nr0 : pr0, cb = j < M ? nr1 - nr0 : r0 - pr0;
+  double* P = F + fo[j] + pad4((long long)b * b);
+  for (int e = tid; e < b * cb; e += T) {
+    int qt = e / cb, cc = e % cb;
+    int c = c0 + cc;
+    const int* cl = lcol + coff + lr[c];
+    const double* cv = lval + coff + lr[c];
+    int cnt = lcntI[off + c];
+    double v = 0;
+    for (int q = 0; q < cnt; ++q) {
+      int a = cl[q];
+      if (a >= r0 && a < r0 + b) v += X[qt * b + (a - r0)] * cv[q];
+    }
+    P[e] = v;
+  }
+  __syncthreads();
+}
+
+// fo: per subdomain, L + 1 factor offsets (elements from the start of the factor array).
 __global__ void k_block_lu(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
                            const int* __restrict__ levptr, const int* __restrict__ lrow,
                            const int* __restrict__ lcntI, const int* __restrict__ lcol,
-                           const double* __restrict__ lval, double* F, int s_in_smem, DevStatus* st) {
+                           const double* __restrict__ lval, const long long* __restrict__ lvfo, double* F,
+                           int s_in_smem, DevStatus* st) {
   extern __shared__ double smem[];
   __shared__ int piv[HK_MAXB];
   __shared__ double red_v[32];
@@ -45,9 +120,10 @@ __global__ void k_block_lu(const int* __restrict__ sub_info, const long long* __
   int s = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
   const int* si = sub_info + 8 * s;
   int nI = si[0], L = si[2], off = si[3], loff = si[5];
-  long long foff = sub_off[3 * s], coff = sub_off[3 * s + 1];
+  long long coff = sub_off[3 * s + 1];
   const int* lp = levptr + loff;
   const int* lr = lrow + off + s;
+  const long long* fo = lvfo + loff;
   // scale for the singularity test: max |B_i| entry
   double mx = 0;
   for (int a = tid; a < nI; a += T)
@@ -64,52 +140,12 @@ __global__ void k_block_lu(const int* __restrict__ sub_info, const long long* __
   __syncthreads();
   double scale = red_v[0];
   __syncthreads();
-  long long bo = foff, prev_go = -1;
-  int prev_r0 = 0;
-  for (int j = 0; j < L; ++j) {
-    int r0 = lp[j], b = lp[j + 1] - r0;
-    int r1 = lp[j + 1];
-    int bn = j + 1 < L ? lp[j + 2] - r1 : 0;
-    // S = D_j - L_j G_{j-1}, in shared memory, or in place in the factor array for wide levels
-    double* S = s_in_smem ? smem : F + bo;
-    for (int e = tid; e < b * b; e += T) {
-      int qa = e / b, t = e % b;
-      int a = r0 + qa;
-      const int* cl = lcol + coff + lr[a];
-      const double* cv = lval + coff + lr[a];
-      int cnt = lcntI[off + a];
-      double v = 0;
-      for (int q = 0; q < cnt; ++q) {
-        int c = cl[q];
-        if (c == r0 + t) v += cv[q];
-        else if (j > 0 && c >= prev_r0 && c < r0) v -= cv[q] * F[prev_go + (long long)(c - prev_r0) * b + t];
-      }
-      S[e] = v;
-    }
-    __syncthreads();
-    gauss_jordan_inverse(S, b, piv, red_v, red_i, &minpiv);
-    if (s_in_smem)
-      for (int e = tid; e < b * b; e += T) F[bo + e] = S[e];
-    long long go = bo + pad4((long long)b * b);
-    // G_j = S_j^{-1} U_j, with U_j[a, c] = B[c, a] read from the rows of level j+1
-    for (int e = tid; e < b * bn; e += T) {
-      int qt = e / bn, cc = e % bn;
-      int c = r1 + cc;
-      const int* cl = lcol + coff + lr[c];
-      const double* cv = lval + coff + lr[c];
-      int cnt = lcntI[off + c];
-      double v = 0;
-      for (int q = 0; q < cnt; ++q) {
-        int a = cl[q];
-        if (a >= r0 && a < r1) v += S[qt * b + (a - r0)] * cv[q];
-      }
-      F[go + e] = v;
-    }
-    __syncthreads();
-    prev_go = go;
-    prev_r0 = r0;
-    bo = go + pad4((long long)b * bn);
-  }
+  int M = twist_mid(L);
+  for (int j = 0; j < M; ++j)
+    twisted_level(j, L, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv);
+  for (int j = L - 1; j > M; --j)
+    twisted_level(j, L, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv);
+  twisted_level(M, L, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv);
   if (tid == 0 && !(minpiv > 1e-10 * scale)) dev_fail(st, HK_SINGULAR_LOCAL, s, minpiv / scale);
 }
 
@@ -145,10 +181,15 @@ void launch_to_f32(const double* a, float* b, long long n, cudaStream_t st) {
 
 
 // ====================================================================== apply
-// Level records, streamed by the apply kernel one after another, row-major with rows
-// padded to a multiple of 4 entries (zeros), so that rows start on 16-byte boundaries:
-//   forward record j:  F_j = [-W_j | S_j^{-1}]   b_j x pad4(b_{j-1} + b_j), T
-//   backward record j: G_j                      b_j x pad4(b_{j+1}),       T
+// Level records, streamed by the apply kernel, row-major with rows padded to a multiple
+// of 4 entries (zeros), so that rows start on 16-byte boundaries (T = float or double):
+//   first-sweep record j: above the middle [-S_j^{-1} L_j | S_j^{-1}] (b_j x pad4(b_{j-1}+b_j)),
+//                         below it [T_j^{-1} | -T_j^{-1} U_j] (b_j x pad4(b_j+b_{j+1})),
+//                         at the middle [-Sigma^{-1} L_M | Sigma^{-1} | -Sigma^{-1} U_M];
+//   second-sweep record j: G_j (b_j x pad4(b_{j+1})) above the middle, H_j (b_j x pad4(b_{j-1}))
+//                         below it, none at the middle.
+// The top stream is: first sweep 0 .. M-1, middle, second sweep M-1 .. 0; the bottom stream:
+// first sweep L-1 .. M+1, second sweep M+1 .. L-1.
 // A record streams as chunks of consecutive rows, one 1-D TMA bulk copy each, of at most
 // HK_CHUNK_BYTES (one chunk per record on 2D subdomains).
 // Level table entry (4 x int64 per level): fwd offset, bwd offset, fwd | bwd bytes << 32,
@@ -221,47 +262,54 @@ __global__ void k_pack_levels(const int* __restrict__ sub_info, const long long*
                               const int* __restrict__ levptr, const int* __restrict__ lrow,
                               const int* __restrict__ lcntI, const int* __restrict__ lcol,
                               const double* __restrict__ lvalB, const double* __restrict__ F,
-                              const long long* __restrict__ lvtab, unsigned char* pack) {
+                              const long long* __restrict__ lvfo, const long long* __restrict__ lvtab,
+                              unsigned char* pack) {
   int s = blockIdx.x, tid = threadIdx.x, T_ = blockDim.x;
   const int* si = sub_info + 8 * s;
   int L = si[2], off = si[3], loff = si[5];
-  long long foff = sub_off[3 * s], coff = sub_off[3 * s + 1];
+  long long coff = sub_off[3 * s + 1];
   const int* lp = levptr + loff;
   const int* lr = lrow + off + s;
-  long long bo = foff;
+  const long long* fo = lvfo + loff;
+  int M = twist_mid(L);
+  // -X^{-1} B[level j, c] for a node c of a neighbour level: the couplings of row c inside level j
+  auto coupled = [&](const double* Xi, int b, int r0, int row, int c) -> double {
+    const int* cl = lcol + coff + lr[c];
+    const double* cv = lvalB + coff + lr[c];
+    double v = 0;
+    for (int t = 0; t < lcntI[off + c]; ++t) {
+      int a = cl[t];
+      if (a >= r0 && a < r0 + b) v -= Xi[(long long)row * b + (a - r0)] * cv[t];
+    }
+    return v;
+  };
   for (int j = 0; j < L; ++j) {
     int r0 = lp[j], b = lp[j + 1] - r0, bn = j + 1 < L ? lp[j + 2] - lp[j + 1] : 0;
-    int pr0 = j > 0 ? lp[j - 1] : r0, bp = r0 - pr0;
+    int pr0 = j > 0 ? lp[j - 1] : r0, bp = r0 - pr0, nr0 = lp[j + 1];
+    int lb = (j > 0 && j <= M) ? bp : 0, rb = (j < L - 1 && j >= M) ? bn : 0;
     const long long* e = lvtab + 4 * (long long)(loff + j);
-    int ldf = (int)pad4(bp + b), ldb = (int)pad4(bn);
-    long long go = bo + pad4((long long)b * b);
+    int ldf = (int)pad4(lb + b + rb);
+    const double* Xi = F + fo[j];
+    // first-sweep record: [-X^{-1} L_j (top, middle) | X^{-1} | -X^{-1} U_j (bottom, middle)]
     T* Fr = reinterpret_cast<T*>(pack + e[0]);
     for (int q = tid; q < b * ldf; q += T_) {
       int row = q / ldf, col = q % ldf;
       double v = 0;
-      if (col < bp) {
-        // -W_j[row][c] = -sum_a S_j^{-1}[row][a] B[a][c]; B symmetric: the couplings of row c of
-        // level j-1 with level j
-        int c = pr0 + col;
-        const int* cl = lcol + coff + lr[c];
-        const double* cv = lvalB + coff + lr[c];
-        for (int t = 0; t < lcntI[off + c]; ++t) {
-          int a = cl[t];
-          if (a >= r0 && a < r0 + b) v -= F[bo + (long long)row * b + (a - r0)] * cv[t];
-        }
-      } else if (col < bp + b) {
-        v = F[bo + (long long)row * b + (col - bp)];
-      }
+      if (col < lb) v = coupled(Xi, b, r0, row, pr0 + col);
+      else if (col < lb + b) v = Xi[(long long)row * b + (col - lb)];
+      else if (col < lb + b + rb) v = coupled(Xi, b, r0, row, nr0 + (col - lb - b));
       Fr[q] = (T)v;
     }
-    if (bn > 0) {
+    if (j != M) {
+      // second-sweep record: G_j (b x b_{j+1}) above the middle, H_j (b x b_{j-1}) below it
+      int cb = j < M ? bn : bp, ldb = (int)pad4(cb);
+      const double* P = Xi + pad4((long long)b * b);
       T* Gr = reinterpret_cast<T*>(pack + e[1]);
       for (int q = tid; q < b * ldb; q += T_) {
         int row = q / ldb, col = q % ldb;
-        Gr[q] = col < bn ? (T)F[go + (long long)row * bn + col] : (T)0;
+        Gr[q] = col < cb ? (T)P[(long long)row * cb + col] : (T)0;
       }
     }
-    bo = go + pad4((long long)b * bn);
   }
 }
 
@@ -282,7 +330,7 @@ __global__ void k_pack_levels(const int* __restrict__ sub_info, const long long*
 // zero rows after each group's rows keep the padded last columns of a record finite.
 // Every wait is bounded; a wait that gives up reports HK_TIMEOUT, and the producer lets
 // the copies it has in flight land before the CTA exits.
-#define HK_APPLY_MAXK 24
+#define HK_APPLY_MAXK 12
 #define HK_APPLY_MAXT 768  // threads of a CTA at most (24 warps)
 
 // R-vector loads and stores of shared-memory rows, as 16- or 8-byte accesses where the
@@ -335,7 +383,7 @@ __device__ __forceinline__ bool mbar_wait_or_fail(uint64_t* bar, unsigned parity
   return false;
 }
 
-// Barrier over the WG warps of a sweep group that also ORs a flag across them.
+// Barrier over WG warps (a sweep half group, or both halves) that also ORs a flag across them.
 __device__ __forceinline__ int group_any(int flag, int WG, int id) {
   if (WG == 1) {
     __syncwarp();
@@ -393,52 +441,38 @@ __global__ void __launch_bounds__(HK_APPLY_MAXT, 1) k_local_apply(
     int stage_bytes, int K, int WG, int max_L, int max_dof, T* ybuf, DevStatus* st, const int* __restrict__ jp,
     long long jstride) {
   constexpr int R = NR < 4 ? NR : 4;
-  constexpr int WS = NR / R;  // sweep groups
+  constexpr int WS = NR / R;  // right-hand-side groups, each two half groups of WG warps
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full[HK_APPLY_MAXK], empty[HK_APPLY_MAXK], meta;
+  __shared__ __align__(8) uint64_t full[2][HK_APPLY_MAXK], empty[2][HK_APPLY_MAXK], meta;
   __shared__ int sh_fail;
   if (jp) v += (long long)(*jp) * jstride;  // captured inner step: v = v_j with j read on the device
   int s = blockIdx.x, r_base = blockIdx.y * NR;
   int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int nwarps = blockDim.x >> 5, nwc = nwarps - 1;  // consumer warps; the last warp produces
+  int nwarps = blockDim.x >> 5, nwc = nwarps - 2;  // consumer warps; the last two warps produce
   int nct = nwc * 32;
-  bool producer = warp == nwarps - 1;
+  int prod = warp - nwc;  // 0: top stream, 1: bottom stream, < 0: consumer
   const int* si = sub_info + 8 * s;
   int nI = si[0], L = si[2], off = si[3], loff = si[5];
+  int M = twist_mid(L);
   int xs = nI + 4;  // rows per group slice of x
-  // shared memory: record ring | level table (4 x int64 per level) | step parameters (int4 per
-  // level step) | dof indices (16-byte aligned span around dof(Omega_i)) | x
-  long long* tab = reinterpret_cast<long long*>(smem_raw + (long long)K * stage_bytes);
-  int4* lvp = reinterpret_cast<int4*>(tab + 4 * (long long)max_L);
-  int* idx = reinterpret_cast<int*>(lvp + 2 * (long long)max_L);
+  int nst[2] = {2 * M + 1, 2 * (L - 1 - M)};  // steps of the top and bottom streams
+  // shared memory: two record rings | level table (4 x int64 per level) | step parameters of both
+  // streams (int4 each) | their record offsets | dof indices (16-byte aligned span) | x
+  long long* tab = reinterpret_cast<long long*>(smem_raw + 2LL * K * stage_bytes);
+  int4* sp = reinterpret_cast<int4*>(tab + 4 * (long long)max_L);              // [2][max_L]
+  long long* so = reinterpret_cast<long long*>(sp + 2 * (long long)max_L);     // [2][max_L]
+  int* idx = reinterpret_cast<int*>(so + 2 * (long long)max_L);
   int ioff = off & 3;  // position of the first index in the aligned span
   int ispan = (ioff + nI + 3) & ~3;
   T* x = reinterpret_cast<T*>(idx + ((max_dof + 7) & ~3));  // WS groups x (nI + 4) x R
   int nr = s_tot - r_base < NR ? s_tot - r_base : NR;
-  int nlev = 2 * L - 1;  // level steps: forward 0 .. L-1, backward L-2 .. 0
-  // the producer's position in the chunk stream: level step ps_rs, chunk ps_c
-  int ps_rs = 0, ps_c = 0;
-  auto next_chunk = [&](const unsigned char*& src, unsigned& bytes) -> bool {
-    if (ps_rs >= nlev) return false;
-    bool fwd = ps_rs < L;
-    const long long* e = tab + 4 * (fwd ? ps_rs : 2 * L - 2 - ps_rs);
-    long long e3 = e[3];
-    int b = lv_b(e3), rc = fwd ? lv_rcf(e3) : lv_rcb(e3);
-    long long tot = fwd ? (e[2] & 0xffffffffLL) : (long long)((unsigned long long)e[2] >> 32);
-    long long rowb = tot / b;
-    int row0 = ps_c * rc, nrows = b - row0 < rc ? b - row0 : rc;
-    src = pack + (fwd ? e[0] : e[1]) + row0 * rowb;
-    bytes = (unsigned)(nrows * rowb);
-    if (row0 + nrows >= b) ++ps_rs, ps_c = 0;
-    else ++ps_c;
-    return true;
-  };
   if (tid == 0) {
     sh_fail = 0;
-    for (int k = 0; k < K; ++k) {
-      mbar_init(&full[k], 1);
-      mbar_init(&empty[k], WS * WG);
-    }
+    for (int h = 0; h < 2; ++h)
+      for (int k = 0; k < K; ++k) {
+        mbar_init(&full[h][k], 1);
+        mbar_init(&empty[h][k], WS * WG);
+      }
     mbar_init(&meta, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     // the level table and the dof indices by two bulk copies
@@ -449,17 +483,70 @@ __global__ void __launch_bounds__(HK_APPLY_MAXT, 1) k_local_apply(
   __syncthreads();
   bool meta_ok = mbar_wait_or_fail(&meta, 0u, &sh_fail);
   if (!meta_ok && tid == 0 && atomicExch(&sh_fail, 1) == 0) dev_fail(st, HK_TIMEOUT, s, -1);
-  int issued = 0;
-  if (producer && lane == 0 && meta_ok) {
-    const unsigned char* src;
-    unsigned bytes;
-    for (; issued < K && next_chunk(src, bytes); ++issued) {
-      mbar_expect_tx(&full[issued], bytes);
-      tma_load_1d(smem_raw + (long long)issued * stage_bytes, src, bytes, &full[issued]);
+  int nthr = 32 * WG;
+  if (meta_ok) {
+    // step parameters of both streams: b | lg << 16, ld | assign << 16, level start, first input
+    // row | rows per chunk << 16; and the record's byte offset in the pack
+    for (int e = tid; e < nst[0] + nst[1]; e += blockDim.x) {
+      int h = e < nst[0] ? 0 : 1, k = h ? e - nst[0] : e;
+      int j, kind;  // kind 0: first sweep (and middle), 1: second sweep
+      if (h == 0) {
+        j = k <= M ? k : 2 * M - k;
+        kind = k <= M ? 0 : 1;
+      } else {
+        int nf = L - 1 - M;
+        j = k < nf ? L - 1 - k : M + 1 + (k - nf);
+        kind = k < nf ? 0 : 1;
+      }
+      const long long* en = tab + 4 * j;
+      long long e3 = en[3];
+      int b = lv_b(e3), ls = lv_start(e3);
+      int bp = j > 0 ? ls - lv_start(tab[4 * (j - 1) + 3]) : 0;
+      int bn = j + 1 < L ? lv_b(tab[4 * (j + 1) + 3]) : 0;
+      int ld, in_row, rc;
+      if (kind == 0) {
+        int lb = (j > 0 && j <= M) ? bp : 0, rb = (j < L - 1 && j >= M) ? bn : 0;
+        ld = (int)pad4(lb + b + rb);
+        in_row = ls - lb;
+        rc = lv_rcf(e3);
+      } else {
+        int cb = j < M ? bn : bp;
+        ld = (int)pad4(cb);
+        in_row = j < M ? ls + b : ls - bp;
+        rc = lv_rcb(e3);
+      }
+      int lg = 0;  // G = 2^lg lanes per row, as many as keep b * G <= nthr (one pass)
+      while (lg < 5 && (b << (lg + 1)) <= nthr) ++lg;
+      sp[h * max_L + k] = make_int4(b | (lg << 16), ld | ((kind == 0) << 16), ls, in_row | (rc << 16));
+      so[h * max_L + k] = kind == 0 ? en[0] : en[1];
     }
   }
-  int nthr = 32 * WG;
-  if (!producer && meta_ok) {
+  __syncthreads();
+  // producer of stream h: position (step ps_k, chunk ps_c)
+  int ps_k = 0, ps_c = 0;
+  auto next_chunk = [&](int h, const unsigned char*& src, unsigned& bytes) -> bool {
+    if (ps_k >= nst[h]) return false;
+    int4 pv = sp[h * max_L + ps_k];
+    int b = pv.x & 0xFFFF, ld = pv.y & 0xFFFF, rc = pv.w >> 16;
+    long long rowb = (long long)ld * sizeof(T);
+    int row0 = ps_c * rc, nrows = b - row0 < rc ? b - row0 : rc;
+    src = pack + so[h * max_L + ps_k] + row0 * rowb;
+    bytes = (unsigned)(nrows * rowb);
+    if (row0 + nrows >= b) ++ps_k, ps_c = 0;
+    else ++ps_c;
+    return true;
+  };
+  int issued = 0;
+  unsigned char* ring = prod >= 0 ? smem_raw + (long long)prod * K * stage_bytes : nullptr;
+  if (prod >= 0 && lane == 0 && meta_ok) {
+    const unsigned char* src;
+    unsigned bytes;
+    for (; issued < K && next_chunk(prod, src, bytes); ++issued) {
+      mbar_expect_tx(&full[prod][issued], bytes);
+      tma_load_1d(ring + (long long)issued * stage_bytes, src, bytes, &full[prod][issued]);
+    }
+  }
+  if (prod < 0 && meta_ok) {
     // gather, eight values per thread in flight
     int tot = nI * NR;
     for (int e0 = tid; e0 < tot; e0 += 8 * nct) {
@@ -480,58 +567,58 @@ __global__ void __launch_bounds__(HK_APPLY_MAXT, 1) k_local_apply(
         }
       }
     }
-    // per level step: b | lg << 16, ld | bo << 16, level start, rows per chunk
-    for (int rs = tid; rs < nlev; rs += nct) {
-      bool fwd = rs < L;
-      int j = fwd ? rs : 2 * L - 2 - rs;
-      long long e3 = tab[4 * j + 3];
-      int b = lv_b(e3), ls = lv_start(e3), rc = fwd ? lv_rcf(e3) : lv_rcb(e3);
-      int bo = fwd ? (j > 0 ? ls - lv_start(tab[4 * (j - 1) + 3]) : 0) : lv_b(tab[4 * (j + 1) + 3]);
-      int ld = fwd ? (int)pad4(bo + b) : (int)pad4(bo);
-      int lg = 0;  // G = 2^lg lanes per row, as many as keep b * G <= nthr (one pass)
-      while (lg < 5 && (b << (lg + 1)) <= nthr) ++lg;
-      lvp[rs] = make_int4(b | (lg << 16), ld | (bo << 16), ls, rc);
-    }
     for (int e = tid; e < WS * 4 * R; e += nct) {  // the zero rows after each group's slice
       int g = e / (4 * R), q = e % (4 * R);
       x[((long long)g * xs + nI) * R + q] = (T)0;
     }
   }
   __syncthreads();
-  if (producer) {
+  if (prod >= 0) {
     if (lane != 0 || !meta_ok) return;
     const unsigned char* src;
     unsigned bytes;
     bool failed = false;
-    for (; next_chunk(src, bytes); ++issued) {
+    for (; next_chunk(prod, src, bytes); ++issued) {
       int k = issued % K;
-      if (!mbar_wait_or_fail(&empty[k], (unsigned)((issued / K) - 1) & 1u, &sh_fail)) {
+      if (!mbar_wait_or_fail(&empty[prod][k], (unsigned)((issued / K) - 1) & 1u, &sh_fail)) {
         if (atomicExch(&sh_fail, 1) == 0) dev_fail(st, HK_TIMEOUT, s, issued);
         failed = true;
         break;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_expect_tx(&full[k], bytes);
-      tma_load_1d(smem_raw + (long long)k * stage_bytes, src, bytes, &full[k]);
+      mbar_expect_tx(&full[prod][k], bytes);
+      tma_load_1d(ring + (long long)k * stage_bytes, src, bytes, &full[prod][k]);
     }
     if (failed) {  // let the copies in flight land before the CTA exits
       for (int r = issued - K < 0 ? 0 : issued - K; r < issued; ++r)
-        mbar_wait_bounded(&full[r % K], (unsigned)(r / K) & 1u);
+        mbar_wait_bounded(&full[prod][r % K], (unsigned)(r / K) & 1u);
     }
     return;
   }
   if (!meta_ok) return;
-  int g = warp / WG, wr = warp % WG;
-  int bar_id = 1 + g, gt = wr * 32 + lane;
+  int g = warp / (2 * WG), h = (warp / WG) & 1, wr = warp % WG;
+  int hid = 1 + 3 * g + h, jid = 3 + 3 * g;  // named barriers: this half, both halves
+  int gt = wr * 32 + lane;
   T* xg = x + (long long)g * xs * R;
-  int ks = 0;            // stage of the next chunk
-  unsigned kph = 0;       // its phase parity
-  for (int rs = 0; rs < nlev; ++rs) {
-    bool fwd = rs < L;
-    int4 pv = lvp[rs];
-    int b = pv.x & 0xFFFF, lg = pv.x >> 16, ld = pv.y & 0xFFFF, bo = pv.y >> 16, ls = pv.z, rc = pv.w;
-    // forward: input rows [ls - bo, ls + b) = [y_{j-1}; r_j]; backward: x_{j+1} at [ls + b, ls + b + bo)
-    const T* xin = xg + (long long)(fwd ? ls - bo : ls + b) * R;
+  const unsigned char* myring = smem_raw + (long long)h * K * stage_bytes;
+  uint64_t* myfull = full[h];
+  uint64_t* myempty = empty[h];
+  bool dead = false;  // a wait gave up: from then on only the barriers are kept
+  int ks = 0;          // stage of the next chunk
+  unsigned kph = 0;    // its phase parity
+  // joint point of the two halves: top, before and after the middle step; bottom, between its sweeps
+  int n_first = h == 0 ? M : L - 1 - M;
+  for (int k = 0; k <= nst[h]; ++k) {
+    if (k == n_first) {
+      dead = group_any(dead, 2 * WG, jid) != 0;  // the bottom sweep's z_{M+1} is ready
+      if (h == 1) dead = group_any(dead, 2 * WG, jid) != 0;  // x_M is ready
+    }
+    if (h == 0 && k == n_first + 1) dead = group_any(dead, 2 * WG, jid) != 0;
+    if (k == nst[h]) break;
+    int4 pv = sp[h * max_L + k];
+    int b = pv.x & 0xFFFF, lg = pv.x >> 16, ld = pv.y & 0xFFFF, assign = pv.y >> 16, ls = pv.z,
+        in_row = pv.w & 0xFFFF, rc = pv.w >> 16;
+    const T* xin = xg + (long long)in_row * R;
     int G = 1 << lg;
     int q = gt >> lg, gl = gt & (G - 1);
     int nv = ld >> 2, cv = (nv + G - 1) >> lg;
@@ -539,32 +626,33 @@ __global__ void __launch_bounds__(HK_APPLY_MAXT, 1) k_local_apply(
     T acc[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) acc[i] = (T)0;
-    bool okl = true;
-    for (int row0 = 0; row0 < b; row0 += rc) {
-      int k = ks;
-      bool ok = mbar_wait_or_fail(&full[k], kph, &sh_fail);
-      if (++ks == K) ks = 0, kph ^= 1u;
-      if (!ok) {
-        if (atomicExch(&sh_fail, 1) == 0) dev_fail(st, HK_TIMEOUT, s, rs);
-        okl = false;
-        continue;
+    bool okl = !dead;
+    if (!dead)
+      for (int row0 = 0; row0 < b; row0 += rc) {
+        int kk = ks;
+        bool ok = mbar_wait_or_fail(&myfull[kk], kph, &sh_fail);
+        if (++ks == K) ks = 0, kph ^= 1u;
+        if (!ok) {
+          if (atomicExch(&sh_fail, 1) == 0) dev_fail(st, HK_TIMEOUT, s, k);
+          okl = false;
+          break;
+        }
+        const T* buf = reinterpret_cast<const T*>(myring + (long long)kk * stage_bytes);
+        if (q >= row0 && q < b && q < row0 + rc) row_chunk_dot<T, R>(buf + (long long)(q - row0) * ld, xin, v0, v1, acc);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&myempty[kk]);
       }
-      const T* buf = reinterpret_cast<const T*>(smem_raw + (long long)k * stage_bytes);
-      if (q >= row0 && q < b && q < row0 + rc) row_chunk_dot<T, R>(buf + (long long)(q - row0) * ld, xin, v0, v1, acc);
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[k]);
-    }
 #pragma unroll
     for (int i = 0; i < R; ++i)
       for (int o = G >> 1; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
     bool own = q < b && gl == 0;
-    if (fwd) {
-      // y_j = [-W_j | S_j^{-1}] [y_{j-1}; r_j]: every read of r_j ends before y_j overwrites it
-      if (group_any(!okl, WG, bar_id)) return;
-      if (own) stv<T, R>(xg + (long long)(ls + q) * R, acc);
-      group_sync(WG, bar_id);
+    if (assign) {
+      // first sweep and middle: every read of r_j ends before the result overwrites it
+      dead = group_any(!okl, WG, hid) != 0;
+      if (!dead && own) stv<T, R>(xg + (long long)(ls + q) * R, acc);
+      group_sync(WG, hid);
     } else {
-      // x_j = y_j - G_j x_{j+1}
+      // second sweep: x_j = (first-sweep value) - coupling product x_neighbour
       if (okl && own) {
         T y[R];
         ldv<T, R>(y, xg + (long long)(ls + q) * R);
@@ -572,10 +660,12 @@ __global__ void __launch_bounds__(HK_APPLY_MAXT, 1) k_local_apply(
         for (int i = 0; i < R; ++i) y[i] -= acc[i];
         stv<T, R>(xg + (long long)(ls + q) * R, y);
       }
-      if (group_any(!okl, WG, bar_id)) return;
+      dead = group_any(!okl, WG, hid) != 0;
     }
   }
-  for (int e = gt; e < nI * R; e += nthr) {
+  dead = group_any(dead, 2 * WG, jid) != 0;  // both halves done: x complete
+  if (dead) return;
+  for (int e = h * 32 * WG + gt; e < nI * R; e += 2 * nthr) {
     int a = e / R, i = e % R, rr = g * R + i;
     if (rr < nr && (active == nullptr || active[8 * (r_base + rr)]))
       ybuf[(long long)(r_base + rr) * I_total + off + a] = xg[e];
@@ -798,19 +888,19 @@ static ApplyShape apply_shape(hk_handle* h, int s) {
   constexpr int R = NR < 4 ? NR : 4, WS = NR / R;
   ApplyShape a;
   a.WG = apply_wg(h);
-  a.threads = 32 * (WS * a.WG + 1);
-  size_t vec = 64 * (size_t)h->max_L + 4 * (size_t)((h->max_dof + 7) & ~3) +
+  a.threads = 32 * (WS * 2 * a.WG + 2);
+  size_t vec = 80 * (size_t)h->max_L + 4 * (size_t)((h->max_dof + 7) & ~3) +
                sizeof(T) * (size_t)NR * ((size_t)h->max_dof + 4);
   size_t stage = (size_t)h->pack_stage;
   if (!h->n_sm) cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->dev);
   long long ctas = (long long)h->n_sub * ((s + NR - 1) / NR);
   // one wave: the whole shared memory for a deep ring; more: half of it, so two CTAs share an SM
   size_t budget = ctas <= h->n_sm ? 220 * 1024 : 112 * 1024;
-  int K = HK_APPLY_MAXK;
-  while (K > 4 && K * stage + vec > budget) --K;
-  while (K > 2 && K * stage + vec > 220 * 1024) --K;
+  int K = HK_APPLY_MAXK;  // stages per ring (two rings)
+  while (K > 4 && 2 * K * stage + vec > budget) --K;
+  while (K > 2 && 2 * K * stage + vec > 220 * 1024) --K;
   a.K = K;
-  a.shm = K * stage + vec;
+  a.shm = 2 * K * stage + vec;
   return a;
 }
 
@@ -839,12 +929,12 @@ static hk_status apply_t(hk_handle* h, int s, const double* v, double* z, const 
   const T* Einv = sizeof(T) == 4 ? reinterpret_cast<const T*>(h->d_Einv32) : reinterpret_cast<const T*>(h->d_Einv64);
   int do_local = h->p.levels != HK_COARSE_ONLY;
   int do_coarse = h->p.levels != HK_ONE_LEVEL && h->n0 > 0;
-  size_t budget = 220 * 1024 - 2 * (size_t)h->pack_stage;
+  size_t budget = 220 * 1024 - 4 * (size_t)h->pack_stage;
   int nr = 16;
-  budget -= 64 * (size_t)h->max_L + 4 * (size_t)((h->max_dof + 7) & ~3);
+  budget -= 80 * (size_t)h->max_L + 4 * (size_t)((h->max_dof + 7) & ~3);
   int wg = apply_wg(h);
   while (nr > 1 && (nr > s || sizeof(T) * ((size_t)h->max_dof + 4) * nr > budget ||
-                    32 * ((nr / std::min(nr, 4)) * wg + 1) > HK_APPLY_MAXT))
+                    32 * ((nr / std::min(nr, 4)) * 2 * wg + 2) > HK_APPLY_MAXT))
     nr >>= 1;
   auto tuned = h->nr_tuned.find(s);
   if (tuned != h->nr_tuned.end() && tuned->second <= nr) nr = tuned->second;
@@ -1098,17 +1188,24 @@ hk_status phase_local_factors_begin(hk_handle* h) {
   // level records for the apply, in the arithmetic type of the precision form
   size_t esz = h->p.precision == HK_FP32_PRECOND ? 4 : 8;
   std::vector<long long> tab(4 * (h->I_total + ns), 0);
+  std::vector<long long> lvfo(h->I_total + ns, 0);  // per level: offset of its factor blocks
   long long cur = 0, stage = 16;
   for (int s = 0; s < ns; ++s) {
     const Sub& u = h->subs[s];
     const int* lp = &lev[u.lev_off];
+    int M = twist_mid(u.L);
+    long long fcur = u.f_off;
     for (int j = 0; j < u.L; ++j) {
       long long b = lp[j + 1] - lp[j], bn = j + 1 < u.L ? lp[j + 2] - lp[j + 1] : 0, c = nc[u.lev_off + j];
       long long bp = j > 0 ? lp[j] - lp[j - 1] : 0;
-      long long rowf = pad4(bp + b) * esz, rowb = pad4(bn) * esz;  // multiples of 16 bytes
+      lvfo[u.lev_off + j] = fcur;
+      fcur += pad4(b * b) + pad4(b * coupling_cols(lp, u.L, j));
+      long long lb = (j > 0 && j <= M) ? bp : 0, rb = (j < u.L - 1 && j >= M) ? bn : 0;
+      long long cb = j < M ? bn : j > M ? bp : 0;
+      long long rowf = pad4(lb + b + rb) * esz, rowb = pad4(cb) * esz;  // multiples of 16 bytes
       long long fb = b * rowf, bb = b * rowb;
       long long rcf = std::max(1LL, std::min(b, HK_CHUNK_BYTES / rowf));
-      long long rcb = bn > 0 ? std::max(1LL, std::min(b, HK_CHUNK_BYTES / rowb)) : 1;
+      long long rcb = cb > 0 ? std::max(1LL, std::min(b, HK_CHUNK_BYTES / rowb)) : 1;
       (void)c;
       long long* e = &tab[4 * (size_t)(u.lev_off + j)];
       e[0] = cur;
@@ -1124,8 +1221,10 @@ hk_status phase_local_factors_begin(hk_handle* h) {
   h->pack_stage = stage;
   HK_TRY(dalloc(h, &h->d_F64, fo));
   HK_TRY(dalloc(h, &h->d_lvtab, tab.size()));
+  HK_TRY(dalloc(h, &h->d_lvfo, lvfo.size()));
   HK_TRY(dalloc(h, &h->d_pack, cur));
   HK_CUDA(cudaMemcpyAsync(h->d_lvtab, tab.data(), sizeof(long long) * tab.size(), cudaMemcpyHostToDevice, st));
+  HK_CUDA(cudaMemcpyAsync(h->d_lvfo, lvfo.data(), sizeof(long long) * lvfo.size(), cudaMemcpyHostToDevice, st));
   size_t shm = sizeof(double) * (size_t)h->max_level * h->max_level;
   int s_in_smem = shm <= 200 * 1024;
   if (!s_in_smem) shm = 0;
@@ -1139,13 +1238,13 @@ hk_status phase_local_factors_begin(hk_handle* h) {
   HK_CUDA(cudaStreamWaitEvent(h->aux_stream, h->ev_lf, 0));
   cudaStream_t ax = h->aux_stream;
   k_block_lu<<<ns, 256, shm, ax>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
-                                   h->d_lvalB, h->d_F64, s_in_smem, h->d_status); HK_COUNT_LAUNCH();
+                                   h->d_lvalB, h->d_lvfo, h->d_F64, s_in_smem, h->d_status); HK_COUNT_LAUNCH();
   if (esz == 4)
     k_pack_levels<float><<<ns, 256, 0, ax>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI,
-                                             h->d_lcol, h->d_lvalB, h->d_F64, h->d_lvtab, h->d_pack);
+                                             h->d_lcol, h->d_lvalB, h->d_F64, h->d_lvfo, h->d_lvtab, h->d_pack);
   else
     k_pack_levels<double><<<ns, 256, 0, ax>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI,
-                                              h->d_lcol, h->d_lvalB, h->d_F64, h->d_lvtab, h->d_pack);
+                                              h->d_lcol, h->d_lvalB, h->d_F64, h->d_lvfo, h->d_lvtab, h->d_pack);
   HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   HK_CUDA(cudaEventRecord(h->ev_lf, ax));
@@ -1161,6 +1260,8 @@ hk_status phase_local_factors_end(hk_handle* h) {
   HK_TRY(check_device_status(h, "local factors"));
   dfree(h, h->d_F64);
   h->d_F64 = nullptr;
+  dfree(h, h->d_lvfo);
+  h->d_lvfo = nullptr;
   return HK_OK;
 }
 
