@@ -15,8 +15,8 @@
 
 static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
-#define RED_BLOCKS 304
-#define RED_THREADS 256
+#define RED_BLOCKS 152
+#define RED_THREADS 512
 
 // state words per rhs
 enum { ST_ACTIVE = 0, ST_DONE = 1, ST_ITERS = 2, ST_JD = 3, ST_CONV = 4 };
@@ -34,6 +34,79 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
   __syncthreads();
   if (amlast) __threadfence();
   return amlast;
+}
+
+// New Hessenberg column j of rhs r (h1 + h2 above the diagonal, hn below), the previous
+// rotations applied to it, the new rotation, the residual estimate and the stopping decision.
+// Called by every thread of one CTA: the column and the previous rotations are first staged in
+// shared memory (sc, 3 (m + 1) doubles), then one thread runs the chain of rotations, the
+// rotated entry carried from one rotation to the next in a register.
+__device__ void givens_column(int r, int j, int m, double hn, int* state, double* rstate, const double* hcoef,
+                              double* H, double* cs, double* sn, double* g, double* hist, int max_iters,
+                              double tol, double* sc) {
+  const double* h1 = hcoef + (long long)r * 2 * (m + 1);
+  const double* h2 = h1 + (m + 1);
+  double* csr = cs + (long long)r * m;
+  double* snr = sn + (long long)r * m;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) sc[i] = h1[i] + h2[i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    sc[(m + 1) + i] = csr[i];
+    sc[2 * (m + 1) + i] = snr[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double* Hr = H + (long long)r * (m + 1) * m;  // H[i][jj] at i * m + jj
+    double* gr = g + (long long)r * (m + 1);
+    const double* c_ = sc + (m + 1);
+    const double* s_ = sc + 2 * (m + 1);
+    double cur = sc[0];
+    for (int i = 0; i < j; ++i) {
+      double a = cur, b = sc[i + 1];
+      Hr[i * m + j] = c_[i] * a + s_[i] * b;
+      cur = -s_[i] * a + c_[i] * b;
+    }
+    double a = cur, b = hn;
+    double den = hypot(a, b);
+    csr[j] = a / den;
+    snr[j] = b / den;
+    Hr[j * m + j] = den;
+    Hr[(j + 1) * m + j] = 0.0;
+    gr[j + 1] = -snr[j] * gr[j];
+    gr[j] = csr[j] * gr[j];
+    int it = ++state[8 * r + ST_ITERS];
+    double nf = rstate[8 * r + RS_NF];
+    double est = fabs(gr[j + 1]);
+    rstate[8 * r + RS_EST] = est;
+    if (hist && it <= max_iters) hist[(long long)r * max_iters + it - 1] = est / nf;
+    state[8 * r + ST_JD] = j + 1;
+    bool stop = est <= tol * nf || it >= max_iters || hn == 0.0 || j + 1 == m;
+    if (stop) state[8 * r + ST_ACTIVE] = 0;
+  }
+  __syncthreads();
+}
+
+// out[i] = sum over CTAs b (lanes over b in order, then the shuffle tree) of
+// part[(b * s + r) * (m + 2) + i] for i < nc: a warp per value, four values of a warp in flight
+// together.
+#define RED_VPW 4
+__device__ __forceinline__ void reduce_parts(const double* part, int s, int r, int m, int nc, double* out) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i0 = warp; i0 < nc; i0 += nw * RED_VPW) {
+    double acc[RED_VPW];
+#pragma unroll
+    for (int u = 0; u < RED_VPW; ++u) acc[u] = 0;
+    for (int b = lane; b < gridDim.x; b += 32) {
+      const double* pb = part + ((long long)b * s + r) * (m + 2);
+#pragma unroll
+      for (int u = 0; u < RED_VPW; ++u)
+        if (i0 + u * nw < nc) acc[u] += pb[i0 + u * nw];
+    }
+#pragma unroll
+    for (int u = 0; u < RED_VPW; ++u) {
+      double a = warp_sum(acc[u]);
+      if (lane == 0 && i0 + u * nw < nc) out[i0 + u * nw] = a;
+    }
+  }
 }
 
 __global__ void k_spmv(int n, int s, const int* __restrict__ rowptr, const int* __restrict__ col,
@@ -115,55 +188,22 @@ __global__ void k_gs(int n, int s, int m, int j, const int* __restrict__ jp, con
     if (tid == 0) pr[0] = acc;
   }
   if (!last_block(counter + 8 + r)) return;
-  // final reduction: one warp per value, lanes over CTAs in a fixed order
-  for (int i = warp; i < nc; i += nw) {
-    double acc = 0;
-    for (int b = lane; b < gridDim.x; b += 32) acc += part[((long long)b * s + r) * (m + 2) + i];
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      if (MODE == 0) hcoef[(long long)r * 2 * (m + 1) + i] = acc;
-      else if (MODE == 1) hcoef[(long long)r * 2 * (m + 1) + (m + 1) + i] = acc;
-      else {
-        double hn = sqrt(acc);
-        rstate[8 * r + RS_HNEXT] = hn;
-        rstate[8 * r + RS_HINV] = hn > 0.0 ? 1.0 / hn : 0.0;  // once here, not per entry in k_normalize
-      }
-    }
+  // final reduction in the fixed CTA order
+  __shared__ double fin[HK_MAXRESTART + 1];
+  reduce_parts(part, s, r, m, nc, fin);
+  __syncthreads();
+  for (int i = tid; i < nc; i += blockDim.x) {
+    if (MODE == 0) hcoef[(long long)r * 2 * (m + 1) + i] = fin[i];
+    else if (MODE == 1) hcoef[(long long)r * 2 * (m + 1) + (m + 1) + i] = fin[i];
   }
   if (MODE == 2) {
-    __syncthreads();
+    __shared__ double gsc[3 * (HK_MAXRESTART + 1)];
+    double hn = sqrt(fin[0]);
     if (tid == 0) {
-      double* Hr = H + (long long)r * (m + 1) * m;  // H[i][jj] at i * m + jj
-      const double* h1 = hcoef + (long long)r * 2 * (m + 1);
-      const double* h2 = h1 + (m + 1);
-      double* csr = cs + (long long)r * m;
-      double* snr = sn + (long long)r * m;
-      double* gr = g + (long long)r * (m + 1);
-      for (int i = 0; i <= j; ++i) Hr[i * m + j] = h1[i] + h2[i];
-      double hn = rstate[8 * r + RS_HNEXT];
-      Hr[(j + 1) * m + j] = hn;
-      for (int i = 0; i < j; ++i) {
-        double a = Hr[i * m + j], b = Hr[(i + 1) * m + j];
-        Hr[i * m + j] = csr[i] * a + snr[i] * b;
-        Hr[(i + 1) * m + j] = -snr[i] * a + csr[i] * b;
-      }
-      double a = Hr[j * m + j], b = Hr[(j + 1) * m + j];
-      double den = hypot(a, b);
-      csr[j] = a / den;
-      snr[j] = b / den;
-      Hr[j * m + j] = den;
-      Hr[(j + 1) * m + j] = 0.0;
-      gr[j + 1] = -snr[j] * gr[j];
-      gr[j] = csr[j] * gr[j];
-      int it = ++state[8 * r + ST_ITERS];
-      double nf = rstate[8 * r + RS_NF];
-      double est = fabs(gr[j + 1]);
-      rstate[8 * r + RS_EST] = est;
-      if (hist && it <= max_iters) hist[(long long)r * max_iters + it - 1] = est / nf;
-      state[8 * r + ST_JD] = j + 1;
-      bool stop = est <= tol * nf || it >= max_iters || hn == 0.0 || j + 1 == m;
-      if (stop) state[8 * r + ST_ACTIVE] = 0;
+      rstate[8 * r + RS_HNEXT] = hn;
+      rstate[8 * r + RS_HINV] = hn > 0.0 ? 1.0 / hn : 0.0;  // once here, not per entry in k_normalize
     }
+    givens_column(r, j, m, hn, state, rstate, hcoef, H, cs, sn, g, hist, max_iters, tol, gsc);
   }
   __syncthreads();
   if (tid == 0) counter[8 + r] = 0u;
@@ -201,18 +241,6 @@ __device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, Dev
     __threadfence();
   }
   __syncthreads();
-}
-
-// sum over CTAs b (lanes over b, then the shuffle tree) of part[(b * s + r) * (m + 2) + i], for
-// i < nc, into out[i]: a warp per value, the order of k_gs's final reduction.
-__device__ __forceinline__ void reduce_parts(const double* part, int s, int r, int m, int nc, double* out) {
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = warp; i < nc; i += nw) {
-    double acc = 0;
-    for (int b = lane; b < gridDim.x; b += 32) acc += part[((long long)b * s + r) * (m + 2) + i];
-    acc = warp_sum(acc);
-    if (lane == 0) out[i] = acc;
-  }
 }
 
 __global__ void __launch_bounds__(RED_THREADS) k_arnoldi_coop(
@@ -298,38 +326,14 @@ __global__ void __launch_bounds__(RED_THREADS) k_arnoldi_coop(
     const double* wr = w + (long long)r * n;
     double* vn = V + ((long long)(j + 1) * s + r) * n;
     for (int l = l0 + tid; l < l1; l += blockDim.x) vn[l] = wr[l] * hinv;
-    if (blockIdx.x == 0 && tid == 0) {
-      rstate[8 * r + RS_HNEXT] = hn;
-      rstate[8 * r + RS_HINV] = hinv;
-      double* Hr = H + (long long)r * (m + 1) * m;
-      const double* h1 = hcoef + (long long)r * 2 * (m + 1);
-      const double* h2 = h1 + (m + 1);
-      double* csr = cs + (long long)r * m;
-      double* snr = sn + (long long)r * m;
-      double* gr = g + (long long)r * (m + 1);
-      for (int i = 0; i <= j; ++i) Hr[i * m + j] = h1[i] + h2[i];
-      Hr[(j + 1) * m + j] = hn;
-      for (int i = 0; i < j; ++i) {
-        double a = Hr[i * m + j], b = Hr[(i + 1) * m + j];
-        Hr[i * m + j] = csr[i] * a + snr[i] * b;
-        Hr[(i + 1) * m + j] = -snr[i] * a + csr[i] * b;
+    if (blockIdx.x == 0) {
+      if (tid == 0) {
+        rstate[8 * r + RS_HNEXT] = hn;
+        rstate[8 * r + RS_HINV] = hinv;
       }
-      double a = Hr[j * m + j], b = Hr[(j + 1) * m + j];
-      double den = hypot(a, b);
-      csr[j] = a / den;
-      snr[j] = b / den;
-      Hr[j * m + j] = den;
-      Hr[(j + 1) * m + j] = 0.0;
-      gr[j + 1] = -snr[j] * gr[j];
-      gr[j] = csr[j] * gr[j];
-      int it = ++state[8 * r + ST_ITERS];
-      double nf = rstate[8 * r + RS_NF];
-      double est = fabs(gr[j + 1]);
-      rstate[8 * r + RS_EST] = est;
-      if (hist && it <= max_iters) hist[(long long)r * max_iters + it - 1] = est / nf;
-      state[8 * r + ST_JD] = j + 1;
-      bool stop = est <= tol * nf || it >= max_iters || hn == 0.0 || j + 1 == m;
-      if (stop) state[8 * r + ST_ACTIVE] = 0;
+      // the staging area reuses hsh: every thread has read hsh[r][0] (hn) above
+      __syncthreads();
+      givens_column(r, j, m, hn, state, rstate, hcoef, H, cs, sn, g, hist, max_iters, tol, &hsh[0][0]);
     }
   }
 }
