@@ -203,8 +203,8 @@ hk_status hk_apply_precond(hk_handle* h, int n_rhs, const double* v, double* z);
  * 8 in the FP64 form, each part rounded up to 256 bytes) returns HK_UNSUPPORTED before any
  * launch.  The first call on a device looks the array's address up (call it before any stream
  * capture).  All calls share the array: calls that overlap on the GPU race.  Ordered on the
- * handle's stream (the coarse part runs on the handle's auxiliary stream, forked from and
- * joined back into it); calls no cudaMalloc/cudaFree or allocating library routine. */
+ * handle's stream (the coarse part runs on a second, high-priority stream of the handle, forked
+ * from and joined back into it); calls no cudaMalloc/cudaFree or allocating library routine. */
 hk_status hk_apply_precond_noalloc(hk_handle* h, int n_rhs, const double* v_dev, double* z_dev);
 
 /* y = B x for n_rhs host vectors. */

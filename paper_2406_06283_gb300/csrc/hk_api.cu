@@ -109,6 +109,11 @@ static void destroy_all(hk_handle* h) {
   }
   if (h->ev_lf) cudaEventDestroy(h->ev_lf);
   h->ev_lf = nullptr;
+  if (h->co_stream) {
+    cudaStreamSynchronize(h->co_stream);
+    cudaStreamDestroy(h->co_stream);
+    h->co_stream = nullptr;
+  }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   h->ev_fork = h->ev_join = nullptr;

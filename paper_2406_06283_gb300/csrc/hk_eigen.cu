@@ -1181,6 +1181,19 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   HK_CUDA(up(d_voff, voff.data(), 4 * ns));
   HK_CUDA(up(d_bw, bw.data(), 4 * ns));
   HK_CUDA(up(d_o_off, o_off.data(), 4 * ns));
+  // The banded Cholesky of D_II needs only D_k and the band widths: it runs on the handle's second
+  // stream beside the Gamma-block, ovdof and Gamma-elimination kernels (disjoint workspace regions)
+  // and joins before the standard form.
+  bool side = h->co_stream && h->ev_fork && h->ev_join;
+  if (side) {
+    HK_CUDA(cudaEventRecord(h->ev_fork, st));
+    HK_CUDA(cudaStreamWaitEvent(h->co_stream, h->ev_fork, 0));
+    k_dchol<<<ns, 512, 0, h->co_stream>>>(h->d_sub_info, h->d_sub_off, d_bw, h->d_lrow, h->d_lcntI, h->d_lcol,
+                                          h->d_lvalD, d_L, d_L32, d_ws, d_ws32, h->d_status);
+    HK_COUNT_LAUNCH();
+    HK_LAUNCH_CHECK();
+    HK_CUDA(cudaEventRecord(h->ev_join, h->co_stream));
+  }
 
   // ---- B^N on Gamma x Gamma, then the ovdof structure (before the Cholesky of BG overwrites it)
   k_gamma_block<<<ns, 128, 0, st>>>(h->dim, h->n_elems, h->d_xyz, h->d_elems, h->d_coeff, h->k * h->k,
@@ -1225,7 +1238,6 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
                               h->d_lvalB, d_W, d_Gw, d_Rw, d_ring, d_ws, h->d_status);
   HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
-  HK_TRY(check_device_status(h, "eigen: Gamma elimination"));
   int maxbw = 0;
   for (int s = 0; s < ns; ++s) maxbw = std::max(maxbw, bw[s]);
   size_t sf_shm = sizeof(float) * (size_t)(maxbw + 1) * (HK_SF_TILE + HK_SF_CHUNK);
@@ -1233,11 +1245,15 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
     hk_set_error("local band width %d too large for the standard-form kernels", maxbw);
     return HK_UNSUPPORTED;
   }
-  k_dchol<<<ns, 512, 0, st>>>(h->d_sub_info, h->d_sub_off, d_bw, h->d_lrow, h->d_lcntI, h->d_lcol, h->d_lvalD, d_L,
-                              d_L32, d_ws, d_ws32, h->d_status);
-  HK_COUNT_LAUNCH();
-  HK_LAUNCH_CHECK();
-  HK_TRY(check_device_status(h, "eigen: Cholesky of D_II"));
+  if (side) {
+    HK_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
+  } else {
+    k_dchol<<<ns, 512, 0, st>>>(h->d_sub_info, h->d_sub_off, d_bw, h->d_lrow, h->d_lcntI, h->d_lcol, h->d_lvalD,
+                                d_L, d_L32, d_ws, d_ws32, h->d_status);
+    HK_COUNT_LAUNCH();
+    HK_LAUNCH_CHECK();
+  }
+  HK_TRY(check_device_status(h, "eigen: Gamma elimination and Cholesky of D_II"));
   dim3 sfgrid(ns, (maxn + HK_SF_TILE - 1) / HK_SF_TILE);
   HK_TRY(hk_allow_smem(k_sf_solve1));
   HK_TRY(hk_allow_smem(k_sf_solve2));

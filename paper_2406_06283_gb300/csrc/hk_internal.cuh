@@ -191,6 +191,7 @@ struct hk_handle {
   cudaStream_t aux_stream = nullptr;  // setup: local factors overlapping the eigenproblems
   cudaEvent_t ev_lf = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // apply: coarse path beside the local sweeps
+  cudaStream_t co_stream = nullptr;                    // apply: the coarse path's stream (high priority)
   bool lf_pending = false;
   int* d_ctl = nullptr;         // [0] inner step j, [1] cycles run, [2] inner steps run
   const int* g_jp = nullptr;    // while an inner step is captured: the device word holding j

@@ -943,13 +943,13 @@ static hk_status apply_t(hk_handle* h, int s, const double* v, double* z, const 
   // the handle's stream (in a captured solve graph these become parallel branches).
   int cr = s >= 8 ? 8 : s >= 4 ? 4 : s >= 2 ? 2 : 1;
   T* zc = ybuf + (size_t)s * h->I_total;  // coarse prolongation per subdomain row
-  bool fork = do_local && do_coarse && h->aux_stream && h->ev_fork && h->ev_join;
+  bool fork = do_local && do_coarse && h->co_stream && h->ev_fork && h->ev_join;
   cudaStream_t main_st = h->stream;
   if (do_coarse) {
     if (fork) {
       HK_CUDA(cudaEventRecord(h->ev_fork, main_st));
-      HK_CUDA(cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0));
-      h->stream = h->aux_stream;
+      HK_CUDA(cudaStreamWaitEvent(h->co_stream, h->ev_fork, 0));
+      h->stream = h->co_stream;
     }
     int rb = cr;
     dim3 rg(h->n_sub, (s + rb - 1) / rb);
@@ -999,7 +999,7 @@ static hk_status apply_t(hk_handle* h, int s, const double* v, double* z, const 
     HK_COUNT_LAUNCH();
     HK_COUNT_LAUNCH();
     h->stream = main_st;
-    if (fork) HK_CUDA(cudaEventRecord(h->ev_join, h->aux_stream));
+    if (fork) HK_CUDA(cudaEventRecord(h->ev_join, h->co_stream));
     if (!cs_ok) {
       hk_set_error("coarse space too large for the coarse solve (n0 = %d)", h->n0);
       return HK_UNSUPPORTED;
@@ -1232,6 +1232,12 @@ hk_status phase_local_factors_begin(hk_handle* h) {
   // the auxiliary stream starts after everything above (allocations, memsets, table upload)
   if (!h->aux_stream) HK_CUDA(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
   if (!h->ev_lf) HK_CUDA(cudaEventCreateWithFlags(&h->ev_lf, cudaEventDisableTiming));
+  if (!h->co_stream) {
+    // the apply's coarse branch: short kernels that should not queue behind the local sweeps' CTAs
+    int lo = 0, hi = 0;
+    HK_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    HK_CUDA(cudaStreamCreateWithPriority(&h->co_stream, cudaStreamNonBlocking, hi));
+  }
   if (!h->ev_fork) HK_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   if (!h->ev_join) HK_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   HK_CUDA(cudaEventRecord(h->ev_lf, st));

@@ -160,6 +160,28 @@ def test_preconditioner_apply_fp64(case):
     assert _rel(z, want) <= 1e-10
 
 
+@pytest.mark.parametrize("shape", [(12, 12, 1), (12, 6, 1), (16, 8, 2)])
+def test_apply_parity_small_subdomains(shape):
+    """Subdomains of 1 to 23 dofs, so one to a few level sets each: the degenerate shapes of the
+    twisted block factorisation (middle level only; middle and bottom; both halves short).  The
+    FP64 form against the oracle's preconditioner at 1e-10; the FP32 form (factors, Z and E^{-1}
+    stored and applied in FP32, unit roundoff 6e-8, condition numbers of these local and coarse
+    matrices below 1e3) within 1e-4 of it."""
+    cells, parts, ov = shape
+    p = W.small_problem(cells=cells, parts=parts, k=3.0, overlap=ov, checker=2)
+    o = OS.setup_problem(p)
+    v = np.random.default_rng(4).standard_normal((2, o.n))
+    want = np.stack([o.precond.apply(vi) for vi in v])
+    h = hk.setup_problem(p, precision=hk.HK_FP64)
+    z = hk.hk_apply_precond(h, v)
+    hk.hk_destroy(h)
+    assert _rel(z, want) <= 1e-10
+    h = hk.setup_problem(p, precision=hk.HK_FP32_PRECOND)
+    z32 = hk.hk_apply_precond(h, v)
+    hk.hk_destroy(h)
+    assert _rel(z32, want) <= 1e-4
+
+
 @pytest.mark.parametrize("levels", [hk.HK_ONE_LEVEL, hk.HK_COARSE_ONLY])
 @pytest.mark.parametrize("weighting", [hk.HK_AS, hk.HK_RAS_POU])
 def test_preconditioner_variants(levels, weighting):
