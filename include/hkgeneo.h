@@ -124,10 +124,12 @@ typedef struct {
   int nnz;                     /* nonzeros of B */
   int precision, levels;
   size_t bytes_resident;       /* device bytes held by the handle */
-  long long factor_elems;      /* entries of all local factor blocks S_j^{-1}, G_j (with 4-entry padding) */
+  long long factor_elems;      /* entries of all local factor blocks (FP64, setup only): the inverse of each
+                                  level's Schur complement and its coupling product of the twisted
+                                  block factorisation, each padded to 4 entries */
   long long dof_total;         /* sum_i |dof(Omega_i)| */
   long long coarse_elems;      /* entries of all Z_i, sum_i |dof(Omega_i)| m_i */
-  long long lower_nnz;         /* couplings L_j read by the forward sweeps, sum over subdomains */
+  long long lower_nnz;         /* couplings L_j between consecutive level sets, sum over subdomains */
   double setup_ms[8];          /* phases: assembly, decomposition, local factors, eigen, coarse,
                                   total; [6] the Householder tridiagonalisation kernel alone; [7] 0 */
   size_t bytes_peak;           /* most device bytes the handle held at once (setup temporaries included) */
