@@ -238,25 +238,6 @@ __host__ __device__ __forceinline__ int lv_rcb(long long e3) { return (int)((e3 
 __host__ __device__ __forceinline__ int lv_b(long long e3) { return (int)((e3 >> 20) & 0xFFFFF); }
 __host__ __device__ __forceinline__ int lv_start(long long e3) { return (int)(e3 >> 40); }
 
-// Lower couplings per level (row in level j, column in level j-1).
-__global__ void k_level_counts(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
-                               const int* __restrict__ levptr, const int* __restrict__ lrow,
-                               const int* __restrict__ lcntI, const int* __restrict__ lcol, int* nc_out) {
-  int s = blockIdx.x;
-  const int* si = sub_info + 8 * s;
-  int L = si[2], off = si[3], loff = si[5];
-  long long coff = sub_off[3 * s + 1];
-  const int* lp = levptr + loff;
-  const int* lr = lrow + off + s;
-  for (int j = threadIdx.x; j < L; j += blockDim.x) {
-    int c = 0;
-    if (j > 0)
-      for (int a = lp[j]; a < lp[j + 1]; ++a)
-        for (int q = 0; q < lcntI[off + a]; ++q) c += lcol[coff + lr[a] + q] < lp[j];
-    nc_out[loff + j] = c;
-  }
-}
-
 template <typename T>
 __global__ void k_pack_levels(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
                               const int* __restrict__ levptr, const int* __restrict__ lrow,
@@ -314,22 +295,28 @@ __global__ void k_pack_levels(const int* __restrict__ sub_info, const long long*
 }
 
 // One CTA per (subdomain, group of NR right-hand sides): gather r_i = v[dof(Omega_i)]
-// (R_i of Eq. 2.22), the forward and backward block sweeps of B_i^{-1}, and the local
-// solution written to ybuf.  T: float (FP32 form) or double.
+// (R_i of Eq. 2.22), the two half sweeps of the twisted factorisation of B_i^{-1} at once,
+// and the local solution written to ybuf.  T: float (FP32 form) or double.
 //
-// Warp roles.  The last warp is the producer: one lane streams the 2L-1 level records
-// into a ring of K shared-memory stages by 1-D TMA bulk copies, each stage guarded by a
-// "full" mbarrier (transaction bytes) and an "empty" mbarrier (one arrival per sweeping
-// warp), so up to K records are in flight while the sweeps run.  The other warps gather
-// together, then split into sweep groups: group g owns right-hand sides
-// g*R .. g*R+R-1 (R = min(NR, 4)) and has WG warps.  A level's rows are spread over the
-// group's threads, G lanes per row on contiguous 4-column chunks (G as large as keeps
-// every row in one pass), then a shuffle sum over the G lanes.  A level step is a few
-// dependent shared-memory loads and FMAs and one or two barriers of the group only.
+// Warp roles.  The last two warps are producers, one per record stream (top: first sweep
+// above the middle, the middle, second sweep above it; bottom: first and second sweep below
+// the middle): one lane streams its records, chunk by chunk, into a ring of K shared-memory
+// stages by 1-D TMA bulk copies, each stage guarded by a "full" mbarrier (transaction bytes)
+// and an "empty" mbarrier (one arrival per consuming warp), so up to K chunks per stream are in
+// flight while the sweeps run.  The other warps gather together, then split into
+// right-hand-side groups: group g owns right-hand sides g*R .. g*R+R-1 (R = min(NR, 4)) and
+// has two half groups of WG warps, one per stream.  A level's rows are spread over a half
+// group's threads, G lanes per row on contiguous 4-column chunks (G as large as keeps every
+// row in one pass), then a shuffle sum over the G lanes.  A level step is a few dependent
+// shared-memory loads and FMAs and one or two barriers of the half group; the two halves of a
+// group meet only around the middle level (the top half computes it once the bottom half's
+// first sweep is done, the bottom half's second sweep starts from it).
 // Shared vectors are level-row major within a group, x[(g * (nI + 4) + a) * R + i]; four
-// zero rows after each group's rows keep the padded last columns of a record finite.
-// Every wait is bounded; a wait that gives up reports HK_TIMEOUT, and the producer lets
-// the copies it has in flight land before the CTA exits.
+// zero rows after each group's rows keep the padded last columns of a record finite (padded
+// columns are zero, so the values they meet never matter).
+// Every wait is bounded; a wait that gives up reports HK_TIMEOUT, after which the warps keep
+// only their barriers (so no barrier is left waiting), and a producer lets the copies it has in
+// flight land before the CTA exits.
 #define HK_APPLY_MAXK 12
 #define HK_APPLY_MAXT 768  // threads of a CTA at most (24 warps)
 
@@ -1166,25 +1153,17 @@ hk_status phase_local_factors_begin(hk_handle* h) {
   h->f_total = fo;
   HK_TRY(upload_sub_info(h));
   if (h->p.levels == HK_COARSE_ONLY) return HK_OK;
-  int* d_nc = nullptr;
   {
     unsigned long long* d_cnt = nullptr;
     HK_TRY(dalloc(h, &d_cnt, 1));
-    HK_TRY(dalloc(h, &d_nc, h->I_total + ns));
     k_count_lower<<<ns, 128, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
                                       d_cnt); HK_COUNT_LAUNCH();
-    k_level_counts<<<ns, 128, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
-                                       d_nc); HK_COUNT_LAUNCH();
     unsigned long long c = 0;
     HK_CUDA(cudaMemcpyAsync(&c, d_cnt, sizeof(c), cudaMemcpyDeviceToHost, st));
     HK_CUDA(cudaStreamSynchronize(st));
     h->lower_nnz = (long long)c;
     dfree(h, d_cnt);
   }
-  std::vector<int> nc(h->I_total + ns);
-  HK_CUDA(cudaMemcpyAsync(nc.data(), d_nc, sizeof(int) * nc.size(), cudaMemcpyDeviceToHost, st));
-  HK_CUDA(cudaStreamSynchronize(st));
-  dfree(h, d_nc);
   // level records for the apply, in the arithmetic type of the precision form
   size_t esz = h->p.precision == HK_FP32_PRECOND ? 4 : 8;
   std::vector<long long> tab(4 * (h->I_total + ns), 0);
@@ -1196,7 +1175,7 @@ hk_status phase_local_factors_begin(hk_handle* h) {
     int M = twist_mid(u.L);
     long long fcur = u.f_off;
     for (int j = 0; j < u.L; ++j) {
-      long long b = lp[j + 1] - lp[j], bn = j + 1 < u.L ? lp[j + 2] - lp[j + 1] : 0, c = nc[u.lev_off + j];
+      long long b = lp[j + 1] - lp[j], bn = j + 1 < u.L ? lp[j + 2] - lp[j + 1] : 0;
       long long bp = j > 0 ? lp[j] - lp[j - 1] : 0;
       lvfo[u.lev_off + j] = fcur;
       fcur += pad4(b * b) + pad4(b * coupling_cols(lp, u.L, j));
@@ -1206,7 +1185,6 @@ hk_status phase_local_factors_begin(hk_handle* h) {
       long long fb = b * rowf, bb = b * rowb;
       long long rcf = std::max(1LL, std::min(b, HK_CHUNK_BYTES / rowf));
       long long rcb = cb > 0 ? std::max(1LL, std::min(b, HK_CHUNK_BYTES / rowb)) : 1;
-      (void)c;
       long long* e = &tab[4 * (size_t)(u.lev_off + j)];
       e[0] = cur;
       cur += fb;
