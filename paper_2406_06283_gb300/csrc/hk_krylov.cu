@@ -39,8 +39,11 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
 // New Hessenberg column j of rhs r (h1 + h2 above the diagonal, hn below), the previous
 // rotations applied to it, the new rotation, the residual estimate and the stopping decision.
 // Called by every thread of one CTA: the column and the previous rotations are first staged in
-// shared memory (sc, 3 (m + 1) doubles), then one thread runs the chain of rotations, the
-// rotated entry carried from one rotation to the next in a register.
+// shared memory (sc, 3 (m + 1) + 1 doubles).  Applying rotation i to the pair (x_i, b_{i+1}),
+// x_0 = b_0, gives H[i][j] = c_i x_i + s_i b_{i+1} and x_{i+1} = -s_i x_i + c_i b_{i+1}: an affine
+// recurrence x_{i+1} = alpha_i x_i + beta_i, so warp 0 composes the maps of consecutive rotations
+// with a shuffle scan (each lane a run of ceil(j / 32) rotations) instead of one chain of j
+// dependent FP64 steps; lane 0 then forms the new rotation from (x_j, hn).
 __device__ void givens_column(int r, int j, int m, double hn, int* state, double* rstate, const double* hcoef,
                               double* H, double* cs, double* sn, double* g, double* hist, int max_iters,
                               double tol, double* sc) {
@@ -53,34 +56,59 @@ __device__ void givens_column(int r, int j, int m, double hn, int* state, double
     sc[(m + 1) + i] = csr[i];
     sc[2 * (m + 1) + i] = snr[i];
   }
+  double* xj = sc + 3 * (m + 1);  // x_j, passed from the lane holding the last rotation to lane 0
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    int lane = threadIdx.x;
     double* Hr = H + (long long)r * (m + 1) * m;  // H[i][jj] at i * m + jj
-    double* gr = g + (long long)r * (m + 1);
     const double* c_ = sc + (m + 1);
     const double* s_ = sc + 2 * (m + 1);
-    double cur = sc[0];
-    for (int i = 0; i < j; ++i) {
-      double a = cur, b = sc[i + 1];
-      Hr[i * m + j] = c_[i] * a + s_[i] * b;
-      cur = -s_[i] * a + c_[i] * b;
+    double b0 = sc[0];
+    int E = (j + 31) / 32, i0 = lane * E, i1 = min(j, i0 + E);
+    // this lane's run of maps composed: x -> A x + B
+    double A = 1.0, B = 0.0;
+    for (int i = i0; i < i1; ++i) {
+      double al = -s_[i], be = c_[i] * sc[i + 1];
+      A = al * A;
+      B = al * B + be;
     }
-    double a = cur, b = hn;
-    double den = hypot(a, b);
-    csr[j] = a / den;
-    snr[j] = b / den;
-    Hr[j * m + j] = den;
-    Hr[(j + 1) * m + j] = 0.0;
-    gr[j + 1] = -snr[j] * gr[j];
-    gr[j] = csr[j] * gr[j];
-    int it = ++state[8 * r + ST_ITERS];
-    double nf = rstate[8 * r + RS_NF];
-    double est = fabs(gr[j + 1]);
-    rstate[8 * r + RS_EST] = est;
-    if (hist && it <= max_iters) hist[(long long)r * max_iters + it - 1] = est / nf;
-    state[8 * r + ST_JD] = j + 1;
-    bool stop = est <= tol * nf || it >= max_iters || hn == 0.0 || j + 1 == m;
-    if (stop) state[8 * r + ST_ACTIVE] = 0;
+    // inclusive scan over the lanes (earlier runs applied first), then the exclusive prefix
+    for (int d = 1; d < 32; d <<= 1) {
+      double Ao = __shfl_up_sync(0xffffffffu, A, d), Bo = __shfl_up_sync(0xffffffffu, B, d);
+      if (lane >= d) {
+        B = A * Bo + B;
+        A = A * Ao;
+      }
+    }
+    double Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
+    if (lane == 0) Ae = 1.0, Be = 0.0;
+    double x = Ae * b0 + Be;  // x_{i0}
+    for (int i = i0; i < i1; ++i) {
+      double b = sc[i + 1];
+      Hr[i * m + j] = c_[i] * x + s_[i] * b;
+      x = -s_[i] * x + c_[i] * b;
+    }
+    if (j == 0 ? lane == 0 : (i0 < j && i1 == j)) *xj = j == 0 ? b0 : x;
+    __syncwarp();
+    if (lane == 0) {
+      double* gr = g + (long long)r * (m + 1);
+      double a = *xj, b = hn;
+      double den = hypot(a, b);
+      csr[j] = a / den;
+      snr[j] = b / den;
+      Hr[j * m + j] = den;
+      Hr[(j + 1) * m + j] = 0.0;
+      gr[j + 1] = -snr[j] * gr[j];
+      gr[j] = csr[j] * gr[j];
+      int it = ++state[8 * r + ST_ITERS];
+      double nf = rstate[8 * r + RS_NF];
+      double est = fabs(gr[j + 1]);
+      rstate[8 * r + RS_EST] = est;
+      if (hist && it <= max_iters) hist[(long long)r * max_iters + it - 1] = est / nf;
+      state[8 * r + ST_JD] = j + 1;
+      bool stop = est <= tol * nf || it >= max_iters || hn == 0.0 || j + 1 == m;
+      if (stop) state[8 * r + ST_ACTIVE] = 0;
+    }
   }
   __syncthreads();
 }
@@ -197,7 +225,7 @@ __global__ void k_gs(int n, int s, int m, int j, const int* __restrict__ jp, con
     else if (MODE == 1) hcoef[(long long)r * 2 * (m + 1) + (m + 1) + i] = fin[i];
   }
   if (MODE == 2) {
-    __shared__ double gsc[3 * (HK_MAXRESTART + 1)];
+    __shared__ double gsc[3 * (HK_MAXRESTART + 1) + 1];
     double hn = sqrt(fin[0]);
     if (tid == 0) {
       rstate[8 * r + RS_HNEXT] = hn;
