@@ -138,8 +138,7 @@ struct hk_handle {
   // coarse space
   double* d_lam = nullptr;        // per subdomain kept eigenvalues (HK_MAXM each)
   double* d_Z64 = nullptr;        // z_total, per subdomain nI x m row-major
-  void* d_Zr = nullptr;           // Z in the apply's type, row-major (the pull-form prolongation)
-  void* d_Zt = nullptr;           // Z in the apply's type, per subdomain m x nI (the restriction)
+  void* d_Zt = nullptr;           // Z in the apply's type, per subdomain m x nI (restriction and prolongation)
   double* d_E = nullptr;          // n0 x n0
   double* d_Einv64 = nullptr;
   float* d_Einv32 = nullptr;

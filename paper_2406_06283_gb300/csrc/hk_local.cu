@@ -1097,10 +1097,11 @@ hk_status op_apply(hk_handle* h, int s, const double* v, double* z, const int* a
   return apply_t<double>(h, s, v, z, active, h->d_ybuf64, h->d_c64, h->d_cc64);
 }
 
-// Transposed (m x |dof|) copy of each Z_i in the apply's arithmetic type.
+// Transposed (m x |dof|) copy of each Z_i in the apply's arithmetic type (the restriction and
+// the prolongation both read it, coalesced over the dofs).
 template <typename T>
 __global__ void k_transpose_z(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
-                              const double* __restrict__ Z, T* Zt, T* Zr) {
+                              const double* __restrict__ Z, T* Zt) {
   int s = blockIdx.x;
   const int* si = sub_info + 8 * s;
   int nI = si[0], m = si[6];
@@ -1108,25 +1109,21 @@ __global__ void k_transpose_z(const int* __restrict__ sub_info, const long long*
   for (long long e = threadIdx.x; e < (long long)nI * m; e += blockDim.x) {
     int a = (int)(e / m), l = (int)(e % m);
     Zt[zo + (long long)l * nI + a] = (T)Z[zo + e];
-    if (Zr) Zr[zo + e] = (T)Z[zo + e];
   }
 }
 
 hk_status build_apply_z(hk_handle* h) {
   if (h->n0 == 0) return HK_OK;
   if (h->p.precision == HK_FP32_PRECOND) {
-    float *zt = nullptr, *zr = nullptr;
+    float* zt = nullptr;
     HK_TRY(dalloc(h, &zt, h->z_total));
-    HK_TRY(dalloc(h, &zr, h->z_total));
-    k_transpose_z<float><<<h->n_sub, 256, 0, h->stream>>>(h->d_sub_info, h->d_sub_off, h->d_Z64, zt, zr); HK_COUNT_LAUNCH();
+    k_transpose_z<float><<<h->n_sub, 256, 0, h->stream>>>(h->d_sub_info, h->d_sub_off, h->d_Z64, zt); HK_COUNT_LAUNCH();
     h->d_Zt = zt;
-    h->d_Zr = zr;
   } else {
     double* zt = nullptr;
     HK_TRY(dalloc(h, &zt, h->z_total));
-    k_transpose_z<double><<<h->n_sub, 256, 0, h->stream>>>(h->d_sub_info, h->d_sub_off, h->d_Z64, zt, nullptr); HK_COUNT_LAUNCH();
+    k_transpose_z<double><<<h->n_sub, 256, 0, h->stream>>>(h->d_sub_info, h->d_sub_off, h->d_Z64, zt); HK_COUNT_LAUNCH();
     h->d_Zt = zt;
-    h->d_Zr = h->d_Z64;
   }
   HK_LAUNCH_CHECK();
   return HK_OK;
