@@ -854,9 +854,10 @@ __global__ void k_scatter(int n, int s, const int* __restrict__ pull_ptr, const 
   }
 }
 
-// Launch shape of k_local_apply<T, NR> for this handle: warps per sweep group, ring depth,
-// threads and dynamic shared memory.  The ring gets as many stages (up to 16) as fit in
-// half an SM's shared memory, so that two CTAs can share an SM, and at least two.
+// Launch shape of k_local_apply<T, NR> for this handle: warps per half group, ring depth,
+// threads and dynamic shared memory.  Each of the two rings gets as many stages (up to
+// HK_APPLY_MAXK) as fit: in the whole of an SM's shared memory when the grid is a single
+// wave, in half of it otherwise (so that two CTAs can share an SM), and at least two.
 struct ApplyShape {
   int WG = 1, K = 0, threads = 0;
   size_t shm = 0;
