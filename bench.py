@@ -39,9 +39,36 @@ from paper_2406_06283_gb300 import workloads as W  # noqa: E402
 
 METRIC = "Helmholtz solves/s and p99 latency at 1e-8 residual; FP32-precond vs FP64 form"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# DRAM bytes (read + write) of one k_tridiag32 launch from an ncu capture of the same kernel, per workload
-# (profiles/k_tridiag32_h256_k50.md); absent until a capture of the current kernel exists.
-TRIDIAG_TRAFFIC = {"c2": 6741196032 + 27854091520}
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+CSRC = os.path.join(ROOT, "paper_2406_06283_gb300", "csrc")
+
+
+def source_digest(kernel: str) -> str | None:
+    """sha256 (first 16 hex digits) of the CUDA source file that defines `kernel`."""
+    import hashlib
+    for f in sorted(os.listdir(CSRC)):
+        if not f.endswith(".cu"):
+            continue
+        text = open(os.path.join(CSRC, f), "rb").read()
+        if (f"{kernel}(".encode() in text or f"{kernel}<".encode() in text) and b"__global__" in text:
+            return hashlib.sha256(text).hexdigest()[:16]
+    return None
+
+
+def measured_traffic(kernel: str, workload: str):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload`, from the ncu record in
+    profiles/dram_traffic.txt, or None when there is no record or the kernel's source file has
+    changed since the counters were taken."""
+    try:
+        lines = open(TRAFFIC_PATH).read().splitlines()
+    except OSError:
+        return None
+    dig = source_digest(kernel)
+    for ln in lines:
+        f = ln.split()
+        if len(f) >= 4 and not ln.startswith("#") and f[0] == kernel and f[1] == workload:
+            return int(f[3]) if f[2] == dig else None
+    return None
 
 
 def workload(name: str):
@@ -162,6 +189,78 @@ def oracle_step(p):
     return t1 - t0, t2 - t1, [x.iters for x in r]
 
 
+class OracleSampler:
+    """Bounded samples of one oracle setup + solve of a workload.  The oracle's cost separates into a
+    global part (assembly, decomposition, coarse matrix and its factorisation: timed once while the
+    sampler is prepared), a per-subdomain part (local pencil, eigenproblem and local LU factorisation
+    of Omega_i) and a per-iteration part (one FGMRES inner step at the solve's mean Krylov depth: one
+    preconditioner apply, one matvec and the modified Gram-Schmidt sweep).  A sample runs the
+    per-subdomain work of one subdomain (in turn) and one inner step; the time of a whole solve is
+    then  t_global + n_sub * t_subdomain + iterations * t_iteration."""
+
+    def __init__(self, p):
+        import scipy.linalg as sla
+
+        from oracle import decomposition as OD
+        from oracle import fem as OF
+        from oracle import geneo as OG
+        from oracle import solver as OS
+        self.p, self.OD, self.OF, self.OG, self.sla = p, OD, OF, OG, sla
+        t0 = time.perf_counter()
+        self.h = OS.setup_problem(p)
+        t1 = time.perf_counter()
+        self.f = OS.load_vector(p)[0]
+        r = OS.solve(self.h, self.f[None, :], p.tol)[0]
+        t2 = time.perf_counter()
+        self.iters = r.iters
+        self.setup_s, self.solve_s = t1 - t0, t2 - t1
+        m = p.mesh
+        # global part of the setup: everything but the per-subdomain eigen and LU work
+        g0 = time.perf_counter()
+        OF.helmholtz_matrices(m.xyz, m.elems, p.coeff, m.is_boundary, p.k)
+        OD.decompose(m.xyz, m.elems, m.is_boundary, p.elem_to_sub, p.n_sub, p.overlap)
+        E = self.h.precond.E
+        sla.lu_factor(E)
+        self.global_s = time.perf_counter() - g0
+        self.depth = max(1, min(p.restart, self.iters) // 2)
+        rng = np.random.default_rng(0)
+        self.V = np.linalg.qr(rng.standard_normal((self.h.n, self.depth + 1)))[0].T.copy()
+        self.k = 0
+        self.t_sub, self.t_it = [], []
+
+    def step(self):
+        p, h, m = self.p, self.h, self.p.mesh
+        i = self.k % p.n_sub
+        self.k += 1
+        t0 = time.perf_counter()
+        sd = h.subs[i]
+        BN, C, w = self.OG.local_pencil(m.xyz, m.elems, p.coeff, m.is_boundary, p.k, sd, h.mu)
+        self.OG.local_eigen(BN, C, w, p.tau)
+        Bi = h.B.tocsr()[sd.dof][:, sd.dof].toarray()
+        self.sla.lu_factor(Bi)
+        t1 = time.perf_counter()
+        z = h.precond.apply(self.V[self.depth])
+        wv = h.B @ z
+        for q in range(self.depth + 1):
+            wv = wv - float(np.dot(wv, self.V[q])) * self.V[q]
+        np.linalg.norm(wv)
+        t2 = time.perf_counter()
+        self.t_sub.append(t1 - t0)
+        self.t_it.append(t2 - t1)
+        return t2 - t0
+
+    def solve_seconds(self):
+        return self.global_s + self.p.n_sub * statistics.mean(self.t_sub) + self.iters * statistics.mean(self.t_it)
+
+    def describe(self):
+        return (f"{len(self.t_sub)} samples, each: one subdomain's local pencil + eigenproblem + LU "
+                f"({1e3 * statistics.mean(self.t_sub):.0f} ms) and one FGMRES inner step at Krylov depth "
+                f"{self.depth} ({1e3 * statistics.mean(self.t_it):.1f} ms); solve = global setup "
+                f"{self.global_s:.2f} s + {self.p.n_sub} subdomains + {self.iters} iterations (the oracle's "
+                f"count); one whole oracle setup + solve for comparison: {self.setup_s + self.solve_s:.1f} s; "
+                f"numpy/scipy, BLAS threads up to {os.cpu_count()}")
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -177,32 +276,32 @@ def run_reference(args, world, rank):
         return
     p = workload(args.workload)
     cores = os.cpu_count()
-    # each oracle step is a whole setup + solve (tens of seconds): at most two timed steps, no warm-up
-    steps = max(1, min(args.steps, 2))
-    times, iters = [], []
-    for _ in range(steps):
-        ts, tv, it = oracle_step(p)
-        times.append(ts + tv)
-        iters = it
-    total = sum(times)
-    value = steps * (1 if p.rhs is None else p.rhs.shape[0]) / total
+    smp = OracleSampler(p)
+    for _ in range(args.warmup):
+        smp.step()
+    smp.t_sub.clear()
+    smp.t_it.clear()
+    step_s = [smp.step() for _ in range(args.steps)]
+    s = 1 if p.rhs is None else p.rhs.shape[0]
+    value = s / smp.solve_seconds()
+    cb = {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": smp.describe()}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": steps, "warmup": 0, "ms_per_step": 1e3 * total / steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(p, args.workload, "fp64 (oracle)"),
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{steps} full setup+solve of the workload on numpy/scipy "
-                                       f"(BLAS threads up to {cores}); iterations {iters}"},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(step_s),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)", "config": workload_config(p, args.workload, args.precision),
+            "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(p, budget_s=40.0):
-    """The oracle as it stands on this host: one full setup + solve of the workload."""
-    ts, tv, it = oracle_step(p)
-    return {"value": 1.0 / (ts + tv), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"one full setup+solve of the workload (setup {ts:.1f} s, solve {tv:.1f} s, "
-                      f"{it[0]} iterations); numpy/scipy, BLAS threads up to {os.cpu_count()}"}
+def cpu_baseline(p, samples=12):
+    """The oracle as it stands on this host, timed on a bounded sample of the workload (OracleSampler)."""
+    smp = OracleSampler(p)
+    for _ in range(samples):
+        smp.step()
+    s = 1 if p.rhs is None else p.rhs.shape[0]
+    return {"value": s / smp.solve_seconds(), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": smp.describe()}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -355,7 +454,9 @@ def run_ours(args, world, rank, local):
     apply_ms = max(per["local_apply"], per.get("coarse_solve", 0.0)) + per["scatter"]
     apply_bytes = bytes_local + bytes_coarse + bytes_scatter
     roof_apply = {"bound": "hbm", "achieved": apply_bytes / (apply_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                  "frac": apply_bytes / (apply_ms * 1e-3) / 1e9 / hbm, "traffic": None,
+                  "frac": apply_bytes / (apply_ms * 1e-3) / 1e9 / hbm,
+                  "traffic": measured_traffic("k_local_apply", f"{args.workload}_{args.precision}"),
+                  "traffic_kernel": "k_local_apply (the sweeps; the coarse branch and scatter are not included)",
                   "kernels": "k_local_apply || (k_restrict -> k_coarse_solve -> k_prolong), then k_scatter",
                   "bytes_per_apply": apply_bytes, "rhs_per_apply": s, "ms_per_apply": apply_ms,
                   "peak_source": src}
@@ -365,15 +466,17 @@ def run_ours(args, world, rank, local):
     dom = max(tot, key=tot.get)
     sizes = [nI_list]
     if dom == "tridiag":
-        # Householder reduction in FP32 on the lower triangle: step k reads and writes the trailing
-        # triangle rows i > k, columns k+1..i once, 4 B * 2 * (n-k-1)(n-k)/2; summed over k this is
-        # 4 (n-1) n (n+1) / 3 bytes per subdomain of n = |dof(Omega_i)| unknowns.
-        b = sum(4.0 * (nI - 1) * nI * (nI + 1) / 3.0 for nI in sizes[0])
+        # Householder reduction in FP32 of the lower triangle of each subdomain's standard-form matrix
+        # (n = |dof(Omega_i)|): the least it must move is one read of that triangle, 4 n (n + 1) / 2
+        # bytes, and the diagonal and off-diagonal it returns, 8 n bytes.  (Its unblocked steps re-read
+        # the trailing triangle, mostly from L2; those re-reads are not counted.)
+        b = sum(4.0 * nI * (nI + 1) / 2.0 + 8.0 * nI for nI in sizes[0])
         ach = b / (statistics.mean(tri_ms) * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": TRIDIAG_TRAFFIC.get(args.workload), "algorithmic_bytes": b,
+                "traffic": measured_traffic("k_tridiag32", args.workload), "algorithmic_bytes": b,
                 "kernel": "k_tridiag32 (FP32 Householder tridiagonalisation, lower triangle, thread-block clusters)",
-                "ms_per_launch": statistics.mean(tri_ms), "peak_source": src}
+                "ms_per_launch": statistics.mean(tri_ms), "peak_source": src,
+                "note": "latency-bound chain of |dof| dependent Householder steps per subdomain"}
     else:
         b = {"local_apply": bytes_local, "coarse_solve": bytes_coarse, "scatter": bytes_scatter}.get(dom)
         if b is None:

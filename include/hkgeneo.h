@@ -168,6 +168,19 @@ hk_status hk_kernel_times(hk_handle* h, double* ms, int32_t* count);
  * other handles' on other streams (the serving calls) run faster without them. */
 hk_status hk_set_solve_graphs(hk_handle* h, int on);
 
+/* Waits for the handle's device work and reports a failure that a kernel recorded since the last
+ * check: a bounded device wait that ran out (HK_TIMEOUT) or a failed pivot.  The record is cleared
+ * by this call (and by every call that reports it: hk_solve, hk_solve_device, hk_apply_precond),
+ * so each failure is reported once.  Callers of hk_apply_precond_noalloc use it after their work,
+ * since that call does not synchronise. */
+hk_status hk_check_status(hk_handle* h);
+
+/* Test hook of the failure path: the number of polls a grid barrier of the cooperative
+ * Gram-Schmidt step makes before it gives up and records HK_TIMEOUT (default 2^25, about a second;
+ * 0 restores the default).  With a small limit a solve ends after the inner step whose barrier gave
+ * up, returns HK_TIMEOUT and leaves the handle usable.  Other waits keep their limits. */
+hk_status hk_set_wait_limit(hk_handle* h, int grid_barrier_polls);
+
 /* Number of CUDA kernels the library has launched in this process so far (all handles). */
 long long hk_kernel_launches(void);
 
@@ -203,10 +216,12 @@ hk_status hk_apply_precond(hk_handle* h, int n_rhs, const double* v, double* z);
  * 8 MiB device array per device, held from library load until process exit; a request that
  * needs more (n_rhs * (2 sum_i |dof(Omega_i)| + 2 (n0 + 1)) elements of 4 bytes in the FP32 form,
  * 8 in the FP64 form, each part rounded up to 256 bytes) returns HK_UNSUPPORTED before any
- * launch.  The first call on a device looks the array's address up (call it before any stream
- * capture).  All calls share the array: calls that overlap on the GPU race.  Ordered on the
- * handle's stream (the coarse part runs on a second, high-priority stream of the handle, forked
- * from and joined back into it); calls no cudaMalloc/cudaFree or allocating library routine. */
+ * launch.  The first call on a device looks the array's address up and raises the apply kernels'
+ * shared-memory limits (call it before any stream capture).  All calls share the array: calls
+ * that overlap on the GPU race.  Ordered on the handle's stream (the coarse part runs on a
+ * second, high-priority stream of the handle, forked from and joined back into it); calls no
+ * cudaMalloc/cudaFree or allocating library routine.  Like the other apply calls, a bounded
+ * device wait that runs out is recorded on the handle: hk_check_status reports it. */
 hk_status hk_apply_precond_noalloc(hk_handle* h, int n_rhs, const double* v_dev, double* z_dev);
 
 /* y = B x for n_rhs host vectors. */

@@ -36,6 +36,7 @@ extern "C" const char* hk_status_string(hk_status s) {
     case HK_TIMEOUT: return "HK_TIMEOUT";
     case HK_CUDA_ERROR: return "HK_CUDA_ERROR";
     case HK_UNSUPPORTED: return "HK_UNSUPPORTED";
+    case HK_PENDING: return "HK_PENDING";
   }
   return "unknown";
 }
@@ -90,7 +91,32 @@ hk_status check_device_status(hk_handle* h, const char* phase) {
   }
   if (st.code != HK_OK) {
     hk_set_error("%s: %s at index %d (value %.6g)", phase, hk_status_string((hk_status)st.code), st.where, st.value);
+    // cleared, so that a later phase or call is not blamed for this failure
+    cudaMemsetAsync(h->d_status, 0, sizeof(DevStatus), h->stream);
+    cudaStreamSynchronize(h->stream);
     return (hk_status)st.code;
+  }
+  return HK_OK;
+}
+
+extern "C" hk_status hk_check_status(hk_handle* h) {
+  if (!h) return HK_BAD_ARG;
+  int cur = -1;
+  HK_CUDA(cudaGetDevice(&cur));
+  if (cur != h->dev) HK_CUDA(cudaSetDevice(h->dev));
+  hk_status s = check_device_status(h, "device work");
+  if (cur != h->dev) cudaSetDevice(cur);
+  return s;
+}
+
+extern "C" hk_status hk_set_wait_limit(hk_handle* h, int grid_barrier_polls) {
+  if (!h || grid_barrier_polls < 0) return HK_BAD_ARG;
+  unsigned polls = grid_barrier_polls == 0 ? (1u << 25) : (unsigned)grid_barrier_polls;
+  if (polls != h->wait_polls) {
+    // the limit is a kernel argument: cached solve graphs hold the old one
+    HK_CUDA(cudaStreamSynchronize(h->stream));
+    hk_drop_graphs(h);
+    h->wait_polls = polls;
   }
   return HK_OK;
 }
@@ -436,7 +462,9 @@ static hk_status load_fn(hk_handle* h, int, const double* f, double* r) { return
 extern "C" hk_status hk_apply_precond(hk_handle* h, int n_rhs, const double* v, double* z) {
   if (!h || n_rhs < 1 || !v || !z) return HK_BAD_ARG;
   HK_TRY(ensure_workspace(h, n_rhs));
-  return with_device_vectors(h, h->n, h->n, n_rhs, v, z, apply_fn);
+  HK_TRY(with_device_vectors(h, h->n, h->n, n_rhs, v, z, apply_fn));
+  // a bounded wait of the apply that ran out leaves z untrusted
+  return check_device_status(h, "preconditioner apply");
 }
 
 extern "C" hk_status hk_matvec(hk_handle* h, int n_rhs, const double* x, double* y) {

@@ -168,6 +168,8 @@ struct hk_handle {
   double* d_hist = nullptr;       // s x max_iters
   int* h_state = nullptr;         // pinned host mirror of d_state
   double* h_rstate = nullptr;
+  int h_code = 0;                 // host copy of d_status->code (host-driven solve loop)
+  unsigned wait_polls = 1u << 25; // polls of a grid barrier before it gives up (hk_set_wait_limit)
 
   std::vector<std::pair<void*, size_t>> allocs;  // live allocations and their sizes
   size_t bytes_peak = 0;
@@ -258,7 +260,8 @@ hk_status hk_allow_smem(F* fn) {
   return hk_allow_smem_fn(reinterpret_cast<const void*>(fn));
 }
 
-// Reads the device status record; returns its code with a message.
+// Reads the device status record (synchronising the handle's stream) and clears it; returns its code
+// with a message naming the phase.
 hk_status check_device_status(hk_handle* h, const char* phase);
 
 // ---- phases (each file implements one) ----

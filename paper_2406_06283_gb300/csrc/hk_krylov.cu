@@ -245,8 +245,10 @@ __global__ void k_gs(int n, int s, int m, int j, const int* __restrict__ jp, con
 #define HK_COOP_RHS 4
 
 // Grid-wide barrier of a cooperative launch: arrival counter and generation word; the spin is
-// bounded (about a second), after which HK_TIMEOUT is recorded and the CTA goes on.
-__device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, DevStatus* st) {
+// bounded (`polls` polls, about a second at the default 2^25), after which HK_TIMEOUT is recorded and
+// the CTA goes on.  The solve then stops at the end of the inner step and reports HK_TIMEOUT; the
+// barrier words are zeroed at the start of every solve.
+__device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, DevStatus* st, unsigned polls) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* vg = gen;
@@ -259,7 +261,7 @@ __device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, Dev
     } else {
       unsigned it = 0;
       while (*vg == g0) {
-        if (++it > (1u << 25)) {
+        if (++it > polls) {
           dev_fail(st, HK_TIMEOUT, -2, 0.0);
           break;
         }
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_arnoldi_coop(
     int n, int s, int m, int j, const int* __restrict__ jp, double* V, double* w, int* state, double* rstate,
     double* hcoef, double* partA, double* partB, unsigned* bar, double* H, double* cs, double* sn, double* g,
     double* hist, int max_iters, double tol, const int* __restrict__ rowptr, const int* __restrict__ col,
-    const double* __restrict__ val, const double* __restrict__ Zk, DevStatus* st) {
+    const double* __restrict__ val, const double* __restrict__ Zk, DevStatus* st, unsigned polls) {
   __shared__ double red[32];
   __shared__ double hsh[HK_COOP_RHS][HK_MAXRESTART + 1];
   __shared__ int act[HK_COOP_RHS];
@@ -306,7 +308,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_arnoldi_coop(
       if (lane == 0) pr[i] = acc;
     }
   }
-  grid_barrier(bar, bar + 1, st);
+  grid_barrier(bar, bar + 1, st, polls);
   // B: h1, w -= V h1, h2 partials;  C: h2, w -= V h2, ||w||^2 partials
   for (int pass = 0; pass < 2; ++pass) {
     const double* pin = pass == 0 ? partA : partB;
@@ -342,7 +344,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_arnoldi_coop(
       }
       __syncthreads();
     }
-    grid_barrier(bar, bar + 1, st);
+    grid_barrier(bar, bar + 1, st, polls);
   }
   // D: ||w||, v_{j+1} = w / ||w|| on the CTA's rows; CTA 0: Hessenberg column, Givens, stop test
   for (int r = 0; r < s; ++r) {
@@ -496,27 +498,28 @@ __global__ void k_zero_rhs_init(int s, int* state, double* rstate) {
 
 // ---- device-side loop control of the graph form.  ctl[0] = inner step j of the cycle, ctl[1] = cycles
 // run, ctl[2] = inner steps run.  Both loops are bounded by counters that only grow: the inner one by
-// j < m, the outer one by the cycle count.
+// j < m, the outer one by the cycle count; both end at once when a kernel has recorded a failure (a
+// bounded wait that ran out).
 __global__ void k_ctl_cycle_begin(int* ctl, cudaGraphConditionalHandle inner) {
   ctl[0] = 0;
   cudaGraphSetConditional(inner, 1u);  // a nested condition keeps its last value: re-arm it every cycle
 }
 
 __global__ void k_ctl_step_end(int s, const int* __restrict__ state, int* ctl, int m,
-                               cudaGraphConditionalHandle inner) {
+                               const DevStatus* __restrict__ st, cudaGraphConditionalHandle inner) {
   int j = ++ctl[0];
   ++ctl[2];
   int any = 0;
   for (int r = 0; r < s; ++r) any |= state[8 * r + ST_ACTIVE];
-  cudaGraphSetConditional(inner, (any && j < m) ? 1u : 0u);
+  cudaGraphSetConditional(inner, (any && j < m && st->code == 0) ? 1u : 0u);
 }
 
 __global__ void k_ctl_cycle_end(int s, const int* __restrict__ state, int* ctl, int max_cycles,
-                                cudaGraphConditionalHandle outer) {
+                                const DevStatus* __restrict__ st, cudaGraphConditionalHandle outer) {
   int c = ++ctl[1];
   int all = 1;
   for (int r = 0; r < s; ++r) all &= state[8 * r + ST_DONE] != 0;
-  cudaGraphSetConditional(outer, (!all && c < max_cycles) ? 1u : 0u);
+  cudaGraphSetConditional(outer, (!all && c < max_cycles && st->code == 0) ? 1u : 0u);
 }
 
 void hk_drop_graphs(hk_handle* h) {
@@ -648,7 +651,7 @@ static hk_status fgmres_step(hk_handle* h, int s, double tol, int j, const int* 
     const double* Zk = h->d_Zk;
     void* args[] = {&n, &s, &m, &j, (void*)&jp, &V, &h->d_w, &h->d_state, &h->d_rstate, &h->d_hcol, &h->d_part,
                     &partB, &bar, &h->d_H, &h->d_cs, &h->d_sn, &h->d_g, &h->d_hist, &mi, &tol, &h->d_rowptr,
-                    &h->d_col, &h->d_valB, (void*)&Zk, &h->d_status};
+                    &h->d_col, &h->d_valB, (void*)&Zk, &h->d_status, &h->wait_polls};
     HK_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_coop, dim3(RED_BLOCKS), dim3(RED_THREADS), args, 0, st));
     HK_COUNT_LAUNCH();
     if (h->timing) {
@@ -752,7 +755,7 @@ static hk_status build_solve_graph(hk_handle* h, int s, double tol, hk_handle::S
     if (e == cudaSuccess) {
       body_in = pi.conditional.phGraph_out[0];
       rc = fgmres_cycle_end(h, s, tol);
-      k_ctl_cycle_end<<<1, 1, 0, st>>>(s, h->d_state, h->d_ctl, max_cycles, c_out);
+      k_ctl_cycle_end<<<1, 1, 0, st>>>(s, h->d_state, h->d_ctl, max_cycles, h->d_status, c_out);
       HK_COUNT_LAUNCH();
     } else {
       hk_set_error("graph capture: %s", cudaGetErrorString(e));
@@ -774,7 +777,7 @@ static hk_status build_solve_graph(hk_handle* h, int s, double tol, hk_handle::S
     } else {
       g_hk_capture_count = 0;
       rc = fgmres_step(h, s, tol, 0, h->d_ctl);
-      k_ctl_step_end<<<1, 1, 0, st>>>(s, h->d_state, h->d_ctl, m, c_in);
+      k_ctl_step_end<<<1, 1, 0, st>>>(s, h->d_state, h->d_ctl, m, h->d_status, c_in);
       HK_COUNT_LAUNCH();
       G.iter_kernels = g_hk_capture_count;
       e = cudaStreamEndCapture(st, &tmp);
@@ -808,6 +811,9 @@ static hk_status fgmres_results(hk_handle* h, int s, double* u_dev, int32_t* ite
   if (res_hist)
     HK_CUDA(cudaMemcpyAsync(res_hist, h->d_hist, sizeof(double) * (size_t)s * mi, cudaMemcpyDeviceToHost, st));
   HK_CUDA(cudaStreamSynchronize(st));
+  // a bounded device wait that ran out during the solve (apply or Gram-Schmidt): the outputs are
+  // written but not trusted
+  HK_TRY(check_device_status(h, "solve"));
   bool allconv = true;
   for (int r = 0; r < s; ++r) {
     if (iters) iters[r] = h->h_state[8 * r + ST_ITERS];
@@ -865,7 +871,9 @@ hk_status run_fgmres(hk_handle* h, int s, const double* rhs_dev, double tol, dou
     for (int j = 0; j < m; ++j) {
       HK_TRY(fgmres_step(h, s, tol, j, nullptr));
       HK_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(int) * 8 * s, cudaMemcpyDeviceToHost, st));
+      HK_CUDA(cudaMemcpyAsync(&h->h_code, &h->d_status->code, sizeof(int), cudaMemcpyDeviceToHost, st));
       HK_CUDA(cudaStreamSynchronize(st));
+      if (h->h_code != 0) return fgmres_results(h, s, u_dev, iters, res_hist, final_res, nullptr);
       bool any = false;
       for (int r = 0; r < s; ++r) any |= h->h_state[8 * r + ST_ACTIVE] != 0;
       if (!any) break;

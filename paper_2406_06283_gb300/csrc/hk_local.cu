@@ -1262,8 +1262,8 @@ hk_status phase_local_factors_end(hk_handle* h) {
 // every device that loads the library until the process exits.  Its device
 // address is looked up once per device (host code may not use the symbol
 // itself as a pointer: it is only a host-side stand-in), on the first call
-// made on that device; that first call should happen before any stream
-// capture.  Every call uses the same array, so calls whose kernels overlap on
+// made on that device, which also raises the apply kernels' shared-memory
+// limits; that first call should happen before any stream capture.  Every call uses the same array, so calls whose kernels overlap on
 // the GPU race with each other.  The array keeps the contents of the last
 // call; each call writes every scratch element it reads before reading it, so
 // nothing has to be cleared.
@@ -1316,7 +1316,10 @@ extern "C" hk_status hk_apply_precond_noalloc(hk_handle* h, int n_rhs, const dou
   HK_CUDA(cudaGetDevice(&cur));
   if (cur != h->dev) HK_CUDA(cudaSetDevice(h->dev));
   void* base = nullptr;
-  hk_status s = noalloc_scratch(h->dev, &base);
+  // raises the apply kernels' dynamic shared-memory limits (once per process and device; allocates
+  // nothing), so that this call works when it is the first apply made on the device
+  hk_status s = apply_prepare(h);
+  if (s == HK_OK) s = noalloc_scratch(h->dev, &base);
   if (s == HK_OK) {
     unsigned char* b = static_cast<unsigned char*>(base);
     if (h->p.precision == HK_FP32_PRECOND)

@@ -108,12 +108,15 @@ def lib():
     L.hk_server_poll.argtypes = [_P, C.c_uint64, C.c_int, _P, _P, _P, _P, C.POINTER(hk_request_info)]
     L.hk_server_get_stats.argtypes = [_P, C.POINTER(hk_server_stats)]
     L.hk_server_destroy.argtypes = [_P]
+    L.hk_check_status.argtypes = [_P]
+    L.hk_set_wait_limit.argtypes = [_P, C.c_int]
+    L.hk_apply_precond_noalloc.argtypes = [_P, C.c_int, _P, _P]
     for f in ("hk_server_create", "hk_server_add_operator", "hk_server_submit", "hk_server_poll",
               "hk_server_get_stats", "hk_server_destroy"):
         getattr(L, f).restype = C.c_int
     for f in ("hk_setup", "hk_setup_device", "hk_set_timing", "hk_kernel_times", "hk_solve", "hk_solve_device", "hk_info", "hk_destroy", "hk_get_matrix",
               "hk_get_subdomain", "hk_get_mu", "hk_get_eigen", "hk_get_coarse", "hk_apply_precond", "hk_matvec",
-              "hk_assemble_load"):
+              "hk_assemble_load", "hk_check_status", "hk_set_wait_limit", "hk_apply_precond_noalloc"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -196,6 +199,16 @@ def hk_kernel_launches() -> int:
 
 def hk_set_solve_graphs(h: Handle, on: bool = True):
     _check(lib().hk_set_solve_graphs(h.ptr, int(bool(on))), "hk_set_solve_graphs")
+
+
+def hk_check_status(h: Handle) -> int:
+    """Status of the handle's device work since the last check (the record is cleared)."""
+    return int(lib().hk_check_status(h.ptr))
+
+
+def hk_set_wait_limit(h: Handle, polls: int):
+    """Test hook: polls of the cooperative Gram-Schmidt grid barrier before it gives up (0 = default)."""
+    _check(lib().hk_set_wait_limit(h.ptr, int(polls)), "hk_set_wait_limit")
 
 
 def hk_set_timing(h: Handle, on: bool = True):

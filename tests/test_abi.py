@@ -39,6 +39,10 @@ def test_status_strings_without_gpu(library):
     library.hk_status_string.restype = ctypes.c_char_p
     assert library.hk_status_string(0) == b"HK_OK"
     assert library.hk_status_string(2) == b"HK_SINGULAR_LOCAL"
+    # every status the header declares has its own name
+    text = open(os.path.join(ROOT, "include", "hkgeneo.h")).read()
+    for name, code in re.findall(r"\b(HK_[A-Z_]+) = (\d+),?\s", text[:text.index("} hk_status;")]):
+        assert library.hk_status_string(int(code)) == name.encode(), name
 
 
 def test_setup_rejects_bad_arguments_before_touching_the_device(library):

@@ -1,7 +1,8 @@
 """Parity at the benchmark sizes, in the launch configuration bench.py times.
 
 * h = 1/256, k = 50 checkerboard workload (65,025 dofs, 64 subdomains, one N(0,1) right-hand side):
-  the whole oracle runs (about half a minute); iteration counts, solution, every subdomain's kept
+  the whole oracle runs (about half a minute, then 16 re-runs of its solve for the rounding range of
+  the iteration count); iteration counts, residual histories, solution, every subdomain's kept
   eigenvalues and coarse subspace are compared with the tolerances of test_gpu_parity.py.
 * h = 1/512, k = 100 layered workload (261,121 dofs, 256 subdomains, 16 right-hand sides): too large for
   the oracle as a whole, so the eigenproblems of sampled subdomains are compared one by one, and the
@@ -19,7 +20,7 @@ from oracle import geneo as OG
 from oracle import solver as OS
 from paper_2406_06283_gb300 import hk
 from paper_2406_06283_gb300 import workloads as W
-from test_gpu_parity import oracle_count_range
+from test_gpu_parity import check_counts, check_history, oracle_count_range
 
 pytestmark = pytest.mark.gpu
 
@@ -52,23 +53,22 @@ def test_c2_full_parity_fp64(c2):
     h = hk.setup_problem(p)
     for i, ev in enumerate(o.eigs):
         _check_eigen(h, i, ev)
-    want = OS.solve(o, p.rhs, p.tol)[0]
     got = hk.hk_solve(h, p.rhs, p.tol)
-    lo, hi = oracle_count_range(o, p.rhs[0], p.tol, trials=2)
-    assert lo <= got.iters[0] <= hi, (got.iters[0], want.iters, (lo, hi))
-    assert _rel(got.u[0], want.x) <= 1e-7
+    rng_out = oracle_count_range(o, p.rhs[0], p.tol, key=("c2", 0))
+    check_counts("c2_h256_k50_p8", 0, "fp64", got.iters[0], rng_out)
+    assert _rel(got.u[0], rng_out[0].x) <= 1e-7
     assert got.true_rel_res[0] <= p.tol
+    check_history(got.history[0, : got.iters[0]], rng_out)
     hk.hk_destroy(h)
 
 
 def test_c2_full_parity_fp32_preconditioner(c2):
     p, o = c2
     h = hk.setup_problem(p, precision=hk.HK_FP32_PRECOND)
-    want = OS.solve(o, p.rhs, p.tol)[0]
     got = hk.hk_solve(h, p.rhs, p.tol)
-    lo, hi = oracle_count_range(o, p.rhs[0], p.tol, trials=2, eps=6e-8)
-    assert lo - 1 <= got.iters[0] <= hi + 1, (got.iters[0], want.iters, (lo, hi))
-    assert _rel(got.u[0], want.x) <= 1e-7
+    rng_out = oracle_count_range(o, p.rhs[0], p.tol, key=("c2", 0))
+    check_counts("c2_h256_k50_p8", 0, "fp32", got.iters[0], rng_out, widen=1)
+    assert _rel(got.u[0], rng_out[0].x) <= 1e-7
     hk.hk_destroy(h)
 
 

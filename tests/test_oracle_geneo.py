@@ -97,3 +97,40 @@ def test_coarse_vectors_are_pou_weighted():
     ev = geneo.local_eigen(BN, C, w, tau=0.5)
     np.testing.assert_allclose(ev.Z, ev.P[:, : ev.m] / mu[subs[0].dof][:, None])
     assert np.all(ev.lam[: ev.m] < 0.5) and (ev.m == ev.lam.size or ev.lam[ev.m] >= 0.5)
+
+
+def _dense_z_by_definition(subs, eigs, mu, n):
+    """Def. 5.1 written out entry by entry: column l of subdomain i is E_i Xi_i p_l, i.e. zero
+    off dof(Omega_i) and p_l[a] / mu_l at the a-th dof l of Omega_i (dofs in increasing order)."""
+    cols = []
+    for sd, ev in zip(subs, eigs):
+        for l in range(ev.m):
+            z = np.zeros(n)
+            for a in range(sd.dof.size):
+                g = int(sd.dof[a])
+                z[g] = ev.P[a, l] / float(mu[g])
+            cols.append(z)
+    return np.stack(cols, axis=1) if cols else np.zeros((n, 0))
+
+
+@pytest.mark.parametrize("cells,parts,ov,k", [(10, 2, 1, 5.0), (12, 3, 2, 7.0)])
+def test_coarse_basis_matches_definition(cells, parts, ov, k):
+    p = W.small_problem(cells=cells, parts=parts, k=k, overlap=ov, checker=2)
+    m = p.mesh
+    subs, mu = D.decompose(m.xyz, m.elems, m.is_boundary, p.elem_to_sub, p.n_sub, ov)
+    eigs = []
+    for sd in subs:
+        BN, C, w = geneo.local_pencil(m.xyz, m.elems, p.coeff, m.is_boundary, p.k, sd, mu)
+        eigs.append(geneo.local_eigen(BN, C, w, tau=0.5))
+    assert sum(e.m for e in eigs) > 0
+    want = _dense_z_by_definition(subs, eigs, mu, m.n_dofs)
+    got = geneo.coarse_basis(subs, eigs, m.n_dofs).toarray()
+    assert got.shape == want.shape
+    # p / mu and p * (1 / mu) may differ in the last bit; a misplaced row or column differs by O(1)
+    np.testing.assert_allclose(got, want, rtol=1e-15, atol=0.0)
+    # each column is supported on its own subdomain's dof set only
+    c0 = 0
+    for sd, ev in zip(subs, eigs):
+        off = np.setdiff1d(np.arange(m.n_dofs), sd.dof)
+        assert np.all(got[off, c0:c0 + ev.m] == 0.0)
+        c0 += ev.m

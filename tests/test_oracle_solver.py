@@ -131,3 +131,41 @@ def test_load_vector_helper_f1():
     p = W.config_c1()
     f = solver.load_vector(p)
     np.testing.assert_allclose(f, 1.0 / 64 ** 2, rtol=1e-12)
+
+
+@pytest.mark.parametrize("levels", ["one", "two", "coarse"])
+@pytest.mark.parametrize("weighting", ["as", "ras_pou"])
+def test_preconditioner_variants_match_dense_definition(levels, weighting):
+    """Every variant of the preconditioner written with dense matrices built from the
+    definitions: R_i the Boolean restriction to dof(Omega_i) (Sec. 2.3), the local term
+    R_i^T W_i B_i^{-1} R_i with W_i = I (Eq. 2.22) or diag(1/mu) (the partition-of-unity
+    variant), and the coarse term Z (Z^T B Z)^{-1} Z^T (Eq. 2.23) with Z assembled entry by
+    entry from Def. 5.1 (column l of subdomain i is p_l / mu on dof(Omega_i), zero elsewhere)."""
+    p = W.small_problem(cells=12, parts=3, k=6.0, overlap=2, checker=2, seed=4)
+    h = solver.setup_problem(p, levels=levels, weighting=weighting)
+    Bd = h.B.toarray()
+    n = h.n
+    M = np.zeros((n, n))
+    if levels in ("one", "two"):
+        for sd in h.subs:
+            R = np.zeros((sd.dof.size, n))
+            for a in range(sd.dof.size):
+                R[a, sd.dof[a]] = 1.0
+            Wt = np.diag(1.0 / h.mu[sd.dof]) if weighting == "ras_pou" else np.eye(sd.dof.size)
+            M += R.T @ Wt @ np.linalg.inv(R @ Bd @ R.T) @ R
+    if levels in ("two", "coarse"):
+        subs, mu = D.decompose(p.mesh.xyz, p.mesh.elems, p.mesh.is_boundary, p.elem_to_sub, p.n_sub, p.overlap)
+        cols = []
+        for sd in subs:
+            BN, C, w = geneo.local_pencil(p.mesh.xyz, p.mesh.elems, p.coeff, p.mesh.is_boundary, p.k, sd, mu)
+            ev = geneo.local_eigen(BN, C, w, p.tau)
+            for l in range(ev.m):
+                z = np.zeros(n)
+                for a in range(sd.dof.size):
+                    z[sd.dof[a]] = ev.P[a, l] / mu[sd.dof[a]]
+                cols.append(z)
+        Z = np.stack(cols, axis=1)
+        assert Z.shape[1] == h.n0 > 0
+        M += Z @ np.linalg.inv(Z.T @ Bd @ Z) @ Z.T
+    v = np.random.default_rng(6).standard_normal(n)
+    np.testing.assert_allclose(h.precond.apply(v), M @ v, rtol=1e-9, atol=1e-11 * np.abs(M @ v).max())

@@ -8,10 +8,18 @@ test calls it through the C ABI twice in a row with different vectors, for
 both precision forms, and checks each result against the allocating entry
 point within the 1e-10 relative tolerance of the other apply tests.  It also
 checks that a request larger than the fixed array is refused before any work.
+A third test runs in a fresh process in which the allocation-free apply is
+the first apply made, with subdomains large enough (about 1,200 dofs, 8
+right-hand sides, FP64) that the coarse restriction needs more shared memory
+than the default limit: the entry point must raise that limit itself.
 This file is collected last so that a failure here leaves every other test
 already run; it passes alone and after the rest.
 """
 import ctypes
+import os
+import subprocess
+import sys
+import textwrap
 
 import numpy as np
 import pytest
@@ -60,3 +68,47 @@ def test_noalloc_refuses_requests_beyond_its_array():
     assert _noalloc(h, v_dev, z_dev, n_rhs=100000) == hk.HK_UNSUPPORTED
     assert b"scratch" in hk.lib().hk_last_error()
     hk.hk_destroy(h)
+
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _big_problem():
+    # h = 1/128, 4 x 4 boxes: subdomains of up to 35^2 = 1,225 dofs
+    return W.small_problem(cells=128, parts=4, k=20.0, overlap=2, checker=4, seed=12)
+
+
+def test_noalloc_as_the_first_apply_of_a_process(tmp_path):
+    from oracle import solver as OS
+    out = tmp_path / "z.npy"
+    code = textwrap.dedent(f"""
+        import sys
+        sys.path.insert(0, {ROOT!r})
+        sys.path.insert(0, {os.path.join(ROOT, "tests")!r})
+        import numpy as np, torch
+        from paper_2406_06283_gb300 import hk
+        from test_zz_no_alloc import _big_problem
+        p = _big_problem()
+        h = hk.setup_problem(p, precision=hk.HK_FP64)
+        info = hk.hk_info(h)
+        assert info["max_dof"] > 768, info["max_dof"]
+        v = np.random.default_rng(13).standard_normal((8, p.mesh.n_dofs))
+        v_dev = torch.tensor(v, dtype=torch.float64, device="cuda")
+        z_dev = torch.full_like(v_dev, float("nan"))
+        torch.cuda.synchronize()
+        st = hk.lib().hk_apply_precond_noalloc(h.ptr, 8, v_dev.data_ptr(), z_dev.data_ptr())
+        assert st == hk.HK_OK, (st, hk.lib().hk_last_error())
+        assert hk.hk_check_status(h) == hk.HK_OK
+        torch.cuda.synchronize()
+        np.save({str(out)!r}, z_dev.cpu().numpy())
+        hk.hk_destroy(h)
+    """)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+    got = np.load(out)
+    p = _big_problem()
+    o = OS.setup_problem(p)
+    v = np.random.default_rng(13).standard_normal((8, p.mesh.n_dofs))
+    want = np.stack([o.precond.apply(vi) for vi in v])
+    assert np.all(np.isfinite(got))
+    assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
