@@ -443,10 +443,11 @@ def run_ours(args, world, rank, local):
     bytes_coarse = 2 * ze * pf + n0 * n0 * pf
     bytes_scatter = s * n * 8 + It * 4
     agg = {k: [ms, c] for k, (ms, c) in kt0.items()}
-    tri_ms, setup_ms = [], []
+    eig_ms, setup_ms = [], []
     for info, _, _ in rec:
-        tri_ms.append(info["setup_ms"][6])
+        eig_ms.append(info["eigen_kernel_ms"][:3])
         setup_ms.append(info["setup_ms"][5])
+    eig_mean = [statistics.mean(x[i] for x in eig_ms) for i in range(3)]
     hbm, src = peaks()
     per = {k: (v[0] / max(v[1], 1)) for k, v in agg.items()}
     # the coarse branch runs beside the local sweeps (forked stream): the apply takes the longer
@@ -460,23 +461,14 @@ def run_ours(args, world, rank, local):
                   "kernels": "k_local_apply || (k_restrict -> k_coarse_solve -> k_prolong), then k_scatter",
                   "bytes_per_apply": apply_bytes, "rhs_per_apply": s, "ms_per_apply": apply_ms,
                   "peak_source": src}
-    # dominant kernel over the step: the tridiagonalisation (setup) vs the solve kernels
+    # dominant kernel over the step: the eigen kernels of the setup vs the solve kernels
     tot = {k: v[0] for k, v in agg.items()}
-    tot["tridiag"] = sum(tri_ms)
+    tot["eigen_inertia"], tot["eigen_lanczos"], tot["eigen_refine"] = eig_mean
     dom = max(tot, key=tot.get)
-    sizes = [nI_list]
-    if dom == "tridiag":
-        # Householder reduction in FP32 of the lower triangle of each subdomain's standard-form matrix
-        # (n = |dof(Omega_i)|): the least it must move is one read of that triangle, 4 n (n + 1) / 2
-        # bytes, and the diagonal and off-diagonal it returns, 8 n bytes.  (Its unblocked steps re-read
-        # the trailing triangle, mostly from L2; those re-reads are not counted.)
-        b = sum(4.0 * nI * (nI + 1) / 2.0 + 8.0 * nI for nI in sizes[0])
-        ach = b / (statistics.mean(tri_ms) * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": measured_traffic("k_tridiag32", args.workload), "algorithmic_bytes": b,
-                "kernel": "k_tridiag32 (FP32 Householder tridiagonalisation, lower triangle, thread-block clusters)",
-                "ms_per_launch": statistics.mean(tri_ms), "peak_source": src,
-                "note": "latency-bound chain of |dof| dependent Householder steps per subdomain"}
+    if dom.startswith("eigen_"):
+        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "kernel": {"eigen_inertia": "k_inertia", "eigen_lanczos": "k_lanczos",
+                           "eigen_refine": "k_refine"}[dom], "ms_per_launch": tot[dom], "peak_source": src}
     else:
         b = {"local_apply": bytes_local, "coarse_solve": bytes_coarse, "scatter": bytes_scatter}.get(dom)
         if b is None:
@@ -493,7 +485,7 @@ def run_ours(args, world, rank, local):
             "setup_phases_ms": dict(zip(["assembly", "decomposition", "local_factors", "eigen", "coarse"],
                                         [round(x, 3) for x in info0["setup_ms"][:5]])),
             "phases_ms": {"setup": statistics.mean(setup_ms),
-                          "tridiag": statistics.mean(tri_ms),
+                          "eigen_kernels": dict(zip(["inertia", "lanczos", "refine"], eig_mean)),
                           "solve": statistics.mean(step_ms) - statistics.mean(setup_ms)},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "solve_only": {"fp32_precond": so32, "fp64": so64},

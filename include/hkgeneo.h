@@ -131,11 +131,13 @@ typedef struct {
   long long coarse_elems;      /* entries of all Z_i, sum_i |dof(Omega_i)| m_i */
   long long lower_nnz;         /* couplings L_j between consecutive level sets, sum over subdomains */
   double setup_ms[8];          /* phases: assembly, decomposition, local factors, eigen, coarse,
-                                  total; [6] the Householder tridiagonalisation kernel alone; [7] 0 */
+                                  total; [6], [7] 0 (unused) */
   size_t bytes_peak;           /* most device bytes the handle held at once (setup temporaries included) */
   long long graph_solves;      /* solves run as one CUDA graph (device-side loops); the others were
                                   driven from the host (kernel timing on, graph capture unavailable, or
                                   graphs switched off by hk_set_solve_graphs) */
+  double eigen_kernel_ms[4];   /* setup kernels of the eigenproblems: [0] FP64 inertia count below tau,
+                                  [1] FP32 Lanczos candidates, [2] FP64 refinement, [3] 0 */
 } hk_info_t;
 
 hk_status hk_info(const hk_handle* h, hk_info_t* info);

@@ -19,8 +19,8 @@ OUT_DIR = os.path.join(PKG, "_lib")
 OBJ_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libhkgeneo.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["hk_api.cu", "hk_assembly.cu", "hk_decomp.cu", "hk_local.cu", "hk_eigen.cu", "hk_coarse.cu",
-           "hk_krylov.cu", "hk_server.cu"]
+SOURCES = ["hk_api.cu", "hk_assembly.cu", "hk_decomp.cu", "hk_local.cu", "hk_eigen.cu", "hk_lanczos.cu",
+           "hk_coarse.cu", "hk_krylov.cu", "hk_server.cu"]
 
 
 def nvcc() -> str:

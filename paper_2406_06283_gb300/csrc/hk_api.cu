@@ -369,6 +369,7 @@ extern "C" hk_status hk_info(const hk_handle* h, hk_info_t* info) {
   for (int i = 0; i < 8; ++i) info->setup_ms[i] = h->setup_ms[i];
   info->bytes_peak = h->bytes_peak;
   info->graph_solves = h->graph_solves;
+  for (int i = 0; i < 4; ++i) info->eigen_kernel_ms[i] = h->eigen_ms[i];
   return HK_OK;
 }
 

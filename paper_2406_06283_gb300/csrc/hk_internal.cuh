@@ -94,6 +94,7 @@ struct hk_handle {
   long long I_total = 0, G_total = 0, f_total = 0, csr_total = 0, z_total = 0, lower_nnz = 0;
   std::vector<Sub> subs;
   double setup_ms[8] = {0};
+  double eigen_ms[4] = {0};  // inertia, Lanczos, refinement (hk_info_t.eigen_kernel_ms)
 
   // ---- device data kept for the solve ----
   DevStatus* d_status = nullptr;
@@ -263,6 +264,29 @@ hk_status hk_allow_smem(F* fn) {
 // Reads the device status record (synchronising the handle's stream) and clears it; returns its code
 // with a message naming the phase.
 hk_status check_device_status(hk_handle* h, const char* phase);
+
+// Sparse H_k-GenEO pencil (B^N, C) over ovdof(Omega_i) of every subdomain, rows in the level order of
+// ovdof (built in hk_eigen.cu; used by the eigenvalue kernels of hk_lanczos.cu and the refinement).
+struct OvdofPencil {
+  const int* o_off = nullptr;     // device: first row of each subdomain
+  const int* levptr = nullptr;    // device: per subdomain L + 1 level pointers, at o_off[s] + s
+  const int* L = nullptr;         // device: level count per subdomain
+  const int* cnt = nullptr;       // device: row lengths
+  const int* col = nullptr;       // device: maxrow columns per row
+  const double* B = nullptr;      // device: B^N values
+  const double* C = nullptr;      // device: C values
+  const int* o2i = nullptr;       // device: dof level position of each row (-1 on Gamma)
+  int maxrow = 0, max_b = 0, max_nO = 0;
+  std::vector<int> h_off, h_nO, h_L;   // host copies: first row, rows, levels per subdomain
+  std::vector<int> h_levptr;           // host copy of the level pointers
+};
+// #{lambda < tau} per subdomain (FP64 inertia of B^N - tau C), into d_neg.
+hk_status eigen_inertia(hk_handle* h, const OvdofPencil& op, double tau, int* d_neg, cudaStream_t st);
+// Candidate eigenvalues below lam_cut per subdomain (FP32 shift-invert block Lanczos), ascending, into
+// d_lamhat (HK_MAXM per subdomain) and their number into d_cnt; neg: the counts of eigen_inertia, which
+// size each subdomain's Krylov basis.  *ms: the kernel's time.
+hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<int>& neg, double lam_cut,
+                        double* d_lamhat, int* d_cnt, float* ms);
 
 // ---- phases (each file implements one) ----
 hk_status phase_assembly(hk_handle* h, const hk_mesh* mesh, const double* coeff);

@@ -1,0 +1,934 @@
+// Locating and counting the H_k-GenEO eigenvalues (Eq. 5.12, Def. 5.1) without dense reductions.
+//
+// The pencil lives on ovdof(Omega_i) (O = dof U Gamma): B^N p = lambda C p, with B^N the local Neumann
+// Helmholtz matrix and C = Xi D^N Xi, which vanishes on Gamma.  Its finite eigenvalues are real (the
+// paper's lemma on indefinite pencils), and B^N_GG is positive definite on the workloads (HK_EIG_FAIL
+// otherwise, from the setup's Gamma block).  In the level-set order of O both matrices are block
+// tridiagonal (levels couple only to their neighbours), so every factorisation below is a block
+// elimination over the level sets with dense diagonal blocks.
+//
+// Two kernels:
+//  * k_inertia (FP64): the number of eigenvalues below tau.  With B^N - tau C = L D L^T block-wise
+//    (D_j the Schur complements of the levels), Sylvester's law and Haynsworth's inertia additivity give
+//        #{lambda < tau} = #neg(B^N - tau C) - #neg(B^N_GG) = sum_j #neg(D_j)
+//    (B^N_GG positive definite).  #neg(D_j) is read off a symmetric indefinite factorisation of D_j
+//    with Bunch-Kaufman pivoting (1x1 and 2x2 pivots); D_j^{-1} for the next level comes from
+//    Gauss-Jordan elimination with partial pivoting.  This count certifies the kept number m_i.
+//  * k_lanczos (FP32): candidate eigenvalues.  A shift sigma below the smallest eigenvalue makes
+//    M = B^N - sigma C positive definite (checked: its block elimination without pivoting must meet
+//    only positive pivots, otherwise sigma is lowered, by 0.5, 0.5, 1, 2, 4, ... from -0.5, and the
+//    factorisation repeated; two bisection steps between the last indefinite and the definite shift then
+//    bring sigma within a quarter step of the smallest eigenvalue).  The operator
+//    Op = M^{-1} C is self-adjoint in the C inner product with eigenvalues theta = 1 / (lambda - sigma),
+//    so the wanted eigenvalues lambda < tau + delta are its largest ones.  A block Krylov basis
+//    (block size 4, C-orthonormal, classical Gram-Schmidt twice against all earlier blocks, columns
+//    that collapse replaced by fresh seeded vectors) spans Q; the Rayleigh quotient T = Q^T C (Op Q)
+//    is formed from the stored products Op Q, reduced to tridiagonal form by Householder reflections in
+//    FP64 and its eigenvalues above 1 / (tau + delta - sigma) found by bisection on Sturm counts.  The
+//    candidates lambda = sigma + 1 / theta go to the FP64 refinement of hk_eigen.cu.
+#include <cmath>
+
+#include "hk_internal.cuh"
+
+#define LZ_P 4            // Krylov block size
+#define LZ_THREADS 256
+#define LZ_MAX_DIM 160    // largest Krylov basis (columns)
+#define LZ_SIGMA_TRIES 8  // shifts tried: sigma0, then 0.5, 0.5, 1, 2, 4, ... lower while the matrix is not definite
+#define LZ_SIGMA_BISECT 2 // bisection steps between the last indefinite and the first definite shift
+
+// Sparse rows of B^N and C over ovdof(Omega_i) of one subdomain, in level order.
+struct OPen {
+  int nO, L, maxrow;
+  const int* lp;       // L + 1 level pointers
+  const int* cnt;      // nO row lengths
+  const int* col;      // nO x maxrow column (level-order index)
+  const double* B;     // nO x maxrow values of B^N
+  const double* C;     // nO x maxrow values of C
+  const int* o2i;      // nO: position in the dof level order, -1 on Gamma
+};
+
+__device__ __forceinline__ OPen open_sub(int s, const int* o_off, const int* O_levptr, const int* O_L, int maxrow,
+                                         const int* ocnt, const int* ocol, const double* oB, const double* oC,
+                                         const int* o2i, const int* sub_info) {
+  OPen p;
+  int oo = o_off[s];
+  p.nO = sub_info[8 * s] + sub_info[8 * s + 1];
+  p.L = O_L[s];
+  p.maxrow = maxrow;
+  p.lp = O_levptr + oo + s;
+  p.cnt = ocnt + oo;
+  p.col = ocol + (long long)oo * maxrow;
+  p.B = oB + (long long)oo * maxrow;
+  p.C = oC + (long long)oo * maxrow;
+  p.o2i = o2i + oo;
+  return p;
+}
+
+// Seeded start and replacement vectors: SplitMix64 finaliser of a key, mapped to [-0.5, 0.5).
+__device__ __forceinline__ float lz_hash_unit(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ULL;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+  x ^= x >> 31;
+  return (float)((double)(x >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+}
+
+// In-place inverse of the b x b row-major matrix A (shared or global memory) by Gauss-Jordan
+// elimination without pivoting.  For a symmetric positive definite A the pivots are the diagonal of its
+// LDL^T factorisation, all positive; the smallest one is returned through *minpiv (thread 0).
+template <typename T>
+__device__ void gj_inverse_nopiv(T* A, int b, T* sh_inv, double* minpiv) {
+  int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, nw = NT >> 5;
+  for (int k = 0; k < b; ++k) {
+    if (tid == 0) {
+      T pv = A[k * b + k];
+      if ((double)pv < *minpiv) *minpiv = (double)pv;
+      *sh_inv = pv > (T)0 ? (T)1 / pv : (T)0;
+      A[k * b + k] = (T)1;
+    }
+    __syncthreads();
+    T inv = *sh_inv;
+    for (int c = tid; c < b; c += NT) A[k * b + c] *= inv;
+    __syncthreads();
+    for (int i = tid >> 5; i < b; i += nw) {
+      if (i == k) continue;
+      T g = A[i * b + k];
+      for (int c = lane; c < b; c += 32)
+        if (c != k) A[i * b + c] -= g * A[k * b + c];
+    }
+    __syncthreads();
+    for (int i = tid; i < b; i += NT)
+      if (i != k) A[i * b + k] = -A[i * b + k] * A[k * b + k];
+    __syncthreads();
+  }
+}
+
+// Block elimination of M = B^N - sigma C over the level sets without pivoting (T = float):
+// per level j the inverse of the Schur complement S_j = M_jj - M_{j,j-1} X_{j-1} (b_j x b_j) followed
+// by X_j = S_j^{-1} M_{j,j+1} (b_j x b_{j+1}), stored one after another in F.  S (max_b^2) is the
+// working block (shared memory when it fits, else the level's place in F).  Returns the smallest pivot
+// (> 0 exactly when M is positive definite, up to rounding).
+template <typename T>
+__device__ double lz_factor(const OPen& P, double sigma, T* F, T* Ssm, T* sh_inv, double* sh_min) {
+  int tid = threadIdx.x, NT = blockDim.x;
+  if (tid == 0) *sh_min = 1e300;
+  __syncthreads();
+  long long bo = 0, prev_x = -1;
+  int prev_r0 = 0;
+  for (int j = 0; j < P.L; ++j) {
+    int r0 = P.lp[j], r1 = P.lp[j + 1], b = r1 - r0;
+    int bn = j + 1 < P.L ? P.lp[j + 2] - r1 : 0;
+    T* S = Ssm ? Ssm : F + bo;
+    for (int e = tid; e < b * b; e += NT) {
+      int qa = e / b, t = e - qa * b;
+      int a = r0 + qa;
+      const int* cl = P.col + (long long)a * P.maxrow;
+      const double* bv = P.B + (long long)a * P.maxrow;
+      const double* cv = P.C + (long long)a * P.maxrow;
+      int c_n = min(P.cnt[a], P.maxrow);
+      double v = 0;
+      for (int q = 0; q < c_n; ++q) {
+        int c = cl[q];
+        double mv = bv[q] - sigma * cv[q];
+        if (c == r0 + t) v += mv;
+        else if (j > 0 && c >= prev_r0 && c < r0) v -= mv * (double)F[prev_x + (long long)(c - prev_r0) * b + t];
+      }
+      S[e] = (T)v;
+    }
+    __syncthreads();
+    gj_inverse_nopiv<T>(S, b, sh_inv, sh_min);
+    if (Ssm)
+      for (int e = tid; e < b * b; e += NT) F[bo + e] = S[e];
+    long long xo = bo + (long long)b * b;
+    // X_j[q][c] = sum_a S^{-1}[q][a] M[a][r1 + c]  (M symmetric: read row r1 + c's entries in level j)
+    for (int e = tid; e < b * bn; e += NT) {
+      int qt = e / bn, cc = e - qt * bn;
+      int c = r1 + cc;
+      const int* cl = P.col + (long long)c * P.maxrow;
+      const double* bv = P.B + (long long)c * P.maxrow;
+      const double* cv = P.C + (long long)c * P.maxrow;
+      int c_n = min(P.cnt[c], P.maxrow);
+      double v = 0;
+      for (int q = 0; q < c_n; ++q) {
+        int a = cl[q];
+        if (a >= r0 && a < r1) v += (double)S[qt * b + (a - r0)] * (bv[q] - sigma * cv[q]);
+      }
+      F[xo + e] = (T)v;
+    }
+    __syncthreads();
+    prev_x = xo;
+    prev_r0 = r0;
+    bo = xo + (long long)b * bn;
+  }
+  return *sh_min;
+}
+
+// Y = M^{-1} Y for LZ_P vectors (row-major nO x LZ_P, in shared memory) with the factors of lz_factor:
+// forward  t_j = y_j - M_{j,j-1} y_{j-1},  y_j = S_j^{-1} t_j;  backward  y_j -= X_j y_{j+1}.
+// tv: max_b x LZ_P shared scratch.
+template <typename T>
+__device__ void lz_solve(const OPen& P, double sigma, const T* __restrict__ F, T* Y, T* tv) {
+  int tid = threadIdx.x, NT = blockDim.x;
+  long long fo = 0;
+  for (int j = 0; j < P.L; ++j) {
+    int r0 = P.lp[j], b = P.lp[j + 1] - r0, bn = j + 1 < P.L ? P.lp[j + 2] - P.lp[j + 1] : 0;
+    for (int e = tid; e < b * LZ_P; e += NT) {
+      int q = e / LZ_P, pc = e - q * LZ_P;
+      int a = r0 + q;
+      const int* cl = P.col + (long long)a * P.maxrow;
+      const double* bv = P.B + (long long)a * P.maxrow;
+      const double* cv = P.C + (long long)a * P.maxrow;
+      int c_n = min(P.cnt[a], P.maxrow);
+      T acc = Y[a * LZ_P + pc];
+      for (int q2 = 0; q2 < c_n; ++q2) {
+        int c = cl[q2];
+        if (c < r0) acc -= (T)(bv[q2] - sigma * cv[q2]) * Y[c * LZ_P + pc];
+      }
+      tv[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < b * LZ_P; e += NT) {
+      int q = e / LZ_P, pc = e - q * LZ_P;
+      const T* Sr = F + fo + (long long)q * b;
+      T acc = 0;
+      for (int c = 0; c < b; ++c) acc += Sr[c] * tv[c * LZ_P + pc];
+      Y[(r0 + q) * LZ_P + pc] = acc;
+    }
+    __syncthreads();
+    fo += (long long)b * b + (long long)b * bn;
+  }
+  {
+    int bl = P.lp[P.L] - P.lp[P.L - 1];
+    fo -= (long long)bl * bl;
+  }
+  for (int j = P.L - 2; j >= 0; --j) {
+    int r0 = P.lp[j], b = P.lp[j + 1] - r0, r1 = P.lp[j + 1], bn = P.lp[j + 2] - r1;
+    fo -= (long long)b * b + (long long)b * bn;
+    const T* Xm = F + fo + (long long)b * b;
+    for (int e = tid; e < b * LZ_P; e += NT) {
+      int q = e / LZ_P, pc = e - q * LZ_P;
+      T acc = 0;
+      for (int c = 0; c < bn; ++c) acc += Xm[(long long)q * bn + c] * Y[(r1 + c) * LZ_P + pc];
+      tv[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < b * LZ_P; e += NT) {
+      int q = e / LZ_P, pc = e - q * LZ_P;
+      Y[(r0 + q) * LZ_P + pc] -= tv[e];
+    }
+    __syncthreads();
+  }
+}
+
+// Y_out = C Y_in for LZ_P vectors (row-major nO x LZ_P); in and out distinct.
+template <typename T>
+__device__ void lz_cmul(const OPen& P, const T* Yin, T* Yout) {
+  for (int e = threadIdx.x; e < P.nO * LZ_P; e += blockDim.x) {
+    int a = e / LZ_P, pc = e - a * LZ_P;
+    const int* cl = P.col + (long long)a * P.maxrow;
+    const double* cv = P.C + (long long)a * P.maxrow;
+    int c_n = min(P.cnt[a], P.maxrow);
+    T acc = 0;
+    for (int q = 0; q < c_n; ++q) acc += (T)cv[q] * Yin[cl[q] * LZ_P + pc];
+    Yout[e] = acc;
+  }
+}
+
+// Block-wide sums of NV floats (all threads get them); red: 32 * NV floats of shared memory.
+template <int NV>
+__device__ __forceinline__ void lz_block_sums(float (&v)[NV], float* red) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) red[w * NV + i] = v[i];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    float t = 0;
+    for (int q = 0; q < nw; ++q) t += red[q * NV + i];
+    v[i] = t;
+  }
+  __syncthreads();
+}
+
+// One classical Gram-Schmidt pass of the block Y (nO x LZ_P, shared memory) against the C-orthonormal
+// blocks Q_0 .. Q_{nb-1} (global, with their products C Q_i): Y -= Q_i (CQ_i^T Y).  A warp per block
+// computes its LZ_P x LZ_P coefficients (coef, shared), then every thread updates its rows.
+__device__ void lz_cgs_pass(int nO, int nb, const float* __restrict__ Qg, const float* __restrict__ CQg, float* Y,
+                            float* coef) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  long long bs = (long long)nO * LZ_P;
+  for (int i = warp; i < nb; i += nw) {
+    const float4* cq = reinterpret_cast<const float4*>(CQg + i * bs);
+    float acc[LZ_P][LZ_P];
+#pragma unroll
+    for (int p = 0; p < LZ_P; ++p)
+#pragma unroll
+      for (int q = 0; q < LZ_P; ++q) acc[p][q] = 0.f;
+    for (int a = lane; a < nO; a += 32) {
+      float4 c4 = cq[a];
+      float4 y4 = reinterpret_cast<const float4*>(Y)[a];
+      float c[4] = {c4.x, c4.y, c4.z, c4.w}, y[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+      for (int p = 0; p < LZ_P; ++p)
+#pragma unroll
+        for (int q = 0; q < LZ_P; ++q) acc[p][q] += c[p] * y[q];
+    }
+#pragma unroll
+    for (int p = 0; p < LZ_P; ++p)
+#pragma unroll
+      for (int q = 0; q < LZ_P; ++q) {
+        float t = acc[p][q];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) coef[(i * LZ_P + p) * LZ_P + q] = t;
+      }
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < nO; a += blockDim.x) {
+    float4 y4 = reinterpret_cast<float4*>(Y)[a];
+    float y[4] = {y4.x, y4.y, y4.z, y4.w};
+    for (int i = 0; i < nb; ++i) {
+      float4 q4 = reinterpret_cast<const float4*>(Qg + i * bs)[a];
+      float qv[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+      for (int p = 0; p < LZ_P; ++p)
+#pragma unroll
+        for (int q = 0; q < LZ_P; ++q) y[q] -= qv[p] * coef[(i * LZ_P + p) * LZ_P + q];
+    }
+    reinterpret_cast<float4*>(Y)[a] = make_float4(y[0], y[1], y[2], y[3]);
+  }
+  __syncthreads();
+}
+
+// Seeded vector on the dof rows (zero on Gamma) into column pc of Y.
+__device__ void lz_seed_column(const OPen& P, int s, int blk, int pc, int attempt, float* Y) {
+  for (int a = threadIdx.x; a < P.nO; a += blockDim.x) {
+    unsigned long long key = ((unsigned long long)s << 40) ^ ((unsigned long long)(blk * 16 + pc * 4 + attempt) << 24) ^
+                             (unsigned long long)a;
+    Y[a * LZ_P + pc] = P.o2i[a] >= 0 ? lz_hash_unit(key) : 0.f;
+  }
+}
+
+// C-norm of column pc of Y (C Y written into column pc of CY).
+__device__ float lz_cnorm_col(const OPen& P, const float* Y, float* CY, int pc, float* red) {
+  float nv[1] = {0.f};
+  for (int a = threadIdx.x; a < P.nO; a += blockDim.x) {
+    const int* cl = P.col + (long long)a * P.maxrow;
+    const double* cv = P.C + (long long)a * P.maxrow;
+    int c_n = min(P.cnt[a], P.maxrow);
+    float acc = 0;
+    for (int q = 0; q < c_n; ++q) acc += (float)cv[q] * Y[cl[q] * LZ_P + pc];
+    CY[a * LZ_P + pc] = acc;
+    nv[0] += acc * Y[a * LZ_P + pc];
+  }
+  lz_block_sums<1>(nv, red);
+  return sqrtf(fmaxf(nv[0], 0.f));
+}
+
+// C-orthonormalises the columns of Y (modified Gram-Schmidt inside the block, twice, after the block
+// has been orthogonalised against the earlier blocks) and leaves C Y in CY.  ref[pc]: C-norm of column
+// pc before any orthogonalisation.  A column whose C-norm falls below 1e-4 of it has collapsed into the
+// span already built: it is replaced by a seeded vector, orthogonalised twice against every earlier
+// block and column; if that keeps less than 1e-3 of its own norm, the column is set to zero (it then
+// adds only a zero row and column to the Rayleigh quotient).
+__device__ void lz_orthonormalise(const OPen& P, int s, int blk, int nb, const float* Qg, const float* CQg, float* Y,
+                                  float* CY, const float* ref, float* coef, float* red) {
+  for (int pc = 0; pc < LZ_P; ++pc) {
+    float r0 = ref[pc];
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      if (attempt == 1) {
+        lz_seed_column(P, s, blk, pc, 1, Y);
+        __syncthreads();
+        r0 = lz_cnorm_col(P, Y, CY, pc, red);
+        // the other columns are orthogonal to the earlier blocks already: the passes change them only
+        // by rounding
+        lz_cgs_pass(P.nO, nb, Qg, CQg, Y, coef);
+        lz_cgs_pass(P.nO, nb, Qg, CQg, Y, coef);
+      }
+      float nrm = lz_cnorm_col(P, Y, CY, pc, red);
+      for (int rep = 0; rep < 2 && pc > 0; ++rep) {
+        float d[LZ_P - 1] = {0.f, 0.f, 0.f};
+        for (int a = threadIdx.x; a < P.nO; a += blockDim.x)
+          for (int q = 0; q < pc; ++q) d[q] += CY[a * LZ_P + q] * Y[a * LZ_P + pc];
+        lz_block_sums<LZ_P - 1>(d, red);
+        for (int a = threadIdx.x; a < P.nO; a += blockDim.x)
+          for (int q = 0; q < pc; ++q) Y[a * LZ_P + pc] -= d[q] * Y[a * LZ_P + q];
+        __syncthreads();
+        nrm = lz_cnorm_col(P, Y, CY, pc, red);
+      }
+      bool ok = nrm > (attempt == 0 ? 1e-4f : 1e-3f) * r0 && nrm > 0.f;
+      if (ok || attempt == 1) {
+        float inv = ok ? 1.f / nrm : 0.f;
+        for (int a = threadIdx.x; a < P.nO; a += blockDim.x) {
+          Y[a * LZ_P + pc] *= inv;
+          CY[a * LZ_P + pc] *= inv;
+        }
+        __syncthreads();
+        break;
+      }
+    }
+  }
+}
+
+// Number of eigenvalues below x of the symmetric tridiagonal matrix (d, e) (Sturm count).
+__device__ int lz_sturm_below(const double* d, const double* e, int n, double x, double pivmin) {
+  int c = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  c += q < 0.0;
+  for (int i = 1; i < n; ++i) {
+    q = d[i] - x - e[i - 1] * e[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    c += q < 0.0;
+  }
+  return c;
+}
+
+// One CTA per subdomain.  Dynamic shared memory: Y (max_nO x 4) | C Y (max_nO x 4) | sweep scratch
+// (max_b x 4) | the working block of the factorisation (max_b^2, when s_in_smem); once the Krylov steps
+// are done the Rayleigh quotient (N x N doubles, N = 4 kdim[s]) reuses the same bytes.
+// Global workspace per subdomain: the factors (F + f_off[s]) and the basis Q, C Q and Op Q
+// (3 kdim[s] blocks of nO x 4, Qw + q_off[s]).
+// Outputs: lam_hat[s * HK_MAXM + t] = the candidates below lam_cut in ascending order, cnt_out[s] their
+// number, sigma_out[s] the shift used.
+__global__ void __launch_bounds__(LZ_THREADS) k_lanczos(
+    const int* __restrict__ sub_info, const int* __restrict__ o_off, const int* __restrict__ O_levptr,
+    const int* __restrict__ O_L, int maxrow, const int* __restrict__ ocnt, const int* __restrict__ ocol,
+    const double* __restrict__ oB, const double* __restrict__ oC, const int* __restrict__ o2i,
+    const int* __restrict__ kdim, const long long* __restrict__ f_off, float* F, const long long* __restrict__ q_off,
+    float* Qw, int max_nO, int max_b, int s_in_smem, double sigma0, double lam_cut, double* lam_hat, int* cnt_out,
+    double* sigma_out, DevStatus* st) {
+  extern __shared__ __align__(16) unsigned char lz_smem[];
+  __shared__ float coef[LZ_MAX_DIM * LZ_P];
+  __shared__ float red[32 * LZ_P];
+  __shared__ float ref[LZ_P];
+  __shared__ float sh_inv;
+  __shared__ double sh_min, sh_scal[4];
+  __shared__ double hd[LZ_MAX_DIM], he[LZ_MAX_DIM], hv[LZ_MAX_DIM], hp[LZ_MAX_DIM];
+  int s = blockIdx.x, tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = NT >> 5;
+  OPen P = open_sub(s, o_off, O_levptr, O_L, maxrow, ocnt, ocol, oB, oC, o2i, sub_info);
+  float* Ys = reinterpret_cast<float*>(lz_smem);
+  float* CYs = Ys + (long long)max_nO * LZ_P;
+  float* tv = CYs + (long long)max_nO * LZ_P;
+  float* Ssm = s_in_smem ? tv + (long long)max_b * LZ_P : nullptr;
+  double* Tm = reinterpret_cast<double*>(lz_smem);
+  float* Fs = F + f_off[s];
+  int nb = kdim[s];
+  long long bs = (long long)P.nO * LZ_P;
+  float* Qg = Qw + q_off[s];
+  float* CQg = Qg + nb * bs;
+  float* Wg = CQg + nb * bs;
+
+  // 1. a shift below the spectrum: M = B^N - sigma C positive definite
+  double sigma = sigma0, step = 0.5, upper = 0.0;
+  bool pd = false, bracket = false;
+  for (int t = 0; t < LZ_SIGMA_TRIES && !pd; ++t) {
+    double mp = lz_factor<float>(P, sigma, Fs, Ssm, &sh_inv, &sh_min);
+    __syncthreads();
+    pd = mp > 0.0;
+    if (!pd) {
+      upper = sigma;
+      bracket = true;
+      sigma -= step;
+      if (t >= 1) step *= 2.0;
+    }
+  }
+  // closer to the spectrum (faster convergence): bisect between the definite and the indefinite shift,
+  // then make sure the stored factors are those of the final shift
+  bool factors_current = true;
+  for (int t = 0; t < LZ_SIGMA_BISECT && pd && bracket; ++t) {
+    double mid = 0.5 * (sigma + upper);
+    double mp = lz_factor<float>(P, mid, Fs, Ssm, &sh_inv, &sh_min);
+    __syncthreads();
+    if (mp > 0.0) {
+      sigma = mid;
+      factors_current = true;
+    } else {
+      upper = mid;
+      factors_current = false;
+    }
+  }
+  if (pd && !factors_current) {
+    lz_factor<float>(P, sigma, Fs, Ssm, &sh_inv, &sh_min);
+    __syncthreads();
+  }
+  if (!pd) {
+    if (tid == 0) {
+      cnt_out[s] = 0;
+      dev_fail(st, HK_EIG_FAIL, s, sigma);
+    }
+    return;
+  }
+  if (tid == 0) sigma_out[s] = sigma;
+
+  // 2. seeded, C-orthonormal start block
+  for (int pc = 0; pc < LZ_P; ++pc) lz_seed_column(P, s, 0, pc, 0, Ys);
+  __syncthreads();
+  for (int pc = 0; pc < LZ_P; ++pc) {
+    float r = lz_cnorm_col(P, Ys, CYs, pc, red);
+    if (tid == 0) ref[pc] = r;
+  }
+  __syncthreads();
+  lz_orthonormalise(P, s, 0, 0, Qg, CQg, Ys, CYs, ref, coef, red);
+  for (long long e = tid; e < bs; e += NT) {
+    Qg[e] = Ys[e];
+    CQg[e] = CYs[e];
+  }
+  __syncthreads();
+
+  // 3. Krylov steps: W_k = Op Q_k, Q_{k+1} from W_k orthogonalised against Q_0 .. Q_k
+  for (int k = 0; k < nb; ++k) {
+    for (long long e = tid; e < bs; e += NT) Ys[e] = CQg[k * bs + e];
+    __syncthreads();
+    lz_solve<float>(P, sigma, Fs, Ys, tv);
+    for (long long e = tid; e < bs; e += NT) Wg[k * bs + e] = Ys[e];
+    __syncthreads();
+    if (k == nb - 1) break;
+    for (int pc = 0; pc < LZ_P; ++pc) {
+      float r = lz_cnorm_col(P, Ys, CYs, pc, red);
+      if (tid == 0) ref[pc] = r;
+    }
+    __syncthreads();
+    lz_cgs_pass(P.nO, k + 1, Qg, CQg, Ys, coef);
+    lz_cgs_pass(P.nO, k + 1, Qg, CQg, Ys, coef);
+    lz_orthonormalise(P, s, k + 1, k + 1, Qg, CQg, Ys, CYs, ref, coef, red);
+    for (long long e = tid; e < bs; e += NT) {
+      Qg[(k + 1) * bs + e] = Ys[e];
+      CQg[(k + 1) * bs + e] = CYs[e];
+    }
+    __syncthreads();
+  }
+
+  // 4. Rayleigh quotient T = Q^T C (Op Q), a warp per pair of blocks; then symmetrised (FP64)
+  int N = nb * LZ_P;
+  for (int pr = warp; pr < nb * nb; pr += nw) {
+    int bi = pr / nb, bj = pr - bi * nb;
+    const float4* cq = reinterpret_cast<const float4*>(CQg + bi * bs);
+    const float4* wq = reinterpret_cast<const float4*>(Wg + bj * bs);
+    float acc[LZ_P][LZ_P];
+#pragma unroll
+    for (int p = 0; p < LZ_P; ++p)
+#pragma unroll
+      for (int q = 0; q < LZ_P; ++q) acc[p][q] = 0.f;
+    for (int a = lane; a < P.nO; a += 32) {
+      float4 c4 = cq[a], w4 = wq[a];
+      float c[4] = {c4.x, c4.y, c4.z, c4.w}, w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+      for (int p = 0; p < LZ_P; ++p)
+#pragma unroll
+        for (int q = 0; q < LZ_P; ++q) acc[p][q] += c[p] * w[q];
+    }
+#pragma unroll
+    for (int p = 0; p < LZ_P; ++p)
+#pragma unroll
+      for (int q = 0; q < LZ_P; ++q) {
+        float t = acc[p][q];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) Tm[(bi * LZ_P + p) * N + bj * LZ_P + q] = (double)t;
+      }
+  }
+  __syncthreads();
+  for (int e = tid; e < N * N; e += NT) {
+    int i = e / N, j = e - i * N;
+    if (i < j) {
+      double v = 0.5 * (Tm[i * N + j] + Tm[j * N + i]);
+      Tm[i * N + j] = v;
+      Tm[j * N + i] = v;
+    }
+  }
+  __syncthreads();
+
+  // 5. Householder reduction of T to tridiagonal form (diagonal hd, off-diagonal he)
+  for (int k = 0; k + 2 < N; ++k) {
+    if (tid == 0) {
+      double x0 = Tm[(k + 1) * N + k], ss = 0;
+      for (int i = k + 2; i < N; ++i) ss += Tm[i * N + k] * Tm[i * N + k];
+      hd[k] = Tm[k * N + k];
+      if (ss == 0.0) {
+        he[k] = x0;
+        sh_scal[0] = 0.0;
+      } else {
+        double nrm = sqrt(x0 * x0 + ss), alpha = x0 > 0 ? -nrm : nrm, v0 = x0 - alpha;
+        he[k] = alpha;
+        sh_scal[0] = 2.0 / (v0 * v0 + ss);
+        hv[k + 1] = v0;
+      }
+    }
+    __syncthreads();
+    double beta = sh_scal[0];
+    __syncthreads();  // every thread has read beta before thread 0 may overwrite it
+    if (beta == 0.0) continue;
+    for (int i = k + 2 + tid; i < N; i += NT) hv[i] = Tm[i * N + k];
+    __syncthreads();
+    for (int i = k + 1 + tid; i < N; i += NT) {
+      double acc = 0;
+      for (int j = k + 1; j < N; ++j) acc += Tm[i * N + j] * hv[j];
+      hp[i] = beta * acc;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double kv = 0;
+      for (int i = k + 1; i < N; ++i) kv += hv[i] * hp[i];
+      sh_scal[1] = 0.5 * beta * kv;
+    }
+    __syncthreads();
+    double kc = sh_scal[1];
+    for (int i = k + 1 + tid; i < N; i += NT) hp[i] -= kc * hv[i];
+    __syncthreads();
+    int m = N - k - 1;
+    for (int e = tid; e < m * m; e += NT) {
+      int i = k + 1 + e / m, j = k + 1 + e % m;
+      Tm[i * N + j] -= hv[i] * hp[j] + hp[i] * hv[j];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (N >= 2) {
+      hd[N - 2] = Tm[(N - 2) * N + N - 2];
+      he[N - 2] = Tm[(N - 1) * N + N - 2];
+    }
+    hd[N - 1] = Tm[(N - 1) * N + N - 1];
+    he[N - 1] = 0.0;
+    double lo = 1e300, hi = -1e300, me = 0;
+    for (int i = 0; i < N; ++i) {
+      double r = (i > 0 ? fabs(he[i - 1]) : 0.0) + (i < N - 1 ? fabs(he[i]) : 0.0);
+      lo = fmin(lo, hd[i] - r);
+      hi = fmax(hi, hd[i] + r);
+      if (i < N - 1) me = fmax(me, he[i] * he[i]);
+    }
+    sh_scal[2] = hi + 1e-12 * fabs(hi) + 1e-300;
+    sh_scal[3] = 1e-290 * fmax(1.0, me);
+  }
+  __syncthreads();
+
+  // 6. candidates: eigenvalues theta > 1 / (lam_cut - sigma) of T, lambda = sigma + 1 / theta
+  double th_cut = 1.0 / (lam_cut - sigma), th_hi = sh_scal[2], pivmin = sh_scal[3];
+  int cnt = th_cut >= th_hi ? 0 : N - lz_sturm_below(hd, he, N, th_cut, pivmin);
+  if (tid == 0) {
+    cnt_out[s] = cnt;
+    if (cnt > HK_MAXM) dev_fail(st, HK_UNSUPPORTED, s, cnt);
+  }
+  for (int t = tid; t < cnt && t < HK_MAXM; t += NT) {
+    int kidx = N - 1 - t;  // ascending index of the t-th largest theta
+    double lo = th_cut, hi = th_hi;
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+      double mid = 0.5 * (lo + hi);
+      if (lz_sturm_below(hd, he, N, mid, pivmin) > kidx) hi = mid;
+      else lo = mid;
+    }
+    lam_hat[(long long)s * HK_MAXM + t] = sigma + 1.0 / (0.5 * (lo + hi));
+  }
+}
+
+// ====================================================================== inertia (FP64)
+// Block-wide (max |value|, its index) over the candidates each thread offers; ties go to the smaller
+// index.  rv/ri: 32 entries of shared memory; the result is returned to every thread.
+__device__ void bk_argmax(double v, int i, double* rv, int* ri, double* out_v, int* out_i) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    if (ov > v || (ov == v && oi < i)) v = ov, i = oi;
+  }
+  __syncthreads();
+  if (lane == 0) rv[w] = v, ri[w] = i;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bv = rv[0];
+    int bi = ri[0];
+    for (int q = 1; q < nw; ++q)
+      if (rv[q] > bv || (rv[q] == bv && ri[q] < bi)) bv = rv[q], bi = ri[q];
+    *out_v = bv;
+    *out_i = bi;
+  }
+  __syncthreads();
+}
+
+// Swaps index i and j of the symmetric b x b matrix A (rows, then columns).
+__device__ void bk_sym_swap(double* A, int b, int i, int j) {
+  if (i == j) return;
+  for (int c = threadIdx.x; c < b; c += blockDim.x) {
+    double t = A[i * b + c];
+    A[i * b + c] = A[j * b + c];
+    A[j * b + c] = t;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < b; r += blockDim.x) {
+    double t = A[r * b + i];
+    A[r * b + i] = A[r * b + j];
+    A[r * b + j] = t;
+  }
+  __syncthreads();
+}
+
+// Number of negative eigenvalues of the symmetric b x b matrix A (row-major, full storage; destroyed),
+// from the Bunch-Kaufman factorisation P A P^T = L D L^T with 1x1 and 2x2 diagonal blocks (partial
+// pivoting, alpha = (1 + sqrt 17) / 8): by Sylvester's law A and D have the same inertia, and a 2x2
+// block [a b; b c] has one negative eigenvalue when ac - b^2 < 0, two when ac - b^2 > 0 and a + c < 0.
+// A zero column is a zero eigenvalue (not counted).  Returns the count to every thread.
+__device__ int bk_neg_count(double* A, int b, double* rv, int* ri, double* shd, int* shi) {
+  const double alpha = 0.6403882032022076;  // (1 + sqrt(17)) / 8
+  int tid = threadIdx.x, NT = blockDim.x;
+  if (tid == 0) shi[2] = 0;  // negative count
+  int k = 0;
+  while (k < b) {
+    // column k below the diagonal: largest entry and its row
+    double cv = 0.0;
+    int ci = b;
+    for (int i = k + 1 + tid; i < b; i += NT) {
+      double a = fabs(A[i * b + k]);
+      if (a > cv || (a == cv && i < ci)) cv = a, ci = i;
+    }
+    bk_argmax(cv, ci, rv, ri, &shd[0], &shi[0]);
+    double colmax = shd[0], akk = fabs(A[k * b + k]);
+    int r = shi[0];
+    bool need_row = fmax(akk, colmax) > 0.0 && akk < alpha * colmax;
+    double rowmax = 0.0;
+    if (need_row) {
+      double rvv = 0.0;
+      int rii = b;
+      for (int j = k + tid; j < b; j += NT) {
+        if (j == r) continue;
+        double a = fabs(A[r * b + j]);
+        if (a > rvv || (a == rvv && j < rii)) rvv = a, rii = j;
+      }
+      bk_argmax(rvv, rii, rv, ri, &shd[1], &shi[1]);
+      rowmax = shd[1];
+    }
+    int kind, swap_from = -1, swap_to = -1;
+    if (fmax(akk, colmax) == 0.0) kind = 0;
+    else if (!need_row || akk * rowmax >= alpha * colmax * colmax) kind = 1;
+    else if (fabs(A[r * b + r]) >= alpha * rowmax) kind = 1, swap_from = r, swap_to = k;
+    else kind = 2, swap_from = r, swap_to = k + 1;
+    // every thread has taken its decision (read A[r][r]) before the swap or the elimination writes
+    __syncthreads();
+    if (swap_from >= 0) bk_sym_swap(A, b, swap_to, swap_from);
+    if (kind == 0) {
+      k += 1;
+      continue;
+    }
+    if (kind == 1) {
+      double d = A[k * b + k];
+      if (tid == 0 && d < 0.0) shi[2] += 1;
+      double inv = 1.0 / d;
+      int m = b - k - 1;
+      for (int e = tid; e < m * m; e += NT) {
+        int i = k + 1 + e / m, j = k + 1 + e % m;
+        A[i * b + j] -= A[i * b + k] * inv * A[k * b + j];
+      }
+      __syncthreads();
+      k += 1;
+    } else {
+      double a = A[k * b + k], bb = A[(k + 1) * b + k], c = A[(k + 1) * b + k + 1];
+      double det = a * c - bb * bb;
+      if (tid == 0) shi[2] += det < 0.0 ? 1 : (a + c < 0.0 ? (det > 0.0 ? 2 : 1) : 0);
+      double i00 = c / det, i01 = -bb / det, i11 = a / det;
+      int m = b - k - 2;
+      for (int e = tid; e < m * m; e += NT) {
+        int i = k + 2 + e / m, j = k + 2 + e % m;
+        double x0 = A[i * b + k], x1 = A[i * b + k + 1];
+        double y0 = A[k * b + j], y1 = A[(k + 1) * b + j];
+        A[i * b + j] -= x0 * (i00 * y0 + i01 * y1) + x1 * (i01 * y0 + i11 * y1);
+      }
+      __syncthreads();
+      k += 2;
+    }
+  }
+  __syncthreads();
+  int neg = shi[2];
+  __syncthreads();
+  return neg;
+}
+
+// #{lambda < tau} of subdomain s (one CTA each): block LDL^T of B^N - tau C over the ovdof level sets,
+// #neg of every Schur complement D_j by bk_neg_count, D_j^{-1} by Gauss-Jordan with partial pivoting
+// (a pivot below 1e-14 max|M| is replaced by +-1e-14 max|M|: the count is then that of a matrix within
+// rounding of it).  Work blocks (D_j, its copy, X_{j-1} = D_{j-1}^{-1} M_{j-1,j} and X_j, max_b^2 each)
+// sit in shared memory when in_smem, else in the subdomain's part of ws (ws_off).
+__global__ void __launch_bounds__(256) k_inertia(
+    const int* __restrict__ sub_info, const int* __restrict__ o_off, const int* __restrict__ O_levptr,
+    const int* __restrict__ O_L, int maxrow, const int* __restrict__ ocnt, const int* __restrict__ ocol,
+    const double* __restrict__ oB, const double* __restrict__ oC, const int* __restrict__ o2i, double tau,
+    int max_b, int in_smem, const long long* __restrict__ ws_off, double* ws, int* neg_out) {
+  extern __shared__ __align__(16) double in_smem_buf[];
+  __shared__ int piv[HK_MAXB];
+  __shared__ double rv[32], shd[4], minpiv;
+  __shared__ int ri[32], shi[4];
+  int s = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
+  OPen P = open_sub(s, o_off, O_levptr, O_L, maxrow, ocnt, ocol, oB, oC, o2i, sub_info);
+  long long mb2 = (long long)max_b * max_b;
+  double* base = in_smem ? in_smem_buf : ws + ws_off[s];
+  double* S = base;
+  double* Sc = base + mb2;
+  double* Xp = base + 2 * mb2;
+  double* Xn = base + 3 * mb2;
+  // scale for the pivot floor
+  double mx = 0;
+  for (long long e = tid; e < (long long)P.nO * P.maxrow; e += NT) {
+    int a = (int)(e / P.maxrow), q = (int)(e % P.maxrow);
+    if (q < P.cnt[a]) mx = fmax(mx, fabs(P.B[e] - tau * P.C[e]));
+  }
+  bk_argmax(mx, 0, rv, ri, &shd[3], &shi[3]);
+  double floor_piv = 1e-14 * shd[3];
+  int neg = 0, prev_r0 = 0;
+  for (int j = 0; j < P.L; ++j) {
+    int r0 = P.lp[j], r1 = P.lp[j + 1], b = r1 - r0;
+    int bn = j + 1 < P.L ? P.lp[j + 2] - r1 : 0;
+    for (int e = tid; e < b * b; e += NT) {
+      int qa = e / b, t = e - qa * b;
+      int a = r0 + qa;
+      const int* cl = P.col + (long long)a * P.maxrow;
+      const double* bv = P.B + (long long)a * P.maxrow;
+      const double* cv = P.C + (long long)a * P.maxrow;
+      int c_n = min(P.cnt[a], P.maxrow);
+      double v = 0;
+      for (int q = 0; q < c_n; ++q) {
+        int c = cl[q];
+        double mv = bv[q] - tau * cv[q];
+        if (c == r0 + t) v += mv;
+        else if (j > 0 && c >= prev_r0 && c < r0) v -= mv * Xp[(long long)(c - prev_r0) * b + t];
+      }
+      S[e] = v;
+      Sc[e] = v;
+    }
+    __syncthreads();
+    // D_j is symmetric up to rounding: count on its symmetric part
+    for (int e = tid; e < b * b; e += NT) {
+      int i = e / b, t = e - i * b;
+      if (i < t) {
+        double v = 0.5 * (Sc[i * b + t] + Sc[t * b + i]);
+        Sc[i * b + t] = v;
+        Sc[t * b + i] = v;
+      }
+    }
+    __syncthreads();
+    neg += bk_neg_count(Sc, b, rv, ri, shd, shi);
+    if (bn > 0) {
+      if (tid == 0) minpiv = 1e300;
+      __syncthreads();
+      gauss_jordan_inverse(S, b, piv, rv, ri, &minpiv, floor_piv);
+      for (int e = tid; e < b * bn; e += NT) {
+        int qt = e / bn, cc = e - qt * bn;
+        int c = r1 + cc;
+        const int* cl = P.col + (long long)c * P.maxrow;
+        const double* bv = P.B + (long long)c * P.maxrow;
+        const double* cv = P.C + (long long)c * P.maxrow;
+        int c_n = min(P.cnt[c], P.maxrow);
+        double v = 0;
+        for (int q = 0; q < c_n; ++q) {
+          int a = cl[q];
+          if (a >= r0 && a < r1) v += S[qt * b + (a - r0)] * (bv[q] - tau * cv[q]);
+        }
+        Xn[e] = v;
+      }
+      __syncthreads();
+      double* t = Xp;
+      Xp = Xn;
+      Xn = t;
+    }
+    prev_r0 = r0;
+  }
+  if (tid == 0) neg_out[s] = neg;
+}
+
+// ====================================================================== host
+hk_status eigen_inertia(hk_handle* h, const OvdofPencil& op, double tau, int* d_neg, cudaStream_t st) {
+  int ns = h->n_sub;
+  size_t need = sizeof(double) * 4 * (size_t)op.max_b * op.max_b;
+  int in_smem = need <= 200 * 1024;
+  double* d_ws = nullptr;
+  long long* d_wo = nullptr;
+  if (!in_smem) {
+    std::vector<long long> wo(ns);
+    for (int s = 0; s < ns; ++s) wo[s] = 4LL * op.max_b * op.max_b * s;
+    HK_TRY(dalloc(h, &d_ws, 4ULL * op.max_b * op.max_b * ns));
+    HK_TRY(dalloc(h, &d_wo, ns));
+    HK_CUDA(cudaMemcpyAsync(d_wo, wo.data(), 8 * ns, cudaMemcpyHostToDevice, h->stream));
+    HK_CUDA(cudaEventRecord(h->ev_fork, h->stream));
+    HK_CUDA(cudaStreamWaitEvent(st, h->ev_fork, 0));
+  }
+  HK_TRY(hk_allow_smem(k_inertia));
+  k_inertia<<<ns, 256, in_smem ? need : 0, st>>>(h->d_sub_info, op.o_off, op.levptr, op.L, op.maxrow, op.cnt, op.col,
+                                                  op.B, op.C, op.o2i, tau, op.max_b, in_smem, d_wo, d_ws, d_neg);
+  HK_COUNT_LAUNCH();
+  HK_LAUNCH_CHECK();
+  if (!in_smem) {
+    // freed on the handle's stream once the kernel is done
+    HK_CUDA(cudaEventRecord(h->ev_join, st));
+    HK_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+    dfree(h, d_ws);
+    dfree(h, d_wo);
+  }
+  return HK_OK;
+}
+
+hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<int>& neg, double lam_cut,
+                        double* d_lamhat, int* d_cnt, float* ms) {
+  cudaStream_t st = h->stream;
+  int ns = h->n_sub;
+  std::vector<int> kd(ns);
+  std::vector<long long> fo(ns), qo(ns);
+  long long ftot = 0, qtot = 0;
+  int kmax = 1;
+  for (int s = 0; s < ns; ++s) {
+    // basis of 4 m + 48 columns (m = the certified count below tau), 32 to LZ_MAX_DIM: enough for the
+    // candidates to reach the FP32 floor (about 1e-7) when m is about 20 eigenvalues with gaps near 1e-3
+    int cols = std::min(LZ_MAX_DIM, std::max(32, 4 * neg[s] + 48));
+    kd[s] = (cols + LZ_P - 1) / LZ_P;
+    kmax = std::max(kmax, kd[s]);
+    const int* lp = &op.h_levptr[op.h_off[s] + s];
+    long long f = 0;
+    for (int j = 0; j < op.h_L[s]; ++j) {
+      long long b = lp[j + 1] - lp[j], bn = j + 1 < op.h_L[s] ? lp[j + 2] - lp[j + 1] : 0;
+      f += b * b + b * bn;
+    }
+    fo[s] = ftot;
+    ftot += (f + 3) & ~3LL;
+    qo[s] = qtot;
+    qtot += 3LL * kd[s] * op.h_nO[s] * LZ_P;
+  }
+  int *d_kd = nullptr;
+  long long *d_fo = nullptr, *d_qo = nullptr;
+  float *d_F = nullptr, *d_Q = nullptr;
+  double* d_sig = nullptr;
+  HK_TRY(dalloc(h, &d_kd, ns));
+  HK_TRY(dalloc(h, &d_fo, ns));
+  HK_TRY(dalloc(h, &d_qo, ns));
+  HK_TRY(dalloc(h, &d_F, ftot));
+  HK_TRY(dalloc(h, &d_Q, qtot));
+  HK_TRY(dalloc(h, &d_sig, ns));
+  HK_CUDA(cudaMemcpyAsync(d_kd, kd.data(), 4 * ns, cudaMemcpyHostToDevice, st));
+  HK_CUDA(cudaMemcpyAsync(d_fo, fo.data(), 8 * ns, cudaMemcpyHostToDevice, st));
+  HK_CUDA(cudaMemcpyAsync(d_qo, qo.data(), 8 * ns, cudaMemcpyHostToDevice, st));
+  size_t vec = sizeof(float) * LZ_P * (2 * (size_t)op.max_nO + op.max_b);
+  size_t sblk = sizeof(float) * (size_t)op.max_b * op.max_b;
+  size_t tmat = sizeof(double) * (size_t)(kmax * LZ_P) * (kmax * LZ_P);
+  int s_in_smem = vec + sblk <= 200 * 1024;
+  size_t shm = std::max(vec + (s_in_smem ? sblk : 0), tmat);
+  if (shm > 220 * 1024) {
+    hk_set_error("subdomain with %d ovdof rows too large for the Lanczos kernel's shared memory", op.max_nO);
+    return HK_UNSUPPORTED;
+  }
+  HK_TRY(hk_allow_smem(k_lanczos));
+  cudaEvent_t e0, e1;
+  HK_CUDA(cudaEventCreate(&e0));
+  HK_CUDA(cudaEventCreate(&e1));
+  cudaEventRecord(e0, st);
+  k_lanczos<<<ns, LZ_THREADS, shm, st>>>(h->d_sub_info, op.o_off, op.levptr, op.L, op.maxrow, op.cnt, op.col, op.B,
+                                         op.C, op.o2i, d_kd, d_fo, d_F, d_qo, d_Q, op.max_nO, op.max_b, s_in_smem,
+                                         -0.5, lam_cut, d_lamhat, d_cnt, d_sig, h->d_status);
+  HK_COUNT_LAUNCH();
+  cudaEventRecord(e1, st);
+  HK_LAUNCH_CHECK();
+  HK_CUDA(cudaEventSynchronize(e1));
+  cudaEventElapsedTime(ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  void* tmp[] = {d_kd, d_fo, d_qo, d_F, d_Q, d_sig};
+  for (void* p : tmp) dfree(h, p);
+  return HK_OK;
+}

@@ -51,7 +51,8 @@ class hk_info_t(C.Structure):
                 ("max_level", C.c_int), ("max_dof", C.c_int), ("nnz", C.c_int), ("precision", C.c_int),
                 ("levels", C.c_int), ("bytes_resident", C.c_size_t), ("factor_elems", C.c_longlong),
                 ("dof_total", C.c_longlong), ("coarse_elems", C.c_longlong), ("lower_nnz", C.c_longlong),
-                ("setup_ms", C.c_double * 8), ("bytes_peak", C.c_size_t), ("graph_solves", C.c_longlong)]
+                ("setup_ms", C.c_double * 8), ("bytes_peak", C.c_size_t), ("graph_solves", C.c_longlong),
+                ("eigen_kernel_ms", C.c_double * 4)]
 
 
 class hk_request_info(C.Structure):
@@ -271,8 +272,9 @@ def hk_solve_device(h: Handle, rhs_dev, u_dev, tol=1e-8, history=False) -> Solve
 def hk_info(h: Handle) -> dict:
     info = hk_info_t()
     _check(lib().hk_info(h.ptr, C.byref(info)), "hk_info")
-    d = {f: getattr(info, f) for f, _ in hk_info_t._fields_ if f != "setup_ms"}
+    d = {f: getattr(info, f) for f, _ in hk_info_t._fields_ if f not in ("setup_ms", "eigen_kernel_ms")}
     d["setup_ms"] = list(info.setup_ms)
+    d["eigen_kernel_ms"] = list(info.eigen_kernel_ms)
     return d
 
 
