@@ -17,7 +17,8 @@
 //  3. FP64 refinement on the sparse pencil.  Candidates closer than 1e-3 max(1,|lambda|) form a
 //     cluster; for each cluster the block-tridiagonal LU of B^N - sigma C over level sets of
 //     ovdof(Omega_i) is formed in FP64 (sigma = the cluster's mean candidate), a seeded block of
-//     cluster size + 2 guard vectors takes five steps of block inverse iteration
+//     cluster size + 2 guard vectors takes block inverse iteration (3 steps for a single candidate, 6 for
+//     a cluster)
 //     ((B^N - sigma C)^{-1} C, C-orthonormalised after each step; the contraction per step is
 //     |lambda - sigma| over the distance to the next eigenvalue outside the block), and a Rayleigh-Ritz
 //     step on B^N gives FP64 eigenpairs; the window of Ritz values closest to the cluster's candidates
@@ -36,9 +37,11 @@
 static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
 #define HK_EIG_DELTA 0.05
+#define LZ_BASIS_MAX 160  // largest Krylov basis of the Lanczos candidates (hk_lanczos.cu)
 #define HK_CLUSTER_GAP 1e-3
 #define HK_MAX_CLUSTER 32
-#define HK_REFINE_STEPS 5
+#define HK_REFINE_STEPS 6          // block inverse-iteration steps of a cluster of candidates
+#define HK_REFINE_STEPS_SINGLE 3   // ... of a single candidate
 #define HK_GUARD 2
 #define HK_MAX_BLOCK (HK_MAX_CLUSTER + HK_GUARD)
 
@@ -331,7 +334,10 @@ __global__ void k_refine(const int* __restrict__ items, const double* __restrict
       X[(long long)t * nO + a] = ia >= 0 ? (double)hash_unitf(key) : 0.0;
     }
   __syncthreads();
-  for (int step = 0; step < HK_REFINE_STEPS; ++step) {
+  // candidates are accurate to about 1e-7: a single eigenvalue converges at |lambda - sigma| / gap <= 1e-3
+  // per step; a cluster's members converge at their spread over the distance to the block's next value
+  int steps = pc == 1 ? HK_REFINE_STEPS_SINGLE : HK_REFINE_STEPS;
+  for (int step = 0; step < steps; ++step) {
     // R = C X, then X = M^{-1} R by the two block sweeps
     o_matvec(nO, oo, maxrow, ocnt, ocol, oB, oC, 1.0, 0, X, R, p);
     __syncthreads();
@@ -456,9 +462,10 @@ __global__ void k_refine(const int* __restrict__ items, const double* __restrict
 // Certification: the number of refined values below tau must equal neg[s], the FP64 inertia count of
 // B^N - tau C (every eigenvalue below tau found once); a difference is accepted only where the value at
 // the boundary lies within 1e-9 max(1, |tau|) of tau (the count then depends on rounding).  Otherwise
-// HK_EIG_FAIL with the subdomain and the difference.
+// fail[s] = 1 (the setup redoes the subdomain once with a larger Krylov basis, then reports HK_EIG_FAIL).
 __global__ void k_select(const int* __restrict__ cnt, const double* __restrict__ lam_ref, double tau,
-                         const int* __restrict__ neg, int* sel, int* m_out, double* lam_out, DevStatus* st) {
+                         const int* __restrict__ neg, int* sel, int* m_out, double* lam_out, int* fail,
+                         DevStatus* st) {
   int s = blockIdx.x;
   if (threadIdx.x != 0) return;
   int c = min(cnt[s], HK_MAXM);
@@ -476,9 +483,10 @@ __global__ void k_select(const int* __restrict__ cnt, const double* __restrict__
   int m = 0;
   while (m < c && lr[ord[m]] < tau) ++m;
   double near = 1e-9 * fmax(1.0, fabs(tau));
+  fail[s] = 0;
   if (m != neg[s]) {
     bool boundary = (m > 0 && tau - lr[ord[m - 1]] <= near) || (m < c && lr[ord[m]] - tau <= near);
-    if (!boundary) dev_fail(st, HK_EIG_FAIL, s, (double)(m - neg[s]));
+    if (!boundary) fail[s] = 1;
   }
   double thr = 1e-8 * fmax(1.0, fabs(tau));
   while (m > 0 && m < c && lr[ord[m]] - lr[ord[m - 1]] <= thr) ++m;
@@ -594,45 +602,37 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   op.h_L = OL;
   op.h_levptr = levO;
 
-  // ---- FP64 count below tau (certifies m_i), then the FP32 Lanczos candidates below tau + delta
+  // ---- FP64 count below tau (certifies m_i) on the second stream, joined at the selection; meanwhile the
+  //      FP32 Lanczos candidates below tau + delta and their FP64 refinement on the setup stream
+  cudaStream_t ist = h->co_stream ? h->co_stream : st;
   cudaEvent_t e0, e1;
   HK_CUDA(cudaEventCreate(&e0));
   HK_CUDA(cudaEventCreate(&e1));
-  cudaEventRecord(e0, st);
-  HK_TRY(eigen_inertia(h, op, h->p.tau, d_neg, st));
-  cudaEventRecord(e1, st);
-  std::vector<int> neg(ns);
-  HK_CUDA(cudaMemcpyAsync(neg.data(), d_neg, 4 * ns, cudaMemcpyDeviceToHost, st));
-  HK_CUDA(cudaStreamSynchronize(st));
-  {
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    h->eigen_ms[0] = ms;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+  if (ist != st) {
+    HK_CUDA(cudaEventRecord(h->ev_fork, st));
+    HK_CUDA(cudaStreamWaitEvent(ist, h->ev_fork, 0));
   }
-  float lz_ms = 0;
-  HK_TRY(eigen_lanczos(h, op, neg, h->p.tau + HK_EIG_DELTA, d_lamhat, d_cnt, &lz_ms));
-  h->eigen_ms[1] = lz_ms;
-  HK_TRY(check_device_status(h, "eigen: Lanczos candidates"));
-  std::vector<int> cnt(ns);
+  cudaEventRecord(e0, ist);
+  HK_TRY(eigen_inertia(h, op, h->p.tau, d_neg, ist));
+  cudaEventRecord(e1, ist);
+  cudaEvent_t inertia_done = nullptr;
+  HK_CUDA(cudaEventCreateWithFlags(&inertia_done, cudaEventDisableTiming));
+  HK_CUDA(cudaEventRecord(inertia_done, ist));
+  // a basis of 96 columns, grown inside the kernel to 4 c + 48 where c candidates ask for more
+  std::vector<int> cols(ns, LZ_BASIS_MAX), cnt(ns);
   std::vector<double> lamhat((size_t)ns * HK_MAXM);
-  HK_CUDA(cudaMemcpyAsync(cnt.data(), d_cnt, 4 * ns, cudaMemcpyDeviceToHost, st));
-  HK_CUDA(cudaMemcpyAsync(lamhat.data(), d_lamhat, sizeof(double) * lamhat.size(), cudaMemcpyDeviceToHost, st));
-  HK_CUDA(cudaStreamSynchronize(st));
-  std::vector<long long> poff(ns);
-  long long ptot = 0;
-  for (int s = 0; s < ns; ++s) {
-    poff[s] = ptot;
-    ptot += (long long)h->subs[s].nI * cnt[s];
-  }
+  float lz_ms = 0;
+  HK_TRY(eigen_lanczos(h, op, cols, 96, h->p.tau + HK_EIG_DELTA, d_lamhat, d_cnt, &lz_ms));
+  HK_TRY(check_device_status(h, "eigen: Lanczos candidates"));
+  h->eigen_ms[1] = lz_ms;
+  int *d_sel = nullptr, *d_m = nullptr, *d_fail = nullptr;
+  HK_TRY(dalloc(h, &d_sel, (size_t)ns * HK_MAXM));
+  HK_TRY(dalloc(h, &d_m, ns));
+  HK_TRY(dalloc(h, &d_fail, ns));
   double* d_P = nullptr;
   long long* d_poff = nullptr;
-  HK_TRY(dalloc(h, &d_P, ptot));
   HK_TRY(dalloc(h, &d_poff, ns));
-  HK_CUDA(up(d_poff, poff.data(), 8 * ns));
-
-  // ---- FP64 refinement: clusters of candidates, one CTA each
+  std::vector<long long> poff(ns);
   std::vector<long long> fsize(ns, 0);
   for (int s = 0; s < ns; ++s) {
     const int* lp = &levO[o_off[s] + s];
@@ -641,78 +641,122 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
       fsize[s] += b * b + b * bn;
     }
   }
-  std::vector<int> items;
-  std::vector<double> sig;
-  std::vector<long long> foff, xoff;
-  long long ftot = 0, xtot = 0;
-  int pmax = 1;
-  for (int s = 0; s < ns; ++s) {
-    const double* lh = &lamhat[(size_t)s * HK_MAXM];
-    int c = std::min(cnt[s], HK_MAXM);
-    int t = 0;
-    while (t < c) {
-      int t1 = t + 1;
-      while (t1 < c && t1 - t < HK_MAX_CLUSTER &&
-             lh[t1] - lh[t1 - 1] <= HK_CLUSTER_GAP * std::max(1.0, std::fabs(lh[t1]))) ++t1;
-      double sm = 0;
-      for (int q = t; q < t1; ++q) sm += lh[q];
-      items.push_back(s); items.push_back(t); items.push_back(t1 - t); items.push_back(0);
-      sig.push_back(sm / (t1 - t));
-      foff.push_back(ftot);
-      ftot += fsize[s];
-      xoff.push_back(xtot);
-      xtot += 2LL * (t1 - t + HK_GUARD) * oc[s];
-      pmax = std::max(pmax, t1 - t + HK_GUARD);
-      t = t1;
-    }
-  }
-  int nit = (int)sig.size();
-  if (nit > 0) {
-    int* d_items = nullptr;
-    double *d_sig = nullptr, *d_F = nullptr, *d_X = nullptr;
-    long long *d_foff = nullptr, *d_xoff = nullptr;
-    HK_TRY(dalloc(h, &d_items, items.size()));
-    HK_TRY(dalloc(h, &d_sig, nit));
-    HK_TRY(dalloc(h, &d_foff, nit));
-    HK_TRY(dalloc(h, &d_xoff, nit));
-    HK_TRY(dalloc(h, &d_F, ftot));
-    HK_TRY(dalloc(h, &d_X, xtot));
-    HK_CUDA(up(d_items, items.data(), 4 * items.size()));
-    HK_CUDA(up(d_sig, sig.data(), 8 * nit));
-    HK_CUDA(up(d_foff, foff.data(), 8 * nit));
-    HK_CUDA(up(d_xoff, xoff.data(), 8 * nit));
-    size_t rshm = sizeof(double) * ((size_t)maxbO * maxbO + (size_t)maxbO * pmax);
-    int s_in_smem = rshm <= 190 * 1024;
-    if (!s_in_smem) rshm = sizeof(double) * (size_t)maxbO * pmax;
-    HK_TRY(hk_allow_smem(k_refine));
-    cudaEvent_t r0, r1;
-    HK_CUDA(cudaEventCreate(&r0));
-    HK_CUDA(cudaEventCreate(&r1));
-    cudaEventRecord(r0, st);
-    k_refine<<<nit, 128, rshm, st>>>(d_items, d_sig, h->d_sub_info, d_o_off, d_Olevptr, d_OL, maxrow, d_ocnt, d_ocol,
-                                     d_oB, d_oC, d_o2i, d_foff, d_xoff, d_F, d_X, d_poff, d_P, d_lamhat, d_lamref,
-                                     maxbO, s_in_smem, h->d_status);
-    HK_COUNT_LAUNCH();
-    cudaEventRecord(r1, st);
-    HK_LAUNCH_CHECK();
+  h->eigen_ms[2] = 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    HK_CUDA(cudaMemcpyAsync(cnt.data(), d_cnt, 4 * ns, cudaMemcpyDeviceToHost, st));
+    HK_CUDA(cudaMemcpyAsync(lamhat.data(), d_lamhat, sizeof(double) * lamhat.size(), cudaMemcpyDeviceToHost, st));
     HK_CUDA(cudaStreamSynchronize(st));
-    {
-      float ms = 0;
-      cudaEventElapsedTime(&ms, r0, r1);
-      h->eigen_ms[2] = ms;
-      cudaEventDestroy(r0);
-      cudaEventDestroy(r1);
+    long long ptot = 0;
+    for (int s = 0; s < ns; ++s) {
+      poff[s] = ptot;
+      ptot += (long long)h->subs[s].nI * cnt[s];
     }
-    HK_TRY(check_device_status(h, "eigen: refinement"));
-    void* tmpf[] = {d_items, d_sig, d_foff, d_xoff, d_F, d_X};
-    for (void* p : tmpf) dfree(h, p);
+    if (d_P) dfree(h, d_P);
+    HK_TRY(dalloc(h, &d_P, ptot));
+    HK_CUDA(up(d_poff, poff.data(), 8 * ns));
+    // ---- FP64 refinement: clusters of candidates, one CTA each
+    std::vector<int> items;
+    std::vector<double> sig;
+    std::vector<long long> foff, xoff;
+    long long ftot = 0, xtot = 0;
+    int pmax = 1;
+    for (int s = 0; s < ns; ++s) {
+      const double* lh = &lamhat[(size_t)s * HK_MAXM];
+      int c = std::min(cnt[s], HK_MAXM);
+      int t = 0;
+      while (t < c) {
+        int t1 = t + 1;
+        while (t1 < c && t1 - t < HK_MAX_CLUSTER &&
+               lh[t1] - lh[t1 - 1] <= HK_CLUSTER_GAP * std::max(1.0, std::fabs(lh[t1]))) ++t1;
+        double sm = 0;
+        for (int q = t; q < t1; ++q) sm += lh[q];
+        items.push_back(s); items.push_back(t); items.push_back(t1 - t); items.push_back(0);
+        sig.push_back(sm / (t1 - t));
+        foff.push_back(ftot);
+        ftot += fsize[s];
+        xoff.push_back(xtot);
+        xtot += 2LL * (t1 - t + HK_GUARD) * oc[s];
+        pmax = std::max(pmax, t1 - t + HK_GUARD);
+        t = t1;
+      }
+    }
+    int nit = (int)sig.size();
+    if (nit > 0) {
+      int* d_items = nullptr;
+      double *d_sig = nullptr, *d_F = nullptr, *d_X = nullptr;
+      long long *d_foff = nullptr, *d_xoff = nullptr;
+      HK_TRY(dalloc(h, &d_items, items.size()));
+      HK_TRY(dalloc(h, &d_sig, nit));
+      HK_TRY(dalloc(h, &d_foff, nit));
+      HK_TRY(dalloc(h, &d_xoff, nit));
+      HK_TRY(dalloc(h, &d_F, ftot));
+      HK_TRY(dalloc(h, &d_X, xtot));
+      HK_CUDA(up(d_items, items.data(), 4 * items.size()));
+      HK_CUDA(up(d_sig, sig.data(), 8 * nit));
+      HK_CUDA(up(d_foff, foff.data(), 8 * nit));
+      HK_CUDA(up(d_xoff, xoff.data(), 8 * nit));
+      size_t rshm = sizeof(double) * ((size_t)maxbO * maxbO + (size_t)maxbO * pmax);
+      int s_in_smem = rshm <= 190 * 1024;
+      if (!s_in_smem) rshm = sizeof(double) * (size_t)maxbO * pmax;
+      HK_TRY(hk_allow_smem(k_refine));
+      cudaEvent_t r0, r1;
+      HK_CUDA(cudaEventCreate(&r0));
+      HK_CUDA(cudaEventCreate(&r1));
+      cudaEventRecord(r0, st);
+      k_refine<<<nit, 128, rshm, st>>>(d_items, d_sig, h->d_sub_info, d_o_off, d_Olevptr, d_OL, maxrow, d_ocnt, d_ocol,
+                                       d_oB, d_oC, d_o2i, d_foff, d_xoff, d_F, d_X, d_poff, d_P, d_lamhat, d_lamref,
+                                       maxbO, s_in_smem, h->d_status);
+      HK_COUNT_LAUNCH();
+      cudaEventRecord(r1, st);
+      HK_LAUNCH_CHECK();
+      HK_CUDA(cudaStreamSynchronize(st));
+      {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, r0, r1);
+        h->eigen_ms[2] += ms;
+        cudaEventDestroy(r0);
+        cudaEventDestroy(r1);
+      }
+      HK_TRY(check_device_status(h, "eigen: refinement"));
+      void* tmpf[] = {d_items, d_sig, d_foff, d_xoff, d_F, d_X};
+      for (void* q : tmpf) dfree(h, q);
+    }
+    // selection and certification against the FP64 count (joined here)
+    HK_CUDA(cudaStreamWaitEvent(st, inertia_done, 0));
+    k_select<<<ns, 32, 0, st>>>(d_cnt, d_lamref, h->p.tau, d_neg, d_sel, d_m, h->d_lam, d_fail, h->d_status);
+    HK_COUNT_LAUNCH();
+    HK_LAUNCH_CHECK();
+    std::vector<int> fail(ns);
+    HK_CUDA(cudaMemcpyAsync(fail.data(), d_fail, 4 * ns, cudaMemcpyDeviceToHost, st));
+    HK_CUDA(cudaStreamSynchronize(st));
+    int nfail = 0, first = -1;
+    for (int s = 0; s < ns; ++s)
+      if (fail[s]) {
+        ++nfail;
+        if (first < 0) first = s;
+      }
+    if (nfail == 0) break;
+    if (attempt == 1) {
+      hk_set_error("eigen: %d subdomain(s), first %d: the refined eigenvalues below tau do not match the FP64 "
+                   "inertia count (even with a %d-column Krylov basis)", nfail, first, LZ_BASIS_MAX);
+      return HK_EIG_FAIL;
+    }
+    // the failed subdomains again with the largest basis; every subdomain is then refined again (the
+    // others reproduce their results: the refinement is deterministic)
+    for (int s = 0; s < ns; ++s) cols[s] = fail[s] ? LZ_BASIS_MAX : 0;
+    float ms = 0;
+    HK_TRY(eigen_lanczos(h, op, cols, LZ_BASIS_MAX, h->p.tau + HK_EIG_DELTA, d_lamhat, d_cnt, &ms));
+    HK_TRY(check_device_status(h, "eigen: Lanczos candidates"));
+    h->eigen_ms[1] += ms;
   }
-  int *d_sel = nullptr, *d_m = nullptr;
-  HK_TRY(dalloc(h, &d_sel, (size_t)ns * HK_MAXM));
-  HK_TRY(dalloc(h, &d_m, ns));
-  k_select<<<ns, 32, 0, st>>>(d_cnt, d_lamref, h->p.tau, d_neg, d_sel, d_m, h->d_lam, h->d_status);
-  HK_COUNT_LAUNCH();
-  HK_LAUNCH_CHECK();
+  {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    h->eigen_ms[0] = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(inertia_done);
+  }
   HK_TRY(check_device_status(h, "eigen: selection"));
   std::vector<int> m(ns);
   HK_CUDA(cudaMemcpyAsync(m.data(), d_m, 4 * ns, cudaMemcpyDeviceToHost, st));
@@ -738,7 +782,7 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   }
   HK_CUDA(cudaStreamSynchronize(st));
   void* tmp[] = {d_ws, d_Gw, d_cnt, d_o_off, d_neg, d_lamhat, d_lamref, d_O, d_okind, d_Operm, d_Olev, d_Olevptr,
-                 d_OL, d_ocnt, d_o2i, d_ocol, d_oB, d_oC, d_P, d_poff, d_sel, d_m};
+                 d_OL, d_ocnt, d_o2i, d_ocol, d_oB, d_oC, d_P, d_poff, d_sel, d_m, d_fail};
   for (void* p : tmp) dfree(h, p);
   return HK_OK;
 }

@@ -280,12 +280,14 @@ struct OvdofPencil {
   std::vector<int> h_off, h_nO, h_L;   // host copies: first row, rows, levels per subdomain
   std::vector<int> h_levptr;           // host copy of the level pointers
 };
-// #{lambda < tau} per subdomain (FP64 inertia of B^N - tau C), into d_neg.
+// #{lambda < tau} per subdomain (FP64 inertia of B^N - tau C), into d_neg, on stream st (which must
+// follow the setup stream's work up to the pencil).
 hk_status eigen_inertia(hk_handle* h, const OvdofPencil& op, double tau, int* d_neg, cudaStream_t st);
-// Candidate eigenvalues below lam_cut per subdomain (FP32 shift-invert block Lanczos), ascending, into
-// d_lamhat (HK_MAXM per subdomain) and their number into d_cnt; neg: the counts of eigen_inertia, which
-// size each subdomain's Krylov basis.  *ms: the kernel's time.
-hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<int>& neg, double lam_cut,
+// Candidate eigenvalues below lam_cut (FP32 shift-invert block Lanczos), ascending, into d_lamhat (HK_MAXM
+// per subdomain) and their number into d_cnt, for every subdomain s with cols[s] > 0 (the largest Krylov
+// basis; the others are left as they are).  The basis starts at cols0 columns and grows to 4 c + 48 (c the
+// candidates counted) when that is larger.  *ms: the kernel's time.
+hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<int>& cols, int cols0, double lam_cut,
                         double* d_lamhat, int* d_cnt, float* ms);
 
 // ---- phases (each file implements one) ----

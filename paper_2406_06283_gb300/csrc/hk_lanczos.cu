@@ -26,6 +26,7 @@
 //    is formed from the stored products Op Q, reduced to tridiagonal form by Householder reflections in
 //    FP64 and its eigenvalues above 1 / (tau + delta - sigma) found by bisection on Sturm counts.  The
 //    candidates lambda = sigma + 1 / theta go to the FP64 refinement of hk_eigen.cu.
+#include <algorithm>
 #include <cmath>
 
 #include "hk_internal.cuh"
@@ -75,30 +76,28 @@ __device__ __forceinline__ float lz_hash_unit(unsigned long long x) {
 
 // In-place inverse of the b x b row-major matrix A (shared or global memory) by Gauss-Jordan
 // elimination without pivoting.  For a symmetric positive definite A the pivots are the diagonal of its
-// LDL^T factorisation, all positive; the smallest one is returned through *minpiv (thread 0).
+// LDL^T factorisation, all positive; the smallest one is returned through *minpiv (thread 0).  Two
+// barriers per pivot: the other rows are eliminated with the unscaled pivot row, then the pivot row and
+// column are scaled.
 template <typename T>
 __device__ void gj_inverse_nopiv(T* A, int b, T* sh_inv, double* minpiv) {
   int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, nw = NT >> 5;
+  (void)sh_inv;
+  __syncthreads();
   for (int k = 0; k < b; ++k) {
-    if (tid == 0) {
-      T pv = A[k * b + k];
-      if ((double)pv < *minpiv) *minpiv = (double)pv;
-      *sh_inv = pv > (T)0 ? (T)1 / pv : (T)0;
-      A[k * b + k] = (T)1;
-    }
-    __syncthreads();
-    T inv = *sh_inv;
-    for (int c = tid; c < b; c += NT) A[k * b + c] *= inv;
-    __syncthreads();
+    T pv = A[k * b + k];
+    T inv = pv > (T)0 ? (T)1 / pv : (T)0;
+    if (tid == 0 && (double)pv < *minpiv) *minpiv = (double)pv;
     for (int i = tid >> 5; i < b; i += nw) {
       if (i == k) continue;
-      T g = A[i * b + k];
+      T g = A[i * b + k] * inv;
       for (int c = lane; c < b; c += 32)
         if (c != k) A[i * b + c] -= g * A[k * b + c];
     }
     __syncthreads();
+    for (int c = tid; c < b; c += NT) A[k * b + c] = c == k ? inv : A[k * b + c] * inv;
     for (int i = tid; i < b; i += NT)
-      if (i != k) A[i * b + k] = -A[i * b + k] * A[k * b + k];
+      if (i != k) A[i * b + k] = -A[i * b + k] * inv;
     __syncthreads();
   }
 }
@@ -163,13 +162,27 @@ __device__ double lz_factor(const OPen& P, double sigma, T* F, T* Ssm, T* sh_inv
   return *sh_min;
 }
 
+__device__ __forceinline__ unsigned lz_smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+// Asynchronous 4-byte global -> shared copies (cp.async), one commit group per staged block.
+__device__ __forceinline__ void lz_stage(float* dst, const float* src, int n) {
+  for (int e = threadIdx.x; e < n; e += blockDim.x)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(lz_smem_u32(dst + e)), "l"(src + e) : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void lz_stage_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // Y = M^{-1} Y for LZ_P vectors (row-major nO x LZ_P, in shared memory) with the factors of lz_factor:
 // forward  t_j = y_j - M_{j,j-1} y_{j-1},  y_j = S_j^{-1} t_j;  backward  y_j -= X_j y_{j+1}.
-// tv: max_b x LZ_P shared scratch.
-template <typename T>
-__device__ void lz_solve(const OPen& P, double sigma, const T* __restrict__ F, T* Y, T* tv) {
+// tv: max_b x LZ_P shared scratch.  Fb: two shared buffers of max_b^2 floats (or null): each level's
+// block is then copied in by cp.async while the previous level computes, and read from shared memory.
+__device__ void lz_solve(const OPen& P, double sigma, const float* __restrict__ F, float* Y, float* tv, float* Fb,
+                         int max_b) {
   int tid = threadIdx.x, NT = blockDim.x;
+  long long mb2 = (long long)max_b * max_b;
   long long fo = 0;
+  if (Fb) lz_stage(Fb, F, (P.lp[1] - P.lp[0]) * (P.lp[1] - P.lp[0]));
   for (int j = 0; j < P.L; ++j) {
     int r0 = P.lp[j], b = P.lp[j + 1] - r0, bn = j + 1 < P.L ? P.lp[j + 2] - P.lp[j + 1] : 0;
     for (int e = tid; e < b * LZ_P; e += NT) {
@@ -179,45 +192,78 @@ __device__ void lz_solve(const OPen& P, double sigma, const T* __restrict__ F, T
       const double* bv = P.B + (long long)a * P.maxrow;
       const double* cv = P.C + (long long)a * P.maxrow;
       int c_n = min(P.cnt[a], P.maxrow);
-      T acc = Y[a * LZ_P + pc];
+      float acc = Y[a * LZ_P + pc];
       for (int q2 = 0; q2 < c_n; ++q2) {
         int c = cl[q2];
-        if (c < r0) acc -= (T)(bv[q2] - sigma * cv[q2]) * Y[c * LZ_P + pc];
+        if (c < r0) acc -= (float)(bv[q2] - sigma * cv[q2]) * Y[c * LZ_P + pc];
       }
       tv[e] = acc;
     }
+    if (Fb) lz_stage_wait();
     __syncthreads();
+    const float* Sb = Fb ? Fb + (j & 1) * mb2 : F + fo;
+    long long fn = fo + (long long)b * b + (long long)b * bn;
+    if (Fb && j + 1 < P.L) {
+      int b1 = bn;
+      lz_stage(Fb + ((j + 1) & 1) * mb2, F + fn, b1 * b1);
+    }
     for (int e = tid; e < b * LZ_P; e += NT) {
       int q = e / LZ_P, pc = e - q * LZ_P;
-      const T* Sr = F + fo + (long long)q * b;
-      T acc = 0;
-      for (int c = 0; c < b; ++c) acc += Sr[c] * tv[c * LZ_P + pc];
-      Y[(r0 + q) * LZ_P + pc] = acc;
+      const float* Sr = Sb + (long long)q * b;
+      float acc0 = 0.f, acc1 = 0.f;
+      int c = 0;
+      for (; c + 1 < b; c += 2) {
+        acc0 += Sr[c] * tv[c * LZ_P + pc];
+        acc1 += Sr[c + 1] * tv[(c + 1) * LZ_P + pc];
+      }
+      if (c < b) acc0 += Sr[c] * tv[c * LZ_P + pc];
+      Y[(r0 + q) * LZ_P + pc] = acc0 + acc1;
     }
     __syncthreads();
-    fo += (long long)b * b + (long long)b * bn;
+    fo = fn;
   }
+  if (P.L < 2) return;
+  // fo is now the end of the factors; walk back to level L - 2
+  long long fj;
   {
-    int bl = P.lp[P.L] - P.lp[P.L - 1];
-    fo -= (long long)bl * bl;
+    int bl = P.lp[P.L] - P.lp[P.L - 1], b2 = P.lp[P.L - 1] - P.lp[P.L - 2];
+    fj = fo - (long long)bl * bl - ((long long)b2 * b2 + (long long)b2 * bl);  // level L - 2's offset
   }
-  for (int j = P.L - 2; j >= 0; --j) {
+  if (Fb) {
+    int b = P.lp[P.L - 1] - P.lp[P.L - 2], bn = P.lp[P.L] - P.lp[P.L - 1];
+    lz_stage(Fb, F + fj + (long long)b * b, b * bn);
+  }
+  for (int j = P.L - 2, it = 0; j >= 0; --j, ++it) {
     int r0 = P.lp[j], b = P.lp[j + 1] - r0, r1 = P.lp[j + 1], bn = P.lp[j + 2] - r1;
-    fo -= (long long)b * b + (long long)b * bn;
-    const T* Xm = F + fo + (long long)b * b;
+    if (Fb) lz_stage_wait();
+    __syncthreads();
+    const float* Xm = Fb ? Fb + (it & 1) * mb2 : F + fj + (long long)b * b;
+    long long fp = 0;
+    if (j > 0) {
+      int bp = P.lp[j] - P.lp[j - 1];
+      fp = fj - ((long long)bp * bp + (long long)bp * b);
+      if (Fb) lz_stage(Fb + ((it + 1) & 1) * mb2, F + fp + (long long)bp * bp, bp * b);
+    }
     for (int e = tid; e < b * LZ_P; e += NT) {
       int q = e / LZ_P, pc = e - q * LZ_P;
-      T acc = 0;
-      for (int c = 0; c < bn; ++c) acc += Xm[(long long)q * bn + c] * Y[(r1 + c) * LZ_P + pc];
-      tv[e] = acc;
+      const float* Xr = Xm + (long long)q * bn;
+      float acc0 = 0.f, acc1 = 0.f;
+      int c = 0;
+      for (; c + 1 < bn; c += 2) {
+        acc0 += Xr[c] * Y[(r1 + c) * LZ_P + pc];
+        acc1 += Xr[c + 1] * Y[(r1 + c + 1) * LZ_P + pc];
+      }
+      if (c < bn) acc0 += Xr[c] * Y[(r1 + c) * LZ_P + pc];
+      tv[e] = acc0 + acc1;
     }
     __syncthreads();
     for (int e = tid; e < b * LZ_P; e += NT) {
       int q = e / LZ_P, pc = e - q * LZ_P;
       Y[(r0 + q) * LZ_P + pc] -= tv[e];
     }
-    __syncthreads();
+    fj = fp;
   }
+  __syncthreads();
 }
 
 // Y_out = C Y_in for LZ_P vectors (row-major nO x LZ_P); in and out distinct.
@@ -329,37 +375,63 @@ __device__ float lz_cnorm_col(const OPen& P, const float* Y, float* CY, int pc, 
   return sqrtf(fmaxf(nv[0], 0.f));
 }
 
-// C-orthonormalises the columns of Y (modified Gram-Schmidt inside the block, twice, after the block
-// has been orthogonalised against the earlier blocks) and leaves C Y in CY.  ref[pc]: C-norm of column
-// pc before any orthogonalisation.  A column whose C-norm falls below 1e-4 of it has collapsed into the
-// span already built: it is replaced by a seeded vector, orthogonalised twice against every earlier
-// block and column; if that keeps less than 1e-3 of its own norm, the column is set to zero (it then
-// adds only a zero row and column to the Rayleigh quotient).
+// Projects column pc of Y (and of CY = C Y) against the C-orthonormal columns 0 .. pc-1 of the same block:
+// one fused reduction gives their C inner products with Y_pc and Y_pc's own C-norm squared.  Returns the
+// C-norm after the projection (all threads).
+__device__ float lz_project_in_block(const OPen& P, float* Y, float* CY, int pc, float* red, float* before) {
+  float v[LZ_P] = {0.f, 0.f, 0.f, 0.f};
+  for (int a = threadIdx.x; a < P.nO; a += blockDim.x) {
+    float y = Y[a * LZ_P + pc];
+    for (int q = 0; q < pc; ++q) v[q] += CY[a * LZ_P + q] * y;
+    v[LZ_P - 1] += CY[a * LZ_P + pc] * y;
+  }
+  lz_block_sums<LZ_P>(v, red);
+  float n2 = v[LZ_P - 1];
+  for (int q = 0; q < pc; ++q) n2 -= v[q] * v[q];
+  if (before) *before = sqrtf(fmaxf(v[LZ_P - 1], 0.f));
+  if (pc > 0) {
+    for (int a = threadIdx.x; a < P.nO; a += blockDim.x) {
+      float y = Y[a * LZ_P + pc], cy = CY[a * LZ_P + pc];
+      for (int q = 0; q < pc; ++q) {
+        y -= v[q] * Y[a * LZ_P + q];
+        cy -= v[q] * CY[a * LZ_P + q];
+      }
+      Y[a * LZ_P + pc] = y;
+      CY[a * LZ_P + pc] = cy;
+    }
+    __syncthreads();
+  }
+  return sqrtf(fmaxf(n2, 0.f));
+}
+
+// C-orthonormalises the columns of Y (after the block has been orthogonalised against the earlier
+// blocks) and leaves C Y in CY.  C Y is formed once and then updated with Y.  Per column: a projection
+// against the earlier columns of the block, repeated once when it removed more than half of the column
+// (classical Gram-Schmidt twice), then a scaling.  ref[pc]: C-norm of column pc before any
+// orthogonalisation.  A column whose C-norm falls below 1e-4 of it has collapsed into the span already
+// built: it is replaced by a seeded vector, orthogonalised twice against every earlier block and column;
+// if that keeps less than 1e-3 of its own norm, the column is set to zero (it then adds only a zero row
+// and column to the Rayleigh quotient).
 __device__ void lz_orthonormalise(const OPen& P, int s, int blk, int nb, const float* Qg, const float* CQg, float* Y,
                                   float* CY, const float* ref, float* coef, float* red) {
+  lz_cmul(P, Y, CY);
+  __syncthreads();
   for (int pc = 0; pc < LZ_P; ++pc) {
     float r0 = ref[pc];
     for (int attempt = 0; attempt < 2; ++attempt) {
       if (attempt == 1) {
         lz_seed_column(P, s, blk, pc, 1, Y);
         __syncthreads();
-        r0 = lz_cnorm_col(P, Y, CY, pc, red);
-        // the other columns are orthogonal to the earlier blocks already: the passes change them only
-        // by rounding
+        r0 = lz_cnorm_col(P, Y, CY, pc, red);  // of the raw seed
+        // the other columns are orthogonal to the earlier blocks already: the passes change them only by
+        // rounding; column pc's C Y is formed again afterwards
         lz_cgs_pass(P.nO, nb, Qg, CQg, Y, coef);
         lz_cgs_pass(P.nO, nb, Qg, CQg, Y, coef);
+        lz_cnorm_col(P, Y, CY, pc, red);
       }
-      float nrm = lz_cnorm_col(P, Y, CY, pc, red);
-      for (int rep = 0; rep < 2 && pc > 0; ++rep) {
-        float d[LZ_P - 1] = {0.f, 0.f, 0.f};
-        for (int a = threadIdx.x; a < P.nO; a += blockDim.x)
-          for (int q = 0; q < pc; ++q) d[q] += CY[a * LZ_P + q] * Y[a * LZ_P + pc];
-        lz_block_sums<LZ_P - 1>(d, red);
-        for (int a = threadIdx.x; a < P.nO; a += blockDim.x)
-          for (int q = 0; q < pc; ++q) Y[a * LZ_P + pc] -= d[q] * Y[a * LZ_P + q];
-        __syncthreads();
-        nrm = lz_cnorm_col(P, Y, CY, pc, red);
-      }
+      float before = 0.f;
+      float nrm = lz_project_in_block(P, Y, CY, pc, red, &before);
+      if (pc > 0 && nrm < 0.5f * before) nrm = lz_project_in_block(P, Y, CY, pc, red, nullptr);
       bool ok = nrm > (attempt == 0 ? 1e-4f : 1e-3f) * r0 && nrm > 0.f;
       if (ok || attempt == 1) {
         float inv = ok ? 1.f / nrm : 0.f;
@@ -374,54 +446,59 @@ __device__ void lz_orthonormalise(const OPen& P, int s, int blk, int nb, const f
   }
 }
 
-// Number of eigenvalues below x of the symmetric tridiagonal matrix (d, e) (Sturm count).
-__device__ int lz_sturm_below(const double* d, const double* e, int n, double x, double pivmin) {
+// Number of eigenvalues below x of the symmetric tridiagonal matrix with diagonal d and squared
+// off-diagonal e2 (Sturm count, FP32).
+__device__ int lz_sturm_below32(const float* d, const float* e2, int n, float x, float pivmin) {
   int c = 0;
-  double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  c += q < 0.0;
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  c += q < 0.f;
   for (int i = 1; i < n; ++i) {
-    q = d[i] - x - e[i - 1] * e[i - 1] / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    c += q < 0.0;
+    q = d[i] - x - e2[i - 1] / q;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    c += q < 0.f;
   }
   return c;
 }
 
 // One CTA per subdomain.  Dynamic shared memory: Y (max_nO x 4) | C Y (max_nO x 4) | sweep scratch
-// (max_b x 4) | the working block of the factorisation (max_b^2, when s_in_smem); once the Krylov steps
-// are done the Rayleigh quotient (N x N doubles, N = 4 kdim[s]) reuses the same bytes.
-// Global workspace per subdomain: the factors (F + f_off[s]) and the basis Q, C Q and Op Q
-// (3 kdim[s] blocks of nO x 4, Qw + q_off[s]).
+// (max_b x 4) | the working block of the factorisation (max_b^2, when s_in_smem) | two staging buffers of
+// the sweeps (2 max_b^2, when use_fb); once the Krylov steps are done the Rayleigh quotient (N x N
+// doubles, N = 4 kdim[s]) reuses the same bytes.
+// CTA i works on subdomain sub_list[i].  Global workspace per subdomain: the factors (F + f_off[s]) and
+// the basis Q, C Q and Op Q (3 kdim[s] blocks of nO x 4, Qw + q_off[s]).
 // Outputs: lam_hat[s * HK_MAXM + t] = the candidates below lam_cut in ascending order, cnt_out[s] their
 // number, sigma_out[s] the shift used.
-__global__ void __launch_bounds__(LZ_THREADS) k_lanczos(
+__global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
     const int* __restrict__ sub_info, const int* __restrict__ o_off, const int* __restrict__ O_levptr,
     const int* __restrict__ O_L, int maxrow, const int* __restrict__ ocnt, const int* __restrict__ ocol,
     const double* __restrict__ oB, const double* __restrict__ oC, const int* __restrict__ o2i,
-    const int* __restrict__ kdim, const long long* __restrict__ f_off, float* F, const long long* __restrict__ q_off,
-    float* Qw, int max_nO, int max_b, int s_in_smem, double sigma0, double lam_cut, double* lam_hat, int* cnt_out,
-    double* sigma_out, DevStatus* st) {
+    const int* __restrict__ sub_list, const int* __restrict__ kdim, const long long* __restrict__ f_off, float* F,
+    const long long* __restrict__ q_off,
+    float* Qw, int max_nO, int max_b, int s_in_smem, int use_fb, int nb0, double sigma0, double lam_cut,
+    double* lam_hat, int* cnt_out, double* sigma_out, DevStatus* st) {
   extern __shared__ __align__(16) unsigned char lz_smem[];
   __shared__ float coef[LZ_MAX_DIM * LZ_P];
+  __shared__ float d32[LZ_MAX_DIM], e32[LZ_MAX_DIM];
   __shared__ float red[32 * LZ_P];
   __shared__ float ref[LZ_P];
   __shared__ float sh_inv;
   __shared__ double sh_min, sh_scal[4];
   __shared__ double hd[LZ_MAX_DIM], he[LZ_MAX_DIM], hv[LZ_MAX_DIM], hp[LZ_MAX_DIM];
-  int s = blockIdx.x, tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = NT >> 5;
+  int s = sub_list[blockIdx.x], tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = NT >> 5;
   OPen P = open_sub(s, o_off, O_levptr, O_L, maxrow, ocnt, ocol, oB, oC, o2i, sub_info);
   float* Ys = reinterpret_cast<float*>(lz_smem);
   float* CYs = Ys + (long long)max_nO * LZ_P;
   float* tv = CYs + (long long)max_nO * LZ_P;
   float* Ssm = s_in_smem ? tv + (long long)max_b * LZ_P : nullptr;
+  float* Fb = use_fb ? (Ssm ? Ssm : tv + (long long)max_b * LZ_P) + (s_in_smem ? (long long)max_b * max_b : 0) : nullptr;
   double* Tm = reinterpret_cast<double*>(lz_smem);
   float* Fs = F + f_off[s];
-  int nb = kdim[s];
+  int nb_max = kdim[s], nb = min(nb0, nb_max);
   long long bs = (long long)P.nO * LZ_P;
   float* Qg = Qw + q_off[s];
-  float* CQg = Qg + nb * bs;
-  float* Wg = CQg + nb * bs;
+  float* CQg = Qg + nb_max * bs;
+  float* Wg = CQg + nb_max * bs;
 
   // 1. a shift below the spectrum: M = B^N - sigma C positive definite
   double sigma = sigma0, step = 0.5, upper = 0.0;
@@ -480,14 +557,19 @@ __global__ void __launch_bounds__(LZ_THREADS) k_lanczos(
   }
   __syncthreads();
 
-  // 3. Krylov steps: W_k = Op Q_k, Q_{k+1} from W_k orthogonalised against Q_0 .. Q_k
-  for (int k = 0; k < nb; ++k) {
+  // 3. Krylov steps: W_k = Op Q_k, Q_{k+1} from W_k orthogonalised against Q_0 .. Q_k.  After nb blocks the
+  // candidates below lam_cut are counted (steps 4 and 5); when a count c asks for more than the 4 nb
+  // columns built (4 c + 48), the same sequence continues, up to nb_max blocks, and steps 4-5 repeat.
+  int k_done = 0, N = 0;
+  double th_hi_d = 0, pivmin_d = 0;
+  while (true) {
+  for (int k = k_done; k < nb; ++k) {
     for (long long e = tid; e < bs; e += NT) Ys[e] = CQg[k * bs + e];
     __syncthreads();
-    lz_solve<float>(P, sigma, Fs, Ys, tv);
+    lz_solve(P, sigma, Fs, Ys, tv, Fb, max_b);
     for (long long e = tid; e < bs; e += NT) Wg[k * bs + e] = Ys[e];
     __syncthreads();
-    if (k == nb - 1) break;
+    if (k == nb_max - 1) break;
     for (int pc = 0; pc < LZ_P; ++pc) {
       float r = lz_cnorm_col(P, Ys, CYs, pc, red);
       if (tid == 0) ref[pc] = r;
@@ -503,8 +585,9 @@ __global__ void __launch_bounds__(LZ_THREADS) k_lanczos(
     __syncthreads();
   }
 
+  k_done = nb;
   // 4. Rayleigh quotient T = Q^T C (Op Q), a warp per pair of blocks; then symmetrised (FP64)
-  int N = nb * LZ_P;
+  N = nb * LZ_P;
   for (int pr = warp; pr < nb * nb; pr += nw) {
     int bi = pr / nb, bj = pr - bi * nb;
     const float4* cq = reinterpret_cast<const float4*>(CQg + bi * bs);
@@ -542,25 +625,30 @@ __global__ void __launch_bounds__(LZ_THREADS) k_lanczos(
   }
   __syncthreads();
 
-  // 5. Householder reduction of T to tridiagonal form (diagonal hd, off-diagonal he)
+  // 5. Householder reduction of T to tridiagonal form (diagonal hd, off-diagonal he); warp 0 forms the
+  // reflection's scalars by lane-parallel sums
   for (int k = 0; k + 2 < N; ++k) {
-    if (tid == 0) {
-      double x0 = Tm[(k + 1) * N + k], ss = 0;
-      for (int i = k + 2; i < N; ++i) ss += Tm[i * N + k] * Tm[i * N + k];
-      hd[k] = Tm[k * N + k];
-      if (ss == 0.0) {
-        he[k] = x0;
-        sh_scal[0] = 0.0;
-      } else {
-        double nrm = sqrt(x0 * x0 + ss), alpha = x0 > 0 ? -nrm : nrm, v0 = x0 - alpha;
-        he[k] = alpha;
-        sh_scal[0] = 2.0 / (v0 * v0 + ss);
-        hv[k + 1] = v0;
+    if (warp == 0) {
+      double ss = 0;
+      for (int i = k + 2 + lane; i < N; i += 32) ss += Tm[i * N + k] * Tm[i * N + k];
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      if (lane == 0) {
+        double x0 = Tm[(k + 1) * N + k];
+        hd[k] = Tm[k * N + k];
+        if (ss == 0.0) {
+          he[k] = x0;
+          sh_scal[0] = 0.0;
+        } else {
+          double nrm = sqrt(x0 * x0 + ss), alpha = x0 > 0 ? -nrm : nrm, v0 = x0 - alpha;
+          he[k] = alpha;
+          sh_scal[0] = 2.0 / (v0 * v0 + ss);
+          hv[k + 1] = v0;
+        }
       }
     }
     __syncthreads();
     double beta = sh_scal[0];
-    __syncthreads();  // every thread has read beta before thread 0 may overwrite it
+    __syncthreads();  // every thread has read beta before warp 0 may overwrite it
     if (beta == 0.0) continue;
     for (int i = k + 2 + tid; i < N; i += NT) hv[i] = Tm[i * N + k];
     __syncthreads();
@@ -570,10 +658,11 @@ __global__ void __launch_bounds__(LZ_THREADS) k_lanczos(
       hp[i] = beta * acc;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (warp == 0) {
       double kv = 0;
-      for (int i = k + 1; i < N; ++i) kv += hv[i] * hp[i];
-      sh_scal[1] = 0.5 * beta * kv;
+      for (int i = k + 1 + lane; i < N; i += 32) kv += hv[i] * hp[i];
+      for (int o = 16; o > 0; o >>= 1) kv += __shfl_xor_sync(0xffffffffu, kv, o);
+      if (lane == 0) sh_scal[1] = 0.5 * beta * kv;
     }
     __syncthreads();
     double kc = sh_scal[1];
@@ -593,34 +682,57 @@ __global__ void __launch_bounds__(LZ_THREADS) k_lanczos(
     }
     hd[N - 1] = Tm[(N - 1) * N + N - 1];
     he[N - 1] = 0.0;
-    double lo = 1e300, hi = -1e300, me = 0;
+    double hi = -1e300, me = 0;
     for (int i = 0; i < N; ++i) {
       double r = (i > 0 ? fabs(he[i - 1]) : 0.0) + (i < N - 1 ? fabs(he[i]) : 0.0);
-      lo = fmin(lo, hd[i] - r);
       hi = fmax(hi, hd[i] + r);
       if (i < N - 1) me = fmax(me, he[i] * he[i]);
     }
-    sh_scal[2] = hi + 1e-12 * fabs(hi) + 1e-300;
-    sh_scal[3] = 1e-290 * fmax(1.0, me);
+    sh_scal[2] = hi + 1e-6 * fabs(hi) + 1e-30;
+    sh_scal[3] = 1e-30 * fmax(1.0, me);
+  }
+  __syncthreads();
+  th_hi_d = sh_scal[2];
+  pivmin_d = sh_scal[3];
+  // FP32 copy for the Sturm counts: diagonal and squared off-diagonal (the projected matrix is itself an
+  // FP32 product)
+  for (int i = tid; i < N; i += NT) {
+    d32[i] = (float)hd[i];
+    e32[i] = (float)(he[i] * he[i]);
   }
   __syncthreads();
 
-  // 6. candidates: eigenvalues theta > 1 / (lam_cut - sigma) of T, lambda = sigma + 1 / theta
-  double th_cut = 1.0 / (lam_cut - sigma), th_hi = sh_scal[2], pivmin = sh_scal[3];
-  int cnt = th_cut >= th_hi ? 0 : N - lz_sturm_below(hd, he, N, th_cut, pivmin);
+  float th_cut = (float)(1.0 / (lam_cut - sigma)), th_hi = (float)th_hi_d, pivmin = (float)pivmin_d;
+  int cnt = th_cut >= th_hi ? 0 : N - lz_sturm_below32(d32, e32, N, th_cut, pivmin);
+  int need = (4 * cnt + 48 + LZ_P - 1) / LZ_P;
+  __syncthreads();  // every thread has its count before the buffers are reused
+  if (need <= nb || nb >= nb_max) break;
+  nb = min(nb_max, need);
+  }  // extension loop
+
+  // 6. candidates: eigenvalues theta > 1 / (lam_cut - sigma) of T, lambda = sigma + 1 / theta, each found by
+  // a warp by 32-way multisection on FP32 Sturm counts down to 2e-7 of the spectral scale
+  float th_cut = (float)(1.0 / (lam_cut - sigma)), th_hi = (float)th_hi_d, pivmin = (float)pivmin_d;
+  int cnt = th_cut >= th_hi ? 0 : N - lz_sturm_below32(d32, e32, N, th_cut, pivmin);
   if (tid == 0) {
     cnt_out[s] = cnt;
     if (cnt > HK_MAXM) dev_fail(st, HK_UNSUPPORTED, s, cnt);
   }
-  for (int t = tid; t < cnt && t < HK_MAXM; t += NT) {
+  float tol = 2e-7f * fmaxf(fabsf(th_hi), fabsf(th_cut));
+  for (int t = warp; t < cnt && t < HK_MAXM; t += nw) {
     int kidx = N - 1 - t;  // ascending index of the t-th largest theta
-    double lo = th_cut, hi = th_hi;
-    for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
-      double mid = 0.5 * (lo + hi);
-      if (lz_sturm_below(hd, he, N, mid, pivmin) > kidx) hi = mid;
-      else lo = mid;
+    float lo = th_cut, hi = th_hi;
+    for (int it = 0; it < 12 && hi - lo > tol; ++it) {
+      float x = lo + (hi - lo) * (float)(lane + 1) / 33.f;
+      int below = lz_sturm_below32(d32, e32, N, x, pivmin) > kidx;  // eigenvalue kidx lies below x
+      unsigned mask = __ballot_sync(0xffffffffu, below);
+      int first = mask ? __ffs(mask) - 1 : 32;
+      float nlo = first == 0 ? lo : lo + (hi - lo) * (float)first / 33.f;
+      float nhi = first == 32 ? hi : lo + (hi - lo) * (float)(first + 1) / 33.f;
+      lo = nlo;
+      hi = nhi;
     }
-    lam_hat[(long long)s * HK_MAXM + t] = sigma + 1.0 / (0.5 * (lo + hi));
+    if (lane == 0) lam_hat[(long long)s * HK_MAXM + t] = sigma + 1.0 / (0.5 * ((double)lo + (double)hi));
   }
 }
 
@@ -845,11 +957,14 @@ hk_status eigen_inertia(hk_handle* h, const OvdofPencil& op, double tau, int* d_
   if (!in_smem) {
     std::vector<long long> wo(ns);
     for (int s = 0; s < ns; ++s) wo[s] = 4LL * op.max_b * op.max_b * s;
+    // allocated on the setup stream, which the caller has forked the inertia stream from afterwards
     HK_TRY(dalloc(h, &d_ws, 4ULL * op.max_b * op.max_b * ns));
     HK_TRY(dalloc(h, &d_wo, ns));
     HK_CUDA(cudaMemcpyAsync(d_wo, wo.data(), 8 * ns, cudaMemcpyHostToDevice, h->stream));
-    HK_CUDA(cudaEventRecord(h->ev_fork, h->stream));
-    HK_CUDA(cudaStreamWaitEvent(st, h->ev_fork, 0));
+    if (st != h->stream) {
+      HK_CUDA(cudaEventRecord(h->ev_fork, h->stream));
+      HK_CUDA(cudaStreamWaitEvent(st, h->ev_fork, 0));
+    }
   }
   HK_TRY(hk_allow_smem(k_inertia));
   k_inertia<<<ns, 256, in_smem ? need : 0, st>>>(h->d_sub_info, op.o_off, op.levptr, op.L, op.maxrow, op.cnt, op.col,
@@ -857,28 +972,36 @@ hk_status eigen_inertia(hk_handle* h, const OvdofPencil& op, double tau, int* d_
   HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   if (!in_smem) {
-    // freed on the handle's stream once the kernel is done
-    HK_CUDA(cudaEventRecord(h->ev_join, st));
-    HK_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-    dfree(h, d_ws);
-    dfree(h, d_wo);
+    // freed on the inertia stream once the kernel is done (stream-ordered)
+    h->allocs.erase(std::remove_if(h->allocs.begin(), h->allocs.end(),
+                                   [&](const std::pair<void*, size_t>& a) {
+                                     if (a.first == d_ws || a.first == d_wo) {
+                                       h->bytes -= a.second;
+                                       return true;
+                                     }
+                                     return false;
+                                   }),
+                    h->allocs.end());
+    cudaFreeAsync(d_ws, st);
+    cudaFreeAsync(d_wo, st);
   }
   return HK_OK;
 }
 
-hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<int>& neg, double lam_cut,
-                        double* d_lamhat, int* d_cnt, float* ms) {
+hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<int>& cols, int cols0,
+                        double lam_cut, double* d_lamhat, int* d_cnt, float* ms) {
   cudaStream_t st = h->stream;
   int ns = h->n_sub;
-  std::vector<int> kd(ns);
-  std::vector<long long> fo(ns), qo(ns);
+  std::vector<int> kd(ns, 0), list;
+  std::vector<long long> fo(ns, 0), qo(ns, 0);
   long long ftot = 0, qtot = 0;
   int kmax = 1;
   for (int s = 0; s < ns; ++s) {
-    // basis of 4 m + 48 columns (m = the certified count below tau), 32 to LZ_MAX_DIM: enough for the
-    // candidates to reach the FP32 floor (about 1e-7) when m is about 20 eigenvalues with gaps near 1e-3
-    int cols = std::min(LZ_MAX_DIM, std::max(32, 4 * neg[s] + 48));
-    kd[s] = (cols + LZ_P - 1) / LZ_P;
+    if (cols[s] <= 0) continue;
+    list.push_back(s);
+    // no more columns than the dof space holds (plus a block for the collapsed ones)
+    int c = std::min(std::min(LZ_MAX_DIM, cols[s]), 4 * ((h->subs[s].nI + 3) / 4) + 4);
+    kd[s] = std::max(2, (c + LZ_P - 1) / LZ_P);
     kmax = std::max(kmax, kd[s]);
     const int* lp = &op.h_levptr[op.h_off[s] + s];
     long long f = 0;
@@ -891,24 +1014,30 @@ hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<i
     qo[s] = qtot;
     qtot += 3LL * kd[s] * op.h_nO[s] * LZ_P;
   }
-  int *d_kd = nullptr;
+  *ms = 0;
+  if (list.empty()) return HK_OK;
+  int nl = (int)list.size();
+  int *d_kd = nullptr, *d_list = nullptr;
   long long *d_fo = nullptr, *d_qo = nullptr;
   float *d_F = nullptr, *d_Q = nullptr;
   double* d_sig = nullptr;
   HK_TRY(dalloc(h, &d_kd, ns));
+  HK_TRY(dalloc(h, &d_list, nl));
   HK_TRY(dalloc(h, &d_fo, ns));
   HK_TRY(dalloc(h, &d_qo, ns));
   HK_TRY(dalloc(h, &d_F, ftot));
   HK_TRY(dalloc(h, &d_Q, qtot));
   HK_TRY(dalloc(h, &d_sig, ns));
   HK_CUDA(cudaMemcpyAsync(d_kd, kd.data(), 4 * ns, cudaMemcpyHostToDevice, st));
+  HK_CUDA(cudaMemcpyAsync(d_list, list.data(), 4 * nl, cudaMemcpyHostToDevice, st));
   HK_CUDA(cudaMemcpyAsync(d_fo, fo.data(), 8 * ns, cudaMemcpyHostToDevice, st));
   HK_CUDA(cudaMemcpyAsync(d_qo, qo.data(), 8 * ns, cudaMemcpyHostToDevice, st));
   size_t vec = sizeof(float) * LZ_P * (2 * (size_t)op.max_nO + op.max_b);
   size_t sblk = sizeof(float) * (size_t)op.max_b * op.max_b;
   size_t tmat = sizeof(double) * (size_t)(kmax * LZ_P) * (kmax * LZ_P);
   int s_in_smem = vec + sblk <= 200 * 1024;
-  size_t shm = std::max(vec + (s_in_smem ? sblk : 0), tmat);
+  int use_fb = vec + (s_in_smem ? sblk : 0) + 2 * sblk <= 200 * 1024;
+  size_t shm = std::max(vec + (s_in_smem ? sblk : 0) + (use_fb ? 2 * sblk : 0), tmat);
   if (shm > 220 * 1024) {
     hk_set_error("subdomain with %d ovdof rows too large for the Lanczos kernel's shared memory", op.max_nO);
     return HK_UNSUPPORTED;
@@ -918,9 +1047,10 @@ hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<i
   HK_CUDA(cudaEventCreate(&e0));
   HK_CUDA(cudaEventCreate(&e1));
   cudaEventRecord(e0, st);
-  k_lanczos<<<ns, LZ_THREADS, shm, st>>>(h->d_sub_info, op.o_off, op.levptr, op.L, op.maxrow, op.cnt, op.col, op.B,
-                                         op.C, op.o2i, d_kd, d_fo, d_F, d_qo, d_Q, op.max_nO, op.max_b, s_in_smem,
-                                         -0.5, lam_cut, d_lamhat, d_cnt, d_sig, h->d_status);
+  k_lanczos<<<nl, LZ_THREADS, shm, st>>>(h->d_sub_info, op.o_off, op.levptr, op.L, op.maxrow, op.cnt, op.col, op.B,
+                                         op.C, op.o2i, d_list, d_kd, d_fo, d_F, d_qo, d_Q, op.max_nO, op.max_b, s_in_smem,
+                                         use_fb, (cols0 + LZ_P - 1) / LZ_P, -0.5, lam_cut, d_lamhat, d_cnt, d_sig,
+                                         h->d_status);
   HK_COUNT_LAUNCH();
   cudaEventRecord(e1, st);
   HK_LAUNCH_CHECK();
@@ -928,7 +1058,7 @@ hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<i
   cudaEventElapsedTime(ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  void* tmp[] = {d_kd, d_fo, d_qo, d_F, d_Q, d_sig};
+  void* tmp[] = {d_kd, d_list, d_fo, d_qo, d_F, d_Q, d_sig};
   for (void* p : tmp) dfree(h, p);
   return HK_OK;
 }
