@@ -138,6 +138,8 @@ typedef struct {
                                   graphs switched off by hk_set_solve_graphs) */
   double eigen_kernel_ms[4];   /* setup kernels of the eigenproblems: [0] FP64 inertia count below tau,
                                   [1] FP32 Lanczos candidates, [2] FP64 refinement, [3] 0 */
+  double eigen_kernel_gflop[4]; /* their algorithmic work in GFLOP (2 per multiply-add of the dense level
+                                  operations: factorisations, sweeps, Gram-Schmidt, projections) */
 } hk_info_t;
 
 hk_status hk_info(const hk_handle* h, hk_info_t* info);

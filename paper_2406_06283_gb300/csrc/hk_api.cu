@@ -370,6 +370,7 @@ extern "C" hk_status hk_info(const hk_handle* h, hk_info_t* info) {
   info->bytes_peak = h->bytes_peak;
   info->graph_solves = h->graph_solves;
   for (int i = 0; i < 4; ++i) info->eigen_kernel_ms[i] = h->eigen_ms[i];
+  for (int i = 0; i < 4; ++i) info->eigen_kernel_gflop[i] = h->eigen_gflop[i];
   return HK_OK;
 }
 

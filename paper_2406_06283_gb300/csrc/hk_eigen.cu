@@ -618,6 +618,7 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   cudaEvent_t inertia_done = nullptr;
   HK_CUDA(cudaEventCreateWithFlags(&inertia_done, cudaEventDisableTiming));
   HK_CUDA(cudaEventRecord(inertia_done, ist));
+  h->eigen_gflop[1] = 0;
   // a basis of 96 columns, grown inside the kernel to 4 c + 48 where c candidates ask for more
   std::vector<int> cols(ns, LZ_BASIS_MAX), cnt(ns);
   std::vector<double> lamhat((size_t)ns * HK_MAXM);
@@ -642,6 +643,7 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
     }
   }
   h->eigen_ms[2] = 0;
+  h->eigen_gflop[2] = 0;
   for (int attempt = 0; attempt < 2; ++attempt) {
     HK_CUDA(cudaMemcpyAsync(cnt.data(), d_cnt, 4 * ns, cudaMemcpyDeviceToHost, st));
     HK_CUDA(cudaMemcpyAsync(lamhat.data(), d_lamhat, sizeof(double) * lamhat.size(), cudaMemcpyDeviceToHost, st));
@@ -681,31 +683,72 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
       }
     }
     int nit = (int)sig.size();
-    if (nit > 0) {
+    // items run in batches whose factor and iterate storage stays below 1 GiB (each item holds the block
+    // LU of its own shifted pencil)
+    const long long batch_bytes = 1LL << 30;
+    for (int i0 = 0; i0 < nit;) {
+      int i1 = i0;
+      long long fb = 0, xb = 0;
+      while (i1 < nit) {
+        long long fi = (i1 + 1 < nit ? foff[i1 + 1] : ftot) - foff[i1];
+        long long xi = (i1 + 1 < nit ? xoff[i1 + 1] : xtot) - xoff[i1];
+        if (i1 > i0 && 8 * (fb + fi + xb + xi) > batch_bytes) break;
+        fb += fi;
+        xb += xi;
+        ++i1;
+      }
+      int nb_it = i1 - i0;
+      std::vector<long long> fo2(nb_it), xo2(nb_it);
+      for (int i = 0; i < nb_it; ++i) {
+        fo2[i] = foff[i0 + i] - foff[i0];
+        xo2[i] = xoff[i0 + i] - xoff[i0];
+      }
       int* d_items = nullptr;
       double *d_sig = nullptr, *d_F = nullptr, *d_X = nullptr;
       long long *d_foff = nullptr, *d_xoff = nullptr;
-      HK_TRY(dalloc(h, &d_items, items.size()));
-      HK_TRY(dalloc(h, &d_sig, nit));
-      HK_TRY(dalloc(h, &d_foff, nit));
-      HK_TRY(dalloc(h, &d_xoff, nit));
-      HK_TRY(dalloc(h, &d_F, ftot));
-      HK_TRY(dalloc(h, &d_X, xtot));
-      HK_CUDA(up(d_items, items.data(), 4 * items.size()));
-      HK_CUDA(up(d_sig, sig.data(), 8 * nit));
-      HK_CUDA(up(d_foff, foff.data(), 8 * nit));
-      HK_CUDA(up(d_xoff, xoff.data(), 8 * nit));
-      size_t rshm = sizeof(double) * ((size_t)maxbO * maxbO + (size_t)maxbO * pmax);
+      HK_TRY(dalloc(h, &d_items, 4 * (size_t)nb_it));
+      HK_TRY(dalloc(h, &d_sig, nb_it));
+      HK_TRY(dalloc(h, &d_foff, nb_it));
+      HK_TRY(dalloc(h, &d_xoff, nb_it));
+      HK_TRY(dalloc(h, &d_F, fb));
+      HK_TRY(dalloc(h, &d_X, xb));
+      HK_CUDA(up(d_items, items.data() + 4 * (size_t)i0, 16 * (size_t)nb_it));
+      HK_CUDA(up(d_sig, sig.data() + i0, 8 * nb_it));
+      HK_CUDA(up(d_foff, fo2.data(), 8 * nb_it));
+      HK_CUDA(up(d_xoff, xo2.data(), 8 * nb_it));
+      int pmax_b = 1;
+      for (int i = i0; i < i1; ++i) pmax_b = std::max(pmax_b, items[4 * i + 2] + HK_GUARD);
+      size_t rshm = sizeof(double) * ((size_t)maxbO * maxbO + (size_t)maxbO * pmax_b);
       int s_in_smem = rshm <= 190 * 1024;
-      if (!s_in_smem) rshm = sizeof(double) * (size_t)maxbO * pmax;
+      if (!s_in_smem) rshm = sizeof(double) * (size_t)maxbO * pmax_b;
       HK_TRY(hk_allow_smem(k_refine));
+      {
+        // algorithmic FMAs per item: the block LU of B^N - sigma C (Gauss-Jordan, b^3 per level), every
+        // inverse-iteration step (a sweep with p vectors, C X, C-orthonormalisation twice: 4 p^2 nO) and the
+        // Rayleigh-Ritz products (p^2 nO)
+        double fma = 0;
+        for (int it = i0; it < i1; ++it) {
+          int s = items[4 * it], pc = items[4 * it + 2], p = pc + HK_GUARD;
+          int steps = pc == 1 ? HK_REFINE_STEPS_SINGLE : HK_REFINE_STEPS;
+          const int* lp = &levO[o_off[s] + s];
+          double fac = 0, sweep = 0;
+          for (int j = 0; j < OL[s]; ++j) {
+            double b = lp[j + 1] - lp[j], bn = j + 1 < OL[s] ? lp[j + 2] - lp[j + 1] : 0;
+            fac += b * b * b;
+            sweep += (b * b + b * bn) * p;
+          }
+          double nO = oc[s];
+          fma += fac + steps * (sweep + 14.0 * nO * p + 4.0 * p * p * nO) + p * p * nO;
+        }
+        h->eigen_gflop[2] += 2.0 * fma * 1e-9;
+      }
       cudaEvent_t r0, r1;
       HK_CUDA(cudaEventCreate(&r0));
       HK_CUDA(cudaEventCreate(&r1));
       cudaEventRecord(r0, st);
-      k_refine<<<nit, 128, rshm, st>>>(d_items, d_sig, h->d_sub_info, d_o_off, d_Olevptr, d_OL, maxrow, d_ocnt, d_ocol,
-                                       d_oB, d_oC, d_o2i, d_foff, d_xoff, d_F, d_X, d_poff, d_P, d_lamhat, d_lamref,
-                                       maxbO, s_in_smem, h->d_status);
+      k_refine<<<nb_it, 128, rshm, st>>>(d_items, d_sig, h->d_sub_info, d_o_off, d_Olevptr, d_OL, maxrow, d_ocnt,
+                                         d_ocol, d_oB, d_oC, d_o2i, d_foff, d_xoff, d_F, d_X, d_poff, d_P, d_lamhat,
+                                         d_lamref, maxbO, s_in_smem, h->d_status);
       HK_COUNT_LAUNCH();
       cudaEventRecord(r1, st);
       HK_LAUNCH_CHECK();
@@ -720,6 +763,7 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
       HK_TRY(check_device_status(h, "eigen: refinement"));
       void* tmpf[] = {d_items, d_sig, d_foff, d_xoff, d_F, d_X};
       for (void* q : tmpf) dfree(h, q);
+      i0 = i1;
     }
     // selection and certification against the FP64 count (joined here)
     HK_CUDA(cudaStreamWaitEvent(st, inertia_done, 0));
@@ -737,6 +781,18 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
       }
     if (nfail == 0) break;
     if (attempt == 1) {
+      std::vector<int> negv(ns);
+      HK_CUDA(cudaMemcpy(negv.data(), d_neg, 4 * ns, cudaMemcpyDeviceToHost));
+      int most = 0;
+      for (int s = 0; s < ns; ++s)
+        if (fail[s]) most = std::max(most, negv[s]);
+      if (4 * most + 48 > LZ_BASIS_MAX) {
+        // more eigenvalues below tau than a Krylov basis of LZ_BASIS_MAX columns resolves
+        hk_set_error("eigen: subdomain %d has %d eigenvalues below tau; the Lanczos candidates resolve at most %d "
+                     "per subdomain (use more subdomains or a smaller tau)", first, negv[first],
+                     (LZ_BASIS_MAX - 48) / 4);
+        return HK_UNSUPPORTED;
+      }
       hk_set_error("eigen: %d subdomain(s), first %d: the refined eigenvalues below tau do not match the FP64 "
                    "inertia count (even with a %d-column Krylov basis)", nfail, first, LZ_BASIS_MAX);
       return HK_EIG_FAIL;

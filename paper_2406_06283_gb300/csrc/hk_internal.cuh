@@ -94,7 +94,8 @@ struct hk_handle {
   long long I_total = 0, G_total = 0, f_total = 0, csr_total = 0, z_total = 0, lower_nnz = 0;
   std::vector<Sub> subs;
   double setup_ms[8] = {0};
-  double eigen_ms[4] = {0};  // inertia, Lanczos, refinement (hk_info_t.eigen_kernel_ms)
+  double eigen_ms[4] = {0};     // inertia, Lanczos, refinement (hk_info_t.eigen_kernel_ms)
+  double eigen_gflop[4] = {0};  // their algorithmic GFLOP (hk_info_t.eigen_kernel_gflop)
 
   // ---- device data kept for the solve ----
   DevStatus* d_status = nullptr;

@@ -464,7 +464,8 @@ __device__ int lz_sturm_below32(const float* d, const float* e2, int n, float x,
 // One CTA per subdomain.  Dynamic shared memory: Y (max_nO x 4) | C Y (max_nO x 4) | sweep scratch
 // (max_b x 4) | the working block of the factorisation (max_b^2, when s_in_smem) | two staging buffers of
 // the sweeps (2 max_b^2, when use_fb); once the Krylov steps are done the Rayleigh quotient (N x N
-// doubles, N = 4 kdim[s]) reuses the same bytes.
+// doubles, N = 4 kdim[s]) reuses the same bytes.  When Yw is given, Y and C Y live there instead
+// (2 nO x 4 floats at y_off[s]) and shared memory starts with the sweep scratch.
 // CTA i works on subdomain sub_list[i].  Global workspace per subdomain: the factors (F + f_off[s]) and
 // the basis Q, C Q and Op Q (3 kdim[s] blocks of nO x 4, Qw + q_off[s]).
 // Outputs: lam_hat[s * HK_MAXM + t] = the candidates below lam_cut in ascending order, cnt_out[s] their
@@ -475,8 +476,9 @@ __global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
     const double* __restrict__ oB, const double* __restrict__ oC, const int* __restrict__ o2i,
     const int* __restrict__ sub_list, const int* __restrict__ kdim, const long long* __restrict__ f_off, float* F,
     const long long* __restrict__ q_off,
-    float* Qw, int max_nO, int max_b, int s_in_smem, int use_fb, int nb0, double sigma0, double lam_cut,
-    double* lam_hat, int* cnt_out, double* sigma_out, DevStatus* st) {
+    float* Qw, float* Yw, const long long* __restrict__ y_off, int max_nO, int max_b, int s_in_smem, int use_fb,
+    int nb0, double sigma0, double lam_cut,
+    double* lam_hat, int* cnt_out, double* sigma_out, int* nb_out, DevStatus* st) {
   extern __shared__ __align__(16) unsigned char lz_smem[];
   __shared__ float coef[LZ_MAX_DIM * LZ_P];
   __shared__ float d32[LZ_MAX_DIM], e32[LZ_MAX_DIM];
@@ -487,9 +489,10 @@ __global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
   __shared__ double hd[LZ_MAX_DIM], he[LZ_MAX_DIM], hv[LZ_MAX_DIM], hp[LZ_MAX_DIM];
   int s = sub_list[blockIdx.x], tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = NT >> 5;
   OPen P = open_sub(s, o_off, O_levptr, O_L, maxrow, ocnt, ocol, oB, oC, o2i, sub_info);
-  float* Ys = reinterpret_cast<float*>(lz_smem);
-  float* CYs = Ys + (long long)max_nO * LZ_P;
-  float* tv = CYs + (long long)max_nO * LZ_P;
+  // Y and C Y in shared memory, or (subdomains too large for it) in the global scratch Yw
+  float* Ys = Yw ? Yw + y_off[s] : reinterpret_cast<float*>(lz_smem);
+  float* CYs = Ys + (long long)(Yw ? P.nO : max_nO) * LZ_P;
+  float* tv = Yw ? reinterpret_cast<float*>(lz_smem) : CYs + (long long)max_nO * LZ_P;
   float* Ssm = s_in_smem ? tv + (long long)max_b * LZ_P : nullptr;
   float* Fb = use_fb ? (Ssm ? Ssm : tv + (long long)max_b * LZ_P) + (s_in_smem ? (long long)max_b * max_b : 0) : nullptr;
   double* Tm = reinterpret_cast<double*>(lz_smem);
@@ -716,6 +719,7 @@ __global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
   int cnt = th_cut >= th_hi ? 0 : N - lz_sturm_below32(d32, e32, N, th_cut, pivmin);
   if (tid == 0) {
     cnt_out[s] = cnt;
+    nb_out[s] = nb;
     if (cnt > HK_MAXM) dev_fail(st, HK_UNSUPPORTED, s, cnt);
   }
   float tol = 2e-7f * fmaxf(fabsf(th_hi), fabsf(th_cut));
@@ -967,6 +971,18 @@ hk_status eigen_inertia(hk_handle* h, const OvdofPencil& op, double tau, int* d_
     }
   }
   HK_TRY(hk_allow_smem(k_inertia));
+  {
+    // algorithmic FMAs: per level Gauss-Jordan (b^3) and Bunch-Kaufman (b^3 / 3)
+    double fma = 0;
+    for (int s = 0; s < ns; ++s) {
+      const int* lp = &op.h_levptr[op.h_off[s] + s];
+      for (int j = 0; j < op.h_L[s]; ++j) {
+        double b = lp[j + 1] - lp[j];
+        fma += b * b * b * (4.0 / 3.0);
+      }
+    }
+    h->eigen_gflop[0] = 2.0 * fma * 1e-9;
+  }
   k_inertia<<<ns, 256, in_smem ? need : 0, st>>>(h->d_sub_info, op.o_off, op.levptr, op.L, op.maxrow, op.cnt, op.col,
                                                   op.B, op.C, op.o2i, tau, op.max_b, in_smem, d_wo, d_ws, d_neg);
   HK_COUNT_LAUNCH();
@@ -1028,12 +1044,29 @@ hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<i
   HK_TRY(dalloc(h, &d_F, ftot));
   HK_TRY(dalloc(h, &d_Q, qtot));
   HK_TRY(dalloc(h, &d_sig, ns));
+  int* d_nb = nullptr;
+  HK_TRY(dalloc(h, &d_nb, ns));
   HK_CUDA(cudaMemcpyAsync(d_kd, kd.data(), 4 * ns, cudaMemcpyHostToDevice, st));
   HK_CUDA(cudaMemcpyAsync(d_list, list.data(), 4 * nl, cudaMemcpyHostToDevice, st));
   HK_CUDA(cudaMemcpyAsync(d_fo, fo.data(), 8 * ns, cudaMemcpyHostToDevice, st));
   HK_CUDA(cudaMemcpyAsync(d_qo, qo.data(), 8 * ns, cudaMemcpyHostToDevice, st));
   size_t vec = sizeof(float) * LZ_P * (2 * (size_t)op.max_nO + op.max_b);
   size_t sblk = sizeof(float) * (size_t)op.max_b * op.max_b;
+  float* d_Y = nullptr;
+  long long* d_yo = nullptr;
+  if (vec > 120 * 1024) {
+    // the vectors of large subdomains go to global memory
+    std::vector<long long> yo(ns, 0);
+    long long ytot = 0;
+    for (int s : list) {
+      yo[s] = ytot;
+      ytot += 2LL * op.h_nO[s] * LZ_P;
+    }
+    HK_TRY(dalloc(h, &d_Y, ytot));
+    HK_TRY(dalloc(h, &d_yo, ns));
+    HK_CUDA(cudaMemcpyAsync(d_yo, yo.data(), 8 * ns, cudaMemcpyHostToDevice, st));
+    vec = sizeof(float) * LZ_P * (size_t)op.max_b;
+  }
   size_t tmat = sizeof(double) * (size_t)(kmax * LZ_P) * (kmax * LZ_P);
   int s_in_smem = vec + sblk <= 200 * 1024;
   int use_fb = vec + (s_in_smem ? sblk : 0) + 2 * sblk <= 200 * 1024;
@@ -1048,9 +1081,10 @@ hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<i
   HK_CUDA(cudaEventCreate(&e1));
   cudaEventRecord(e0, st);
   k_lanczos<<<nl, LZ_THREADS, shm, st>>>(h->d_sub_info, op.o_off, op.levptr, op.L, op.maxrow, op.cnt, op.col, op.B,
-                                         op.C, op.o2i, d_list, d_kd, d_fo, d_F, d_qo, d_Q, op.max_nO, op.max_b, s_in_smem,
+                                         op.C, op.o2i, d_list, d_kd, d_fo, d_F, d_qo, d_Q, d_Y, d_yo, op.max_nO, op.max_b,
+                                         s_in_smem,
                                          use_fb, (cols0 + LZ_P - 1) / LZ_P, -0.5, lam_cut, d_lamhat, d_cnt, d_sig,
-                                         h->d_status);
+                                         d_nb, h->d_status);
   HK_COUNT_LAUNCH();
   cudaEventRecord(e1, st);
   HK_LAUNCH_CHECK();
@@ -1058,7 +1092,27 @@ hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<i
   cudaEventElapsedTime(ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  void* tmp[] = {d_kd, d_list, d_fo, d_qo, d_F, d_Q, d_sig};
+  // algorithmic FMAs of the launch (dense level operations; the sparse products are small beside them):
+  // the factorisation at the final shift (Gauss-Jordan, b^3 per level), every Krylov step (a sweep with 4
+  // right-hand sides, C Q, two Gram-Schmidt passes over the earlier blocks), the projection (N^2 nO) and the
+  // FP64 Householder reduction (4 N^3 / 3)
+  std::vector<int> nbv(ns);
+  HK_CUDA(cudaMemcpy(nbv.data(), d_nb, 4 * ns, cudaMemcpyDeviceToHost));
+  double fma = 0;
+  for (int s : list) {
+    const int* lp = &op.h_levptr[op.h_off[s] + s];
+    double fac = 0, sweep = 0;
+    for (int j = 0; j < op.h_L[s]; ++j) {
+      double b = lp[j + 1] - lp[j], bn = j + 1 < op.h_L[s] ? lp[j + 2] - lp[j + 1] : 0;
+      fac += b * b * b;
+      sweep += (b * b + b * bn) * LZ_P;
+    }
+    double nO = op.h_nO[s], nbs = nbv[s], N = nbs * LZ_P;
+    fma += fac + nbs * (sweep + 28.0 * nO) + 2.0 * 32.0 * nO * nbs * (nbs + 1) / 2.0 + N * N * nO +
+           4.0 * N * N * N / 3.0;
+  }
+  h->eigen_gflop[1] += 2.0 * fma * 1e-9;
+  void* tmp[] = {d_kd, d_list, d_fo, d_qo, d_F, d_Q, d_sig, d_nb, d_Y, d_yo};
   for (void* p : tmp) dfree(h, p);
   return HK_OK;
 }

@@ -191,7 +191,8 @@ void launch_to_f32(const double* a, float* b, long long n, cudaStream_t st) {
 // The top stream is: first sweep 0 .. M-1, middle, second sweep M-1 .. 0; the bottom stream:
 // first sweep L-1 .. M+1, second sweep M+1 .. L-1.
 // A record streams as chunks of consecutive rows, one 1-D TMA bulk copy each, of at most
-// HK_CHUNK_BYTES (one chunk per record on 2D subdomains).
+// HK_CHUNK_BYTES (one chunk per record on 2D subdomains of up to 35^2 dofs; smaller chunks on
+// subdomains so large that two ring stages would not fit beside the vectors).
 // Level table entry (4 x int64 per level): fwd offset, bwd offset, fwd | bwd bytes << 32,
 // fwd rows per chunk | bwd rows per chunk << 10 | b << 20 | level start << 40.
 #define HK_CHUNK_BYTES (32 * 1024)
@@ -933,13 +934,19 @@ static hk_status apply_t(hk_handle* h, int s, const double* v, double* z, const 
   T* zc = ybuf + (size_t)s * h->I_total;  // coarse prolongation per subdomain row
   bool fork = do_local && do_coarse && h->co_stream && h->ev_fork && h->ev_join;
   cudaStream_t main_st = h->stream;
+  // the restriction stages a subdomain's rows of rb right-hand sides in shared memory
+  int rb = cr;
+  while (rb > 1 && sizeof(T) * (size_t)h->max_dof * rb > 200 * 1024) rb >>= 1;
+  if (do_coarse && sizeof(T) * (size_t)h->max_dof * rb > 200 * 1024) {
+    hk_set_error("subdomain with %d dofs too large for the coarse restriction's shared memory", h->max_dof);
+    return HK_UNSUPPORTED;
+  }
   if (do_coarse) {
     if (fork) {
       HK_CUDA(cudaEventRecord(h->ev_fork, main_st));
       HK_CUDA(cudaStreamWaitEvent(h->co_stream, h->ev_fork, 0));
       h->stream = h->co_stream;
     }
-    int rb = cr;
     dim3 rg(h->n_sub, (s + rb - 1) / rb);
     size_t rshm = sizeof(T) * (size_t)h->max_dof * rb;
     // coarse solve: up to 16 right-hand sides per pass, c staged in column tiles
@@ -1164,6 +1171,13 @@ hk_status phase_local_factors_begin(hk_handle* h) {
   }
   // level records for the apply, in the arithmetic type of the precision form
   size_t esz = h->p.precision == HK_FP32_PRECOND ? 4 : 8;
+  // record chunks of at most 32 KB, smaller where two stages per ring would not fit beside the vectors of
+  // a one-right-hand-side apply of the largest subdomain
+  long long chunk = HK_CHUNK_BYTES;
+  {
+    long long vec1 = 80LL * h->max_L + 4LL * ((h->max_dof + 7) & ~3) + (long long)esz * (h->max_dof + 4);
+    while (chunk > 2048 && 4 * chunk + vec1 > 216 * 1024) chunk >>= 1;
+  }
   std::vector<long long> tab(4 * (h->I_total + ns), 0);
   std::vector<long long> lvfo(h->I_total + ns, 0);  // per level: offset of its factor blocks
   long long cur = 0, stage = 16;
@@ -1181,8 +1195,8 @@ hk_status phase_local_factors_begin(hk_handle* h) {
       long long cb = j < M ? bn : j > M ? bp : 0;
       long long rowf = pad4(lb + b + rb) * esz, rowb = pad4(cb) * esz;  // multiples of 16 bytes
       long long fb = b * rowf, bb = b * rowb;
-      long long rcf = std::max(1LL, std::min(b, HK_CHUNK_BYTES / rowf));
-      long long rcb = cb > 0 ? std::max(1LL, std::min(b, HK_CHUNK_BYTES / rowb)) : 1;
+      long long rcf = std::max(1LL, std::min(b, chunk / rowf));
+      long long rcb = cb > 0 ? std::max(1LL, std::min(b, chunk / rowb)) : 1;
       long long* e = &tab[4 * (size_t)(u.lev_off + j)];
       e[0] = cur;
       cur += fb;

@@ -52,7 +52,7 @@ class hk_info_t(C.Structure):
                 ("levels", C.c_int), ("bytes_resident", C.c_size_t), ("factor_elems", C.c_longlong),
                 ("dof_total", C.c_longlong), ("coarse_elems", C.c_longlong), ("lower_nnz", C.c_longlong),
                 ("setup_ms", C.c_double * 8), ("bytes_peak", C.c_size_t), ("graph_solves", C.c_longlong),
-                ("eigen_kernel_ms", C.c_double * 4)]
+                ("eigen_kernel_ms", C.c_double * 4), ("eigen_kernel_gflop", C.c_double * 4)]
 
 
 class hk_request_info(C.Structure):
@@ -272,9 +272,11 @@ def hk_solve_device(h: Handle, rhs_dev, u_dev, tol=1e-8, history=False) -> Solve
 def hk_info(h: Handle) -> dict:
     info = hk_info_t()
     _check(lib().hk_info(h.ptr, C.byref(info)), "hk_info")
-    d = {f: getattr(info, f) for f, _ in hk_info_t._fields_ if f not in ("setup_ms", "eigen_kernel_ms")}
+    d = {f: getattr(info, f) for f, _ in hk_info_t._fields_
+         if f not in ("setup_ms", "eigen_kernel_ms", "eigen_kernel_gflop")}
     d["setup_ms"] = list(info.setup_ms)
     d["eigen_kernel_ms"] = list(info.eigen_kernel_ms)
+    d["eigen_kernel_gflop"] = list(info.eigen_kernel_gflop)
     return d
 
 
@@ -410,8 +412,9 @@ class ServedResult:
     info: dict
 
 
-def hk_server_poll(srv: Server, ticket: int, op: int, n_rhs: int, wait_ms: int = -1):
-    """None while the request runs; else a ServedResult (raises HKError on a failed request)."""
+def hk_server_poll(srv: Server, ticket: int, op: int, n_rhs: int, wait_ms: int = -1, raise_on_failure: bool = True):
+    """None while the request runs; else a ServedResult.  A failed request raises HKError, or with
+    raise_on_failure=False comes back as a ServedResult whose status is the failure's."""
     n, mi = srv.n_dofs[op], srv.max_iters[op]
     u = np.zeros((n_rhs, n))
     it = np.zeros(n_rhs, dtype=np.int32)
@@ -422,7 +425,8 @@ def hk_server_poll(srv: Server, ticket: int, op: int, n_rhs: int, wait_ms: int =
                               C.byref(info))
     if st == HK_PENDING:
         return None
-    _check(st, "hk_server_poll", ok=(HK_OK, HK_NO_CONVERGENCE))
+    if raise_on_failure or st == HK_BAD_ARG:
+        _check(st, "hk_server_poll", ok=(HK_OK, HK_NO_CONVERGENCE))
     return ServedResult(u, it, hist, res, st, {f: getattr(info, f) for f, _ in hk_request_info._fields_})
 
 

@@ -222,15 +222,14 @@ def config_c3(n_rhs: int = 16) -> Problem:
 def config_c4(seed: int = 4, n_instances: int = 64):
     """Batched workload: 64 independent 2D instances.  h = 1/cells with cells uniform in
     {128, 192, 256, 384}, k ~ U[20, 80], 8x8 checkerboard a in 10^U[0,2], P x P boxes with P uniform in
-    [4, 12] raised to ceil(cells / 32) where needed (a box holds at most 32 x 32 cells, the dense
-    eigensolver stage's limit), overlap 2, s ~ U{1..8} seeded N(0,1) right-hand sides each."""
+    [4, 12], overlap 2, s ~ U{1..8} seeded N(0,1) right-hand sides each."""
     out, meshes = [], {}
     choices = [128, 192, 256, 384]
     for i in range(n_instances):
         u = uniform(stream_seed(seed, i, 0), 4)
         cells = choices[min(int(u[0] * len(choices)), len(choices) - 1)]
         k = 20.0 + 60.0 * float(u[1])
-        P = max(4 + min(int(u[2] * 9), 8), -(-cells // 32))
+        P = 4 + min(int(u[2] * 9), 8)
         s = 1 + min(int(u[3] * 8), 7)
         m = meshes.setdefault(cells, square_mesh(cells))
         a = checkerboard(m, 8, stream_seed(seed, i, 1))
@@ -243,9 +242,7 @@ def config_c5(seed: int = 5, pool: int = 8):
     """Serving workload: 24 operators and a request-stream recipe.
 
     16 operators in 2D: h = 1/cells with cells uniform in {128, 192, 256, 384, 512}, k ~ U[20, 100],
-    an 8x8 checkerboard a in 10^U[0,2], P x P boxes with P = max(ceil(k / 6), ceil(cells / 32)), so that
-    H k <= 6 and a box holds at most 32 x 32 cells (|dof(Omega_i)| <= 35^2, as at h = 1/256 and 1/512
-    with 8x8 and 16x16 boxes), overlap 2.
+    an 8x8 checkerboard a in 10^U[0,2], P x P boxes with P = ceil(k / 6), so that H k <= 6, overlap 2.
     8 operators in 3D: unit cube, Kuhn tetrahedra, h = 1/32 (29,791 dofs), k = 20, 4x4x4 boxes,
     a from a 4x4x4 checkerboard.  Each operator carries `pool` seeded N(0,1) right-hand sides that
     the requests of serving_stream draw from.
@@ -256,7 +253,7 @@ def config_c5(seed: int = 5, pool: int = 8):
         u = uniform(stream_seed(seed, i, 0), 2)
         cells = choices[min(int(u[0] * len(choices)), len(choices) - 1)]
         k = 20.0 + 80.0 * float(u[1])
-        P = max(int(math.ceil(k / 6.0)), -(-cells // 32))
+        P = int(math.ceil(k / 6.0))
         m = meshes.setdefault(cells, square_mesh(cells))
         a = checkerboard(m, 8, stream_seed(seed, i, 1))
         rhs = np.stack([normal(stream_seed(seed, i, 2, r), m.n_dofs) for r in range(pool)])
