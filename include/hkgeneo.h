@@ -46,7 +46,7 @@ typedef enum {
   HK_PENDING = 10          /* hk_server_poll: the request has not finished yet */
 } hk_status;
 
-enum { HK_FP64 = 0, HK_FP32_PRECOND = 1 };                     /* hk_params.precision */
+enum { HK_FP64 = 0, HK_FP32_PRECOND = 1, HK_SPLIT_BF16_PRECOND = 2 };  /* hk_params.precision */
 enum { HK_TWO_LEVEL = 0, HK_ONE_LEVEL = 1, HK_COARSE_ONLY = 2 };  /* hk_params.levels */
 enum { HK_AS = 0, HK_RAS_POU = 1 };                            /* hk_params.weighting */
 
@@ -68,7 +68,15 @@ typedef struct {
   double tau;                  /* keep local eigenvalues lambda < tau (> 0); Def. 5.1 */
   int precision;               /* HK_FP64: whole solver in FP64.  HK_FP32_PRECOND: the
                                   preconditioner (local and coarse solves) applied in FP32 from
-                                  factors computed in FP64; Krylov vectors, matvec and Arnoldi FP64. */
+                                  factors computed in FP64; Krylov vectors, matvec and Arnoldi FP64.
+                                  HK_SPLIT_BF16_PRECOND: as HK_FP32_PRECOND, with the local block sweeps
+                                  (Eq. 2.22) as tensor-core products: every level record R and vector x
+                                  split into BF16 pairs (R = R_hi + R_lo, x = x_hi + x_lo) and
+                                  R_hi x_hi + R_hi x_lo + R_lo x_hi accumulated in FP32, x kept as the
+                                  BF16 pair between levels (about 16 significant bits); where those
+                                  sweeps are unavailable (a level wider than 256 dofs, or a subdomain
+                                  whose vectors do not fit shared memory) or measured slower for a batch
+                                  size, the FP32 sweeps run instead (hk_set_sweep_path). */
   int levels;                  /* HK_TWO_LEVEL (Eq. 2.23), HK_ONE_LEVEL (Eq. 2.22), HK_COARSE_ONLY */
   int weighting;               /* HK_AS: unweighted sum of local solves (Eq. 2.22);
                                   HK_RAS_POU: local solves weighted by 1/mu (variant) */
@@ -140,6 +148,10 @@ typedef struct {
                                   [1] FP32 Lanczos candidates, [2] FP64 refinement, [3] 0 */
   double eigen_kernel_gflop[4]; /* their algorithmic work in GFLOP (2 per multiply-add of the dense level
                                   operations: factorisations, sweeps, Gram-Schmidt, projections) */
+  long long tc_record_bytes;   /* device bytes of the split-BF16 level records of the tensor-core sweeps
+                                  (0: not built, i.e. another precision form or sweeps unavailable) */
+  int last_sweeps;             /* local sweeps of the last preconditioner apply: HK_SWEEPS_CUDA_CORE or
+                                  HK_SWEEPS_TENSOR_CORE (0 before the first apply) */
 } hk_info_t;
 
 hk_status hk_info(const hk_handle* h, hk_info_t* info);
@@ -171,6 +183,16 @@ hk_status hk_kernel_times(hk_handle* h, double* ms, int32_t* count);
  * are bitwise the same.  Graphs pay off for a handle solved alone; handles whose solves overlap with
  * other handles' on other streams (the serving calls) run faster without them. */
 hk_status hk_set_solve_graphs(hk_handle* h, int on);
+
+/* Local sweeps of the split-BF16 form (hk_params.precision == HK_SPLIT_BF16_PRECOND):
+ * HK_SWEEPS_AUTO (the default) runs the tensor-core sweeps unless the handle's autotuner, which times
+ * both on the first solve of each batch size, measured the FP32 CUDA-core sweeps faster;
+ * HK_SWEEPS_CUDA_CORE always runs the FP32 sweeps; HK_SWEEPS_TENSOR_CORE always runs the tensor-core
+ * sweeps.  Pinning a path makes results reproducible bit for bit across processes (the automatic
+ * choice depends on timings).  Errors: HK_BAD_ARG (unknown path), HK_UNSUPPORTED (tensor-core sweeps
+ * asked for in another precision form, or unavailable for this handle's subdomains). */
+enum { HK_SWEEPS_AUTO = 0, HK_SWEEPS_CUDA_CORE = 1, HK_SWEEPS_TENSOR_CORE = 2 };
+hk_status hk_set_sweep_path(hk_handle* h, int path);
 
 /* Waits for the handle's device work and reports a failure that a kernel recorded since the last
  * check: a bounded device wait that ran out (HK_TIMEOUT) or a failed pivot.  The record is cleared

@@ -225,7 +225,7 @@ static hk_status setup_common(const hk_mesh* mesh, const double* elem_coeff, dou
   if ((mesh->dim != 2 && mesh->dim != 3) || mesh->n_nodes <= 0 || mesh->n_elems <= 0 || prm->n_sub <= 0 ||
       prm->overlap_layers < 1 || !(prm->tau > 0) || !(k >= 0) || prm->restart < 1 ||
       prm->restart > HK_MAXRESTART || prm->max_iters < 1 || prm->precision < HK_FP64 ||
-      prm->precision > HK_FP32_PRECOND || prm->levels < HK_TWO_LEVEL || prm->levels > HK_COARSE_ONLY ||
+      prm->precision > HK_SPLIT_BF16_PRECOND || prm->levels < HK_TWO_LEVEL || prm->levels > HK_COARSE_ONLY ||
       prm->weighting < HK_AS || prm->weighting > HK_RAS_POU) {
     hk_set_error("invalid sizes or parameters (dim %d, n_sub %d, overlap %d, tau %g, restart %d)", mesh->dim,
                  prm->n_sub, prm->overlap_layers, prm->tau, prm->restart);
@@ -284,6 +284,25 @@ extern "C" hk_status hk_set_timing(hk_handle* h, int on) {
 extern "C" hk_status hk_set_solve_graphs(hk_handle* h, int on) {
   if (!h) return HK_BAD_ARG;
   h->use_graphs = on != 0;
+  return HK_OK;
+}
+
+extern "C" hk_status hk_set_sweep_path(hk_handle* h, int path) {
+  if (!h || path < HK_SWEEPS_AUTO || path > HK_SWEEPS_TENSOR_CORE) {
+    hk_set_error("hk_set_sweep_path: invalid arguments");
+    return HK_BAD_ARG;
+  }
+  if (path == HK_SWEEPS_TENSOR_CORE && !h->tc_ok) {
+    hk_set_error(h->p.precision == HK_SPLIT_BF16_PRECOND
+                     ? "tensor-core sweeps unavailable for this handle's subdomains"
+                     : "tensor-core sweeps need the split-BF16 precision form");
+    return HK_UNSUPPORTED;
+  }
+  if (path != h->sweep_path) {
+    HK_CUDA(cudaStreamSynchronize(h->stream));
+    hk_drop_graphs(h);  // captured solves hold the launches of the old path
+  }
+  h->sweep_path = path;
   return HK_OK;
 }
 
@@ -371,6 +390,8 @@ extern "C" hk_status hk_info(const hk_handle* h, hk_info_t* info) {
   info->graph_solves = h->graph_solves;
   for (int i = 0; i < 4; ++i) info->eigen_kernel_ms[i] = h->eigen_ms[i];
   for (int i = 0; i < 4; ++i) info->eigen_kernel_gflop[i] = h->eigen_gflop[i];
+  info->tc_record_bytes = h->tc_ok ? h->tc_bytes : 0;
+  info->last_sweeps = h->last_sweeps;
   return HK_OK;
 }
 

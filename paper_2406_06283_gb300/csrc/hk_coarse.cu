@@ -389,7 +389,7 @@ hk_status phase_coarse(hk_handle* h) {
     hk_set_error("coarse matrix singular: pivot %.3e, max|E| %.3e", sc[1], sc[0]);
     return HK_SINGULAR_COARSE;
   }
-  if (h->p.precision == HK_FP32_PRECOND) {
+  if (precond_f32(h->p)) {
     HK_TRY(dalloc(h, &h->d_Einv32, (size_t)n0 * n0));
     launch_to_f32(h->d_Einv64, h->d_Einv32, (long long)n0 * n0, st);
     HK_LAUNCH_CHECK();

@@ -69,6 +69,9 @@ struct DArr {
   size_t n = 0;
 };
 
+// The preconditioner is applied in FP32 arithmetic (FP32 and split-BF16 forms).
+inline bool precond_f32(const hk_params& p) { return p.precision != HK_FP64; }
+
 // Per-subdomain Krylov / apply workspace sizes are derived from these.
 struct Sub {
   int nI, nG, L;        // |dof|, |ovdof \ dof|, number of level sets
@@ -137,6 +140,17 @@ struct hk_handle {
   long long* d_lvtab = nullptr;
   long long* d_lvfo = nullptr;    // setup only: per level, offset of its blocks in the FP64 factors
   long long pack_bytes = 0, pack_stage = 0;
+  // split-BF16 form: level records of the tensor-core sweeps (see hk_tc.cu), their table, the ring
+  // stage size, the widest padded level-ordered vector and whether the sweeps are available
+  unsigned char* d_pack_tc = nullptr;
+  long long* d_lvtab_tc = nullptr;
+  int* d_tc_prow = nullptr;     // per local dof (level order): its row in the padded level order
+  long long tc_bytes = 0;
+  int tc_stage = 0, tc_max_apad = 0;
+  bool tc_ok = false;
+  int sweep_path = 0;           // hk_set_sweep_path
+  int last_sweeps = 0;          // HK_SWEEPS_* of the last apply
+  std::map<int, int> tc_tuned;  // per batch size: 1 if the tensor-core sweeps measured faster
   // coarse space
   double* d_lam = nullptr;        // per subdomain kept eigenvalues (HK_MAXM each)
   double* d_Z64 = nullptr;        // z_total, per subdomain nI x m row-major
@@ -306,8 +320,21 @@ void hk_drop_graphs(hk_handle* h);
 // Raises the shared-memory limit of every apply kernel instantiation (before any graph capture).
 hk_status apply_prepare(hk_handle* h);
 // Times the apply for every admissible number of right-hand sides per CTA (1, 2, 4, 8, 16) at batch size s
-// and keeps the fastest (the arithmetic per right-hand side is the same for all of them).
+// and keeps the fastest (the arithmetic per right-hand side is the same for all of them); in the split-BF16
+// form also the tensor-core sweeps against the fastest of those.
 hk_status apply_autotune(hk_handle* h, int s);
+// True when apply_autotune has not yet run for batch size s.
+bool apply_needs_tuning(const hk_handle* h, int s);
+
+// ---- tensor-core sweeps of the split-BF16 form (hk_tc.cu) ----
+// Host part of the record layout: the level table, the records' size and the launch limits, from the
+// level pointers `lev` (host copy); sets h->tc_ok.  Allocates the records and the table.
+hk_status tc_plan(hk_handle* h, const std::vector<int>& lev);
+// Packs the records from the FP64 factors h->d_F64 (per-level offsets h->d_lvfo) on stream st.
+hk_status tc_pack(hk_handle* h, cudaStream_t st);
+// The local sweeps of s right-hand sides (gather of v, block sweeps, local solutions into ybuf).
+hk_status tc_launch(hk_handle* h, int s, const double* v, const int* active, float* ybuf);
+hk_status tc_prepare();
 // z = M^{-1} v for s vectors (v, z: s x n device arrays, FP64).  `active` is NULL or
 // the per-rhs state words (8 ints per rhs, word 0 nonzero = process this rhs).
 hk_status op_apply(hk_handle* h, int s, const double* v, double* z, const int* active);

@@ -553,7 +553,7 @@ hk_status ensure_workspace(hk_handle* h, int s) {
   HK_TRY(dalloc(h, &h->d_w, (size_t)s * n));
   HK_TRY(dalloc(h, &h->d_x, (size_t)s * n));
   HK_TRY(dalloc(h, &h->d_f, (size_t)s * n));
-  if (h->p.precision == HK_FP32_PRECOND) {
+  if (precond_f32(h->p)) {
     HK_TRY(dalloc(h, &h->d_ybuf32, 2 * (size_t)s * h->I_total));  // local solutions | coarse prolongation
     HK_TRY(dalloc(h, &h->d_c32, (size_t)s * (h->n0 + 1)));
     HK_TRY(dalloc(h, &h->d_cc32, (size_t)s * (h->n0 + 1)));
@@ -580,6 +580,7 @@ hk_status ensure_workspace(hk_handle* h, int s) {
   h->ws_rhs = s;
   h->ws_m = m;
   h->nr_tuned.clear();
+  h->tc_tuned.clear();
   return HK_OK;
 }
 
@@ -826,7 +827,7 @@ static hk_status fgmres_results(hk_handle* h, int s, double* u_dev, int32_t* ite
 hk_status run_fgmres(hk_handle* h, int s, const double* rhs_dev, double tol, double* u_dev, int32_t* iters,
                      double* res_hist, double* final_res) {
   HK_TRY(ensure_workspace(h, s));
-  if (s > 1 && !h->nr_tuned.count(s)) HK_TRY(apply_autotune(h, s));
+  if (apply_needs_tuning(h, s)) HK_TRY(apply_autotune(h, s));
   cudaStream_t st = h->stream;
   int m = h->p.restart;
   HK_TRY(fgmres_init(h, s, rhs_dev));

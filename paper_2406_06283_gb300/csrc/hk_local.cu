@@ -1002,7 +1002,16 @@ static hk_status apply_t(hk_handle* h, int s, const double* v, double* z, const 
     HK_LAUNCH_CHECK();
   }
   hk_status rc = HK_OK;
-  if (do_local) {
+  bool use_tc = false;
+  if constexpr (sizeof(T) == 4) {
+    if (h->tc_ok && h->sweep_path != HK_SWEEPS_CUDA_CORE) {
+      auto tt = h->tc_tuned.find(s);
+      use_tc = h->sweep_path == HK_SWEEPS_TENSOR_CORE || tt == h->tc_tuned.end() || tt->second;
+    }
+    if (do_local && use_tc) rc = tc_launch(h, s, v, active, ybuf);
+  }
+  if (do_local) h->last_sweeps = use_tc ? HK_SWEEPS_TENSOR_CORE : HK_SWEEPS_CUDA_CORE;
+  if (do_local && !use_tc) {
     switch (nr) {
       case 16: rc = launch_local<T, 16>(h, s, v, active, ybuf); break;
       case 8: rc = launch_local<T, 8>(h, s, v, active, ybuf); break;
@@ -1059,49 +1068,69 @@ hk_status apply_prepare(hk_handle*) {
   HK_TRY(hk_allow_smem(k_local_apply<double, 4>));
   HK_TRY(hk_allow_smem(k_local_apply<double, 8>));
   HK_TRY(hk_allow_smem(k_local_apply<double, 16>));
+  HK_TRY(tc_prepare());
   return HK_OK;
 }
 
+bool apply_needs_tuning(const hk_handle* h, int s) {
+  return (s > 1 && !h->nr_tuned.count(s)) || (h->tc_ok && h->sweep_path == HK_SWEEPS_AUTO && !h->tc_tuned.count(s));
+}
+
 hk_status apply_autotune(hk_handle* h, int s) {
-  if (s < 2) return HK_OK;
+  bool tune_tc = h->tc_ok && h->sweep_path == HK_SWEEPS_AUTO;
+  if (s < 2 && !tune_tc) return HK_OK;
   bool timing = h->timing;
+  int path = h->sweep_path;
   h->timing = false;
   cudaEvent_t a, b;
   HK_CUDA(cudaEventCreate(&a));
   HK_CUDA(cudaEventCreate(&b));
-  int best = 0;
-  float best_ms = 1e30f;
-  hk_status rc = HK_OK;
-  for (int nr = 1; nr <= 16 && nr <= s && rc == HK_OK; nr *= 2) {
-    h->nr_tuned[s] = nr;
-    // inputs: the (zero-initialised) first Krylov block; output: the first flexible block
-    rc = op_apply(h, s, h->d_V, h->d_Zk, nullptr);  // warm-up
-    float t = 0;
-    for (int rep = 0; rep < 3 && rc == HK_OK; ++rep) {
+  // inputs: the (zero-initialised) first Krylov block; output: the first flexible block
+  auto time_apply = [&](float& t) -> hk_status {
+    hk_status r = op_apply(h, s, h->d_V, h->d_Zk, nullptr);  // warm-up
+    t = 0;
+    for (int rep = 0; rep < 3 && r == HK_OK; ++rep) {
       cudaEventRecord(a, h->stream);
-      rc = op_apply(h, s, h->d_V, h->d_Zk, nullptr);
+      r = op_apply(h, s, h->d_V, h->d_Zk, nullptr);
       cudaEventRecord(b, h->stream);
       cudaEventSynchronize(b);
       float ms = 0;
       cudaEventElapsedTime(&ms, a, b);
       t += ms;
     }
+    return r;
+  };
+  int best = 0;
+  float best_ms = 1e30f;
+  hk_status rc = HK_OK;
+  h->sweep_path = HK_SWEEPS_CUDA_CORE;
+  for (int nr = 1; nr <= 16 && nr <= s && rc == HK_OK; nr *= 2) {
+    h->nr_tuned[s] = nr;
+    float t = 0;
+    rc = time_apply(t);
     if (rc == HK_OK && t < best_ms) {
       best_ms = t;
       best = nr;
     }
   }
+  if (best) h->nr_tuned[s] = best;
+  else h->nr_tuned.erase(s);
+  if (tune_tc && rc == HK_OK) {
+    h->sweep_path = HK_SWEEPS_TENSOR_CORE;
+    float t = 0;
+    rc = time_apply(t);
+    if (rc == HK_OK) h->tc_tuned[s] = t < best_ms ? 1 : 0;
+  }
+  h->sweep_path = path;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   h->timing = timing;
-  if (best) h->nr_tuned[s] = best;
-  else h->nr_tuned.erase(s);
   return rc;
 }
 
 hk_status op_apply(hk_handle* h, int s, const double* v, double* z, const int* active) {
   HK_TRY(ensure_workspace(h, s));
-  if (h->p.precision == HK_FP32_PRECOND) return apply_t<float>(h, s, v, z, active, h->d_ybuf32, h->d_c32, h->d_cc32);
+  if (precond_f32(h->p)) return apply_t<float>(h, s, v, z, active, h->d_ybuf32, h->d_c32, h->d_cc32);
   return apply_t<double>(h, s, v, z, active, h->d_ybuf64, h->d_c64, h->d_cc64);
 }
 
@@ -1122,7 +1151,7 @@ __global__ void k_transpose_z(const int* __restrict__ sub_info, const long long*
 
 hk_status build_apply_z(hk_handle* h) {
   if (h->n0 == 0) return HK_OK;
-  if (h->p.precision == HK_FP32_PRECOND) {
+  if (precond_f32(h->p)) {
     float* zt = nullptr;
     HK_TRY(dalloc(h, &zt, h->z_total));
     k_transpose_z<float><<<h->n_sub, 256, 0, h->stream>>>(h->d_sub_info, h->d_sub_off, h->d_Z64, zt); HK_COUNT_LAUNCH();
@@ -1170,7 +1199,7 @@ hk_status phase_local_factors_begin(hk_handle* h) {
     dfree(h, d_cnt);
   }
   // level records for the apply, in the arithmetic type of the precision form
-  size_t esz = h->p.precision == HK_FP32_PRECOND ? 4 : 8;
+  size_t esz = precond_f32(h->p) ? 4 : 8;
   // record chunks of at most 32 KB, smaller where two stages per ring would not fit beside the vectors of
   // a one-right-hand-side apply of the largest subdomain
   long long chunk = HK_CHUNK_BYTES;
@@ -1209,6 +1238,7 @@ hk_status phase_local_factors_begin(hk_handle* h) {
   }
   h->pack_bytes = cur;
   h->pack_stage = stage;
+  HK_TRY(tc_plan(h, lev));
   HK_TRY(dalloc(h, &h->d_F64, fo));
   HK_TRY(dalloc(h, &h->d_lvtab, tab.size()));
   HK_TRY(dalloc(h, &h->d_lvfo, lvfo.size()));
@@ -1243,6 +1273,7 @@ hk_status phase_local_factors_begin(hk_handle* h) {
                                               h->d_lcol, h->d_lvalB, h->d_F64, h->d_lvfo, h->d_lvtab, h->d_pack);
   HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
+  HK_TRY(tc_pack(h, ax));
   HK_CUDA(cudaEventRecord(h->ev_lf, ax));
   h->lf_pending = true;
   return HK_OK;
@@ -1317,7 +1348,7 @@ extern "C" hk_status hk_apply_precond_noalloc(hk_handle* h, int n_rhs, const dou
     hk_set_error("hk_apply_precond_noalloc: invalid arguments");
     return HK_BAD_ARG;
   }
-  size_t esz = h->p.precision == HK_FP32_PRECOND ? sizeof(float) : sizeof(double);
+  size_t esz = precond_f32(h->p) ? sizeof(float) : sizeof(double);
   size_t ylen = align256(esz * 2 * (size_t)n_rhs * (size_t)h->I_total);
   size_t clen = align256(esz * (size_t)n_rhs * (size_t)(h->n0 + 1));
   size_t need = ylen + 2 * clen;
@@ -1336,7 +1367,7 @@ extern "C" hk_status hk_apply_precond_noalloc(hk_handle* h, int n_rhs, const dou
   if (s == HK_OK) s = noalloc_scratch(h->dev, &base);
   if (s == HK_OK) {
     unsigned char* b = static_cast<unsigned char*>(base);
-    if (h->p.precision == HK_FP32_PRECOND)
+    if (precond_f32(h->p))
       s = apply_t<float>(h, n_rhs, v_dev, z_dev, nullptr, reinterpret_cast<float*>(b),
                          reinterpret_cast<float*>(b + ylen), reinterpret_cast<float*>(b + ylen + clen));
     else

@@ -85,7 +85,7 @@ static size_t solve_workspace_bytes(const SrvOp* o, const hk_handle* h, int s) {
   while (cap < s) cap <<= 1;
   s = cap;
   size_t m = (size_t)o->prm.restart, n = (size_t)o->n_dofs;
-  size_t pf = o->prm.precision == HK_FP32_PRECOND ? 4 : 8;
+  size_t pf = precond_f32(o->prm) ? 4 : 8;
   size_t b = 8 * (size_t)s * ((2 * m + 6) * n + (m + 1) * (m + 4) + (size_t)o->prm.max_iters);
   if (h) b += pf * (size_t)s * ((size_t)h->I_total + 2 * ((size_t)h->n0 + 1));
   return b + (1 << 20);

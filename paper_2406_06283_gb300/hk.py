@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libhkgeneo.so")
 
 HK_OK, HK_BAD_ARG, HK_SINGULAR_LOCAL, HK_SINGULAR_COARSE, HK_EIG_FAIL = 0, 1, 2, 3, 4
 HK_NO_CONVERGENCE, HK_OOM, HK_TIMEOUT, HK_CUDA_ERROR, HK_UNSUPPORTED, HK_PENDING = 5, 6, 7, 8, 9, 10
-HK_FP64, HK_FP32_PRECOND = 0, 1
+HK_FP64, HK_FP32_PRECOND, HK_SPLIT_BF16_PRECOND = 0, 1, 2
+HK_SWEEPS_AUTO, HK_SWEEPS_CUDA_CORE, HK_SWEEPS_TENSOR_CORE = 0, 1, 2
 HK_TWO_LEVEL, HK_ONE_LEVEL, HK_COARSE_ONLY = 0, 1, 2
 HK_AS, HK_RAS_POU = 0, 1
 
@@ -52,7 +53,8 @@ class hk_info_t(C.Structure):
                 ("levels", C.c_int), ("bytes_resident", C.c_size_t), ("factor_elems", C.c_longlong),
                 ("dof_total", C.c_longlong), ("coarse_elems", C.c_longlong), ("lower_nnz", C.c_longlong),
                 ("setup_ms", C.c_double * 8), ("bytes_peak", C.c_size_t), ("graph_solves", C.c_longlong),
-                ("eigen_kernel_ms", C.c_double * 4), ("eigen_kernel_gflop", C.c_double * 4)]
+                ("eigen_kernel_ms", C.c_double * 4), ("eigen_kernel_gflop", C.c_double * 4),
+                ("tc_record_bytes", C.c_longlong), ("last_sweeps", C.c_int)]
 
 
 class hk_request_info(C.Structure):
@@ -112,12 +114,14 @@ def lib():
     L.hk_check_status.argtypes = [_P]
     L.hk_set_wait_limit.argtypes = [_P, C.c_int]
     L.hk_apply_precond_noalloc.argtypes = [_P, C.c_int, _P, _P]
+    L.hk_set_sweep_path.argtypes = [_P, C.c_int]
     for f in ("hk_server_create", "hk_server_add_operator", "hk_server_submit", "hk_server_poll",
               "hk_server_get_stats", "hk_server_destroy"):
         getattr(L, f).restype = C.c_int
     for f in ("hk_setup", "hk_setup_device", "hk_set_timing", "hk_kernel_times", "hk_solve", "hk_solve_device", "hk_info", "hk_destroy", "hk_get_matrix",
               "hk_get_subdomain", "hk_get_mu", "hk_get_eigen", "hk_get_coarse", "hk_apply_precond", "hk_matvec",
-              "hk_assemble_load", "hk_check_status", "hk_set_wait_limit", "hk_apply_precond_noalloc"):
+              "hk_assemble_load", "hk_check_status", "hk_set_wait_limit", "hk_apply_precond_noalloc",
+              "hk_set_sweep_path"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -200,6 +204,11 @@ def hk_kernel_launches() -> int:
 
 def hk_set_solve_graphs(h: Handle, on: bool = True):
     _check(lib().hk_set_solve_graphs(h.ptr, int(bool(on))), "hk_set_solve_graphs")
+
+
+def hk_set_sweep_path(h: Handle, path: int):
+    """Local sweeps of the split-BF16 form: HK_SWEEPS_AUTO, HK_SWEEPS_CUDA_CORE or HK_SWEEPS_TENSOR_CORE."""
+    _check(lib().hk_set_sweep_path(h.ptr, int(path)), "hk_set_sweep_path")
 
 
 def hk_check_status(h: Handle) -> int:

@@ -72,6 +72,60 @@ def test_c2_full_parity_fp32_preconditioner(c2):
     hk.hk_destroy(h)
 
 
+def test_c2_full_parity_split_bf16(c2):
+    """Split-BF16 form on the h = 1/256 workload: the apply of 16 right-hand sides (one CTA group per
+    subdomain, the launch shape of a 16-right-hand-side solve) against the oracle's apply, and the
+    single-right-hand-side solve's count within +-1 of the oracle's range (tolerances of
+    test_gpu_split_bf16.py)."""
+    from test_gpu_split_bf16 import TOL_SPLIT
+    p, o = c2
+    h = hk.setup_problem(p, precision=hk.HK_SPLIT_BF16_PRECOND)
+    hk.hk_set_sweep_path(h, hk.HK_SWEEPS_TENSOR_CORE)
+    v = np.random.default_rng(21).standard_normal((16, o.n))
+    z = hk.hk_apply_precond(h, v)
+    want = np.stack([o.precond.apply(vi) for vi in v])
+    err = np.linalg.norm(z - want, axis=1) / np.linalg.norm(want, axis=1)
+    assert np.all(err <= TOL_SPLIT), err
+    got = hk.hk_solve(h, p.rhs, p.tol)
+    rng_out = oracle_count_range(o, p.rhs[0], p.tol, key=("c2", 0))
+    check_counts("c2_h256_k50_p8", 0, "split_bf16", got.iters[0], rng_out, widen=1)
+    assert _rel(got.u[0], rng_out[0].x) <= 1e-7
+    hk.hk_destroy(h)
+
+
+def test_c3_split_bf16_one_level_apply_sampled():
+    """h = 1/512 layered workload, 16 right-hand sides together (the bench's launch shape): the
+    one-level split-BF16 apply on the dofs of sampled subdomains against the oracle, which solves
+    B_j y_j = v[dof(Omega_j)] for every subdomain j sharing a dof with the sample (Eq. 2.22 summed
+    over those j) and compares at TOL_SPLIT."""
+    from test_gpu_split_bf16 import TOL_SPLIT
+    p = W.config_c3()
+    m = p.mesh
+    h = hk.setup_problem(p, precision=hk.HK_SPLIT_BF16_PRECOND, levels=hk.HK_ONE_LEVEL)
+    hk.hk_set_sweep_path(h, hk.HK_SWEEPS_TENSOR_CORE)
+    B, _, _, _ = OF.helmholtz_matrices(m.xyz, m.elems, p.coeff, m.is_boundary, p.k)
+    v = np.random.default_rng(31).standard_normal((16, B.shape[0]))
+    z = hk.hk_apply_precond(h, v)
+    hk.hk_destroy(h)
+    subs, mu = OD.decompose(m.xyz, m.elems, m.is_boundary, p.elem_to_sub, p.n_sub, p.overlap)
+    Bc = B.tocsr()
+    for i in (0, 17, 136, 255):
+        di = subs[i].dof
+        want = np.zeros((16, di.size))
+        pos = {int(d): t for t, d in enumerate(di)}
+        for sd in subs:
+            common = np.intersect1d(sd.dof, di)
+            if common.size == 0:
+                continue
+            y = np.linalg.solve(Bc[sd.dof][:, sd.dof].toarray(), v[:, sd.dof].T).T
+            where = np.searchsorted(sd.dof, common) if np.all(np.diff(sd.dof) > 0) else \
+                np.array([int(np.flatnonzero(sd.dof == c)[0]) for c in common])
+            for c, wpos in zip(common, where):
+                want[:, pos[int(c)]] += y[:, wpos]
+        err = np.linalg.norm(z[:, di] - want, axis=1) / np.linalg.norm(want, axis=1)
+        assert np.all(err <= TOL_SPLIT), (i, err)
+
+
 @pytest.fixture(scope="module")
 def c3():
     p = W.config_c3()
