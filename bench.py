@@ -41,6 +41,23 @@ METRIC = "Helmholtz solves/s and p99 latency at 1e-8 residual; FP32-precond vs F
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_PATH = os.path.join(ROOT, "profiles", "dram_traffic.txt")
 CSRC = os.path.join(ROOT, "paper_2406_06283_gb300", "csrc")
+# hk_params.precision of each --precision choice (HK_FP64, HK_FP32_PRECOND, HK_SPLIT_BF16_PRECOND) and the
+# arithmetic it computes in
+PRECISIONS = {"fp64": 0, "fp32": 1, "split": 2}
+DTYPES = {"fp64": "f64", "fp32": "f64 Krylov / f32 preconditioner",
+          "split": "f64 Krylov / split-bf16 tensor-core local solves, f32 coarse"}
+TC_NRHS = 16  # right-hand sides per tensor-core sweep CTA (the MMA's N)
+
+
+def bf16_peak() -> float:
+    try:
+        with open(PEAKS_PATH) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:  # noqa: BLE001
+        return 1900.0
+
+
+BF16_PEAK = bf16_peak()
 
 
 def source_digest(kernel: str) -> str | None:
@@ -313,7 +330,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     p = workload(args.workload)
-    prec = hk.HK_FP32_PRECOND if args.precision == "fp32" else hk.HK_FP64
+    prec = PRECISIONS[args.precision]
     m = p.mesh
     rhs_host = np.ascontiguousarray(np.atleast_2d(p.rhs), dtype=np.float64)
     s = rhs_host.shape[0]
@@ -358,6 +375,17 @@ def run_ours(args, world, rank, local):
     step_ms = []
     if args.profile_run:
         device_step(graphs=False)
+        if prec == PRECISIONS["split"]:
+            # the local sweeps of 16 right-hand sides on both paths, twice each
+            h = setup_dev()
+            v16 = np.random.default_rng(1).standard_normal((TC_NRHS, m.n_dofs))
+            for path in (hk.HK_SWEEPS_TENSOR_CORE, hk.HK_SWEEPS_CUDA_CORE):
+                if path == hk.HK_SWEEPS_TENSOR_CORE and hk.hk_info(h)["tc_record_bytes"] == 0:
+                    continue
+                hk.hk_set_sweep_path(h, path)
+                for _ in range(2):
+                    hk.hk_apply_precond(h, v16)
+            hk.hk_destroy(h)
         torch.cuda.synchronize()
         if rank == 0:
             print(json.dumps({"profile_run": True, "workload": p.name}), flush=True)
@@ -427,11 +455,47 @@ def run_ours(args, world, rank, local):
 
     so32 = solve_only(hk.HK_FP32_PRECOND, args.solve_reps)
     so64 = solve_only(hk.HK_FP64, args.solve_reps)
+    sosp = solve_only(hk.HK_SPLIT_BF16_PRECOND, args.solve_reps)
+
+    # ---- tensor-core local sweeps of the split-BF16 form against the FP32 CUDA-core sweeps, on one
+    # apply of 16 right-hand sides (the multi-right-hand-side case the tensor cores are for)
+    def sweeps_compare(n_rhs=16, reps=10):
+        h = setup_dev(hk.HK_SPLIT_BF16_PRECOND)
+        info = hk.hk_info(h)
+        if info["tc_record_bytes"] == 0:
+            hk.hk_destroy(h)
+            return {"unavailable": "tensor-core sweeps not built for these subdomains"}
+        v = np.random.default_rng(1).standard_normal((n_rhs, info["n_dofs"]))
+        out = {"rhs_per_apply": n_rhs}
+        for name, path in (("tensor_core", hk.HK_SWEEPS_TENSOR_CORE), ("cuda_core_fp32", hk.HK_SWEEPS_CUDA_CORE)):
+            hk.hk_set_sweep_path(h, path)
+            hk.hk_apply_precond(h, v)
+            hk.hk_set_timing(h, True)
+            for _ in range(reps):
+                hk.hk_apply_precond(h, v)
+            t = hk.hk_kernel_times(h)
+            hk.hk_set_timing(h, False)
+            out[name] = {k: 1e3 * t[k][0] / reps for k in ("local_apply", "coarse_solve", "scatter")}
+        hk.hk_destroy(h)
+        # MMA work per launch: every record entry (BF16 pair) meets 16 right-hand sides in three products
+        flops = 3 * 2 * TC_NRHS * info["tc_record_bytes"] / 4
+        tc_s = out["tensor_core"]["local_apply"] * 1e-6
+        out["speedup_local_sweeps"] = out["cuda_core_fp32"]["local_apply"] / out["tensor_core"]["local_apply"]
+        out["roofline"] = {"bound": "tensor", "kernel": "k_local_apply_tc", "achieved": flops / tc_s / 1e12,
+                           "peak": BF16_PEAK, "unit": "TFLOP/s", "frac": flops / tc_s / 1e12 / BF16_PEAK,
+                           "mma_tflop_per_launch": flops / 1e12, "record_bytes_per_launch": info["tc_record_bytes"],
+                           "record_gbs": info["tc_record_bytes"] / tc_s / 1e9,
+                           "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)",
+                           "note": "a chain of about L/2 dependent level steps per subdomain, each a few dozen "
+                                   "N = 16 MMAs: issue- and latency-bound, not throughput-bound"}
+        return out
+
+    tc_cmp = sweeps_compare()
 
     # ---- roofline from the live kernel timings of the timed steps
     info0, _, its0 = rec[0]
     kt0 = rec_t[0][1]
-    pf = 4 if prec == hk.HK_FP32_PRECOND else 8
+    pf = 8 if prec == hk.HK_FP64 else 4
     n, n0 = info0["n_dofs"], info0["n0"]
     It, ze = info0["dof_total"], info0["coarse_elems"]
     # algorithmic bytes of one apply of s right-hand sides: the banded-LU fill |I_i| (3 w_i + 1) of
@@ -491,7 +555,7 @@ def run_ours(args, world, rank, local):
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64 Krylov / f32 preconditioner" if prec == hk.HK_FP32_PRECOND else "f64",
+            "dtype": DTYPES[args.precision],
             "data": "synthetic (seeded)", "config": workload_config(p, args.workload, args.precision),
             "iterations": [int(x) for x in its0],
             "setup_phases_ms": dict(zip(["assembly", "decomposition", "local_factors", "eigen", "coarse"],
@@ -501,7 +565,8 @@ def run_ours(args, world, rank, local):
                           "eigen_kernels_gflop": dict(zip(["inertia", "lanczos", "refine"], eig_gflop)),
                           "solve": statistics.mean(step_ms) - statistics.mean(setup_ms)},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
-            "solve_only": {"fp32_precond": so32, "fp64": so64},
+            "solve_only": {"fp32_precond": so32, "fp64": so64, "split_bf16": sosp},
+            "split_bf16_local_sweeps": tc_cmp,
             "kernel_ms_per_launch": per, "roofline": roof, "roofline_apply": roof_apply,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
@@ -526,7 +591,7 @@ def run_serving(args, world, rank, local):
 
     torch.cuda.set_device(local)
     ops = W.config_c5()
-    prec = hk.HK_FP32_PRECOND if args.precision == "fp32" else hk.HK_FP64
+    prec = PRECISIONS[args.precision]
     budget = int(args.budget_gb * (1 << 30))
     srv = hk.hk_server_create(budget, n_slots=args.slots, max_batch_rhs=16)
     ids = [hk.server_add_problem(srv, p, prec) for p in ops]
@@ -588,7 +653,7 @@ def run_serving(args, world, rank, local):
     line = {"metric": METRIC, "value": burst["solves_per_s"], "unit": "solves/s", "n_gpus": world,
             "steps": args.requests, "warmup": len(ops), "ms_per_step": 1e3 * burst["span_s"] / args.requests,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64 Krylov / f32 preconditioner" if prec == hk.HK_FP32_PRECOND else "f64",
+            "dtype": DTYPES[args.precision],
             "data": "synthetic (seeded)",
             "config": {"workload": "c5 serving: 24 cached operators (16 2D h in 1/128..1/512, k in [20,100], "
                                    "checkerboard a in 10^U[0,2]; 8 3D h=1/32 Kuhn tets, k=20, 4x4x4 boxes); "
@@ -640,7 +705,7 @@ def run_batched(args, world, rank, local):
 
     torch.cuda.set_device(local)
     probs = W.config_c4()
-    prec = hk.HK_FP32_PRECOND if args.precision == "fp32" else hk.HK_FP64
+    prec = PRECISIONS[args.precision]
     budget = int(args.budget_gb * (1 << 30))
     nrhs = sum(p.rhs.shape[0] for p in probs)
 
@@ -683,7 +748,7 @@ def run_batched(args, world, rank, local):
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": len(times),
             "warmup": max(1, args.warmup), "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64 Krylov / f32 preconditioner" if prec == hk.HK_FP32_PRECOND else "f64",
+            "dtype": DTYPES[args.precision],
             "data": "synthetic (seeded)",
             "config": {"workload": f"c4 batched: {len(probs)} independent 2D instances (h in 1/128..1/384, "
                                    f"k in [20,80], checkerboard a in 10^U[0,2], 4..12 boxes per side), "
@@ -730,7 +795,7 @@ def main():
     ap.add_argument("--requests", type=int, default=2000, help="c5: requests per replay")
     ap.add_argument("--slots", type=int, default=4, help="c5: server worker slots")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="c5: server device-memory budget")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "split"])
     ap.add_argument("--solve-reps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-run", action="store_true",

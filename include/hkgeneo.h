@@ -152,6 +152,11 @@ typedef struct {
                                   (0: not built, i.e. another precision form or sweeps unavailable) */
   int last_sweeps;             /* local sweeps of the last preconditioner apply: HK_SWEEPS_CUDA_CORE or
                                   HK_SWEEPS_TENSOR_CORE (0 before the first apply) */
+  int twist_moved;             /* subdomains whose block factorisation meets at a level other than the
+                                  middle one (chosen for a smaller pivot growth, see local_growth) */
+  double local_growth[2];      /* largest pivot growth max|pivot block inverse| x max|B_i| over the local
+                                  factorisations: [0] as factored (twist level chosen per subdomain),
+                                  [1] had every subdomain been factored towards its middle level */
 } hk_info_t;
 
 hk_status hk_info(const hk_handle* h, hk_info_t* info);

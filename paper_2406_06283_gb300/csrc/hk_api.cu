@@ -199,8 +199,9 @@ static hk_status setup_impl(hk_handle* h, const hk_mesh* mesh, const double* coe
     h->setup_ms[2] = t.stop();
     HK_TRY(phase_eigen(h, d_elem_in));
     h->setup_ms[3] = t.stop();
-    HK_TRY(phase_local_factors_end(h));
+    HK_TRY(phase_local_factors_mid(h));
     HK_TRY(phase_coarse(h));
+    HK_TRY(phase_local_factors_end(h));
     h->setup_ms[4] = t.stop();
   } else {
     HK_TRY(phase_local_factors_end(h));
@@ -392,6 +393,9 @@ extern "C" hk_status hk_info(const hk_handle* h, hk_info_t* info) {
   for (int i = 0; i < 4; ++i) info->eigen_kernel_gflop[i] = h->eigen_gflop[i];
   info->tc_record_bytes = h->tc_ok ? h->tc_bytes : 0;
   info->last_sweeps = h->last_sweeps;
+  info->twist_moved = h->twist_moved;
+  info->local_growth[0] = h->growth_twist;
+  info->local_growth[1] = h->growth_mid;
   return HK_OK;
 }
 

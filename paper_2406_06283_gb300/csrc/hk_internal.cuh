@@ -84,6 +84,7 @@ struct Sub {
   int c_off;            // offset in the coarse vector
   long long z_off;      // offset of Z_i (nI * m)
   int bw;               // half bandwidth of D_II in level order
+  int M;                // twist level of its local factorisation (see hk_local.cu)
 };
 
 struct hk_handle {
@@ -210,6 +211,14 @@ struct hk_handle {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // apply: coarse path beside the local sweeps
   cudaStream_t co_stream = nullptr;                    // apply: the coarse path's stream (high priority)
   bool lf_pending = false;
+  int lf_stage = 0;             // local factors: 1 growth pass launched, 2 factors launched
+  std::vector<int> lev_host;    // setup only: host copy of the level pointers
+  double* d_gF = nullptr;       // setup only: growth pass scratch factors, offsets, results
+  long long* d_gfo = nullptr;
+  double* d_gval = nullptr;
+  int* d_twist = nullptr;       // per subdomain: twist level M of its factorisation
+  double growth_twist = 0, growth_mid = 0;  // max over subdomains of the pivot growth (chosen M; M = (L-1)/2)
+  int twist_moved = 0;          // subdomains whose twist level is not the middle one
   int* d_ctl = nullptr;         // [0] inner step j, [1] cycles run, [2] inner steps run
   const int* g_jp = nullptr;    // while an inner step is captured: the device word holding j
   long long g_jstride = 0;      // ... and the distance between consecutive Krylov vectors
@@ -309,6 +318,7 @@ hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<i
 hk_status phase_assembly(hk_handle* h, const hk_mesh* mesh, const double* coeff);
 hk_status phase_decomposition(hk_handle* h, const int32_t* elem_to_sub, uint8_t** d_elem_in_out);
 hk_status phase_local_factors_begin(hk_handle* h);
+hk_status phase_local_factors_mid(hk_handle* h);
 hk_status phase_local_factors_end(hk_handle* h);
 hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in);
 hk_status phase_coarse(hk_handle* h);

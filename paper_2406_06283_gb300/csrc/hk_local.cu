@@ -30,20 +30,19 @@ static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 __host__ __device__ __forceinline__ long long pad4(long long x) { return (x + 3) & ~3LL; }
 __host__ __device__ __forceinline__ int twist_mid(int L) { return (L - 1) / 2; }
 
-// Columns of the coupling product stored after the inverse block of level j.
-__host__ __device__ __forceinline__ long long coupling_cols(const int* lp, int L, int j) {
-  int M = twist_mid(L);
+// Columns of the coupling product stored after the inverse block of level j (twist level M).
+__host__ __device__ __forceinline__ long long coupling_cols(const int* lp, int L, int M, int j) {
   if (j < M) return lp[j + 2] - lp[j + 1];
   if (j > M) return lp[j] - lp[j - 1];
   return 0;
 }
 
-// Element count of the factor blocks of one subdomain.
-long long factor_elems(const int* lp, int L) {
+// Element count of the factor blocks of one subdomain factored towards level M.
+long long factor_elems(const int* lp, int L, int M) {
   long long t = 0;
   for (int j = 0; j < L; ++j) {
     long long b = lp[j + 1] - lp[j];
-    t += pad4(b * b) + pad4(b * coupling_cols(lp, L, j));
+    t += pad4(b * b) + pad4(b * coupling_cols(lp, L, M, j));
   }
   return t;
 }
@@ -52,10 +51,13 @@ long long factor_elems(const int* lp, int L) {
 // coupling products of its already eliminated neighbours (G_{j-1} above, H_{j+1} below),
 // its inverse, and its own coupling product (G_j = X^{-1} U_j towards the middle from the
 // top, H_j = X^{-1} L_j from the bottom).
-__device__ void twisted_level(int j, int L, const int* lp, const long long* fo, const int* lr, const int* lcntI,
-                              const int* lcol, const double* lval, int off, long long coff, double* F, double* S,
-                              int s_in_smem, int* piv, double* red_v, int* red_i, double* minpiv) {
-  int tid = threadIdx.x, T = blockDim.x, M = twist_mid(L);
+// gout (or NULL) receives max |X^{-1}| of the level (inf where the inverse is not finite): the growth of
+// the level's pivot block, from which the twist level is chosen.
+__device__ void twisted_level(int j, int L, int M, const int* lp, const long long* fo, const int* lr,
+                              const int* lcntI, const int* lcol, const double* lval, int off, long long coff,
+                              double* F, double* S, int s_in_smem, int* piv, double* red_v, int* red_i,
+                              double* minpiv, double* gout) {
+  int tid = threadIdx.x, T = blockDim.x;
   int r0 = lp[j], b = lp[j + 1] - r0;
   bool up = j > 0 && j <= M;        // eliminated neighbour above (top part or middle)
   bool down = j < L - 1 && j >= M;  // eliminated neighbour below (bottom part or middle)
@@ -80,6 +82,23 @@ __device__ void twisted_level(int j, int L, const int* lp, const long long* fo, 
   }
   __syncthreads();
   gauss_jordan_inverse(X, b, piv, red_v, red_i, minpiv);
+  if (gout) {
+    __syncthreads();
+    double g = 0;
+    for (int e = tid; e < b * b; e += T) {
+      double a = fabs(X[e]);
+      g = a <= 1e300 ? fmax(g, a) : INFINITY;
+    }
+    for (int o = 16; o > 0; o >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
+    if ((tid & 31) == 0) red_v[tid >> 5] = g;
+    __syncthreads();
+    if (tid == 0) {
+      double m2 = 0;
+      for (int w = 0; w < (T >> 5); ++w) m2 = fmax(m2, red_v[w]);
+      gout[j] = m2;
+    }
+    __syncthreads();
+  }
   if (s_in_smem)
     for (int e = tid; e < b * b; e += T) F[fo[j] + e] = X[e];
   if (j == M) {
@@ -106,47 +125,93 @@ __device__ void twisted_level(int j, int L, const int* lp, const long long* fo, 
   __syncthreads();
 }
 
-// fo: per subdomain, L + 1 factor offsets (elements from the start of the factor array).
-__global__ void k_block_lu(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
-                           const int* __restrict__ levptr, const int* __restrict__ lrow,
-                           const int* __restrict__ lcntI, const int* __restrict__ lcol,
-                           const double* __restrict__ lval, const long long* __restrict__ lvfo, double* F,
-                           int s_in_smem, DevStatus* st) {
-  extern __shared__ double smem[];
-  __shared__ int piv[HK_MAXB];
-  __shared__ double red_v[32];
-  __shared__ int red_i[32];
-  __shared__ double minpiv;
-  int s = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
-  const int* si = sub_info + 8 * s;
-  int nI = si[0], L = si[2], off = si[3], loff = si[5];
-  long long coff = sub_off[3 * s + 1];
-  const int* lp = levptr + loff;
-  const int* lr = lrow + off + s;
-  const long long* fo = lvfo + loff;
-  // scale for the singularity test: max |B_i| entry
+// max |B_i| entry of subdomain s (the scale of the singularity test and of the growth measure), over the CTA.
+__device__ double block_scale(int nI, int off, long long coff, const int* lr, const int* lcntI, const double* lval,
+                              double* red_v) {
+  int tid = threadIdx.x, T = blockDim.x;
   double mx = 0;
   for (int a = tid; a < nI; a += T)
     for (int q = 0; q < lcntI[off + a]; ++q) mx = fmax(mx, fabs(lval[coff + lr[a] + q]));
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((tid & 31) == 0) red_v[tid >> 5] = mx;
   __syncthreads();
+  double m2 = 0;
+  for (int w = 0; w < (T >> 5); ++w) m2 = fmax(m2, red_v[w]);
+  __syncthreads();
+  return m2;
+}
+
+// fo: per subdomain, L + 1 factor offsets (elements from the start of the factor array); twist: the
+// level M each subdomain is factored towards.
+__global__ void k_block_lu(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
+                           const int* __restrict__ levptr, const int* __restrict__ lrow,
+                           const int* __restrict__ lcntI, const int* __restrict__ lcol,
+                           const double* __restrict__ lval, const long long* __restrict__ lvfo,
+                           const int* __restrict__ twist, double* F, int s_in_smem, DevStatus* st) {
+  extern __shared__ double smem[];
+  __shared__ int piv[HK_MAXB];
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ double minpiv;
+  int s = blockIdx.x, tid = threadIdx.x;
+  const int* si = sub_info + 8 * s;
+  int nI = si[0], L = si[2], off = si[3], loff = si[5];
+  long long coff = sub_off[3 * s + 1];
+  const int* lp = levptr + loff;
+  const int* lr = lrow + off + s;
+  const long long* fo = lvfo + loff;
+  double scale = block_scale(nI, off, coff, lr, lcntI, lval, red_v);
+  if (tid == 0) minpiv = 1e300;
+  __syncthreads();
+  int M = twist[s];
+  for (int j = 0; j < M; ++j)
+    twisted_level(j, L, M, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv,
+                  nullptr);
+  for (int j = L - 1; j > M; --j)
+    twisted_level(j, L, M, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv,
+                  nullptr);
+  twisted_level(M, L, M, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv,
+                nullptr);
+  if (tid == 0 && !(minpiv > 1e-10 * scale)) dev_fail(st, HK_SINGULAR_LOCAL, s, minpiv / scale);
+}
+
+// Growth pass for the choice of the twist level.  Both one-sided block eliminations of B_i over all
+// levels: from the top (the factorisation towards M = L - 1: S_0 = D_0, S_j = D_j - L_j S_{j-1}^{-1} U_{j-1})
+// and from the bottom (towards M = 0: T_{L-1} = D_{L-1}, T_j = D_j - U_j T_{j+1}^{-1} L_{j+1}), each into its
+// own scratch factor array, with max |S_j^{-1}| into gtop and max |T_j^{-1}| into gbot per level and
+// max |B_i| into gscale.  A twisted factorisation towards M uses S_j for j < M and T_j for j > M; its middle
+// block Sigma_M has Sigma_M^{-1} = (B_i^{-1})_{MM}, bounded by B_i^{-1} whatever M is.
+__global__ void k_chain_growth(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
+                               const int* __restrict__ levptr, const int* __restrict__ lrow,
+                               const int* __restrict__ lcntI, const int* __restrict__ lcol,
+                               const double* __restrict__ lval, const long long* __restrict__ fo_top,
+                               const long long* __restrict__ fo_bot, double* Ftop, double* Fbot, int s_in_smem,
+                               double* gtop, double* gbot, double* gscale) {
+  extern __shared__ double smem[];
+  __shared__ int piv[HK_MAXB];
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ double minpiv;
+  int s = blockIdx.x, tid = threadIdx.x;
+  const int* si = sub_info + 8 * s;
+  int nI = si[0], L = si[2], off = si[3], loff = si[5];
+  long long coff = sub_off[3 * s + 1];
+  const int* lp = levptr + loff;
+  const int* lr = lrow + off + s;
+  double scale = block_scale(nI, off, coff, lr, lcntI, lval, red_v);
   if (tid == 0) {
-    double m2 = 0;
-    for (int w = 0; w < (T >> 5); ++w) m2 = fmax(m2, red_v[w]);
-    red_v[0] = m2;
     minpiv = 1e300;
+    gscale[s] = scale;
   }
   __syncthreads();
-  double scale = red_v[0];
-  __syncthreads();
-  int M = twist_mid(L);
-  for (int j = 0; j < M; ++j)
-    twisted_level(j, L, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv);
-  for (int j = L - 1; j > M; --j)
-    twisted_level(j, L, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv);
-  twisted_level(M, L, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv);
-  if (tid == 0 && !(minpiv > 1e-10 * scale)) dev_fail(st, HK_SINGULAR_LOCAL, s, minpiv / scale);
+  const long long* ft = fo_top + loff;
+  for (int j = 0; j < L; ++j)
+    twisted_level(j, L, L - 1, lp, ft, lr, lcntI, lcol, lval, off, coff, Ftop, smem, s_in_smem, piv, red_v, red_i,
+                  &minpiv, gtop + loff);
+  const long long* fb = fo_bot + loff;
+  for (int j = L - 1; j >= 0; --j)
+    twisted_level(j, L, 0, lp, fb, lr, lcntI, lcol, lval, off, coff, Fbot, smem, s_in_smem, piv, red_v, red_i,
+                  &minpiv, gbot + loff);
 }
 
 // Number of couplings L_j (row in level j, column in level j-1) of every subdomain.
@@ -245,7 +310,7 @@ __global__ void k_pack_levels(const int* __restrict__ sub_info, const long long*
                               const int* __restrict__ lcntI, const int* __restrict__ lcol,
                               const double* __restrict__ lvalB, const double* __restrict__ F,
                               const long long* __restrict__ lvfo, const long long* __restrict__ lvtab,
-                              unsigned char* pack) {
+                              const int* __restrict__ twist, unsigned char* pack) {
   int s = blockIdx.x, tid = threadIdx.x, T_ = blockDim.x;
   const int* si = sub_info + 8 * s;
   int L = si[2], off = si[3], loff = si[5];
@@ -253,7 +318,7 @@ __global__ void k_pack_levels(const int* __restrict__ sub_info, const long long*
   const int* lp = levptr + loff;
   const int* lr = lrow + off + s;
   const long long* fo = lvfo + loff;
-  int M = twist_mid(L);
+  int M = twist[s];
   // -X^{-1} B[level j, c] for a node c of a neighbour level: the couplings of row c inside level j
   auto coupled = [&](const double* Xi, int b, int r0, int row, int c) -> double {
     const int* cl = lcol + coff + lr[c];
@@ -427,7 +492,7 @@ __global__ void __launch_bounds__(HK_APPLY_MAXT, 1) k_local_apply(
     const int* __restrict__ sub_info, const long long* __restrict__ sub_off, const int* __restrict__ Ilev,
     const long long* __restrict__ lvtab, const unsigned char* __restrict__ pack, long long I_total,
     int stage_bytes, int K, int WG, int max_L, int max_dof, T* ybuf, DevStatus* st, const int* __restrict__ jp,
-    long long jstride) {
+    long long jstride, const int* __restrict__ twist) {
   constexpr int R = NR < 4 ? NR : 4;
   constexpr int WS = NR / R;  // right-hand-side groups, each two half groups of WG warps
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -441,15 +506,17 @@ __global__ void __launch_bounds__(HK_APPLY_MAXT, 1) k_local_apply(
   int prod = warp - nwc;  // 0: top stream, 1: bottom stream, < 0: consumer
   const int* si = sub_info + 8 * s;
   int nI = si[0], L = si[2], off = si[3], loff = si[5];
-  int M = twist_mid(L);
+  int M = twist[s];
   int xs = nI + 4;  // rows per group slice of x
   int nst[2] = {2 * M + 1, 2 * (L - 1 - M)};  // steps of the top and bottom streams
   // shared memory: two record rings | level table (4 x int64 per level) | step parameters of both
   // streams (int4 each) | their record offsets | dof indices (16-byte aligned span) | x
   long long* tab = reinterpret_cast<long long*>(smem_raw + 2LL * K * stage_bytes);
-  int4* sp = reinterpret_cast<int4*>(tab + 4 * (long long)max_L);              // [2][max_L]
-  long long* so = reinterpret_cast<long long*>(sp + 2 * (long long)max_L);     // [2][max_L]
-  int* idx = reinterpret_cast<int*>(so + 2 * (long long)max_L);
+  // a stream has at most 2L - 1 steps (the twist level may be any level)
+  int SL = 2 * max_L;
+  int4* sp = reinterpret_cast<int4*>(tab + 4 * (long long)max_L);  // [2][SL]
+  long long* so = reinterpret_cast<long long*>(sp + 2 * (long long)SL);  // [2][SL]
+  int* idx = reinterpret_cast<int*>(so + 2 * (long long)SL);
   int ioff = off & 3;  // position of the first index in the aligned span
   int ispan = (ioff + nI + 3) & ~3;
   T* x = reinterpret_cast<T*>(idx + ((max_dof + 7) & ~3));  // WS groups x (nI + 4) x R
@@ -505,8 +572,8 @@ __global__ void __launch_bounds__(HK_APPLY_MAXT, 1) k_local_apply(
       }
       int lg = 0;  // G = 2^lg lanes per row, as many as keep b * G <= nthr (one pass)
       while (lg < 5 && (b << (lg + 1)) <= nthr) ++lg;
-      sp[h * max_L + k] = make_int4(b | (lg << 16), ld | ((kind == 0) << 16), ls, in_row | (rc << 16));
-      so[h * max_L + k] = kind == 0 ? en[0] : en[1];
+      sp[h * SL + k] = make_int4(b | (lg << 16), ld | ((kind == 0) << 16), ls, in_row | (rc << 16));
+      so[h * SL + k] = kind == 0 ? en[0] : en[1];
     }
   }
   __syncthreads();
@@ -514,11 +581,11 @@ __global__ void __launch_bounds__(HK_APPLY_MAXT, 1) k_local_apply(
   int ps_k = 0, ps_c = 0;
   auto next_chunk = [&](int h, const unsigned char*& src, unsigned& bytes) -> bool {
     if (ps_k >= nst[h]) return false;
-    int4 pv = sp[h * max_L + ps_k];
+    int4 pv = sp[h * SL + ps_k];
     int b = pv.x & 0xFFFF, ld = pv.y & 0xFFFF, rc = pv.w >> 16;
     long long rowb = (long long)ld * sizeof(T);
     int row0 = ps_c * rc, nrows = b - row0 < rc ? b - row0 : rc;
-    src = pack + so[h * max_L + ps_k] + row0 * rowb;
+    src = pack + so[h * SL + ps_k] + row0 * rowb;
     bytes = (unsigned)(nrows * rowb);
     if (row0 + nrows >= b) ++ps_k, ps_c = 0;
     else ++ps_c;
@@ -603,7 +670,7 @@ __global__ void __launch_bounds__(HK_APPLY_MAXT, 1) k_local_apply(
     }
     if (h == 0 && k == n_first + 1) dead = group_any(dead, 2 * WG, jid) != 0;
     if (k == nst[h]) break;
-    int4 pv = sp[h * max_L + k];
+    int4 pv = sp[h * SL + k];
     int b = pv.x & 0xFFFF, lg = pv.x >> 16, ld = pv.y & 0xFFFF, assign = pv.y >> 16, ls = pv.z,
         in_row = pv.w & 0xFFFF, rc = pv.w >> 16;
     const T* xin = xg + (long long)in_row * R;
@@ -878,7 +945,7 @@ static ApplyShape apply_shape(hk_handle* h, int s) {
   ApplyShape a;
   a.WG = apply_wg(h);
   a.threads = 32 * (WS * 2 * a.WG + 2);
-  size_t vec = 80 * (size_t)h->max_L + 4 * (size_t)((h->max_dof + 7) & ~3) +
+  size_t vec = 128 * (size_t)h->max_L + 4 * (size_t)((h->max_dof + 7) & ~3) +
                sizeof(T) * (size_t)NR * ((size_t)h->max_dof + 4);
   size_t stage = (size_t)h->pack_stage;
   if (!h->n_sm) cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->dev);
@@ -906,7 +973,8 @@ static hk_status launch_local(hk_handle* h, int s, const double* v, const int* a
   HK_TIMED(h, HK_T_LOCAL_APPLY,
            (k_local_apply<T, NR><<<grid, a.threads, a.shm, h->stream>>>(
                h->n, s, v, active, h->d_sub_info, h->d_sub_off, h->d_I, h->d_lvtab, h->d_pack, h->I_total,
-               (int)h->pack_stage, a.K, a.WG, h->max_L, h->max_dof, ybuf, h->d_status, h->g_jp, h->g_jstride))); HK_COUNT_LAUNCH();
+               (int)h->pack_stage, a.K, a.WG, h->max_L, h->max_dof, ybuf, h->d_status, h->g_jp, h->g_jstride,
+               h->d_twist))); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   return HK_OK;
 }
@@ -920,7 +988,7 @@ static hk_status apply_t(hk_handle* h, int s, const double* v, double* z, const 
   int do_coarse = h->p.levels != HK_ONE_LEVEL && h->n0 > 0;
   size_t budget = 220 * 1024 - 4 * (size_t)h->pack_stage;
   int nr = 16;
-  budget -= 80 * (size_t)h->max_L + 4 * (size_t)((h->max_dof + 7) & ~3);
+  budget -= 128 * (size_t)h->max_L + 4 * (size_t)((h->max_dof + 7) & ~3);
   int wg = apply_wg(h);
   while (nr > 1 && (nr > s || sizeof(T) * ((size_t)h->max_dof + 4) * nr > budget ||
                     32 * ((nr / std::min(nr, 4)) * 2 * wg + 2) > HK_APPLY_MAXT))
@@ -1166,25 +1234,30 @@ hk_status build_apply_z(hk_handle* h) {
   return HK_OK;
 }
 
-// Host work, sizes and allocations of the local factorisation on the setup stream; then the factor
-// kernels (block LU, level records) on the handle's auxiliary stream, where they overlap the
-// eigenproblems (which leave SMs and the FP64 pipes idle for most of their time).
-// phase_local_factors_end joins them.
+// Host work, sizes and allocations of the local factorisation, in three parts.
+//   begin: the growth pass (both one-sided block eliminations of every B_i) on the handle's auxiliary
+//     stream, where it overlaps the eigenproblems;
+//   mid: the twist level of every subdomain from the growth pass, the factor and record tables, then the
+//     factor kernels (block LU, level records) on the auxiliary stream, where they overlap the coarse
+//     phase;
+//   end: joins them.
+// Twist level.  G(M) = max(max_{j<M} g_top[j], max_{j>M} g_bot[j]) (g = max |pivot block inverse| x
+// max |B_i|) is the growth of the factorisation towards M; the middle block never adds to it.  The
+// choice is the M nearest the middle level (the shortest dependent chain of the apply) among those
+// with G(M) <= 2 min G.
 hk_status phase_local_factors_begin(hk_handle* h) {
   cudaStream_t st = h->stream;
   int ns = h->n_sub;
-  std::vector<int> lev(h->I_total + ns);
+  std::vector<int>& lev = h->lev_host;
+  lev.assign(h->I_total + ns, 0);
   HK_CUDA(cudaMemcpyAsync(lev.data(), h->d_lev, sizeof(int) * lev.size(), cudaMemcpyDeviceToHost, st));
   HK_CUDA(cudaStreamSynchronize(st));
-  long long fo = 0;
   h->max_L = 0;
   for (int s = 0; s < ns; ++s) {
     Sub& u = h->subs[s];
     h->max_L = std::max(h->max_L, u.L);
-    u.f_off = fo;
-    fo += factor_elems(&lev[u.lev_off], u.L);
+    u.M = twist_mid(u.L);
   }
-  h->f_total = fo;
   HK_TRY(upload_sub_info(h));
   if (h->p.levels == HK_COARSE_ONLY) return HK_OK;
   {
@@ -1198,13 +1271,115 @@ hk_status phase_local_factors_begin(hk_handle* h) {
     h->lower_nnz = (long long)c;
     dfree(h, d_cnt);
   }
+  // scratch factors of the two one-sided eliminations and their per-level offsets
+  std::vector<long long> fot(h->I_total + ns, 0), fob(h->I_total + ns, 0);
+  long long tt = 0, tb = 0;
+  for (int s = 0; s < ns; ++s) {
+    const Sub& u = h->subs[s];
+    const int* lp = &lev[u.lev_off];
+    for (int j = 0; j < u.L; ++j) {
+      long long b = lp[j + 1] - lp[j];
+      fot[u.lev_off + j] = tt;
+      fob[u.lev_off + j] = tb;
+      tt += pad4(b * b) + pad4(b * coupling_cols(lp, u.L, u.L - 1, j));
+      tb += pad4(b * b) + pad4(b * coupling_cols(lp, u.L, 0, j));
+    }
+  }
+  HK_TRY(dalloc(h, &h->d_gF, (size_t)(tt + tb)));
+  HK_TRY(dalloc(h, &h->d_gfo, fot.size() + fob.size()));
+  HK_TRY(dalloc(h, &h->d_gval, 2 * lev.size() + (size_t)ns));
+  HK_CUDA(cudaMemcpyAsync(h->d_gfo, fot.data(), sizeof(long long) * fot.size(), cudaMemcpyHostToDevice, st));
+  HK_CUDA(cudaMemcpyAsync(h->d_gfo + fot.size(), fob.data(), sizeof(long long) * fob.size(), cudaMemcpyHostToDevice,
+                          st));
+  size_t shm = sizeof(double) * (size_t)h->max_level * h->max_level;
+  int s_in_smem = shm <= 200 * 1024;
+  if (!s_in_smem) shm = 0;
+  HK_TRY(hk_allow_smem(k_block_lu));
+  HK_TRY(hk_allow_smem(k_chain_growth));
+  // the auxiliary stream starts after everything above (allocations, memsets, table upload)
+  if (!h->aux_stream) HK_CUDA(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
+  if (!h->ev_lf) HK_CUDA(cudaEventCreateWithFlags(&h->ev_lf, cudaEventDisableTiming));
+  if (!h->co_stream) {
+    // the apply's coarse branch: short kernels that should not queue behind the local sweeps' CTAs
+    int lo = 0, hi = 0;
+    HK_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    HK_CUDA(cudaStreamCreateWithPriority(&h->co_stream, cudaStreamNonBlocking, hi));
+  }
+  if (!h->ev_fork) HK_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  if (!h->ev_join) HK_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  HK_CUDA(cudaEventRecord(h->ev_lf, st));
+  HK_CUDA(cudaStreamWaitEvent(h->aux_stream, h->ev_lf, 0));
+  double* gv = h->d_gval;
+  k_chain_growth<<<ns, 256, shm, h->aux_stream>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI,
+                                                  h->d_lcol, h->d_lvalB, h->d_gfo, h->d_gfo + fot.size(), h->d_gF,
+                                                  h->d_gF + tt, s_in_smem, gv, gv + lev.size(),
+                                                  gv + 2 * lev.size());
+  HK_COUNT_LAUNCH();
+  HK_LAUNCH_CHECK();
+  HK_CUDA(cudaEventRecord(h->ev_lf, h->aux_stream));
+  h->lf_stage = 1;
+  return HK_OK;
+}
+
+hk_status phase_local_factors_mid(hk_handle* h) {
+  if (h->lf_stage != 1) return HK_OK;
+  h->lf_stage = 2;
+  cudaStream_t st = h->stream;
+  int ns = h->n_sub;
+  const std::vector<int>& lev = h->lev_host;
+  // growth pass results, then the twist levels
+  std::vector<double> g(2 * lev.size() + ns);
+  HK_CUDA(cudaEventSynchronize(h->ev_lf));
+  HK_CUDA(cudaMemcpy(g.data(), h->d_gval, sizeof(double) * g.size(), cudaMemcpyDeviceToHost));
+  dfree(h, h->d_gF);
+  dfree(h, h->d_gfo);
+  dfree(h, h->d_gval);
+  h->d_gF = nullptr;
+  h->d_gfo = nullptr;
+  h->d_gval = nullptr;
+  const double* gt = g.data();
+  const double* gb = g.data() + lev.size();
+  const double* gs = g.data() + 2 * lev.size();
+  h->growth_twist = 0;
+  h->growth_mid = 0;
+  h->twist_moved = 0;
+  std::vector<int> twist(ns);
+  long long fo = 0;
+  for (int s = 0; s < ns; ++s) {
+    Sub& u = h->subs[s];
+    int L = u.L, mid = twist_mid(L);
+    const double* a = gt + u.lev_off;
+    const double* b = gb + u.lev_off;
+    std::vector<double> pre(L + 1, 0), suf(L + 1, 0);  // pre[M] = max_{j<M} a_j, suf[M] = max_{j>M} b_j
+    for (int j = 0; j < L; ++j) pre[j + 1] = std::max(pre[j], a[j]);
+    for (int j = L - 1; j > 0; --j) suf[j - 1] = std::max(suf[j], b[j]);
+    double best = 1e308;
+    for (int M = 0; M < L; ++M) best = std::min(best, std::max(pre[M], suf[M]));
+    int choice = mid;
+    for (int d = 0; d < L; ++d) {  // nearest the middle first
+      int c0 = mid - d, c1 = mid + d;
+      if (c0 >= 0 && std::max(pre[c0], suf[c0]) <= 2 * best) { choice = c0; break; }
+      if (c1 < L && std::max(pre[c1], suf[c1]) <= 2 * best) { choice = c1; break; }
+    }
+    u.M = choice;
+    twist[s] = choice;
+    h->growth_twist = std::max(h->growth_twist, std::max(pre[choice], suf[choice]) * gs[s]);
+    h->growth_mid = std::max(h->growth_mid, std::max(pre[mid], suf[mid]) * gs[s]);
+    h->twist_moved += choice != mid;
+    u.f_off = fo;
+    fo += factor_elems(&lev[u.lev_off], u.L, u.M);
+  }
+  h->f_total = fo;
+  HK_TRY(upload_sub_info(h));
+  HK_TRY(dalloc(h, &h->d_twist, (size_t)ns));
+  HK_CUDA(cudaMemcpyAsync(h->d_twist, twist.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
   // level records for the apply, in the arithmetic type of the precision form
   size_t esz = precond_f32(h->p) ? 4 : 8;
   // record chunks of at most 32 KB, smaller where two stages per ring would not fit beside the vectors of
   // a one-right-hand-side apply of the largest subdomain
   long long chunk = HK_CHUNK_BYTES;
   {
-    long long vec1 = 80LL * h->max_L + 4LL * ((h->max_dof + 7) & ~3) + (long long)esz * (h->max_dof + 4);
+    long long vec1 = 128LL * h->max_L + 4LL * ((h->max_dof + 7) & ~3) + (long long)esz * (h->max_dof + 4);
     while (chunk > 2048 && 4 * chunk + vec1 > 216 * 1024) chunk >>= 1;
   }
   std::vector<long long> tab(4 * (h->I_total + ns), 0);
@@ -1213,13 +1388,13 @@ hk_status phase_local_factors_begin(hk_handle* h) {
   for (int s = 0; s < ns; ++s) {
     const Sub& u = h->subs[s];
     const int* lp = &lev[u.lev_off];
-    int M = twist_mid(u.L);
+    int M = u.M;
     long long fcur = u.f_off;
     for (int j = 0; j < u.L; ++j) {
       long long b = lp[j + 1] - lp[j], bn = j + 1 < u.L ? lp[j + 2] - lp[j + 1] : 0;
       long long bp = j > 0 ? lp[j] - lp[j - 1] : 0;
       lvfo[u.lev_off + j] = fcur;
-      fcur += pad4(b * b) + pad4(b * coupling_cols(lp, u.L, j));
+      fcur += pad4(b * b) + pad4(b * coupling_cols(lp, u.L, M, j));
       long long lb = (j > 0 && j <= M) ? bp : 0, rb = (j < u.L - 1 && j >= M) ? bn : 0;
       long long cb = j < M ? bn : j > M ? bp : 0;
       long long rowf = pad4(lb + b + rb) * esz, rowb = pad4(cb) * esz;  // multiples of 16 bytes
@@ -1248,29 +1423,21 @@ hk_status phase_local_factors_begin(hk_handle* h) {
   size_t shm = sizeof(double) * (size_t)h->max_level * h->max_level;
   int s_in_smem = shm <= 200 * 1024;
   if (!s_in_smem) shm = 0;
-  HK_TRY(hk_allow_smem(k_block_lu));
   // the auxiliary stream starts after everything above (allocations, memsets, table upload)
-  if (!h->aux_stream) HK_CUDA(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
-  if (!h->ev_lf) HK_CUDA(cudaEventCreateWithFlags(&h->ev_lf, cudaEventDisableTiming));
-  if (!h->co_stream) {
-    // the apply's coarse branch: short kernels that should not queue behind the local sweeps' CTAs
-    int lo = 0, hi = 0;
-    HK_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-    HK_CUDA(cudaStreamCreateWithPriority(&h->co_stream, cudaStreamNonBlocking, hi));
-  }
-  if (!h->ev_fork) HK_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-  if (!h->ev_join) HK_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   HK_CUDA(cudaEventRecord(h->ev_lf, st));
   HK_CUDA(cudaStreamWaitEvent(h->aux_stream, h->ev_lf, 0));
   cudaStream_t ax = h->aux_stream;
   k_block_lu<<<ns, 256, shm, ax>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
-                                   h->d_lvalB, h->d_lvfo, h->d_F64, s_in_smem, h->d_status); HK_COUNT_LAUNCH();
+                                   h->d_lvalB, h->d_lvfo, h->d_twist, h->d_F64, s_in_smem, h->d_status);
+  HK_COUNT_LAUNCH();
   if (esz == 4)
     k_pack_levels<float><<<ns, 256, 0, ax>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI,
-                                             h->d_lcol, h->d_lvalB, h->d_F64, h->d_lvfo, h->d_lvtab, h->d_pack);
+                                             h->d_lcol, h->d_lvalB, h->d_F64, h->d_lvfo, h->d_lvtab, h->d_twist,
+                                             h->d_pack);
   else
     k_pack_levels<double><<<ns, 256, 0, ax>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI,
-                                              h->d_lcol, h->d_lvalB, h->d_F64, h->d_lvfo, h->d_lvtab, h->d_pack);
+                                              h->d_lcol, h->d_lvalB, h->d_F64, h->d_lvfo, h->d_lvtab, h->d_twist,
+                                              h->d_pack);
   HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   HK_TRY(tc_pack(h, ax));
@@ -1281,6 +1448,9 @@ hk_status phase_local_factors_begin(hk_handle* h) {
 
 // Joins the factor kernels into the setup stream, checks them, frees the FP64 factors.
 hk_status phase_local_factors_end(hk_handle* h) {
+  HK_TRY(phase_local_factors_mid(h));
+  h->lev_host.clear();
+  h->lev_host.shrink_to_fit();
   if (!h->lf_pending) return HK_OK;
   h->lf_pending = false;
   HK_CUDA(cudaStreamWaitEvent(h->stream, h->ev_lf, 0));

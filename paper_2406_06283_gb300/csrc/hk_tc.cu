@@ -59,7 +59,6 @@
 __host__ __device__ __forceinline__ int tc_pad8(int x) { return (x + 7) & ~7; }
 __host__ __device__ __forceinline__ int tc_pad16(int x) { return (x + 15) & ~15; }
 __host__ __device__ __forceinline__ long long tc_align128(long long x) { return (x + 127) & ~127LL; }
-__host__ __device__ __forceinline__ int tc_mid(int L) { return (L - 1) / 2; }
 
 // Level table entry (4 x int64 per level): [0] first-sweep record offset (bytes), [1] second-sweep
 // record offset, [2] level start | P_j << 32, [3] b | Kf << 16 | Kb << 32 (record columns, multiples
@@ -223,7 +222,7 @@ __global__ void k_pack_tc(const int* __restrict__ sub_info, const long long* __r
                           const int* __restrict__ lcntI, const int* __restrict__ lcol,
                           const double* __restrict__ lvalB, const double* __restrict__ F,
                           const long long* __restrict__ lvfo, const long long* __restrict__ tab,
-                          unsigned char* pack) {
+                          const int* __restrict__ twist, unsigned char* pack) {
   int s = blockIdx.x, tid = threadIdx.x, T_ = blockDim.x;
   const int* si = sub_info + 8 * s;
   int L = si[2], off = si[3], loff = si[5];
@@ -232,7 +231,7 @@ __global__ void k_pack_tc(const int* __restrict__ sub_info, const long long* __r
   const int* lr = lrow + off + s;
   const long long* fo = lvfo + loff;
   const long long* tb = tab + 4 * (long long)loff;
-  int M = tc_mid(L);
+  int M = twist[s];
   for (int j = 0; j < L; ++j) {
     int r0 = lp[j], b = lp[j + 1] - r0, pb = tc_pad8(b);
     int bn = j + 1 < L ? lp[j + 2] - lp[j + 1] : 0, bp = j > 0 ? r0 - lp[j - 1] : 0;
@@ -304,7 +303,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_local_apply_tc(
     const int* __restrict__ sub_info, const int* __restrict__ Ilev, const int* __restrict__ Iprow,
     const long long* __restrict__ tabg, const unsigned char* __restrict__ pack, long long I_total,
     int stage_bytes, int K, int max_L, int max_dof, int max_apad, float* ybuf, DevStatus* st,
-    const int* __restrict__ jp, long long jstride) {
+    const int* __restrict__ jp, long long jstride, const int* __restrict__ twist) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[2][TC_MAXK], empty[2][TC_MAXK], mbar[2], meta;
   __shared__ int sh_fail, sh_act;
@@ -316,15 +315,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_local_apply_tc(
   int s = blockIdx.x, r_base = blockIdx.y * TC_NRHS;
   int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int prod = warp - 8;  // 0: top stream, 1: bottom stream, < 0: sweeps
-  int M = tc_mid(L);
+  int M = twist[s];
   int nst[2] = {2 * M + 1, 2 * (L - 1 - M)};
   unsigned char* rings = smem_raw;
   unsigned char* xh = smem_raw + 2LL * K * stage_bytes + TC_GUARD;
   unsigned char* xl = xh + 32LL * max_apad;
   long long* tab = reinterpret_cast<long long*>(xl + 32LL * max_apad);
-  int4* sp = reinterpret_cast<int4*>(tab + 4LL * (max_L + 1));
-  long long* so = reinterpret_cast<long long*>(sp + 2LL * max_L);
-  int* idx = reinterpret_cast<int*>(so + 2LL * max_L);
+  // a stream has at most 2L - 1 steps (the twist level may be any level)
+  int SL = 2 * max_L;
+  int4* sp = reinterpret_cast<int4*>(tab + 4LL * (max_L + 1));  // [2][SL]
+  long long* so = reinterpret_cast<long long*>(sp + 2LL * SL);  // [2][SL]
+  int* idx = reinterpret_cast<int*>(so + 2LL * SL);
   int* prow = idx + ((max_dof + 7) & ~3);
   int ioff = off & 3;  // position of the subdomain's first dof in the aligned spans
   int ispan = (ioff + nI + 3) & ~3;
@@ -384,8 +385,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_local_apply_tc(
         w = j < M ? (int)(tab[4 * (j + 1) + 2] >> 32) : (int)(tab[4 * (j - 1) + 2] >> 32);
       }
       int spc = stage_bytes / (tc_pad8(b) * 64);
-      sp[h * max_L + k] = make_int4(b | (kind << 16), (kc >> 4) | (spc << 16), w, Pj);
-      so[h * max_L + k] = tab[4 * j + kind];
+      sp[h * SL + k] = make_int4(b | (kind << 16), (kc >> 4) | (spc << 16), w, Pj);
+      so[h * SL + k] = tab[4 * j + kind];
     }
   }
   __syncthreads();
@@ -394,10 +395,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_local_apply_tc(
   int issued = 0, ps_k = 0, ps_c = 0;
   auto next_chunk = [&](int h, const unsigned char*& src, unsigned& bytes) -> bool {
     if (ps_k >= nst[h]) return false;
-    int4 pv = sp[h * max_L + ps_k];
+    int4 pv = sp[h * SL + ps_k];
     int sb = tc_pad8(pv.x & 0xFFFF) * 64, ns = pv.y & 0xFFFF, spc = pv.y >> 16;
     int c0 = ps_c * spc, cnt = ns - c0 < spc ? ns - c0 : spc;
-    src = pack + so[h * max_L + ps_k] + (long long)c0 * sb;
+    src = pack + so[h * SL + ps_k] + (long long)c0 * sb;
     bytes = (unsigned)(cnt * sb);
     if (c0 + cnt >= ns) ++ps_k, ps_c = 0;
     else ++ps_c;
@@ -489,7 +490,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_local_apply_tc(
     }
     if (h == 0 && k == n_first + 1) dead = tc_bar_any(dead, 3, 256) != 0;
     if (k == nst[h]) break;
-    int4 pv = sp[h * max_L + k];
+    int4 pv = sp[h * SL + k];
     int b = pv.x & 0xFFFF, kind = pv.x >> 16, w = pv.z, Pj = pv.w;
     int pb = tc_pad8(b), sb = pb * 64, ns = pv.y & 0xFFFF, spc = pv.y >> 16;
     bool m128 = b > 64;
@@ -603,7 +604,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_local_apply_tc(
 // ------------------------------------------------------------------ host
 // Shared memory of the sweeps apart from the rings.
 static size_t tc_fixed_smem(const hk_handle* h) {
-  return TC_GUARD + 64 * (size_t)h->tc_max_apad + 32 * (size_t)(h->max_L + 1) + 48 * (size_t)h->max_L +
+  return TC_GUARD + 64 * (size_t)h->tc_max_apad + 32 * (size_t)(h->max_L + 1) + 96 * (size_t)h->max_L +
          8 * (size_t)((h->max_dof + 7) & ~3);
 }
 
@@ -618,7 +619,7 @@ hk_status tc_plan(hk_handle* h, const std::vector<int>& lev) {
   for (int s = 0; s < ns; ++s) {
     const Sub& u = h->subs[s];
     const int* lp = &lev[u.lev_off];
-    int L = u.L, M = tc_mid(L);
+    int L = u.L, M = u.M;
     std::vector<int> P(L + 1, 0);
     for (int j = 0; j < L; ++j) {
       P[j + 1] = P[j] + tc_pad8(lp[j + 1] - lp[j]);
@@ -661,7 +662,7 @@ hk_status tc_plan(hk_handle* h, const std::vector<int>& lev) {
 hk_status tc_pack(hk_handle* h, cudaStream_t st) {
   if (!h->tc_ok) return HK_OK;
   k_pack_tc<<<h->n_sub, 256, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
-                                      h->d_lvalB, h->d_F64, h->d_lvfo, h->d_lvtab_tc, h->d_pack_tc);
+                                      h->d_lvalB, h->d_F64, h->d_lvfo, h->d_lvtab_tc, h->d_twist, h->d_pack_tc);
   HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   return HK_OK;
@@ -689,7 +690,7 @@ hk_status tc_launch(hk_handle* h, int s, const double* v, const int* active, flo
   HK_TIMED(h, HK_T_LOCAL_APPLY,
            (k_local_apply_tc<<<grid, TC_THREADS, shm, h->stream>>>(
                h->n, s, v, active, h->d_sub_info, h->d_I, h->d_tc_prow, h->d_lvtab_tc, h->d_pack_tc, h->I_total, (int)stage, K,
-               h->max_L, h->max_dof, h->tc_max_apad, ybuf, h->d_status, h->g_jp, h->g_jstride)));
+               h->max_L, h->max_dof, h->tc_max_apad, ybuf, h->d_status, h->g_jp, h->g_jstride, h->d_twist)));
   HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
   return HK_OK;

@@ -54,7 +54,8 @@ class hk_info_t(C.Structure):
                 ("dof_total", C.c_longlong), ("coarse_elems", C.c_longlong), ("lower_nnz", C.c_longlong),
                 ("setup_ms", C.c_double * 8), ("bytes_peak", C.c_size_t), ("graph_solves", C.c_longlong),
                 ("eigen_kernel_ms", C.c_double * 4), ("eigen_kernel_gflop", C.c_double * 4),
-                ("tc_record_bytes", C.c_longlong), ("last_sweeps", C.c_int)]
+                ("tc_record_bytes", C.c_longlong), ("last_sweeps", C.c_int), ("twist_moved", C.c_int),
+                ("local_growth", C.c_double * 2)]
 
 
 class hk_request_info(C.Structure):
@@ -282,7 +283,8 @@ def hk_info(h: Handle) -> dict:
     info = hk_info_t()
     _check(lib().hk_info(h.ptr, C.byref(info)), "hk_info")
     d = {f: getattr(info, f) for f, _ in hk_info_t._fields_
-         if f not in ("setup_ms", "eigen_kernel_ms", "eigen_kernel_gflop")}
+         if f not in ("setup_ms", "eigen_kernel_ms", "eigen_kernel_gflop", "local_growth")}
+    d["local_growth"] = list(info.local_growth)
     d["setup_ms"] = list(info.setup_ms)
     d["eigen_kernel_ms"] = list(info.eigen_kernel_ms)
     d["eigen_kernel_gflop"] = list(info.eigen_kernel_gflop)

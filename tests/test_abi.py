@@ -57,3 +57,24 @@ def test_binding_fails_loudly_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(hk, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(hk.HKLibraryMissing):
         hk.lib()
+
+
+def test_info_struct_layout_matches_the_header(tmp_path):
+    """hk.hk_info_t (ctypes) has the size and field offsets of the C struct in include/hkgeneo.h."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in hk.hk_info_t._fields_]
+    src = tmp_path / "layout.c"
+    body = "\n".join(f'  printf("{f} %zu\\n", offsetof(hk_info_t, {f}));' for f in fields)
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "hkgeneo.h"\nint main(void) {\n'
+                   f'  printf("size %zu\\n", sizeof(hk_info_t));\n{body}\n  return 0;\n}}\n')
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.splitlines())
+    assert int(out["size"]) == ctypes.sizeof(hk.hk_info_t)
+    for f in fields:
+        assert int(out[f]) == getattr(hk.hk_info_t, f).offset, f

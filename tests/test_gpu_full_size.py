@@ -93,23 +93,33 @@ def test_c2_full_parity_split_bf16(c2):
     hk.hk_destroy(h)
 
 
-def test_c3_split_bf16_one_level_apply_sampled():
+def test_c3_one_level_apply_sampled_all_forms():
     """h = 1/512 layered workload, 16 right-hand sides together (the bench's launch shape): the
-    one-level split-BF16 apply on the dofs of sampled subdomains against the oracle, which solves
-    B_j y_j = v[dof(Omega_j)] for every subdomain j sharing a dof with the sample (Eq. 2.22 summed
-    over those j) and compares at TOL_SPLIT."""
+    one-level apply (Eq. 2.22) in all three precision forms on the dofs of sampled subdomains against
+    the oracle, which solves B_j y_j = v[dof(Omega_j)] for every subdomain j sharing a dof with the
+    sample and sums.  The samples include subdomain 152, whose neighbourhood (151..153) has a nearly
+    singular leading level block: factored towards the middle level its pivot growth is about 4e3
+    (FP64 apply error 1e-11, FP32 8e-3); the factorisation meets at another level there (twist_moved),
+    which keeps the growth near that of the other subdomains.  Tolerances: FP64 1e-10, FP32 1e-4 and
+    split-BF16 TOL_SPLIT, as on the small cases."""
     from test_gpu_split_bf16 import TOL_SPLIT
     p = W.config_c3()
     m = p.mesh
-    h = hk.setup_problem(p, precision=hk.HK_SPLIT_BF16_PRECOND, levels=hk.HK_ONE_LEVEL)
-    hk.hk_set_sweep_path(h, hk.HK_SWEEPS_TENSOR_CORE)
     B, _, _, _ = OF.helmholtz_matrices(m.xyz, m.elems, p.coeff, m.is_boundary, p.k)
     v = np.random.default_rng(31).standard_normal((16, B.shape[0]))
-    z = hk.hk_apply_precond(h, v)
-    hk.hk_destroy(h)
+    got = {}
+    for name, prec in (("fp64", hk.HK_FP64), ("fp32", hk.HK_FP32_PRECOND), ("split", hk.HK_SPLIT_BF16_PRECOND)):
+        h = hk.setup_problem(p, precision=prec, levels=hk.HK_ONE_LEVEL)
+        if prec == hk.HK_SPLIT_BF16_PRECOND:
+            hk.hk_set_sweep_path(h, hk.HK_SWEEPS_TENSOR_CORE)
+        info = hk.hk_info(h)
+        assert info["twist_moved"] > 0 and info["local_growth"][0] < info["local_growth"][1] / 10, info["local_growth"]
+        got[name] = hk.hk_apply_precond(h, v)
+        hk.hk_destroy(h)
+    tol = {"fp64": 1e-10, "fp32": 1e-4, "split": TOL_SPLIT}
     subs, mu = OD.decompose(m.xyz, m.elems, m.is_boundary, p.elem_to_sub, p.n_sub, p.overlap)
     Bc = B.tocsr()
-    for i in (0, 17, 136, 255):
+    for i in (0, 17, 136, 152, 255):
         di = subs[i].dof
         want = np.zeros((16, di.size))
         pos = {int(d): t for t, d in enumerate(di)}
@@ -118,12 +128,12 @@ def test_c3_split_bf16_one_level_apply_sampled():
             if common.size == 0:
                 continue
             y = np.linalg.solve(Bc[sd.dof][:, sd.dof].toarray(), v[:, sd.dof].T).T
-            where = np.searchsorted(sd.dof, common) if np.all(np.diff(sd.dof) > 0) else \
-                np.array([int(np.flatnonzero(sd.dof == c)[0]) for c in common])
-            for c, wpos in zip(common, where):
-                want[:, pos[int(c)]] += y[:, wpos]
-        err = np.linalg.norm(z[:, di] - want, axis=1) / np.linalg.norm(want, axis=1)
-        assert np.all(err <= TOL_SPLIT), (i, err)
+            where = {int(d): t for t, d in enumerate(sd.dof)}
+            for c in common:
+                want[:, pos[int(c)]] += y[:, where[int(c)]]
+        for name, z in got.items():
+            err = np.linalg.norm(z[:, di] - want, axis=1) / np.linalg.norm(want, axis=1)
+            assert np.all(err <= tol[name]), (i, name, float(err.max()))
 
 
 @pytest.fixture(scope="module")
