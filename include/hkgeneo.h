@@ -122,6 +122,44 @@ hk_status hk_solve(hk_handle* h, int n_rhs, const double* rhs, double tol, doubl
 hk_status hk_solve_device(hk_handle* h, int n_rhs, const double* rhs_dev, double tol, double* u_dev,
                           int32_t* iters, double* res_hist, double* final_true_rel_res);
 
+/* Left-preconditioned GMRES(m) in the D_k inner product: the Krylov method of Thm. 3.1, on the
+ * preconditioned system M^{-1} B u = M^{-1} f of Eq. 2.24 (M^{-1} the setup's preconditioner, in its
+ * precision form), with <x, y>_D = y^T D_k x, D_k = A + k^2 S (Prop. 2.6), in the Arnoldi process and
+ * the residual minimisation.  x_0 = 0; restart and max_iters from the parameters.  A right-hand side
+ * has converged when ||M^{-1}(rhs - B u)||_{D_k} <= tol ||M^{-1} rhs||_{D_k} (the residual of Eq. 4.22).
+ *   rhs, u: n_rhs * n_dofs (host).  iters: n_rhs (written).  res_hist: NULL or n_rhs * max_iters,
+ *   the recurrence estimates ||M^{-1} r_j||_{D_k} / ||M^{-1} rhs||_{D_k} of each inner step (unused tail
+ *   untouched).  final_true_rel_res: NULL or n_rhs, ||rhs - B u|| / ||rhs||.  final_pc_rel_res: NULL or
+ *   n_rhs, the D_k-norm ratio at the end.
+ * Returns HK_NO_CONVERGENCE (outputs still written) if any rhs did not converge.  The loop is driven
+ * from the host (one small device-to-host copy per inner step); results do not depend on n_rhs. */
+hk_status hk_solve_left_dk(hk_handle* h, int n_rhs, const double* rhs, double tol, double* u, int32_t* iters,
+                           double* res_hist, double* final_true_rel_res, double* final_pc_rel_res);
+/* Same with rhs_dev and u_dev in device memory (n_rhs * n_dofs doubles each). */
+hk_status hk_solve_left_dk_device(hk_handle* h, int n_rhs, const double* rhs_dev, double tol, double* u_dev,
+                                  int32_t* iters, double* res_hist, double* final_true_rel_res,
+                                  double* final_pc_rel_res);
+
+/* The quantities of Thm. 3.1 for this handle (two-level preconditioner). */
+typedef struct {
+  double Lambda;          /* most subdomains sharing one element (the fine subdomains are the subdomains) */
+  double tau;             /* min_i lambda_{m_i+1}: the smallest local eigenvalue left out of the coarse space
+                             (the FP64-refined value next above the kept ones; not certified by an inertia
+                             count) */
+  int tau_is_lower_bound; /* 1: no subdomain had a refined value above its kept ones below tau + 0.05, and
+                             tau holds that bound */
+  double Theta;           /* 1 / tau */
+  double k;               /* wavenumber */
+  double H_f;             /* largest subdomain diameter used (given, or the largest bounding-box diagonal of
+                             a subdomain's dof nodes when the caller passes H_f <= 0) */
+  double c_stab;          /* the stability constant C_stab of the problem (caller's value) */
+  double s;               /* Eq. 4.3 */
+  double gamma;           /* Eq. 4.5: ||r^(m)||_D^2 <= (1 - gamma^2)^m ||r^(0)||_D^2 when s < 1 */
+  int guaranteed;         /* s < 1 */
+} hk_theory_t;
+/* Errors: HK_BAD_ARG; HK_UNSUPPORTED for a one-level or coarse-only handle. */
+hk_status hk_theory(const hk_handle* h, double c_stab, double H_f, hk_theory_t* out);
+
 typedef struct {
   int dim, n_nodes, n_elems, n_dofs, n_sub;
   int n0;                      /* coarse dimension sum_i m_i */

@@ -12,7 +12,9 @@ Modules, each citing the passages it follows:
   decomposition  overlap extension (Def. 2.3), dof/ovdof (Def. 3.2), partition of unity (Def. 2.7)
   geneo          H_k-GenEO local eigenproblems (Def. of Eq. 5.12) and coarse space (Def. 5.1)
   schwarz        one- and two-level additive Schwarz (Eq. 2.22, 2.23)
-  fgmres         right-preconditioned flexible GMRES (the Krylov solver of Sec. 3, Thm. 3.1 setting)
+  fgmres         right-preconditioned flexible GMRES (Euclidean inner product; the library's default solver)
+  gmres_dk       left-preconditioned GMRES in the D_k inner product (the setting of Thm. 3.1, Eq. 2.24,
+                 Prop. 2.6) and the theorem's quantities Lambda, tau, Theta, s, gamma
   solver         setup/solve pipeline mirroring the library's boundary
 
 Parity status: every function is pinned by tests against closed forms,

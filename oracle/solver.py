@@ -15,6 +15,7 @@ import numpy as np
 
 from . import decomposition, fem, geneo, schwarz
 from .fgmres import fgmres
+from .gmres_dk import gmres_left_dk
 
 
 @dataclass
@@ -85,3 +86,9 @@ def solve(h: OracleHandle, rhs: np.ndarray, tol=1e-8):
     for f in rhs:
         out.append(fgmres(lambda v: h.B @ v, h.precond.apply, f, tol, h.restart, h.max_iters))
     return out
+
+
+def solve_left_dk(h: OracleHandle, rhs: np.ndarray, tol=1e-8):
+    """Left-preconditioned GMRES in the D_k inner product (the setting of Thm. 3.1) for each right-hand side."""
+    rhs = np.atleast_2d(rhs)
+    return [gmres_left_dk(lambda v: h.B @ v, h.precond.apply, h.Dk, f, tol, h.restart, h.max_iters) for f in rhs]

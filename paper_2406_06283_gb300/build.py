@@ -20,7 +20,7 @@ OBJ_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libhkgeneo.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["hk_api.cu", "hk_assembly.cu", "hk_decomp.cu", "hk_local.cu", "hk_eigen.cu", "hk_lanczos.cu",
-           "hk_coarse.cu", "hk_krylov.cu", "hk_server.cu", "hk_tc.cu"]
+           "hk_coarse.cu", "hk_krylov.cu", "hk_server.cu", "hk_tc.cu", "hk_dkgmres.cu"]
 
 
 def nvcc() -> str:

@@ -7,6 +7,9 @@
 #include <mutex>
 #include <set>
 
+#include <algorithm>
+#include <cmath>
+#include <vector>
 #include "hk_internal.cuh"
 
 static thread_local char g_err[512] = "";
@@ -330,6 +333,87 @@ extern "C" hk_status hk_solve_device(hk_handle* h, int n_rhs, const double* rhs_
     return HK_BAD_ARG;
   }
   return run_fgmres(h, n_rhs, rhs_dev, tol, u_dev, iters, res_hist, final_true_rel_res);
+}
+
+extern "C" hk_status hk_solve_left_dk_device(hk_handle* h, int n_rhs, const double* rhs_dev, double tol,
+                                             double* u_dev, int32_t* iters, double* res_hist, double* final_true,
+                                             double* final_pc) {
+  if (!h || n_rhs < 1 || !rhs_dev || !u_dev || !iters || !(tol > 0)) {
+    hk_set_error("invalid solve arguments");
+    return HK_BAD_ARG;
+  }
+  return run_left_dk_gmres(h, n_rhs, rhs_dev, tol, u_dev, iters, res_hist, final_true, final_pc);
+}
+
+extern "C" hk_status hk_solve_left_dk(hk_handle* h, int n_rhs, const double* rhs, double tol, double* u,
+                                      int32_t* iters, double* res_hist, double* final_true, double* final_pc) {
+  if (!h || n_rhs < 1 || !rhs || !u || !iters || !(tol > 0)) {
+    hk_set_error("invalid solve arguments");
+    return HK_BAD_ARG;
+  }
+  size_t bytes = sizeof(double) * (size_t)n_rhs * h->n;
+  double *d_in = nullptr, *d_out = nullptr;
+  if (dalloc(h, &d_in, bytes / sizeof(double)) != HK_OK || dalloc(h, &d_out, bytes / sizeof(double)) != HK_OK) {
+    if (d_in) dfree(h, d_in);
+    return HK_OOM;
+  }
+  hk_status s = HK_OK;
+  if (cudaMemcpyAsync(d_in, rhs, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) s = HK_CUDA_ERROR;
+  if (s == HK_OK) s = run_left_dk_gmres(h, n_rhs, d_in, tol, d_out, iters, res_hist, final_true, final_pc);
+  if (s == HK_OK || s == HK_NO_CONVERGENCE) {
+    cudaError_t e = cudaMemcpyAsync(u, d_out, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      hk_set_error("copy-out: %s", cudaGetErrorString(e));
+      s = HK_CUDA_ERROR;
+    }
+  }
+  dfree(h, d_in);
+  dfree(h, d_out);
+  return s;
+}
+
+extern "C" hk_status hk_theory(const hk_handle* h, double c_stab, double H_f, hk_theory_t* out) {
+  if (!h || !out || !(c_stab >= 0)) {
+    hk_set_error("hk_theory: invalid arguments");
+    return HK_BAD_ARG;
+  }
+  if (h->p.levels != HK_TWO_LEVEL) {
+    hk_set_error("hk_theory: the theorem is stated for the two-level preconditioner");
+    return HK_UNSUPPORTED;
+  }
+  if (!(H_f > 0)) {
+    // largest bounding-box diagonal of a subdomain's dof nodes
+    std::vector<double> xyz((size_t)h->n_nodes * h->dim);
+    std::vector<int> node(h->n), I(h->I_total);
+    HK_CUDA(cudaMemcpy(xyz.data(), h->d_xyz, sizeof(double) * xyz.size(), cudaMemcpyDeviceToHost));
+    HK_CUDA(cudaMemcpy(node.data(), h->d_node_of_dof, sizeof(int) * node.size(), cudaMemcpyDeviceToHost));
+    HK_CUDA(cudaMemcpy(I.data(), h->d_I, sizeof(int) * I.size(), cudaMemcpyDeviceToHost));
+    H_f = 0;
+    for (const Sub& u : h->subs) {
+      double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+      for (int a = 0; a < u.nI; ++a) {
+        const double* p = &xyz[(size_t)node[I[(size_t)u.I_off + a]] * h->dim];
+        for (int d = 0; d < h->dim; ++d) lo[d] = std::min(lo[d], p[d]), hi[d] = std::max(hi[d], p[d]);
+      }
+      double d2 = 0;
+      for (int d = 0; d < h->dim; ++d) d2 += (hi[d] - lo[d]) * (hi[d] - lo[d]);
+      if (u.nI > 0) H_f = std::max(H_f, std::sqrt(d2));
+    }
+  }
+  double Lam = h->lambda_elems, tau = h->tau_next, k = h->k;
+  double Theta = 1.0 / tau, a = 2.0 + 3.0 * std::pow(Lam, 4) * Theta;
+  out->Lambda = Lam;
+  out->tau = tau;
+  out->tau_is_lower_bound = h->tau_next_lb ? 1 : 0;
+  out->Theta = Theta;
+  out->k = k;
+  out->H_f = H_f;
+  out->c_stab = c_stab;
+  out->s = 2.0 * Lam * Lam * a * (2.0 * k * std::sqrt(Theta) * (1.0 + c_stab) + 3.0 * k * H_f);
+  out->gamma = (1.0 - out->s) / (a * (18.0 + 8.0 * Lam * Lam * Lam));
+  out->guaranteed = out->s < 1.0 ? 1 : 0;
+  return HK_OK;
 }
 
 extern "C" hk_status hk_solve(hk_handle* h, int n_rhs, const double* rhs, double tol, double* u, int32_t* iters,

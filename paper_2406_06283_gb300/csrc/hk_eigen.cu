@@ -463,9 +463,11 @@ __global__ void k_refine(const int* __restrict__ items, const double* __restrict
 // B^N - tau C (every eigenvalue below tau found once); a difference is accepted only where the value at
 // the boundary lies within 1e-9 max(1, |tau|) of tau (the count then depends on rounding).  Otherwise
 // fail[s] = 1 (the setup redoes the subdomain once with a larger Krylov basis, then reports HK_EIG_FAIL).
+// lam_next[s]: the smallest refined value not kept (lambda_{m_i+1} when the candidates below tau + delta
+// are complete), or +inf when every candidate was kept.
 __global__ void k_select(const int* __restrict__ cnt, const double* __restrict__ lam_ref, double tau,
                          const int* __restrict__ neg, int* sel, int* m_out, double* lam_out, int* fail,
-                         DevStatus* st) {
+                         double* lam_next, DevStatus* st) {
   int s = blockIdx.x;
   if (threadIdx.x != 0) return;
   int c = min(cnt[s], HK_MAXM);
@@ -492,6 +494,7 @@ __global__ void k_select(const int* __restrict__ cnt, const double* __restrict__
   while (m > 0 && m < c && lr[ord[m]] - lr[ord[m - 1]] <= thr) ++m;
   if (m == c && c == cnt[s] && m > 0 && lr[ord[m - 1]] >= tau) dev_fail(st, HK_EIG_FAIL, s, m);
   m_out[s] = m;
+  lam_next[s] = m < c ? lr[ord[m]] : INFINITY;
   for (int i = 0; i < m; ++i) lam_out[(long long)s * HK_MAXM + i] = lr[ord[i]];
 }
 
@@ -630,6 +633,8 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   HK_TRY(dalloc(h, &d_sel, (size_t)ns * HK_MAXM));
   HK_TRY(dalloc(h, &d_m, ns));
   HK_TRY(dalloc(h, &d_fail, ns));
+  double* d_lamnext = nullptr;
+  HK_TRY(dalloc(h, &d_lamnext, ns));
   double* d_P = nullptr;
   long long* d_poff = nullptr;
   HK_TRY(dalloc(h, &d_poff, ns));
@@ -767,7 +772,8 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
     }
     // selection and certification against the FP64 count (joined here)
     HK_CUDA(cudaStreamWaitEvent(st, inertia_done, 0));
-    k_select<<<ns, 32, 0, st>>>(d_cnt, d_lamref, h->p.tau, d_neg, d_sel, d_m, h->d_lam, d_fail, h->d_status);
+    k_select<<<ns, 32, 0, st>>>(d_cnt, d_lamref, h->p.tau, d_neg, d_sel, d_m, h->d_lam, d_fail, d_lamnext,
+                                h->d_status);
     HK_COUNT_LAUNCH();
     HK_LAUNCH_CHECK();
     std::vector<int> fail(ns);
@@ -779,7 +785,22 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
         ++nfail;
         if (first < 0) first = s;
       }
-    if (nfail == 0) break;
+    if (nfail == 0) {
+      // tau of Thm. 3.1: min over subdomains of lambda_{m_i+1}; subdomains without a candidate above the
+      // kept ones only bound it below by tau + delta
+      std::vector<double> nx(ns);
+      HK_CUDA(cudaMemcpy(nx.data(), d_lamnext, sizeof(double) * ns, cudaMemcpyDeviceToHost));
+      double lo = INFINITY;
+      bool unknown = false;
+      for (int s = 0; s < ns; ++s) {
+        if (std::isfinite(nx[s])) lo = std::min(lo, nx[s]);
+        else unknown = true;
+      }
+      h->tau_next = lo;
+      h->tau_next_lb = unknown && !(lo < h->p.tau + HK_EIG_DELTA);
+      if (h->tau_next_lb) h->tau_next = h->p.tau + HK_EIG_DELTA;
+      break;
+    }
     if (attempt == 1) {
       std::vector<int> negv(ns);
       HK_CUDA(cudaMemcpy(negv.data(), d_neg, 4 * ns, cudaMemcpyDeviceToHost));
@@ -838,7 +859,7 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
   }
   HK_CUDA(cudaStreamSynchronize(st));
   void* tmp[] = {d_ws, d_Gw, d_cnt, d_o_off, d_neg, d_lamhat, d_lamref, d_O, d_okind, d_Operm, d_Olev, d_Olevptr,
-                 d_OL, d_ocnt, d_o2i, d_ocol, d_oB, d_oC, d_P, d_poff, d_sel, d_m, d_fail};
+                 d_OL, d_ocnt, d_o2i, d_ocol, d_oB, d_oC, d_P, d_poff, d_sel, d_m, d_fail, d_lamnext};
   for (void* p : tmp) dfree(h, p);
   return HK_OK;
 }

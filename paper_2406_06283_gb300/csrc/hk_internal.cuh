@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <cmath>
 #include <string>
 #include <map>
 #include <vector>
@@ -219,6 +220,8 @@ struct hk_handle {
   int* d_twist = nullptr;       // per subdomain: twist level M of its factorisation
   double growth_twist = 0, growth_mid = 0;  // max over subdomains of the pivot growth (chosen M; M = (L-1)/2)
   int twist_moved = 0;          // subdomains whose twist level is not the middle one
+  double tau_next = INFINITY;   // min over subdomains of the first local eigenvalue not kept (Thm. 3.1 tau)
+  bool tau_next_lb = false;     // tau_next is only the lower bound tau + delta (no candidate above the kept)
   int* d_ctl = nullptr;         // [0] inner step j, [1] cycles run, [2] inner steps run
   const int* g_jp = nullptr;    // while an inner step is captured: the device word holding j
   long long g_jstride = 0;      // ... and the distance between consecutive Krylov vectors
@@ -350,6 +353,11 @@ hk_status tc_prepare();
 hk_status op_apply(hk_handle* h, int s, const double* v, double* z, const int* active);
 // y = B x for s vectors.
 hk_status op_matvec(hk_handle* h, int s, const double* x, double* y, const int* active);
+// y = A x for s vectors, A with the sparsity of B and the values val (h->d_valB or h->d_valD).
+hk_status op_spmv_values(hk_handle* h, int s, const double* val, const double* x, double* y, const int* active);
+// Left-preconditioned GMRES in the D_k inner product (hk_dkgmres.cu); device vectors.
+hk_status run_left_dk_gmres(hk_handle* h, int s, const double* rhs_dev, double tol, double* u_dev, int32_t* iters,
+                            double* res_hist, double* final_true, double* final_pc);
 hk_status op_load(hk_handle* h, const double* f_nodal_dev, double* rhs_dev);
 hk_status run_fgmres(hk_handle* h, int s, const double* rhs_dev, double tol, double* u_dev,
                      int32_t* iters, double* res_hist, double* final_res);

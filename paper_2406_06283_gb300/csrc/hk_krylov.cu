@@ -152,6 +152,13 @@ __global__ void k_spmv(int n, int s, const int* __restrict__ rowptr, const int* 
   }
 }
 
+// y = A x for s vectors with the sparsity of B and the values `val` (B or D_k); active as for op_apply.
+hk_status op_spmv_values(hk_handle* h, int s, const double* val, const double* x, double* y, const int* active) {
+  k_spmv<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->n, s, h->d_rowptr, h->d_col, val, x, y, active); HK_COUNT_LAUNCH();
+  HK_LAUNCH_CHECK();
+  return HK_OK;
+}
+
 hk_status op_matvec(hk_handle* h, int s, const double* x, double* y, const int* active) {
   k_spmv<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->n, s, h->d_rowptr, h->d_col, h->d_valB, x, y, active); HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();

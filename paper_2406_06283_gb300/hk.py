@@ -58,6 +58,12 @@ class hk_info_t(C.Structure):
                 ("local_growth", C.c_double * 2)]
 
 
+class hk_theory_t(C.Structure):
+    _fields_ = [("Lambda", C.c_double), ("tau", C.c_double), ("tau_is_lower_bound", C.c_int), ("Theta", C.c_double),
+                ("k", C.c_double), ("H_f", C.c_double), ("c_stab", C.c_double), ("s", C.c_double),
+                ("gamma", C.c_double), ("guaranteed", C.c_int)]
+
+
 class hk_request_info(C.Structure):
     _fields_ = [("submit_ms", C.c_double), ("start_ms", C.c_double), ("end_ms", C.c_double),
                 ("batch_rhs", C.c_int32), ("setup_ran", C.c_int32), ("slot", C.c_int32), ("n_rhs", C.c_int32)]
@@ -116,13 +122,16 @@ def lib():
     L.hk_set_wait_limit.argtypes = [_P, C.c_int]
     L.hk_apply_precond_noalloc.argtypes = [_P, C.c_int, _P, _P]
     L.hk_set_sweep_path.argtypes = [_P, C.c_int]
+    L.hk_solve_left_dk.argtypes = [_P, C.c_int, _P, C.c_double, _P, _P, _P, _P, _P]
+    L.hk_solve_left_dk_device.argtypes = [_P, C.c_int, _P, C.c_double, _P, _P, _P, _P, _P]
+    L.hk_theory.argtypes = [_P, C.c_double, C.c_double, C.POINTER(hk_theory_t)]
     for f in ("hk_server_create", "hk_server_add_operator", "hk_server_submit", "hk_server_poll",
               "hk_server_get_stats", "hk_server_destroy"):
         getattr(L, f).restype = C.c_int
     for f in ("hk_setup", "hk_setup_device", "hk_set_timing", "hk_kernel_times", "hk_solve", "hk_solve_device", "hk_info", "hk_destroy", "hk_get_matrix",
               "hk_get_subdomain", "hk_get_mu", "hk_get_eigen", "hk_get_coarse", "hk_apply_precond", "hk_matvec",
               "hk_assemble_load", "hk_check_status", "hk_set_wait_limit", "hk_apply_precond_noalloc",
-              "hk_set_sweep_path"):
+              "hk_set_sweep_path", "hk_solve_left_dk", "hk_solve_left_dk_device", "hk_theory"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -265,6 +274,40 @@ def hk_solve(h: Handle, rhs, tol=1e-8) -> SolveResult:
     st = _check(lib().hk_solve(h.ptr, s, _ptr(rhs), float(tol), _ptr(u), _ptr(it), _ptr(hist), _ptr(res)),
                 "hk_solve", ok=(HK_OK, HK_NO_CONVERGENCE))
     return SolveResult(u, it, hist, res, st)
+
+
+def hk_solve_left_dk(h: Handle, rhs, tol=1e-8):
+    """Left-preconditioned GMRES in the D_k inner product (Thm. 3.1).  Returns (SolveResult, pc_rel_res):
+    the history holds ||M^{-1} r_j||_D / ||M^{-1} f||_D, true_rel_res ||f - B u|| / ||f||."""
+    rhs = np.ascontiguousarray(np.atleast_2d(rhs), dtype=np.float64)
+    s = rhs.shape[0]
+    u = np.zeros_like(rhs)
+    it = np.zeros(s, dtype=np.int32)
+    hist = np.zeros((s, h.max_iters))
+    res = np.zeros(s)
+    pc = np.zeros(s)
+    st = _check(lib().hk_solve_left_dk(h.ptr, s, _ptr(rhs), float(tol), _ptr(u), _ptr(it), _ptr(hist), _ptr(res),
+                                       _ptr(pc)), "hk_solve_left_dk", ok=(HK_OK, HK_NO_CONVERGENCE))
+    return SolveResult(u, it, hist, res, st), pc
+
+
+def hk_solve_left_dk_device(h: Handle, rhs_dev, u_dev, tol=1e-8):
+    """rhs_dev, u_dev: contiguous float64 CUDA tensors of shape (n_rhs, n).  Returns (iters, true, pc)."""
+    s = int(rhs_dev.shape[0])
+    it = np.zeros(s, dtype=np.int32)
+    res = np.zeros(s)
+    pc = np.zeros(s)
+    _check(lib().hk_solve_left_dk_device(h.ptr, s, _P(rhs_dev.data_ptr()), float(tol), _P(u_dev.data_ptr()),
+                                         _ptr(it), None, _ptr(res), _ptr(pc)),
+           "hk_solve_left_dk_device", ok=(HK_OK, HK_NO_CONVERGENCE))
+    return it, res, pc
+
+
+def hk_theory(h: Handle, c_stab: float, H_f: float = 0.0) -> dict:
+    """Lambda, tau, Theta, s, gamma of Thm. 3.1 (H_f <= 0: the largest subdomain bounding-box diagonal)."""
+    t = hk_theory_t()
+    _check(lib().hk_theory(h.ptr, float(c_stab), float(H_f), C.byref(t)), "hk_theory")
+    return {f: getattr(t, f) for f, _ in hk_theory_t._fields_}
 
 
 def hk_solve_device(h: Handle, rhs_dev, u_dev, tol=1e-8, history=False) -> SolveResult:
