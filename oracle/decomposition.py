@@ -41,8 +41,9 @@ class Subdomain:
     ovdof: np.ndarray     # global dof ids of ovdof(Omega_i), increasing (O_i)
 
 
-def extend_by_layers(elems, is_boundary, elem_set: np.ndarray, layers: int, inc=None) -> np.ndarray:
-    """Def. 2.3 applied `layers` times to a boolean element mask."""
+def extend_by_layers(elems, is_boundary, elem_set: np.ndarray, layers: int, inc=None, within=None) -> np.ndarray:
+    """Def. 2.3 applied `layers` times to a boolean element mask; with `within` (a boolean element mask),
+    in the mesh of that region: each layer keeps only the elements of `within`."""
     n_nodes = is_boundary.size
     if inc is None:
         inc = node_element_incidence(elems, n_nodes)
@@ -53,7 +54,17 @@ def extend_by_layers(elems, is_boundary, elem_set: np.ndarray, layers: int, inc=
         grow_nodes = touched & interior                       # basis functions of V^h meeting cur
         star_hit = (inc.T @ grow_nodes.astype(np.int8)) > 0   # elements in those supports
         cur = cur | star_hit
+        if within is not None:
+            cur &= within
     return cur
+
+
+def subdomain_of(mask, inc, dofs, interior, star_size) -> "Subdomain":
+    """dof and ovdof (Def. 3.2) of the overlapping subdomain with element mask `mask`."""
+    in_star = np.asarray(inc @ mask.astype(np.int64)).ravel()     # elements of the star inside D
+    ov_nodes = np.flatnonzero(interior & (in_star > 0))
+    dof_nodes = np.flatnonzero(interior & (in_star == star_size))
+    return Subdomain(np.flatnonzero(mask), np.sort(dofs[dof_nodes]), np.sort(dofs[ov_nodes]))
 
 
 def decompose(xyz, elems, is_boundary, elem_to_sub, n_sub: int, overlap: int):
@@ -67,13 +78,42 @@ def decompose(xyz, elems, is_boundary, elem_to_sub, n_sub: int, overlap: int):
     mu = np.zeros(int(interior.sum()), dtype=np.int64)
     for i in range(n_sub):
         mask = extend_by_layers(elems, is_boundary, elem_to_sub == i, overlap, inc)
-        in_star = np.asarray(inc @ mask.astype(np.int64)).ravel()     # elements of the star inside D
-        ov_nodes = np.flatnonzero(interior & (in_star > 0))
-        dof_nodes = np.flatnonzero(interior & (in_star == star_size))
-        sd = Subdomain(np.flatnonzero(mask), np.sort(dofs[dof_nodes]), np.sort(dofs[ov_nodes]))
+        sd = subdomain_of(mask, inc, dofs, interior, star_size)
         mu[sd.dof] += 1
         subs.append(sd)
     return subs, mu
+
+
+def decompose_nested(xyz, elems, is_boundary, elem_to_sub, n_sub: int, overlap: int, elem_to_fine,
+                     fine_overlap: int):
+    """The two nested decompositions of Sec. 2.3.  Coarse: the subdomains Omega_i^c of `decompose`.
+    Fine: inside each Omega_i^c, its elements grouped by their label in `elem_to_fine` (a partition of
+    Omega_i^c into Q_i pieces), each piece extended `fine_overlap` times by Def. 2.3 in the mesh of
+    Omega_i^c, so that Omega_i^c is the union of its fine subdomains Omega^f_{i,j}.  A fine subdomain
+    without a dof (a sliver of Omega_i^c) spans the zero space and is left out.
+    Returns (coarse subdomains, mu^c, fine subdomains, parent coarse index of each, mu^f)."""
+    coarse, mu_c = decompose(xyz, elems, is_boundary, elem_to_sub, n_sub, overlap)
+    n_nodes = is_boundary.size
+    inc = node_element_incidence(elems, n_nodes)
+    dofs = dof_map(is_boundary)
+    interior = is_boundary == 0
+    star_size = np.asarray(inc.sum(axis=1)).ravel()
+    ne = elems.shape[0]
+    fine, parent = [], []
+    mu_f = np.zeros(int(interior.sum()), dtype=np.int64)
+    for i, sd in enumerate(coarse):
+        cmask = np.zeros(ne, dtype=bool)
+        cmask[sd.elems] = True
+        for g in np.unique(elem_to_fine[sd.elems]):
+            piece = cmask & (elem_to_fine == g)
+            mask = extend_by_layers(elems, is_boundary, piece, fine_overlap, inc, within=cmask)
+            fd = subdomain_of(mask, inc, dofs, interior, star_size)
+            if fd.dof.size == 0:
+                continue
+            mu_f[fd.dof] += 1
+            fine.append(fd)
+            parent.append(i)
+    return coarse, mu_c, fine, np.array(parent, dtype=np.int64), mu_f
 
 
 def multiplicity_lambda(elems, subs, n_elems) -> int:

@@ -48,27 +48,37 @@ class OracleHandle:
 
 
 def setup(xyz, elems, is_boundary, coeff, k, elem_to_sub, n_sub, overlap=2, tau=0.5,
-          levels="two", weighting="as", restart=50, max_iters=1000) -> OracleHandle:
+          levels="two", weighting="as", restart=50, max_iters=1000, nested=None) -> OracleHandle:
+    """nested = (elem_to_fine, fine_overlap): the two decompositions of Sec. 2.3; the eigenproblems and the
+    coarse space on the coarse subdomains, the local solves (Eq. 2.22) on the fine ones, Lambda over the
+    fine ones.  The handle's subs and mu are then the fine ones; coarse_subs and mu_c the coarse ones."""
     B, Dk, _, _ = fem.helmholtz_matrices(xyz, elems, coeff, is_boundary, k)
-    subs, mu = decomposition.decompose(xyz, elems, is_boundary, elem_to_sub, n_sub, overlap)
-    if mu.min() < 1:
+    if nested is None:
+        subs, mu = decomposition.decompose(xyz, elems, is_boundary, elem_to_sub, n_sub, overlap)
+        csubs, mu_c = subs, mu
+    else:
+        csubs, mu_c, subs, _, mu = decomposition.decompose_nested(xyz, elems, is_boundary, elem_to_sub, n_sub,
+                                                                  overlap, nested[0], nested[1])
+    if mu_c.min() < 1 or mu.min() < 1:
         raise ValueError("some dof lies in no dof(Omega_i): the partition of unity is undefined")
     Lam = decomposition.multiplicity_lambda(elems, subs, elems.shape[0])
     eigs, Z = [], None
     if levels in ("two", "coarse"):
-        for sd in subs:
-            BN, C, w = geneo.local_pencil(xyz, elems, coeff, is_boundary, k, sd, mu)
+        for sd in csubs:
+            BN, C, w = geneo.local_pencil(xyz, elems, coeff, is_boundary, k, sd, mu_c)
             eigs.append(geneo.local_eigen(BN, C, w, tau))
-        Z = geneo.coarse_basis(subs, eigs, B.shape[0])
+        Z = geneo.coarse_basis(csubs, eigs, B.shape[0])
     pc = schwarz.AdditiveSchwarz(B, subs, mu, Z, levels, weighting)
-    return OracleHandle(B, Dk, subs, mu, eigs, Z, pc, restart, max_iters, Lam)
+    h = OracleHandle(B, Dk, subs, mu, eigs, Z, pc, restart, max_iters, Lam)
+    h.coarse_subs, h.mu_c = csubs, mu_c
+    return h
 
 
-def setup_problem(p, levels="two", weighting="as") -> OracleHandle:
-    """Convenience wrapper for a workloads.Problem-like object."""
+def setup_problem(p, levels="two", weighting="as", nested=None) -> OracleHandle:
+    """Convenience wrapper for a workloads.Problem-like object (nested: (elem_to_fine, fine_overlap))."""
     m = p.mesh
     return setup(m.xyz, m.elems, m.is_boundary, p.coeff, p.k, p.elem_to_sub, p.n_sub,
-                 p.overlap, p.tau, levels, weighting, p.restart, p.max_iters)
+                 p.overlap, p.tau, levels, weighting, p.restart, p.max_iters, nested)
 
 
 def load_vector(p) -> np.ndarray:
