@@ -104,6 +104,26 @@ hk_status hk_setup(const hk_mesh* mesh, const double* elem_coeff, double k,
 hk_status hk_setup_device(const hk_mesh* mesh_dev, const double* elem_coeff_dev, double k,
                           const hk_params* params, void* cuda_stream, hk_handle** out);
 
+/* Setup with the two nested decompositions of Sec. 2.3.  Coarse: the subdomains of params
+ * (elem_to_sub extended overlap_layers times, Def. 2.3), on which the H_k-GenEO eigenproblems, the
+ * partition of unity Xi^c and the coarse space are built (Def. 5.1).  Fine: inside every coarse
+ * subdomain Omega_i^c, its elements grouped by elem_to_fine (labels 0 .. n_fine_labels-1, e.g. a finer
+ * box partition), each group extended fine_overlap_layers times by Def. 2.3 within Omega_i^c, so that
+ * Omega_i^c is the union of its Q_i fine subdomains (groups whose subdomain holds no dof are left out).
+ * The one-level part of the preconditioner sums the local solves over all fine subdomains (Eq. 2.22);
+ * the coarse correction is that of Eq. 2.23.  Every dof must lie in some fine dof set (so
+ * fine_overlap_layers >= 1 in practice), else HK_BAD_ARG.  params->levels must be HK_TWO_LEVEL.
+ * The handle serves hk_solve, hk_solve_left_dk, hk_apply_precond and hk_theory (Lambda and H^f of the
+ * fine subdomains); hk_apply_precond_noalloc and the serving calls do not take it (HK_UNSUPPORTED).
+ * Other errors as hk_setup. */
+hk_status hk_setup_nested(const hk_mesh* mesh, const double* elem_coeff, double k, const hk_params* params,
+                          int n_fine_labels, const int32_t* elem_to_fine, int fine_overlap_layers,
+                          void* cuda_stream, hk_handle** out);
+/* Same as hk_setup_nested with every array in device memory (as hk_setup_device). */
+hk_status hk_setup_nested_device(const hk_mesh* mesh_dev, const double* elem_coeff_dev, double k,
+                                 const hk_params* params, int n_fine_labels, const int32_t* elem_to_fine_dev,
+                                 int fine_overlap_layers, void* cuda_stream, hk_handle** out);
+
 /* Solve B u = rhs for n_rhs right-hand sides (load vectors) with FGMRES
  * preconditioned on the right by the setup's preconditioner, x_0 = 0, until
  * the relative residual ||rhs - B u|| / ||rhs|| <= tol (checked on the true
@@ -195,6 +215,12 @@ typedef struct {
   double local_growth[2];      /* largest pivot growth max|pivot block inverse| x max|B_i| over the local
                                   factorisations: [0] as factored (twist level chosen per subdomain),
                                   [1] had every subdomain been factored towards its middle level */
+  int fine_subdomains;         /* nested decompositions (hk_setup_nested): number of fine subdomains
+                                  (sum_i Q_i), else 0; the local solves, max_level, twist_moved,
+                                  local_growth, tc_record_bytes and last_sweeps then refer to them */
+  int fine_lambda_elems;       /* Lambda over the fine subdomains (Sec. 2.4), else 0 */
+  int fine_max_dof;            /* largest |dof(Omega^f_{i,j})|, else 0 */
+  long long fine_dof_total;    /* sum of |dof(Omega^f_{i,j})|, else 0 */
 } hk_info_t;
 
 hk_status hk_info(const hk_handle* h, hk_info_t* info);

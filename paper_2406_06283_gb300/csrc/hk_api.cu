@@ -126,6 +126,10 @@ extern "C" hk_status hk_set_wait_limit(hk_handle* h, int grid_barrier_polls) {
 
 static void destroy_all(hk_handle* h) {
   if (!h) return;
+  if (h->child) {
+    destroy_all(h->child);
+    h->child = nullptr;
+  }
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(h->dev);
@@ -188,14 +192,51 @@ struct PhaseTimer {
   }
 };
 
-static hk_status setup_impl(hk_handle* h, const hk_mesh* mesh, const double* coeff, const hk_params* prm) {
+// Nested decompositions (Sec. 2.3): the fine label of every element and the fine overlap layers.
+struct NestedArgs {
+  int n_labels;
+  const int32_t* elem_to_fine;
+  int fine_overlap;
+};
+
+static hk_status setup_impl(hk_handle* h, const hk_mesh* mesh, const double* coeff, const hk_params* prm,
+                            const NestedArgs* nest = nullptr) {
   HK_TRY(dalloc(h, &h->d_status, 1));
   PhaseTimer t(h->stream);
   HK_TRY(phase_assembly(h, mesh, coeff));
   h->setup_ms[0] = t.stop();
   uint8_t* d_elem_in = nullptr;
   HK_TRY(phase_decomposition(h, prm->elem_to_sub, &d_elem_in));
+  hk_handle* c = nullptr;
+  if (nest) {
+    // the fine subdomains and their local solves in a child handle (one level, apply only); this handle
+    // keeps the coarse subdomains for the eigenproblems and the coarse space
+    c = new hk_handle();
+    h->child = c;
+    c->dev = h->dev;
+    c->stream = h->stream;
+    c->dim = h->dim;
+    c->nv = h->nv;
+    c->n_nodes = h->n_nodes;
+    c->n_elems = h->n_elems;
+    c->k = h->k;
+    c->p = h->p;
+    c->p.levels = HK_ONE_LEVEL;
+    c->dev_inputs = h->dev_inputs;
+    c->apply_only = true;
+    HK_TRY(dalloc(c, &c->d_status, 1));
+    HK_TRY(phase_assembly(c, mesh, coeff));
+    uint8_t* d_fin = nullptr;
+    int nf = 0;
+    HK_TRY(nested_fine_membership(h, d_elem_in, nest->n_labels, nest->elem_to_fine, nest->fine_overlap, &d_fin, &nf,
+                                  &h->fine_parent));
+    c->n_sub = c->p.n_sub = nf;
+    hk_status ds = decomposition_from_membership(c, d_fin);
+    dfree(h, d_fin);
+    HK_TRY(ds);
+  }
   h->setup_ms[1] = t.stop();
+  if (c) HK_TRY(phase_local_factors_begin(c));
   HK_TRY(phase_local_factors_begin(h));
   if (h->p.levels != HK_ONE_LEVEL) {
     // the factor kernels run on the auxiliary stream meanwhile; setup_ms[2] is their host part
@@ -203,8 +244,10 @@ static hk_status setup_impl(hk_handle* h, const hk_mesh* mesh, const double* coe
     HK_TRY(phase_eigen(h, d_elem_in));
     h->setup_ms[3] = t.stop();
     HK_TRY(phase_local_factors_mid(h));
+    if (c) HK_TRY(phase_local_factors_mid(c));
     HK_TRY(phase_coarse(h));
     HK_TRY(phase_local_factors_end(h));
+    if (c) HK_TRY(phase_local_factors_end(c));
     h->setup_ms[4] = t.stop();
   } else {
     HK_TRY(phase_local_factors_end(h));
@@ -216,7 +259,7 @@ static hk_status setup_impl(hk_handle* h, const hk_mesh* mesh, const double* coe
 }
 
 static hk_status setup_common(const hk_mesh* mesh, const double* elem_coeff, double k, const hk_params* prm,
-                              void* cuda_stream, hk_handle** out, bool dev_inputs) {
+                              void* cuda_stream, hk_handle** out, bool dev_inputs, const NestedArgs* nest = nullptr) {
   if (!out) {
     hk_set_error("out is NULL");
     return HK_BAD_ARG;
@@ -247,7 +290,8 @@ static hk_status setup_common(const hk_mesh* mesh, const double* elem_coeff, dou
   h->p = *prm;
   h->p.elem_to_sub = nullptr;
   h->dev_inputs = dev_inputs;
-  hk_status s = setup_impl(h, mesh, elem_coeff, prm);
+  if (nest) h->p.levels = HK_COARSE_ONLY;  // its own apply is the coarse correction; the child adds the local part
+  hk_status s = setup_impl(h, mesh, elem_coeff, prm, nest);
   if (s != HK_OK) {
     cudaGetLastError();
     destroy_all(h);
@@ -260,6 +304,32 @@ static hk_status setup_common(const hk_mesh* mesh, const double* elem_coeff, dou
 extern "C" hk_status hk_setup(const hk_mesh* mesh, const double* elem_coeff, double k, const hk_params* prm,
                               void* cuda_stream, hk_handle** out) {
   return setup_common(mesh, elem_coeff, k, prm, cuda_stream, out, false);
+}
+
+static hk_status setup_nested_common(const hk_mesh* mesh, const double* elem_coeff, double k, const hk_params* prm,
+                                     int n_fine_labels, const int32_t* elem_to_fine, int fine_overlap,
+                                     void* cuda_stream, hk_handle** out, bool dev_inputs) {
+  if (out) *out = nullptr;
+  if (!prm || prm->levels != HK_TWO_LEVEL || n_fine_labels < 1 || !elem_to_fine || fine_overlap < 0) {
+    hk_set_error("hk_setup_nested: needs the two-level preconditioner, fine labels and fine_overlap >= 0");
+    return HK_BAD_ARG;
+  }
+  NestedArgs nest{n_fine_labels, elem_to_fine, fine_overlap};
+  return setup_common(mesh, elem_coeff, k, prm, cuda_stream, out, dev_inputs, &nest);
+}
+
+extern "C" hk_status hk_setup_nested(const hk_mesh* mesh, const double* elem_coeff, double k, const hk_params* prm,
+                                     int n_fine_labels, const int32_t* elem_to_fine, int fine_overlap_layers,
+                                     void* cuda_stream, hk_handle** out) {
+  return setup_nested_common(mesh, elem_coeff, k, prm, n_fine_labels, elem_to_fine, fine_overlap_layers, cuda_stream,
+                             out, false);
+}
+
+extern "C" hk_status hk_setup_nested_device(const hk_mesh* mesh_dev, const double* elem_coeff_dev, double k,
+                                            const hk_params* prm, int n_fine_labels, const int32_t* elem_to_fine_dev,
+                                            int fine_overlap_layers, void* cuda_stream, hk_handle** out) {
+  return setup_nested_common(mesh_dev, elem_coeff_dev, k, prm, n_fine_labels, elem_to_fine_dev, fine_overlap_layers,
+                             cuda_stream, out, true);
 }
 
 extern "C" hk_status hk_setup_device(const hk_mesh* mesh_dev, const double* elem_coeff_dev, double k,
@@ -282,6 +352,11 @@ extern "C" hk_status hk_set_timing(hk_handle* h, int on) {
   h->tl.clear();
   h->ev_used = 0;
   h->timing = on != 0;
+  if (h->child) {
+    h->child->tl.clear();
+    h->child->ev_used = 0;
+    h->child->timing = on != 0;
+  }
   return HK_OK;
 }
 
@@ -295,6 +370,12 @@ extern "C" hk_status hk_set_sweep_path(hk_handle* h, int path) {
   if (!h || path < HK_SWEEPS_AUTO || path > HK_SWEEPS_TENSOR_CORE) {
     hk_set_error("hk_set_sweep_path: invalid arguments");
     return HK_BAD_ARG;
+  }
+  if (h->child) {  // nested decompositions: the local sweeps are the fine handle's
+    HK_TRY(hk_set_sweep_path(h->child, path));
+    HK_CUDA(cudaStreamSynchronize(h->stream));
+    hk_drop_graphs(h);
+    return HK_OK;
   }
   if (path == HK_SWEEPS_TENSOR_CORE && !h->tc_ok) {
     hk_set_error(h->p.precision == HK_SPLIT_BF16_PRECOND
@@ -317,12 +398,13 @@ extern "C" hk_status hk_kernel_times(hk_handle* h, double* ms, int32_t* count) {
     ms[c] = 0;
     count[c] = 0;
   }
-  for (auto& t : h->tl) {
-    float e = 0;
-    HK_CUDA(cudaEventElapsedTime(&e, t.a, t.b));
-    ms[t.cat] += e;
-    count[t.cat] += 1;
-  }
+  for (const hk_handle* q = h; q; q = q->child)  // a nested handle's local sweeps are its child's
+    for (auto& t : q->tl) {
+      float e = 0;
+      HK_CUDA(cudaEventElapsedTime(&e, t.a, t.b));
+      ms[t.cat] += e;
+      count[t.cat] += 1;
+    }
   return HK_OK;
 }
 
@@ -378,19 +460,21 @@ extern "C" hk_status hk_theory(const hk_handle* h, double c_stab, double H_f, hk
     hk_set_error("hk_theory: invalid arguments");
     return HK_BAD_ARG;
   }
-  if (h->p.levels != HK_TWO_LEVEL) {
+  if (h->p.levels != HK_TWO_LEVEL && !h->child) {
     hk_set_error("hk_theory: the theorem is stated for the two-level preconditioner");
     return HK_UNSUPPORTED;
   }
+  // Lambda and H^f are those of the fine subdomains (the subdomains themselves with one decomposition)
+  const hk_handle* f = h->child ? h->child : h;
   if (!(H_f > 0)) {
     // largest bounding-box diagonal of a subdomain's dof nodes
     std::vector<double> xyz((size_t)h->n_nodes * h->dim);
-    std::vector<int> node(h->n), I(h->I_total);
-    HK_CUDA(cudaMemcpy(xyz.data(), h->d_xyz, sizeof(double) * xyz.size(), cudaMemcpyDeviceToHost));
-    HK_CUDA(cudaMemcpy(node.data(), h->d_node_of_dof, sizeof(int) * node.size(), cudaMemcpyDeviceToHost));
-    HK_CUDA(cudaMemcpy(I.data(), h->d_I, sizeof(int) * I.size(), cudaMemcpyDeviceToHost));
+    std::vector<int> node(f->n), I(f->I_total);
+    HK_CUDA(cudaMemcpy(xyz.data(), f->d_xyz, sizeof(double) * xyz.size(), cudaMemcpyDeviceToHost));
+    HK_CUDA(cudaMemcpy(node.data(), f->d_node_of_dof, sizeof(int) * node.size(), cudaMemcpyDeviceToHost));
+    HK_CUDA(cudaMemcpy(I.data(), f->d_I, sizeof(int) * I.size(), cudaMemcpyDeviceToHost));
     H_f = 0;
-    for (const Sub& u : h->subs) {
+    for (const Sub& u : f->subs) {
       double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
       for (int a = 0; a < u.nI; ++a) {
         const double* p = &xyz[(size_t)node[I[(size_t)u.I_off + a]] * h->dim];
@@ -401,7 +485,7 @@ extern "C" hk_status hk_theory(const hk_handle* h, double c_stab, double H_f, hk
       if (u.nI > 0) H_f = std::max(H_f, std::sqrt(d2));
     }
   }
-  double Lam = h->lambda_elems, tau = h->tau_next, k = h->k;
+  double Lam = f->lambda_elems, tau = h->tau_next, k = h->k;
   double Theta = 1.0 / tau, a = 2.0 + 3.0 * std::pow(Lam, 4) * Theta;
   out->Lambda = Lam;
   out->tau = tau;
@@ -464,8 +548,8 @@ extern "C" hk_status hk_info(const hk_handle* h, hk_info_t* info) {
   info->max_dof = h->max_dof;
   info->nnz = h->nnz;
   info->precision = h->p.precision;
-  info->levels = h->p.levels;
-  info->bytes_resident = h->bytes;
+  info->levels = h->child ? HK_TWO_LEVEL : h->p.levels;
+  info->bytes_resident = h->bytes + (h->child ? h->child->bytes : 0);
   info->factor_elems = h->f_total;
   info->dof_total = h->I_total;
   info->coarse_elems = h->z_total;
@@ -480,6 +564,19 @@ extern "C" hk_status hk_info(const hk_handle* h, hk_info_t* info) {
   info->twist_moved = h->twist_moved;
   info->local_growth[0] = h->growth_twist;
   info->local_growth[1] = h->growth_mid;
+  const hk_handle* c = h->child;
+  info->fine_subdomains = c ? c->n_sub : 0;
+  info->fine_lambda_elems = c ? c->lambda_elems : 0;
+  info->fine_max_dof = c ? c->max_dof : 0;
+  info->fine_dof_total = c ? c->I_total : 0;
+  if (c) {
+    info->max_level = c->max_level;
+    info->twist_moved = c->twist_moved;
+    info->local_growth[0] = c->growth_twist;
+    info->local_growth[1] = c->growth_mid;
+    info->tc_record_bytes = c->tc_ok ? c->tc_bytes : 0;
+    info->last_sweeps = c->last_sweeps;
+  }
   return HK_OK;
 }
 

@@ -392,15 +392,15 @@ hk_status upload_sub_info(hk_handle* h) {
 
 hk_status phase_decomposition(hk_handle* h, const int32_t* elem_to_sub, uint8_t** d_elem_in_out) {
   cudaStream_t st = h->stream;
-  int ns = h->n_sub, ne = h->n_elems, nn = h->n_nodes, n = h->n, nv = h->nv;
+  int ns = h->n_sub, ne = h->n_elems, nn = h->n_nodes, nv = h->nv;
   int* d_e2s = nullptr;
   HK_TRY(dalloc(h, &d_e2s, ne));
   HK_CUDA(cudaMemcpyAsync(d_e2s, elem_to_sub, sizeof(int) * ne,
                           h->dev_inputs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-  uint8_t *d_elem_in = nullptr, *d_node_in = nullptr, *d_cls = nullptr;
+  uint8_t *d_elem_in = nullptr, *d_node_in = nullptr;
   HK_TRY(dalloc(h, &d_elem_in, (size_t)ne * ns));
   HK_TRY(dalloc(h, &d_node_in, (size_t)nn * ns));
-  long long NE = (long long)ne * ns, NN = (long long)nn * ns, ND = (long long)n * ns;
+  long long NE = (long long)ne * ns, NN = (long long)nn * ns;
   k_init_elem_in<<<nblk(NE, 256), 256, 0, st>>>(d_e2s, ne, ns, d_elem_in, h->d_status); HK_COUNT_LAUNCH();
   for (int layer = 0; layer < h->p.overlap_layers; ++layer) {
     k_mark_nodes<<<nblk(NN, 256), 256, 0, st>>>(nn, ns, ne, h->d_dof_of_node, h->d_ne_ptr, h->d_ne_idx, d_elem_in,
@@ -411,6 +411,18 @@ hk_status phase_decomposition(hk_handle* h, const int32_t* elem_to_sub, uint8_t*
   HK_TRY(check_device_status(h, "partition"));
   dfree(h, d_node_in);
   dfree(h, d_e2s);
+  *d_elem_in_out = d_elem_in;
+  return decomposition_from_membership(h, d_elem_in);
+}
+
+// Everything after the element membership of the overlapping subdomains (elem_in[s * n_elems + e]): dof
+// and ovdof (Def. 3.2), mu (Def. 2.7), Lambda, the level order of every dof(Omega_s), the local matrices
+// and the pull map of the scatter.  The membership stays owned by the caller.
+hk_status decomposition_from_membership(hk_handle* h, const uint8_t* d_elem_in) {
+  cudaStream_t st = h->stream;
+  int ns = h->n_sub, ne = h->n_elems, n = h->n;
+  long long ND = (long long)n * ns;
+  uint8_t* d_cls = nullptr;
   HK_TRY(dalloc(h, &d_cls, (size_t)n * ns));
   k_classify<<<nblk(ND, 256), 256, 0, st>>>(n, ns, ne, h->d_node_of_dof, h->d_ne_ptr, h->d_ne_idx, d_elem_in,
                                             d_cls); HK_COUNT_LAUNCH();
@@ -519,6 +531,129 @@ hk_status phase_decomposition(hk_handle* h, const int32_t* elem_to_sub, uint8_t*
   dfree(h, d_nI);
   dfree(h, d_nG);
   dfree(h, d_scal);
-  *d_elem_in_out = d_elem_in;
+  return HK_OK;
+}
+
+
+// ================================================================ nested decompositions (Sec. 2.3)
+// The fine subdomains Omega^f_{i,j} inside each coarse subdomain Omega_i^c: its elements grouped by their
+// fine label, each group extended fine_overlap times by Def. 2.3 in the mesh of Omega_i^c (a layer adds
+// only elements of Omega_i^c), so that the union of the fine subdomains of Omega_i^c is Omega_i^c.
+
+// present[s * nlab + t] = 1 when coarse subdomain s has an element of fine label t.
+__global__ void k_fine_labels(int ne, int n_sub, int nlab, const int* __restrict__ e2f,
+                              const uint8_t* __restrict__ cin, uint8_t* present, DevStatus* st) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)ne * n_sub) return;
+  int s = (int)(i / ne), e = (int)(i % ne);
+  int t = e2f[e];
+  if (s == 0 && (t < 0 || t >= nlab)) dev_fail(st, HK_BAD_ARG, e, t);
+  if (cin[i] && t >= 0 && t < nlab) present[(long long)s * nlab + t] = 1;
+}
+
+// Fine subdomain f: the elements of coarse subdomain par[f] whose label is lab[f].
+__global__ void k_init_fine(int ne, int nf, const int* __restrict__ par, const int* __restrict__ lab,
+                            const int* __restrict__ e2f, const uint8_t* __restrict__ cin, uint8_t* fin) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)ne * nf) return;
+  int f = (int)(i / ne), e = (int)(i % ne);
+  fin[i] = (cin[(long long)par[f] * ne + e] && e2f[e] == lab[f]) ? 1 : 0;
+}
+
+// One growth layer (as k_grow) kept inside the parent coarse subdomain.
+__global__ void k_grow_within(int ne, int nf, int nn, int nv, const int* __restrict__ elems,
+                              const uint8_t* __restrict__ node_in, const int* __restrict__ par,
+                              const uint8_t* __restrict__ cin, uint8_t* fin) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)ne * nf) return;
+  int f = (int)(i / ne), e = (int)(i % ne);
+  if (fin[i] || !cin[(long long)par[f] * ne + e]) return;
+  const uint8_t* nin = node_in + (long long)f * nn;
+  for (int j = 0; j < nv; ++j)
+    if (nin[elems[e * nv + j]]) { fin[i] = 1; return; }
+}
+
+// dst row r = src row keep[r] (rows of ne bytes).
+__global__ void k_gather_rows(int ne, int nk, const int* __restrict__ keep, const uint8_t* __restrict__ src,
+                              uint8_t* dst) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)ne * nk) return;
+  int r = (int)(i / ne), e = (int)(i % ne);
+  dst[i] = src[(long long)keep[r] * ne + e];
+}
+
+hk_status nested_fine_membership(hk_handle* h, const uint8_t* d_cin, int nlab, const int32_t* elem_to_fine,
+                                 int fine_overlap, uint8_t** d_fin_out, int* nf_out, std::vector<int>* parent_out) {
+  cudaStream_t st = h->stream;
+  int N = h->n_sub, ne = h->n_elems, nn = h->n_nodes, n = h->n, nv = h->nv;
+  int* d_e2f = nullptr;
+  uint8_t* d_present = nullptr;
+  HK_TRY(dalloc(h, &d_e2f, ne));
+  HK_CUDA(cudaMemcpyAsync(d_e2f, elem_to_fine, sizeof(int) * ne,
+                          h->dev_inputs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  HK_TRY(dalloc(h, &d_present, (size_t)N * nlab));
+  HK_CUDA(cudaMemsetAsync(d_present, 0, (size_t)N * nlab, st));
+  k_fine_labels<<<nblk((long long)ne * N, 256), 256, 0, st>>>(ne, N, nlab, d_e2f, d_cin, d_present, h->d_status);
+  HK_COUNT_LAUNCH();
+  HK_LAUNCH_CHECK();
+  std::vector<uint8_t> present((size_t)N * nlab);
+  HK_CUDA(cudaMemcpyAsync(present.data(), d_present, present.size(), cudaMemcpyDeviceToHost, st));
+  HK_CUDA(cudaStreamSynchronize(st));
+  HK_TRY(check_device_status(h, "fine labels"));
+  dfree(h, d_present);
+  std::vector<int> par, lab;
+  for (int s = 0; s < N; ++s)
+    for (int t = 0; t < nlab; ++t)
+      if (present[(size_t)s * nlab + t]) par.push_back(s), lab.push_back(t);
+  int nf = (int)par.size();
+  int *d_par = nullptr, *d_lab = nullptr;
+  uint8_t *d_fin = nullptr, *d_node = nullptr, *d_cls = nullptr;
+  HK_TRY(dalloc(h, &d_par, nf));
+  HK_TRY(dalloc(h, &d_lab, nf));
+  HK_TRY(dalloc(h, &d_fin, (size_t)ne * nf));
+  HK_TRY(dalloc(h, &d_node, (size_t)nn * nf));
+  HK_CUDA(cudaMemcpyAsync(d_par, par.data(), sizeof(int) * nf, cudaMemcpyHostToDevice, st));
+  HK_CUDA(cudaMemcpyAsync(d_lab, lab.data(), sizeof(int) * nf, cudaMemcpyHostToDevice, st));
+  long long NE = (long long)ne * nf, NN = (long long)nn * nf, ND = (long long)n * nf;
+  k_init_fine<<<nblk(NE, 256), 256, 0, st>>>(ne, nf, d_par, d_lab, d_e2f, d_cin, d_fin);
+  HK_COUNT_LAUNCH();
+  for (int layer = 0; layer < fine_overlap; ++layer) {
+    k_mark_nodes<<<nblk(NN, 256), 256, 0, st>>>(nn, nf, ne, h->d_dof_of_node, h->d_ne_ptr, h->d_ne_idx, d_fin,
+                                                d_node);
+    HK_COUNT_LAUNCH();
+    k_grow_within<<<nblk(NE, 256), 256, 0, st>>>(ne, nf, nn, nv, h->d_elems, d_node, d_par, d_cin, d_fin);
+    HK_COUNT_LAUNCH();
+  }
+  // leave out the fine subdomains without a dof (slivers of Omega_i^c: they span the zero space)
+  HK_TRY(dalloc(h, &d_cls, (size_t)ND));
+  int *d_nI = nullptr, *d_nG = nullptr;
+  HK_TRY(dalloc(h, &d_nI, nf));
+  HK_TRY(dalloc(h, &d_nG, nf));
+  k_classify<<<nblk(ND, 256), 256, 0, st>>>(n, nf, ne, h->d_node_of_dof, h->d_ne_ptr, h->d_ne_idx, d_fin, d_cls);
+  HK_COUNT_LAUNCH();
+  k_count_cls<<<nf, 512, 0, st>>>(n, d_cls, d_nI, d_nG);
+  HK_COUNT_LAUNCH();
+  HK_LAUNCH_CHECK();
+  std::vector<int> nI(nf);
+  HK_CUDA(cudaMemcpyAsync(nI.data(), d_nI, sizeof(int) * nf, cudaMemcpyDeviceToHost, st));
+  HK_CUDA(cudaStreamSynchronize(st));
+  std::vector<int> keep;
+  parent_out->clear();
+  for (int f = 0; f < nf; ++f)
+    if (nI[f] > 0) keep.push_back(f), parent_out->push_back(par[f]);
+  int nk = (int)keep.size();
+  int* d_keep = nullptr;
+  uint8_t* d_out = nullptr;
+  HK_TRY(dalloc(h, &d_keep, nk));
+  HK_TRY(dalloc(h, &d_out, (size_t)ne * nk));
+  HK_CUDA(cudaMemcpyAsync(d_keep, keep.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
+  k_gather_rows<<<nblk((long long)ne * nk, 256), 256, 0, st>>>(ne, nk, d_keep, d_fin, d_out);
+  HK_COUNT_LAUNCH();
+  HK_LAUNCH_CHECK();
+  HK_CUDA(cudaStreamSynchronize(st));
+  void* fr[] = {d_e2f, d_par, d_lab, d_fin, d_node, d_cls, d_nI, d_nG, d_keep};
+  for (void* p : fr) dfree(h, p);
+  *d_fin_out = d_out;
+  *nf_out = nk;
   return HK_OK;
 }

@@ -109,6 +109,10 @@ struct DkState {  // host side of one right-hand side's GMRES
 hk_status run_left_dk_gmres(hk_handle* h, int s, const double* f, double tol, double* u, int32_t* iters_out,
                             double* res_hist, double* final_true, double* final_pc) {
   HK_TRY(ensure_workspace(h, s));
+  if (h->child) {
+    HK_TRY(ensure_workspace(h->child, s));
+    if (apply_needs_tuning(h->child, s)) HK_TRY(apply_autotune(h->child, s));
+  }
   if (apply_needs_tuning(h, s)) HK_TRY(apply_autotune(h, s));
   cudaStream_t st = h->stream;
   int n = h->n, m = h->p.restart, mi = h->p.max_iters, ld = m + 2;

@@ -220,6 +220,12 @@ struct hk_handle {
   int* d_twist = nullptr;       // per subdomain: twist level M of its factorisation
   double growth_twist = 0, growth_mid = 0;  // max over subdomains of the pivot growth (chosen M; M = (L-1)/2)
   int twist_moved = 0;          // subdomains whose twist level is not the middle one
+  // nested decompositions (Sec. 2.3): this handle holds the coarse subdomains (eigenproblems, coarse
+  // space) and child the fine ones (local solves, a one-level handle that only applies); fine_parent: the
+  // coarse subdomain of each fine one
+  hk_handle* child = nullptr;
+  bool apply_only = false;
+  std::vector<int> fine_parent;
   double tau_next = INFINITY;   // min over subdomains of the first local eigenvalue not kept (Thm. 3.1 tau)
   bool tau_next_lb = false;     // tau_next is only the lower bound tau + delta (no candidate above the kept)
   int* d_ctl = nullptr;         // [0] inner step j, [1] cycles run, [2] inner steps run
@@ -320,6 +326,12 @@ hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<i
 // ---- phases (each file implements one) ----
 hk_status phase_assembly(hk_handle* h, const hk_mesh* mesh, const double* coeff);
 hk_status phase_decomposition(hk_handle* h, const int32_t* elem_to_sub, uint8_t** d_elem_in_out);
+// The rest of the decomposition from an element membership elem_in[s * n_elems + e] of h->n_sub subdomains.
+hk_status decomposition_from_membership(hk_handle* h, const uint8_t* d_elem_in);
+// Nested decompositions (Sec. 2.3): the membership of the fine subdomains inside the coarse subdomains of h
+// (coarse membership d_cin), allocated in h; their number and parent coarse subdomain.
+hk_status nested_fine_membership(hk_handle* h, const uint8_t* d_cin, int nlab, const int32_t* elem_to_fine,
+                                 int fine_overlap, uint8_t** d_fin_out, int* nf_out, std::vector<int>* parent_out);
 hk_status phase_local_factors_begin(hk_handle* h);
 hk_status phase_local_factors_mid(hk_handle* h);
 hk_status phase_local_factors_end(hk_handle* h);

@@ -547,6 +547,32 @@ hk_status ensure_workspace(hk_handle* h, int s) {
   s = cap;
   hk_drop_graphs(h);
   HK_TRY(apply_prepare(h));
+  if (h->apply_only) {
+    // the fine handle of a nested pair: the preconditioner's buffers only (and an input and an output block
+    // for the autotuner)
+    void* oldb[] = {h->d_V, h->d_Zk, h->d_ybuf64, h->d_ybuf32, h->d_c64, h->d_cc64, h->d_c32, h->d_cc32};
+    for (void* p : oldb)
+      if (p) dfree(h, p);
+    h->d_V = h->d_Zk = h->d_ybuf64 = h->d_c64 = h->d_cc64 = nullptr;
+    h->d_ybuf32 = h->d_c32 = h->d_cc32 = nullptr;
+    HK_TRY(dalloc(h, &h->d_V, (size_t)s * h->n));
+    HK_TRY(dalloc(h, &h->d_Zk, (size_t)s * h->n));
+    if (precond_f32(h->p)) {
+      HK_TRY(dalloc(h, &h->d_ybuf32, 2 * (size_t)s * h->I_total));
+      HK_TRY(dalloc(h, &h->d_c32, (size_t)s * (h->n0 + 1)));
+      HK_TRY(dalloc(h, &h->d_cc32, (size_t)s * (h->n0 + 1)));
+    } else {
+      HK_TRY(dalloc(h, &h->d_ybuf64, 2 * (size_t)s * h->I_total));
+      HK_TRY(dalloc(h, &h->d_c64, (size_t)s * (h->n0 + 1)));
+      HK_TRY(dalloc(h, &h->d_cc64, (size_t)s * (h->n0 + 1)));
+    }
+    HK_CUDA(cudaMemsetAsync(h->d_V, 0, sizeof(double) * (size_t)s * h->n, h->stream));
+    h->ws_rhs = s;
+    h->ws_m = m;
+    h->nr_tuned.clear();
+    h->tc_tuned.clear();
+    return HK_OK;
+  }
   void* old[] = {h->d_V, h->d_Zk, h->d_w, h->d_x, h->d_f, h->d_ybuf64, h->d_ybuf32, h->d_c64, h->d_cc64,
                  h->d_c32, h->d_cc32, h->d_part, h->d_counter, h->d_H, h->d_cs, h->d_sn, h->d_g, h->d_hcol,
                  h->d_state, h->d_rstate, h->d_hist, h->d_ctl};
@@ -834,6 +860,10 @@ static hk_status fgmres_results(hk_handle* h, int s, double* u_dev, int32_t* ite
 hk_status run_fgmres(hk_handle* h, int s, const double* rhs_dev, double tol, double* u_dev, int32_t* iters,
                      double* res_hist, double* final_res) {
   HK_TRY(ensure_workspace(h, s));
+  if (h->child) {
+    HK_TRY(ensure_workspace(h->child, s));
+    if (apply_needs_tuning(h->child, s)) HK_TRY(apply_autotune(h->child, s));
+  }
   if (apply_needs_tuning(h, s)) HK_TRY(apply_autotune(h, s));
   cudaStream_t st = h->stream;
   int m = h->p.restart;

@@ -895,7 +895,7 @@ template <typename T, int SR>
 __global__ void k_scatter(int n, int s, const int* __restrict__ pull_ptr, const int* __restrict__ pull_row,
                           const T* __restrict__ ybuf, const T* __restrict__ zc, long long I_total, int do_local,
                           int do_coarse, int ras, const int* __restrict__ mu, double* z,
-                          const int* __restrict__ active, const int* __restrict__ jp, long long jstride) {
+                          const int* __restrict__ active, const int* __restrict__ jp, long long jstride, int accum) {
   int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n) return;
   if (jp) z += (long long)(*jp) * jstride;  // captured inner step: z = z_j
@@ -918,7 +918,10 @@ __global__ void k_scatter(int n, int s, const int* __restrict__ pull_ptr, const 
     }
 #pragma unroll
     for (int r = 0; r < SR; ++r)
-      if (r < nr && (!active || active[8 * (r0 + r)])) z[(long long)(r0 + r) * n + l] = (double)acc[r];
+      if (r < nr && (!active || active[8 * (r0 + r)])) {
+        long long o = (long long)(r0 + r) * n + l;
+        z[o] = accum ? z[o] + (double)acc[r] : (double)acc[r];  // accum: added to the fine local part (nested)
+      }
   }
 }
 
@@ -1094,7 +1097,7 @@ static hk_status apply_t(hk_handle* h, int s, const double* v, double* z, const 
   HK_TIMED(h, HK_T_SCATTER,                                                                                   \
            (k_scatter<T, SRV><<<nblk(h->n, 128), 128, 0, h->stream>>>(                                        \
                h->n, s, h->d_pull_ptr, h->d_pull_row, ybuf, zc, h->I_total, do_local, do_coarse,              \
-               h->p.weighting == HK_RAS_POU, h->d_mu, z, active, h->g_jp, h->g_jstride)))
+               h->p.weighting == HK_RAS_POU, h->d_mu, z, active, h->g_jp, h->g_jstride, h->child != nullptr)))
   switch (cr) {
     case 8: HK_SCATTER_LAUNCH(8); break;
     case 4: HK_SCATTER_LAUNCH(4); break;
@@ -1141,6 +1144,7 @@ hk_status apply_prepare(hk_handle*) {
 }
 
 bool apply_needs_tuning(const hk_handle* h, int s) {
+  if (h->p.levels == HK_COARSE_ONLY) return false;  // no local sweeps to tune
   return (s > 1 && !h->nr_tuned.count(s)) || (h->tc_ok && h->sweep_path == HK_SWEEPS_AUTO && !h->tc_tuned.count(s));
 }
 
@@ -1198,6 +1202,16 @@ hk_status apply_autotune(hk_handle* h, int s) {
 
 hk_status op_apply(hk_handle* h, int s, const double* v, double* z, const int* active) {
   HK_TRY(ensure_workspace(h, s));
+  if (h->child) {
+    // nested decompositions: the local solves on the fine subdomains (the child writes z), then this
+    // handle's coarse correction added to it (Eq. 2.23 with the one-level part of Eq. 2.22 on the fine ones)
+    hk_handle* c = h->child;
+    c->stream = h->stream;
+    c->g_jp = h->g_jp;
+    c->g_jstride = h->g_jstride;
+    c->timing = h->timing;
+    HK_TRY(op_apply(c, s, v, z, active));
+  }
   if (precond_f32(h->p)) return apply_t<float>(h, s, v, z, active, h->d_ybuf32, h->d_c32, h->d_cc32);
   return apply_t<double>(h, s, v, z, active, h->d_ybuf64, h->d_c64, h->d_cc64);
 }
@@ -1517,6 +1531,10 @@ extern "C" hk_status hk_apply_precond_noalloc(hk_handle* h, int n_rhs, const dou
   if (!h || n_rhs < 1 || !v_dev || !z_dev) {
     hk_set_error("hk_apply_precond_noalloc: invalid arguments");
     return HK_BAD_ARG;
+  }
+  if (h->child) {
+    hk_set_error("hk_apply_precond_noalloc: handles of nested decompositions are not supported (use hk_apply_precond)");
+    return HK_UNSUPPORTED;
   }
   size_t esz = precond_f32(h->p) ? sizeof(float) : sizeof(double);
   size_t ylen = align256(esz * 2 * (size_t)n_rhs * (size_t)h->I_total);

@@ -55,7 +55,8 @@ class hk_info_t(C.Structure):
                 ("setup_ms", C.c_double * 8), ("bytes_peak", C.c_size_t), ("graph_solves", C.c_longlong),
                 ("eigen_kernel_ms", C.c_double * 4), ("eigen_kernel_gflop", C.c_double * 4),
                 ("tc_record_bytes", C.c_longlong), ("last_sweeps", C.c_int), ("twist_moved", C.c_int),
-                ("local_growth", C.c_double * 2)]
+                ("local_growth", C.c_double * 2), ("fine_subdomains", C.c_int), ("fine_lambda_elems", C.c_int),
+                ("fine_max_dof", C.c_int), ("fine_dof_total", C.c_longlong)]
 
 
 class hk_theory_t(C.Structure):
@@ -90,6 +91,10 @@ def lib():
     L = C.CDLL(LIB_PATH)
     L.hk_setup.argtypes = [C.POINTER(hk_mesh), _P, C.c_double, C.POINTER(hk_params), _P, C.POINTER(_P)]
     L.hk_setup_device.argtypes = [C.POINTER(hk_mesh), _P, C.c_double, C.POINTER(hk_params), _P, C.POINTER(_P)]
+    L.hk_setup_nested.argtypes = [C.POINTER(hk_mesh), _P, C.c_double, C.POINTER(hk_params), C.c_int, _P, C.c_int, _P,
+                                  C.POINTER(_P)]
+    L.hk_setup_nested_device.argtypes = [C.POINTER(hk_mesh), _P, C.c_double, C.POINTER(hk_params), C.c_int, _P,
+                                         C.c_int, _P, C.POINTER(_P)]
     L.hk_set_timing.argtypes = [_P, C.c_int]
     L.hk_set_solve_graphs.argtypes = [_P, C.c_int]
     L.hk_set_solve_graphs.restype = C.c_int
@@ -131,7 +136,8 @@ def lib():
     for f in ("hk_setup", "hk_setup_device", "hk_set_timing", "hk_kernel_times", "hk_solve", "hk_solve_device", "hk_info", "hk_destroy", "hk_get_matrix",
               "hk_get_subdomain", "hk_get_mu", "hk_get_eigen", "hk_get_coarse", "hk_apply_precond", "hk_matvec",
               "hk_assemble_load", "hk_check_status", "hk_set_wait_limit", "hk_apply_precond_noalloc",
-              "hk_set_sweep_path", "hk_solve_left_dk", "hk_solve_left_dk_device", "hk_theory"):
+              "hk_set_sweep_path", "hk_solve_left_dk", "hk_solve_left_dk_device", "hk_theory", "hk_setup_nested",
+              "hk_setup_nested_device"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -185,6 +191,35 @@ def hk_setup(xyz, elems, is_boundary, elem_coeff, k, elem_to_sub, n_sub, overlap
            "hk_setup")
     h = Handle(out, int((bnd == 0).sum()), int(max_iters))
     return h
+
+
+def hk_setup_nested(xyz, elems, is_boundary, elem_coeff, k, elem_to_sub, n_sub, elem_to_fine, n_fine_labels,
+                    overlap=2, fine_overlap=1, tau=0.5, precision=HK_FP64, weighting=HK_AS, restart=50,
+                    max_iters=1000, stream=None) -> Handle:
+    """The nested coarse/fine decompositions of Sec. 2.3 (hk_setup_nested)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    elems = np.ascontiguousarray(elems, dtype=np.int32)
+    bnd = np.ascontiguousarray(is_boundary, dtype=np.uint8)
+    coeff = np.ascontiguousarray(elem_coeff, dtype=np.float64)
+    e2s = np.ascontiguousarray(elem_to_sub, dtype=np.int32)
+    e2f = np.ascontiguousarray(elem_to_fine, dtype=np.int32)
+    mesh = hk_mesh(xyz.shape[1], xyz.shape[0], xyz.ctypes.data_as(C.POINTER(C.c_double)), elems.shape[0],
+                   elems.ctypes.data_as(C.POINTER(C.c_int32)), bnd.ctypes.data_as(C.POINTER(C.c_uint8)))
+    prm = hk_params(int(n_sub), e2s.ctypes.data_as(C.POINTER(C.c_int32)), int(overlap), float(tau), int(precision),
+                    HK_TWO_LEVEL, int(weighting), int(restart), int(max_iters))
+    out = _P()
+    _check(lib().hk_setup_nested(C.byref(mesh), _ptr(coeff), float(k), C.byref(prm), int(n_fine_labels), _ptr(e2f),
+                                 int(fine_overlap), _P(stream or 0), C.byref(out)), "hk_setup_nested")
+    return Handle(out, int((bnd == 0).sum()), int(max_iters))
+
+
+def setup_problem_nested(p, elem_to_fine, n_fine_labels, fine_overlap=1, precision=HK_FP64, weighting=HK_AS,
+                         stream=None) -> Handle:
+    """hk_setup_nested for a workloads.Problem and a fine element labelling."""
+    m = p.mesh
+    return hk_setup_nested(m.xyz, m.elems, m.is_boundary, p.coeff, p.k, p.elem_to_sub, p.n_sub, elem_to_fine,
+                           n_fine_labels, p.overlap, fine_overlap, p.tau, precision, weighting, p.restart,
+                           p.max_iters, stream)
 
 
 def hk_setup_device(xyz_dev, elems_dev, is_boundary_dev, elem_coeff_dev, k, elem_to_sub_dev, n_sub, overlap=2,
