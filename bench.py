@@ -98,10 +98,12 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
-def workload_config(p, name, precision):
+def workload_config(p, name, precision, fine_parts=0, fine_overlap=0):
+    nest = (f", nested: fine {fine_parts}x{fine_parts} boxes inside the coarse subdomains, fine overlap "
+            f"{fine_overlap} (Sec. 2.3)") if fine_parts else ""
     return {"workload": f"{p.name}: 2D P1 h=1/{p.mesh.cells} ({p.mesh.n_dofs} dofs), k={p.k:g}, "
                         f"{p.parts}x{p.parts} subdomains, overlap {p.overlap}, tau {p.tau}, "
-                        f"FGMRES({p.restart}) to {p.tol:g}, {1 if p.rhs is None else p.rhs.shape[0]} rhs",
+                        f"FGMRES({p.restart}) to {p.tol:g}, {1 if p.rhs is None else p.rhs.shape[0]} rhs{nest}",
             "precision_form": precision, "global_batch": 1 if p.rhs is None else int(p.rhs.shape[0]),
             "l2": "flushed between timed steps (512 MB write)", "parallelism": "replicas"}
 
@@ -213,9 +215,11 @@ class OracleSampler:
     of Omega_i) and a per-iteration part (one FGMRES inner step at the solve's mean Krylov depth: one
     preconditioner apply, one matvec and the modified Gram-Schmidt sweep).  A sample runs the
     per-subdomain work of one subdomain (in turn) and one inner step; the time of a whole solve is
-    then  t_global + n_sub * t_subdomain + iterations * t_iteration."""
+    then  t_global + n_sub * t_subdomain + iterations * t_iteration.  With nested decompositions
+    (Sec. 2.3) a sample adds one fine subdomain's LU, and the solve  n_fine * t_fine_lu  more (the
+    eigenproblems stay on the coarse subdomains)."""
 
-    def __init__(self, p):
+    def __init__(self, p, nested=None):
         import scipy.linalg as sla
 
         from oracle import decomposition as OD
@@ -223,8 +227,9 @@ class OracleSampler:
         from oracle import geneo as OG
         from oracle import solver as OS
         self.p, self.OD, self.OF, self.OG, self.sla = p, OD, OF, OG, sla
+        self.nested = nested
         t0 = time.perf_counter()
-        self.h = OS.setup_problem(p)
+        self.h = OS.setup_problem(p, nested=nested)
         t1 = time.perf_counter()
         self.f = OS.load_vector(p)[0]
         r = OS.solve(self.h, self.f[None, :], p.tol)[0]
@@ -243,18 +248,24 @@ class OracleSampler:
         rng = np.random.default_rng(0)
         self.V = np.linalg.qr(rng.standard_normal((self.h.n, self.depth + 1)))[0].T.copy()
         self.k = 0
-        self.t_sub, self.t_it = [], []
+        self.t_sub, self.t_it, self.t_fine = [], [], []
 
     def step(self):
         p, h, m = self.p, self.h, self.p.mesh
         i = self.k % p.n_sub
         self.k += 1
         t0 = time.perf_counter()
-        sd = h.subs[i]
-        BN, C, w = self.OG.local_pencil(m.xyz, m.elems, p.coeff, m.is_boundary, p.k, sd, h.mu)
+        sd = h.coarse_subs[i]
+        BN, C, w = self.OG.local_pencil(m.xyz, m.elems, p.coeff, m.is_boundary, p.k, sd, h.mu_c)
         self.OG.local_eigen(BN, C, w, p.tau)
-        Bi = h.B.tocsr()[sd.dof][:, sd.dof].toarray()
-        self.sla.lu_factor(Bi)
+        if self.nested is None:
+            Bi = h.B.tocsr()[sd.dof][:, sd.dof].toarray()
+            self.sla.lu_factor(Bi)
+        else:
+            tf = time.perf_counter()
+            fd = h.subs[(self.k - 1) % len(h.subs)]
+            self.sla.lu_factor(h.B.tocsr()[fd.dof][:, fd.dof].toarray())
+            self.t_fine.append(time.perf_counter() - tf)
         t1 = time.perf_counter()
         z = h.precond.apply(self.V[self.depth])
         wv = h.B @ z
@@ -267,7 +278,10 @@ class OracleSampler:
         return t2 - t0
 
     def solve_seconds(self):
-        return self.global_s + self.p.n_sub * statistics.mean(self.t_sub) + self.iters * statistics.mean(self.t_it)
+        t = self.global_s + self.p.n_sub * statistics.mean(self.t_sub) + self.iters * statistics.mean(self.t_it)
+        if self.nested is not None:
+            t += (len(self.h.subs) - self.p.n_sub) * statistics.mean(self.t_fine)
+        return t
 
     def describe(self):
         return (f"{len(self.t_sub)} samples, each: one subdomain's local pencil + eigenproblem + LU "
@@ -311,9 +325,9 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(p, samples=12):
+def cpu_baseline(p, samples=12, nested=None):
     """The oracle as it stands on this host, timed on a bounded sample of the workload (OracleSampler)."""
-    smp = OracleSampler(p)
+    smp = OracleSampler(p, nested)
     for _ in range(samples):
         smp.step()
     s = 1 if p.rhs is None else p.rhs.shape[0]
@@ -346,7 +360,15 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
 
+    fine = args.fine_parts
+    if fine:
+        d_e2f = torch.tensor(W.box_partition(m, fine), dtype=torch.int32, device=dev)
+
     def setup_dev(precision=prec):
+        if fine:  # the nested decompositions of Sec. 2.3: fine boxes inside the coarse subdomains
+            return hk.hk_setup_nested_device(d_xyz, d_el, d_bnd, d_coeff, p.k, d_e2s, p.n_sub, d_e2f, fine ** m.dim,
+                                             p.overlap, args.fine_overlap, p.tau, precision, hk.HK_AS, p.restart,
+                                             p.max_iters, sptr, n_dofs=m.n_dofs)
         return hk.hk_setup_device(d_xyz, d_el, d_bnd, d_coeff, p.k, d_e2s, p.n_sub, p.overlap, p.tau, precision,
                                   hk.HK_TWO_LEVEL, hk.HK_AS, p.restart, p.max_iters, sptr, n_dofs=m.n_dofs)
 
@@ -373,6 +395,19 @@ def run_ours(args, world, rank, local):
     sampler = ClockSampler(local)
     rec = []
     step_ms = []
+    if args.profile_sweeps:
+        # only the local sweeps of 16 right-hand sides: tensor-core, then CUDA-core, twice each
+        h = setup_dev()
+        v16 = np.random.default_rng(1).standard_normal((TC_NRHS, m.n_dofs))
+        for path in (hk.HK_SWEEPS_TENSOR_CORE, hk.HK_SWEEPS_CUDA_CORE):
+            hk.hk_set_sweep_path(h, path)
+            for _ in range(2):
+                hk.hk_apply_precond(h, v16)
+        hk.hk_destroy(h)
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile_sweeps": True, "workload": p.name}), flush=True)
+        return
     if args.profile_run:
         device_step(graphs=False)
         if prec == PRECISIONS["split"]:
@@ -556,7 +591,8 @@ def run_ours(args, world, rank, local):
             "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[args.precision],
-            "data": "synthetic (seeded)", "config": workload_config(p, args.workload, args.precision),
+            "data": "synthetic (seeded)",
+            "config": workload_config(p, args.workload, args.precision, args.fine_parts, args.fine_overlap),
             "iterations": [int(x) for x in its0],
             "setup_phases_ms": dict(zip(["assembly", "decomposition", "local_factors", "eigen", "coarse"],
                                         [round(x, 3) for x in info0["setup_ms"][:5]])),
@@ -565,6 +601,9 @@ def run_ours(args, world, rank, local):
                           "eigen_kernels_gflop": dict(zip(["inertia", "lanczos", "refine"], eig_gflop)),
                           "solve": statistics.mean(step_ms) - statistics.mean(setup_ms)},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+            "local_factors": {"twist_moved": info0["twist_moved"], "pivot_growth": info0["local_growth"][0],
+                              "pivot_growth_middle_twist": info0["local_growth"][1],
+                              "fine_subdomains": info0["fine_subdomains"]},
             "solve_only": {"fp32_precond": so32, "fp64": so64, "split_bf16": sosp},
             "split_bf16_local_sweeps": tc_cmp,
             "kernel_ms_per_launch": per, "roofline": roof, "roofline_apply": roof_apply,
@@ -574,7 +613,8 @@ def run_ours(args, world, rank, local):
             "solve_path": "one CUDA graph per solve (device-side loops)" if info0["graph_solves"] > 0
                           else "host-driven loop"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(p)
+        line["cpu_baseline"] = cpu_baseline(
+            p, nested=(W.box_partition(m, args.fine_parts), args.fine_overlap) if args.fine_parts else None)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -798,6 +838,13 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "split"])
     ap.add_argument("--solve-reps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fine-parts", type=int, default=0,
+                    help="nested decompositions (Sec. 2.3): fine boxes per axis inside the coarse subdomains (0: one "
+                         "decomposition)")
+    ap.add_argument("--fine-overlap", type=int, default=2, help="overlap layers of the fine subdomains")
+    ap.add_argument("--profile-sweeps", action="store_true",
+                    help="only 16-right-hand-side applies, tensor-core then CUDA-core sweeps, twice each (split form; "
+                         "for ncu captures of the sweep kernels)")
     ap.add_argument("--profile-run", action="store_true",
                     help="one warm-up step and one step with the solve's kernels launched one by one, "
                          "nothing else (for ncu captures)")

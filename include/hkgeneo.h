@@ -212,9 +212,11 @@ typedef struct {
                                   HK_SWEEPS_TENSOR_CORE (0 before the first apply) */
   int twist_moved;             /* subdomains whose block factorisation meets at a level other than the
                                   middle one (chosen for a smaller pivot growth, see local_growth) */
-  double local_growth[2];      /* largest pivot growth max|pivot block inverse| x max|B_i| over the local
-                                  factorisations: [0] as factored (twist level chosen per subdomain),
-                                  [1] had every subdomain been factored towards its middle level */
+  double local_growth[2];      /* largest pivot growth ||pivot block inverse||_inf x ||B_i||_inf over the
+                                  local factorisations: [0] as factored (a subdomain whose growth towards
+                                  its middle level exceeds 1000 and 50x the median is factored towards
+                                  another level), [1] had every subdomain been factored towards its middle
+                                  level */
   int fine_subdomains;         /* nested decompositions (hk_setup_nested): number of fine subdomains
                                   (sum_i Q_i), else 0; the local solves, max_level, twist_moved,
                                   local_growth, tc_record_bytes and last_sweeps then refer to them */

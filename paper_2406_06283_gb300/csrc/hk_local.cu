@@ -51,8 +51,8 @@ long long factor_elems(const int* lp, int L, int M) {
 // coupling products of its already eliminated neighbours (G_{j-1} above, H_{j+1} below),
 // its inverse, and its own coupling product (G_j = X^{-1} U_j towards the middle from the
 // top, H_j = X^{-1} L_j from the bottom).
-// gout (or NULL) receives max |X^{-1}| of the level (inf where the inverse is not finite): the growth of
-// the level's pivot block, from which the twist level is chosen.
+// gout (or NULL) receives ||X^{-1}||_inf of the level, its largest absolute row sum (inf where the inverse
+// is not finite): the growth of the level's pivot block, from which the twist level is chosen.
 __device__ void twisted_level(int j, int L, int M, const int* lp, const long long* fo, const int* lr,
                               const int* lcntI, const int* lcol, const double* lval, int off, long long coff,
                               double* F, double* S, int s_in_smem, int* piv, double* red_v, int* red_i,
@@ -85,8 +85,9 @@ __device__ void twisted_level(int j, int L, int M, const int* lp, const long lon
   if (gout) {
     __syncthreads();
     double g = 0;
-    for (int e = tid; e < b * b; e += T) {
-      double a = fabs(X[e]);
+    for (int r = tid; r < b; r += T) {
+      double a = 0;
+      for (int c = 0; c < b; ++c) a += fabs(X[r * b + c]);
       g = a <= 1e300 ? fmax(g, a) : INFINITY;
     }
     for (int o = 16; o > 0; o >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
@@ -125,13 +126,21 @@ __device__ void twisted_level(int j, int L, int M, const int* lp, const long lon
   __syncthreads();
 }
 
-// max |B_i| entry of subdomain s (the scale of the singularity test and of the growth measure), over the CTA.
+// max |B_i| entry of subdomain s (rows = 0: the scale of the singularity test), or ||B_i||_inf, its largest
+// absolute row sum (rows = 1: the scale of the growth measure), over the CTA.
 __device__ double block_scale(int nI, int off, long long coff, const int* lr, const int* lcntI, const double* lval,
-                              double* red_v) {
+                              double* red_v, int rows = 0) {
   int tid = threadIdx.x, T = blockDim.x;
   double mx = 0;
-  for (int a = tid; a < nI; a += T)
-    for (int q = 0; q < lcntI[off + a]; ++q) mx = fmax(mx, fabs(lval[coff + lr[a] + q]));
+  for (int a = tid; a < nI; a += T) {
+    double rs = 0;
+    for (int q = 0; q < lcntI[off + a]; ++q) {
+      double v = fabs(lval[coff + lr[a] + q]);
+      mx = rows ? mx : fmax(mx, v);
+      rs += v;
+    }
+    if (rows) mx = fmax(mx, rs);
+  }
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((tid & 31) == 0) red_v[tid >> 5] = mx;
   __syncthreads();
@@ -142,12 +151,14 @@ __device__ double block_scale(int nI, int off, long long coff, const int* lr, co
 }
 
 // fo: per subdomain, L + 1 factor offsets (elements from the start of the factor array); twist: the
-// level M each subdomain is factored towards.
+// level M each subdomain is factored towards.  gout (or NULL): per level max |pivot block inverse|
+// (indexed like the level pointers), gscale: per subdomain max |B_i|.
 __global__ void k_block_lu(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
                            const int* __restrict__ levptr, const int* __restrict__ lrow,
                            const int* __restrict__ lcntI, const int* __restrict__ lcol,
                            const double* __restrict__ lval, const long long* __restrict__ lvfo,
-                           const int* __restrict__ twist, double* F, int s_in_smem, DevStatus* st) {
+                           const int* __restrict__ twist, double* F, int s_in_smem, DevStatus* st, double* gout,
+                           double* gscale) {
   extern __shared__ double smem[];
   __shared__ int piv[HK_MAXB];
   __shared__ double red_v[32];
@@ -161,25 +172,27 @@ __global__ void k_block_lu(const int* __restrict__ sub_info, const long long* __
   const int* lr = lrow + off + s;
   const long long* fo = lvfo + loff;
   double scale = block_scale(nI, off, coff, lr, lcntI, lval, red_v);
-  if (tid == 0) minpiv = 1e300;
+  double rscale = gscale ? block_scale(nI, off, coff, lr, lcntI, lval, red_v, 1) : 0.0;
+  if (tid == 0) {
+    minpiv = 1e300;
+    if (gscale) gscale[s] = rscale;
+  }
   __syncthreads();
   int M = twist[s];
+  double* g = gout ? gout + loff : nullptr;
   for (int j = 0; j < M; ++j)
-    twisted_level(j, L, M, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv,
-                  nullptr);
+    twisted_level(j, L, M, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv, g);
   for (int j = L - 1; j > M; --j)
-    twisted_level(j, L, M, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv,
-                  nullptr);
-  twisted_level(M, L, M, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv,
-                nullptr);
+    twisted_level(j, L, M, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv, g);
+  twisted_level(M, L, M, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv, g);
   if (tid == 0 && !(minpiv > 1e-10 * scale)) dev_fail(st, HK_SINGULAR_LOCAL, s, minpiv / scale);
 }
 
 // Growth pass for the choice of the twist level.  Both one-sided block eliminations of B_i over all
 // levels: from the top (the factorisation towards M = L - 1: S_0 = D_0, S_j = D_j - L_j S_{j-1}^{-1} U_{j-1})
 // and from the bottom (towards M = 0: T_{L-1} = D_{L-1}, T_j = D_j - U_j T_{j+1}^{-1} L_{j+1}), each into its
-// own scratch factor array, with max |S_j^{-1}| into gtop and max |T_j^{-1}| into gbot per level and
-// max |B_i| into gscale.  A twisted factorisation towards M uses S_j for j < M and T_j for j > M; its middle
+// own scratch factor array, with ||S_j^{-1}||_inf into gtop and ||T_j^{-1}||_inf into gbot per level and
+// ||B_i||_inf into gscale.  A twisted factorisation towards M uses S_j for j < M and T_j for j > M; its middle
 // block Sigma_M has Sigma_M^{-1} = (B_i^{-1})_{MM}, bounded by B_i^{-1} whatever M is.
 __global__ void k_chain_growth(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
                                const int* __restrict__ levptr, const int* __restrict__ lrow,
@@ -198,7 +211,7 @@ __global__ void k_chain_growth(const int* __restrict__ sub_info, const long long
   long long coff = sub_off[3 * s + 1];
   const int* lp = levptr + loff;
   const int* lr = lrow + off + s;
-  double scale = block_scale(nI, off, coff, lr, lcntI, lval, red_v);
+  double scale = block_scale(nI, off, coff, lr, lcntI, lval, red_v, 1);
   if (tid == 0) {
     minpiv = 1e300;
     gscale[s] = scale;
@@ -1248,144 +1261,44 @@ hk_status build_apply_z(hk_handle* h) {
   return HK_OK;
 }
 
-// Host work, sizes and allocations of the local factorisation, in three parts.
-//   begin: the growth pass (both one-sided block eliminations of every B_i) on the handle's auxiliary
-//     stream, where it overlaps the eigenproblems;
-//   mid: the twist level of every subdomain from the growth pass, the factor and record tables, then the
-//     factor kernels (block LU, level records) on the auxiliary stream, where they overlap the coarse
-//     phase;
+// Host part of the local factorisation:
+//   begin: the factor and record tables with every subdomain factored towards its middle level, then the
+//     factor kernels (block LU, which also records ||pivot block inverse||_inf of every level, and the
+//     level records) on the handle's auxiliary stream, where they overlap the eigenproblems;
+//   mid: the growth of each factorisation (below; the middle block is never the problem: Sigma_M^{-1} is a
+//     diagonal block of B_i^{-1}).  A subdomain whose growth is far above the others' has a nearly singular
+//     leading (or trailing) level block and is factored towards another level:
+//     both one-sided block eliminations over all levels (k_chain_growth) give the growth
+//     G(M) = max(max_{j<M} g_top[j], max_{j>M} g_bot[j]) of every twist level, and the choice is the M
+//     nearest the middle (the shortest dependent chain of the apply) with G(M) <= 2 min G.  The tables
+//     and factors are then rebuilt (on the auxiliary stream again, beside the coarse phase);
 //   end: joins them.
-// Twist level.  G(M) = max(max_{j<M} g_top[j], max_{j>M} g_bot[j]) (g = max |pivot block inverse| x
-// max |B_i|) is the growth of the factorisation towards M; the middle block never adds to it.  The
-// choice is the M nearest the middle level (the shortest dependent chain of the apply) among those
-// with G(M) <= 2 min G.
-hk_status phase_local_factors_begin(hk_handle* h) {
-  cudaStream_t st = h->stream;
-  int ns = h->n_sub;
-  std::vector<int>& lev = h->lev_host;
-  lev.assign(h->I_total + ns, 0);
-  HK_CUDA(cudaMemcpyAsync(lev.data(), h->d_lev, sizeof(int) * lev.size(), cudaMemcpyDeviceToHost, st));
-  HK_CUDA(cudaStreamSynchronize(st));
-  h->max_L = 0;
-  for (int s = 0; s < ns; ++s) {
-    Sub& u = h->subs[s];
-    h->max_L = std::max(h->max_L, u.L);
-    u.M = twist_mid(u.L);
-  }
-  HK_TRY(upload_sub_info(h));
-  if (h->p.levels == HK_COARSE_ONLY) return HK_OK;
-  {
-    unsigned long long* d_cnt = nullptr;
-    HK_TRY(dalloc(h, &d_cnt, 1));
-    k_count_lower<<<ns, 128, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
-                                      d_cnt); HK_COUNT_LAUNCH();
-    unsigned long long c = 0;
-    HK_CUDA(cudaMemcpyAsync(&c, d_cnt, sizeof(c), cudaMemcpyDeviceToHost, st));
-    HK_CUDA(cudaStreamSynchronize(st));
-    h->lower_nnz = (long long)c;
-    dfree(h, d_cnt);
-  }
-  // scratch factors of the two one-sided eliminations and their per-level offsets
-  std::vector<long long> fot(h->I_total + ns, 0), fob(h->I_total + ns, 0);
-  long long tt = 0, tb = 0;
-  for (int s = 0; s < ns; ++s) {
-    const Sub& u = h->subs[s];
-    const int* lp = &lev[u.lev_off];
-    for (int j = 0; j < u.L; ++j) {
-      long long b = lp[j + 1] - lp[j];
-      fot[u.lev_off + j] = tt;
-      fob[u.lev_off + j] = tb;
-      tt += pad4(b * b) + pad4(b * coupling_cols(lp, u.L, u.L - 1, j));
-      tb += pad4(b * b) + pad4(b * coupling_cols(lp, u.L, 0, j));
-    }
-  }
-  HK_TRY(dalloc(h, &h->d_gF, (size_t)(tt + tb)));
-  HK_TRY(dalloc(h, &h->d_gfo, fot.size() + fob.size()));
-  HK_TRY(dalloc(h, &h->d_gval, 2 * lev.size() + (size_t)ns));
-  HK_CUDA(cudaMemcpyAsync(h->d_gfo, fot.data(), sizeof(long long) * fot.size(), cudaMemcpyHostToDevice, st));
-  HK_CUDA(cudaMemcpyAsync(h->d_gfo + fot.size(), fob.data(), sizeof(long long) * fob.size(), cudaMemcpyHostToDevice,
-                          st));
-  size_t shm = sizeof(double) * (size_t)h->max_level * h->max_level;
-  int s_in_smem = shm <= 200 * 1024;
-  if (!s_in_smem) shm = 0;
-  HK_TRY(hk_allow_smem(k_block_lu));
-  HK_TRY(hk_allow_smem(k_chain_growth));
-  // the auxiliary stream starts after everything above (allocations, memsets, table upload)
-  if (!h->aux_stream) HK_CUDA(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
-  if (!h->ev_lf) HK_CUDA(cudaEventCreateWithFlags(&h->ev_lf, cudaEventDisableTiming));
-  if (!h->co_stream) {
-    // the apply's coarse branch: short kernels that should not queue behind the local sweeps' CTAs
-    int lo = 0, hi = 0;
-    HK_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-    HK_CUDA(cudaStreamCreateWithPriority(&h->co_stream, cudaStreamNonBlocking, hi));
-  }
-  if (!h->ev_fork) HK_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-  if (!h->ev_join) HK_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
-  HK_CUDA(cudaEventRecord(h->ev_lf, st));
-  HK_CUDA(cudaStreamWaitEvent(h->aux_stream, h->ev_lf, 0));
-  double* gv = h->d_gval;
-  k_chain_growth<<<ns, 256, shm, h->aux_stream>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI,
-                                                  h->d_lcol, h->d_lvalB, h->d_gfo, h->d_gfo + fot.size(), h->d_gF,
-                                                  h->d_gF + tt, s_in_smem, gv, gv + lev.size(),
-                                                  gv + 2 * lev.size());
-  HK_COUNT_LAUNCH();
-  HK_LAUNCH_CHECK();
-  HK_CUDA(cudaEventRecord(h->ev_lf, h->aux_stream));
-  h->lf_stage = 1;
-  return HK_OK;
-}
+// Growth measure: max over the pivot blocks X of ||X^{-1}||_inf ||B_i||_inf.  The apply's own error is of
+// the size of cond(B_i) u, so growth matters where it exceeds the conditioning of B_i, which an
+// ill-conditioned (near-resonant) local problem can have as well; measured on the h = 1/256, k = 50
+// checkerboard workload: median 82, largest 598 (never above 0.2 cond(B_i)); on the h = 1/512, k = 100
+// layered one: median 22, and 9.5e3 = 3.65 cond(B_i) on the subdomains whose leading level block is nearly
+// singular.  A factorisation is refactored when its growth exceeds both HK_GROWTH_OK and HK_GROWTH_REL
+// times the median over the operator's subdomains.
+#define HK_GROWTH_OK 1000.0
+#define HK_GROWTH_REL 50.0
 
-hk_status phase_local_factors_mid(hk_handle* h) {
-  if (h->lf_stage != 1) return HK_OK;
-  h->lf_stage = 2;
+// Tables, allocations and factor kernels for the subdomains' current twist levels (Sub::M).
+static hk_status factors_launch(hk_handle* h, bool growth) {
   cudaStream_t st = h->stream;
   int ns = h->n_sub;
   const std::vector<int>& lev = h->lev_host;
-  // growth pass results, then the twist levels
-  std::vector<double> g(2 * lev.size() + ns);
-  HK_CUDA(cudaEventSynchronize(h->ev_lf));
-  HK_CUDA(cudaMemcpy(g.data(), h->d_gval, sizeof(double) * g.size(), cudaMemcpyDeviceToHost));
-  dfree(h, h->d_gF);
-  dfree(h, h->d_gfo);
-  dfree(h, h->d_gval);
-  h->d_gF = nullptr;
-  h->d_gfo = nullptr;
-  h->d_gval = nullptr;
-  const double* gt = g.data();
-  const double* gb = g.data() + lev.size();
-  const double* gs = g.data() + 2 * lev.size();
-  h->growth_twist = 0;
-  h->growth_mid = 0;
-  h->twist_moved = 0;
   std::vector<int> twist(ns);
   long long fo = 0;
   for (int s = 0; s < ns; ++s) {
     Sub& u = h->subs[s];
-    int L = u.L, mid = twist_mid(L);
-    const double* a = gt + u.lev_off;
-    const double* b = gb + u.lev_off;
-    std::vector<double> pre(L + 1, 0), suf(L + 1, 0);  // pre[M] = max_{j<M} a_j, suf[M] = max_{j>M} b_j
-    for (int j = 0; j < L; ++j) pre[j + 1] = std::max(pre[j], a[j]);
-    for (int j = L - 1; j > 0; --j) suf[j - 1] = std::max(suf[j], b[j]);
-    double best = 1e308;
-    for (int M = 0; M < L; ++M) best = std::min(best, std::max(pre[M], suf[M]));
-    int choice = mid;
-    for (int d = 0; d < L; ++d) {  // nearest the middle first
-      int c0 = mid - d, c1 = mid + d;
-      if (c0 >= 0 && std::max(pre[c0], suf[c0]) <= 2 * best) { choice = c0; break; }
-      if (c1 < L && std::max(pre[c1], suf[c1]) <= 2 * best) { choice = c1; break; }
-    }
-    u.M = choice;
-    twist[s] = choice;
-    h->growth_twist = std::max(h->growth_twist, std::max(pre[choice], suf[choice]) * gs[s]);
-    h->growth_mid = std::max(h->growth_mid, std::max(pre[mid], suf[mid]) * gs[s]);
-    h->twist_moved += choice != mid;
+    twist[s] = u.M;
     u.f_off = fo;
     fo += factor_elems(&lev[u.lev_off], u.L, u.M);
   }
   h->f_total = fo;
   HK_TRY(upload_sub_info(h));
-  HK_TRY(dalloc(h, &h->d_twist, (size_t)ns));
+  if (!h->d_twist) HK_TRY(dalloc(h, &h->d_twist, (size_t)ns));
   HK_CUDA(cudaMemcpyAsync(h->d_twist, twist.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
   // level records for the apply, in the arithmetic type of the precision form
   size_t esz = precond_f32(h->p) ? 4 : 8;
@@ -1434,6 +1347,7 @@ hk_status phase_local_factors_mid(hk_handle* h) {
   HK_TRY(dalloc(h, &h->d_pack, cur));
   HK_CUDA(cudaMemcpyAsync(h->d_lvtab, tab.data(), sizeof(long long) * tab.size(), cudaMemcpyHostToDevice, st));
   HK_CUDA(cudaMemcpyAsync(h->d_lvfo, lvfo.data(), sizeof(long long) * lvfo.size(), cudaMemcpyHostToDevice, st));
+  if (growth) HK_TRY(dalloc(h, &h->d_gval, lev.size() + (size_t)ns));
   size_t shm = sizeof(double) * (size_t)h->max_level * h->max_level;
   int s_in_smem = shm <= 200 * 1024;
   if (!s_in_smem) shm = 0;
@@ -1442,7 +1356,8 @@ hk_status phase_local_factors_mid(hk_handle* h) {
   HK_CUDA(cudaStreamWaitEvent(h->aux_stream, h->ev_lf, 0));
   cudaStream_t ax = h->aux_stream;
   k_block_lu<<<ns, 256, shm, ax>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
-                                   h->d_lvalB, h->d_lvfo, h->d_twist, h->d_F64, s_in_smem, h->d_status);
+                                   h->d_lvalB, h->d_lvfo, h->d_twist, h->d_F64, s_in_smem, h->d_status,
+                                   growth ? h->d_gval : nullptr, growth ? h->d_gval + lev.size() : nullptr);
   HK_COUNT_LAUNCH();
   if (esz == 4)
     k_pack_levels<float><<<ns, 256, 0, ax>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI,
@@ -1458,6 +1373,169 @@ hk_status phase_local_factors_mid(hk_handle* h) {
   HK_CUDA(cudaEventRecord(h->ev_lf, ax));
   h->lf_pending = true;
   return HK_OK;
+}
+
+// Frees what factors_launch allocated (after its kernels have finished).
+static void factors_free(hk_handle* h) {
+  void* fr[] = {h->d_F64, h->d_lvtab, h->d_lvfo, h->d_pack, h->d_pack_tc, h->d_lvtab_tc, h->d_tc_prow};
+  for (void* p : fr)
+    if (p) dfree(h, p);
+  h->d_F64 = nullptr;
+  h->d_lvtab = nullptr;
+  h->d_lvfo = nullptr;
+  h->d_pack = nullptr;
+  h->d_pack_tc = nullptr;
+  h->d_lvtab_tc = nullptr;
+  h->d_tc_prow = nullptr;
+  h->tc_ok = false;
+}
+
+hk_status phase_local_factors_begin(hk_handle* h) {
+  cudaStream_t st = h->stream;
+  int ns = h->n_sub;
+  std::vector<int>& lev = h->lev_host;
+  lev.assign(h->I_total + ns, 0);
+  HK_CUDA(cudaMemcpyAsync(lev.data(), h->d_lev, sizeof(int) * lev.size(), cudaMemcpyDeviceToHost, st));
+  HK_CUDA(cudaStreamSynchronize(st));
+  h->max_L = 0;
+  for (int s = 0; s < ns; ++s) {
+    Sub& u = h->subs[s];
+    h->max_L = std::max(h->max_L, u.L);
+    u.M = twist_mid(u.L);
+  }
+  HK_TRY(upload_sub_info(h));
+  if (h->p.levels == HK_COARSE_ONLY) return HK_OK;
+  {
+    unsigned long long* d_cnt = nullptr;
+    HK_TRY(dalloc(h, &d_cnt, 1));
+    k_count_lower<<<ns, 128, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
+                                      d_cnt); HK_COUNT_LAUNCH();
+    unsigned long long c = 0;
+    HK_CUDA(cudaMemcpyAsync(&c, d_cnt, sizeof(c), cudaMemcpyDeviceToHost, st));
+    HK_CUDA(cudaStreamSynchronize(st));
+    h->lower_nnz = (long long)c;
+    dfree(h, d_cnt);
+  }
+  HK_TRY(hk_allow_smem(k_block_lu));
+  HK_TRY(hk_allow_smem(k_chain_growth));
+  if (!h->aux_stream) HK_CUDA(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
+  if (!h->ev_lf) HK_CUDA(cudaEventCreateWithFlags(&h->ev_lf, cudaEventDisableTiming));
+  if (!h->co_stream) {
+    // the apply's coarse branch: short kernels that should not queue behind the local sweeps' CTAs
+    int lo = 0, hi = 0;
+    HK_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    HK_CUDA(cudaStreamCreateWithPriority(&h->co_stream, cudaStreamNonBlocking, hi));
+  }
+  if (!h->ev_fork) HK_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  if (!h->ev_join) HK_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  HK_TRY(factors_launch(h, true));
+  h->lf_stage = 1;
+  return HK_OK;
+}
+
+hk_status phase_local_factors_mid(hk_handle* h) {
+  if (h->lf_stage != 1) return HK_OK;
+  h->lf_stage = 2;
+  cudaStream_t st = h->stream;
+  int ns = h->n_sub;
+  const std::vector<int>& lev = h->lev_host;
+  // growth of the factorisations towards the middle levels
+  std::vector<double> g(lev.size() + ns);
+  HK_CUDA(cudaEventSynchronize(h->ev_lf));
+  HK_CUDA(cudaMemcpy(g.data(), h->d_gval, sizeof(double) * g.size(), cudaMemcpyDeviceToHost));
+  dfree(h, h->d_gval);
+  h->d_gval = nullptr;
+  const double* gs = g.data() + lev.size();
+  std::vector<double> gmid(ns, 0.0);
+  std::vector<int> bad;
+  h->growth_mid = 0;
+  for (int s = 0; s < ns; ++s) {
+    const Sub& u = h->subs[s];
+    double m = 0;
+    for (int j = 0; j < u.L; ++j)
+      if (j != u.M) m = std::max(m, g[u.lev_off + j] <= 1e300 ? g[u.lev_off + j] : INFINITY);
+    gmid[s] = m * gs[s];
+    h->growth_mid = std::max(h->growth_mid, gmid[s]);
+  }
+  std::vector<double> srt(gmid);
+  std::nth_element(srt.begin(), srt.begin() + ns / 2, srt.end());
+  double limit = std::max(HK_GROWTH_OK, HK_GROWTH_REL * srt[ns / 2]);
+  for (int s = 0; s < ns; ++s)
+    if (!(gmid[s] <= limit)) bad.push_back(s);
+  h->growth_twist = h->growth_mid;
+  h->twist_moved = 0;
+  if (bad.empty()) return HK_OK;  // the factors towards the middle levels stand
+  // growth pass: both one-sided eliminations of every subdomain, into scratch factors
+  factors_free(h);
+  std::vector<long long> fot(h->I_total + ns, 0), fob(h->I_total + ns, 0);
+  long long tt = 0, tb = 0;
+  for (int s = 0; s < ns; ++s) {
+    const Sub& u = h->subs[s];
+    const int* lp = &lev[u.lev_off];
+    for (int j = 0; j < u.L; ++j) {
+      long long b = lp[j + 1] - lp[j];
+      fot[u.lev_off + j] = tt;
+      fob[u.lev_off + j] = tb;
+      tt += pad4(b * b) + pad4(b * coupling_cols(lp, u.L, u.L - 1, j));
+      tb += pad4(b * b) + pad4(b * coupling_cols(lp, u.L, 0, j));
+    }
+  }
+  HK_TRY(dalloc(h, &h->d_gF, (size_t)(tt + tb)));
+  HK_TRY(dalloc(h, &h->d_gfo, fot.size() + fob.size()));
+  HK_TRY(dalloc(h, &h->d_gval, 2 * lev.size() + (size_t)ns));
+  HK_CUDA(cudaMemcpyAsync(h->d_gfo, fot.data(), sizeof(long long) * fot.size(), cudaMemcpyHostToDevice, st));
+  HK_CUDA(cudaMemcpyAsync(h->d_gfo + fot.size(), fob.data(), sizeof(long long) * fob.size(), cudaMemcpyHostToDevice,
+                          st));
+  size_t shm = sizeof(double) * (size_t)h->max_level * h->max_level;
+  int s_in_smem = shm <= 200 * 1024;
+  if (!s_in_smem) shm = 0;
+  double* gv = h->d_gval;
+  k_chain_growth<<<ns, 256, shm, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
+                                       h->d_lvalB, h->d_gfo, h->d_gfo + fot.size(), h->d_gF, h->d_gF + tt, s_in_smem,
+                                       gv, gv + lev.size(), gv + 2 * lev.size());
+  HK_COUNT_LAUNCH();
+  HK_LAUNCH_CHECK();
+  std::vector<double> gg(2 * lev.size() + ns);
+  HK_CUDA(cudaMemcpyAsync(gg.data(), gv, sizeof(double) * gg.size(), cudaMemcpyDeviceToHost, st));
+  HK_CUDA(cudaStreamSynchronize(st));
+  dfree(h, h->d_gF);
+  dfree(h, h->d_gfo);
+  dfree(h, h->d_gval);
+  h->d_gF = nullptr;
+  h->d_gfo = nullptr;
+  h->d_gval = nullptr;
+  const double* gt = gg.data();
+  const double* gb = gg.data() + lev.size();
+  const double* gsc = gg.data() + 2 * lev.size();
+  h->growth_twist = 0;
+  std::vector<char> isbad(ns, 0);
+  for (int s : bad) isbad[s] = 1;
+  for (int s = 0; s < ns; ++s) {
+    if (!isbad[s]) {
+      h->growth_twist = std::max(h->growth_twist, gmid[s]);
+      continue;
+    }
+    Sub& u = h->subs[s];
+    int L = u.L, mid = twist_mid(L);
+    const double* a = gt + u.lev_off;
+    const double* b = gb + u.lev_off;
+    auto fin = [](double x) { return x <= 1e300 ? x : INFINITY; };
+    std::vector<double> pre(L + 1, 0), suf(L + 1, 0);  // pre[M] = max_{j<M} a_j, suf[M] = max_{j>M} b_j
+    for (int j = 0; j < L; ++j) pre[j + 1] = std::max(pre[j], fin(a[j]));
+    for (int j = L - 1; j > 0; --j) suf[j - 1] = std::max(suf[j], fin(b[j]));
+    double best = INFINITY;
+    for (int M = 0; M < L; ++M) best = std::min(best, std::max(pre[M], suf[M]));
+    int choice = mid;
+    for (int d = 0; d < L; ++d) {  // nearest the middle first
+      int c0 = mid - d, c1 = mid + d;
+      if (c0 >= 0 && std::max(pre[c0], suf[c0]) <= 2 * best) { choice = c0; break; }
+      if (c1 < L && std::max(pre[c1], suf[c1]) <= 2 * best) { choice = c1; break; }
+    }
+    u.M = choice;
+    h->twist_moved += choice != mid;
+    h->growth_twist = std::max(h->growth_twist, std::max(pre[choice], suf[choice]) * gsc[s]);
+  }
+  return factors_launch(h, false);
 }
 
 // Joins the factor kernels into the setup stream, checks them, frees the FP64 factors.

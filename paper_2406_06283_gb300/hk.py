@@ -239,6 +239,23 @@ def hk_setup_device(xyz_dev, elems_dev, is_boundary_dev, elem_coeff_dev, k, elem
     return Handle(out, n, int(max_iters))
 
 
+def hk_setup_nested_device(xyz_dev, elems_dev, is_boundary_dev, elem_coeff_dev, k, elem_to_sub_dev, n_sub,
+                           elem_to_fine_dev, n_fine_labels, overlap=2, fine_overlap=1, tau=0.5, precision=HK_FP64,
+                           weighting=HK_AS, restart=50, max_iters=1000, stream=None, n_dofs=None) -> Handle:
+    """hk_setup_nested_device from device-resident torch tensors (as hk_setup_device, plus int32 fine labels)."""
+    mesh = hk_mesh(int(xyz_dev.shape[1]), int(xyz_dev.shape[0]), C.cast(_P(xyz_dev.data_ptr()), C.POINTER(C.c_double)),
+                   int(elems_dev.shape[0]), C.cast(_P(elems_dev.data_ptr()), C.POINTER(C.c_int32)),
+                   C.cast(_P(is_boundary_dev.data_ptr()), C.POINTER(C.c_uint8)))
+    prm = hk_params(int(n_sub), C.cast(_P(elem_to_sub_dev.data_ptr()), C.POINTER(C.c_int32)), int(overlap), float(tau),
+                    int(precision), HK_TWO_LEVEL, int(weighting), int(restart), int(max_iters))
+    out = _P()
+    _check(lib().hk_setup_nested_device(C.byref(mesh), _P(elem_coeff_dev.data_ptr()), float(k), C.byref(prm),
+                                        int(n_fine_labels), _P(elem_to_fine_dev.data_ptr()), int(fine_overlap),
+                                        _P(stream or 0), C.byref(out)), "hk_setup_nested_device")
+    n = n_dofs if n_dofs is not None else int((is_boundary_dev == 0).sum().item())
+    return Handle(out, n, int(max_iters))
+
+
 HK_T_NAMES = ("local_apply", "coarse_solve", "scatter", "spmv", "arnoldi", "cycle_end")
 
 
