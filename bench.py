@@ -517,6 +517,7 @@ def run_ours(args, world, rank, local):
         tc_s = out["tensor_core"]["local_apply"] * 1e-6
         out["speedup_local_sweeps"] = out["cuda_core_fp32"]["local_apply"] / out["tensor_core"]["local_apply"]
         out["roofline"] = {"bound": "tensor", "kernel": "k_local_apply_tc", "achieved": flops / tc_s / 1e12,
+                           "traffic": measured_traffic("k_local_apply_tc", f"{args.workload}_split_16rhs"),
                            "peak": BF16_PEAK, "unit": "TFLOP/s", "frac": flops / tc_s / 1e12 / BF16_PEAK,
                            "mma_tflop_per_launch": flops / 1e12, "record_bytes_per_launch": info["tc_record_bytes"],
                            "record_gbs": info["tc_record_bytes"] / tc_s / 1e9,
