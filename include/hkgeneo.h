@@ -214,9 +214,10 @@ typedef struct {
                                   middle one (chosen for a smaller pivot growth, see local_growth) */
   double local_growth[2];      /* largest pivot growth ||pivot block inverse||_inf x ||B_i||_inf over the
                                   local factorisations: [0] as factored (a subdomain whose growth towards
-                                  its middle level exceeds 1000 and 50x the median is factored towards
-                                  another level), [1] had every subdomain been factored towards its middle
-                                  level */
+                                  its middle level exceeds 1000 and 50x the median, or which meets a
+                                  pivot below 1e-10 max|B_i| there, is factored towards another level),
+                                  [1] had every subdomain been factored towards its middle level (inf
+                                  where a level block was singular in floating point) */
   int fine_subdomains;         /* nested decompositions (hk_setup_nested): number of fine subdomains
                                   (sum_i Q_i), else 0; the local solves, max_level, twist_moved,
                                   local_growth, tc_record_bytes and last_sweeps then refer to them */

@@ -158,7 +158,6 @@ __global__ void k_levels(int dim, const double* __restrict__ xyz, const int* __r
     double cm = 1e300;
     for (int a = threadIdx.x; a < nI; a += blockDim.x)
       if (lev[a] < 0) cm = fmin(cm, coord(a));
-    // block min via negated sum trick is wrong; do a proper min reduction
     for (int o = 16; o > 0; o >>= 1) cm = fmin(cm, __shfl_xor_sync(0xffffffffu, cm, o));
     if ((threadIdx.x & 31) == 0) shd[threadIdx.x >> 5] = cm;
     __syncthreads();

@@ -52,13 +52,16 @@ long long factor_elems(const int* lp, int L, int M) {
 // its inverse, and its own coupling product (G_j = X^{-1} U_j towards the middle from the
 // top, H_j = X^{-1} L_j from the bottom).
 // gout (or NULL) receives ||X^{-1}||_inf of the level, its largest absolute row sum (inf where the inverse
-// is not finite): the growth of the level's pivot block, from which the twist level is chosen.
+// is not finite or a pivot is at most `tiny`): the growth of the level's pivot block, from which the twist
+// level is chosen.  *minpiv takes the smallest pivot met.
 __device__ void twisted_level(int j, int L, int M, const int* lp, const long long* fo, const int* lr,
                               const int* lcntI, const int* lcol, const double* lval, int off, long long coff,
                               double* F, double* S, int s_in_smem, int* piv, double* red_v, int* red_i,
-                              double* minpiv, double* gout) {
+                              double* minpiv, double* gout, double tiny) {
+  __shared__ double lvpiv;  // smallest pivot of this level's block
   int tid = threadIdx.x, T = blockDim.x;
   int r0 = lp[j], b = lp[j + 1] - r0;
+  if (tid == 0) lvpiv = 1e300;
   bool up = j > 0 && j <= M;        // eliminated neighbour above (top part or middle)
   bool down = j < L - 1 && j >= M;  // eliminated neighbour below (bottom part or middle)
   int pr0 = j > 0 ? lp[j - 1] : r0, nr0 = lp[j + 1], nr1 = j + 1 < L ? lp[j + 2] : nr0;
@@ -81,7 +84,8 @@ __device__ void twisted_level(int j, int L, int M, const int* lp, const long lon
     X[e] = v;
   }
   __syncthreads();
-  gauss_jordan_inverse(X, b, piv, red_v, red_i, minpiv);
+  gauss_jordan_inverse(X, b, piv, red_v, red_i, &lvpiv);
+  if (tid == 0) *minpiv = fmin(*minpiv, lvpiv);
   if (gout) {
     __syncthreads();
     double g = 0;
@@ -96,7 +100,7 @@ __device__ void twisted_level(int j, int L, int M, const int* lp, const long lon
     if (tid == 0) {
       double m2 = 0;
       for (int w = 0; w < (T >> 5); ++w) m2 = fmax(m2, red_v[w]);
-      gout[j] = m2;
+      gout[j] = lvpiv > tiny ? m2 : INFINITY;  // a pivot at the singularity floor: no usable inverse
     }
     __syncthreads();
   }
@@ -151,8 +155,12 @@ __device__ double block_scale(int nI, int off, long long coff, const int* lr, co
 }
 
 // fo: per subdomain, L + 1 factor offsets (elements from the start of the factor array); twist: the
-// level M each subdomain is factored towards.  gout (or NULL): per level max |pivot block inverse|
-// (indexed like the level pointers), gscale: per subdomain max |B_i|.
+// level M each subdomain is factored towards.  Without gout a pivot below 1e-10 max|B_i| reports
+// HK_SINGULAR_LOCAL.  With gout (the first factorisation, towards the middle levels) nothing is reported:
+// gout receives ||pivot block inverse||_inf per level (indexed like the level pointers; inf for a block
+// with a pivot at that floor), gscale[s] ||B_i||_inf and gscale[n_sub + s] the smallest pivot / max|B_i|,
+// and the host refactors every subdomain whose growth or pivot is out of bounds (the refactorisation
+// then reports a singular B_i).
 __global__ void k_block_lu(const int* __restrict__ sub_info, const long long* __restrict__ sub_off,
                            const int* __restrict__ levptr, const int* __restrict__ lrow,
                            const int* __restrict__ lcntI, const int* __restrict__ lcol,
@@ -180,12 +188,19 @@ __global__ void k_block_lu(const int* __restrict__ sub_info, const long long* __
   __syncthreads();
   int M = twist[s];
   double* g = gout ? gout + loff : nullptr;
+  double tiny = 1e-10 * scale;
   for (int j = 0; j < M; ++j)
-    twisted_level(j, L, M, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv, g);
+    twisted_level(j, L, M, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv, g,
+                  tiny);
   for (int j = L - 1; j > M; --j)
-    twisted_level(j, L, M, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv, g);
-  twisted_level(M, L, M, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv, g);
-  if (tid == 0 && !(minpiv > 1e-10 * scale)) dev_fail(st, HK_SINGULAR_LOCAL, s, minpiv / scale);
+    twisted_level(j, L, M, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv, g,
+                  tiny);
+  twisted_level(M, L, M, lp, fo, lr, lcntI, lcol, lval, off, coff, F, smem, s_in_smem, piv, red_v, red_i, &minpiv, g,
+                tiny);
+  if (tid == 0) {
+    if (gscale) gscale[gridDim.x + s] = minpiv / scale;
+    else if (!(minpiv > tiny)) dev_fail(st, HK_SINGULAR_LOCAL, s, minpiv / scale);
+  }
 }
 
 // Growth pass for the choice of the twist level.  Both one-sided block eliminations of B_i over all
@@ -212,6 +227,7 @@ __global__ void k_chain_growth(const int* __restrict__ sub_info, const long long
   const int* lp = levptr + loff;
   const int* lr = lrow + off + s;
   double scale = block_scale(nI, off, coff, lr, lcntI, lval, red_v, 1);
+  double tiny = 1e-10 * block_scale(nI, off, coff, lr, lcntI, lval, red_v);
   if (tid == 0) {
     minpiv = 1e300;
     gscale[s] = scale;
@@ -220,11 +236,11 @@ __global__ void k_chain_growth(const int* __restrict__ sub_info, const long long
   const long long* ft = fo_top + loff;
   for (int j = 0; j < L; ++j)
     twisted_level(j, L, L - 1, lp, ft, lr, lcntI, lcol, lval, off, coff, Ftop, smem, s_in_smem, piv, red_v, red_i,
-                  &minpiv, gtop + loff);
+                  &minpiv, gtop + loff, tiny);
   const long long* fb = fo_bot + loff;
   for (int j = L - 1; j >= 0; --j)
     twisted_level(j, L, 0, lp, fb, lr, lcntI, lcol, lval, off, coff, Fbot, smem, s_in_smem, piv, red_v, red_i,
-                  &minpiv, gbot + loff);
+                  &minpiv, gbot + loff, tiny);
 }
 
 // Number of couplings L_j (row in level j, column in level j-1) of every subdomain.
@@ -1279,7 +1295,9 @@ hk_status build_apply_z(hk_handle* h) {
 // checkerboard workload: median 82, largest 598 (never above 0.2 cond(B_i)); on the h = 1/512, k = 100
 // layered one: median 22, and 9.5e3 = 3.65 cond(B_i) on the subdomains whose leading level block is nearly
 // singular.  A factorisation is refactored when its growth exceeds both HK_GROWTH_OK and HK_GROWTH_REL
-// times the median over the operator's subdomains.
+// times the median over the operator's subdomains, or when one of its pivots is at the singularity floor
+// (1e-10 max|B_i|: a leading or trailing level block singular in floating point, while B_i may not be);
+// the refactorisation reports HK_SINGULAR_LOCAL if a pivot is still at the floor (B_i itself singular).
 #define HK_GROWTH_OK 1000.0
 #define HK_GROWTH_REL 50.0
 
@@ -1347,7 +1365,7 @@ static hk_status factors_launch(hk_handle* h, bool growth) {
   HK_TRY(dalloc(h, &h->d_pack, cur));
   HK_CUDA(cudaMemcpyAsync(h->d_lvtab, tab.data(), sizeof(long long) * tab.size(), cudaMemcpyHostToDevice, st));
   HK_CUDA(cudaMemcpyAsync(h->d_lvfo, lvfo.data(), sizeof(long long) * lvfo.size(), cudaMemcpyHostToDevice, st));
-  if (growth) HK_TRY(dalloc(h, &h->d_gval, lev.size() + (size_t)ns));
+  if (growth) HK_TRY(dalloc(h, &h->d_gval, lev.size() + 2 * (size_t)ns));
   size_t shm = sizeof(double) * (size_t)h->max_level * h->max_level;
   int s_in_smem = shm <= 200 * 1024;
   if (!s_in_smem) shm = 0;
@@ -1440,12 +1458,13 @@ hk_status phase_local_factors_mid(hk_handle* h) {
   int ns = h->n_sub;
   const std::vector<int>& lev = h->lev_host;
   // growth of the factorisations towards the middle levels
-  std::vector<double> g(lev.size() + ns);
+  std::vector<double> g(lev.size() + 2 * (size_t)ns);
   HK_CUDA(cudaEventSynchronize(h->ev_lf));
   HK_CUDA(cudaMemcpy(g.data(), h->d_gval, sizeof(double) * g.size(), cudaMemcpyDeviceToHost));
   dfree(h, h->d_gval);
   h->d_gval = nullptr;
   const double* gs = g.data() + lev.size();
+  const double* gp = gs + ns;  // smallest pivot / max|B_i|
   std::vector<double> gmid(ns, 0.0);
   std::vector<int> bad;
   h->growth_mid = 0;
@@ -1461,7 +1480,7 @@ hk_status phase_local_factors_mid(hk_handle* h) {
   std::nth_element(srt.begin(), srt.begin() + ns / 2, srt.end());
   double limit = std::max(HK_GROWTH_OK, HK_GROWTH_REL * srt[ns / 2]);
   for (int s = 0; s < ns; ++s)
-    if (!(gmid[s] <= limit)) bad.push_back(s);
+    if (!(gmid[s] <= limit) || !(gp[s] > 1e-10)) bad.push_back(s);
   h->growth_twist = h->growth_mid;
   h->twist_moved = 0;
   if (bad.empty()) return HK_OK;  // the factors towards the middle levels stand

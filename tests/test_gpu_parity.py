@@ -328,6 +328,58 @@ def test_grid_barrier_timeout_is_reported_and_the_handle_recovers():
     hk.hk_destroy(h)
 
 
+def _leading_level_resonance(p, j0_from_mid=2):
+    """k at which the leading level block (levels 0..j0, j0 = middle level - j0_from_mid) of subdomain 0
+    of p, in the factor's level order, is singular: the smallest k^2 of the generalised eigenproblem
+    A_lead x = k^2 S_lead x of the stiffness and mass blocks (Eq. 2.12 restricted to those dofs)."""
+    from oracle import fem
+    h = hk.setup_problem(p)  # the level order depends on the mesh and the partition, not on k
+    sd = hk.hk_get_subdomain(h, 0)
+    hk.hk_destroy(h)
+    dof, lp = sd["dof"], sd["level_ptr"]
+    L = lp.size - 1
+    j0 = (L - 1) // 2 - j0_from_mid
+    m = p.mesh
+    A, S = fem.assemble(m.xyz, m.elems, p.coeff, m.is_boundary)
+    lead = dof[: lp[j0 + 1]]
+    kap = sla.eigh(A[lead][:, lead].toarray(), S[lead][:, lead].toarray(), eigvals_only=True)
+    Ai, Si = A[dof][:, dof].toarray(), S[dof][:, dof].toarray()
+    kap_i = sla.eigh(Ai, Si, eigvals_only=True)
+    return float(np.sqrt(kap[0])), float(np.min(np.abs(kap_i - kap[0])) / kap[0])
+
+
+def test_singular_leading_level_block_moves_the_twist():
+    """A subdomain whose leading level block is singular (in floating point) while B_i is not: k is put
+    on the first resonance of the leading block, levels 0 .. middle - 2, of subdomain 0 (A = 1, h = 1/32,
+    2 x 2 boxes, overlap 2; B_0 itself stays 0.17 away, relatively, from its nearest resonance).  The
+    factorisation towards the middle level meets a pivot at the singularity floor there; the setup must
+    not report HK_SINGULAR_LOCAL but factor that subdomain towards another level, after which the apply
+    and the solve meet the FP64 parity bars (and the FP32 apply its own)."""
+    p = W.small_problem(cells=32, parts=2, k=8.0, overlap=2, checker=0, seed=11)
+    k, gap = _leading_level_resonance(p)
+    assert gap > 0.1
+    p.k = k
+    o = OS.setup_problem(p)
+    v = np.random.default_rng(5).standard_normal((3, o.n))
+    want = np.stack([o.precond.apply(vi) for vi in v])
+    for prec, tol in ((hk.HK_FP64, 1e-10), (hk.HK_FP32_PRECOND, 1e-4)):
+        h = hk.setup_problem(p, precision=prec)
+        info = hk.hk_info(h)
+        assert info["twist_moved"] >= 1
+        assert not (info["local_growth"][1] < 1e12)  # towards the middle level: a singular block
+        assert info["local_growth"][0] < 1e4
+        z = hk.hk_apply_precond(h, v)
+        err = np.linalg.norm(z - want, axis=1) / np.linalg.norm(want, axis=1)
+        assert np.all(err <= tol), err
+        if prec == hk.HK_FP64:
+            f = OS.load_vector(p)
+            got = hk.hk_solve(h, f, p.tol)
+            rng_out = oracle_count_range(o, f[0], p.tol, key=("singular_lead_h32", 0))
+            check_counts("singular_lead_h32", 0, "fp64", got.iters[0], rng_out)
+            assert _rel(got.u[0], rng_out[0].x) <= 1e-7
+        hk.hk_destroy(h)
+
+
 def test_errors_are_reported():
     from oracle import fem
     p = W.small_problem(cells=8, parts=1, k=1.0, overlap=1)
