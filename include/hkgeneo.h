@@ -220,10 +220,15 @@ typedef struct {
                                   where a level block was singular in floating point) */
   int fine_subdomains;         /* nested decompositions (hk_setup_nested): number of fine subdomains
                                   (sum_i Q_i), else 0; the local solves, max_level, twist_moved,
-                                  local_growth, tc_record_bytes and last_sweeps then refer to them */
+                                  local_growth, tc_record_bytes, last_sweeps and levels_merged then
+                                  refer to them */
   int fine_lambda_elems;       /* Lambda over the fine subdomains (Sec. 2.4), else 0 */
   int fine_max_dof;            /* largest |dof(Omega^f_{i,j})|, else 0 */
   long long fine_dof_total;    /* sum of |dof(Omega^f_{i,j})|, else 0 */
+  int levels_merged;           /* level boundaries removed from the local factorisations: where no twist
+                                  level avoids a singular (or outlying) leading or trailing level block,
+                                  the first such level of each one-sided elimination is merged with its
+                                  successor (wider blocks, fewer levels; see max_level) */
 } hk_info_t;
 
 hk_status hk_info(const hk_handle* h, hk_info_t* info);

@@ -562,6 +562,7 @@ extern "C" hk_status hk_info(const hk_handle* h, hk_info_t* info) {
   info->tc_record_bytes = h->tc_ok ? h->tc_bytes : 0;
   info->last_sweeps = h->last_sweeps;
   info->twist_moved = h->twist_moved;
+  info->levels_merged = h->levels_merged;
   info->local_growth[0] = h->growth_twist;
   info->local_growth[1] = h->growth_mid;
   const hk_handle* c = h->child;
@@ -572,6 +573,7 @@ extern "C" hk_status hk_info(const hk_handle* h, hk_info_t* info) {
   if (c) {
     info->max_level = c->max_level;
     info->twist_moved = c->twist_moved;
+    info->levels_merged = c->levels_merged;
     info->local_growth[0] = c->growth_twist;
     info->local_growth[1] = c->growth_mid;
     info->tc_record_bytes = c->tc_ok ? c->tc_bytes : 0;

@@ -265,12 +265,17 @@ __global__ void k_refine(const int* __restrict__ items, const double* __restrict
   double* Fw = F + f_off[it];
   double* X = Xw + x_off[it];                 // p x nO
   double* R = X + (long long)p * nO;          // p x nO
+  double* Mv = R + (long long)p * nO;         // nO x maxrow: the entries of M = B^N - sigma C, formed once
   double* Ps = P + poff[s];
-  // scale for the pivot floor
+  // the entries of M and the scale for the pivot floor
   double mx = 0;
   for (long long e = tid; e < (long long)nO * maxrow; e += T) {
     int a = (int)(e / maxrow), q = (int)(e % maxrow);
-    if (q < ocnt[oo + a]) mx = fmax(mx, fabs(oB[(long long)oo * maxrow + e] - sigma * oC[(long long)oo * maxrow + e]));
+    if (q < ocnt[oo + a]) {
+      double v = oB[(long long)oo * maxrow + e] - sigma * oC[(long long)oo * maxrow + e];
+      Mv[e] = v;
+      mx = fmax(mx, fabs(v));
+    }
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((tid & 31) == 0) red_v[tid >> 5] = mx;
@@ -294,13 +299,13 @@ __global__ void k_refine(const int* __restrict__ items, const double* __restrict
       int qa = e / b, t = e % b;
       int a = r0 + qa;
       long long base = (long long)(oo + a) * maxrow;
+      const double* mr = Mv + (long long)a * maxrow;
       int cnt = min(ocnt[oo + a], maxrow);
       double v = 0;
       for (int q = 0; q < cnt; ++q) {
         int c = ocol[base + q];
-        double mv = oB[base + q] - sigma * oC[base + q];
-        if (c == r0 + t) v += mv;
-        else if (j > 0 && c >= prev_r0 && c < r0) v -= mv * Fw[prev_go + (long long)(c - prev_r0) * b + t];
+        if (c == r0 + t) v += mr[q];
+        else if (j > 0 && c >= prev_r0 && c < r0) v -= mr[q] * Fw[prev_go + (long long)(c - prev_r0) * b + t];
       }
       S[e] = v;
     }
@@ -313,11 +318,12 @@ __global__ void k_refine(const int* __restrict__ items, const double* __restrict
       int qt = e / bn, cc = e % bn;
       int c = r1 + cc;
       long long base = (long long)(oo + c) * maxrow;
+      const double* mr = Mv + (long long)c * maxrow;
       int cnt = min(ocnt[oo + c], maxrow);
       double v = 0;
       for (int q = 0; q < cnt; ++q) {
         int a = ocol[base + q];
-        if (a >= r0 && a < r1) v += S[qt * b + (a - r0)] * (oB[base + q] - sigma * oC[base + q]);
+        if (a >= r0 && a < r1) v += S[qt * b + (a - r0)] * mr[q];
       }
       Fw[go + e] = v;
     }
@@ -347,11 +353,12 @@ __global__ void k_refine(const int* __restrict__ items, const double* __restrict
       for (int e = tid; e < b * p; e += T) {
         int t = e / b, a = r0 + e % b;
         long long base = (long long)(oo + a) * maxrow;
+        const double* mr = Mv + (long long)a * maxrow;
         int cnt = min(ocnt[oo + a], maxrow);
         double acc = R[(long long)t * nO + a];
         for (int q = 0; q < cnt; ++q) {
           int c = ocol[base + q];
-          if (c < r0) acc -= (oB[base + q] - sigma * oC[base + q]) * R[(long long)t * nO + c];
+          if (c < r0) acc -= mr[q] * R[(long long)t * nO + c];
         }
         tv[e] = acc;
       }
@@ -682,7 +689,7 @@ hk_status phase_eigen(hk_handle* h, const uint8_t* d_elem_in) {
         foff.push_back(ftot);
         ftot += fsize[s];
         xoff.push_back(xtot);
-        xtot += 2LL * (t1 - t + HK_GUARD) * oc[s];
+        xtot += 2LL * (t1 - t + HK_GUARD) * oc[s] + (long long)oc[s] * maxrow;
         pmax = std::max(pmax, t1 - t + HK_GUARD);
         t = t1;
       }

@@ -220,6 +220,7 @@ struct hk_handle {
   int* d_twist = nullptr;       // per subdomain: twist level M of its factorisation
   double growth_twist = 0, growth_mid = 0;  // max over subdomains of the pivot growth (chosen M; M = (L-1)/2)
   int twist_moved = 0;          // subdomains whose twist level is not the middle one
+  int levels_merged = 0;        // level boundaries removed where no twist level avoided a singular block
   // nested decompositions (Sec. 2.3): this handle holds the coarse subdomains (eigenproblems, coarse
   // space) and child the fine ones (local solves, a one-level handle that only applies); fine_parent: the
   // coarse subdomain of each fine one

@@ -1298,8 +1298,15 @@ hk_status build_apply_z(hk_handle* h) {
 // times the median over the operator's subdomains, or when one of its pivots is at the singularity floor
 // (1e-10 max|B_i|: a leading or trailing level block singular in floating point, while B_i may not be);
 // the refactorisation reports HK_SINGULAR_LOCAL if a pivot is still at the floor (B_i itself singular).
+// Where even the best twist level leaves a growth HK_MERGE_FACTOR times above that limit (a leading and a
+// trailing level block both singular: on a constant-coefficient strip every band of the same rows is the
+// same matrix), the first offending level of each one-sided elimination is merged with its successor in that
+// elimination (one wider block, so the singular leading or trailing block is never formed) and the levels are
+// scored again, up to HK_MERGE_ROUNDS times.
 #define HK_GROWTH_OK 1000.0
 #define HK_GROWTH_REL 50.0
+#define HK_MERGE_ROUNDS 3    // rounds of level merging for subdomains that no twist level serves
+#define HK_MERGE_FACTOR 20.0 // merge levels where the best twist level's growth is still this far above the limit
 
 // Tables, allocations and factor kernels for the subdomains' current twist levels (Sub::M).
 static hk_status factors_launch(hk_handle* h, bool growth) {
@@ -1451,41 +1458,13 @@ hk_status phase_local_factors_begin(hk_handle* h) {
   return HK_OK;
 }
 
-hk_status phase_local_factors_mid(hk_handle* h) {
-  if (h->lf_stage != 1) return HK_OK;
-  h->lf_stage = 2;
+// Both one-sided block eliminations of every subdomain over its current levels (k_chain_growth), into scratch
+// factors: gg = [||S_j^{-1}||_inf per level | ||T_j^{-1}||_inf per level | ||B_i||_inf per subdomain], the
+// per-level parts indexed like the level pointers.
+static hk_status chain_growth(hk_handle* h, std::vector<double>& gg) {
   cudaStream_t st = h->stream;
   int ns = h->n_sub;
   const std::vector<int>& lev = h->lev_host;
-  // growth of the factorisations towards the middle levels
-  std::vector<double> g(lev.size() + 2 * (size_t)ns);
-  HK_CUDA(cudaEventSynchronize(h->ev_lf));
-  HK_CUDA(cudaMemcpy(g.data(), h->d_gval, sizeof(double) * g.size(), cudaMemcpyDeviceToHost));
-  dfree(h, h->d_gval);
-  h->d_gval = nullptr;
-  const double* gs = g.data() + lev.size();
-  const double* gp = gs + ns;  // smallest pivot / max|B_i|
-  std::vector<double> gmid(ns, 0.0);
-  std::vector<int> bad;
-  h->growth_mid = 0;
-  for (int s = 0; s < ns; ++s) {
-    const Sub& u = h->subs[s];
-    double m = 0;
-    for (int j = 0; j < u.L; ++j)
-      if (j != u.M) m = std::max(m, g[u.lev_off + j] <= 1e300 ? g[u.lev_off + j] : INFINITY);
-    gmid[s] = m * gs[s];
-    h->growth_mid = std::max(h->growth_mid, gmid[s]);
-  }
-  std::vector<double> srt(gmid);
-  std::nth_element(srt.begin(), srt.begin() + ns / 2, srt.end());
-  double limit = std::max(HK_GROWTH_OK, HK_GROWTH_REL * srt[ns / 2]);
-  for (int s = 0; s < ns; ++s)
-    if (!(gmid[s] <= limit) || !(gp[s] > 1e-10)) bad.push_back(s);
-  h->growth_twist = h->growth_mid;
-  h->twist_moved = 0;
-  if (bad.empty()) return HK_OK;  // the factors towards the middle levels stand
-  // growth pass: both one-sided eliminations of every subdomain, into scratch factors
-  factors_free(h);
   std::vector<long long> fot(h->I_total + ns, 0), fob(h->I_total + ns, 0);
   long long tt = 0, tb = 0;
   for (int s = 0; s < ns; ++s) {
@@ -1514,7 +1493,7 @@ hk_status phase_local_factors_mid(hk_handle* h) {
                                        gv, gv + lev.size(), gv + 2 * lev.size());
   HK_COUNT_LAUNCH();
   HK_LAUNCH_CHECK();
-  std::vector<double> gg(2 * lev.size() + ns);
+  gg.assign(2 * lev.size() + ns, 0.0);
   HK_CUDA(cudaMemcpyAsync(gg.data(), gv, sizeof(double) * gg.size(), cudaMemcpyDeviceToHost, st));
   HK_CUDA(cudaStreamSynchronize(st));
   dfree(h, h->d_gF);
@@ -1523,36 +1502,121 @@ hk_status phase_local_factors_mid(hk_handle* h) {
   h->d_gF = nullptr;
   h->d_gfo = nullptr;
   h->d_gval = nullptr;
-  const double* gt = gg.data();
-  const double* gb = gg.data() + lev.size();
-  const double* gsc = gg.data() + 2 * lev.size();
-  h->growth_twist = 0;
-  std::vector<char> isbad(ns, 0);
-  for (int s : bad) isbad[s] = 1;
+  return HK_OK;
+}
+
+hk_status phase_local_factors_mid(hk_handle* h) {
+  if (h->lf_stage != 1) return HK_OK;
+  h->lf_stage = 2;
+  cudaStream_t st = h->stream;
+  int ns = h->n_sub;
+  const std::vector<int>& lev = h->lev_host;
+  // growth of the factorisations towards the middle levels
+  std::vector<double> g(lev.size() + 2 * (size_t)ns);
+  HK_CUDA(cudaEventSynchronize(h->ev_lf));
+  HK_CUDA(cudaMemcpy(g.data(), h->d_gval, sizeof(double) * g.size(), cudaMemcpyDeviceToHost));
+  dfree(h, h->d_gval);
+  h->d_gval = nullptr;
+  const double* gs = g.data() + lev.size();
+  const double* gp = gs + ns;  // smallest pivot / max|B_i|
+  std::vector<double> gmid(ns, 0.0);
+  std::vector<int> bad;
+  h->growth_mid = 0;
   for (int s = 0; s < ns; ++s) {
-    if (!isbad[s]) {
-      h->growth_twist = std::max(h->growth_twist, gmid[s]);
-      continue;
+    const Sub& u = h->subs[s];
+    double m = 0;
+    for (int j = 0; j < u.L; ++j)
+      if (j != u.M) m = std::max(m, g[u.lev_off + j] <= 1e300 ? g[u.lev_off + j] : INFINITY);
+    gmid[s] = m * gs[s];
+    h->growth_mid = std::max(h->growth_mid, gmid[s]);
+  }
+  // the median over the finite growths (a singular level block makes a growth infinite)
+  std::vector<double> srt;
+  for (double x : gmid)
+    if (x <= 1e300) srt.push_back(x);
+  double med = 0;
+  if (!srt.empty()) {
+    std::nth_element(srt.begin(), srt.begin() + srt.size() / 2, srt.end());
+    med = srt[srt.size() / 2];
+  }
+  double limit = std::max(HK_GROWTH_OK, HK_GROWTH_REL * med);
+  for (int s = 0; s < ns; ++s)
+    if (!(gmid[s] <= limit) || !(gp[s] > 1e-10)) bad.push_back(s);
+  h->growth_twist = h->growth_mid;
+  h->twist_moved = 0;
+  h->levels_merged = 0;
+  if (bad.empty()) return HK_OK;  // the factors towards the middle levels stand
+  factors_free(h);
+  std::vector<int>& levm = h->lev_host;
+  std::vector<char> pending(ns, 0);
+  for (int s : bad) pending[s] = 1;
+  h->growth_twist = 0;
+  for (int s = 0; s < ns; ++s)
+    if (!pending[s]) h->growth_twist = std::max(h->growth_twist, gmid[s]);
+  for (int round = 0;; ++round) {
+    std::vector<double> gg;
+    HK_TRY(chain_growth(h, gg));
+    const double* gt = gg.data();
+    const double* gb = gg.data() + lev.size();
+    const double* gsc = gg.data() + 2 * lev.size();
+    bool merged = false;
+    for (int s = 0; s < ns; ++s) {
+      if (!pending[s]) continue;
+      Sub& u = h->subs[s];
+      int L = u.L, mid = twist_mid(L);
+      const double* a = gt + u.lev_off;
+      const double* b = gb + u.lev_off;
+      auto fin = [](double x) { return x <= 1e300 ? x : INFINITY; };
+      std::vector<double> pre(L + 1, 0), suf(L + 1, 0);  // pre[M] = max_{j<M} a_j, suf[M] = max_{j>M} b_j
+      for (int j = 0; j < L; ++j) pre[j + 1] = std::max(pre[j], fin(a[j]));
+      for (int j = L - 1; j > 0; --j) suf[j - 1] = std::max(suf[j], fin(b[j]));
+      double best = INFINITY;
+      for (int M = 0; M < L; ++M) best = std::min(best, std::max(pre[M], suf[M]));
+      double tmerge = HK_MERGE_FACTOR * limit;
+      if (!(best * gsc[s] <= tmerge) && round < HK_MERGE_ROUNDS) {
+        // no twist level avoids a singular (or outlying) one-sided block: merge the first such level of
+        // each chain with its successor in that chain, so that the offending leading block [0, j_t] and
+        // trailing block [j_b, L - 1] are no longer formed, and score the new levels again
+        int jt = -1, jb = -1;
+        for (int j = 0; j < L && jt < 0; ++j)
+          if (!(fin(a[j]) * gsc[s] <= tmerge)) jt = j;
+        for (int j = L - 1; j >= 0 && jb < 0; --j)
+          if (!(fin(b[j]) * gsc[s] <= tmerge)) jb = j;
+        int* lp = &levm[u.lev_off];
+        std::vector<char> drop(L + 1, 0);  // boundary q merges levels q - 1 and q
+        if (jt >= 0 && jt + 1 < L) drop[jt + 1] = 1;
+        if (jb >= 1) drop[jb] = 1;
+        std::vector<int> nl;
+        for (int q = 0; q <= L; ++q)
+          if (!drop[q]) nl.push_back(lp[q]);
+        int wmax = 0;
+        for (size_t q = 0; q + 1 < nl.size(); ++q) wmax = std::max(wmax, nl[q + 1] - nl[q]);
+        if ((int)nl.size() < L + 1 && wmax <= HK_MAXB) {
+          for (size_t q = 0; q < nl.size(); ++q) lp[q] = nl[q];
+          u.L = (int)nl.size() - 1;
+          h->max_level = std::max(h->max_level, wmax);
+          h->levels_merged += L - u.L;
+          merged = true;
+          continue;
+        }
+      }
+      int choice = mid;
+      for (int d = 0; d < L; ++d) {  // nearest the middle first
+        int c0 = mid - d, c1 = mid + d;
+        if (c0 >= 0 && std::max(pre[c0], suf[c0]) <= 2 * best) { choice = c0; break; }
+        if (c1 < L && std::max(pre[c1], suf[c1]) <= 2 * best) { choice = c1; break; }
+      }
+      u.M = choice;
+      pending[s] = 0;
+      h->twist_moved += choice != mid;
+      h->growth_twist = std::max(h->growth_twist, std::max(pre[choice], suf[choice]) * gsc[s]);
     }
-    Sub& u = h->subs[s];
-    int L = u.L, mid = twist_mid(L);
-    const double* a = gt + u.lev_off;
-    const double* b = gb + u.lev_off;
-    auto fin = [](double x) { return x <= 1e300 ? x : INFINITY; };
-    std::vector<double> pre(L + 1, 0), suf(L + 1, 0);  // pre[M] = max_{j<M} a_j, suf[M] = max_{j>M} b_j
-    for (int j = 0; j < L; ++j) pre[j + 1] = std::max(pre[j], fin(a[j]));
-    for (int j = L - 1; j > 0; --j) suf[j - 1] = std::max(suf[j], fin(b[j]));
-    double best = INFINITY;
-    for (int M = 0; M < L; ++M) best = std::min(best, std::max(pre[M], suf[M]));
-    int choice = mid;
-    for (int d = 0; d < L; ++d) {  // nearest the middle first
-      int c0 = mid - d, c1 = mid + d;
-      if (c0 >= 0 && std::max(pre[c0], suf[c0]) <= 2 * best) { choice = c0; break; }
-      if (c1 < L && std::max(pre[c1], suf[c1]) <= 2 * best) { choice = c1; break; }
-    }
-    u.M = choice;
-    h->twist_moved += choice != mid;
-    h->growth_twist = std::max(h->growth_twist, std::max(pre[choice], suf[choice]) * gsc[s]);
+    if (!merged) break;
+    // the merged level pointers and level counts to the device, for the next scoring pass
+    HK_CUDA(cudaMemcpyAsync(h->d_lev, levm.data(), sizeof(int) * levm.size(), cudaMemcpyHostToDevice, st));
+    for (int s = 0; s < ns; ++s)
+      if (pending[s]) h->subs[s].M = twist_mid(h->subs[s].L);
+    HK_TRY(upload_sub_info(h));
   }
   return factors_launch(h, false);
 }

@@ -56,7 +56,7 @@ class hk_info_t(C.Structure):
                 ("eigen_kernel_ms", C.c_double * 4), ("eigen_kernel_gflop", C.c_double * 4),
                 ("tc_record_bytes", C.c_longlong), ("last_sweeps", C.c_int), ("twist_moved", C.c_int),
                 ("local_growth", C.c_double * 2), ("fine_subdomains", C.c_int), ("fine_lambda_elems", C.c_int),
-                ("fine_max_dof", C.c_int), ("fine_dof_total", C.c_longlong)]
+                ("fine_max_dof", C.c_int), ("fine_dof_total", C.c_longlong), ("levels_merged", C.c_int)]
 
 
 class hk_theory_t(C.Structure):

@@ -348,25 +348,19 @@ def _leading_level_resonance(p, j0_from_mid=2):
     return float(np.sqrt(kap[0])), float(np.min(np.abs(kap_i - kap[0])) / kap[0])
 
 
-def test_singular_leading_level_block_moves_the_twist():
-    """A subdomain whose leading level block is singular (in floating point) while B_i is not: k is put
-    on the first resonance of the leading block, levels 0 .. middle - 2, of subdomain 0 (A = 1, h = 1/32,
-    2 x 2 boxes, overlap 2; B_0 itself stays 0.17 away, relatively, from its nearest resonance).  The
-    factorisation towards the middle level meets a pivot at the singularity floor there; the setup must
-    not report HK_SINGULAR_LOCAL but factor that subdomain towards another level, after which the apply
-    and the solve meet the FP64 parity bars (and the FP32 apply its own)."""
-    p = W.small_problem(cells=32, parts=2, k=8.0, overlap=2, checker=0, seed=11)
-    k, gap = _leading_level_resonance(p)
-    assert gap > 0.1
+def _check_resonant_case(p, name, k):
+    """Setup (FP64 and FP32 forms), apply and FP64 solve parity on p at wavenumber k; returns the FP64
+    handle's hk_info."""
     p.k = k
     o = OS.setup_problem(p)
     v = np.random.default_rng(5).standard_normal((3, o.n))
     want = np.stack([o.precond.apply(vi) for vi in v])
+    infos = []
     for prec, tol in ((hk.HK_FP64, 1e-10), (hk.HK_FP32_PRECOND, 1e-4)):
         h = hk.setup_problem(p, precision=prec)
         info = hk.hk_info(h)
-        assert info["twist_moved"] >= 1
-        assert not (info["local_growth"][1] < 1e12)  # towards the middle level: a singular block
+        infos.append(info)
+        assert not (info["local_growth"][1] < 1e12)  # towards the middle levels: a singular block
         assert info["local_growth"][0] < 1e4
         z = hk.hk_apply_precond(h, v)
         err = np.linalg.norm(z - want, axis=1) / np.linalg.norm(want, axis=1)
@@ -374,10 +368,38 @@ def test_singular_leading_level_block_moves_the_twist():
         if prec == hk.HK_FP64:
             f = OS.load_vector(p)
             got = hk.hk_solve(h, f, p.tol)
-            rng_out = oracle_count_range(o, f[0], p.tol, key=("singular_lead_h32", 0))
-            check_counts("singular_lead_h32", 0, "fp64", got.iters[0], rng_out)
+            rng_out = oracle_count_range(o, f[0], p.tol, key=(name, 0))
+            check_counts(name, 0, "fp64", got.iters[0], rng_out)
             assert _rel(got.u[0], rng_out[0].x) <= 1e-7
         hk.hk_destroy(h)
+    return infos[0]
+
+
+def test_singular_leading_level_block_moves_the_twist():
+    """A subdomain whose leading level block is singular (in floating point) while B_i is not: k is put on
+    the first resonance of the leading block, levels 0 .. middle - 2, of subdomain 0 (2 x 2 checkerboard A,
+    h = 1/32, 2 x 2 boxes, overlap 2; B_0 itself stays 0.10 away, relatively, from its nearest resonance).
+    The factorisation towards the middle level meets a pivot at the singularity floor; the setup must not
+    report HK_SINGULAR_LOCAL but factor that subdomain towards a level below the singular block, after
+    which the apply and the solve meet the FP64 parity bars (and the FP32 apply its own)."""
+    p = W.small_problem(cells=32, parts=2, k=8.0, overlap=2, checker=2, seed=11)
+    k, gap = _leading_level_resonance(p)
+    assert gap > 0.05
+    info = _check_resonant_case(p, "singular_lead_h32_checker", k)
+    assert info["twist_moved"] >= 1 and info["levels_merged"] == 0
+
+
+def test_singular_leading_and_trailing_blocks_merge_levels():
+    """The same construction with A = 1: the stencil is translation invariant, so the band of the top rows
+    of subdomain 0 is the same matrix as its leading band and is singular too, and so are the bands of the
+    point-symmetric subdomain 3 (B_0 stays 0.17 away from its nearest resonance).  No twist level avoids
+    both; the setup must merge the offending levels with their neighbours (wider blocks) and then meet the
+    same parity bars."""
+    p = W.small_problem(cells=32, parts=2, k=8.0, overlap=2, checker=0, seed=11)
+    k, gap = _leading_level_resonance(p)
+    assert gap > 0.1
+    info = _check_resonant_case(p, "singular_lead_trail_h32", k)
+    assert info["levels_merged"] >= 2
 
 
 def test_errors_are_reported():
