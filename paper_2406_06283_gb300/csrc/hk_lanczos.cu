@@ -46,6 +46,8 @@ struct OPen {
   const double* B;     // nO x maxrow values of B^N
   const double* C;     // nO x maxrow values of C
   const int* o2i;      // nO: position in the dof level order, -1 on Gamma
+  const float* B32 = nullptr;  // FP32 copies of B and C (the Lanczos kernel's own, formed once per subdomain)
+  const float* C32 = nullptr;
 };
 
 __device__ __forceinline__ OPen open_sub(int s, const int* o_off, const int* O_levptr, const int* O_L, int maxrow,
@@ -122,17 +124,17 @@ __device__ double lz_factor(const OPen& P, double sigma, T* F, T* Ssm, T* sh_inv
       int qa = e / b, t = e - qa * b;
       int a = r0 + qa;
       const int* cl = P.col + (long long)a * P.maxrow;
-      const double* bv = P.B + (long long)a * P.maxrow;
-      const double* cv = P.C + (long long)a * P.maxrow;
+      const float* bv = P.B32 + (long long)a * P.maxrow;
+      const float* cv = P.C32 + (long long)a * P.maxrow;
       int c_n = min(P.cnt[a], P.maxrow);
-      double v = 0;
-      for (int q = 0; q < c_n; ++q) {
+      T v = 0;
+      T sg = (T)sigma;
+      for (int q = 0; q < c_n; ++q) {  // the entry of M formed only where it is used
         int c = cl[q];
-        double mv = bv[q] - sigma * cv[q];
-        if (c == r0 + t) v += mv;
-        else if (j > 0 && c >= prev_r0 && c < r0) v -= mv * (double)F[prev_x + (long long)(c - prev_r0) * b + t];
+        if (c == r0 + t) v += (T)bv[q] - sg * (T)cv[q];
+        else if (j > 0 && c >= prev_r0 && c < r0) v -= ((T)bv[q] - sg * (T)cv[q]) * F[prev_x + (long long)(c - prev_r0) * b + t];
       }
-      S[e] = (T)v;
+      S[e] = v;
     }
     __syncthreads();
     gj_inverse_nopiv<T>(S, b, sh_inv, sh_min);
@@ -144,15 +146,15 @@ __device__ double lz_factor(const OPen& P, double sigma, T* F, T* Ssm, T* sh_inv
       int qt = e / bn, cc = e - qt * bn;
       int c = r1 + cc;
       const int* cl = P.col + (long long)c * P.maxrow;
-      const double* bv = P.B + (long long)c * P.maxrow;
-      const double* cv = P.C + (long long)c * P.maxrow;
+      const float* bv = P.B32 + (long long)c * P.maxrow;
+      const float* cv = P.C32 + (long long)c * P.maxrow;
       int c_n = min(P.cnt[c], P.maxrow);
-      double v = 0;
+      T v = 0;
       for (int q = 0; q < c_n; ++q) {
         int a = cl[q];
-        if (a >= r0 && a < r1) v += (double)S[qt * b + (a - r0)] * (bv[q] - sigma * cv[q]);
+        if (a >= r0 && a < r1) v += S[qt * b + (a - r0)] * ((T)bv[q] - (T)sigma * (T)cv[q]);
       }
-      F[xo + e] = (T)v;
+      F[xo + e] = v;
     }
     __syncthreads();
     prev_x = xo;
@@ -189,13 +191,13 @@ __device__ void lz_solve(const OPen& P, double sigma, const float* __restrict__ 
       int q = e / LZ_P, pc = e - q * LZ_P;
       int a = r0 + q;
       const int* cl = P.col + (long long)a * P.maxrow;
-      const double* bv = P.B + (long long)a * P.maxrow;
-      const double* cv = P.C + (long long)a * P.maxrow;
+      const float* bv = P.B32 + (long long)a * P.maxrow;
+      const float* cv = P.C32 + (long long)a * P.maxrow;
       int c_n = min(P.cnt[a], P.maxrow);
-      float acc = Y[a * LZ_P + pc];
+      float acc = Y[a * LZ_P + pc], sg = (float)sigma;
       for (int q2 = 0; q2 < c_n; ++q2) {
         int c = cl[q2];
-        if (c < r0) acc -= (float)(bv[q2] - sigma * cv[q2]) * Y[c * LZ_P + pc];
+        if (c < r0) acc -= (bv[q2] - sg * cv[q2]) * Y[c * LZ_P + pc];
       }
       tv[e] = acc;
     }
@@ -272,7 +274,7 @@ __device__ void lz_cmul(const OPen& P, const T* Yin, T* Yout) {
   for (int e = threadIdx.x; e < P.nO * LZ_P; e += blockDim.x) {
     int a = e / LZ_P, pc = e - a * LZ_P;
     const int* cl = P.col + (long long)a * P.maxrow;
-    const double* cv = P.C + (long long)a * P.maxrow;
+    const float* cv = P.C32 + (long long)a * P.maxrow;
     int c_n = min(P.cnt[a], P.maxrow);
     T acc = 0;
     for (int q = 0; q < c_n; ++q) acc += (T)cv[q] * Yin[cl[q] * LZ_P + pc];
@@ -364,10 +366,10 @@ __device__ float lz_cnorm_col(const OPen& P, const float* Y, float* CY, int pc, 
   float nv[1] = {0.f};
   for (int a = threadIdx.x; a < P.nO; a += blockDim.x) {
     const int* cl = P.col + (long long)a * P.maxrow;
-    const double* cv = P.C + (long long)a * P.maxrow;
+    const float* cv = P.C32 + (long long)a * P.maxrow;
     int c_n = min(P.cnt[a], P.maxrow);
     float acc = 0;
-    for (int q = 0; q < c_n; ++q) acc += (float)cv[q] * Y[cl[q] * LZ_P + pc];
+    for (int q = 0; q < c_n; ++q) acc += cv[q] * Y[cl[q] * LZ_P + pc];
     CY[a * LZ_P + pc] = acc;
     nv[0] += acc * Y[a * LZ_P + pc];
   }
@@ -467,7 +469,8 @@ __device__ int lz_sturm_below32(const float* d, const float* e2, int n, float x,
 // doubles, N = 4 kdim[s]) reuses the same bytes.  When Yw is given, Y and C Y live there instead
 // (2 nO x 4 floats at y_off[s]) and shared memory starts with the sweep scratch.
 // CTA i works on subdomain sub_list[i].  Global workspace per subdomain: the factors (F + f_off[s]) and
-// the basis Q, C Q and Op Q (3 kdim[s] blocks of nO x 4, Qw + q_off[s]).
+// the basis Q, C Q and Op Q (3 kdim[s] blocks of nO x 4, Qw + q_off[s]), then FP32 copies of the rows of B^N
+// and C (nO x maxrow each).
 // Outputs: lam_hat[s * HK_MAXM + t] = the candidates below lam_cut in ascending order, cnt_out[s] their
 // number, sigma_out[s] the shift used.
 __global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
@@ -502,6 +505,20 @@ __global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
   float* Qg = Qw + q_off[s];
   float* CQg = Qg + nb_max * bs;
   float* Wg = CQg + nb_max * bs;
+  // FP32 copies of the pencil's rows (the sweeps, products with C and factorisations read them)
+  {
+    float* B32 = Wg + nb_max * bs;
+    float* C32 = B32 + (long long)P.nO * maxrow;
+    for (long long e = tid; e < (long long)P.nO * maxrow; e += NT) {
+      int a = (int)(e / maxrow), q = (int)(e - (long long)a * maxrow);
+      bool in = q < P.cnt[a];
+      B32[e] = in ? (float)P.B[e] : 0.f;
+      C32[e] = in ? (float)P.C[e] : 0.f;
+    }
+    P.B32 = B32;
+    P.C32 = C32;
+    __syncthreads();
+  }
 
   // 1. a shift below the spectrum: M = B^N - sigma C positive definite
   double sigma = sigma0, step = 0.5, upper = 0.0;
@@ -902,11 +919,10 @@ __global__ void __launch_bounds__(256) k_inertia(
       const double* cv = P.C + (long long)a * P.maxrow;
       int c_n = min(P.cnt[a], P.maxrow);
       double v = 0;
-      for (int q = 0; q < c_n; ++q) {
+      for (int q = 0; q < c_n; ++q) {  // the entry of M = B^N - tau C formed only where it is used
         int c = cl[q];
-        double mv = bv[q] - tau * cv[q];
-        if (c == r0 + t) v += mv;
-        else if (j > 0 && c >= prev_r0 && c < r0) v -= mv * Xp[(long long)(c - prev_r0) * b + t];
+        if (c == r0 + t) v += bv[q] - tau * cv[q];
+        else if (j > 0 && c >= prev_r0 && c < r0) v -= (bv[q] - tau * cv[q]) * Xp[(long long)(c - prev_r0) * b + t];
       }
       S[e] = v;
       Sc[e] = v;
@@ -1028,7 +1044,7 @@ hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<i
     fo[s] = ftot;
     ftot += (f + 3) & ~3LL;
     qo[s] = qtot;
-    qtot += 3LL * kd[s] * op.h_nO[s] * LZ_P;
+    qtot += 3LL * kd[s] * op.h_nO[s] * LZ_P + ((2LL * op.h_nO[s] * op.maxrow + 3) & ~3LL);  // 16-byte aligned
   }
   *ms = 0;
   if (list.empty()) return HK_OK;
