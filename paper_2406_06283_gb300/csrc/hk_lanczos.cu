@@ -104,22 +104,26 @@ __device__ void gj_inverse_nopiv(T* A, int b, T* sh_inv, double* minpiv) {
   }
 }
 
-// Block elimination of M = B^N - sigma C over the level sets without pivoting (T = float):
-// per level j the inverse of the Schur complement S_j = M_jj - M_{j,j-1} X_{j-1} (b_j x b_j) followed
-// by X_j = S_j^{-1} M_{j,j+1} (b_j x b_{j+1}), stored one after another in F.  S (max_b^2) is the
-// working block (shared memory when it fits, else the level's place in F).  Returns the smallest pivot
-// (> 0 exactly when M is positive definite, up to rounding).
+// Block elimination of M = B^N - sigma C over the level sets without pivoting (T = float).  Per level j:
+// the inverse of the Schur complement S_j = M_jj - M_{j,j-1} X_{j-1} (b_j x b_j), the forward record
+// G_j = -S_j^{-1} M_{j,j-1} (b_j x b_{j-1}) and X_j = S_j^{-1} M_{j,j+1} (b_j x b_{j+1}), stored one after
+// another in F, so that the forward sweep is y_j = S_j^{-1} r_j + G_j y_{j-1} (one dense product per level)
+// and the backward sweep y_j -= X_j y_{j+1}.  S (max_b^2) is the working block (shared memory when it fits,
+// else the level's place in F); Xsm (max_b^2, or null) keeps X_{j-1} in shared memory for the next level.
+// Returns the smallest pivot (> 0 exactly when M is positive definite, up to rounding).
 template <typename T>
-__device__ double lz_factor(const OPen& P, double sigma, T* F, T* Ssm, T* sh_inv, double* sh_min) {
+__device__ double lz_factor(const OPen& P, double sigma, T* F, T* Ssm, T* Xsm, T* sh_inv, double* sh_min) {
   int tid = threadIdx.x, NT = blockDim.x;
   if (tid == 0) *sh_min = 1e300;
   __syncthreads();
   long long bo = 0, prev_x = -1;
   int prev_r0 = 0;
+  T sg = (T)sigma;
   for (int j = 0; j < P.L; ++j) {
     int r0 = P.lp[j], r1 = P.lp[j + 1], b = r1 - r0;
-    int bn = j + 1 < P.L ? P.lp[j + 2] - r1 : 0;
+    int bn = j + 1 < P.L ? P.lp[j + 2] - r1 : 0, bp = j > 0 ? r0 - prev_r0 : 0;
     T* S = Ssm ? Ssm : F + bo;
+    const T* Xp = Xsm ? Xsm : F + prev_x;  // X_{j-1}: b_{j-1} x b
     for (int e = tid; e < b * b; e += NT) {
       int qa = e / b, t = e - qa * b;
       int a = r0 + qa;
@@ -128,11 +132,10 @@ __device__ double lz_factor(const OPen& P, double sigma, T* F, T* Ssm, T* sh_inv
       const float* cv = P.C32 + (long long)a * P.maxrow;
       int c_n = min(P.cnt[a], P.maxrow);
       T v = 0;
-      T sg = (T)sigma;
       for (int q = 0; q < c_n; ++q) {  // the entry of M formed only where it is used
         int c = cl[q];
         if (c == r0 + t) v += (T)bv[q] - sg * (T)cv[q];
-        else if (j > 0 && c >= prev_r0 && c < r0) v -= ((T)bv[q] - sg * (T)cv[q]) * F[prev_x + (long long)(c - prev_r0) * b + t];
+        else if (j > 0 && c >= prev_r0 && c < r0) v -= ((T)bv[q] - sg * (T)cv[q]) * Xp[(long long)(c - prev_r0) * b + t];
       }
       S[e] = v;
     }
@@ -140,11 +143,14 @@ __device__ double lz_factor(const OPen& P, double sigma, T* F, T* Ssm, T* sh_inv
     gj_inverse_nopiv<T>(S, b, sh_inv, sh_min);
     if (Ssm)
       for (int e = tid; e < b * b; e += NT) F[bo + e] = S[e];
-    long long xo = bo + (long long)b * b;
-    // X_j[q][c] = sum_a S^{-1}[q][a] M[a][r1 + c]  (M symmetric: read row r1 + c's entries in level j)
-    for (int e = tid; e < b * bn; e += NT) {
-      int qt = e / bn, cc = e - qt * bn;
-      int c = r1 + cc;
+    // G_j[q][c] = -sum_a S^{-1}[q][a] M[a][prev_r0 + c] and X_j[q][c] = sum_a S^{-1}[q][a] M[a][r1 + c]
+    // (M symmetric: the entries of row prev_r0 + c, or r1 + c, that lie in level j)
+    long long go = bo + (long long)b * b, xo = go + (long long)b * bp;
+    for (int e = tid; e < b * (bp + bn); e += NT) {
+      bool fwd = e < b * bp;
+      int e2 = fwd ? e : e - b * bp, w = fwd ? bp : bn;
+      int qt = e2 / w, cc = e2 - qt * w;
+      int c = fwd ? prev_r0 + cc : r1 + cc;
       const int* cl = P.col + (long long)c * P.maxrow;
       const float* bv = P.B32 + (long long)c * P.maxrow;
       const float* cv = P.C32 + (long long)c * P.maxrow;
@@ -152,9 +158,14 @@ __device__ double lz_factor(const OPen& P, double sigma, T* F, T* Ssm, T* sh_inv
       T v = 0;
       for (int q = 0; q < c_n; ++q) {
         int a = cl[q];
-        if (a >= r0 && a < r1) v += S[qt * b + (a - r0)] * ((T)bv[q] - (T)sigma * (T)cv[q]);
+        if (a >= r0 && a < r1) v += S[qt * b + (a - r0)] * ((T)bv[q] - sg * (T)cv[q]);
       }
-      F[xo + e] = v;
+      if (fwd) {
+        F[go + e2] = -v;
+      } else {
+        F[xo + e2] = v;
+        if (Xsm) Xsm[e2] = v;  // X_{j-1} is no longer read: the Schur complement above is complete
+      }
     }
     __syncthreads();
     prev_x = xo;
@@ -176,76 +187,87 @@ __device__ __forceinline__ void lz_stage(float* dst, const float* src, int n) {
 __device__ __forceinline__ void lz_stage_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Y = M^{-1} Y for LZ_P vectors (row-major nO x LZ_P, in shared memory) with the factors of lz_factor:
-// forward  t_j = y_j - M_{j,j-1} y_{j-1},  y_j = S_j^{-1} t_j;  backward  y_j -= X_j y_{j+1}.
-// tv: max_b x LZ_P shared scratch.  Fb: two shared buffers of max_b^2 floats (or null): each level's
-// block is then copied in by cp.async while the previous level computes, and read from shared memory.
-__device__ void lz_solve(const OPen& P, double sigma, const float* __restrict__ F, float* Y, float* tv, float* Fb,
-                         int max_b) {
-  int tid = threadIdx.x, NT = blockDim.x;
-  long long mb2 = (long long)max_b * max_b;
+// forward  y_j = S_j^{-1} r_j + G_j y_{j-1};  backward  y_j -= X_j y_{j+1}.  One barrier per level step: the
+// forward step writes y_j into one of two scratch blocks (tv: 2 x max_b x LZ_P) and the next step copies it
+// into Y (whose level-j rows the step itself still reads as r_j); the backward step updates its own rows of
+// Y in place from the finished rows of level j + 1.  Fb: two shared staging buffers of 2 max_b^2 floats (or
+// null): each level's records are copied in by cp.async while the previous level computes.
+__device__ void lz_solve(const OPen& P, const float* __restrict__ F, float* Y, float* tv, float* Fb, int max_b) {
+  int tid = threadIdx.x, NT = blockDim.x, L = P.L;
+  long long mb2 = 2LL * max_b * max_b, tvs = (long long)max_b * LZ_P;
+  auto lvl = [&](int j, int& r0, int& b, int& bp, int& bn) {
+    r0 = P.lp[j];
+    b = P.lp[j + 1] - r0;
+    bp = j > 0 ? r0 - P.lp[j - 1] : 0;
+    bn = j + 1 < L ? P.lp[j + 2] - P.lp[j + 1] : 0;
+  };
   long long fo = 0;
-  if (Fb) lz_stage(Fb, F, (P.lp[1] - P.lp[0]) * (P.lp[1] - P.lp[0]));
-  for (int j = 0; j < P.L; ++j) {
-    int r0 = P.lp[j], b = P.lp[j + 1] - r0, bn = j + 1 < P.L ? P.lp[j + 2] - P.lp[j + 1] : 0;
-    for (int e = tid; e < b * LZ_P; e += NT) {
-      int q = e / LZ_P, pc = e - q * LZ_P;
-      int a = r0 + q;
-      const int* cl = P.col + (long long)a * P.maxrow;
-      const float* bv = P.B32 + (long long)a * P.maxrow;
-      const float* cv = P.C32 + (long long)a * P.maxrow;
-      int c_n = min(P.cnt[a], P.maxrow);
-      float acc = Y[a * LZ_P + pc], sg = (float)sigma;
-      for (int q2 = 0; q2 < c_n; ++q2) {
-        int c = cl[q2];
-        if (c < r0) acc -= (bv[q2] - sg * cv[q2]) * Y[c * LZ_P + pc];
-      }
-      tv[e] = acc;
-    }
+  int r0, b, bp, bn;
+  lvl(0, r0, b, bp, bn);
+  if (Fb) lz_stage(Fb, F, b * b);
+  for (int j = 0; j < L; ++j) {
+    lvl(j, r0, b, bp, bn);
     if (Fb) lz_stage_wait();
-    __syncthreads();
+    __syncthreads();  // level j's records staged; y_{j-1} complete in tv[(j - 1) & 1]
+    long long fn = fo + (long long)b * b + (long long)b * bp + (long long)b * bn;
+    if (Fb && j + 1 < L) {
+      int r0n, b1, bp1, bn1;
+      lvl(j + 1, r0n, b1, bp1, bn1);
+      lz_stage(Fb + ((j + 1) & 1) * mb2, F + fn, b1 * b1 + b1 * bp1);
+    }
     const float* Sb = Fb ? Fb + (j & 1) * mb2 : F + fo;
-    long long fn = fo + (long long)b * b + (long long)b * bn;
-    if (Fb && j + 1 < P.L) {
-      int b1 = bn;
-      lz_stage(Fb + ((j + 1) & 1) * mb2, F + fn, b1 * b1);
+    const float* Gb = Sb + (long long)b * b;
+    const float* yp = tv + ((j + 1) & 1) * tvs;  // y_{j-1}
+    float* yc = tv + (j & 1) * tvs;
+    if (j > 0) {
+      int pr0 = P.lp[j - 1];
+      for (int e = tid; e < bp * LZ_P; e += NT) Y[pr0 * LZ_P + e] = yp[e];
     }
     for (int e = tid; e < b * LZ_P; e += NT) {
       int q = e / LZ_P, pc = e - q * LZ_P;
       const float* Sr = Sb + (long long)q * b;
+      const float* Gr = Gb + (long long)q * bp;
       float acc0 = 0.f, acc1 = 0.f;
       int c = 0;
       for (; c + 1 < b; c += 2) {
-        acc0 += Sr[c] * tv[c * LZ_P + pc];
-        acc1 += Sr[c + 1] * tv[(c + 1) * LZ_P + pc];
+        acc0 += Sr[c] * Y[(r0 + c) * LZ_P + pc];
+        acc1 += Sr[c + 1] * Y[(r0 + c + 1) * LZ_P + pc];
       }
-      if (c < b) acc0 += Sr[c] * tv[c * LZ_P + pc];
-      Y[(r0 + q) * LZ_P + pc] = acc0 + acc1;
+      if (c < b) acc0 += Sr[c] * Y[(r0 + c) * LZ_P + pc];
+      for (c = 0; c + 1 < bp; c += 2) {
+        acc0 += Gr[c] * yp[c * LZ_P + pc];
+        acc1 += Gr[c + 1] * yp[(c + 1) * LZ_P + pc];
+      }
+      if (c < bp) acc0 += Gr[c] * yp[c * LZ_P + pc];
+      yc[e] = acc0 + acc1;
     }
-    __syncthreads();
     fo = fn;
   }
-  if (P.L < 2) return;
-  // fo is now the end of the factors; walk back to level L - 2
-  long long fj;
-  {
-    int bl = P.lp[P.L] - P.lp[P.L - 1], b2 = P.lp[P.L - 1] - P.lp[P.L - 2];
-    fj = fo - (long long)bl * bl - ((long long)b2 * b2 + (long long)b2 * bl);  // level L - 2's offset
-  }
-  if (Fb) {
-    int b = P.lp[P.L - 1] - P.lp[P.L - 2], bn = P.lp[P.L] - P.lp[P.L - 1];
-    lz_stage(Fb, F + fj + (long long)b * b, b * bn);
-  }
-  for (int j = P.L - 2, it = 0; j >= 0; --j, ++it) {
-    int r0 = P.lp[j], b = P.lp[j + 1] - r0, r1 = P.lp[j + 1], bn = P.lp[j + 2] - r1;
-    if (Fb) lz_stage_wait();
+  __syncthreads();
+  for (int e = tid; e < b * LZ_P; e += NT) Y[r0 * LZ_P + e] = tv[((L - 1) & 1) * tvs + e];
+  if (L < 2) {
     __syncthreads();
-    const float* Xm = Fb ? Fb + (it & 1) * mb2 : F + fj + (long long)b * b;
+    return;
+  }
+  // backward, from level L - 2: fo walks back over the level sizes
+  lvl(L - 1, r0, b, bp, bn);
+  fo -= (long long)b * b + (long long)b * bp;  // start of level L - 1 (bn = 0)
+  lvl(L - 2, r0, b, bp, bn);
+  long long fj = fo - ((long long)b * b + (long long)b * bp + (long long)b * bn);
+  if (Fb) lz_stage(Fb, F + fj + (long long)b * b + (long long)b * bp, b * bn);
+  for (int j = L - 2, it = 0; j >= 0; --j, ++it) {
+    lvl(j, r0, b, bp, bn);
+    if (Fb) lz_stage_wait();
+    __syncthreads();  // X_j staged; rows of level j + 1 final
+    const float* Xm = Fb ? Fb + (it & 1) * mb2 : F + fj + (long long)b * b + (long long)b * bp;
     long long fp = 0;
     if (j > 0) {
-      int bp = P.lp[j] - P.lp[j - 1];
-      fp = fj - ((long long)bp * bp + (long long)bp * b);
-      if (Fb) lz_stage(Fb + ((it + 1) & 1) * mb2, F + fp + (long long)bp * bp, bp * b);
+      int r0p, b2, bp2, bn2;
+      lvl(j - 1, r0p, b2, bp2, bn2);
+      fp = fj - ((long long)b2 * b2 + (long long)b2 * bp2 + (long long)b2 * bn2);
+      if (Fb) lz_stage(Fb + ((it + 1) & 1) * mb2, F + fp + (long long)b2 * b2 + (long long)b2 * bp2, b2 * bn2);
     }
+    int r1 = r0 + b;
     for (int e = tid; e < b * LZ_P; e += NT) {
       int q = e / LZ_P, pc = e - q * LZ_P;
       const float* Xr = Xm + (long long)q * bn;
@@ -256,12 +278,7 @@ __device__ void lz_solve(const OPen& P, double sigma, const float* __restrict__ 
         acc1 += Xr[c + 1] * Y[(r1 + c + 1) * LZ_P + pc];
       }
       if (c < bn) acc0 += Xr[c] * Y[(r1 + c) * LZ_P + pc];
-      tv[e] = acc0 + acc1;
-    }
-    __syncthreads();
-    for (int e = tid; e < b * LZ_P; e += NT) {
-      int q = e / LZ_P, pc = e - q * LZ_P;
-      Y[(r0 + q) * LZ_P + pc] -= tv[e];
+      Y[(r0 + q) * LZ_P + pc] -= acc0 + acc1;
     }
     fj = fp;
   }
@@ -317,7 +334,8 @@ __device__ void lz_cgs_pass(int nO, int nb, const float* __restrict__ Qg, const 
     for (int p = 0; p < LZ_P; ++p)
 #pragma unroll
       for (int q = 0; q < LZ_P; ++q) acc[p][q] = 0.f;
-    for (int a = lane; a < nO; a += 32) {
+#pragma unroll 4
+    for (int a = lane; a < nO; a += 32) {  // unrolled: several L2 loads in flight per lane
       float4 c4 = cq[a];
       float4 y4 = reinterpret_cast<const float4*>(Y)[a];
       float c[4] = {c4.x, c4.y, c4.z, c4.w}, y[4] = {y4.x, y4.y, y4.z, y4.w};
@@ -339,6 +357,7 @@ __device__ void lz_cgs_pass(int nO, int nb, const float* __restrict__ Qg, const 
   for (int a = threadIdx.x; a < nO; a += blockDim.x) {
     float4 y4 = reinterpret_cast<float4*>(Y)[a];
     float y[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll 4
     for (int i = 0; i < nb; ++i) {
       float4 q4 = reinterpret_cast<const float4*>(Qg + i * bs)[a];
       float qv[4] = {q4.x, q4.y, q4.z, q4.w};
@@ -464,8 +483,9 @@ __device__ int lz_sturm_below32(const float* d, const float* e2, int n, float x,
 }
 
 // One CTA per subdomain.  Dynamic shared memory: Y (max_nO x 4) | C Y (max_nO x 4) | sweep scratch
-// (max_b x 4) | the working block of the factorisation (max_b^2, when s_in_smem) | two staging buffers of
-// the sweeps (2 max_b^2, when use_fb); once the Krylov steps are done the Rayleigh quotient (N x N
+// (2 max_b x 4) | the working block of the factorisation and X_{j-1} (2 max_b^2, when s_in_smem) | two
+// staging buffers of the sweeps (2 x 2 max_b^2, when use_fb); once the Krylov steps are done the Rayleigh
+// quotient (N x N
 // doubles, N = 4 kdim[s]) reuses the same bytes.  When Yw is given, Y and C Y live there instead
 // (2 nO x 4 floats at y_off[s]) and shared memory starts with the sweep scratch.
 // CTA i works on subdomain sub_list[i].  Global workspace per subdomain: the factors (F + f_off[s]) and
@@ -495,9 +515,11 @@ __global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
   // Y and C Y in shared memory, or (subdomains too large for it) in the global scratch Yw
   float* Ys = Yw ? Yw + y_off[s] : reinterpret_cast<float*>(lz_smem);
   float* CYs = Ys + (long long)(Yw ? P.nO : max_nO) * LZ_P;
-  float* tv = Yw ? reinterpret_cast<float*>(lz_smem) : CYs + (long long)max_nO * LZ_P;
-  float* Ssm = s_in_smem ? tv + (long long)max_b * LZ_P : nullptr;
-  float* Fb = use_fb ? (Ssm ? Ssm : tv + (long long)max_b * LZ_P) + (s_in_smem ? (long long)max_b * max_b : 0) : nullptr;
+  float* tv = Yw ? reinterpret_cast<float*>(lz_smem) : CYs + (long long)max_nO * LZ_P;  // 2 x max_b x LZ_P
+  long long mb2 = (long long)max_b * max_b;
+  float* Ssm = s_in_smem ? tv + 2LL * max_b * LZ_P : nullptr;
+  float* Xsm = s_in_smem ? Ssm + mb2 : nullptr;
+  float* Fb = use_fb ? tv + 2LL * max_b * LZ_P + (s_in_smem ? 2 * mb2 : 0) : nullptr;  // 2 x 2 max_b^2
   double* Tm = reinterpret_cast<double*>(lz_smem);
   float* Fs = F + f_off[s];
   int nb_max = kdim[s], nb = min(nb0, nb_max);
@@ -524,7 +546,7 @@ __global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
   double sigma = sigma0, step = 0.5, upper = 0.0;
   bool pd = false, bracket = false;
   for (int t = 0; t < LZ_SIGMA_TRIES && !pd; ++t) {
-    double mp = lz_factor<float>(P, sigma, Fs, Ssm, &sh_inv, &sh_min);
+    double mp = lz_factor<float>(P, sigma, Fs, Ssm, Xsm, &sh_inv, &sh_min);
     __syncthreads();
     pd = mp > 0.0;
     if (!pd) {
@@ -539,7 +561,7 @@ __global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
   bool factors_current = true;
   for (int t = 0; t < LZ_SIGMA_BISECT && pd && bracket; ++t) {
     double mid = 0.5 * (sigma + upper);
-    double mp = lz_factor<float>(P, mid, Fs, Ssm, &sh_inv, &sh_min);
+    double mp = lz_factor<float>(P, mid, Fs, Ssm, Xsm, &sh_inv, &sh_min);
     __syncthreads();
     if (mp > 0.0) {
       sigma = mid;
@@ -550,7 +572,7 @@ __global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
     }
   }
   if (pd && !factors_current) {
-    lz_factor<float>(P, sigma, Fs, Ssm, &sh_inv, &sh_min);
+    lz_factor<float>(P, sigma, Fs, Ssm, Xsm, &sh_inv, &sh_min);
     __syncthreads();
   }
   if (!pd) {
@@ -586,7 +608,7 @@ __global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
   for (int k = k_done; k < nb; ++k) {
     for (long long e = tid; e < bs; e += NT) Ys[e] = CQg[k * bs + e];
     __syncthreads();
-    lz_solve(P, sigma, Fs, Ys, tv, Fb, max_b);
+    lz_solve(P, Fs, Ys, tv, Fb, max_b);
     for (long long e = tid; e < bs; e += NT) Wg[k * bs + e] = Ys[e];
     __syncthreads();
     if (k == nb_max - 1) break;
@@ -617,6 +639,7 @@ __global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
     for (int p = 0; p < LZ_P; ++p)
 #pragma unroll
       for (int q = 0; q < LZ_P; ++q) acc[p][q] = 0.f;
+#pragma unroll 4
     for (int a = lane; a < P.nO; a += 32) {
       float4 c4 = cq[a], w4 = wq[a];
       float c[4] = {c4.x, c4.y, c4.z, c4.w}, w[4] = {w4.x, w4.y, w4.z, w4.w};
@@ -1039,7 +1062,8 @@ hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<i
     long long f = 0;
     for (int j = 0; j < op.h_L[s]; ++j) {
       long long b = lp[j + 1] - lp[j], bn = j + 1 < op.h_L[s] ? lp[j + 2] - lp[j + 1] : 0;
-      f += b * b + b * bn;
+      long long bp = j > 0 ? lp[j] - lp[j - 1] : 0;
+      f += b * b + b * bp + b * bn;  // S_j^{-1}, G_j, X_j
     }
     fo[s] = ftot;
     ftot += (f + 3) & ~3LL;
@@ -1066,7 +1090,7 @@ hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<i
   HK_CUDA(cudaMemcpyAsync(d_list, list.data(), 4 * nl, cudaMemcpyHostToDevice, st));
   HK_CUDA(cudaMemcpyAsync(d_fo, fo.data(), 8 * ns, cudaMemcpyHostToDevice, st));
   HK_CUDA(cudaMemcpyAsync(d_qo, qo.data(), 8 * ns, cudaMemcpyHostToDevice, st));
-  size_t vec = sizeof(float) * LZ_P * (2 * (size_t)op.max_nO + op.max_b);
+  size_t vec = sizeof(float) * LZ_P * (2 * (size_t)op.max_nO + 2 * (size_t)op.max_b);
   size_t sblk = sizeof(float) * (size_t)op.max_b * op.max_b;
   float* d_Y = nullptr;
   long long* d_yo = nullptr;
@@ -1081,12 +1105,12 @@ hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<i
     HK_TRY(dalloc(h, &d_Y, ytot));
     HK_TRY(dalloc(h, &d_yo, ns));
     HK_CUDA(cudaMemcpyAsync(d_yo, yo.data(), 8 * ns, cudaMemcpyHostToDevice, st));
-    vec = sizeof(float) * LZ_P * (size_t)op.max_b;
+    vec = sizeof(float) * LZ_P * 2 * (size_t)op.max_b;
   }
   size_t tmat = sizeof(double) * (size_t)(kmax * LZ_P) * (kmax * LZ_P);
-  int s_in_smem = vec + sblk <= 200 * 1024;
-  int use_fb = vec + (s_in_smem ? sblk : 0) + 2 * sblk <= 200 * 1024;
-  size_t shm = std::max(vec + (s_in_smem ? sblk : 0) + (use_fb ? 2 * sblk : 0), tmat);
+  int s_in_smem = vec + 2 * sblk <= 200 * 1024;  // S and X_{j-1} of the factorisation
+  int use_fb = vec + (s_in_smem ? 2 * sblk : 0) + 4 * sblk <= 200 * 1024;  // two record stages of 2 max_b^2
+  size_t shm = std::max(vec + (s_in_smem ? 2 * sblk : 0) + (use_fb ? 4 * sblk : 0), tmat);
   if (shm > 220 * 1024) {
     hk_set_error("subdomain with %d ovdof rows too large for the Lanczos kernel's shared memory", op.max_nO);
     return HK_UNSUPPORTED;
@@ -1120,8 +1144,9 @@ hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<i
     double fac = 0, sweep = 0;
     for (int j = 0; j < op.h_L[s]; ++j) {
       double b = lp[j + 1] - lp[j], bn = j + 1 < op.h_L[s] ? lp[j + 2] - lp[j + 1] : 0;
-      fac += b * b * b;
-      sweep += (b * b + b * bn) * LZ_P;
+      double bp = j > 0 ? lp[j] - lp[j - 1] : 0;
+      fac += b * b * b + b * b * (bp + bn);
+      sweep += (b * b + b * bp + b * bn) * LZ_P;
     }
     double nO = op.h_nO[s], nbs = nbv[s], N = nbs * LZ_P;
     fma += fac + nbs * (sweep + 28.0 * nO) + 2.0 * 32.0 * nO * nbs * (nbs + 1) / 2.0 + N * N * nO +
