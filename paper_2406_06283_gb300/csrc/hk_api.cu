@@ -68,11 +68,14 @@ hk_status hk_allow_smem_fn(const void* fn) {
   cudaFuncAttributes fa;
   HK_CUDA(cudaFuncGetAttributes(&fa, fn));
   HK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
-  // every kernel asks for the largest shared-memory carveout: an SM configured for a small carveout takes
-  // no block that needs a large one until it drains, which left the eigensolver's blocks waiting behind
-  // the concurrent setup kernels
-  HK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared));
   done.insert({fn, dev});
+  return HK_OK;
+}
+
+// The setup kernels that run beside the eigensolver's Lanczos blocks ask for the largest shared-memory
+// carveout: an SM configured for a small one takes no block that needs a large one until it drains.
+hk_status hk_max_carveout_fn(const void* fn) {
+  HK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared));
   return HK_OK;
 }
 

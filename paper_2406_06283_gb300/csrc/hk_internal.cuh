@@ -290,6 +290,11 @@ void dfree(hk_handle* h, void* p);
 // once (instead of to each launch's size) keeps concurrent setups on other host threads from
 // lowering it under a launch.  The launch still asks for exactly the bytes it uses.
 hk_status hk_allow_smem_fn(const void* fn);
+hk_status hk_max_carveout_fn(const void* fn);
+template <typename F>
+hk_status hk_max_carveout(F* fn) {
+  return hk_max_carveout_fn(reinterpret_cast<const void*>(fn));
+}
 template <typename F>
 hk_status hk_allow_smem(F* fn) {
   return hk_allow_smem_fn(reinterpret_cast<const void*>(fn));

@@ -34,6 +34,7 @@
 #define LZ_P 4            // Krylov block size
 #define LZ_THREADS 256
 #define LZ_MAX_DIM 160    // largest Krylov basis (columns)
+#define LZ_T_SMEM 128     // largest Rayleigh quotient kept in shared memory (columns)
 #define LZ_SIGMA_TRIES 8  // shifts tried: sigma0, then 0.5, 0.5, 1, 2, 4, ... lower while the matrix is not definite
 #define LZ_SIGMA_BISECT 2 // bisection steps between the last indefinite and the first definite shift
 
@@ -493,14 +494,14 @@ __device__ int lz_sturm_below32(const float* d, const float* e2, int n, float x,
 // and C (nO x maxrow each).
 // Outputs: lam_hat[s * HK_MAXM + t] = the candidates below lam_cut in ascending order, cnt_out[s] their
 // number, sigma_out[s] the shift used.
-__global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
+__global__ void __launch_bounds__(LZ_THREADS, 2) k_lanczos(
     const int* __restrict__ sub_info, const int* __restrict__ o_off, const int* __restrict__ O_levptr,
     const int* __restrict__ O_L, int maxrow, const int* __restrict__ ocnt, const int* __restrict__ ocol,
     const double* __restrict__ oB, const double* __restrict__ oC, const int* __restrict__ o2i,
     const int* __restrict__ sub_list, const int* __restrict__ kdim, const long long* __restrict__ f_off, float* F,
     const long long* __restrict__ q_off,
     float* Qw, float* Yw, const long long* __restrict__ y_off, int max_nO, int max_b, int s_in_smem, int use_fb,
-    int nb0, double sigma0, double lam_cut,
+    int nb0, double sigma0, double lam_cut, double* Tw, long long t_stride, int tcap,
     double* lam_hat, int* cnt_out, double* sigma_out, int* nb_out, DevStatus* st) {
   extern __shared__ __align__(16) unsigned char lz_smem[];
   __shared__ float coef[LZ_MAX_DIM * LZ_P];
@@ -520,7 +521,6 @@ __global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
   float* Ssm = s_in_smem ? tv + 2LL * max_b * LZ_P : nullptr;
   float* Xsm = s_in_smem ? Ssm + mb2 : nullptr;
   float* Fb = use_fb ? tv + 2LL * max_b * LZ_P + (s_in_smem ? 2 * mb2 : 0) : nullptr;  // 2 x 2 max_b^2
-  double* Tm = reinterpret_cast<double*>(lz_smem);
   float* Fs = F + f_off[s];
   int nb_max = kdim[s], nb = min(nb0, nb_max);
   long long bs = (long long)P.nO * LZ_P;
@@ -630,6 +630,9 @@ __global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
   k_done = nb;
   // 4. Rayleigh quotient T = Q^T C (Op Q), a warp per pair of blocks; then symmetrised (FP64)
   N = nb * LZ_P;
+  int ldT = N | 1;  // odd row stride (in doubles): row- and column-wise accesses of T hit distinct banks
+  // T in the shared memory the vectors used (up to tcap columns), else in this block's global scratch
+  double* Tm = N <= tcap ? reinterpret_cast<double*>(lz_smem) : Tw + (long long)blockIdx.x * t_stride;
   for (int pr = warp; pr < nb * nb; pr += nw) {
     int bi = pr / nb, bj = pr - bi * nb;
     const float4* cq = reinterpret_cast<const float4*>(CQg + bi * bs);
@@ -654,16 +657,16 @@ __global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
       for (int q = 0; q < LZ_P; ++q) {
         float t = acc[p][q];
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) Tm[(bi * LZ_P + p) * N + bj * LZ_P + q] = (double)t;
+        if (lane == 0) Tm[(bi * LZ_P + p) * ldT + bj * LZ_P + q] = (double)t;
       }
   }
   __syncthreads();
   for (int e = tid; e < N * N; e += NT) {
     int i = e / N, j = e - i * N;
     if (i < j) {
-      double v = 0.5 * (Tm[i * N + j] + Tm[j * N + i]);
-      Tm[i * N + j] = v;
-      Tm[j * N + i] = v;
+      double v = 0.5 * (Tm[i * ldT + j] + Tm[j * ldT + i]);
+      Tm[i * ldT + j] = v;
+      Tm[j * ldT + i] = v;
     }
   }
   __syncthreads();
@@ -673,11 +676,11 @@ __global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
   for (int k = 0; k + 2 < N; ++k) {
     if (warp == 0) {
       double ss = 0;
-      for (int i = k + 2 + lane; i < N; i += 32) ss += Tm[i * N + k] * Tm[i * N + k];
+      for (int i = k + 2 + lane; i < N; i += 32) ss += Tm[i * ldT + k] * Tm[i * ldT + k];
       for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
       if (lane == 0) {
-        double x0 = Tm[(k + 1) * N + k];
-        hd[k] = Tm[k * N + k];
+        double x0 = Tm[(k + 1) * ldT + k];
+        hd[k] = Tm[k * ldT + k];
         if (ss == 0.0) {
           he[k] = x0;
           sh_scal[0] = 0.0;
@@ -693,12 +696,16 @@ __global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
     double beta = sh_scal[0];
     __syncthreads();  // every thread has read beta before warp 0 may overwrite it
     if (beta == 0.0) continue;
-    for (int i = k + 2 + tid; i < N; i += NT) hv[i] = Tm[i * N + k];
+    for (int i = k + 2 + tid; i < N; i += NT) hv[i] = Tm[i * ldT + k];
     __syncthreads();
-    for (int i = k + 1 + tid; i < N; i += NT) {
+    // p = beta T v over rows k+1 .. N-1: two threads per row, each summing every other column
+    for (int base = 0; base < 2 * (N - k - 1); base += NT) {
+      int t2 = base + tid, i = k + 1 + (t2 >> 1);
       double acc = 0;
-      for (int j = k + 1; j < N; ++j) acc += Tm[i * N + j] * hv[j];
-      hp[i] = beta * acc;
+      if (i < N)
+        for (int j = k + 1 + (t2 & 1); j < N; j += 2) acc += Tm[i * ldT + j] * hv[j];
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      if (i < N && !(t2 & 1)) hp[i] = beta * acc;
     }
     __syncthreads();
     if (warp == 0) {
@@ -711,19 +718,25 @@ __global__ void __launch_bounds__(LZ_THREADS, 1) k_lanczos(
     double kc = sh_scal[1];
     for (int i = k + 1 + tid; i < N; i += NT) hp[i] -= kc * hv[i];
     __syncthreads();
-    int m = N - k - 1;
-    for (int e = tid; e < m * m; e += NT) {
-      int i = k + 1 + e / m, j = k + 1 + e % m;
-      Tm[i * N + j] -= hv[i] * hp[j] + hp[i] * hv[j];
+    // symmetric rank-2 update on the lower triangle, mirrored to the upper one
+    int m = N - k - 1, tri = m * (m + 1) / 2;
+    for (int e = tid; e < tri; e += NT) {
+      int ii = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+      while (ii * (ii + 1) / 2 > e) --ii;
+      while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+      int i = k + 1 + ii, j = k + 1 + (e - ii * (ii + 1) / 2);
+      double v = Tm[i * ldT + j] - (hv[i] * hp[j] + hp[i] * hv[j]);
+      Tm[i * ldT + j] = v;
+      Tm[j * ldT + i] = v;
     }
     __syncthreads();
   }
   if (tid == 0) {
     if (N >= 2) {
-      hd[N - 2] = Tm[(N - 2) * N + N - 2];
-      he[N - 2] = Tm[(N - 1) * N + N - 2];
+      hd[N - 2] = Tm[(N - 2) * ldT + N - 2];
+      he[N - 2] = Tm[(N - 1) * ldT + N - 2];
     }
-    hd[N - 1] = Tm[(N - 1) * N + N - 1];
+    hd[N - 1] = Tm[(N - 1) * ldT + N - 1];
     he[N - 1] = 0.0;
     double hi = -1e300, me = 0;
     for (int i = 0; i < N; ++i) {
@@ -1010,6 +1023,7 @@ hk_status eigen_inertia(hk_handle* h, const OvdofPencil& op, double tau, int* d_
     }
   }
   HK_TRY(hk_allow_smem(k_inertia));
+  HK_TRY(hk_max_carveout(k_inertia));  // runs beside the Lanczos blocks
   {
     // algorithmic FMAs: per level Gauss-Jordan (b^3) and Bunch-Kaufman (b^3 / 3)
     double fma = 0;
@@ -1107,7 +1121,17 @@ hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<i
     HK_CUDA(cudaMemcpyAsync(d_yo, yo.data(), 8 * ns, cudaMemcpyHostToDevice, st));
     vec = sizeof(float) * LZ_P * 2 * (size_t)op.max_b;
   }
-  size_t tmat = sizeof(double) * (size_t)(kmax * LZ_P) * (kmax * LZ_P);
+  // the Rayleigh quotient (N x (N | 1) doubles) in shared memory up to LZ_T_SMEM columns, beyond in a global
+  // scratch: a block that needs the whole shared memory waits for an empty SM, and the setup kernels beside
+  // this one occupy most of them
+  int tcap = std::min(kmax * LZ_P, LZ_T_SMEM);
+  size_t tmat = sizeof(double) * (size_t)tcap * (tcap | 1);
+  double* d_T = nullptr;
+  long long t_stride = 0;
+  if (kmax * LZ_P > tcap) {
+    t_stride = (long long)(kmax * LZ_P) * ((kmax * LZ_P) | 1);
+    HK_TRY(dalloc(h, &d_T, (size_t)t_stride * nl));
+  }
   int s_in_smem = vec + 2 * sblk <= 200 * 1024;  // S and X_{j-1} of the factorisation
   int use_fb = vec + (s_in_smem ? 2 * sblk : 0) + 4 * sblk <= 200 * 1024;  // two record stages of 2 max_b^2
   size_t shm = std::max(vec + (s_in_smem ? 2 * sblk : 0) + (use_fb ? 4 * sblk : 0), tmat);
@@ -1116,6 +1140,7 @@ hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<i
     return HK_UNSUPPORTED;
   }
   HK_TRY(hk_allow_smem(k_lanczos));
+  HK_TRY(hk_max_carveout(k_lanczos));
   cudaEvent_t e0, e1;
   HK_CUDA(cudaEventCreate(&e0));
   HK_CUDA(cudaEventCreate(&e1));
@@ -1123,8 +1148,8 @@ hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<i
   k_lanczos<<<nl, LZ_THREADS, shm, st>>>(h->d_sub_info, op.o_off, op.levptr, op.L, op.maxrow, op.cnt, op.col, op.B,
                                          op.C, op.o2i, d_list, d_kd, d_fo, d_F, d_qo, d_Q, d_Y, d_yo, op.max_nO, op.max_b,
                                          s_in_smem,
-                                         use_fb, (cols0 + LZ_P - 1) / LZ_P, -0.5, lam_cut, d_lamhat, d_cnt, d_sig,
-                                         d_nb, h->d_status);
+                                         use_fb, (cols0 + LZ_P - 1) / LZ_P, -0.5, lam_cut, d_T, t_stride, tcap,
+                                         d_lamhat, d_cnt, d_sig, d_nb, h->d_status);
   HK_COUNT_LAUNCH();
   cudaEventRecord(e1, st);
   HK_LAUNCH_CHECK();
@@ -1153,7 +1178,7 @@ hk_status eigen_lanczos(hk_handle* h, const OvdofPencil& op, const std::vector<i
            4.0 * N * N * N / 3.0;
   }
   h->eigen_gflop[1] += 2.0 * fma * 1e-9;
-  void* tmp[] = {d_kd, d_list, d_fo, d_qo, d_F, d_Q, d_sig, d_nb, d_Y, d_yo};
+  void* tmp[] = {d_kd, d_list, d_fo, d_qo, d_F, d_Q, d_sig, d_nb, d_Y, d_yo, d_T};
   for (void* p : tmp) dfree(h, p);
   return HK_OK;
 }

@@ -1443,8 +1443,9 @@ hk_status phase_local_factors_begin(hk_handle* h) {
   }
   HK_TRY(hk_allow_smem(k_block_lu));
   HK_TRY(hk_allow_smem(k_chain_growth));
-  HK_TRY(hk_allow_smem(k_pack_levels<float>));
-  HK_TRY(hk_allow_smem(k_pack_levels<double>));
+  HK_TRY(hk_max_carveout(k_block_lu));  // these run beside the eigensolver
+  HK_TRY(hk_max_carveout(k_pack_levels<float>));
+  HK_TRY(hk_max_carveout(k_pack_levels<double>));
   if (!h->aux_stream) HK_CUDA(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
   if (!h->ev_lf) HK_CUDA(cudaEventCreateWithFlags(&h->ev_lf, cudaEventDisableTiming));
   if (!h->co_stream) {

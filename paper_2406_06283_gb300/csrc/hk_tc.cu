@@ -661,7 +661,7 @@ hk_status tc_plan(hk_handle* h, const std::vector<int>& lev) {
 
 hk_status tc_pack(hk_handle* h, cudaStream_t st) {
   if (!h->tc_ok) return HK_OK;
-  HK_TRY(hk_allow_smem(k_pack_tc));
+  HK_TRY(hk_max_carveout(k_pack_tc));  // runs beside the eigensolver
   k_pack_tc<<<h->n_sub, 256, 0, st>>>(h->d_sub_info, h->d_sub_off, h->d_lev, h->d_lrow, h->d_lcntI, h->d_lcol,
                                       h->d_lvalB, h->d_F64, h->d_lvfo, h->d_lvtab_tc, h->d_twist, h->d_pack_tc);
   HK_COUNT_LAUNCH();
