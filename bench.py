@@ -580,7 +580,10 @@ def run_ours(args, world, rank, local):
                 "kernel": kname + (" (FP32 shift-invert block Lanczos)" if fp32 else " (FP64)"),
                 "ms_per_launch": tot[dom],
                 "peak_source": "derived: " + ("FP32 CUDA cores" if fp32 else "FP64 units") + " x 2.07 GHz",
-                "note": "one CTA per subdomain; a latency-bound chain of level steps"}
+                "note": {"k_inertia": "one CTA per subdomain; a chain of FP64 level steps",
+                         "k_lanczos": "one CTA per subdomain; a latency-bound chain of level steps",
+                         "k_refine": "one CTA per candidate cluster; FP64-pipe bound (block LU and sweeps of "
+                                     "the shifted pencil) with a barrier chain per pivot"}[kname]}
     else:
         b = {"local_apply": bytes_local, "coarse_solve": bytes_coarse, "scatter": bytes_scatter}.get(dom)
         if b is None:
