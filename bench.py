@@ -362,7 +362,8 @@ def run_ours(args, world, rank, local):
 
     fine = args.fine_parts
     if fine:
-        d_e2f = torch.tensor(W.box_partition(m, fine), dtype=torch.int32, device=dev)
+        e2f_host = W.box_partition(m, fine)
+        d_e2f = torch.tensor(e2f_host, dtype=torch.int32, device=dev)
 
     def setup_dev(precision=prec):
         if fine:  # the nested decompositions of Sec. 2.3: fine boxes inside the coarse subdomains
@@ -451,15 +452,20 @@ def run_ours(args, world, rank, local):
 
     # ---- e2e through the host-pointer calls (copies inside the timed region)
     h2d = m.xyz.nbytes + m.elems.astype(np.int32).nbytes + m.is_boundary.nbytes + p.coeff.nbytes + \
-        p.elem_to_sub.astype(np.int32).nbytes + rhs_host.nbytes
+        p.elem_to_sub.astype(np.int32).nbytes + rhs_host.nbytes + (4 * m.n_elems if fine else 0)
     d2h = rhs_host.nbytes + 4 * s + 8 * s
     e2e_ms = []
     for k in range(max(1, min(args.steps, 5))):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h = hk.hk_setup(m.xyz, m.elems, m.is_boundary, p.coeff, p.k, p.elem_to_sub, p.n_sub, p.overlap, p.tau, prec,
-                        hk.HK_TWO_LEVEL, hk.HK_AS, p.restart, p.max_iters, sptr)
+        if fine:  # the same nested decompositions as the device-timed step
+            h = hk.hk_setup_nested(m.xyz, m.elems, m.is_boundary, p.coeff, p.k, p.elem_to_sub, p.n_sub, e2f_host,
+                                   fine ** m.dim, p.overlap, args.fine_overlap, p.tau, prec, hk.HK_AS, p.restart,
+                                   p.max_iters, sptr)
+        else:
+            h = hk.hk_setup(m.xyz, m.elems, m.is_boundary, p.coeff, p.k, p.elem_to_sub, p.n_sub, p.overlap, p.tau,
+                            prec, hk.HK_TWO_LEVEL, hk.HK_AS, p.restart, p.max_iters, sptr)
         hk.hk_solve(h, rhs_host, p.tol)
         hk.hk_destroy(h)
         torch.cuda.synchronize()
