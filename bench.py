@@ -60,16 +60,22 @@ def bf16_peak() -> float:
 BF16_PEAK = bf16_peak()
 
 
+def kernel_source(kernel: str) -> str | None:
+    """Path of the CUDA source file whose `__global__` declaration defines `kernel` (not merely names it)."""
+    import re
+    pat = re.compile(rb"__global__\s+(?:void\s+)?(?:__launch_bounds__\([^)]*\)\s+)?(?:void\s+)?" +
+                     re.escape(kernel.encode()) + rb"\s*\(")
+    for f in sorted(os.listdir(CSRC)):
+        if f.endswith(".cu") and pat.search(open(os.path.join(CSRC, f), "rb").read()):
+            return os.path.join(CSRC, f)
+    return None
+
+
 def source_digest(kernel: str) -> str | None:
     """sha256 (first 16 hex digits) of the CUDA source file that defines `kernel`."""
     import hashlib
-    for f in sorted(os.listdir(CSRC)):
-        if not f.endswith(".cu"):
-            continue
-        text = open(os.path.join(CSRC, f), "rb").read()
-        if (f"{kernel}(".encode() in text or f"{kernel}<".encode() in text) and b"__global__" in text:
-            return hashlib.sha256(text).hexdigest()[:16]
-    return None
+    path = kernel_source(kernel)
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16] if path else None
 
 
 def measured_traffic(kernel: str, workload: str):
